@@ -1,0 +1,172 @@
+/*
+ * rara.h -- C ABI of the GB300 (sm_103a) RaRa clipped Gaussian-splat renderer.
+ *
+ * The render has four steps (arXiv 2506.20202, "RaRa Clipper"):
+ *   rara_preprocess  per-Gaussian three-way classification against the clip plane
+ *                    (Section 3.2, Eq. 3; Algorithm 1 step 1), EWA projection to a 2D
+ *                    conic (Section 3.4, Eq. 9-10), SH colour, tile rectangle
+ *   rara_bin         one (tile id | depth) key per touched tile, radix-sorted so every tile
+ *                    holds its Gaussians front to back (Section 3.1, "sorted by depth")
+ *   rara_render      per pixel, front-to-back compositing (Eq. 2) of alpha from Eq. 10,
+ *                    with the ray-ellipsoid decay weight (Eq. 4-8, Eq. 11, Eq. 12;
+ *                    Algorithm 1 steps 2-3) for cutoff Gaussians and early termination
+ *   rara_render_frame   the three calls in sequence
+ *
+ * Conventions
+ *   - All device pointers are CUDA device memory on the current device; sizes are
+ *     elements. Arrays are planar (structure of arrays): means[3][n] holds all x, then all
+ *     y, then all z. quats[4][n] is (w, x, y, z), normalised inside. sh[(L+1)^2 * 3][n]:
+ *     plane k*3 + c is real-SH coefficient k = l*l + l + m of colour channel c.
+ *   - Camera: world_to_cam = [R | t] row-major 3x4, OpenCV axes (x right, y down,
+ *     z forward); pixel (i, j) has its centre at (i + 0.5, j + 0.5); fx, fy, cx, cy in
+ *     pixels.
+ *   - Plane: n . x + d = 0, the visible side is where n points (Section 3.2). (n, d) are
+ *     used as given, so pass a unit n for d to be a distance. k_sigma scales the
+ *     ray-traced ellipsoid M = k_sigma R S (3 = the 3-sigma support; Section 3).
+ *   - Every call is asynchronous on the given stream (a cudaStream_t, or NULL for the
+ *     legacy default stream), except that rara_bin waits for the stream once to read the
+ *     number of rendered Gaussians and pairs. The caller keeps inputs alive and unchanged
+ *     until the work queued on the stream has finished.
+ *   - Errors: every call returns a rara_status. RARA_OK is 0. On error nothing further is
+ *     queued and rara_last_error() holds a message. Device-side faults of the bounded
+ *     waits inside the kernels (RARA_ERR_TIMEOUT) are reported by the next rara_bin or
+ *     rara_ctx_sync call. Nothing traps or exits.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef RARA_H
+#define RARA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rara_status {
+    RARA_OK = 0,
+    RARA_ERR_INVALID_ARG = 1, /* null pointer, n < 0, sh_degree outside [0,3], W or H <= 0,
+                                 non-finite camera/plane, unknown mode, call out of order */
+    RARA_ERR_BUDGET = 2,      /* the context's device-memory budget cannot hold this frame */
+    RARA_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+    RARA_ERR_TIMEOUT = 4      /* a bounded device-side wait gave up (results invalid) */
+} rara_status;
+
+typedef enum rara_mode {
+    RARA_MODE_NONE = 0,     /* no clipping: every Gaussian visible */
+    RARA_MODE_HARD = 1,     /* centre test only: invisible iff n.mu + d < 0 (Section 1) */
+    RARA_MODE_RARA = 2,     /* the paper's method (Algorithm 1) */
+    RARA_MODE_RARA_ALL = 3  /* ablation "wo RaRa" (Section 4.3): weight on every
+                               non-invisible Gaussian */
+} rara_mode;
+
+typedef enum rara_label { RARA_INVISIBLE = 0, RARA_VISIBLE = 1, RARA_CUTOFF = 2 } rara_label;
+
+typedef struct rara_gaussians {
+    const float *means;          /* device [3][n] */
+    const float *log_scales;     /* device [3][n], log of the per-axis standard deviation */
+    const float *quats;          /* device [4][n], (w, x, y, z) */
+    const float *opacity_logits; /* device [n], opacity delta = sigmoid(logit) */
+    const float *sh;             /* device [(sh_degree+1)^2 * 3][n] */
+    int64_t n;                   /* number of Gaussians, 0 <= n < 2^31 */
+    int32_t sh_degree;           /* 0..3 */
+} rara_gaussians;
+
+typedef struct rara_camera {
+    float world_to_cam[12]; /* row-major [R | t] */
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} rara_camera;
+
+typedef struct rara_plane {
+    float n[3];
+    float d;
+    float k_sigma; /* > 0 */
+    int32_t mode;  /* rara_mode */
+} rara_plane;
+
+typedef struct rara_ctx rara_ctx;
+
+/* Create a context on the current CUDA device. budget_bytes caps the device scratch the
+ * context may hold (0 = no cap). tile_w x tile_h is the screen tile (16 x 16; the render
+ * kernel uses one 256-thread block per tile, so tile_w * tile_h must be 256).
+ * Returns RARA_ERR_INVALID_ARG for other tile shapes. */
+int rara_ctx_create(size_t budget_bytes, int32_t tile_w, int32_t tile_h, rara_ctx **out);
+
+/* Free every device and pinned buffer the context owns. Waits for the device first.
+ * NULL is accepted. */
+int rara_ctx_destroy(rara_ctx *ctx);
+
+/* Last error message of the context ("" if none). Valid until the next call. */
+const char *rara_last_error(const rara_ctx *ctx);
+
+/* Bytes of device scratch currently held by the context. */
+size_t rara_ctx_bytes(const rara_ctx *ctx);
+
+/* Wait for `stream` and report a device-side wait failure of earlier work. */
+int rara_ctx_sync(rara_ctx *ctx, void *stream);
+
+/* Number of kernel launches this context has queued since creation (all entry points). */
+int64_t rara_ctx_launches(const rara_ctx *ctx);
+
+/* Step (a): classify, project and shade the Gaussians for one camera and plane.
+ * Section 3.2 (Eq. 3), Algorithm 1 step 1, Section 3.4 (Eq. 9-10). Inputs are read on
+ * the stream; the frame state lives in ctx until the next rara_preprocess. */
+int rara_preprocess(rara_ctx *ctx, const rara_gaussians *g, const rara_camera *cam,
+                    const rara_plane *plane, void *stream);
+
+/* Step (b): emit one pair per (Gaussian, touched tile), radix-sort by (tile id, depth),
+ * and build per-tile ranges. Must follow rara_preprocess on the same context. Blocks the
+ * host once (stream synchronisation) to size the pair buffers. */
+int rara_bin(rara_ctx *ctx, void *stream);
+
+/* Steps (c)+(d): composite every pixel. image is device float [3][H][W] (planar RGB),
+ * final_T device float [H][W] (transmittance left after the last blended Gaussian),
+ * n_contrib device uint32 [H][W] (1 + position, within the pixel's tile list, of the last
+ * blended Gaussian; 0 if none). final_T and n_contrib may be NULL. bg is a host float[3].
+ * Eq. 2, Eq. 10-12, Algorithm 1 steps 2-3. Must follow rara_bin. */
+int rara_render(rara_ctx *ctx, const float bg[3], float *image, float *final_T,
+                uint32_t *n_contrib, void *stream);
+
+/* rara_preprocess + rara_bin + rara_render. */
+int rara_render_frame(rara_ctx *ctx, const rara_gaussians *g, const rara_camera *cam,
+                      const rara_plane *plane, const float bg[3], float *image,
+                      float *final_T, uint32_t *n_contrib, void *stream);
+
+/* Counts of the current frame, valid after rara_bin; the render counts refer to the last
+ * rara_render. Waits for the context's last stream to read them. */
+typedef struct rara_frame_info {
+    int64_t n;            /* Gaussians in the frame */
+    int64_t n_rendered;   /* not invisible, not culled, at least one tile */
+    int64_t n_cutoff;     /* rendered and labelled cutoff */
+    int64_t n_pairs;      /* (Gaussian, tile) pairs */
+    int32_t tiles_x, tiles_y;
+    int64_t n_evaluated;  /* (pixel, Gaussian) pairs of the last rara_render inside the
+                             q <= 9 support (alpha computed) */
+    int64_t n_walked;     /* (pixel, Gaussian) pairs whose q was computed, i.e. tile-list
+                             entries visited by pixels still compositing */
+    int64_t n_cut_evaluated; /* evaluated pairs that needed the ray-traced weight */
+} rara_frame_info;
+
+int rara_frame_info_get(rara_ctx *ctx, rara_frame_info *out);
+
+/* Copy per-Gaussian preprocess results into caller device buffers (any may be NULL):
+ * labels uint8[n]; depth float[n] (camera z); mean2d float[2][n]; conic float[3][n]
+ * (a, b, c of [[a,b],[b,c]], the inverse 2D covariance); rgb float[3][n]; opacity float[n];
+ * rect int32[4][n] (inclusive tx0, ty0, tx1, ty1); tiles uint32[n] (0 when culled).
+ * Fields other than labels are defined only where tiles > 0. */
+int rara_frame_gaussians(rara_ctx *ctx, uint8_t *labels, float *depth, float *mean2d,
+                         float *conic, float *rgb, float *opacity, int32_t *rect,
+                         uint32_t *tiles, void *stream);
+
+/* Copy the sorted pair list into caller device buffers: keys uint64[n_pairs]
+ * (tile id << 32 | float bits of the depth), values uint32[n_pairs] (Gaussian index), and
+ * ranges int64[num_tiles][2] ([start, end) of each tile, tile id = ty * tiles_x + tx). */
+int rara_frame_pairs(rara_ctx *ctx, uint64_t *keys, uint32_t *values, int64_t *ranges,
+                     void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RARA_H */

@@ -21,9 +21,11 @@ _lib = None
 INVISIBLE, VISIBLE, CUTOFF = 0, 1, 2
 EV_Q, EV_ALPHA, EV_T, EV_GAUSS, EV_DISC, EV_DEPTH, EV_T1 = 1, 2, 4, 8, 16, 32, 64
 
-# Event tolerances (q relative to 9, alpha relative to 1/255, T relative to 1e-4,
-# 1 - b^2 absolute, class / cull threshold distance in world units).
-DEFAULT_TOL = (2e-4, 2e-4, 2e-3, 1e-3, 1e-6)
+# Event tolerances: q relative to 9, alpha relative to 1/255, T relative to 1e-4,
+# 1 - b^2 absolute, threshold distance (world units), projected-position error (pixels),
+# depth ulps for near-tie flags (0: only identical float32 depths, ordered by index on
+# both sides, so never a hazard). They bound the float32 error of the CUDA path.
+DEFAULT_TOL = (2e-5, 2e-4, 2e-3, 2e-4, 1e-6, 3e-4, 0)
 
 
 def build(force: bool = False) -> str:
@@ -44,7 +46,7 @@ def _load():
         P = C.c_void_p
         lib.orc_preprocess.restype = C.c_int
         lib.orc_preprocess.argtypes = [C.c_int64, P, P, P, P, P, C.c_int, P, C.c_int, C.c_int, P,
-                                       C.c_int, C.c_int, C.c_int] + [P] * 14
+                                       C.c_double, C.c_int, C.c_int, C.c_int] + [P] * 15
         lib.orc_count_pairs.restype = C.c_int64
         lib.orc_count_pairs.argtypes = [C.c_int64, P, P]
         lib.orc_build_keys.restype = C.c_int
@@ -52,7 +54,7 @@ def _load():
         lib.orc_render.restype = C.c_int
         lib.orc_render.argtypes = ([C.c_int64, P, P, P, P, P, P, P, P, P, P, P, P, C.c_int, C.c_int,
                                     P, C.c_double, C.c_int, C.c_int, P, P, P, P, P, C.c_int,
-                                    P, P, P, P])
+                                    C.c_int, C.c_int, P, P, P, P])
         lib.orc_rara_weight.restype = C.c_double
         lib.orc_rara_weight.argtypes = [P, P, P, P, P, C.c_double, P, P]
         lib.orc_sh_colour.restype = None
@@ -91,17 +93,18 @@ def preprocess(scene, cam, plane, tile=(16, 16)) -> dict:
         label=np.zeros(n, np.uint8), culled=np.zeros(n, np.uint8), depth=np.zeros(n),
         mean2d=np.zeros((n, 2)), cov2d=np.zeros((n, 3)), conic=np.zeros((n, 3)),
         rect=np.zeros((n, 4), np.int32), tiles=np.zeros(n, np.int32), rgb=np.zeros((n, 3)),
-        opacity=np.zeros(n), d_ep=np.zeros(n), radius=np.zeros(n),
+        opacity=np.zeros(n), d_ep=np.zeros(n), radius=np.zeros(n), margin_class=np.zeros(n),
         margin_gauss=np.zeros(n), margin_rect=np.zeros(n))
     sc = [_f32(scene.means), _f32(scene.log_scales), _f32(scene.quats),
           _f32(scene.opacity_logits), _f32(scene.sh)]
     c16, p4 = cam16(cam), plane4(plane)
     rc = lib.orc_preprocess(n, *[_p(a) for a in sc], int(scene.sh_degree), _p(c16),
-                            int(cam.width), int(cam.height), _p(p4), int(plane.mode),
-                            int(tile[0]), int(tile[1]),
+                            int(cam.width), int(cam.height), _p(p4), float(np.float32(plane.k_sigma)),
+                            int(plane.mode), int(tile[0]), int(tile[1]),
                             *[_p(out[k]) for k in ("label", "culled", "depth", "mean2d", "cov2d",
                                                    "conic", "rect", "tiles", "rgb", "opacity",
-                                                   "d_ep", "radius", "margin_gauss", "margin_rect")])
+                                                   "d_ep", "radius", "margin_class", "margin_gauss",
+                                                   "margin_rect")])
     assert rc == 0
     out["tiles_x"] = (cam.width + tile[0] - 1) // tile[0]
     out["tiles_y"] = (cam.height + tile[1] - 1) // tile[1]
@@ -125,8 +128,9 @@ def build_keys(pre: dict):
 
 
 def render(scene, pre: dict, cam, plane, bg=(0.0, 0.0, 0.0), binned=None, tol=DEFAULT_TOL,
-           threads: int | None = None):
+           threads: int | None = None, rows=None):
     """Render with the oracle. binned=(keys, vals, ranges) walks tile lists; None = brute force.
+    rows=(begin, end) renders only that band of rows (the rest of the outputs stay zero).
 
     Returns dict(image [3,H,W], T [H,W], n_contrib [H,W] int32, events [H,W] uint8).
     """
@@ -152,7 +156,8 @@ def render(scene, pre: dict, cam, plane, bg=(0.0, 0.0, 0.0), binned=None, tol=DE
                         _p(pre["depth"]), _p(pre["mean2d"]), _p(pre["conic"]), _p(pre["rgb"]),
                         _p(pre["opacity"]), _p(pre["margin_gauss"]), _p(c16), W, H, _p(p4),
                         float(np.float32(plane.k_sigma)), pre["tile"][0], pre["tile"][1], _p(bgv),
-                        kp, vp, rp, _p(tolv), int(threads), _p(image), _p(T), _p(nc), _p(ev))
+                        kp, vp, rp, _p(tolv), int(threads), int(rows[0] if rows else 0),
+                        int(rows[1] if rows else H), _p(image), _p(T), _p(nc), _p(ev))
     assert rc == 0
     return dict(image=image, T=T, n_contrib=nc, events=ev)
 

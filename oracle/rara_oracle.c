@@ -51,7 +51,7 @@
 #define EV_T 4u        /* transmittance near the 1e-4 stop */
 #define EV_GAUSS 8u    /* candidate Gaussian flagged near a class or cull threshold */
 #define EV_DISC 16u    /* ray grazing a cutoff ellipsoid (discriminant near 0) */
-#define EV_DEPTH 32u   /* two candidates whose float32 depths are within 2 ulp */
+#define EV_DEPTH 32u   /* two candidates whose float32 depths differ by a few ulp */
 #define EV_T1 64u      /* camera on the surface of a cutoff ellipsoid */
 
 /* ------------------------------------------------------------------------------------ */
@@ -156,7 +156,10 @@ static void eval_colour(const float *sh, int64_t n, int64_t i, int degree, const
  *   rect[4i..]    inclusive tile rectangle (tx0, ty0, tx1, ty1)
  *   tiles[i]      number of tiles in the rectangle (0 when culled)
  *   rgb[3i..], opacity[i], d_ep[i], radius[i] (= 3 max sigma)
- *   margin_gauss[i]  distance to the nearest class / cull threshold (world units or z)
+ *   margin_class[i]  distance of d_ep to the nearest label threshold (world units)
+ *   margin_gauss[i]  distance to the nearest threshold across which the image is
+ *                    discontinuous: the near cull (z) and, for hard clipping or k_sigma > 3,
+ *                    the label thresholds
  *   margin_rect[i]   distance (pixels) of the rectangle bounds to the nearest tile edge
  * Modes: NONE labels all visible; HARD labels invisible iff d_ep < 0 (centre test);
  * RARA is the paper's three-way rule; RARA_ALL uses the three-way rule but ray-traces
@@ -164,11 +167,12 @@ static void eval_colour(const float *sh, int64_t n, int64_t i, int degree, const
  */
 int orc_preprocess(int64_t n, const float *means, const float *log_scales, const float *quats,
                    const float *opacity_logits, const float *sh, int sh_degree,
-                   const double *cam16, int W, int H, const double *plane4, int mode,
+                   const double *cam16, int W, int H, const double *plane4, double k_sigma, int mode,
                    int tile_w, int tile_h,
                    uint8_t *label, uint8_t *culled, double *depth, double *mean2d, double *cov2d,
                    double *conic, int32_t *rect, int32_t *tiles, double *rgb, double *opacity,
-                   double *d_ep, double *radius, double *margin_gauss, double *margin_rect)
+                   double *d_ep, double *radius, double *margin_class, double *margin_gauss,
+                   double *margin_rect)
 {
     cam_t cam;
     load_cam(cam16, W, H, &cam);
@@ -187,20 +191,26 @@ int orc_preprocess(int64_t n, const float *means, const float *log_scales, const
         d_ep[i] = dep;
         radius[i] = r;
         int lab;
-        double mg = INFINITY;
+        double mc = INFINITY;   /* distance to the label thresholds */
+        double mg = INFINITY;   /* distance to thresholds where the image is discontinuous */
         if (mode == ORC_MODE_NONE) {
             lab = ORC_VISIBLE;
         } else if (mode == ORC_MODE_HARD) {
             lab = dep < 0.0 ? ORC_INVISIBLE : ORC_VISIBLE;
-            mg = fabs(dep);
+            mc = mg = fabs(dep);
         } else {
             if (dep < -r) lab = ORC_INVISIBLE;
             else if (dep > r) lab = ORC_VISIBLE;
             else lab = ORC_CUTOFF;
             if (mode == ORC_MODE_RARA_ALL && lab != ORC_INVISIBLE) lab = ORC_CUTOFF;
-            mg = fmin(fabs(dep - r), fabs(dep + r));
+            mc = fmin(fabs(dep - r), fabs(dep + r));
+            /* With k_sigma <= 3 the traced ellipsoid lies inside the radius-r sphere, so at
+             * d_ep = +r every chord is visible (w = 1) and at d_ep = -r none is (w = 0): the
+             * labels change there but the image does not jump. A larger ellipsoid pokes out. */
+            if (k_sigma > 3.0) mg = mc;
         }
         label[i] = (uint8_t)lab;
+        margin_class[i] = mc;
 
         culled[i] = 1; tiles[i] = 0;
         rect[4 * i + 0] = rect[4 * i + 1] = 0; rect[4 * i + 2] = rect[4 * i + 3] = -1;
@@ -452,8 +462,10 @@ static int f32_ulp_close(float a, float b, int ulps)
  * Render. bg[3]: background colour. Binned mode when keys/vals/ranges are non-NULL: the
  * pixel walks its tile's sorted list; brute mode otherwise: the pixel gathers every
  * rendered Gaussian and sorts by (float32(depth), index). Both apply the same per-pixel
- * rule, so they agree exactly. tol[5] = {q, alpha, T, disc, gauss_margin} tolerances for
- * the event bits. Outputs: image [3, H, W] planar, final_T [H, W], n_contrib [H, W]
+ * rule, so they agree exactly. tol[7] = {q (relative), alpha (relative), T (relative),
+ * 1 - b^2 (absolute), Gaussian threshold margin, position (pixels), depth ulps (0 = equal
+ * float32 depths only, which both sides order by index)} for the event bits. Only rows [row_begin, row_end) are rendered (the others are left as
+ * passed in). Outputs: image [3, H, W] planar, final_T [H, W], n_contrib [H, W]
  * (1 + list position of the last blended Gaussian in binned mode, the count of walked
  * candidates in brute mode), events [H, W].
  */
@@ -464,7 +476,7 @@ int orc_render(int64_t n, const float *means, const float *log_scales, const flo
                const double *cam16, int W, int H, const double *plane4, double k_sigma,
                int tile_w, int tile_h, const double *bg,
                const uint64_t *keys, const uint32_t *vals, const int64_t *ranges,
-               const double *tol, int nthreads,
+               const double *tol, int nthreads, int row_begin, int row_end,
                double *image, double *final_T, int32_t *n_contrib, uint8_t *events)
 {
     cam_t cam;
@@ -473,6 +485,8 @@ int orc_render(int64_t n, const float *means, const float *log_scales, const flo
     const double pn[3] = {plane4[0], plane4[1], plane4[2]}, pd = plane4[3];
     const int binned = keys != NULL && vals != NULL && ranges != NULL;
     const double tol_q = tol[0], tol_a = tol[1], tol_T = tol[2], tol_disc = tol[3], tol_g = tol[4];
+    const double tol_pos = tol[5];
+    const int tol_ulps = (int)tol[6];
     (void)keys;
 
     /* brute-mode candidate list, in (float32 depth, index) order for the whole frame */
@@ -486,8 +500,10 @@ int orc_render(int64_t n, const float *means, const float *log_scales, const flo
         qsort(all, (size_t)nall, sizeof(cand_t), cmp_cand);
     }
 
+    if (row_begin < 0) row_begin = 0;
+    if (row_end > H) row_end = H;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
-    for (int py = 0; py < H; ++py) {
+    for (int py = row_begin; py < row_end; ++py) {
         for (int px = 0; px < W; ++px) {
             const double pxc = px + 0.5, pyc = py + 0.5;
             /* ProjectRay / CameraOrigin (Algorithm 1): ray through the pixel centre */
@@ -513,11 +529,15 @@ int orc_render(int64_t n, const float *means, const float *log_scales, const flo
                 uint32_t i = binned ? vals[k] : all[k].idx;
                 double dx = pxc - mean2d[2 * i], dy = pyc - mean2d[2 * i + 1];
                 double q = conic[3 * i] * dx * dx + 2.0 * conic[3 * i + 1] * dx * dy + conic[3 * i + 2] * dy * dy;
-                if (fabs(q - 9.0) <= tol_q * 9.0) ev |= EV_Q;
+                /* q near 9: relative conic error plus a position error tol_pos (pixels)
+                 * amplified by the splat's inverse size, dq ~ 2 sqrt(q) |conic|^(1/2) dpos */
+                double tq = tol_q * 9.0 + 6.0 * tol_pos * sqrt(fabs(conic[3 * i]) + fabs(conic[3 * i + 2]));
+                if (fabs(q - 9.0) <= tq) ev |= EV_Q;
                 if (q > 9.0) continue;            /* outside the 3-sigma support */
                 if (margin_gauss[i] <= tol_g) ev |= EV_GAUSS;
                 float fd = (float)depth[i];
-                if (have_prev && f32_ulp_close(fd, prev_depth, 2)) ev |= EV_DEPTH;
+                if (tol_ulps > 0 && have_prev && fd != prev_depth && f32_ulp_close(fd, prev_depth, tol_ulps))
+                    ev |= EV_DEPTH;
                 prev_depth = fd; have_prev = 1;
                 /* Eq. 10 with the normalisation dropped */
                 double a0 = opacity[i] * exp(-0.5 * q);

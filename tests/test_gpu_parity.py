@@ -1,0 +1,161 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Bars: labels, tile counts, rectangles and per-tile key order bit-exact except Gaussians
+within 1e-6 of a class threshold or 2e-3 px of a tile edge (counted); depth keys within
+2 ulp; images within max-abs 2e-3 and mean-abs 1e-4 per channel on pixels whose oracle
+sequence is not within tolerance of a discontinuity of the method (counted, bounded).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2506_20202_gb300 import scenes
+from tests import parity
+from tests.helpers import axis_camera, make_scene, plane
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_20202_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def full_check(scene, cam, pl, bg=(0.0, 0.0, 0.0), rows=None, max_flag_frac=0.05):
+    report = {}
+    gpu = parity.gpu_frame(scene, cam, pl, bg)
+    pre = oracle.preprocess(scene, cam, pl)
+    kvr = oracle.build_keys(pre)
+    parity.check_gaussians(pre, gpu["g"], report)
+    parity.check_pairs(pre, kvr, gpu, report)
+    ref = oracle.render(scene, pre, cam, pl, bg, kvr, rows=rows)
+    parity.check_image(pre, ref, gpu, report, rows=rows, max_flag_frac=max_flag_frac)
+    assert gpu["info"]["n_pairs"] == report["pairs_gpu"]
+    print(report)
+    return report, gpu, ref
+
+
+def test_small_uniform_scene():
+    """10k Gaussians, SH 0, 256x256, plane through the origin with a seeded normal."""
+    scene, cam, pl = scenes.small_uniform_workload()
+    rep, gpu, ref = full_check(scene, cam, pl)
+    assert gpu["info"]["n_cutoff"] > 100
+    assert rep["tiles_exact"] >= rep["tiles"] - 5
+
+
+@pytest.mark.parametrize("mode", [scenes.MODE_NONE, scenes.MODE_HARD, scenes.MODE_RARA_ALL])
+def test_other_modes(mode):
+    scene, cam, pl = scenes.small_uniform_workload(n=4000, width=160, height=128, seed=2)
+    pl.mode = mode
+    full_check(scene, cam, pl, bg=(0.2, 0.1, 0.05))
+
+
+@pytest.mark.parametrize("n,wh", [(1, (250, 198)), (37, (33, 17)), (1000, (250, 198)), (2561, (17, 250))])
+def test_ragged_sizes(n, wh):
+    scene, cam, pl = scenes.small_uniform_workload(n=n, width=wh[0], height=wh[1], seed=n)
+    full_check(scene, cam, pl, bg=(0.3, 0.3, 0.3))
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3])
+def test_sh_degrees(degree):
+    scene = scenes.uniform_scene(3000, seed=11, sh_degree=degree)
+    cam = scenes.look_at_camera((0.4, -0.6, -2.8), (0.0, 0.0, 0.0), 128, 112, 60.0)
+    pl = scenes.Plane(np.float32(scenes.random_unit_normal(12)), 0.1, 3.0, scenes.MODE_RARA)
+    full_check(scene, cam, pl)
+
+
+def test_k_sigma_one():
+    scene, cam, pl = scenes.small_uniform_workload(n=3000, width=128, height=128, seed=13)
+    pl.k_sigma = 1.0
+    full_check(scene, cam, pl)
+
+
+def test_empty_scene_is_background():
+    scene = scenes.uniform_scene(5, seed=1).subset(np.arange(0))
+    cam = scenes.look_at_camera((0, 0, -3), (0, 0, 0), 40, 24)
+    gpu = parity.gpu_frame(scene, cam, scenes.Plane(np.float32([0, 0, 1]), 0.0), bg=(0.1, 0.2, 0.3), export=False)
+    for c, v in enumerate((0.1, 0.2, 0.3)):
+        assert np.all(gpu["image"][c] == np.float32(v))
+    assert np.all(gpu["T"] == 1.0) and np.all(gpu["n_contrib"] == 0)
+
+
+def test_everything_culled_or_invisible_is_background():
+    scene, cam, pl = scenes.small_uniform_workload(n=3000, width=96, height=64, seed=3)
+    bg = (0.25, 0.5, 0.75)
+    back = scenes.look_at_camera((0, 0, -3), (0, 0, -6), 96, 64)   # looks away from the scene
+    g1 = parity.gpu_frame(scene, back, pl, bg, export=False)
+    far = scenes.Plane(np.float32([0.3, 0.5, 0.8]), -1e20, 3.0, scenes.MODE_RARA)
+    g2 = parity.gpu_frame(scene, cam, far, bg, export=False)
+    for g in (g1, g2):
+        for c in range(3):
+            assert np.all(g["image"][c] == np.float32(bg[c]))
+        assert np.all(g["T"] == 1.0)
+
+
+def test_plane_at_infinity_bit_identical_to_unclipped():
+    """Section 4.3 / Table 2: no cutoff Gaussian exists, so the clipped render equals the
+    unclipped one exactly (for RaRa and for the weight-on-all ablation)."""
+    scene, cam, _ = scenes.small_uniform_workload(n=6000, width=200, height=150, seed=4)
+    nrm = np.float32(scenes.random_unit_normal(9))
+    ref = parity.gpu_frame(scene, cam, scenes.Plane(nrm, 1e20, 3.0, scenes.MODE_NONE), export=False)
+    for mode in (scenes.MODE_RARA, scenes.MODE_RARA_ALL):
+        got = parity.gpu_frame(scene, cam, scenes.Plane(nrm, 1e20, 3.0, mode), export=False)
+        assert np.array_equal(got["image"], ref["image"]) and np.array_equal(got["T"], ref["T"])
+
+
+def test_deterministic_repeat():
+    scene, cam, pl = scenes.small_uniform_workload(n=8000, width=160, height=160, seed=5)
+    a = parity.gpu_frame(scene, cam, pl, export=True)
+    b = parity.gpu_frame(scene, cam, pl, export=True)
+    assert np.array_equal(a["image"], b["image"]) and np.array_equal(a["keys"], b["keys"])
+    assert np.array_equal(a["vals"], b["vals"])
+
+
+def test_stacked_cutoff_closed_form():
+    """One cutoff Gaussian centred on a pixel, tilted plane through its centre: the pixel's
+    ray bisects the chord, alpha = delta / 2 (Eq. 11 with L_vis = L / 2)."""
+    cam = axis_camera(64, 64, 64.0)
+    z = 2.0
+    mu = [(30 + 0.5 - 32) * z / 64.0, (33 + 0.5 - 32) * z / 64.0, z]
+    rng = np.random.default_rng(3)
+    n = rng.standard_normal(3)
+    n /= np.linalg.norm(n)
+    sc = make_scene([mu], [[0.03, 0.05, 0.02]], quats=[rng.standard_normal(4)], opacity=[0.5])
+    mu32 = np.float32(mu).astype(np.float64)
+    pl = plane(n, float(-(np.float32(n).astype(np.float64) @ mu32)))
+    g = parity.gpu_frame(sc, cam, pl, export=False)
+    delta = 1 / (1 + np.exp(-np.float32(np.log(0.5 / 0.5))))
+    assert g["T"][33, 30] == pytest.approx(1 - 0.5 * delta, abs=1e-4)
+
+
+def test_hair_strand_scene():
+    """Anisotropic strands (1:1:40) with a plane cutting 30-50% of them (reduced count)."""
+    scene, nrm, d = scenes.hair_scene(curves=1500, segments=50, seed=2)
+    cam = scenes.look_at_camera((0.2, -0.3, -3.2), (0.0, 0.3, 0.0), 256, 256, 60.0)
+    pl = scenes.Plane(np.float32(nrm), float(d), 3.0, scenes.MODE_RARA)
+    rep, gpu, ref = full_check(scene, cam, pl, max_flag_frac=0.08)
+    frac = gpu["info"]["n_cutoff"] / max(1, gpu["info"]["n_rendered"])
+    assert 0.2 <= frac <= 0.6, frac
+
+
+def test_shell_scene():
+    scene = scenes.shells_scene(per_shell=30_000, seed=1)
+    cam = scenes.look_at_camera((0.5, -0.4, -2.6), (0.0, 0.0, 0.0), 192, 160, 60.0)
+    pl = scenes.Plane(np.float32(scenes.random_unit_normal(21)), 0.05, 3.0, scenes.MODE_RARA)
+    full_check(scene, cam, pl)
+
+
+def test_general_scene_full_size_sampled_rows():
+    """1M Gaussians, SH 3, 1920x1080 (the benchmark workload) at the middle sweep offset:
+    every label, tile count and key checked; the image checked on a band of rows."""
+    scene, cam, planes = scenes.general_workload()
+    pl = planes[8]
+    rep, gpu, ref = full_check(scene, cam, pl, rows=(520, 552), max_flag_frac=0.05)
+    assert rep["pixels"] == 32 * 1920
+    assert gpu["info"]["n_cutoff"] > 1000
