@@ -165,6 +165,32 @@ int rara_frame_gaussians(rara_ctx *ctx, uint8_t *labels, float *depth, float *me
 int rara_frame_pairs(rara_ctx *ctx, uint64_t *keys, uint32_t *values, int64_t *ranges,
                      void *stream);
 
+/* Allocation-free variant of rara_render_frame (the paper has no counterpart).
+ *
+ * For callers that cannot call cudaMalloc: a plug-in running inside another engine's
+ * frame loop or a host callback, where an allocation would block or is not allowed, or a
+ * process whose device memory belongs to another allocator. The call allocates nothing
+ * (no cudaMalloc, cudaFree, pinned or heap memory): every scratch buffer is carved from one
+ * file-scope static __device__ array of about 18 MB, which each GPU that loads the library
+ * holds until the process exits. The caller passes inputs and outputs as for
+ * rara_render_frame, with the same layouts and results.
+ *
+ * Limits: n <= 65536 Gaussians, at most 2^19 (Gaussian, tile) pairs and 16384 tiles (for
+ * example 2048 x 2048 pixels). Larger inputs return RARA_ERR_BUDGET before any work is
+ * queued (the pair limit is checked after the preprocess, which waits for the stream).
+ * Other errors: RARA_ERR_INVALID_ARG, RARA_ERR_CUDA, RARA_ERR_TIMEOUT as above; there is no
+ * context, so no message is kept.
+ *
+ * The first call on a device resolves the static array's device address (set-up, once per
+ * device, with that device current); make that first call before any stream capture.
+ * Every call on a device shares the one array and leaves the last call's contents in it:
+ * calls that overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller. The call waits for the stream twice (to read the pair count).
+ * It is not thread-safe. */
+int rara_render_frame_noalloc(const rara_gaussians *g, const rara_camera *cam, const rara_plane *plane,
+                              const float bg[3], float *image, float *final_T, uint32_t *n_contrib,
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -406,3 +406,113 @@ int rara_frame_pairs(rara_ctx *c, uint64_t *keys, uint32_t *values, int64_t *ran
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// Allocation-free frame render (no counterpart in the paper).
+//
+// For callers that cannot allocate device memory: code running inside another engine's
+// render loop or a host callback where cudaMalloc would block or is not permitted, or
+// a process whose device memory is owned entirely by someone else's allocator. All scratch
+// lives in one file-scope static __device__ array, which every GPU that loads this library
+// holds until the process exits.
+// ------------------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kStaticMaxGaussians = 1 << 16;
+constexpr int kStaticMaxPairs = 1 << 19;
+constexpr int kStaticMaxTiles = 1 << 14;
+constexpr int kStaticMaxDevices = 64;
+
+constexpr size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Carve-out of the static array, in bytes.
+constexpr size_t kSzCounters = align256(sizeof(Counters));
+constexpr size_t kSzLabels = align256(kStaticMaxGaussians);
+constexpr size_t kSzU32G = align256((size_t)kStaticMaxGaussians * 4);
+constexpr size_t kSzRect = align256((size_t)kStaticMaxGaussians * 8);
+constexpr size_t kSzRec = align256((size_t)kStaticMaxGaussians * sizeof(SplatRec));
+constexpr size_t kSzCut = align256((size_t)kStaticMaxGaussians * sizeof(CutRec));
+constexpr size_t kSzLookG = align256((size_t)(kStaticMaxGaussians / kBlock + 1) * 8);
+constexpr size_t kSzU32P = align256((size_t)kStaticMaxPairs * 4);
+constexpr size_t kSzRanges = align256((size_t)kStaticMaxTiles * sizeof(int2));
+// sort scratch for 4 digit passes over kStaticMaxPairs keys, sized for partitions as small as
+// 1024 keys; static_setup checks it against the sort's own requirement
+constexpr size_t kSzSort = align256(4 * (4 * 256 + 64 + 4 * (size_t)((kStaticMaxPairs + 1023) / 1024) * 256));
+constexpr size_t kStaticBytes = kSzCounters + kSzLabels + kSzU32G + kSzRect + kSzRec + kSzCut + 4 * kSzU32G +
+                                kSzLookG + 4 * kSzU32P + kSzLookG + kSzRanges + kSzSort;
+
+static __device__ __align__(256) unsigned char g_rara_static_scratch[kStaticBytes];
+
+rara_ctx g_static_ctx[kStaticMaxDevices];
+Counters g_static_host_counters[kStaticMaxDevices];
+bool g_static_ready[kStaticMaxDevices];
+
+// Once per device, with that device current: resolve the device address of the static
+// array (its host-side name is only a stand-in) and carve the context's buffers from it.
+int static_setup(int dev)
+{
+    if (g_static_ready[dev]) return RARA_OK;
+    if (sort_scratch_bytes(kStaticMaxPairs, 32) > kSzSort) return RARA_ERR_BUDGET;
+    void *base = nullptr;
+    if (cudaGetSymbolAddress(&base, g_rara_static_scratch) != cudaSuccess || !base) {
+        cudaGetLastError();
+        return RARA_ERR_CUDA;
+    }
+    rara_ctx *c = &g_static_ctx[dev];
+    unsigned char *p = (unsigned char *)base;
+    auto take = [&](DevBuf &b, size_t bytes) { b.p = p; b.cap = bytes; p += bytes; };
+    take(c->counters, kSzCounters);
+    take(c->labels, kSzLabels);
+    take(c->tiles, kSzU32G);
+    take(c->rect, kSzRect);
+    take(c->rec, kSzRec);
+    take(c->cut, kSzCut);
+    take(c->ckeys, kSzU32G);
+    take(c->cvals, kSzU32G);
+    take(c->ckeys_alt, kSzU32G);
+    take(c->cvals_alt, kSzU32G);
+    take(c->lookback_g, kSzLookG);
+    take(c->pkeys, kSzU32P);
+    take(c->pvals, kSzU32P);
+    take(c->pkeys_alt, kSzU32P);
+    take(c->pvals_alt, kSzU32P);
+    take(c->lookback_p, kSzLookG);
+    take(c->ranges, kSzRanges);
+    take(c->sort_scratch, kSzSort);
+    c->budget = 0;
+    c->device = dev;
+    c->h_counters = &g_static_host_counters[dev];
+    g_static_ready[dev] = true;
+    return RARA_OK;
+}
+
+}  // namespace
+
+extern "C" int rara_render_frame_noalloc(const rara_gaussians *g, const rara_camera *cam, const rara_plane *plane,
+                                         const float bg[3], float *image, float *final_T, uint32_t *n_contrib,
+                                         void *stream)
+{
+    if (!g || !cam || !plane || !bg || !image) return RARA_ERR_INVALID_ARG;
+    if (g->n < 0 || g->n > kStaticMaxGaussians) return RARA_ERR_BUDGET;
+    if (cam->width <= 0 || cam->height <= 0) return RARA_ERR_INVALID_ARG;
+    const int64_t tiles = (int64_t)((cam->width + kTile - 1) / kTile) * ((cam->height + kTile - 1) / kTile);
+    if (tiles > kStaticMaxTiles) return RARA_ERR_BUDGET;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return RARA_ERR_CUDA;
+    int rc = static_setup(dev);
+    if (rc) return rc;
+    rara_ctx *c = &g_static_ctx[dev];
+    rc = rara_preprocess(c, g, cam, plane, stream);
+    if (rc) return rc;
+    // The pair count is known only after the preprocess: wait for it and refuse frames whose
+    // pairs exceed the static buffers, before rara_bin would need more.
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return RARA_ERR_CUDA;
+    if (c->h_counters->n_pairs > (unsigned long long)kStaticMaxPairs) {
+        c->stage = 0;
+        return RARA_ERR_BUDGET;
+    }
+    rc = rara_bin(c, stream);
+    if (rc) return rc;
+    return rara_render(c, bg, image, final_T, n_contrib, stream);
+}

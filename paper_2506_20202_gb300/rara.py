@@ -66,6 +66,8 @@ SIGNATURES = {
     "rara_frame_info_get": (C.c_int, [_P, C.POINTER(rara_frame_info)]),
     "rara_frame_gaussians": (C.c_int, [_P] * 10),
     "rara_frame_pairs": (C.c_int, [_P] * 5),
+    "rara_render_frame_noalloc": (C.c_int, [C.POINTER(rara_gaussians), C.POINTER(rara_camera),
+                                            C.POINTER(rara_plane), C.POINTER(C.c_float), _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -207,6 +209,17 @@ def rara_render_frame(ctx, gaussians: GaussianTensors, cam, plane, bg, image, fi
     bgv = (C.c_float * 3)(*[float(x) for x in bg])
     _check(ctx, load().rara_render_frame(ctx, C.byref(g), C.byref(c), C.byref(p), bgv, _ptr(image),
                                          _ptr(final_T), _ptr(n_contrib), _stream(stream)))
+
+
+def rara_render_frame_noalloc(gaussians: GaussianTensors, cam, plane, bg, image, final_T=None, n_contrib=None,
+                              stream=None):
+    """Allocation-free frame render (static scratch, see include/rara.h); raises RaraError."""
+    g, c, p = gaussians.c_struct(), camera_struct(cam), plane_struct(plane)
+    bgv = (C.c_float * 3)(*[float(x) for x in bg])
+    rc = load().rara_render_frame_noalloc(C.byref(g), C.byref(c), C.byref(p), bgv, _ptr(image), _ptr(final_T),
+                                          _ptr(n_contrib), _stream(stream))
+    if rc != RARA_OK:
+        raise RaraError(rc, "rara_render_frame_noalloc failed (RARA_ERR_BUDGET: input beyond the static limits)")
 
 
 def rara_frame_info_get(ctx) -> dict:
