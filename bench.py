@@ -37,10 +37,11 @@ METRIC = "clipped frames/sec at 1080p/1M Gaussians + p50/p99 latency, batched vs
 UNIT = "frames/s"
 
 # Algorithmic FP32 work of the render kernel per unit (see the design notes):
+#   rectangle test   min of q over a warp's 8x4 pixel box (4 edges)  36 FLOP (one per warp and entry)
 #   walked pair      dx, dy and the conic quadratic form q            9 FLOP
 #   in-support pair  alpha = delta exp(-q/2), clamp, T update, RGB   12 FLOP + 1 MUFU (ex2)
 #   cutoff pair      ray-traced decay weight (Eq. 4-8, 11)           60 FLOP + 3 MUFU
-FLOP_WALKED, FLOP_EVAL, FLOP_CUT = 9, 12, 60
+FLOP_TEST, FLOP_WALKED, FLOP_EVAL, FLOP_CUT = 36, 9, 12, 60
 SMS, FP32_LANES = 152, 128  # GB300: 152 SMs x 128 FP32 lanes, FMA = 2 FLOP
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "render_fwd_general_1080p.txt")
@@ -331,8 +332,8 @@ def run_ours(args):
     peaks, peak_kind = measured_peaks()
     stage_ms = {"preprocess": statistics.mean(t_pre), "bin": statistics.mean(t_bin),
                 "render": statistics.mean(t_ren)}
-    flop = [FLOP_WALKED * c["n_walked"] + FLOP_EVAL * c["n_evaluated"] + FLOP_CUT * c["n_cut_evaluated"]
-            for c in counts]
+    flop = [FLOP_TEST * c["n_tested"] + FLOP_WALKED * c["n_walked"] + FLOP_EVAL * c["n_evaluated"]
+            + FLOP_CUT * c["n_cut_evaluated"] for c in counts]
     ren_by_plane = [statistics.mean(t_ren[i::len(planes)]) for i in range(len(planes))]
     achieved = statistics.mean([f / (t * 1e-3) for f, t in zip(flop, ren_by_plane)]) / 1e12
     sm_max = float(clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
@@ -341,7 +342,8 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": traffic_for_current_kernel(),
                 "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES} lanes x 2 FLOP x {sm_max:.0f} MHz "
                               f"(recipe unit counts, max SM clock)",
-                "per_frame_units": {"walked": statistics.mean(c["n_walked"] for c in counts),
+                "per_frame_units": {"tested": statistics.mean(c["n_tested"] for c in counts),
+                                    "walked": statistics.mean(c["n_walked"] for c in counts),
                                     "evaluated": statistics.mean(c["n_evaluated"] for c in counts),
                                     "cut_evaluated": statistics.mean(c["n_cut_evaluated"] for c in counts)}}
     # HBM view of the other stages (context)

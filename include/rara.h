@@ -106,6 +106,15 @@ size_t rara_ctx_bytes(const rara_ctx *ctx);
 /* Wait for `stream` and report a device-side wait failure of earlier work. */
 int rara_ctx_sync(rara_ctx *ctx, void *stream);
 
+/* Render scheduling knobs of the context. The render splits a tile whose list holds at
+ * least 2^(split2_bits - 1) entries into 2 work items of 16x8 pixels with 2 lanes per
+ * pixel, and one with at least 2^(split4_bits - 1) entries into 4 items of 16x4 pixels with 4
+ * lanes per pixel (split4 wins when both apply); the lanes of a pixel combine consecutive
+ * entries, which shortens the pixel's dependent chain. Values are clamped to [0, 33]
+ * (0: always split, 33: never). Images do not depend on them beyond the float rounding
+ * order of the compositing sums. Defaults: 11 and 12. */
+int rara_ctx_set_tuning(rara_ctx *ctx, int32_t split2_bits, int32_t split4_bits);
+
 /* Number of kernel launches this context has queued since creation (all entry points). */
 int64_t rara_ctx_launches(const rara_ctx *ctx);
 
@@ -146,6 +155,7 @@ typedef struct rara_frame_info {
     int64_t n_walked;     /* (pixel, Gaussian) pairs whose q was computed, i.e. tile-list
                              entries visited by pixels still compositing */
     int64_t n_cut_evaluated; /* evaluated pairs that needed the ray-traced weight */
+    int64_t n_tested;     /* (warp rectangle, Gaussian) culling tests of the last render */
 } rara_frame_info;
 
 int rara_frame_info_get(rara_ctx *ctx, rara_frame_info *out);

@@ -34,11 +34,14 @@ struct rara_ctx {
     int64_t n_rendered = 0, n_pairs = 0, n_cutoff = 0;
     cudaStream_t last_stream = nullptr;
 
+    int sm_count = 0, render_bpsm = 0;
+    int split2_bits = 11, split4_bits = 12;  // heavy-tile split thresholds (list length bit counts)
+
     // per-Gaussian
-    DevBuf labels, tiles, rect, rec, cut, ckeys, cvals, ckeys_alt, cvals_alt, lookback_g;
+    DevBuf labels, tiles, rect, rec, cut, depth, ckeys, cvals, ckeys_alt, cvals_alt, lookback_g;
     // per-pair
     DevBuf pkeys, pvals, pkeys_alt, pvals_alt, lookback_p;
-    DevBuf ranges, sort_scratch, counters;
+    DevBuf ranges, tile_order, sort_scratch, counters;
     Counters *h_counters = nullptr;  // pinned
     const uint32_t *sorted_gauss = nullptr;  // depth-ordered indices (ckeys/cvals or alt)
     const uint32_t *sorted_tile_keys = nullptr;
@@ -145,9 +148,9 @@ int rara_ctx_destroy(rara_ctx *c)
 {
     if (!c) return RARA_OK;
     cudaDeviceSynchronize();
-    DevBuf *all[] = {&c->labels, &c->tiles, &c->rect, &c->rec, &c->cut, &c->ckeys, &c->cvals, &c->ckeys_alt,
-                     &c->cvals_alt, &c->lookback_g, &c->pkeys, &c->pvals, &c->pkeys_alt, &c->pvals_alt,
-                     &c->lookback_p, &c->ranges, &c->sort_scratch, &c->counters};
+    DevBuf *all[] = {&c->labels, &c->tiles, &c->rect, &c->rec, &c->cut, &c->depth, &c->ckeys, &c->cvals,
+                     &c->ckeys_alt, &c->cvals_alt, &c->lookback_g, &c->pkeys, &c->pvals, &c->pkeys_alt,
+                     &c->pvals_alt, &c->lookback_p, &c->ranges, &c->tile_order, &c->sort_scratch, &c->counters};
     for (DevBuf *b : all) release(c, *b);
     if (c->h_counters) cudaFreeHost(c->h_counters);
     delete c;
@@ -159,6 +162,14 @@ const char *rara_last_error(const rara_ctx *c) { return c ? c->err : "null conte
 size_t rara_ctx_bytes(const rara_ctx *c) { return c ? c->held : 0; }
 
 int64_t rara_ctx_launches(const rara_ctx *c) { return c ? c->launches : 0; }
+
+int rara_ctx_set_tuning(rara_ctx *c, int32_t split2_bits, int32_t split4_bits)
+{
+    if (!c) return RARA_ERR_INVALID_ARG;
+    c->split2_bits = split2_bits < 0 ? 0 : (split2_bits > 33 ? 33 : split2_bits);
+    c->split4_bits = split4_bits < 0 ? 0 : (split4_bits > 33 ? 33 : split4_bits);
+    return RARA_OK;
+}
 
 int rara_ctx_sync(rara_ctx *c, void *stream)
 {
@@ -211,6 +222,7 @@ int rara_preprocess(rara_ctx *c, const rara_gaussians *g, const rara_camera *cam
     if ((rc = ensure(c, c->labels, nn, "labels")) || (rc = ensure(c, c->tiles, nn * 4, "tiles")) ||
         (rc = ensure(c, c->rect, nn * 8, "rect")) || (rc = ensure(c, c->rec, nn * sizeof(SplatRec), "records")) ||
         (rc = ensure(c, c->cut, nn * sizeof(CutRec), "cutoff records")) ||
+        (rc = ensure(c, c->depth, nn * 4, "depth")) ||
         (rc = ensure(c, c->ckeys, nn * 4, "depth keys")) || (rc = ensure(c, c->cvals, nn * 4, "depth values")) ||
         (rc = ensure(c, c->ckeys_alt, nn * 4, "depth keys alt")) ||
         (rc = ensure(c, c->cvals_alt, nn * 4, "depth values alt")) ||
@@ -238,6 +250,7 @@ int rara_preprocess(rara_ctx *c, const rara_gaussians *g, const rara_camera *cam
     a.rect = (uint2 *)c->rect.p;
     a.rec = (SplatRec *)c->rec.p;
     a.cut = (CutRec *)c->cut.p;
+    a.depth = (float *)c->depth.p;
     a.ckeys = (uint32_t *)c->ckeys.p;
     a.cvals = (uint32_t *)c->cvals.p;
     a.lookback = (unsigned long long *)c->lookback_g.p;
@@ -283,6 +296,7 @@ int rara_bin(rara_ctx *c, void *stream)
         (rc = ensure(c, c->pvals_alt, pp * 4, "pair values alt")) ||
         (rc = ensure(c, c->lookback_p, (size_t)(eblocks + 1) * 8, "emit scan words")) ||
         (rc = ensure(c, c->ranges, (size_t)c->num_tiles * sizeof(int2), "ranges")) ||
+        (rc = ensure(c, c->tile_order, (size_t)c->num_tiles * 16, "render items")) ||
         (rc = ensure(c, c->sort_scratch, sbytes, "sort scratch")))
         return rc;
     uint32_t *status = &((Counters *)c->counters.p)->status;
@@ -323,6 +337,11 @@ int rara_bin(rara_ctx *c, void *stream)
         return rc;
     launch_ranges(c->sorted_tile_keys, np, c->num_tiles, (int2 *)c->ranges.p, s);
     if ((rc = launched(c, "ranges", np > 0))) return rc;
+
+    // 5. heaviest-first order of the tiles for the render's persistent blocks
+    launch_tile_order((const int2 *)c->ranges.p, c->num_tiles, c->split2_bits, c->split4_bits,
+                      (uint32_t *)c->tile_order.p, (Counters *)c->counters.p, s);
+    if ((rc = launched(c, "tile order", c->num_tiles > 0))) return rc;
     c->last_stream = s;
     c->stage = 2;
     return RARA_OK;
@@ -334,8 +353,18 @@ int rara_render(rara_ctx *c, const float bg[3], float *image, float *final_T, ui
     if (c->stage < 2) return fail(c, RARA_ERR_INVALID_ARG, "rara_render called before rara_bin");
     if (!bg || !image) return fail(c, RARA_ERR_INVALID_ARG, "null bg or image");
     cudaStream_t s = (cudaStream_t)stream;
+    if (c->sm_count == 0) {
+        if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+            c->sm_count < 1) {
+            cudaGetLastError();
+            c->sm_count = 1;
+        }
+        c->render_bpsm = render_blocks_per_sm();
+    }
     RenderArgs a;
     a.ranges = (const int2 *)c->ranges.p;
+    a.tile_order = (const uint32_t *)c->tile_order.p;
+    a.num_tiles = c->num_tiles;
     a.pair_vals = c->sorted_pair_vals;
     a.rec = (const SplatRec *)c->rec.p;
     a.cut = (const CutRec *)c->cut.p;
@@ -348,10 +377,12 @@ int rara_render(rara_ctx *c, const float bg[3], float *image, float *final_T, ui
     a.n_contrib = n_contrib;
     a.counters = (Counters *)c->counters.p;
     int rc;
-    if ((rc = check_cuda(c, cudaMemsetAsync(&a.counters->n_evaluated, 0, 3 * sizeof(unsigned long long), s),
+    if ((rc = check_cuda(c, cudaMemsetAsync(&a.counters->n_evaluated, 0, kRenderCounterBytes, s),
                          "memset render counters")))
         return rc;
-    launch_render(a, c->num_tiles, s);
+    const int slots = c->sm_count * c->render_bpsm;
+    const int grid = 4 * c->num_tiles < slots ? 4 * c->num_tiles : slots;
+    launch_render(a, grid, s);
     if ((rc = launched(c, "render launch", c->num_tiles > 0))) return rc;
     c->last_stream = s;
     return RARA_OK;
@@ -382,6 +413,7 @@ int rara_frame_info_get(rara_ctx *c, rara_frame_info *out)
     out->n_evaluated = (int64_t)c->h_counters->n_evaluated;
     out->n_walked = (int64_t)c->h_counters->n_walked;
     out->n_cut_evaluated = (int64_t)c->h_counters->n_cut_evaluated;
+    out->n_tested = (int64_t)c->h_counters->n_tested;
     return RARA_OK;
 }
 
@@ -391,7 +423,8 @@ int rara_frame_gaussians(rara_ctx *c, uint8_t *labels, float *depth, float *mean
     if (!c) return RARA_ERR_INVALID_ARG;
     if (c->stage < 1) return fail(c, RARA_ERR_INVALID_ARG, "no preprocessed frame");
     launch_export_gaussians(c->n, (const uint8_t *)c->labels.p, (const uint32_t *)c->tiles.p,
-                            (const uint2 *)c->rect.p, (const SplatRec *)c->rec.p, labels, depth, mean2d, conic,
+                            (const uint2 *)c->rect.p, (const SplatRec *)c->rec.p, (const float *)c->depth.p, labels,
+                            depth, mean2d, conic,
                             rgb, opacity, rect, tiles, (cudaStream_t)stream);
     return launched(c, "export gaussians", c->n > 0);
 }
@@ -400,7 +433,7 @@ int rara_frame_pairs(rara_ctx *c, uint64_t *keys, uint32_t *values, int64_t *ran
 {
     if (!c) return RARA_ERR_INVALID_ARG;
     if (c->stage < 2) return fail(c, RARA_ERR_INVALID_ARG, "no binned frame");
-    launch_export_pairs((int)c->n_pairs, c->sorted_tile_keys, c->sorted_pair_vals, (const SplatRec *)c->rec.p,
+    launch_export_pairs((int)c->n_pairs, c->sorted_tile_keys, c->sorted_pair_vals, (const float *)c->depth.p,
                         (const int2 *)c->ranges.p, c->num_tiles, keys, values, ranges, (cudaStream_t)stream);
     return launched(c, "export pairs", 1);
 }
@@ -439,8 +472,9 @@ constexpr size_t kSzRanges = align256((size_t)kStaticMaxTiles * sizeof(int2));
 // sort scratch for 4 digit passes over kStaticMaxPairs keys, sized for partitions as small as
 // 1024 keys; static_setup checks it against the sort's own requirement
 constexpr size_t kSzSort = align256(4 * (4 * 256 + 64 + 4 * (size_t)((kStaticMaxPairs + 1023) / 1024) * 256));
-constexpr size_t kStaticBytes = kSzCounters + kSzLabels + kSzU32G + kSzRect + kSzRec + kSzCut + 4 * kSzU32G +
-                                kSzLookG + 4 * kSzU32P + kSzLookG + kSzRanges + kSzSort;
+constexpr size_t kSzOrder = align256((size_t)kStaticMaxTiles * 16);
+constexpr size_t kStaticBytes = kSzCounters + kSzLabels + kSzU32G + kSzRect + kSzRec + kSzCut + kSzU32G +
+                                4 * kSzU32G + kSzLookG + 4 * kSzU32P + kSzLookG + kSzRanges + kSzOrder + kSzSort;
 
 static __device__ __align__(256) unsigned char g_rara_static_scratch[kStaticBytes];
 
@@ -468,6 +502,7 @@ int static_setup(int dev)
     take(c->rect, kSzRect);
     take(c->rec, kSzRec);
     take(c->cut, kSzCut);
+    take(c->depth, kSzU32G);
     take(c->ckeys, kSzU32G);
     take(c->cvals, kSzU32G);
     take(c->ckeys_alt, kSzU32G);
@@ -479,6 +514,7 @@ int static_setup(int dev)
     take(c->pvals_alt, kSzU32P);
     take(c->lookback_p, kSzLookG);
     take(c->ranges, kSzRanges);
+    take(c->tile_order, kSzOrder);
     take(c->sort_scratch, kSzSort);
     c->budget = 0;
     c->device = dev;

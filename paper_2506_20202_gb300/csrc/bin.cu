@@ -75,7 +75,8 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, int n, int num_tiles
 }
 
 __global__ void k_export_gaussians(int n, const uint8_t *labels_src, const uint32_t *tiles_src,
-                                   const uint2 *rect_src, const SplatRec *rec, uint8_t *labels, float *depth,
+                                   const uint2 *rect_src, const SplatRec *rec, const float *depth_src,
+                                   uint8_t *labels, float *depth,
                                    float *mean2d, float *conic, float *rgb, float *opacity, int32_t *rect,
                                    uint32_t *tiles)
 {
@@ -86,7 +87,7 @@ __global__ void k_export_gaussians(int n, const uint8_t *labels_src, const uint3
     if (tiles) tiles[i] = nt;
     if (!nt) return;
     const SplatRec r = rec[i];
-    if (depth) depth[i] = r.r2.z;
+    if (depth) depth[i] = depth_src[i];
     if (mean2d) { mean2d[i] = r.r0.x; mean2d[n + i] = r.r0.y; }
     if (conic) { conic[i] = r.r0.z; conic[n + i] = r.r0.w; conic[2 * n + i] = r.r1.x; }
     if (rgb) { rgb[i] = r.r1.z; rgb[n + i] = r.r1.w; rgb[2 * n + i] = r.r2.x; }
@@ -98,14 +99,14 @@ __global__ void k_export_gaussians(int n, const uint8_t *labels_src, const uint3
     }
 }
 
-__global__ void k_export_pairs(int np, const uint32_t *tile_keys, const uint32_t *vals, const SplatRec *rec,
+__global__ void k_export_pairs(int np, const uint32_t *tile_keys, const uint32_t *vals, const float *depth,
                                const int2 *ranges, int num_tiles, uint64_t *keys, uint32_t *values,
                                int64_t *ranges_out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < np) {
         const uint32_t g = vals[i];
-        if (keys) keys[i] = ((uint64_t)tile_keys[i] << 32) | __float_as_uint(rec[g].r2.z);
+        if (keys) keys[i] = ((uint64_t)tile_keys[i] << 32) | __float_as_uint(depth[g]);
         if (values) values[i] = g;
     }
     if (ranges_out && i < num_tiles) {
@@ -115,7 +116,52 @@ __global__ void k_export_pairs(int np, const uint32_t *tile_keys, const uint32_t
     }
 }
 
+// One block: bucket the tiles by the bit length of their list length, longest first, and
+// expand heavy tiles into 2 or 4 work items. The order inside a bucket is whatever the
+// atomics give; it only affects scheduling, never the image.
+__global__ void __launch_bounds__(1024) k_tile_order(const int2 *__restrict__ ranges, int num_tiles, int split2_bits,
+                                                     int split4_bits, uint32_t *__restrict__ order,
+                                                     Counters *__restrict__ counters)
+{
+    __shared__ unsigned s_cnt[33];
+    if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < num_tiles; t += blockDim.x) {
+        const int2 r = ranges[t];
+        atomicAdd(&s_cnt[__clz((unsigned)(r.y - r.x))], 1u);  // bucket = 32 - bit length
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned acc = 0;
+        for (int b = 0; b < 33; ++b) {
+            const int bits = 32 - b;
+            const unsigned per = bits >= split4_bits ? 4u : (bits >= split2_bits ? 2u : 1u);
+            const unsigned c = s_cnt[b];
+            s_cnt[b] = acc;
+            acc += c * per;
+        }
+        counters->num_items = acc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < num_tiles; t += blockDim.x) {
+        const int2 r = ranges[t];
+        const int b = __clz((unsigned)(r.y - r.x));
+        const int bits = 32 - b;
+        const unsigned lg = bits >= split4_bits ? 2u : (bits >= split2_bits ? 1u : 0u);
+        const unsigned per = 1u << lg;
+        const unsigned pos = atomicAdd(&s_cnt[b], per);
+        for (unsigned p = 0; p < per; ++p) order[pos + p] = ((uint32_t)t << 4) | (lg << 2) | p;
+    }
+}
+
 }  // namespace
+
+void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int split4_bits, uint32_t *order,
+                       Counters *counters, cudaStream_t s)
+{
+    if (num_tiles > 0)
+        k_tile_order<<<1, 1024, 0, s>>>(ranges, num_tiles, split2_bits, split4_bits, order, counters);
+}
 
 void launch_emit(const EmitArgs &a, int num_blocks, cudaStream_t s)
 {
@@ -128,21 +174,22 @@ void launch_ranges(const uint32_t *keys, int n, int num_tiles, int2 *ranges, cud
 }
 
 void launch_export_gaussians(int n, const uint8_t *labels_src, const uint32_t *tiles_src, const uint2 *rect_src,
-                             const SplatRec *rec, uint8_t *labels, float *depth, float *mean2d, float *conic,
-                             float *rgb, float *opacity, int32_t *rect, uint32_t *tiles, cudaStream_t s)
+                             const SplatRec *rec, const float *depth_src, uint8_t *labels, float *depth,
+                             float *mean2d, float *conic, float *rgb, float *opacity, int32_t *rect, uint32_t *tiles,
+                             cudaStream_t s)
 {
     if (n > 0)
-        k_export_gaussians<<<(n + 255) / 256, 256, 0, s>>>(n, labels_src, tiles_src, rect_src, rec, labels, depth,
-                                                           mean2d, conic, rgb, opacity, rect, tiles);
+        k_export_gaussians<<<(n + 255) / 256, 256, 0, s>>>(n, labels_src, tiles_src, rect_src, rec, depth_src,
+                                                           labels, depth, mean2d, conic, rgb, opacity, rect, tiles);
 }
 
-void launch_export_pairs(int np, const uint32_t *tile_keys, const uint32_t *vals, const SplatRec *rec,
+void launch_export_pairs(int np, const uint32_t *tile_keys, const uint32_t *vals, const float *depth,
                          const int2 *ranges, int num_tiles, uint64_t *keys, uint32_t *values, int64_t *ranges_out,
                          cudaStream_t s)
 {
     const int m = np > num_tiles ? np : num_tiles;
     if (m > 0)
-        k_export_pairs<<<(m + 255) / 256, 256, 0, s>>>(np, tile_keys, vals, rec, ranges, num_tiles, keys, values,
+        k_export_pairs<<<(m + 255) / 256, 256, 0, s>>>(np, tile_keys, vals, depth, ranges, num_tiles, keys, values,
                                                        ranges_out);
 }
 

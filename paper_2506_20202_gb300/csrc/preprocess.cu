@@ -188,8 +188,9 @@ __global__ void __launch_bounds__(kBlock) k_preprocess(PreprocessArgs a)
                     SplatRec rec;
                     rec.r0 = make_float4(mx2, my2, cc * idet, -cb * idet);
                     rec.r1 = make_float4(ca * idet, op, rgb[0], rgb[1]);
-                    rec.r2 = make_float4(rgb[2], cutoff ? 1.0f : 0.0f, depth, 0.0f);
+                    rec.r2 = make_float4(rgb[2], cutoff ? 1.0f : 0.0f, cb / cc, cb / ca);
                     a.rec[i] = rec;
+                    a.depth[i] = depth;
 
                     if (cutoff) {
                         // Ray-tracing record in the unit-sphere frame of M = k R S

@@ -24,7 +24,9 @@ constexpr uint32_t kStatusLookbackTimeout = 1u;
 // by the render kernel: 3 x float4 = 48 bytes.
 //   r0 = (mean2d.x, mean2d.y, conic.a, conic.b)
 //   r1 = (conic.c, opacity, rgb.r, rgb.g)
-//   r2 = (rgb.b, cutoff flag as float (1 or 0), depth, unused)
+//   r2 = (rgb.b, cutoff flag as float (1 or 0), -b/a, -b/c)
+// The last two are the minimisers of q along a horizontal / vertical line (dx* = -b/a dy,
+// dy* = -b/c dx), used by the render's exact rectangle test.
 struct __align__(16) SplatRec {
     float4 r0, r1, r2;
 };
@@ -59,12 +61,18 @@ struct Counters {
     unsigned long long n_rendered;
     unsigned long long n_pairs;
     unsigned long long n_cutoff;
+    unsigned int num_items;              // render work items (written by the item-order kernel)
+    unsigned int pad0;
+    // render counters, zeroed together before each render (n_evaluated .. tile_queue)
     unsigned long long n_evaluated;      // (pixel, Gaussian) pairs inside the q <= 9 support
     unsigned long long n_walked;         // (pixel, Gaussian) pairs whose q was computed
     unsigned long long n_cut_evaluated;  // evaluated pairs that needed the ray-traced weight
+    unsigned long long n_tested;         // (warp, Gaussian) rectangle tests
+    unsigned int tile_queue;             // next entry of the heaviest-first item order
     unsigned int status;
-    unsigned int part_counter[11];  // partition tickets for chained scans
+    unsigned int part_counter[8];  // partition tickets for chained scans
 };
+constexpr size_t kRenderCounterBytes = 4 * sizeof(unsigned long long) + sizeof(unsigned int);
 
 struct PreprocessArgs {
     const float *means, *log_scales, *quats, *logits, *sh;
@@ -79,6 +87,7 @@ struct PreprocessArgs {
     uint2 *rect;           // (tx0 | ty0 << 16, tx1 | ty1 << 16)
     SplatRec *rec;
     CutRec *cut;
+    float *depth;          // camera-space depth (float32 key value) of rendered Gaussians
     uint32_t *ckeys;       // compacted depth keys (float bits) of rendered Gaussians
     uint32_t *cvals;       // their indices, ascending
     unsigned long long *lookback;  // per-block chained-scan words, zeroed before launch
@@ -112,8 +121,18 @@ void launch_emit(const EmitArgs &a, int num_blocks, cudaStream_t s);
 
 void launch_ranges(const uint32_t *sorted_tile_keys, int n_pairs, int num_tiles, int2 *ranges, cudaStream_t s);
 
+// Render work items ordered by descending list length (log2 buckets): heaviest first.
+// A tile whose list has at least 2^(split4_bits-1) entries becomes 4 items (16x4 pixels,
+// 4 lanes per pixel), at least 2^(split2_bits-1) entries 2 items (16x8, 2 lanes per pixel),
+// otherwise 1 item. Item = tile << 4 | log2(lanes per pixel) << 2 | part. order must hold
+// 4 * num_tiles entries; the item count goes to counters->num_items.
+void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int split4_bits, uint32_t *order,
+                       Counters *counters, cudaStream_t s);
+
 struct RenderArgs {
     const int2 *ranges;
+    const uint32_t *tile_order;
+    int num_tiles;
     const uint32_t *pair_vals;
     const SplatRec *rec;
     const CutRec *cut;
@@ -124,15 +143,16 @@ struct RenderArgs {
     uint32_t *n_contrib;
     Counters *counters;
 };
-void launch_render(const RenderArgs &a, int num_tiles, cudaStream_t s);
+void launch_render(const RenderArgs &a, int grid, cudaStream_t s);
+int render_blocks_per_sm();
 
 // Debug exports
 void launch_export_gaussians(int n, const uint8_t *labels_src, const uint32_t *tiles_src,
-                             const uint2 *rect_src, const SplatRec *rec, uint8_t *labels,
+                             const uint2 *rect_src, const SplatRec *rec, const float *depth_src, uint8_t *labels,
                              float *depth, float *mean2d, float *conic, float *rgb,
                              float *opacity, int32_t *rect, uint32_t *tiles, cudaStream_t s);
 void launch_export_pairs(int n_pairs, const uint32_t *tile_keys, const uint32_t *vals,
-                         const SplatRec *rec, const int2 *ranges, int num_tiles,
+                         const float *depth, const int2 *ranges, int num_tiles,
                          uint64_t *keys, uint32_t *values, int64_t *ranges_out, cudaStream_t s);
 
 }  // namespace rara

@@ -1,10 +1,21 @@
 // Steps (c)+(d): per-tile front-to-back compositing with the RaRa decay weight.
 //
-// One 256-thread block per 16x16 tile, one pixel per thread. The tile's depth-sorted
-// list is walked in batches of 256: each thread gathers one splat record (and, for a
-// cutoff Gaussian, its ray-tracing record) into shared memory, then every pixel walks the
-// batch. A pixel stops at the first Gaussian that would take its transmittance below
-// 1e-4; the block stops once all of its pixels have stopped.
+// Work items come from a queue ordered heaviest first (by tile-list length). A light tile
+// is one item: a 256-thread block composites its 16x16 pixels, one lane per pixel. A heavy
+// tile is split into 2 or 4 items of 16x8 or 16x4 pixels with 2 or 4 lanes per pixel: the
+// lanes of a pixel take consecutive list entries and combine them with a prefix product of
+// (1 - alpha), so the pixel's chain of dependent steps is 2 or 4 times shorter. That
+// matters because a pixel that never saturates (for example one that looks through the
+// clipped region, where cutoff Gaussians get w ~ 0) walks its whole list, and the longest
+// such walk bounds the launch.
+//
+// The tile's depth-sorted list is walked in batches of 256 entries: each thread gathers one
+// splat record (and, for a cutoff Gaussian, its ray-tracing record) into shared memory.
+// Each warp owns a rectangle of the item's pixels; before walking a 32-entry chunk of the
+// batch, its lanes test one entry each against the rectangle (exact minimum of q over the
+// rectangle of pixel centres) and the warp walks only the entries whose q <= 9 support
+// reaches the rectangle, in list order. An entry it skips has q > 9 at all its pixels and
+// would have been skipped pixel by pixel.
 //
 // Decay weight (Eq. 4-8, Eq. 11, Algorithm 1 step 2), evaluated in the unit-sphere frame
 // of the ellipsoid M = k R S without forming t1, t2 or t_p explicitly:
@@ -19,6 +30,8 @@
 //               s1,2 = d_ep + m.c -/+ sqrt(1 - |c|^2) (m.V) / |V|
 //   weight      both >= 0: 1; both < 0: 0; otherwise the visible share of the chord,
 //               max(s1, s2) / |s2 - s1|  (= (t2 - t_p)/(t2 - t1) or (t_p - t1)/(t2 - t1)).
+// Because w <= 1, an entry whose unweighted alpha is already below 1/255 is skipped before
+// the weight is computed (the weighted alpha could only be smaller).
 #include "rara_internal.cuh"
 
 namespace rara {
@@ -35,7 +48,7 @@ __device__ __forceinline__ float rara_weight(const float4 c0, const float4 c1, c
     const float V0 = c0.x + p0, V1 = c0.y + p1, V2 = c0.z + p2;
     const float VV = fmaf(V0, V0, fmaf(V1, V1, V2 * V2));
     const float pV = fmaf(p0, V0, fmaf(p1, V1, p2 * V2));
-    const float f = pV / VV;
+    const float f = __fdividef(pV, VV);
     const float e0 = fmaf(-f, V0, p0), e1 = fmaf(-f, V1, p1), e2 = fmaf(-f, V2, p2);
     const float cc = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
     if (cc >= 1.0f) return 1.0f;                    // misses or grazes: keep rasterization
@@ -50,26 +63,94 @@ __device__ __forceinline__ float rara_weight(const float4 c0, const float4 c1, c
     const bool v1 = s1 >= 0.0f, v2 = s2 >= 0.0f;
     if (v1 && v2) return 1.0f;
     if (!v1 && !v2) return 0.0f;
-    return fminf(1.0f, fmaxf(s1, s2) / fabsf(s2 - s1));
+    return fminf(1.0f, __fdividef(fmaxf(s1, s2), fabsf(s2 - s1)));
 }
 
-__global__ void __launch_bounds__(kBlock) k_render(RenderArgs a)
+// Minimum of q(dx, dy) = a dx^2 + 2 b dx dy + c dy^2 over the box [ax, bx] x [ay, by] of
+// offsets from the projected centre. q is convex, so when the centre lies outside the box
+// the minimum is on an edge, at the edge's 1D minimiser clamped to the edge
+// (dx* = nba dy on a horizontal edge, dy* = nbc dx on a vertical one).
+__device__ __forceinline__ float box_min_q(float ax, float bx, float ay, float by, float a, float b, float c,
+                                           float nba, float nbc)
 {
-    __shared__ float4 s_r0[kBlock], s_r1[kBlock], s_r2[kBlock];
-    __shared__ float4 s_c0[kBlock], s_c1[kBlock], s_c2[kBlock], s_c3[kBlock];
+    if (ax <= 0.0f && bx >= 0.0f && ay <= 0.0f && by >= 0.0f) return 0.0f;
+    float best;
+    {
+        const float dx = fminf(bx, fmaxf(ax, nba * ay));
+        best = fmaf(dx, fmaf(a, dx, 2.0f * b * ay), c * ay * ay);
+    }
+    {
+        const float dx = fminf(bx, fmaxf(ax, nba * by));
+        best = fminf(best, fmaf(dx, fmaf(a, dx, 2.0f * b * by), c * by * by));
+    }
+    {
+        const float dy = fminf(by, fmaxf(ay, nbc * ax));
+        best = fminf(best, fmaf(ax, fmaf(a, ax, 2.0f * b * dy), c * dy * dy));
+    }
+    {
+        const float dy = fminf(by, fmaxf(ay, nbc * bx));
+        best = fminf(best, fmaf(bx, fmaf(a, bx, 2.0f * b * dy), c * dy * dy));
+    }
+    return best;
+}
 
-    const int tile = blockIdx.x;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py = ty * kTile + (threadIdx.x / kTile);
+constexpr float kCullQ = kSupportQ * 1.0001f;  // margin over float32 rounding of the test
+
+struct Stage {
+    float4 r0[kBlock], r1[kBlock], r2[kBlock];
+    float4 c0[kBlock], c1[kBlock], c2[kBlock], c3[kBlock];
+};
+
+struct Tally {
+    uint32_t evaluated = 0, walked = 0, cut = 0, tested = 0;
+};
+
+// Alpha of list entry j (in the staged batch) at pixel offset (dx, dy); 0 when the entry
+// does not contribute (outside the q <= 9 support or below 1/255 after the weight).
+__device__ __forceinline__ float entry_alpha(const Stage &st, int j, float pxf, float pyf, Tally &ty)
+{
+    const float4 r0 = st.r0[j];
+    const float dx = pxf - r0.x, dy = pyf - r0.y;
+    const float4 r1 = st.r1[j];
+    const float q = fmaf(dx, fmaf(r0.z, dx, 2.0f * r0.w * dy), r1.x * dy * dy);
+    ++ty.walked;
+    if (q > kSupportQ) return 0.0f;
+    ++ty.evaluated;
+    float alpha = r1.y * __expf(-0.5f * q);
+    if (alpha < kAlphaMin) return 0.0f;
+    if (st.r2[j].y != 0.0f) {
+        alpha *= rara_weight(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
+        ++ty.cut;
+    }
+    alpha = fminf(kAlphaMax, alpha);
+    return alpha < kAlphaMin ? 0.0f : alpha;
+}
+
+// One work item: LPP lanes per pixel. Item geometry (inside the 16x16 tile):
+//   LPP 1: the whole tile, warp rectangles 8x4
+//   LPP 2: rows [8 part, 8 part + 8), warp rectangles 8x2
+//   LPP 4: rows [4 part, 4 part + 4), warp rectangles 4x2
+template <int LPP>
+__device__ __forceinline__ void render_item(const RenderArgs &a, Stage &st, int tile, int part, Tally &ty)
+{
+    constexpr int RW = LPP == 4 ? 4 : 8;     // warp rectangle width
+    constexpr int RH = LPP == 1 ? 4 : 2;     // warp rectangle height
+    constexpr int WPR = kTile / RW;          // warp rectangles per row
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane % LPP, pix = lane / LPP;
+    const int tx = tile % a.tiles_x, ty0 = tile / a.tiles_x;
+    const int wx0 = (warp % WPR) * RW;
+    const int wy0 = part * (kTile / LPP) + (warp / WPR) * RH;
+    const int px = tx * kTile + wx0 + pix % RW, py = ty0 * kTile + wy0 + pix / RW;
     const bool inside = px < a.W && py < a.H;
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
+    const float rx0 = (float)(tx * kTile + wx0) + 0.5f, rx1 = rx0 + (float)(RW - 1);
+    const float ry0 = (float)(ty0 * kTile + wy0) + 0.5f, ry1 = ry0 + (float)(RH - 1);
     const int2 range = a.ranges[tile];
 
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     bool done = !inside;
     uint32_t last = 0;
-    uint32_t evaluated = 0, walked = 0, cut_evaluated = 0;
 
     for (int base = range.x; base < range.y; base += kBlock) {
         if (__syncthreads_count(done) == kBlock) break;
@@ -77,50 +158,117 @@ __global__ void __launch_bounds__(kBlock) k_render(RenderArgs a)
         if (k < range.y) {
             const uint32_t g = __ldg(&a.pair_vals[k]);
             const SplatRec rec = a.rec[g];
-            s_r0[threadIdx.x] = rec.r0;
-            s_r1[threadIdx.x] = rec.r1;
-            s_r2[threadIdx.x] = rec.r2;
+            st.r0[threadIdx.x] = rec.r0;
+            st.r1[threadIdx.x] = rec.r1;
+            st.r2[threadIdx.x] = rec.r2;
             if (rec.r2.y != 0.0f) {
                 const CutRec c = a.cut[g];
-                s_c0[threadIdx.x] = c.c0;
-                s_c1[threadIdx.x] = c.c1;
-                s_c2[threadIdx.x] = c.c2;
-                s_c3[threadIdx.x] = c.c3;
+                st.c0[threadIdx.x] = c.c0;
+                st.c1[threadIdx.x] = c.c1;
+                st.c2[threadIdx.x] = c.c2;
+                st.c3[threadIdx.x] = c.c3;
             }
         }
         __syncthreads();
-        if (!done) {
-            const int cnt = min(kBlock, range.y - base);
-            int j = 0;
-            for (; j < cnt; ++j) {
-                const float4 r0 = s_r0[j];
-                const float dx = pxf - r0.x, dy = pyf - r0.y;
-                const float4 r1 = s_r1[j];
-                const float q = fmaf(dx, fmaf(r0.z, dx, 2.0f * r0.w * dy), r1.x * dy * dy);
-                if (q > kSupportQ) continue;
-                ++evaluated;
-                const float4 r2 = s_r2[j];
-                float alpha = r1.y * __expf(-0.5f * q);
-                if (r2.y != 0.0f) {
-                    alpha *= rara_weight(s_c0[j], s_c1[j], s_c2[j], s_c3[j], dx, dy);
-                    ++cut_evaluated;
-                }
-                alpha = fminf(kAlphaMax, alpha);
-                if (alpha < kAlphaMin) continue;
-                const float Tn = T * (1.0f - alpha);
-                if (Tn < kTMin) { done = true; break; }
-                const float wgt = alpha * T;
-                C0 = fmaf(r1.z, wgt, C0);
-                C1 = fmaf(r1.w, wgt, C1);
-                C2 = fmaf(r2.x, wgt, C2);
-                T = Tn;
-                last = (uint32_t)(base - range.x + j + 1);
+        const int cnt = min(kBlock, range.y - base);
+        for (int chunk = 0; chunk < cnt; chunk += 32) {
+            if (__all_sync(0xffffffffu, done)) break;
+            bool keep = false;
+            const int jt = chunk + lane;
+            if (jt < cnt) {
+                const float4 t0 = st.r0[jt];
+                const float cq = st.r1[jt].x;
+                const float4 t2 = st.r2[jt];
+                keep = box_min_q(rx0 - t0.x, rx1 - t0.x, ry0 - t0.y, ry1 - t0.y, t0.z, t0.w, cq, t2.z, t2.w) <= kCullQ;
+                ++ty.tested;
             }
-            walked += (uint32_t)min(j + 1, cnt);
+            unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (LPP == 1) {
+                while (m) {
+                    const int j = chunk + __ffs(m) - 1;
+                    m &= m - 1;
+                    if (done) continue;
+                    const float alpha = entry_alpha(st, j, pxf, pyf, ty);
+                    if (alpha == 0.0f) continue;
+                    const float Tn = T * (1.0f - alpha);
+                    if (Tn < kTMin) {
+                        done = true;
+                        continue;
+                    }
+                    const float wgt = alpha * T;
+                    const float4 r1 = st.r1[j];
+                    C0 = fmaf(r1.z, wgt, C0);
+                    C1 = fmaf(r1.w, wgt, C1);
+                    C2 = fmaf(st.r2[j].x, wgt, C2);
+                    T = Tn;
+                    last = (uint32_t)(base - range.x + j + 1);
+                }
+            } else {
+                const int group = pix * LPP;          // first lane of this pixel's group
+                const unsigned gmask = ((1u << LPP) - 1u) << group;
+                while (m) {
+                    // sub-lane s takes the (s+1)-th remaining entry of the chunk
+                    unsigned mine = m;
+                    for (int r = 0; r < sub; ++r) mine &= mine - 1u;
+                    unsigned rest = m;
+#pragma unroll
+                    for (int r = 0; r < LPP; ++r) rest &= rest - 1u;
+                    m = rest;
+                    float alpha = 0.0f;
+                    int j = 0;
+                    if (!done && mine) {
+                        j = chunk + __ffs(mine) - 1;
+                        alpha = entry_alpha(st, j, pxf, pyf, ty);
+                    }
+                    // prefix products of (1 - alpha) over the pixel's lanes, in list order
+                    const float om = 1.0f - alpha;
+                    float incl = om;
+#pragma unroll
+                    for (int o = 1; o < LPP; o <<= 1) {
+                        const float v = __shfl_up_sync(0xffffffffu, incl, o, LPP);
+                        if (sub >= o) incl *= v;
+                    }
+                    float excl = __shfl_up_sync(0xffffffffu, incl, 1, LPP);
+                    if (sub == 0) excl = 1.0f;
+                    // the first entry that would take T below 1e-4 stops the pixel, unblended
+                    const bool stop = alpha > 0.0f && T * incl < kTMin;
+                    const unsigned sb = (__ballot_sync(0xffffffffu, stop) & gmask) >> group;
+                    const int first = sb ? __ffs(sb) - 1 : LPP;
+                    const bool blend = alpha > 0.0f && sub < first;
+                    const float wgt = blend ? alpha * excl : 0.0f;
+                    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+                    uint32_t lp = 0;
+                    if (blend) {
+                        const float4 r1 = st.r1[j];
+                        s0 = r1.z * wgt;
+                        s1 = r1.w * wgt;
+                        s2 = st.r2[j].x * wgt;
+                        lp = (uint32_t)(base - range.x + j + 1);
+                    }
+#pragma unroll
+                    for (int o = 1; o < LPP; o <<= 1) {
+                        s0 += __shfl_xor_sync(0xffffffffu, s0, o, LPP);
+                        s1 += __shfl_xor_sync(0xffffffffu, s1, o, LPP);
+                        s2 += __shfl_xor_sync(0xffffffffu, s2, o, LPP);
+                        lp = max(lp, __shfl_xor_sync(0xffffffffu, lp, o, LPP));
+                    }
+                    // transmittance after the group: before the stopping entry, or after all
+                    const float e_first = __shfl_sync(0xffffffffu, excl, group + (first < LPP ? first : 0));
+                    const float i_last = __shfl_sync(0xffffffffu, incl, group + LPP - 1);
+                    if (!done) {
+                        C0 = fmaf(T, s0, C0);
+                        C1 = fmaf(T, s1, C1);
+                        C2 = fmaf(T, s2, C2);
+                        if (lp) last = lp;
+                        T = T * (first < LPP ? e_first : i_last);
+                        done = first < LPP;
+                    }
+                }
+            }
         }
     }
 
-    if (inside) {
+    if (inside && sub == 0) {
         const size_t p = (size_t)py * a.W + px;
         const size_t plane = (size_t)a.W * a.H;
         a.image[p] = fmaf(T, a.bg[0], C0);
@@ -129,24 +277,59 @@ __global__ void __launch_bounds__(kBlock) k_render(RenderArgs a)
         if (a.final_T) a.final_T[p] = T;
         if (a.n_contrib) a.n_contrib[p] = last;
     }
-    unsigned long long ev = evaluated, wk = walked, ce = cut_evaluated;
+}
+
+__global__ void __launch_bounds__(kBlock, 4) k_render(RenderArgs a)
+{
+    __shared__ Stage st;
+    __shared__ unsigned s_item;
+    Tally ty;
+    const unsigned num_items = *(volatile unsigned *)&a.counters->num_items;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned q = atomicAdd(&a.counters->tile_queue, 1u);
+            s_item = q < num_items ? a.tile_order[q] : 0xffffffffu;
+        }
+        __syncthreads();
+        const unsigned item = s_item;
+        if (item == 0xffffffffu) break;
+        const int tile = (int)(item >> 4), lpp_log2 = (int)((item >> 2) & 3u), part = (int)(item & 3u);
+        if (lpp_log2 == 0) render_item<1>(a, st, tile, 0, ty);
+        else if (lpp_log2 == 1) render_item<2>(a, st, tile, part, ty);
+        else render_item<4>(a, st, tile, part, ty);
+        __syncthreads();  // everyone has read s_item and the staged batch
+    }
+
+    unsigned long long ev = ty.evaluated, wk = ty.walked, ce = ty.cut, ts = ty.tested;
     for (int o = 16; o > 0; o >>= 1) {
         ev += __shfl_xor_sync(0xffffffffu, ev, o);
         wk += __shfl_xor_sync(0xffffffffu, wk, o);
         ce += __shfl_xor_sync(0xffffffffu, ce, o);
+        ts += __shfl_xor_sync(0xffffffffu, ts, o);
     }
     if ((threadIdx.x & 31) == 0) {
         if (ev) atomicAdd(&a.counters->n_evaluated, ev);
         if (wk) atomicAdd(&a.counters->n_walked, wk);
         if (ce) atomicAdd(&a.counters->n_cut_evaluated, ce);
+        if (ts) atomicAdd(&a.counters->n_tested, ts);
     }
 }
 
 }  // namespace
 
-void launch_render(const RenderArgs &a, int num_tiles, cudaStream_t s)
+int render_blocks_per_sm()
 {
-    if (num_tiles > 0) k_render<<<num_tiles, kBlock, 0, s>>>(a);
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_render, kBlock, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return b;
+}
+
+void launch_render(const RenderArgs &a, int grid, cudaStream_t s)
+{
+    if (grid > 0) k_render<<<grid, kBlock, 0, s>>>(a);
 }
 
 }  // namespace rara

@@ -45,7 +45,8 @@ class rara_plane(C.Structure):
 class rara_frame_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_rendered", C.c_int64), ("n_cutoff", C.c_int64),
                 ("n_pairs", C.c_int64), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
-                ("n_evaluated", C.c_int64), ("n_walked", C.c_int64), ("n_cut_evaluated", C.c_int64)]
+                ("n_evaluated", C.c_int64), ("n_walked", C.c_int64), ("n_cut_evaluated", C.c_int64),
+                ("n_tested", C.c_int64)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/rara.h
@@ -57,6 +58,7 @@ SIGNATURES = {
     "rara_ctx_bytes": (C.c_size_t, [_P]),
     "rara_ctx_sync": (C.c_int, [_P, _P]),
     "rara_ctx_launches": (C.c_int64, [_P]),
+    "rara_ctx_set_tuning": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "rara_preprocess": (C.c_int, [_P, C.POINTER(rara_gaussians), C.POINTER(rara_camera),
                                   C.POINTER(rara_plane), _P]),
     "rara_bin": (C.c_int, [_P, _P]),
@@ -185,6 +187,10 @@ def rara_ctx_launches(ctx) -> int:
     return int(load().rara_ctx_launches(ctx))
 
 
+def rara_ctx_set_tuning(ctx, split2_bits: int, split4_bits: int):
+    _check(ctx, load().rara_ctx_set_tuning(ctx, int(split2_bits), int(split4_bits)))
+
+
 def rara_ctx_sync(ctx, stream=None):
     _check(ctx, load().rara_ctx_sync(ctx, _stream(stream)))
 
@@ -245,8 +251,10 @@ def rara_frame_pairs(ctx, keys=None, values=None, ranges=None, stream=None):
 class Renderer:
     """Owns a context and output buffers; render() runs the three stages on a stream."""
 
-    def __init__(self, budget_bytes: int = 0):
+    def __init__(self, budget_bytes: int = 0, tuning=None):
         self.ctx = rara_ctx_create(budget_bytes)
+        if tuning is not None:
+            rara_ctx_set_tuning(self.ctx, *tuning)
 
     def close(self):
         if self.ctx is not None:

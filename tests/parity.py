@@ -16,8 +16,8 @@ CLASS_EXEMPT = 1e-6   # world units from a class threshold
 RECT_EXEMPT = 2e-3    # pixels from a tile edge (float32 position + footprint error)
 
 
-def gpu_frame(scene, cam, plane, bg=(0.0, 0.0, 0.0), renderer=None, export=True):
-    r = renderer or rara.Renderer()
+def gpu_frame(scene, cam, plane, bg=(0.0, 0.0, 0.0), renderer=None, export=True, tuning=None):
+    r = renderer or rara.Renderer(tuning=tuning)
     gs = rara.GaussianTensors.from_scene(scene)
     img, T, nc = r.render(gs, cam, plane, bg)
     torch.cuda.synchronize()

@@ -27,9 +27,9 @@ def _built():
     oracle.build()
 
 
-def full_check(scene, cam, pl, bg=(0.0, 0.0, 0.0), rows=None, max_flag_frac=0.05):
+def full_check(scene, cam, pl, bg=(0.0, 0.0, 0.0), rows=None, max_flag_frac=0.05, tuning=None):
     report = {}
-    gpu = parity.gpu_frame(scene, cam, pl, bg)
+    gpu = parity.gpu_frame(scene, cam, pl, bg, tuning=tuning)
     pre = oracle.preprocess(scene, cam, pl)
     kvr = oracle.build_keys(pre)
     parity.check_gaussians(pre, gpu["g"], report)
@@ -47,6 +47,28 @@ def test_small_uniform_scene():
     rep, gpu, ref = full_check(scene, cam, pl)
     assert gpu["info"]["n_cutoff"] > 100
     assert rep["tiles_exact"] >= rep["tiles"] - 5
+
+
+# (split2_bits, split4_bits): one lane per pixel everywhere, two, four, and a mix
+TUNINGS = [(33, 33), (1, 33), (0, 1), (5, 7)]
+
+
+@pytest.mark.parametrize("tuning", TUNINGS)
+def test_lanes_per_pixel_variants(tuning):
+    """The render's 1-, 2- and 4-lanes-per-pixel paths against the oracle."""
+    scene, cam, pl = scenes.small_uniform_workload(n=8000, width=200, height=136, seed=21)
+    rep, gpu, ref = full_check(scene, cam, pl, bg=(0.05, 0.1, 0.2), tuning=tuning)
+    assert gpu["info"]["n_cutoff"] > 50
+
+
+@pytest.mark.parametrize("tuning", [(33, 33), (0, 1)])
+def test_lanes_per_pixel_same_image(tuning):
+    """All scheduling variants agree with each other to float rounding, n_contrib exactly."""
+    scene, cam, pl = scenes.small_uniform_workload(n=8000, width=200, height=136, seed=22)
+    ref = parity.gpu_frame(scene, cam, pl, export=False, tuning=(11, 12))
+    got = parity.gpu_frame(scene, cam, pl, export=False, tuning=tuning)
+    assert np.abs(got["image"] - ref["image"]).max() <= 1e-5
+    assert np.array_equal(got["n_contrib"], ref["n_contrib"])
 
 
 @pytest.mark.parametrize("mode", [scenes.MODE_NONE, scenes.MODE_HARD, scenes.MODE_RARA_ALL])
@@ -134,12 +156,13 @@ def test_stacked_cutoff_closed_form():
     assert g["T"][33, 30] == pytest.approx(1 - 0.5 * delta, abs=1e-4)
 
 
-def test_hair_strand_scene():
+@pytest.mark.parametrize("tuning", [None, (0, 1)])
+def test_hair_strand_scene(tuning):
     """Anisotropic strands (1:1:40) with a plane cutting 30-50% of them (reduced count)."""
     scene, nrm, d = scenes.hair_scene(curves=1500, segments=50, seed=2)
     cam = scenes.look_at_camera((0.2, -0.3, -3.2), (0.0, 0.3, 0.0), 256, 256, 60.0)
     pl = scenes.Plane(np.float32(nrm), float(d), 3.0, scenes.MODE_RARA)
-    rep, gpu, ref = full_check(scene, cam, pl, max_flag_frac=0.08)
+    rep, gpu, ref = full_check(scene, cam, pl, max_flag_frac=0.08, tuning=tuning)
     frac = gpu["info"]["n_cutoff"] / max(1, gpu["info"]["n_rendered"])
     assert 0.2 <= frac <= 0.6, frac
 
