@@ -11,6 +11,9 @@
  *                    with the ray-ellipsoid decay weight (Eq. 4-8, Eq. 11, Eq. 12;
  *                    Algorithm 1 steps 2-3) for cutoff Gaussians and early termination
  *   rara_render_frame   the three calls in sequence
+ *   rara_render_batch   many views (cameras, planes, resolutions) of one or more scenes in
+ *                    one launch per stage; rara_render_batch_graph replays the batch's stage
+ *                    sequence as a captured CUDA graph
  *
  * Conventions
  *   - All device pointers are CUDA device memory on the current device; sizes are
@@ -49,7 +52,10 @@ typedef enum rara_status {
                                  non-finite camera/plane, unknown mode, call out of order */
     RARA_ERR_BUDGET = 2,      /* the context's device-memory budget cannot hold this frame */
     RARA_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
-    RARA_ERR_TIMEOUT = 4      /* a bounded device-side wait gave up (results invalid) */
+    RARA_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (results invalid) */
+    RARA_ERR_OVERFLOW = 5     /* a graph replay produced more pairs than its capacity: the
+                                 batch's images are invalid; render it again (the context has
+                                 grown the capacity and recaptures on the next call) */
 } rara_status;
 
 typedef enum rara_mode {
@@ -84,6 +90,19 @@ typedef struct rara_plane {
     float k_sigma; /* > 0 */
     int32_t mode;  /* rara_mode */
 } rara_plane;
+
+/* One view of a batch: a camera, a clip plane and output buffers over one of the batch's
+ * scenes. image is device float [3][H][W]; final_T float [H][W] and n_contrib uint32 [H][W]
+ * may be NULL. */
+typedef struct rara_view {
+    int32_t scene;       /* index into the batch's scene array */
+    rara_camera camera;
+    rara_plane plane;
+    float bg[3];
+    float *image;
+    float *final_T;
+    uint32_t *n_contrib;
+} rara_view;
 
 typedef struct rara_ctx rara_ctx;
 
@@ -142,8 +161,29 @@ int rara_render_frame(rara_ctx *ctx, const rara_gaussians *g, const rara_camera 
                       const rara_plane *plane, const float bg[3], float *image,
                       float *final_T, uint32_t *n_contrib, void *stream);
 
-/* Counts of the current frame, valid after rara_bin; the render counts refer to the last
- * rara_render. Waits for the context's last stream to read them. */
+/* Batched render: every view of `views` (any order, any resolutions, any of the scenes)
+ * goes through the same steps as rara_render_frame, each step one launch for the whole
+ * batch (Section 3.2-3.4 and Algorithm 1 per view). At most 4096 views and 64 scenes; the
+ * sum over views of the scene sizes must stay below 2^32. Waits for the stream once (after
+ * the preprocess) to size the pair buffers. The per-view results and counts stay available
+ * through the rara_frame_* calls with the view's index until the next batch or frame. */
+int rara_render_batch(rara_ctx *ctx, const rara_gaussians *scenes, int32_t num_scenes, const rara_view *views,
+                      int32_t num_views, void *stream);
+
+/* Same as rara_render_batch, without any host synchronisation: the first call for a batch
+ * shape (scene sizes and SH degrees, view count, per-view resolution and scene) renders it
+ * with rara_render_batch, sizes the pair capacity from it (+25%), and captures the whole
+ * stage sequence on a private stream into a CUDA graph; later calls with the same shape
+ * copy the new cameras, planes, scene and output pointers into the graph's tables and
+ * launch the graph on `stream`. A replay that would exceed the pair capacity writes no pair
+ * past it and is reported as RARA_ERR_OVERFLOW by the next rara_ctx_sync, which also grows
+ * the capacity so the next call recaptures. */
+int rara_render_batch_graph(rara_ctx *ctx, const rara_gaussians *scenes, int32_t num_scenes,
+                            const rara_view *views, int32_t num_views, void *stream);
+
+/* Counts of one view of the current frame or batch (view 0 for a single frame), valid after
+ * rara_bin; the render counts are totals of the last rara_render over all views. Waits for
+ * the context's last stream to read them. */
 typedef struct rara_frame_info {
     int64_t n;            /* Gaussians in the frame */
     int64_t n_rendered;   /* not invisible, not culled, at least one tile */
@@ -158,21 +198,24 @@ typedef struct rara_frame_info {
     int64_t n_tested;     /* (warp rectangle, Gaussian) culling tests of the last render */
 } rara_frame_info;
 
-int rara_frame_info_get(rara_ctx *ctx, rara_frame_info *out);
+int rara_frame_info_get(rara_ctx *ctx, int32_t view, rara_frame_info *out);
 
-/* Copy per-Gaussian preprocess results into caller device buffers (any may be NULL):
+/* Copy per-Gaussian preprocess results of one view into caller device buffers (any may be
+ * NULL; n is the view's scene size):
  * labels uint8[n]; depth float[n] (camera z); mean2d float[2][n]; conic float[3][n]
  * (a, b, c of [[a,b],[b,c]], the inverse 2D covariance); rgb float[3][n]; opacity float[n];
  * rect int32[4][n] (inclusive tx0, ty0, tx1, ty1); tiles uint32[n] (0 when culled).
  * Fields other than labels are defined only where tiles > 0. */
-int rara_frame_gaussians(rara_ctx *ctx, uint8_t *labels, float *depth, float *mean2d,
+int rara_frame_gaussians(rara_ctx *ctx, int32_t view, uint8_t *labels, float *depth, float *mean2d,
                          float *conic, float *rgb, float *opacity, int32_t *rect,
                          uint32_t *tiles, void *stream);
 
-/* Copy the sorted pair list into caller device buffers: keys uint64[n_pairs]
+/* Copy one view's sorted pair list into caller device buffers: keys uint64[n_pairs]
  * (tile id << 32 | float bits of the depth), values uint32[n_pairs] (Gaussian index), and
- * ranges int64[num_tiles][2] ([start, end) of each tile, tile id = ty * tiles_x + tx). */
-int rara_frame_pairs(rara_ctx *ctx, uint64_t *keys, uint32_t *values, int64_t *ranges,
+ * ranges int64[num_tiles][2] ([start, end) of each tile, tile id = ty * tiles_x + tx),
+ * where n_pairs and the tile counts are the view's (rara_frame_info_get). Waits for the
+ * context's last stream. */
+int rara_frame_pairs(rara_ctx *ctx, int32_t view, uint64_t *keys, uint32_t *values, int64_t *ranges,
                      void *stream);
 
 /* Allocation-free variant of rara_render_frame (the paper has no counterpart).

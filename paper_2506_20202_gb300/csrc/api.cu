@@ -1,7 +1,9 @@
-// C ABI of librara.so: context, buffer management, argument checks and stage order.
+// C ABI of librara.so: context, buffer management, argument checks, batch set-up, stage
+// order, CUDA-graph capture of a batch, and the allocation-free frame render.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -17,6 +19,17 @@ struct DevBuf {
     size_t cap = 0;
 };
 
+constexpr int kMaxViews = 4096;
+constexpr int kMaxScenes = 64;
+
+// Host staging of the batch tables (pinned, so uploads are asynchronous). Two copies are
+// used in turn; a copy is refilled only after the upload that last read it has completed.
+struct Staging {
+    ViewDev *views = nullptr;
+    SceneDev *scenes = nullptr;
+    cudaEvent_t uploaded = nullptr;
+};
+
 }  // namespace
 
 struct rara_ctx {
@@ -25,27 +38,43 @@ struct rara_ctx {
     int device = 0;
     char err[512] = {0};
     int64_t launches = 0;
-
-    // frame state
-    int stage = 0;  // 0 empty, 1 preprocessed, 2 binned
-    int n = 0;
-    int W = 0, H = 0;
-    int tiles_x = 0, tiles_y = 0, num_tiles = 0;
-    int64_t n_rendered = 0, n_pairs = 0, n_cutoff = 0;
-    cudaStream_t last_stream = nullptr;
-
-    int sm_count = 0, render_bpsm = 0;
+    int sm_count = 0, bpsm_render = 0, bpsm_sort = 0, bpsm_emit = 0, bpsm_compact = 0;
     int split2_bits = 11, split4_bits = 12;  // heavy-tile split thresholds (list length bit counts)
 
-    // per-Gaussian
-    DevBuf labels, tiles, rect, rec, cut, depth, ckeys, cvals, ckeys_alt, cvals_alt, lookback_g;
-    // per-pair
-    DevBuf pkeys, pvals, pkeys_alt, pvals_alt, lookback_p;
-    DevBuf ranges, tile_order, sort_scratch, counters;
-    Counters *h_counters = nullptr;  // pinned
-    const uint32_t *sorted_gauss = nullptr;  // depth-ordered indices (ckeys/cvals or alt)
-    const uint32_t *sorted_tile_keys = nullptr;
-    const uint32_t *sorted_pair_vals = nullptr;
+    // current batch
+    int stage = 0;  // 0 empty, 1 preprocessed, 2 binned
+    int num_views = 0, num_scenes = 0;
+    uint32_t num_slots = 0, num_tiles = 0, num_units = 0;
+    int tile_passes = 1;
+    uint32_t cap_pairs = 0;             // pair capacity the binning kernels were launched with
+    cudaStream_t last_stream = nullptr;
+    int max_views = 0, max_scenes = 0;
+    Staging staging[2];
+    int staging_next = 0;
+    ViewDev *h_views = nullptr;         // the staging copy holding the current batch
+    SceneDev *h_scenes = nullptr;
+    int *h_view_map = nullptr;          // caller's view index -> internal (scene-grouped) index
+    int *h_view_n = nullptr;            // scene size of each internal view
+    Counters *h_counters = nullptr;     // pinned
+    ViewCounters *h_view_counters = nullptr;  // pinned [max_views]
+
+    // device
+    DevBuf views_d, scenes_d, view_counters_d, counters;
+    DevBuf labels, tiles, rect, rec, cut, depth;
+    DevBuf ckeys, cvals, ckeys_b, cvals_b, lookback_c;
+    DevBuf pkeys, pvals, pkeys_b, pvals_b, lookback_e;
+    DevBuf hist, ranges, items, sort_scratch;
+
+    // captured batch
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int *shape = nullptr;               // host copy of the captured batch shape
+    size_t shape_len = 0;
+    uint32_t graph_cap_pairs = 0;
+    uint32_t min_cap_pairs = 0;         // raised after an overflow
+    int64_t graph_kernels = 0;          // kernel launches one replay makes
+
+    bool owns_host = true;              // false for the static context
 };
 
 namespace {
@@ -118,6 +147,353 @@ int ceil_bits(uint32_t v)
     return b;
 }
 
+void occupancy_setup(rara_ctx *c)
+{
+    if (c->sm_count) return;
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        c->sm_count < 1) {
+        cudaGetLastError();
+        c->sm_count = 1;
+    }
+    c->bpsm_render = render_blocks_per_sm();
+    c->bpsm_sort = sort_blocks_per_sm();
+    c->bpsm_emit = emit_blocks_per_sm();
+    c->bpsm_compact = compact_blocks_per_sm();
+}
+
+int check_gaussians(rara_ctx *c, const rara_gaussians *g)
+{
+    if (!g) return fail(c, RARA_ERR_INVALID_ARG, "null scene");
+    if (g->n < 0 || g->n >= (int64_t)1 << 31) return fail(c, RARA_ERR_INVALID_ARG, "n = %lld out of range", (long long)g->n);
+    if (g->sh_degree < 0 || g->sh_degree > 3) return fail(c, RARA_ERR_INVALID_ARG, "sh_degree %d not in [0,3]", g->sh_degree);
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+        return fail(c, RARA_ERR_INVALID_ARG, "null Gaussian array");
+    return RARA_OK;
+}
+
+int check_view(rara_ctx *c, const rara_camera *cam, const rara_plane *pl)
+{
+    if (!cam || !pl) return fail(c, RARA_ERR_INVALID_ARG, "null camera or plane");
+    if (cam->width <= 0 || cam->height <= 0 || cam->width > 65535 * kTile || cam->height > 65535 * kTile)
+        return fail(c, RARA_ERR_INVALID_ARG, "image size %dx%d", cam->width, cam->height);
+    for (int k = 0; k < 12; ++k)
+        if (!finite(cam->world_to_cam[k])) return fail(c, RARA_ERR_INVALID_ARG, "non-finite camera pose");
+    if (!(finite(cam->fx) && finite(cam->fy) && finite(cam->cx) && finite(cam->cy) && cam->fx > 0 && cam->fy > 0))
+        return fail(c, RARA_ERR_INVALID_ARG, "bad intrinsics");
+    if (!(finite(pl->n[0]) && finite(pl->n[1]) && finite(pl->n[2]) && finite(pl->d)))
+        return fail(c, RARA_ERR_INVALID_ARG, "non-finite plane");
+    if (!(finite(pl->k_sigma) && pl->k_sigma > 0)) return fail(c, RARA_ERR_INVALID_ARG, "k_sigma must be > 0");
+    if (pl->mode < RARA_MODE_NONE || pl->mode > RARA_MODE_RARA_ALL)
+        return fail(c, RARA_ERR_INVALID_ARG, "unknown mode %d", pl->mode);
+    return RARA_OK;
+}
+
+void fill_view(ViewDev &v, const rara_camera *cam, const rara_plane *pl)
+{
+    for (int k = 0; k < 9; ++k) v.cam.R[k] = cam->world_to_cam[(k / 3) * 4 + (k % 3)];
+    for (int k = 0; k < 3; ++k) v.cam.t[k] = cam->world_to_cam[k * 4 + 3];
+    v.cam.fx = cam->fx; v.cam.fy = cam->fy; v.cam.cx = cam->cx; v.cam.cy = cam->cy;
+    v.cam.W = cam->width; v.cam.H = cam->height;
+    for (int j = 0; j < 3; ++j)  // e = -R^T t
+        v.cam.eye[j] = -(v.cam.R[j] * v.cam.t[0] + v.cam.R[3 + j] * v.cam.t[1] + v.cam.R[6 + j] * v.cam.t[2]);
+    for (int k = 0; k < 3; ++k) v.plane.n[k] = pl->n[k];
+    v.plane.d = pl->d;
+    v.plane.k = pl->k_sigma;
+    v.plane.mode = pl->mode;
+    v.tiles_x = (cam->width + kTile - 1) / kTile;
+    v.tiles_y = (cam->height + kTile - 1) / kTile;
+}
+
+// Take the next staging copy, waiting for the upload that last read it.
+int next_staging(rara_ctx *c)
+{
+    Staging &st = c->staging[c->staging_next];
+    if (st.uploaded) {
+        int rc = check_cuda(c, cudaEventSynchronize(st.uploaded), "staging wait");
+        if (rc) return rc;
+    }
+    c->h_views = st.views;
+    c->h_scenes = st.scenes;
+    return RARA_OK;
+}
+
+int upload_tables(rara_ctx *c, cudaStream_t s)
+{
+    int rc;
+    if ((rc = check_cuda(c, cudaMemcpyAsync(c->views_d.p, c->h_views, sizeof(ViewDev) * (size_t)c->num_views,
+                                            cudaMemcpyHostToDevice, s), "view table upload")))
+        return rc;
+    if ((rc = check_cuda(c, cudaMemcpyAsync(c->scenes_d.p, c->h_scenes, sizeof(SceneDev) * (size_t)c->num_scenes,
+                                            cudaMemcpyHostToDevice, s), "scene table upload")))
+        return rc;
+    Staging &st = c->staging[c->staging_next];
+    if (st.uploaded && (rc = check_cuda(c, cudaEventRecord(st.uploaded, s), "staging event"))) return rc;
+    c->staging_next ^= 1;
+    return RARA_OK;
+}
+
+// Build the batch tables (views grouped by scene, in the caller's order within a scene),
+// size the per-slot buffers and upload the tables.
+int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_view *views, int nv, cudaStream_t s)
+{
+    c->stage = 0;
+    if (ns < 1 || ns > c->max_scenes) return fail(c, RARA_ERR_INVALID_ARG, "%d scenes (1..%d)", ns, c->max_scenes);
+    if (nv < 1 || nv > c->max_views) return fail(c, RARA_ERR_INVALID_ARG, "%d views (1..%d)", nv, c->max_views);
+    int rc;
+    for (int i = 0; i < ns; ++i)
+        if ((rc = check_gaussians(c, &scenes[i]))) return rc;
+    for (int v = 0; v < nv; ++v) {
+        if (views[v].scene < 0 || views[v].scene >= ns)
+            return fail(c, RARA_ERR_INVALID_ARG, "view %d refers to scene %d of %d", v, views[v].scene, ns);
+        if ((rc = check_view(c, &views[v].camera, &views[v].plane))) return rc;
+        if (!views[v].image) return fail(c, RARA_ERR_INVALID_ARG, "view %d has no image buffer", v);
+    }
+    if ((rc = next_staging(c))) return rc;
+    uint64_t slots = 0, tiles = 0;
+    uint32_t units = 0;
+    int k = 0;
+    for (int si = 0; si < ns; ++si) {
+        SceneDev &sd = c->h_scenes[si];
+        const rara_gaussians &g = scenes[si];
+        sd.means = g.means; sd.log_scales = g.log_scales; sd.quats = g.quats; sd.logits = g.opacity_logits;
+        sd.sh = g.sh;
+        sd.n = (int)g.n;
+        sd.sh_degree = g.sh_degree;
+        sd.view_begin = k;
+        sd.unit_begin = units;
+        for (int v = 0; v < nv; ++v) {
+            if (views[v].scene != si) continue;
+            ViewDev &vd = c->h_views[k];
+            fill_view(vd, &views[v].camera, &views[v].plane);
+            vd.scene = si;
+            vd.tile_base = (uint32_t)tiles;
+            vd.slot_base = (uint32_t)slots;
+            for (int j = 0; j < 3; ++j) vd.bg[j] = views[v].bg[j];
+            vd.image = views[v].image;
+            vd.final_T = views[v].final_T;
+            vd.n_contrib = views[v].n_contrib;
+            c->h_view_map[v] = k;
+            c->h_view_n[k] = (int)g.n;
+            tiles += (uint64_t)vd.tiles_x * vd.tiles_y;
+            slots += (uint64_t)g.n;
+            ++k;
+        }
+        sd.view_count = k - sd.view_begin;
+        if (sd.view_count > 0) units += (uint32_t)((g.n + kBlock - 1) / kBlock);
+    }
+    if (slots >= ((uint64_t)1 << 32) - 1)
+        return fail(c, RARA_ERR_INVALID_ARG, "%llu slots exceed 2^32", (unsigned long long)slots);
+    if (tiles >= ((uint64_t)1 << 28))
+        return fail(c, RARA_ERR_INVALID_ARG, "%llu tiles exceed 2^28", (unsigned long long)tiles);
+    c->num_views = nv;
+    c->num_scenes = ns;
+    c->num_slots = (uint32_t)slots;
+    c->num_tiles = (uint32_t)tiles;
+    c->num_units = units;
+    c->tile_passes = (ceil_bits(c->num_tiles) + 7) / 8;
+    if (c->tile_passes < 1) c->tile_passes = 1;
+    const size_t nn = slots > 0 ? (size_t)slots : 1;
+    const size_t nt = tiles > 0 ? (size_t)tiles : 1;
+    if ((rc = ensure(c, c->views_d, sizeof(ViewDev) * (size_t)nv, "view table")) ||
+        (rc = ensure(c, c->scenes_d, sizeof(SceneDev) * (size_t)ns, "scene table")) ||
+        (rc = ensure(c, c->view_counters_d, sizeof(ViewCounters) * (size_t)nv, "view counters")) ||
+        (rc = ensure(c, c->labels, nn, "labels")) || (rc = ensure(c, c->tiles, nn * 4, "tiles")) ||
+        (rc = ensure(c, c->rect, nn * 8, "rect")) || (rc = ensure(c, c->rec, nn * sizeof(SplatRec), "records")) ||
+        (rc = ensure(c, c->cut, nn * sizeof(CutRec), "cutoff records")) ||
+        (rc = ensure(c, c->depth, nn * 4, "depth")) || (rc = ensure(c, c->ckeys, nn * 4, "depth keys")) ||
+        (rc = ensure(c, c->cvals, nn * 4, "depth values")) || (rc = ensure(c, c->ckeys_b, nn * 4, "depth keys B")) ||
+        (rc = ensure(c, c->cvals_b, nn * 4, "depth values B")) ||
+        (rc = ensure(c, c->lookback_c, (nn / 1024 + 2) * 8, "compaction scan words")) ||
+        (rc = ensure(c, c->lookback_e, (nn / kBlock + 2) * 8, "emission scan words")) ||
+        (rc = ensure(c, c->hist, 8 * 256 * 4, "digit histograms")) ||
+        (rc = ensure(c, c->ranges, nt * sizeof(int2), "ranges")) ||
+        (rc = ensure(c, c->items, nt * 16, "render items")))
+        return rc;
+    return upload_tables(c, s);
+}
+
+// Stage (a): preprocess + compaction.
+int batch_preprocess(rara_ctx *c, cudaStream_t s)
+{
+    int rc;
+    occupancy_setup(c);
+    Counters *dc = (Counters *)c->counters.p;
+    const size_t nn = c->num_slots > 0 ? (size_t)c->num_slots : 1;
+    if ((rc = check_cuda(c, cudaMemsetAsync(dc, 0, sizeof(Counters), s), "memset counters")) ||
+        (rc = check_cuda(c, cudaMemsetAsync(c->view_counters_d.p, 0, sizeof(ViewCounters) * (size_t)c->num_views, s),
+                         "memset view counters")) ||
+        (rc = check_cuda(c, cudaMemsetAsync(c->hist.p, 0, 8 * 256 * 4, s), "memset histograms")) ||
+        (rc = check_cuda(c, cudaMemsetAsync(c->lookback_c.p, 0, (nn / 1024 + 2) * 8, s), "memset scan")))
+        return rc;
+    PreprocessArgs a;
+    a.scenes = (const SceneDev *)c->scenes_d.p;
+    a.num_scenes = c->num_scenes;
+    a.views = (const ViewDev *)c->views_d.p;
+    a.num_units = (int)c->num_units;
+    a.labels = (uint8_t *)c->labels.p;
+    a.tiles = (uint32_t *)c->tiles.p;
+    a.rect = (uint2 *)c->rect.p;
+    a.rec = (SplatRec *)c->rec.p;
+    a.cut = (CutRec *)c->cut.p;
+    a.depth = (float *)c->depth.p;
+    a.view_counters = (ViewCounters *)c->view_counters_d.p;
+    a.counters = dc;
+    launch_preprocess(a, (int)c->num_units, s);
+    if ((rc = launched(c, "preprocess launch", c->num_units > 0))) return rc;
+
+    CompactArgs ca;
+    ca.tiles = (const uint32_t *)c->tiles.p;
+    ca.depth = (const float *)c->depth.p;
+    ca.num_slots = c->num_slots;
+    ca.keys = (uint32_t *)c->ckeys.p;
+    ca.vals = (uint32_t *)c->cvals.p;
+    ca.hist = (uint32_t *)c->hist.p;
+    ca.lookback = (unsigned long long *)c->lookback_c.p;
+    ca.counters = dc;
+    const uint32_t parts = (c->num_slots + 1023) / 1024;
+    const uint32_t slots = (uint32_t)(c->sm_count * c->bpsm_compact);
+    const int cgrid = (int)(parts < slots ? parts : slots);
+    launch_compact(ca, cgrid, s);
+    return launched(c, "compaction launch", cgrid > 0);
+}
+
+int copy_counters(rara_ctx *c, cudaStream_t s)
+{
+    int rc;
+    if ((rc = check_cuda(c, cudaMemcpyAsync(c->h_counters, c->counters.p, sizeof(Counters), cudaMemcpyDeviceToHost, s),
+                         "counter copy")))
+        return rc;
+    return check_cuda(c, cudaMemcpyAsync(c->h_view_counters, c->view_counters_d.p,
+                                         sizeof(ViewCounters) * (size_t)c->num_views, cudaMemcpyDeviceToHost, s),
+                      "view counter copy");
+}
+
+// Buffers that depend on the pair capacity.
+int ensure_pairs(rara_ctx *c, uint32_t cap)
+{
+    const size_t pp = cap > 0 ? (size_t)cap : 1;
+    const size_t nn = c->num_slots > 0 ? (size_t)c->num_slots : 1;
+    const size_t sb1 = sort_scratch_bytes((int64_t)nn, 4), sb2 = sort_scratch_bytes((int64_t)pp, c->tile_passes);
+    int rc;
+    if ((rc = ensure(c, c->pkeys, pp * 4, "pair keys")) || (rc = ensure(c, c->pvals, pp * 4, "pair values")) ||
+        (rc = ensure(c, c->pkeys_b, pp * 4, "pair keys B")) || (rc = ensure(c, c->pvals_b, pp * 4, "pair values B")) ||
+        (rc = ensure(c, c->sort_scratch, sb1 > sb2 ? sb1 : sb2, "sort scratch")))
+        return rc;
+    return RARA_OK;
+}
+
+// Stage (b): depth sort, emission, tile sort, ranges, render order. The pair buffers must
+// hold cap pairs (ensure_pairs); counts come from the device.
+int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
+{
+    int rc;
+    occupancy_setup(c);
+    Counters *dc = (Counters *)c->counters.p;
+    uint32_t *hist = (uint32_t *)c->hist.p;
+    const size_t nn = c->num_slots > 0 ? (size_t)c->num_slots : 1;
+    c->cap_pairs = cap;
+    const int sgrid = c->sm_count * c->bpsm_sort;
+    int nl = sort_launch((uint32_t *)c->ckeys.p, (uint32_t *)c->cvals.p, (uint32_t *)c->ckeys_b.p,
+                         (uint32_t *)c->cvals_b.p, &dc->n_rendered, (uint32_t)nn, 4, hist, c->sort_scratch.p,
+                         &dc->ticket[kTicketSortDepth], &dc->status, &dc->depth_in_b, sgrid, s);
+    if ((rc = launched(c, "depth sort", nl))) return rc;
+
+    if ((rc = check_cuda(c, cudaMemsetAsync(c->lookback_e.p, 0, (nn / kBlock + 2) * 8, s), "memset emit")))
+        return rc;
+    EmitArgs e;
+    e.keys_a = (const uint32_t *)c->ckeys.p;
+    e.vals_a = (const uint32_t *)c->cvals.p;
+    e.keys_b = (const uint32_t *)c->ckeys_b.p;
+    e.vals_b = (const uint32_t *)c->cvals_b.p;
+    e.tiles = (const uint32_t *)c->tiles.p;
+    e.rect = (const uint2 *)c->rect.p;
+    e.views = (const ViewDev *)c->views_d.p;
+    e.num_views = c->num_views;
+    e.cap_pairs = cap;
+    e.tile_passes = c->tile_passes;
+    e.pair_keys = (uint32_t *)c->pkeys.p;
+    e.pair_vals = (uint32_t *)c->pvals.p;
+    e.tile_hist = hist + 4 * 256;
+    e.lookback = (unsigned long long *)c->lookback_e.p;
+    e.counters = dc;
+    launch_emit(e, c->sm_count * c->bpsm_emit, s);
+    if ((rc = launched(c, "emit"))) return rc;
+
+    nl = sort_launch((uint32_t *)c->pkeys.p, (uint32_t *)c->pvals.p, (uint32_t *)c->pkeys_b.p,
+                     (uint32_t *)c->pvals_b.p, &dc->n_pairs, cap, c->tile_passes, hist + 4 * 256, c->sort_scratch.p,
+                     &dc->ticket[kTicketSortTile], &dc->status, &dc->tile_in_b, sgrid, s);
+    if ((rc = launched(c, "tile sort", nl))) return rc;
+
+    const size_t nt = c->num_tiles > 0 ? (size_t)c->num_tiles : 1;
+    if ((rc = check_cuda(c, cudaMemsetAsync(c->ranges.p, 0, nt * sizeof(int2), s), "memset ranges"))) return rc;
+    const uint32_t rblocks = (cap + 255) / 256;
+    const uint32_t rmax = (uint32_t)(c->sm_count * 8);
+    const int rgrid = (int)(rblocks < rmax ? (rblocks > 0 ? rblocks : 1) : rmax);
+    launch_ranges((const uint32_t *)c->pkeys.p, (const uint32_t *)c->pkeys_b.p, dc, cap, c->num_tiles,
+                  (int2 *)c->ranges.p, rgrid, s);
+    if ((rc = launched(c, "ranges"))) return rc;
+    launch_tile_order((const int2 *)c->ranges.p, (int)c->num_tiles, c->split2_bits, c->split4_bits,
+                      (uint32_t *)c->items.p, dc, s);
+    return launched(c, "tile order", c->num_tiles > 0);
+}
+
+// Stages (c)+(d): the render of every view.
+int batch_render(rara_ctx *c, cudaStream_t s)
+{
+    int rc;
+    occupancy_setup(c);
+    Counters *dc = (Counters *)c->counters.p;
+    if ((rc = check_cuda(c, cudaMemsetAsync(&dc->n_evaluated, 0, kRenderCounterBytes, s), "memset render counters")))
+        return rc;
+    RenderArgs a;
+    a.ranges = (const int2 *)c->ranges.p;
+    a.tile_order = (const uint32_t *)c->items.p;
+    a.vals_a = (const uint32_t *)c->pvals.p;
+    a.vals_b = (const uint32_t *)c->pvals_b.p;
+    a.rec = (const SplatRec *)c->rec.p;
+    a.cut = (const CutRec *)c->cut.p;
+    a.views = (const ViewDev *)c->views_d.p;
+    a.num_views = c->num_views;
+    a.counters = dc;
+    const long long slots = (long long)c->sm_count * c->bpsm_render;
+    const long long items = 4ll * c->num_tiles;
+    launch_render(a, (int)(items < slots ? items : slots), s);
+    return launched(c, "render launch", c->num_tiles > 0);
+}
+
+// Exact binning: wait for the preprocess to know the pair count, size the buffers, launch.
+int bin_exact(rara_ctx *c, cudaStream_t s)
+{
+    int rc;
+    if ((rc = check_cuda(c, cudaStreamSynchronize(s), "cudaStreamSynchronize"))) return rc;
+    if (c->h_counters->status & kStatusLookbackTimeout) {
+        c->stage = 0;
+        return fail(c, RARA_ERR_TIMEOUT, "a chained-scan wait exceeded its bound; the frame is invalid");
+    }
+    const unsigned long long np = c->h_counters->n_pairs;
+    if (np >= (1ull << 30)) return fail(c, RARA_ERR_BUDGET, "%llu pairs exceed 2^30", np);
+    const uint32_t cap = (uint32_t)(np > 0 ? np : 1);
+    if ((rc = ensure_pairs(c, cap))) return rc;
+    return batch_bin(c, cap, s);
+}
+
+void free_host(rara_ctx *c)
+{
+    if (!c->owns_host) return;
+    for (Staging &st : c->staging) {
+        if (st.views) cudaFreeHost(st.views);
+        if (st.scenes) cudaFreeHost(st.scenes);
+        if (st.uploaded) cudaEventDestroy(st.uploaded);
+    }
+    if (c->h_counters) cudaFreeHost(c->h_counters);
+    if (c->h_view_counters) cudaFreeHost(c->h_view_counters);
+    free(c->h_view_map);
+    free(c->h_view_n);
+    free(c->shape);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+}
+
 }  // namespace
 
 extern "C" {
@@ -131,13 +507,27 @@ int rara_ctx_create(size_t budget_bytes, int32_t tile_w, int32_t tile_h, rara_ct
     if (!c) return RARA_ERR_BUDGET;
     c->budget = budget_bytes;
     cudaGetDevice(&c->device);
-    int rc = ensure(c, c->counters, sizeof(Counters), "counters");
-    if (rc == RARA_OK && cudaHostAlloc((void **)&c->h_counters, sizeof(Counters), cudaHostAllocDefault) != cudaSuccess)
-        rc = fail(c, RARA_ERR_CUDA, "cudaHostAlloc failed");
-    if (rc != RARA_OK) {
+    c->max_views = kMaxViews;
+    c->max_scenes = kMaxScenes;
+    bool ok = ensure(c, c->counters, sizeof(Counters), "counters") == RARA_OK;
+    for (Staging &st : c->staging) {
+        ok = ok && cudaHostAlloc((void **)&st.views, sizeof(ViewDev) * kMaxViews, cudaHostAllocDefault) == cudaSuccess;
+        ok = ok && cudaHostAlloc((void **)&st.scenes, sizeof(SceneDev) * kMaxScenes, cudaHostAllocDefault) ==
+                       cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&st.uploaded, cudaEventDisableTiming) == cudaSuccess;
+    }
+    ok = ok && cudaHostAlloc((void **)&c->h_counters, sizeof(Counters), cudaHostAllocDefault) == cudaSuccess;
+    ok = ok && cudaHostAlloc((void **)&c->h_view_counters, sizeof(ViewCounters) * kMaxViews, cudaHostAllocDefault) ==
+                   cudaSuccess;
+    c->h_view_map = (int *)malloc(sizeof(int) * kMaxViews);
+    c->h_view_n = (int *)malloc(sizeof(int) * kMaxViews);
+    ok = ok && c->h_view_map && c->h_view_n;
+    if (!ok) {
+        cudaGetLastError();
         release(c, c->counters);
+        free_host(c);
         delete c;
-        return rc;
+        return RARA_ERR_CUDA;
     }
     memset(c->h_counters, 0, sizeof(Counters));
     *out = c;
@@ -148,11 +538,12 @@ int rara_ctx_destroy(rara_ctx *c)
 {
     if (!c) return RARA_OK;
     cudaDeviceSynchronize();
-    DevBuf *all[] = {&c->labels, &c->tiles, &c->rect, &c->rec, &c->cut, &c->depth, &c->ckeys, &c->cvals,
-                     &c->ckeys_alt, &c->cvals_alt, &c->lookback_g, &c->pkeys, &c->pvals, &c->pkeys_alt,
-                     &c->pvals_alt, &c->lookback_p, &c->ranges, &c->tile_order, &c->sort_scratch, &c->counters};
+    DevBuf *all[] = {&c->views_d, &c->scenes_d, &c->view_counters_d, &c->counters, &c->labels, &c->tiles,
+                     &c->rect, &c->rec, &c->cut, &c->depth, &c->ckeys, &c->cvals, &c->ckeys_b, &c->cvals_b,
+                     &c->lookback_c, &c->pkeys, &c->pvals, &c->pkeys_b, &c->pvals_b, &c->lookback_e, &c->hist,
+                     &c->ranges, &c->items, &c->sort_scratch};
     for (DevBuf *b : all) release(c, *b);
-    if (c->h_counters) cudaFreeHost(c->h_counters);
+    free_host(c);
     delete c;
     return RARA_OK;
 }
@@ -168,6 +559,7 @@ int rara_ctx_set_tuning(rara_ctx *c, int32_t split2_bits, int32_t split4_bits)
     if (!c) return RARA_ERR_INVALID_ARG;
     c->split2_bits = split2_bits < 0 ? 0 : (split2_bits > 33 ? 33 : split2_bits);
     c->split4_bits = split4_bits < 0 ? 0 : (split4_bits > 33 ? 33 : split4_bits);
+    c->shape_len = 0;  // a captured graph holds the old values: recapture
     return RARA_OK;
 }
 
@@ -182,6 +574,14 @@ int rara_ctx_sync(rara_ctx *c, void *stream)
     if (rc) return rc;
     if (c->h_counters->status & kStatusLookbackTimeout)
         return fail(c, RARA_ERR_TIMEOUT, "a chained-scan wait exceeded its bound; the frame is invalid");
+    if (c->h_counters->status & kStatusOverflow) {
+        const unsigned long long np = c->h_counters->n_pairs;
+        const unsigned long long want = np + np / 4 + 4096;
+        c->min_cap_pairs = (uint32_t)(want < (1ull << 30) ? want : (1ull << 30) - 1);
+        c->shape_len = 0;  // recapture with the larger capacity
+        return fail(c, RARA_ERR_OVERFLOW, "%llu pairs exceeded the captured capacity %u; render the batch again", np,
+                    c->cap_pairs);
+    }
     return RARA_OK;
 }
 
@@ -192,78 +592,17 @@ int rara_preprocess(rara_ctx *c, const rara_gaussians *g, const rara_camera *cam
     c->err[0] = 0;
     c->stage = 0;
     if (!g || !cam || !pl) return fail(c, RARA_ERR_INVALID_ARG, "null argument");
-    if (g->n < 0 || g->n >= (int64_t)1 << 31) return fail(c, RARA_ERR_INVALID_ARG, "n = %lld out of range", (long long)g->n);
-    if (g->sh_degree < 0 || g->sh_degree > 3) return fail(c, RARA_ERR_INVALID_ARG, "sh_degree %d not in [0,3]", g->sh_degree);
-    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
-        return fail(c, RARA_ERR_INVALID_ARG, "null Gaussian array");
-    if (cam->width <= 0 || cam->height <= 0 || cam->width > 65535 * kTile || cam->height > 65535 * kTile)
-        return fail(c, RARA_ERR_INVALID_ARG, "image size %dx%d", cam->width, cam->height);
-    for (int k = 0; k < 12; ++k)
-        if (!finite(cam->world_to_cam[k])) return fail(c, RARA_ERR_INVALID_ARG, "non-finite camera pose");
-    if (!(finite(cam->fx) && finite(cam->fy) && finite(cam->cx) && finite(cam->cy) && cam->fx > 0 && cam->fy > 0))
-        return fail(c, RARA_ERR_INVALID_ARG, "bad intrinsics");
-    if (!(finite(pl->n[0]) && finite(pl->n[1]) && finite(pl->n[2]) && finite(pl->d)))
-        return fail(c, RARA_ERR_INVALID_ARG, "non-finite plane");
-    if (!(finite(pl->k_sigma) && pl->k_sigma > 0)) return fail(c, RARA_ERR_INVALID_ARG, "k_sigma must be > 0");
-    if (pl->mode < RARA_MODE_NONE || pl->mode > RARA_MODE_RARA_ALL)
-        return fail(c, RARA_ERR_INVALID_ARG, "unknown mode %d", pl->mode);
-
+    rara_view v;
+    memset(&v, 0, sizeof(v));
+    v.scene = 0;
+    v.camera = *cam;
+    v.plane = *pl;
+    v.image = (float *)1;  // placeholder checked by batch_setup; rara_render supplies the outputs
     cudaStream_t s = (cudaStream_t)stream;
-    const int n = (int)g->n;
-    c->n = n;
-    c->W = cam->width;
-    c->H = cam->height;
-    c->tiles_x = (cam->width + kTile - 1) / kTile;
-    c->tiles_y = (cam->height + kTile - 1) / kTile;
-    c->num_tiles = c->tiles_x * c->tiles_y;
-    const size_t nn = (size_t)(n > 0 ? n : 1);
-    const int blocks = (n + kBlock - 1) / kBlock;
-    int rc;
-    if ((rc = ensure(c, c->labels, nn, "labels")) || (rc = ensure(c, c->tiles, nn * 4, "tiles")) ||
-        (rc = ensure(c, c->rect, nn * 8, "rect")) || (rc = ensure(c, c->rec, nn * sizeof(SplatRec), "records")) ||
-        (rc = ensure(c, c->cut, nn * sizeof(CutRec), "cutoff records")) ||
-        (rc = ensure(c, c->depth, nn * 4, "depth")) ||
-        (rc = ensure(c, c->ckeys, nn * 4, "depth keys")) || (rc = ensure(c, c->cvals, nn * 4, "depth values")) ||
-        (rc = ensure(c, c->ckeys_alt, nn * 4, "depth keys alt")) ||
-        (rc = ensure(c, c->cvals_alt, nn * 4, "depth values alt")) ||
-        (rc = ensure(c, c->lookback_g, (size_t)(blocks + 1) * 8, "scan words")))
-        return rc;
-
-    PreprocessArgs a;
-    a.means = g->means; a.log_scales = g->log_scales; a.quats = g->quats; a.logits = g->opacity_logits; a.sh = g->sh;
-    a.n = n;
-    a.sh_degree = g->sh_degree;
-    for (int k = 0; k < 9; ++k) a.cam.R[k] = cam->world_to_cam[(k / 3) * 4 + (k % 3)];
-    for (int k = 0; k < 3; ++k) a.cam.t[k] = cam->world_to_cam[k * 4 + 3];
-    a.cam.fx = cam->fx; a.cam.fy = cam->fy; a.cam.cx = cam->cx; a.cam.cy = cam->cy;
-    a.cam.W = cam->width; a.cam.H = cam->height;
-    for (int j = 0; j < 3; ++j)  // e = -R^T t
-        a.cam.eye[j] = -(a.cam.R[j] * a.cam.t[0] + a.cam.R[3 + j] * a.cam.t[1] + a.cam.R[6 + j] * a.cam.t[2]);
-    for (int k = 0; k < 3; ++k) a.plane.n[k] = pl->n[k];
-    a.plane.d = pl->d;
-    a.plane.k = pl->k_sigma;
-    a.plane.mode = pl->mode;
-    a.tiles_x = c->tiles_x;
-    a.tiles_y = c->tiles_y;
-    a.labels = (uint8_t *)c->labels.p;
-    a.tiles = (uint32_t *)c->tiles.p;
-    a.rect = (uint2 *)c->rect.p;
-    a.rec = (SplatRec *)c->rec.p;
-    a.cut = (CutRec *)c->cut.p;
-    a.depth = (float *)c->depth.p;
-    a.ckeys = (uint32_t *)c->ckeys.p;
-    a.cvals = (uint32_t *)c->cvals.p;
-    a.lookback = (unsigned long long *)c->lookback_g.p;
-    a.counters = (Counters *)c->counters.p;
-
-    if ((rc = check_cuda(c, cudaMemsetAsync(c->counters.p, 0, sizeof(Counters), s), "memset counters"))) return rc;
-    if ((rc = check_cuda(c, cudaMemsetAsync(c->lookback_g.p, 0, (size_t)(blocks + 1) * 8, s), "memset scan")))
-        return rc;
-    launch_preprocess(a, blocks, s);
-    if ((rc = launched(c, "preprocess launch", blocks > 0))) return rc;
-    if ((rc = check_cuda(c, cudaMemcpyAsync(c->h_counters, c->counters.p, sizeof(Counters), cudaMemcpyDeviceToHost, s),
-                         "counter copy")))
-        return rc;
+    int rc = batch_setup(c, g, 1, &v, 1, s);
+    if (rc) return rc;
+    if ((rc = batch_preprocess(c, s))) return rc;
+    if ((rc = copy_counters(c, s))) return rc;
     c->last_stream = s;
     c->stage = 1;
     return RARA_OK;
@@ -273,75 +612,11 @@ int rara_bin(rara_ctx *c, void *stream)
 {
     if (!c) return RARA_ERR_INVALID_ARG;
     if (c->stage < 1) return fail(c, RARA_ERR_INVALID_ARG, "rara_bin called before rara_preprocess");
-    cudaStream_t s = (cudaStream_t)stream;
-    int rc;
     // The counter copy was queued by rara_preprocess on its stream; wait for that stream.
-    if ((rc = check_cuda(c, cudaStreamSynchronize(c->last_stream), "cudaStreamSynchronize"))) return rc;
-    if (c->h_counters->status & kStatusLookbackTimeout) {
-        c->stage = 0;
-        return fail(c, RARA_ERR_TIMEOUT, "a chained-scan wait exceeded its bound; the frame is invalid");
-    }
-    c->n_rendered = (int64_t)c->h_counters->n_rendered;
-    c->n_pairs = (int64_t)c->h_counters->n_pairs;
-    c->n_cutoff = (int64_t)c->h_counters->n_cutoff;
-    if (c->n_pairs >= (int64_t)1 << 30) return fail(c, RARA_ERR_BUDGET, "%lld pairs exceed 2^30", (long long)c->n_pairs);
-    const int nr = (int)c->n_rendered;
-    const int np = (int)c->n_pairs;
-    const size_t pp = (size_t)(np > 0 ? np : 1);
-    const int tile_bits = ceil_bits((uint32_t)c->num_tiles);
-    const size_t sbytes = sort_scratch_bytes(np > nr ? np : nr, 32);  // both sorts, worst case
-    const int eblocks = (nr + kBlock - 1) / kBlock;
-    if ((rc = ensure(c, c->pkeys, pp * 4, "pair keys")) || (rc = ensure(c, c->pvals, pp * 4, "pair values")) ||
-        (rc = ensure(c, c->pkeys_alt, pp * 4, "pair keys alt")) ||
-        (rc = ensure(c, c->pvals_alt, pp * 4, "pair values alt")) ||
-        (rc = ensure(c, c->lookback_p, (size_t)(eblocks + 1) * 8, "emit scan words")) ||
-        (rc = ensure(c, c->ranges, (size_t)c->num_tiles * sizeof(int2), "ranges")) ||
-        (rc = ensure(c, c->tile_order, (size_t)c->num_tiles * 16, "render items")) ||
-        (rc = ensure(c, c->sort_scratch, sbytes, "sort scratch")))
-        return rc;
-    uint32_t *status = &((Counters *)c->counters.p)->status;
-
-    // 1. depth sort of the rendered Gaussians (ascending float bits = ascending depth > 0)
-    bool in_alt = false;
-    int nl = sort_pairs((uint32_t *)c->ckeys.p, (uint32_t *)c->cvals.p, (uint32_t *)c->ckeys_alt.p,
-                        (uint32_t *)c->cvals_alt.p, nr, 32, c->sort_scratch.p, status, s, &in_alt);
-    if ((rc = launched(c, "depth sort", nl))) return rc;
-    c->sorted_gauss = (const uint32_t *)(in_alt ? c->cvals_alt.p : c->cvals.p);
-
-    // 2. emit (tile id, index) pairs in depth order
-    if ((rc = check_cuda(c, cudaMemsetAsync(c->lookback_p.p, 0, (size_t)(eblocks + 1) * 8, s), "memset emit")))
-        return rc;
-    EmitArgs e;
-    e.sorted_vals = c->sorted_gauss;
-    e.tiles = (const uint32_t *)c->tiles.p;
-    e.rect = (const uint2 *)c->rect.p;
-    e.n_rendered = nr;
-    e.tiles_x = c->tiles_x;
-    e.n_pairs = (unsigned long long)np;
-    e.pair_keys = (uint32_t *)c->pkeys.p;
-    e.pair_vals = (uint32_t *)c->pvals.p;
-    e.lookback = (unsigned long long *)c->lookback_p.p;
-    e.counters = (Counters *)c->counters.p;
-    launch_emit(e, eblocks, s);
-    if ((rc = launched(c, "emit", eblocks > 0))) return rc;
-
-    // 3. stable sort of the pairs by tile id (the depth order is kept within a tile)
-    nl = sort_pairs((uint32_t *)c->pkeys.p, (uint32_t *)c->pvals.p, (uint32_t *)c->pkeys_alt.p,
-                    (uint32_t *)c->pvals_alt.p, np, tile_bits, c->sort_scratch.p, status, s, &in_alt);
-    if ((rc = launched(c, "tile sort", nl))) return rc;
-    c->sorted_tile_keys = (const uint32_t *)(in_alt ? c->pkeys_alt.p : c->pkeys.p);
-    c->sorted_pair_vals = (const uint32_t *)(in_alt ? c->pvals_alt.p : c->pvals.p);
-
-    // 4. tile ranges
-    if ((rc = check_cuda(c, cudaMemsetAsync(c->ranges.p, 0, (size_t)c->num_tiles * sizeof(int2), s), "memset ranges")))
-        return rc;
-    launch_ranges(c->sorted_tile_keys, np, c->num_tiles, (int2 *)c->ranges.p, s);
-    if ((rc = launched(c, "ranges", np > 0))) return rc;
-
-    // 5. heaviest-first order of the tiles for the render's persistent blocks
-    launch_tile_order((const int2 *)c->ranges.p, c->num_tiles, c->split2_bits, c->split4_bits,
-                      (uint32_t *)c->tile_order.p, (Counters *)c->counters.p, s);
-    if ((rc = launched(c, "tile order", c->num_tiles > 0))) return rc;
+    int rc = check_cuda(c, cudaStreamSynchronize(c->last_stream), "cudaStreamSynchronize");
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = bin_exact(c, s))) return rc;
     c->last_stream = s;
     c->stage = 2;
     return RARA_OK;
@@ -352,38 +627,21 @@ int rara_render(rara_ctx *c, const float bg[3], float *image, float *final_T, ui
     if (!c) return RARA_ERR_INVALID_ARG;
     if (c->stage < 2) return fail(c, RARA_ERR_INVALID_ARG, "rara_render called before rara_bin");
     if (!bg || !image) return fail(c, RARA_ERR_INVALID_ARG, "null bg or image");
+    if (c->num_views != 1) return fail(c, RARA_ERR_INVALID_ARG, "rara_render follows a single-view rara_preprocess");
     cudaStream_t s = (cudaStream_t)stream;
-    if (c->sm_count == 0) {
-        if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
-            c->sm_count < 1) {
-            cudaGetLastError();
-            c->sm_count = 1;
-        }
-        c->render_bpsm = render_blocks_per_sm();
-    }
-    RenderArgs a;
-    a.ranges = (const int2 *)c->ranges.p;
-    a.tile_order = (const uint32_t *)c->tile_order.p;
-    a.num_tiles = c->num_tiles;
-    a.pair_vals = c->sorted_pair_vals;
-    a.rec = (const SplatRec *)c->rec.p;
-    a.cut = (const CutRec *)c->cut.p;
-    a.W = c->W;
-    a.H = c->H;
-    a.tiles_x = c->tiles_x;
-    a.bg[0] = bg[0]; a.bg[1] = bg[1]; a.bg[2] = bg[2];
-    a.image = image;
-    a.final_T = final_T;
-    a.n_contrib = n_contrib;
-    a.counters = (Counters *)c->counters.p;
-    int rc;
-    if ((rc = check_cuda(c, cudaMemsetAsync(&a.counters->n_evaluated, 0, kRenderCounterBytes, s),
-                         "memset render counters")))
-        return rc;
-    const int slots = c->sm_count * c->render_bpsm;
-    const int grid = 4 * c->num_tiles < slots ? 4 * c->num_tiles : slots;
-    launch_render(a, grid, s);
-    if ((rc = launched(c, "render launch", c->num_tiles > 0))) return rc;
+    // The staging copy holding this view was uploaded by rara_preprocess, which rara_bin
+    // waited for; refill its output fields and upload the view again.
+    ViewDev &v = c->h_views[0];
+    for (int j = 0; j < 3; ++j) v.bg[j] = bg[j];
+    v.image = image;
+    v.final_T = final_T;
+    v.n_contrib = n_contrib;
+    int rc = check_cuda(c, cudaMemcpyAsync(c->views_d.p, c->h_views, sizeof(ViewDev), cudaMemcpyHostToDevice, s),
+                        "view table upload");
+    if (rc) return rc;
+    Staging &st = c->staging[c->staging_next ^ 1];  // the copy that holds h_views
+    if (st.uploaded && (rc = check_cuda(c, cudaEventRecord(st.uploaded, s), "staging event"))) return rc;
+    if ((rc = batch_render(c, s))) return rc;
     c->last_stream = s;
     return RARA_OK;
 }
@@ -398,18 +656,132 @@ int rara_render_frame(rara_ctx *c, const rara_gaussians *g, const rara_camera *c
     return rara_render(c, bg, image, final_T, n_contrib, stream);
 }
 
-int rara_frame_info_get(rara_ctx *c, rara_frame_info *out)
+int rara_render_batch(rara_ctx *c, const rara_gaussians *scenes, int32_t num_scenes, const rara_view *views,
+                      int32_t num_views, void *stream)
+{
+    if (!c) return RARA_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (!scenes || !views) return fail(c, RARA_ERR_INVALID_ARG, "null scenes or views");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = batch_setup(c, scenes, num_scenes, views, num_views, s))) return rc;
+    if ((rc = batch_preprocess(c, s))) return rc;
+    if ((rc = copy_counters(c, s))) return rc;
+    if ((rc = bin_exact(c, s))) return rc;
+    if ((rc = batch_render(c, s))) return rc;
+    c->last_stream = s;
+    c->stage = 2;
+    return RARA_OK;
+}
+
+int rara_render_batch_graph(rara_ctx *c, const rara_gaussians *scenes, int32_t num_scenes, const rara_view *views,
+                            int32_t num_views, void *stream)
+{
+    if (!c) return RARA_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (!scenes || !views || num_scenes < 1 || num_views < 1 || num_scenes > c->max_scenes ||
+        num_views > c->max_views)
+        return fail(c, RARA_ERR_INVALID_ARG, "bad batch (%d scenes, %d views)", num_scenes, num_views);
+    if (!c->owns_host) return fail(c, RARA_ERR_INVALID_ARG, "graph batches need a regular context");
+    // batch shape: scene sizes and degrees, views' scene and resolution
+    const size_t len = 2 + 2 * (size_t)num_scenes + 3 * (size_t)num_views;
+    int *shape = (int *)malloc(sizeof(int) * len);
+    if (!shape) return fail(c, RARA_ERR_BUDGET, "host allocation failed");
+    size_t k = 0;
+    shape[k++] = num_scenes;
+    shape[k++] = num_views;
+    for (int i = 0; i < num_scenes; ++i) {
+        shape[k++] = (int)scenes[i].n;
+        shape[k++] = scenes[i].sh_degree;
+    }
+    for (int v = 0; v < num_views; ++v) {
+        shape[k++] = views[v].scene;
+        shape[k++] = views[v].camera.width;
+        shape[k++] = views[v].camera.height;
+    }
+    const bool same = c->graph && c->shape && c->shape_len == len && memcmp(c->shape, shape, sizeof(int) * len) == 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if (same) {
+        free(shape);
+        if ((rc = batch_setup(c, scenes, num_scenes, views, num_views, s))) return rc;
+        c->cap_pairs = c->graph_cap_pairs;
+        if ((rc = check_cuda(c, cudaGraphLaunch(c->graph, s), "cudaGraphLaunch"))) return rc;
+        c->launches += c->graph_kernels;
+        c->last_stream = s;
+        c->stage = 2;
+        return RARA_OK;
+    }
+    // First batch of this shape: render it exactly, then capture the stage sequence.
+    if ((rc = rara_render_batch(c, scenes, num_scenes, views, num_views, stream))) {
+        free(shape);
+        return rc;
+    }
+    // the batch rendered above must finish before its buffers grow
+    rc = check_cuda(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    const unsigned long long np = c->h_counters->n_pairs;
+    unsigned long long cap = np + np / 4 + 4096;
+    if (cap < c->min_cap_pairs) cap = c->min_cap_pairs;
+    if (cap >= (1ull << 30)) cap = (1ull << 30) - 1;
+    if (!rc) rc = ensure_pairs(c, (uint32_t)cap);
+    if (!rc && !c->cap_stream)
+        rc = check_cuda(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
+    if (rc) {
+        free(shape);
+        return rc;
+    }
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    const int64_t launches0 = c->launches;
+    cudaGraph_t g = nullptr;
+    rc = check_cuda(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (!rc) {
+        int rc2 = batch_preprocess(c, c->cap_stream);
+        if (!rc2) rc2 = batch_bin(c, (uint32_t)cap, c->cap_stream);
+        if (!rc2) rc2 = batch_render(c, c->cap_stream);
+        if (!rc2)
+            rc2 = check_cuda(c, cudaMemcpyAsync(c->h_counters, c->counters.p, sizeof(Counters), cudaMemcpyDeviceToHost,
+                                                c->cap_stream), "counter copy");
+        rc = check_cuda(c, cudaStreamEndCapture(c->cap_stream, &g), "end capture");
+        if (rc2) rc = rc2;
+    }
+    c->graph_kernels = c->launches - launches0;
+    c->launches = launches0;  // capturing launches nothing
+    if (!rc) rc = check_cuda(c, cudaGraphInstantiate(&c->graph, g, 0), "graph instantiate");
+    if (g) cudaGraphDestroy(g);
+    if (rc) {
+        free(shape);
+        c->graph = nullptr;
+        return rc;
+    }
+    free(c->shape);
+    c->shape = shape;
+    c->shape_len = len;
+    c->graph_cap_pairs = (uint32_t)cap;
+    return RARA_OK;
+}
+
+int rara_frame_info_get(rara_ctx *c, int32_t view, rara_frame_info *out)
 {
     if (!c || !out) return RARA_ERR_INVALID_ARG;
     if (c->stage < 2) return fail(c, RARA_ERR_INVALID_ARG, "no binned frame");
+    if (view < 0 || view >= c->num_views) return fail(c, RARA_ERR_INVALID_ARG, "view %d of %d", view, c->num_views);
     int rc = rara_ctx_sync(c, c->last_stream);
     if (rc) return rc;
-    out->n = c->n;
-    out->n_rendered = c->n_rendered;
-    out->n_cutoff = c->n_cutoff;
-    out->n_pairs = c->n_pairs;
-    out->tiles_x = c->tiles_x;
-    out->tiles_y = c->tiles_y;
+    if ((rc = check_cuda(c, cudaMemcpy(c->h_view_counters, c->view_counters_d.p,
+                                       sizeof(ViewCounters) * (size_t)c->num_views, cudaMemcpyDeviceToHost),
+                         "view counter copy")))
+        return rc;
+    const int k = c->h_view_map[view];
+    const ViewDev &v = c->h_views[k];
+    out->n = c->h_view_n[k];
+    out->n_rendered = (int64_t)c->h_view_counters[k].n_rendered;
+    out->n_cutoff = (int64_t)c->h_view_counters[k].n_cutoff;
+    out->n_pairs = (int64_t)c->h_view_counters[k].n_pairs;
+    out->tiles_x = v.tiles_x;
+    out->tiles_y = v.tiles_y;
     out->n_evaluated = (int64_t)c->h_counters->n_evaluated;
     out->n_walked = (int64_t)c->h_counters->n_walked;
     out->n_cut_evaluated = (int64_t)c->h_counters->n_cut_evaluated;
@@ -417,24 +789,48 @@ int rara_frame_info_get(rara_ctx *c, rara_frame_info *out)
     return RARA_OK;
 }
 
-int rara_frame_gaussians(rara_ctx *c, uint8_t *labels, float *depth, float *mean2d, float *conic, float *rgb,
-                         float *opacity, int32_t *rect, uint32_t *tiles, void *stream)
+int rara_frame_gaussians(rara_ctx *c, int32_t view, uint8_t *labels, float *depth, float *mean2d, float *conic,
+                         float *rgb, float *opacity, int32_t *rect, uint32_t *tiles, void *stream)
 {
     if (!c) return RARA_ERR_INVALID_ARG;
     if (c->stage < 1) return fail(c, RARA_ERR_INVALID_ARG, "no preprocessed frame");
-    launch_export_gaussians(c->n, (const uint8_t *)c->labels.p, (const uint32_t *)c->tiles.p,
-                            (const uint2 *)c->rect.p, (const SplatRec *)c->rec.p, (const float *)c->depth.p, labels,
-                            depth, mean2d, conic,
-                            rgb, opacity, rect, tiles, (cudaStream_t)stream);
-    return launched(c, "export gaussians", c->n > 0);
+    if (view < 0 || view >= c->num_views) return fail(c, RARA_ERR_INVALID_ARG, "view %d of %d", view, c->num_views);
+    const int k = c->h_view_map[view];
+    launch_export_gaussians(c->h_view_n[k], c->h_views[k].slot_base, (const uint8_t *)c->labels.p,
+                            (const uint32_t *)c->tiles.p, (const uint2 *)c->rect.p, (const SplatRec *)c->rec.p,
+                            (const float *)c->depth.p, labels, depth, mean2d, conic, rgb, opacity, rect, tiles,
+                            (cudaStream_t)stream);
+    return launched(c, "export gaussians", c->h_view_n[k] > 0);
 }
 
-int rara_frame_pairs(rara_ctx *c, uint64_t *keys, uint32_t *values, int64_t *ranges, void *stream)
+int rara_frame_pairs(rara_ctx *c, int32_t view, uint64_t *keys, uint32_t *values, int64_t *ranges, void *stream)
 {
     if (!c) return RARA_ERR_INVALID_ARG;
     if (c->stage < 2) return fail(c, RARA_ERR_INVALID_ARG, "no binned frame");
-    launch_export_pairs((int)c->n_pairs, c->sorted_tile_keys, c->sorted_pair_vals, (const float *)c->depth.p,
-                        (const int2 *)c->ranges.p, c->num_tiles, keys, values, ranges, (cudaStream_t)stream);
+    if (view < 0 || view >= c->num_views) return fail(c, RARA_ERR_INVALID_ARG, "view %d of %d", view, c->num_views);
+    const int k = c->h_view_map[view];
+    const ViewDev &v = c->h_views[k];
+    const int nt = v.tiles_x * v.tiles_y;
+    int rc = rara_ctx_sync(c, c->last_stream);
+    if (rc) return rc;
+    // the view's pairs are contiguous (its tile ids are contiguous): find their span
+    int2 *hr = (int2 *)malloc(sizeof(int2) * (size_t)(nt > 0 ? nt : 1));
+    if (!hr) return fail(c, RARA_ERR_BUDGET, "host allocation failed");
+    rc = check_cuda(c, cudaMemcpy(hr, (const int2 *)c->ranges.p + v.tile_base, sizeof(int2) * (size_t)nt,
+                                  cudaMemcpyDeviceToHost), "ranges copy");
+    uint32_t lo = 0xffffffffu, hi = 0;
+    for (int t = 0; t < nt && !rc; ++t)
+        if (hr[t].y > hr[t].x) {
+            if ((uint32_t)hr[t].x < lo) lo = (uint32_t)hr[t].x;
+            if ((uint32_t)hr[t].y > hi) hi = (uint32_t)hr[t].y;
+        }
+    free(hr);
+    if (rc) return rc;
+    if (lo > hi) lo = hi = 0;
+    launch_export_pairs((const uint32_t *)c->pkeys.p, (const uint32_t *)c->pvals.p, (const uint32_t *)c->pkeys_b.p,
+                        (const uint32_t *)c->pvals_b.p, (const Counters *)c->counters.p, (const float *)c->depth.p,
+                        (const int2 *)c->ranges.p, v.tile_base, v.slot_base, nt, lo, hi, keys, values, ranges,
+                        (cudaStream_t)stream);
     return launched(c, "export pairs", 1);
 }
 
@@ -461,25 +857,36 @@ constexpr size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Carve-out of the static array, in bytes.
 constexpr size_t kSzCounters = align256(sizeof(Counters));
+constexpr size_t kSzViews = align256(sizeof(ViewDev));
+constexpr size_t kSzScenes = align256(sizeof(SceneDev));
+constexpr size_t kSzViewCounters = align256(sizeof(ViewCounters));
 constexpr size_t kSzLabels = align256(kStaticMaxGaussians);
 constexpr size_t kSzU32G = align256((size_t)kStaticMaxGaussians * 4);
 constexpr size_t kSzRect = align256((size_t)kStaticMaxGaussians * 8);
 constexpr size_t kSzRec = align256((size_t)kStaticMaxGaussians * sizeof(SplatRec));
 constexpr size_t kSzCut = align256((size_t)kStaticMaxGaussians * sizeof(CutRec));
-constexpr size_t kSzLookG = align256((size_t)(kStaticMaxGaussians / kBlock + 1) * 8);
+constexpr size_t kSzLookC = align256((size_t)(kStaticMaxGaussians / 1024 + 2) * 8);
+constexpr size_t kSzLookE = align256((size_t)(kStaticMaxGaussians / kBlock + 2) * 8);
 constexpr size_t kSzU32P = align256((size_t)kStaticMaxPairs * 4);
+constexpr size_t kSzHist = align256(8 * 256 * 4);
 constexpr size_t kSzRanges = align256((size_t)kStaticMaxTiles * sizeof(int2));
+constexpr size_t kSzOrder = align256((size_t)kStaticMaxTiles * 16);
 // sort scratch for 4 digit passes over kStaticMaxPairs keys, sized for partitions as small as
 // 1024 keys; static_setup checks it against the sort's own requirement
-constexpr size_t kSzSort = align256(4 * (4 * 256 + 64 + 4 * (size_t)((kStaticMaxPairs + 1023) / 1024) * 256));
-constexpr size_t kSzOrder = align256((size_t)kStaticMaxTiles * 16);
-constexpr size_t kStaticBytes = kSzCounters + kSzLabels + kSzU32G + kSzRect + kSzRec + kSzCut + kSzU32G +
-                                4 * kSzU32G + kSzLookG + 4 * kSzU32P + kSzLookG + kSzRanges + kSzOrder + kSzSort;
+constexpr size_t kSzSort = align256(4 * (4 * (size_t)((kStaticMaxPairs + 1023) / 1024) * 256));
+constexpr size_t kStaticBytes = kSzCounters + kSzViews + kSzScenes + kSzViewCounters + kSzLabels + 2 * kSzU32G +
+                                kSzRect + kSzRec + kSzCut + 4 * kSzU32G + kSzLookC + kSzLookE + 4 * kSzU32P +
+                                kSzHist + kSzRanges + kSzOrder + kSzSort;
 
 static __device__ __align__(256) unsigned char g_rara_static_scratch[kStaticBytes];
 
 rara_ctx g_static_ctx[kStaticMaxDevices];
 Counters g_static_host_counters[kStaticMaxDevices];
+ViewCounters g_static_host_view_counters[kStaticMaxDevices];
+ViewDev g_static_host_views[kStaticMaxDevices][2];
+SceneDev g_static_host_scenes[kStaticMaxDevices][2];
+int g_static_view_map[kStaticMaxDevices];
+int g_static_view_n[kStaticMaxDevices];
 bool g_static_ready[kStaticMaxDevices];
 
 // Once per device, with that device current: resolve the device address of the static
@@ -487,7 +894,7 @@ bool g_static_ready[kStaticMaxDevices];
 int static_setup(int dev)
 {
     if (g_static_ready[dev]) return RARA_OK;
-    if (sort_scratch_bytes(kStaticMaxPairs, 32) > kSzSort) return RARA_ERR_BUDGET;
+    if (sort_scratch_bytes(kStaticMaxPairs, 4) > kSzSort) return RARA_ERR_BUDGET;
     void *base = nullptr;
     if (cudaGetSymbolAddress(&base, g_rara_static_scratch) != cudaSuccess || !base) {
         cudaGetLastError();
@@ -497,6 +904,9 @@ int static_setup(int dev)
     unsigned char *p = (unsigned char *)base;
     auto take = [&](DevBuf &b, size_t bytes) { b.p = p; b.cap = bytes; p += bytes; };
     take(c->counters, kSzCounters);
+    take(c->views_d, kSzViews);
+    take(c->scenes_d, kSzScenes);
+    take(c->view_counters_d, kSzViewCounters);
     take(c->labels, kSzLabels);
     take(c->tiles, kSzU32G);
     take(c->rect, kSzRect);
@@ -505,20 +915,32 @@ int static_setup(int dev)
     take(c->depth, kSzU32G);
     take(c->ckeys, kSzU32G);
     take(c->cvals, kSzU32G);
-    take(c->ckeys_alt, kSzU32G);
-    take(c->cvals_alt, kSzU32G);
-    take(c->lookback_g, kSzLookG);
+    take(c->ckeys_b, kSzU32G);
+    take(c->cvals_b, kSzU32G);
+    take(c->lookback_c, kSzLookC);
+    take(c->lookback_e, kSzLookE);
     take(c->pkeys, kSzU32P);
     take(c->pvals, kSzU32P);
-    take(c->pkeys_alt, kSzU32P);
-    take(c->pvals_alt, kSzU32P);
-    take(c->lookback_p, kSzLookG);
+    take(c->pkeys_b, kSzU32P);
+    take(c->pvals_b, kSzU32P);
+    take(c->hist, kSzHist);
     take(c->ranges, kSzRanges);
-    take(c->tile_order, kSzOrder);
+    take(c->items, kSzOrder);
     take(c->sort_scratch, kSzSort);
     c->budget = 0;
     c->device = dev;
+    c->max_views = 1;
+    c->max_scenes = 1;
+    c->owns_host = false;
+    for (int k = 0; k < 2; ++k) {
+        c->staging[k].views = &g_static_host_views[dev][k];
+        c->staging[k].scenes = &g_static_host_scenes[dev][k];
+        c->staging[k].uploaded = nullptr;
+    }
+    c->h_view_map = &g_static_view_map[dev];
+    c->h_view_n = &g_static_view_n[dev];
     c->h_counters = &g_static_host_counters[dev];
+    c->h_view_counters = &g_static_host_view_counters[dev];
     g_static_ready[dev] = true;
     return RARA_OK;
 }

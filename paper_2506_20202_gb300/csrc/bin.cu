@@ -1,11 +1,12 @@
-// Step (b) around the sort: pair emission in depth order, per-tile ranges, and the
-// debug exports that rebuild full 64-bit (tile | depth) keys.
+// Step (b) around the sorts: pair emission in depth order, per-tile ranges, the render's
+// heaviest-first work order, and the debug exports that rebuild full 64-bit keys.
 //
 // Sorting the 64-bit keys (tile id << 32 | depth bits) with an LSD radix sort processes
 // the 32 depth bits first. Those bits are the same for every pair of one Gaussian, so the
-// build sorts the rendered Gaussians by depth once (n_rendered elements instead of
-// n_pairs), emits each Gaussian's pairs in that order, and finishes with the tile-id digit
-// passes over the pairs. The result is the same list as the full stable key sort.
+// build sorts the rendered slots by depth once (one entry per slot instead of one per
+// pair), emits each slot's pairs in that order, and finishes with the tile-id digit passes
+// over the pairs. The result is the same list as the full stable key sort. Tile ids are
+// global over the batch (view tile base + ty * tiles_x + tx), so one sort serves all views.
 #include "chained_scan.cuh"
 #include "rara_internal.cuh"
 
@@ -13,106 +14,101 @@ namespace rara {
 
 namespace {
 
+// View owning a slot: the last view whose slot base is <= the slot.
+__device__ __forceinline__ int view_of_slot(const ViewDev *views, int num_views, uint32_t slot)
+{
+    int lo = 0, hi = num_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].slot_base <= slot) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
 {
+    __shared__ uint32_t s_hist[4][256];
     __shared__ unsigned s_part;
     __shared__ unsigned long long s_warp[kBlock / 32];
     __shared__ unsigned long long s_prefix;
-    if (threadIdx.x == 0) s_part = atomicAdd(&a.counters->part_counter[1], 1u);
-    __syncthreads();
-    const int part = (int)s_part;
-    const int j = part * kBlock + threadIdx.x;
+    for (int t = threadIdx.x; t < 4 * 256; t += kBlock) (&s_hist[0][0])[t] = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t g = 0, nt = 0;
-    if (j < a.n_rendered) {
-        g = a.sorted_vals[j];
-        nt = a.tiles[g];
-    }
-    // block exclusive scan of nt
-    unsigned long long incl = nt;
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        unsigned long long w = lane < kBlock / 32 ? s_warp[lane] : 0ull;
-        unsigned long long wi = w;
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long v = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += v;
+    const uint32_t n = (uint32_t)a.counters->n_rendered;
+    const uint32_t *vals = a.counters->depth_in_b ? a.vals_b : a.vals_a;
+    const uint32_t parts = (n + kBlock - 1) / kBlock;
+    bool overflow = false;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_part = atomicAdd(&a.counters->ticket[kTicketEmit], 1u);
+        __syncthreads();
+        const uint32_t part = s_part;
+        if (part >= parts) break;
+        const uint32_t j = part * kBlock + threadIdx.x;
+        uint32_t slot = 0, nt = 0;
+        if (j < n) {
+            slot = vals[j];
+            nt = a.tiles[slot];
         }
-        const unsigned long long total = __shfl_sync(0xffffffffu, wi, 31);
-        if (lane < kBlock / 32) s_warp[lane] = wi - w;
-        const unsigned long long prefix = warp_chained_prefix(a.lookback, part, total, &a.counters->status);
-        if (lane == 0) s_prefix = prefix;
+        // block exclusive scan of nt
+        unsigned long long incl = nt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned long long w = lane < kBlock / 32 ? s_warp[lane] : 0ull;
+            unsigned long long wi = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long v = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += v;
+            }
+            const unsigned long long total = __shfl_sync(0xffffffffu, wi, 31);
+            if (lane < kBlock / 32) s_warp[lane] = wi - w;
+            const unsigned long long prefix = warp_chained_prefix(a.lookback, (int)part, total, &a.counters->status);
+            if (lane == 0) s_prefix = prefix;
+        }
+        __syncthreads();
+        if (nt) {
+            unsigned long long off = s_prefix + s_warp[warp] + incl - nt;
+            const ViewDev &vw = a.views[view_of_slot(a.views, a.num_views, slot)];
+            const uint2 rc = a.rect[slot];
+            const int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
+            for (int y = y0; y <= y1; ++y)
+                for (int x = x0; x <= x1; ++x) {
+                    if (off < a.cap_pairs) {
+                        const uint32_t t = vw.tile_base + (uint32_t)(y * vw.tiles_x + x);
+                        a.pair_keys[off] = t;
+                        a.pair_vals[off] = slot;
+                        for (int p = 0; p < a.tile_passes; ++p) atomicAdd(&s_hist[p][(t >> (8 * p)) & 0xffu], 1u);
+                    } else {
+                        overflow = true;
+                    }
+                    ++off;
+                }
+        }
     }
     __syncthreads();
-    if (nt) {
-        unsigned long long off = s_prefix + s_warp[warp] + incl - nt;
-        const uint2 rc = a.rect[g];
-        const int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
-        for (int y = y0; y <= y1; ++y)
-            for (int x = x0; x <= x1; ++x) {
-                if (off < a.n_pairs) {  // always true unless a bounded wait gave up
-                    a.pair_keys[off] = (uint32_t)(y * a.tiles_x + x);
-                    a.pair_vals[off] = g;
-                }
-                ++off;
-            }
+    for (int t = threadIdx.x; t < a.tile_passes * 256; t += kBlock) {
+        const uint32_t v = (&s_hist[0][0])[t];
+        if (v) atomicAdd(&a.tile_hist[t], v);
     }
+    if (overflow) atomicOr(&a.counters->status, kStatusOverflow);
 }
 
-__global__ void k_ranges(const uint32_t *__restrict__ keys, int n, int num_tiles, int2 *__restrict__ ranges)
+__global__ void k_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const Counters *counters,
+                         uint32_t cap_pairs, uint32_t num_tiles, int2 *__restrict__ ranges)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t t = keys[i];
-    if (t >= (uint32_t)num_tiles) return;
-    if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
-    if (i == n - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
-}
-
-__global__ void k_export_gaussians(int n, const uint8_t *labels_src, const uint32_t *tiles_src,
-                                   const uint2 *rect_src, const SplatRec *rec, const float *depth_src,
-                                   uint8_t *labels, float *depth,
-                                   float *mean2d, float *conic, float *rgb, float *opacity, int32_t *rect,
-                                   uint32_t *tiles)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (labels) labels[i] = labels_src[i];
-    const uint32_t nt = tiles_src[i];
-    if (tiles) tiles[i] = nt;
-    if (!nt) return;
-    const SplatRec r = rec[i];
-    if (depth) depth[i] = depth_src[i];
-    if (mean2d) { mean2d[i] = r.r0.x; mean2d[n + i] = r.r0.y; }
-    if (conic) { conic[i] = r.r0.z; conic[n + i] = r.r0.w; conic[2 * n + i] = r.r1.x; }
-    if (rgb) { rgb[i] = r.r1.z; rgb[n + i] = r.r1.w; rgb[2 * n + i] = r.r2.x; }
-    if (opacity) opacity[i] = r.r1.y;
-    if (rect) {
-        const uint2 rc = rect_src[i];
-        rect[i] = rc.x & 0xffff; rect[n + i] = rc.x >> 16;
-        rect[2 * n + i] = rc.y & 0xffff; rect[3 * n + i] = rc.y >> 16;
-    }
-}
-
-__global__ void k_export_pairs(int np, const uint32_t *tile_keys, const uint32_t *vals, const float *depth,
-                               const int2 *ranges, int num_tiles, uint64_t *keys, uint32_t *values,
-                               int64_t *ranges_out)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < np) {
-        const uint32_t g = vals[i];
-        if (keys) keys[i] = ((uint64_t)tile_keys[i] << 32) | __float_as_uint(depth[g]);
-        if (values) values[i] = g;
-    }
-    if (ranges_out && i < num_tiles) {
-        const int2 r = ranges[i];
-        ranges_out[2 * i] = r.x;
-        ranges_out[2 * i + 1] = r.y;
+    const unsigned long long np = counters->n_pairs;
+    const uint32_t n = (uint32_t)(np < cap_pairs ? np : cap_pairs);
+    const uint32_t *keys = counters->tile_in_b ? keys_b : keys_a;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t t = keys[i];
+        if (t >= num_tiles) continue;
+        if (i == 0 || keys[i - 1] != t) ranges[t].x = (int)i;
+        if (i == n - 1 || keys[i + 1] != t) ranges[t].y = (int)(i + 1);
     }
 }
 
@@ -154,7 +150,77 @@ __global__ void __launch_bounds__(1024) k_tile_order(const int2 *__restrict__ ra
     }
 }
 
+__global__ void k_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_src, const uint32_t *tiles_src,
+                                   const uint2 *rect_src, const SplatRec *rec, const float *depth_src,
+                                   uint8_t *labels, float *depth, float *mean2d, float *conic, float *rgb,
+                                   float *opacity, int32_t *rect, uint32_t *tiles)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t s = slot_base + (uint32_t)i;
+    if (labels) labels[i] = labels_src[s];
+    const uint32_t nt = tiles_src[s];
+    if (tiles) tiles[i] = nt;
+    if (!nt) return;
+    const SplatRec r = rec[s];
+    if (depth) depth[i] = depth_src[s];
+    if (mean2d) { mean2d[i] = r.r0.x; mean2d[n + i] = r.r0.y; }
+    if (conic) { conic[i] = r.r0.z; conic[n + i] = r.r0.w; conic[2 * n + i] = r.r1.x; }
+    if (rgb) { rgb[i] = r.r1.z; rgb[n + i] = r.r1.w; rgb[2 * n + i] = r.r2.x; }
+    if (opacity) opacity[i] = r.r1.y;
+    if (rect) {
+        const uint2 rc = rect_src[s];
+        rect[i] = rc.x & 0xffff; rect[n + i] = rc.x >> 16;
+        rect[2 * n + i] = rc.y & 0xffff; rect[3 * n + i] = rc.y >> 16;
+    }
+}
+
+__global__ void k_export_pairs(const uint32_t *keys_a, const uint32_t *vals_a, const uint32_t *keys_b,
+                               const uint32_t *vals_b, const Counters *counters, const float *depth,
+                               const int2 *ranges, uint32_t tile_base, uint32_t slot_base, int num_tiles,
+                               uint32_t pair_begin, uint32_t pair_end, uint64_t *keys, uint32_t *values,
+                               int64_t *ranges_out)
+{
+    const bool in_b = counters->tile_in_b != 0u;
+    const uint32_t *tk = in_b ? keys_b : keys_a;
+    const uint32_t *tv = in_b ? vals_b : vals_a;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t np = pair_end - pair_begin;
+    if (i < np) {
+        const uint32_t slot = tv[pair_begin + i];
+        if (keys) keys[i] = ((uint64_t)(tk[pair_begin + i] - tile_base) << 32) | __float_as_uint(depth[slot]);
+        if (values) values[i] = slot - slot_base;
+    }
+    if (ranges_out && i < (uint32_t)num_tiles) {
+        const int2 r = ranges[tile_base + i];
+        const bool empty = r.y <= r.x;
+        ranges_out[2 * i] = empty ? 0 : (int64_t)r.x - pair_begin;
+        ranges_out[2 * i + 1] = empty ? 0 : (int64_t)r.y - pair_begin;
+    }
+}
+
 }  // namespace
+
+int emit_blocks_per_sm()
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_emit, kBlock, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return b;
+}
+
+void launch_emit(const EmitArgs &a, int grid, cudaStream_t s)
+{
+    if (grid > 0) k_emit<<<grid, kBlock, 0, s>>>(a);
+}
+
+void launch_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const Counters *counters, uint32_t cap_pairs,
+                   uint32_t num_tiles, int2 *ranges, int grid, cudaStream_t s)
+{
+    if (grid > 0) k_ranges<<<grid, 256, 0, s>>>(keys_a, keys_b, counters, cap_pairs, num_tiles, ranges);
+}
 
 void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int split4_bits, uint32_t *order,
                        Counters *counters, cudaStream_t s)
@@ -163,34 +229,28 @@ void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int s
         k_tile_order<<<1, 1024, 0, s>>>(ranges, num_tiles, split2_bits, split4_bits, order, counters);
 }
 
-void launch_emit(const EmitArgs &a, int num_blocks, cudaStream_t s)
-{
-    if (num_blocks > 0) k_emit<<<num_blocks, kBlock, 0, s>>>(a);
-}
-
-void launch_ranges(const uint32_t *keys, int n, int num_tiles, int2 *ranges, cudaStream_t s)
-{
-    if (n > 0) k_ranges<<<(n + 255) / 256, 256, 0, s>>>(keys, n, num_tiles, ranges);
-}
-
-void launch_export_gaussians(int n, const uint8_t *labels_src, const uint32_t *tiles_src, const uint2 *rect_src,
-                             const SplatRec *rec, const float *depth_src, uint8_t *labels, float *depth,
-                             float *mean2d, float *conic, float *rgb, float *opacity, int32_t *rect, uint32_t *tiles,
-                             cudaStream_t s)
+void launch_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_src, const uint32_t *tiles_src,
+                             const uint2 *rect_src, const SplatRec *rec, const float *depth_src, uint8_t *labels,
+                             float *depth, float *mean2d, float *conic, float *rgb, float *opacity, int32_t *rect,
+                             uint32_t *tiles, cudaStream_t s)
 {
     if (n > 0)
-        k_export_gaussians<<<(n + 255) / 256, 256, 0, s>>>(n, labels_src, tiles_src, rect_src, rec, depth_src,
-                                                           labels, depth, mean2d, conic, rgb, opacity, rect, tiles);
+        k_export_gaussians<<<(n + 255) / 256, 256, 0, s>>>(n, slot_base, labels_src, tiles_src, rect_src, rec,
+                                                           depth_src, labels, depth, mean2d, conic, rgb, opacity,
+                                                           rect, tiles);
 }
 
-void launch_export_pairs(int np, const uint32_t *tile_keys, const uint32_t *vals, const float *depth,
-                         const int2 *ranges, int num_tiles, uint64_t *keys, uint32_t *values, int64_t *ranges_out,
-                         cudaStream_t s)
+void launch_export_pairs(const uint32_t *keys_a, const uint32_t *vals_a, const uint32_t *keys_b,
+                         const uint32_t *vals_b, const Counters *counters, const float *depth, const int2 *ranges,
+                         uint32_t tile_base, uint32_t slot_base, int num_tiles, uint32_t pair_begin,
+                         uint32_t pair_end, uint64_t *keys, uint32_t *values, int64_t *ranges_out, cudaStream_t s)
 {
-    const int m = np > num_tiles ? np : num_tiles;
+    const uint32_t np = pair_end - pair_begin;
+    const uint32_t m = np > (uint32_t)num_tiles ? np : (uint32_t)num_tiles;
     if (m > 0)
-        k_export_pairs<<<(m + 255) / 256, 256, 0, s>>>(np, tile_keys, vals, depth, ranges, num_tiles, keys, values,
-                                                       ranges_out);
+        k_export_pairs<<<(m + 255) / 256, 256, 0, s>>>(keys_a, vals_a, keys_b, vals_b, counters, depth, ranges,
+                                                       tile_base, slot_base, num_tiles, pair_begin, pair_end, keys,
+                                                       values, ranges_out);
 }
 
 }  // namespace rara

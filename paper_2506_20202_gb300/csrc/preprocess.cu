@@ -1,10 +1,12 @@
-// Step (a): per-Gaussian classification, projection, SH colour and compaction.
+// Step (a): per-Gaussian classification, projection and SH colour, for every view of a
+// batch, and the compaction of the rendered (view, Gaussian) slots.
 //
-// One thread per Gaussian. Loads are planar (one coalesced 128-byte line per warp per
-// attribute plane). The kernel writes, for every Gaussian, its label and tiles-touched
-// count, and for rendered Gaussians the 48-byte splat record, the tile rectangle, the
-// 64-byte ray-tracing record (cutoff only) and a compacted (depth bits, index) entry in
-// index order, placed by a chained scan across blocks so the order is deterministic.
+// Preprocess: one thread per Gaussian and loop over the views of its scene. Loads are
+// planar (one coalesced 128-byte line per warp per attribute plane). Per slot the kernel
+// writes the label and tiles-touched count, and for rendered slots the 48-byte splat record,
+// the tile rectangle, the depth key and the 64-byte ray-tracing record (cutoff only).
+// Compaction: rendered slots in slot order (view, then Gaussian index), placed by a chained
+// scan across blocks so the order is deterministic.
 #include "chained_scan.cuh"
 #include "rara_internal.cuh"
 
@@ -71,206 +73,288 @@ __device__ void sh_colour(const float *__restrict__ sh, int n, int i, int degree
     }
 }
 
-__global__ void __launch_bounds__(kBlock) k_preprocess(PreprocessArgs a)
+__device__ __forceinline__ void block_add3(unsigned long long v0, unsigned long long v1, unsigned long long v2,
+                                           unsigned long long *s_red, unsigned long long *d0, unsigned long long *d1,
+                                           unsigned long long *d2, unsigned long long *t0, unsigned long long *t1,
+                                           unsigned long long *t2)
 {
-    __shared__ unsigned s_part;
-    __shared__ unsigned s_warp_cnt[kBlock / 32];
-    __shared__ unsigned long long s_prefix;
-    __shared__ unsigned long long s_pairs[kBlock / 32];
-    __shared__ unsigned s_cut[kBlock / 32];
-
-    if (threadIdx.x == 0) s_part = atomicAdd(&a.counters->part_counter[0], 1u);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+    }
+    if (lane == 0) {
+        s_red[3 * warp] = v0;
+        s_red[3 * warp + 1] = v1;
+        s_red[3 * warp + 2] = v2;
+    }
     __syncthreads();
-    const int part = (int)s_part;
-    const int i = part * kBlock + threadIdx.x;
-    const int n = a.n;
-
-    bool rendered = false;
-    bool cutoff = false;
-    uint32_t ntiles = 0;
-    float depth = 0.0f;
-
-    if (i < n) {
-        const float mx = __ldg(&a.means[i]), my = __ldg(&a.means[n + i]), mz = __ldg(&a.means[2 * n + i]);
-        const float s0 = expf(__ldg(&a.log_scales[i]));
-        const float s1 = expf(__ldg(&a.log_scales[n + i]));
-        const float s2 = expf(__ldg(&a.log_scales[2 * n + i]));
-        const PlaneDev &pl = a.plane;
-
-        // Section 3.2 / Algorithm 1 step 1: d_ep = n.mu + d, r = 3 max(sigma)
-        const float dep = fmaf(pl.n[0], mx, fmaf(pl.n[1], my, fmaf(pl.n[2], mz, pl.d)));
-        const float r = 3.0f * fmaxf(s0, fmaxf(s1, s2));
-        int label;
-        if (pl.mode == RARA_MODE_NONE) label = RARA_VISIBLE;
-        else if (pl.mode == RARA_MODE_HARD) label = dep < 0.0f ? RARA_INVISIBLE : RARA_VISIBLE;
-        else {
-            label = dep < -r ? RARA_INVISIBLE : (dep > r ? RARA_VISIBLE : RARA_CUTOFF);
-            if (pl.mode == RARA_MODE_RARA_ALL && label != RARA_INVISIBLE) label = RARA_CUTOFF;
+    if (threadIdx.x < 3) {
+        unsigned long long acc = 0;
+        for (int w = 0; w < kBlock / 32; ++w) acc += s_red[3 * w + threadIdx.x];
+        if (acc) {
+            atomicAdd(threadIdx.x == 0 ? d0 : (threadIdx.x == 1 ? d1 : d2), acc);
+            atomicAdd(threadIdx.x == 0 ? t0 : (threadIdx.x == 1 ? t1 : t2), acc);
         }
-        a.labels[i] = (uint8_t)label;
+    }
+    __syncthreads();
+}
 
-        const CamDev &cam = a.cam;
-        const float tx = fmaf(cam.R[0], mx, fmaf(cam.R[1], my, fmaf(cam.R[2], mz, cam.t[0])));
-        const float ty = fmaf(cam.R[3], mx, fmaf(cam.R[4], my, fmaf(cam.R[5], mz, cam.t[1])));
-        const float tz = fmaf(cam.R[6], mx, fmaf(cam.R[7], my, fmaf(cam.R[8], mz, cam.t[2])));
-        // The sort key holds the depth rounded once from a double-precision dot product, so
-        // it is the correctly rounded float32 of the exact depth (ties order by index).
-        depth = (float)fma((double)cam.R[6], (double)mx,
-                           fma((double)cam.R[7], (double)my, fma((double)cam.R[8], (double)mz, (double)cam.t[2])));
+// One block = one unit of 256 Gaussians of one scene; the Gaussians' attributes are read
+// once and every view of the scene is processed from registers (SH coefficients are re-read
+// per view, from L1/L2 after the first view).
+__global__ void __launch_bounds__(kBlock, 4) k_preprocess(PreprocessArgs a)
+{
+    __shared__ unsigned long long s_red[3 * (kBlock / 32)];
+    const int unit = blockIdx.x;
+    int si = 0;
+    while (si + 1 < a.num_scenes && (int)a.scenes[si + 1].unit_begin <= unit) ++si;
+    const SceneDev &sc = a.scenes[si];
+    const int n = sc.n;
+    const int i = (unit - (int)sc.unit_begin) * kBlock + threadIdx.x;
+    const bool valid = i < n;
 
-        if (label != RARA_INVISIBLE && tz > kNearZ) {
-            // Rotation of the normalised quaternion (w, x, y, z)
-            float qw = __ldg(&a.quats[i]), qx = __ldg(&a.quats[n + i]);
-            float qy = __ldg(&a.quats[2 * n + i]), qz = __ldg(&a.quats[3 * n + i]);
-            const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-            qw *= qn; qx *= qn; qy *= qn; qz *= qn;
-            const float Rg[9] = {
-                1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
-                2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
-                2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
-            const float sg[3] = {s0, s1, s2};
+    float mx = 0.f, my = 0.f, mz = 0.f, s0 = 1.f, s1 = 1.f, s2 = 1.f, logit = 0.f;
+    float Rg[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    if (valid) {
+        mx = __ldg(&sc.means[i]); my = __ldg(&sc.means[n + i]); mz = __ldg(&sc.means[2 * n + i]);
+        s0 = expf(__ldg(&sc.log_scales[i]));
+        s1 = expf(__ldg(&sc.log_scales[n + i]));
+        s2 = expf(__ldg(&sc.log_scales[2 * n + i]));
+        logit = __ldg(&sc.logits[i]);
+        // rotation of the normalised quaternion (w, x, y, z)
+        float qw = __ldg(&sc.quats[i]), qx = __ldg(&sc.quats[n + i]);
+        float qy = __ldg(&sc.quats[2 * n + i]), qz = __ldg(&sc.quats[3 * n + i]);
+        const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        qw *= qn; qx *= qn; qy *= qn; qz *= qn;
+        Rg[0] = 1.f - 2.f * (qy * qy + qz * qz); Rg[1] = 2.f * (qx * qy - qw * qz); Rg[2] = 2.f * (qx * qz + qw * qy);
+        Rg[3] = 2.f * (qx * qy + qw * qz); Rg[4] = 1.f - 2.f * (qx * qx + qz * qz); Rg[5] = 2.f * (qy * qz - qw * qx);
+        Rg[6] = 2.f * (qx * qz - qw * qy); Rg[7] = 2.f * (qy * qz + qw * qx); Rg[8] = 1.f - 2.f * (qx * qx + qy * qy);
+    }
+    const float sg[3] = {s0, s1, s2};
+    const float r = 3.0f * fmaxf(s0, fmaxf(s1, s2));
 
-            // Eq. 9-10: Sigma2 = (J W M)(J W M)^T + 0.3 I with M = R S and J the affine
-            // approximation of the projection at the centre (x/z, y/z clamped).
-            const float itz = 1.0f / tz;
-            const float limx = 1.3f * (0.5f * cam.W / cam.fx), limy = 1.3f * (0.5f * cam.H / cam.fy);
-            const float txz = fminf(limx, fmaxf(-limx, tx * itz));
-            const float tyz = fminf(limy, fmaxf(-limy, ty * itz));
-            const float J00 = cam.fx * itz, J02 = -cam.fx * txz * itz;
-            const float J11 = cam.fy * itz, J12 = -cam.fy * tyz * itz;
-            float T0[3], T1[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                T0[k] = fmaf(J00, cam.R[k], J02 * cam.R[6 + k]);
-                T1[k] = fmaf(J11, cam.R[3 + k], J12 * cam.R[6 + k]);
+    for (int v = sc.view_begin; v < sc.view_begin + sc.view_count; ++v) {
+        const ViewDev &vw = a.views[v];
+        const PlaneDev &pl = vw.plane;
+        const CamDev &cam = vw.cam;
+        bool rendered = false, cutoff = false;
+        uint32_t ntiles = 0;
+        if (valid) {
+            const uint32_t slot = vw.slot_base + (uint32_t)i;
+            // Section 3.2 / Algorithm 1 step 1: d_ep = n.mu + d, r = 3 max(sigma)
+            const float dep = fmaf(pl.n[0], mx, fmaf(pl.n[1], my, fmaf(pl.n[2], mz, pl.d)));
+            int label;
+            if (pl.mode == RARA_MODE_NONE) label = RARA_VISIBLE;
+            else if (pl.mode == RARA_MODE_HARD) label = dep < 0.0f ? RARA_INVISIBLE : RARA_VISIBLE;
+            else {
+                label = dep < -r ? RARA_INVISIBLE : (dep > r ? RARA_VISIBLE : RARA_CUTOFF);
+                if (pl.mode == RARA_MODE_RARA_ALL && label != RARA_INVISIBLE) label = RARA_CUTOFF;
             }
-            float A0[3], A1[3];  // rows of J W R S
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                A0[k] = (T0[0] * Rg[k] + T0[1] * Rg[3 + k] + T0[2] * Rg[6 + k]) * sg[k];
-                A1[k] = (T1[0] * Rg[k] + T1[1] * Rg[3 + k] + T1[2] * Rg[6 + k]) * sg[k];
-            }
-            const float a0 = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2];
-            const float b0 = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
-            const float c0 = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2];
-            // det((A A^T) + 0.3 I) = |A0 x A1|^2 + 0.3 (a0 + c0) + 0.09: every term is
-            // non-negative, so elongated splats keep their precision.
-            const float x0 = A0[1] * A1[2] - A0[2] * A1[1];
-            const float x1 = A0[2] * A1[0] - A0[0] * A1[2];
-            const float x2 = A0[0] * A1[1] - A0[1] * A1[0];
-            const float ca = a0 + kDilation, cb = b0, cc = c0 + kDilation;
-            const float det = (x0 * x0 + x1 * x1 + x2 * x2) + kDilation * (a0 + c0) + kDilation * kDilation;
-            if (det > 0.0f) {
-                const float idet = 1.0f / det;
-                const float mx2 = fmaf(cam.fx, tx * itz, cam.cx);
-                const float my2 = fmaf(cam.fy, ty * itz, cam.cy);
-                // Tile rectangle: axis-aligned box of the q <= 9 ellipse
-                const float hx = 3.0f * sqrtf(ca), hy = 3.0f * sqrtf(cc);
-                const float inv_t = 1.0f / kTile;
-                const float fx0 = floorf((mx2 - hx) * inv_t), fx1 = floorf((mx2 + hx) * inv_t);
-                const float fy0 = floorf((my2 - hy) * inv_t), fy1 = floorf((my2 + hy) * inv_t);
-                const int rx0 = (int)fmaxf(0.0f, fminf((float)a.tiles_x, fx0));
-                const int rx1 = (int)fmaxf(-1.0f, fminf((float)(a.tiles_x - 1), fx1));
-                const int ry0 = (int)fmaxf(0.0f, fminf((float)a.tiles_y, fy0));
-                const int ry1 = (int)fmaxf(-1.0f, fminf((float)(a.tiles_y - 1), fy1));
-                if (rx0 <= rx1 && ry0 <= ry1) {
-                    ntiles = (uint32_t)((rx1 - rx0 + 1) * (ry1 - ry0 + 1));
-                    rendered = true;
-                    cutoff = label == RARA_CUTOFF;
-                    a.rect[i] = make_uint2((uint32_t)rx0 | ((uint32_t)ry0 << 16),
-                                           (uint32_t)rx1 | ((uint32_t)ry1 << 16));
-                    const float op = 1.0f / (1.0f + expf(-__ldg(&a.logits[i])));
-                    // colour at normalize(mu - e)
-                    const float ex = mx - cam.eye[0], ey = my - cam.eye[1], ez = mz - cam.eye[2];
-                    const float il = rsqrtf(ex * ex + ey * ey + ez * ez);
-                    float rgb[3];
-                    sh_colour(a.sh, n, i, a.sh_degree, ex * il, ey * il, ez * il, rgb);
-                    SplatRec rec;
-                    rec.r0 = make_float4(mx2, my2, cc * idet, -cb * idet);
-                    rec.r1 = make_float4(ca * idet, op, rgb[0], rgb[1]);
-                    rec.r2 = make_float4(rgb[2], cutoff ? 1.0f : 0.0f, cb / cc, cb / ca);
-                    a.rec[i] = rec;
-                    a.depth[i] = depth;
+            a.labels[slot] = (uint8_t)label;
 
-                    if (cutoff) {
-                        // Ray-tracing record in the unit-sphere frame of M = k R S
-                        // (Eq. 4): M^-1 = diag(1/(k sigma)) R^T. For the pixel ray with
-                        // offset (dx, dy) from the projected centre, the local ray is
-                        // o + tau V with o = -G, V = G + P (dx, dy): G = M^-1 (mu - e) and
-                        // P = z M^-1 W^T[:, 0:2] diag(1/fx, 1/fy). m = M^T n carries the
-                        // plane into the same frame: s(x) = d_ep + m . u for x = mu + M u.
-                        const float kk = pl.k;
-                        const float iks[3] = {1.0f / (kk * s0), 1.0f / (kk * s1), 1.0f / (kk * s2)};
-                        float G[3], Px[3], Py[3], m[3];
-                        const float cxw[3] = {cam.R[0], cam.R[1], cam.R[2]};  // camera x axis (world)
-                        const float cyw[3] = {cam.R[3], cam.R[4], cam.R[5]};  // camera y axis (world)
-                        const float sx = tz / cam.fx, sy = tz / cam.fy;
+            const float tx = fmaf(cam.R[0], mx, fmaf(cam.R[1], my, fmaf(cam.R[2], mz, cam.t[0])));
+            const float ty = fmaf(cam.R[3], mx, fmaf(cam.R[4], my, fmaf(cam.R[5], mz, cam.t[1])));
+            const float tz = fmaf(cam.R[6], mx, fmaf(cam.R[7], my, fmaf(cam.R[8], mz, cam.t[2])));
+
+            if (label != RARA_INVISIBLE && tz > kNearZ) {
+                // Eq. 9-10: Sigma2 = (J W M)(J W M)^T + 0.3 I with M = R S and J the affine
+                // approximation of the projection at the centre (x/z, y/z clamped).
+                const float itz = 1.0f / tz;
+                const float limx = 1.3f * (0.5f * cam.W / cam.fx), limy = 1.3f * (0.5f * cam.H / cam.fy);
+                const float txz = fminf(limx, fmaxf(-limx, tx * itz));
+                const float tyz = fminf(limy, fmaxf(-limy, ty * itz));
+                const float J00 = cam.fx * itz, J02 = -cam.fx * txz * itz;
+                const float J11 = cam.fy * itz, J12 = -cam.fy * tyz * itz;
+                float T0[3], T1[3];
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const float rk0 = Rg[k], rk1 = Rg[3 + k], rk2 = Rg[6 + k];  // column k of R
-                            G[k] = iks[k] * (rk0 * ex + rk1 * ey + rk2 * ez);
-                            Px[k] = iks[k] * sx * (rk0 * cxw[0] + rk1 * cxw[1] + rk2 * cxw[2]);
-                            Py[k] = iks[k] * sy * (rk0 * cyw[0] + rk1 * cyw[1] + rk2 * cyw[2]);
-                            m[k] = kk * sg[k] * (rk0 * pl.n[0] + rk1 * pl.n[1] + rk2 * pl.n[2]);
+                for (int k = 0; k < 3; ++k) {
+                    T0[k] = fmaf(J00, cam.R[k], J02 * cam.R[6 + k]);
+                    T1[k] = fmaf(J11, cam.R[3 + k], J12 * cam.R[6 + k]);
+                }
+                float A0[3], A1[3];  // rows of J W R S
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    A0[k] = (T0[0] * Rg[k] + T0[1] * Rg[3 + k] + T0[2] * Rg[6 + k]) * sg[k];
+                    A1[k] = (T1[0] * Rg[k] + T1[1] * Rg[3 + k] + T1[2] * Rg[6 + k]) * sg[k];
+                }
+                const float a0 = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2];
+                const float b0 = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
+                const float c0 = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2];
+                // det((A A^T) + 0.3 I) = |A0 x A1|^2 + 0.3 (a0 + c0) + 0.09: every term is
+                // non-negative, so elongated splats keep their precision.
+                const float x0 = A0[1] * A1[2] - A0[2] * A1[1];
+                const float x1 = A0[2] * A1[0] - A0[0] * A1[2];
+                const float x2 = A0[0] * A1[1] - A0[1] * A1[0];
+                const float ca = a0 + kDilation, cb = b0, cc = c0 + kDilation;
+                const float det = (x0 * x0 + x1 * x1 + x2 * x2) + kDilation * (a0 + c0) + kDilation * kDilation;
+                if (det > 0.0f) {
+                    const float idet = 1.0f / det;
+                    const float mx2 = fmaf(cam.fx, tx * itz, cam.cx);
+                    const float my2 = fmaf(cam.fy, ty * itz, cam.cy);
+                    // Tile rectangle: axis-aligned box of the q <= 9 ellipse
+                    const float hx = 3.0f * sqrtf(ca), hy = 3.0f * sqrtf(cc);
+                    const float inv_t = 1.0f / kTile;
+                    const float fx0 = floorf((mx2 - hx) * inv_t), fx1 = floorf((mx2 + hx) * inv_t);
+                    const float fy0 = floorf((my2 - hy) * inv_t), fy1 = floorf((my2 + hy) * inv_t);
+                    const int rx0 = (int)fmaxf(0.0f, fminf((float)vw.tiles_x, fx0));
+                    const int rx1 = (int)fmaxf(-1.0f, fminf((float)(vw.tiles_x - 1), fx1));
+                    const int ry0 = (int)fmaxf(0.0f, fminf((float)vw.tiles_y, fy0));
+                    const int ry1 = (int)fmaxf(-1.0f, fminf((float)(vw.tiles_y - 1), fy1));
+                    if (rx0 <= rx1 && ry0 <= ry1) {
+                        ntiles = (uint32_t)((rx1 - rx0 + 1) * (ry1 - ry0 + 1));
+                        rendered = true;
+                        cutoff = label == RARA_CUTOFF;
+                        a.rect[slot] = make_uint2((uint32_t)rx0 | ((uint32_t)ry0 << 16),
+                                                  (uint32_t)rx1 | ((uint32_t)ry1 << 16));
+                        const float op = 1.0f / (1.0f + expf(-logit));
+                        // colour at normalize(mu - e)
+                        const float ex = mx - cam.eye[0], ey = my - cam.eye[1], ez = mz - cam.eye[2];
+                        const float il = rsqrtf(ex * ex + ey * ey + ez * ez);
+                        float rgb[3];
+                        sh_colour(sc.sh, n, i, sc.sh_degree, ex * il, ey * il, ez * il, rgb);
+                        SplatRec rec;
+                        rec.r0 = make_float4(mx2, my2, cc * idet, -cb * idet);
+                        rec.r1 = make_float4(ca * idet, op, rgb[0], rgb[1]);
+                        rec.r2 = make_float4(rgb[2], cutoff ? 1.0f : 0.0f, cb / cc, cb / ca);
+                        a.rec[slot] = rec;
+                        // The sort key holds the depth rounded once from a double-precision
+                        // dot product: the correctly rounded float32 of the exact depth.
+                        a.depth[slot] = (float)fma((double)cam.R[6], (double)mx,
+                                                   fma((double)cam.R[7], (double)my,
+                                                       fma((double)cam.R[8], (double)mz, (double)cam.t[2])));
+
+                        if (cutoff) {
+                            // Ray-tracing record in the unit-sphere frame of M = k R S
+                            // (Eq. 4): M^-1 = diag(1/(k sigma)) R^T. For the pixel ray with
+                            // offset (dx, dy) from the projected centre, the local ray is
+                            // o + tau V with o = -G, V = G + P (dx, dy): G = M^-1 (mu - e) and
+                            // P = z M^-1 W^T[:, 0:2] diag(1/fx, 1/fy). m = M^T n carries the
+                            // plane into the same frame: s(x) = d_ep + m . u for x = mu + M u.
+                            const float kk = pl.k;
+                            const float iks[3] = {1.0f / (kk * s0), 1.0f / (kk * s1), 1.0f / (kk * s2)};
+                            float G[3], Px[3], Py[3], m[3];
+                            const float sx = tz / cam.fx, sy = tz / cam.fy;
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                const float rk0 = Rg[k], rk1 = Rg[3 + k], rk2 = Rg[6 + k];  // column k of R
+                                G[k] = iks[k] * (rk0 * ex + rk1 * ey + rk2 * ez);
+                                Px[k] = iks[k] * sx * (rk0 * cam.R[0] + rk1 * cam.R[1] + rk2 * cam.R[2]);
+                                Py[k] = iks[k] * sy * (rk0 * cam.R[3] + rk1 * cam.R[4] + rk2 * cam.R[5]);
+                                m[k] = kk * sg[k] * (rk0 * pl.n[0] + rk1 * pl.n[1] + rk2 * pl.n[2]);
+                            }
+                            CutRec c;
+                            c.c0 = make_float4(G[0], G[1], G[2], dep);
+                            c.c1 = make_float4(Px[0], Px[1], Px[2], m[0]);
+                            c.c2 = make_float4(Py[0], Py[1], Py[2], m[1]);
+                            c.c3 = make_float4(m[2], 0.0f, 0.0f, 0.0f);
+                            a.cut[slot] = c;
                         }
-                        CutRec c;
-                        c.c0 = make_float4(G[0], G[1], G[2], dep);
-                        c.c1 = make_float4(Px[0], Px[1], Px[2], m[0]);
-                        c.c2 = make_float4(Py[0], Py[1], Py[2], m[1]);
-                        c.c3 = make_float4(m[2], 0.0f, 0.0f, 0.0f);
-                        a.cut[i] = c;
                     }
                 }
             }
+            a.tiles[slot] = ntiles;
         }
-        a.tiles[i] = ntiles;
+        ViewCounters *vc = &a.view_counters[v];
+        block_add3(rendered ? 1ull : 0ull, ntiles, cutoff ? 1ull : 0ull, s_red, &vc->n_rendered, &vc->n_pairs,
+                   &vc->n_cutoff, &a.counters->n_rendered, &a.counters->n_pairs, &a.counters->n_cutoff);
     }
+}
 
-    // Stable compaction of rendered Gaussians: block prefix by warp ballots, global
-    // prefix by the chained scan.
+// Compaction of rendered slots in slot order: partitions of 1024 slots (4 per thread,
+// consecutive), block prefix by warp scans, global prefix by the chained scan; the 8-bit
+// digit histograms of the depth keys are accumulated on the way.
+constexpr int kCompactItems = 4;
+
+__global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
+{
+    __shared__ uint32_t s_hist[4][256];
+    __shared__ unsigned s_part;
+    __shared__ unsigned s_warp[kBlock / 32];
+    __shared__ unsigned long long s_prefix;
+    for (int t = threadIdx.x; t < 4 * 256; t += kBlock) (&s_hist[0][0])[t] = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned ballot = __ballot_sync(0xffffffffu, rendered);
-    const unsigned cut_ballot = __ballot_sync(0xffffffffu, cutoff);
-    unsigned long long pairs = ntiles;
-    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
-    if (lane == 0) {
-        s_warp_cnt[warp] = __popc(ballot);
-        s_pairs[warp] = pairs;
-        s_cut[warp] = __popc(cut_ballot);
-    }
-    __syncthreads();
-    if (warp == 0) {
-        unsigned cnt = lane < kBlock / 32 ? s_warp_cnt[lane] : 0u;
+    const uint32_t parts = (a.num_slots + kBlock * kCompactItems - 1) / (kBlock * kCompactItems);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_part = atomicAdd(&a.counters->ticket[kTicketCompact], 1u);
+        __syncthreads();
+        const uint32_t part = s_part;
+        if (part >= parts) break;
+        const uint32_t first = part * (kBlock * kCompactItems) + threadIdx.x * kCompactItems;
+        uint32_t key[kCompactItems];
+        bool flag[kCompactItems];
+        unsigned cnt = 0;
+#pragma unroll
+        for (int r = 0; r < kCompactItems; ++r) {
+            const uint32_t slot = first + r;
+            flag[r] = slot < a.num_slots && a.tiles[slot] != 0u;
+            key[r] = flag[r] ? __float_as_uint(a.depth[slot]) : 0u;
+            if (flag[r]) {
+                ++cnt;
+                atomicAdd(&s_hist[0][key[r] & 0xffu], 1u);
+                atomicAdd(&s_hist[1][(key[r] >> 8) & 0xffu], 1u);
+                atomicAdd(&s_hist[2][(key[r] >> 16) & 0xffu], 1u);
+                atomicAdd(&s_hist[3][key[r] >> 24], 1u);
+            }
+        }
         unsigned incl = cnt;
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += v;
         }
-        const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
-        if (lane < kBlock / 32) s_warp_cnt[lane] = incl - cnt;  // exclusive over warps
-        const unsigned long long prefix = warp_chained_prefix(a.lookback, part, total, &a.counters->status);
-        if (lane == 0) {
-            s_prefix = prefix;
-            unsigned long long bp = 0, bc = 0;
-            for (int w = 0; w < kBlock / 32; ++w) { bp += s_pairs[w]; bc += s_cut[w]; }
-            if (total) atomicAdd(&a.counters->n_rendered, (unsigned long long)total);
-            if (bp) atomicAdd(&a.counters->n_pairs, bp);
-            if (bc) atomicAdd(&a.counters->n_cutoff, bc);
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned w = lane < kBlock / 32 ? s_warp[lane] : 0u;
+            unsigned wi = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += v;
+            }
+            const unsigned total = __shfl_sync(0xffffffffu, wi, 31);
+            if (lane < kBlock / 32) s_warp[lane] = wi - w;
+            const unsigned long long prefix = warp_chained_prefix(a.lookback, (int)part, total, &a.counters->status);
+            if (lane == 0) s_prefix = prefix;
         }
+        __syncthreads();
+        unsigned long long pos = s_prefix + s_warp[warp] + incl - cnt;
+#pragma unroll
+        for (int r = 0; r < kCompactItems; ++r)
+            if (flag[r]) {
+                a.keys[pos] = key[r];
+                a.vals[pos] = first + r;
+                ++pos;
+            }
     }
     __syncthreads();
-    if (rendered) {
-        const unsigned long long pos = s_prefix + s_warp_cnt[warp] + __popc(ballot & ((1u << lane) - 1u));
-        a.ckeys[pos] = __float_as_uint(depth);
-        a.cvals[pos] = (uint32_t)i;
+    for (int t = threadIdx.x; t < 4 * 256; t += kBlock) {
+        const uint32_t v = (&s_hist[0][0])[t];
+        if (v) atomicAdd(&a.hist[t], v);
     }
 }
 
 }  // namespace
 
-void launch_preprocess(const PreprocessArgs &a, int num_blocks, cudaStream_t s)
+void launch_preprocess(const PreprocessArgs &a, int grid, cudaStream_t s)
 {
-    if (num_blocks > 0) k_preprocess<<<num_blocks, kBlock, 0, s>>>(a);
+    if (grid > 0) k_preprocess<<<grid, kBlock, 0, s>>>(a);
+}
+
+int compact_blocks_per_sm()
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact, kBlock, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return b;
+}
+
+void launch_compact(const CompactArgs &a, int grid, cudaStream_t s)
+{
+    if (grid > 0) k_compact<<<grid, kBlock, 0, s>>>(a);
 }
 
 }  // namespace rara

@@ -1,4 +1,22 @@
 // Internal declarations shared by the CUDA translation units of librara.so.
+//
+// The render works on a batch: one or more scenes (Gaussian sets) and one or more views,
+// each view a camera, a clip plane, a background and output buffers over one scene. A
+// single frame is a batch of one view. Every stage is one launch for the whole batch:
+//   preprocess   (scene, 256-Gaussian block) units; each loops over the scene's views and
+//                fills dense per-(view, Gaussian) slots: label, tiles touched, rectangle,
+//                splat record, depth, ray-tracing record
+//   compact      rendered slots in slot order -> (depth bits, slot), depth-digit histogram
+//   depth sort   one-sweep radix sort of those pairs
+//   emit         one (global tile id, slot) pair per touched tile, in depth order, plus the
+//                tile-id digit histogram
+//   tile sort    one-sweep radix sort of the pairs on the tile-id bits
+//   ranges       [start, end) of every global tile
+//   item order   render work items, heaviest first
+//   render       compositing of every view's pixels
+// Element counts after the preprocess live in device memory (Counters), so the sequence
+// needs no host synchronisation and can be captured in a CUDA graph; a buffer sized from a
+// capacity that a count exceeds sets kStatusOverflow instead of being written past its end.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -17,11 +35,12 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
-// Device status word bits (bounded waits that gave up).
-constexpr uint32_t kStatusLookbackTimeout = 1u;
+// Device status word bits.
+constexpr uint32_t kStatusLookbackTimeout = 1u;  // a bounded chained-scan wait gave up
+constexpr uint32_t kStatusOverflow = 2u;         // a count exceeded its buffer's capacity
 
-// Per-Gaussian splat record, written by preprocess for rendered Gaussians and gathered
-// by the render kernel: 3 x float4 = 48 bytes.
+// Per-slot splat record, written by preprocess for rendered slots and gathered by the
+// render kernel: 3 x float4 = 48 bytes.
 //   r0 = (mean2d.x, mean2d.y, conic.a, conic.b)
 //   r1 = (conic.c, opacity, rgb.r, rgb.g)
 //   r2 = (rgb.b, cutoff flag as float (1 or 0), -b/a, -b/c)
@@ -31,8 +50,8 @@ struct __align__(16) SplatRec {
     float4 r0, r1, r2;
 };
 
-// Per-cutoff-Gaussian ray-tracing record, 4 x float4 = 64 bytes, relative to the
-// Gaussian's own frame (see preprocess.cu for the derivation):
+// Per-cutoff-slot ray-tracing record, 4 x float4 = 64 bytes, relative to the Gaussian's own
+// frame (see preprocess.cu for the derivation):
 //   c0 = (G.x, G.y, G.z, d_ep)         G = M^-1 (mu - e), d_ep = n.mu + d
 //   c1 = (P00, P10, P20, m.x)          P: 3x2 map from a pixel offset to the local ray
 //   c2 = (P01, P11, P21, m.y)              offset, scaled by the centre depth
@@ -56,13 +75,38 @@ struct PlaneDev {
     int mode;
 };
 
+struct ViewDev {
+    CamDev cam;
+    PlaneDev plane;
+    int scene;
+    int tiles_x, tiles_y;
+    uint32_t tile_base;   // first global tile id of the view
+    uint32_t slot_base;   // first dense (view, Gaussian) slot of the view
+    float bg[3];
+    float *image;         // [3][H][W]
+    float *final_T;       // [H][W] or null
+    uint32_t *n_contrib;  // [H][W] or null
+};
+
+struct SceneDev {
+    const float *means, *log_scales, *quats, *logits, *sh;
+    int n;
+    int sh_degree;
+    int view_begin, view_count;  // the scene's views are contiguous in the view table
+    uint32_t unit_begin;         // first preprocess unit (256-Gaussian block) of the scene
+};
+
+struct ViewCounters {
+    unsigned long long n_rendered, n_pairs, n_cutoff;
+};
+
 // Counters written by the kernels (device), copied to pinned host memory in one block.
 struct Counters {
-    unsigned long long n_rendered;
-    unsigned long long n_pairs;
+    unsigned long long n_rendered;       // rendered slots (all views)
+    unsigned long long n_pairs;          // pairs (all views)
     unsigned long long n_cutoff;
     unsigned int num_items;              // render work items (written by the item-order kernel)
-    unsigned int pad0;
+    unsigned int depth_in_b;             // 1 if the depth sort's result is in its B buffers
     // render counters, zeroed together before each render (n_evaluated .. tile_queue)
     unsigned long long n_evaluated;      // (pixel, Gaussian) pairs inside the q <= 9 support
     unsigned long long n_walked;         // (pixel, Gaussian) pairs whose q was computed
@@ -70,89 +114,108 @@ struct Counters {
     unsigned long long n_tested;         // (warp, Gaussian) rectangle tests
     unsigned int tile_queue;             // next entry of the heaviest-first item order
     unsigned int status;
-    unsigned int part_counter[8];  // partition tickets for chained scans
+    unsigned int tile_in_b;              // 1 if the tile sort's result is in its B buffers
+    unsigned int ticket[13];             // partition tickets of the persistent kernels
 };
 constexpr size_t kRenderCounterBytes = 4 * sizeof(unsigned long long) + sizeof(unsigned int);
+// ticket slots
+constexpr int kTicketPre = 0, kTicketCompact = 1, kTicketEmit = 2, kTicketSortDepth = 3, kTicketSortTile = 7;
 
+// Stage 1: preprocess
 struct PreprocessArgs {
-    const float *means, *log_scales, *quats, *logits, *sh;
-    int n;
-    int sh_degree;
-    CamDev cam;
-    PlaneDev plane;
-    int tiles_x, tiles_y;
-    // outputs
+    const SceneDev *scenes;
+    int num_scenes;
+    const ViewDev *views;
+    int num_units;         // sum over scenes of ceil(n / 256)
+    // dense per-slot outputs
     uint8_t *labels;
     uint32_t *tiles;       // tiles touched (0 = not rendered)
-    uint2 *rect;           // (tx0 | ty0 << 16, tx1 | ty1 << 16)
+    uint2 *rect;           // (tx0 | ty0 << 16, tx1 | ty1 << 16), tile coordinates in the view
     SplatRec *rec;
     CutRec *cut;
-    float *depth;          // camera-space depth (float32 key value) of rendered Gaussians
-    uint32_t *ckeys;       // compacted depth keys (float bits) of rendered Gaussians
-    uint32_t *cvals;       // their indices, ascending
-    unsigned long long *lookback;  // per-block chained-scan words, zeroed before launch
+    float *depth;          // camera-space depth (the float32 sort key) of rendered slots
+    ViewCounters *view_counters;
     Counters *counters;
 };
+void launch_preprocess(const PreprocessArgs &a, int grid, cudaStream_t s);
 
-void launch_preprocess(const PreprocessArgs &a, int num_blocks, cudaStream_t s);
-
-// Stable LSD radix sort of (uint32 key, uint32 value) pairs on bits [0, key_bits).
-// Buffers: keys/vals hold the input and receive the output (ping-pong through alt_*).
-// Returns the number of launches queued; *result_in_alt tells which buffer pair holds the
-// sorted result. scratch must hold sort_scratch_bytes(n, key_bits) bytes.
-size_t sort_scratch_bytes(int64_t n, int key_bits);
-int sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *alt_keys, uint32_t *alt_vals,
-               int n, int key_bits, void *scratch, uint32_t *status, cudaStream_t s,
-               bool *result_in_alt);
-
-struct EmitArgs {
-    const uint32_t *sorted_vals;   // Gaussian indices in depth order, n_rendered of them
+// Stage 2: compaction of rendered slots (slot order) + histogram of the depth-key digits
+struct CompactArgs {
     const uint32_t *tiles;
-    const uint2 *rect;
-    int n_rendered;
-    int tiles_x;
-    unsigned long long n_pairs;    // capacity of pair_keys / pair_vals
-    uint32_t *pair_keys;           // tile id
-    uint32_t *pair_vals;           // Gaussian index
+    const float *depth;
+    uint32_t num_slots;
+    uint32_t *keys;        // depth bits
+    uint32_t *vals;        // slot
+    uint32_t *hist;        // [4][256] digit histogram of the keys, zeroed before
     unsigned long long *lookback;
     Counters *counters;
 };
-void launch_emit(const EmitArgs &a, int num_blocks, cudaStream_t s);
+void launch_compact(const CompactArgs &a, int grid, cudaStream_t s);
+int compact_blocks_per_sm();
 
-void launch_ranges(const uint32_t *sorted_tile_keys, int n_pairs, int num_tiles, int2 *ranges, cudaStream_t s);
+// One-sweep LSD radix sort of (uint32 key, uint32 value) over bits [0, 8 * passes).
+// The element count is read from device memory (*n, clamped to cap). hist holds the
+// 8-bit digit histograms of all passes (built by the producer of the keys). A pass whose
+// digit is the same for every key is skipped; *result_in_b is set on the device to 1 when
+// the result ends in the B buffers. scratch: sort_scratch_bytes(cap, passes) bytes.
+size_t sort_scratch_bytes(int64_t cap, int passes);
+int sort_launch(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, const unsigned long long *n,
+                uint32_t cap, int passes, const uint32_t *hist, void *scratch, unsigned int *tickets,
+                unsigned int *status, unsigned int *result_in_b, int grid, cudaStream_t s);
+int sort_blocks_per_sm();
 
-// Render work items ordered by descending list length (log2 buckets): heaviest first.
-// A tile whose list has at least 2^(split4_bits-1) entries becomes 4 items (16x4 pixels,
-// 4 lanes per pixel), at least 2^(split2_bits-1) entries 2 items (16x8, 2 lanes per pixel),
-// otherwise 1 item. Item = tile << 4 | log2(lanes per pixel) << 2 | part. order must hold
-// 4 * num_tiles entries; the item count goes to counters->num_items.
+// Stage 4: emission of (global tile, slot) pairs in depth order + tile-digit histogram
+struct EmitArgs {
+    const uint32_t *keys_a, *vals_a, *keys_b, *vals_b;  // the depth sort's two buffers
+    const uint32_t *tiles;
+    const uint2 *rect;
+    const ViewDev *views;
+    int num_views;
+    uint32_t cap_pairs;
+    int tile_passes;
+    uint32_t *pair_keys;     // global tile id
+    uint32_t *pair_vals;     // slot
+    uint32_t *tile_hist;     // [tile_passes][256], zeroed before
+    unsigned long long *lookback;
+    Counters *counters;
+};
+void launch_emit(const EmitArgs &a, int grid, cudaStream_t s);
+int emit_blocks_per_sm();
+
+// Stage 6: ranges of the sorted pairs (ranges zeroed before)
+void launch_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const Counters *counters, uint32_t cap_pairs,
+                   uint32_t num_tiles, int2 *ranges, int grid, cudaStream_t s);
+
+// Stage 7: render work items ordered by descending list length (log2 buckets), heaviest
+// first. A tile whose list has at least 2^(split4_bits-1) entries becomes 4 items (16x4
+// pixels, 4 lanes per pixel), at least 2^(split2_bits-1) entries 2 items (16x8, 2 lanes
+// per pixel), otherwise 1 item. Item = tile << 4 | log2(lanes per pixel) << 2 | part.
+// order holds 4 * num_tiles entries; the item count goes to counters->num_items.
 void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int split4_bits, uint32_t *order,
                        Counters *counters, cudaStream_t s);
 
+// Stage 8: render
 struct RenderArgs {
     const int2 *ranges;
     const uint32_t *tile_order;
-    int num_tiles;
-    const uint32_t *pair_vals;
+    const uint32_t *vals_a, *vals_b;  // the tile sort's value buffers (slots)
     const SplatRec *rec;
     const CutRec *cut;
-    int W, H, tiles_x;
-    float bg[3];
-    float *image;
-    float *final_T;
-    uint32_t *n_contrib;
+    const ViewDev *views;
+    int num_views;
     Counters *counters;
 };
 void launch_render(const RenderArgs &a, int grid, cudaStream_t s);
 int render_blocks_per_sm();
 
-// Debug exports
-void launch_export_gaussians(int n, const uint8_t *labels_src, const uint32_t *tiles_src,
+// Debug exports of one view
+void launch_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_src, const uint32_t *tiles_src,
                              const uint2 *rect_src, const SplatRec *rec, const float *depth_src, uint8_t *labels,
-                             float *depth, float *mean2d, float *conic, float *rgb,
-                             float *opacity, int32_t *rect, uint32_t *tiles, cudaStream_t s);
-void launch_export_pairs(int n_pairs, const uint32_t *tile_keys, const uint32_t *vals,
-                         const float *depth, const int2 *ranges, int num_tiles,
-                         uint64_t *keys, uint32_t *values, int64_t *ranges_out, cudaStream_t s);
+                             float *depth, float *mean2d, float *conic, float *rgb, float *opacity, int32_t *rect,
+                             uint32_t *tiles, cudaStream_t s);
+void launch_export_pairs(const uint32_t *keys_a, const uint32_t *vals_a, const uint32_t *keys_b,
+                         const uint32_t *vals_b, const Counters *counters, const float *depth, const int2 *ranges,
+                         uint32_t tile_base, uint32_t slot_base, int num_tiles, uint32_t pair_begin,
+                         uint32_t pair_end, uint64_t *keys, uint32_t *values, int64_t *ranges_out, cudaStream_t s);
 
 }  // namespace rara

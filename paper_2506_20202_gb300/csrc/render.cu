@@ -131,22 +131,24 @@ __device__ __forceinline__ float entry_alpha(const Stage &st, int j, float pxf, 
 //   LPP 2: rows [8 part, 8 part + 8), warp rectangles 8x2
 //   LPP 4: rows [4 part, 4 part + 4), warp rectangles 4x2
 template <int LPP>
-__device__ __forceinline__ void render_item(const RenderArgs &a, Stage &st, int tile, int part, Tally &ty)
+__device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &vw, const uint32_t *pair_vals,
+                                            Stage &st, int gtile, int tile, int part, Tally &ty)
 {
     constexpr int RW = LPP == 4 ? 4 : 8;     // warp rectangle width
     constexpr int RH = LPP == 1 ? 4 : 2;     // warp rectangle height
     constexpr int WPR = kTile / RW;          // warp rectangles per row
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane % LPP, pix = lane / LPP;
-    const int tx = tile % a.tiles_x, ty0 = tile / a.tiles_x;
+    const int W = vw.cam.W, H = vw.cam.H;
+    const int tx = tile % vw.tiles_x, ty0 = tile / vw.tiles_x;
     const int wx0 = (warp % WPR) * RW;
     const int wy0 = part * (kTile / LPP) + (warp / WPR) * RH;
     const int px = tx * kTile + wx0 + pix % RW, py = ty0 * kTile + wy0 + pix / RW;
-    const bool inside = px < a.W && py < a.H;
+    const bool inside = px < W && py < H;
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
     const float rx0 = (float)(tx * kTile + wx0) + 0.5f, rx1 = rx0 + (float)(RW - 1);
     const float ry0 = (float)(ty0 * kTile + wy0) + 0.5f, ry1 = ry0 + (float)(RH - 1);
-    const int2 range = a.ranges[tile];
+    const int2 range = a.ranges[gtile];
 
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     bool done = !inside;
@@ -156,7 +158,7 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, Stage &st, int 
         if (__syncthreads_count(done) == kBlock) break;
         const int k = base + threadIdx.x;
         if (k < range.y) {
-            const uint32_t g = __ldg(&a.pair_vals[k]);
+            const uint32_t g = __ldg(&pair_vals[k]);
             const SplatRec rec = a.rec[g];
             st.r0[threadIdx.x] = rec.r0;
             st.r1[threadIdx.x] = rec.r1;
@@ -269,13 +271,13 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, Stage &st, int 
     }
 
     if (inside && sub == 0) {
-        const size_t p = (size_t)py * a.W + px;
-        const size_t plane = (size_t)a.W * a.H;
-        a.image[p] = fmaf(T, a.bg[0], C0);
-        a.image[plane + p] = fmaf(T, a.bg[1], C1);
-        a.image[2 * plane + p] = fmaf(T, a.bg[2], C2);
-        if (a.final_T) a.final_T[p] = T;
-        if (a.n_contrib) a.n_contrib[p] = last;
+        const size_t p = (size_t)py * W + px;
+        const size_t plane = (size_t)W * H;
+        vw.image[p] = fmaf(T, vw.bg[0], C0);
+        vw.image[plane + p] = fmaf(T, vw.bg[1], C1);
+        vw.image[2 * plane + p] = fmaf(T, vw.bg[2], C2);
+        if (vw.final_T) vw.final_T[p] = T;
+        if (vw.n_contrib) vw.n_contrib[p] = last;
     }
 }
 
@@ -285,6 +287,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_render(RenderArgs a)
     __shared__ unsigned s_item;
     Tally ty;
     const unsigned num_items = *(volatile unsigned *)&a.counters->num_items;
+    const uint32_t *pair_vals = a.counters->tile_in_b ? a.vals_b : a.vals_a;
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned q = atomicAdd(&a.counters->tile_queue, 1u);
@@ -293,10 +296,19 @@ __global__ void __launch_bounds__(kBlock, 4) k_render(RenderArgs a)
         __syncthreads();
         const unsigned item = s_item;
         if (item == 0xffffffffu) break;
-        const int tile = (int)(item >> 4), lpp_log2 = (int)((item >> 2) & 3u), part = (int)(item & 3u);
-        if (lpp_log2 == 0) render_item<1>(a, st, tile, 0, ty);
-        else if (lpp_log2 == 1) render_item<2>(a, st, tile, part, ty);
-        else render_item<4>(a, st, tile, part, ty);
+        const int gtile = (int)(item >> 4), lpp_log2 = (int)((item >> 2) & 3u), part = (int)(item & 3u);
+        // view owning the global tile: the last view whose tile base is <= gtile
+        int lo = 0, hi = a.num_views - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.views[mid].tile_base <= (uint32_t)gtile) lo = mid;
+            else hi = mid - 1;
+        }
+        const ViewDev &vw = a.views[lo];
+        const int tile = gtile - (int)vw.tile_base;
+        if (lpp_log2 == 0) render_item<1>(a, vw, pair_vals, st, gtile, tile, 0, ty);
+        else if (lpp_log2 == 1) render_item<2>(a, vw, pair_vals, st, gtile, tile, part, ty);
+        else render_item<4>(a, vw, pair_vals, st, gtile, tile, part, ty);
         __syncthreads();  // everyone has read s_item and the staged batch
     }
 

@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librara.so")
 
-RARA_OK, RARA_ERR_INVALID_ARG, RARA_ERR_BUDGET, RARA_ERR_CUDA, RARA_ERR_TIMEOUT = 0, 1, 2, 3, 4
+RARA_OK, RARA_ERR_INVALID_ARG, RARA_ERR_BUDGET, RARA_ERR_CUDA, RARA_ERR_TIMEOUT, RARA_ERR_OVERFLOW = 0, 1, 2, 3, 4, 5
 MODE_NONE, MODE_HARD, MODE_RARA, MODE_RARA_ALL = 0, 1, 2, 3
 INVISIBLE, VISIBLE, CUTOFF = 0, 1, 2
 
@@ -42,6 +42,11 @@ class rara_plane(C.Structure):
     _fields_ = [("n", C.c_float * 3), ("d", C.c_float), ("k_sigma", C.c_float), ("mode", C.c_int32)]
 
 
+class rara_view(C.Structure):
+    _fields_ = [("scene", C.c_int32), ("camera", rara_camera), ("plane", rara_plane), ("bg", C.c_float * 3),
+                ("image", C.c_void_p), ("final_T", C.c_void_p), ("n_contrib", C.c_void_p)]
+
+
 class rara_frame_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_rendered", C.c_int64), ("n_cutoff", C.c_int64),
                 ("n_pairs", C.c_int64), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
@@ -65,9 +70,12 @@ SIGNATURES = {
     "rara_render": (C.c_int, [_P, C.POINTER(C.c_float), _P, _P, _P, _P]),
     "rara_render_frame": (C.c_int, [_P, C.POINTER(rara_gaussians), C.POINTER(rara_camera),
                                     C.POINTER(rara_plane), C.POINTER(C.c_float), _P, _P, _P, _P]),
-    "rara_frame_info_get": (C.c_int, [_P, C.POINTER(rara_frame_info)]),
-    "rara_frame_gaussians": (C.c_int, [_P] * 10),
-    "rara_frame_pairs": (C.c_int, [_P] * 5),
+    "rara_render_batch": (C.c_int, [_P, C.POINTER(rara_gaussians), C.c_int32, C.POINTER(rara_view), C.c_int32, _P]),
+    "rara_render_batch_graph": (C.c_int, [_P, C.POINTER(rara_gaussians), C.c_int32, C.POINTER(rara_view), C.c_int32,
+                                          _P]),
+    "rara_frame_info_get": (C.c_int, [_P, C.c_int32, C.POINTER(rara_frame_info)]),
+    "rara_frame_gaussians": (C.c_int, [_P, C.c_int32] + [_P] * 9),
+    "rara_frame_pairs": (C.c_int, [_P, C.c_int32] + [_P] * 4),
     "rara_render_frame_noalloc": (C.c_int, [C.POINTER(rara_gaussians), C.POINTER(rara_camera),
                                             C.POINTER(rara_plane), C.POINTER(C.c_float), _P, _P, _P, _P]),
 }
@@ -228,20 +236,62 @@ def rara_render_frame_noalloc(gaussians: GaussianTensors, cam, plane, bg, image,
         raise RaraError(rc, "rara_render_frame_noalloc failed (RARA_ERR_BUDGET: input beyond the static limits)")
 
 
-def rara_frame_info_get(ctx) -> dict:
+@dataclasses.dataclass
+class View:
+    """One view of a batch: scene index, camera, plane, background and device outputs."""
+    scene: int
+    camera: object
+    plane: object
+    image: "torch.Tensor"
+    final_T: "torch.Tensor" = None
+    n_contrib: "torch.Tensor" = None
+    bg: tuple = (0.0, 0.0, 0.0)
+
+    def c_struct(self) -> rara_view:
+        v = rara_view()
+        v.scene = int(self.scene)
+        v.camera = camera_struct(self.camera)
+        v.plane = plane_struct(self.plane)
+        for k in range(3):
+            v.bg[k] = float(self.bg[k])
+        v.image = self.image.data_ptr()
+        v.final_T = None if self.final_T is None else self.final_T.data_ptr()
+        v.n_contrib = None if self.n_contrib is None else self.n_contrib.data_ptr()
+        return v
+
+
+def _batch_structs(scenes, views):
+    sc = (rara_gaussians * len(scenes))(*[g.c_struct() for g in scenes])
+    vw = (rara_view * len(views))(*[v.c_struct() for v in views])
+    return sc, vw
+
+
+def rara_render_batch(ctx, scenes, views, stream=None):
+    """Render every View of `views` (list) over the GaussianTensors of `scenes` (list)."""
+    sc, vw = _batch_structs(scenes, views)
+    _check(ctx, load().rara_render_batch(ctx, sc, len(scenes), vw, len(views), _stream(stream)))
+
+
+def rara_render_batch_graph(ctx, scenes, views, stream=None):
+    """As rara_render_batch, replaying a CUDA graph of the batch's stages once captured."""
+    sc, vw = _batch_structs(scenes, views)
+    _check(ctx, load().rara_render_batch_graph(ctx, sc, len(scenes), vw, len(views), _stream(stream)))
+
+
+def rara_frame_info_get(ctx, view: int = 0) -> dict:
     info = rara_frame_info()
-    _check(ctx, load().rara_frame_info_get(ctx, C.byref(info)))
+    _check(ctx, load().rara_frame_info_get(ctx, int(view), C.byref(info)))
     return {k: getattr(info, k) for k, _ in rara_frame_info._fields_}
 
 
-def rara_frame_gaussians(ctx, labels=None, depth=None, mean2d=None, conic=None, rgb=None, opacity=None,
-                         rect=None, tiles=None, stream=None):
-    _check(ctx, load().rara_frame_gaussians(ctx, _ptr(labels), _ptr(depth), _ptr(mean2d), _ptr(conic), _ptr(rgb),
-                                            _ptr(opacity), _ptr(rect), _ptr(tiles), _stream(stream)))
+def rara_frame_gaussians(ctx, view: int = 0, labels=None, depth=None, mean2d=None, conic=None, rgb=None,
+                         opacity=None, rect=None, tiles=None, stream=None):
+    _check(ctx, load().rara_frame_gaussians(ctx, int(view), _ptr(labels), _ptr(depth), _ptr(mean2d), _ptr(conic),
+                                            _ptr(rgb), _ptr(opacity), _ptr(rect), _ptr(tiles), _stream(stream)))
 
 
-def rara_frame_pairs(ctx, keys=None, values=None, ranges=None, stream=None):
-    _check(ctx, load().rara_frame_pairs(ctx, _ptr(keys), _ptr(values), _ptr(ranges), _stream(stream)))
+def rara_frame_pairs(ctx, view: int = 0, keys=None, values=None, ranges=None, stream=None):
+    _check(ctx, load().rara_frame_pairs(ctx, int(view), _ptr(keys), _ptr(values), _ptr(ranges), _stream(stream)))
 
 
 # --------------------------------------------------------------------------------------
@@ -278,7 +328,7 @@ class Renderer:
         rara_render_frame(self.ctx, gaussians, cam, plane, bg, image, T, nc, stream)
         return image, T, nc
 
-    def frame_gaussians(self, n: int):
+    def frame_gaussians(self, n: int, view: int = 0):
         import torch
         dev = "cuda"
         out = dict(labels=torch.zeros(n, dtype=torch.uint8, device=dev),
@@ -289,16 +339,16 @@ class Renderer:
                    opacity=torch.zeros(n, dtype=torch.float32, device=dev),
                    rect=torch.zeros((4, n), dtype=torch.int32, device=dev),
                    tiles=torch.zeros(n, dtype=torch.int32, device=dev))
-        rara_frame_gaussians(self.ctx, **out)
+        rara_frame_gaussians(self.ctx, view, **out)
         return out
 
-    def frame_pairs(self):
+    def frame_pairs(self, view: int = 0):
         import torch
-        info = rara_frame_info_get(self.ctx)
+        info = rara_frame_info_get(self.ctx, view)
         p = int(info["n_pairs"])
         nt = info["tiles_x"] * info["tiles_y"]
         keys = torch.zeros(max(p, 1), dtype=torch.int64, device="cuda")
         vals = torch.zeros(max(p, 1), dtype=torch.int32, device="cuda")
         ranges = torch.zeros((nt, 2), dtype=torch.int64, device="cuda")
-        rara_frame_pairs(self.ctx, keys, vals, ranges)
+        rara_frame_pairs(self.ctx, view, keys, vals, ranges)
         return keys[:p], vals[:p], ranges, info

@@ -1,0 +1,138 @@
+"""Batched multi-view render and its CUDA-graph replay, through the C ABI.
+
+A batch renders many views (cameras, planes, resolutions) of one or more scenes with one
+launch per stage; every view must equal the same view rendered alone (bit for bit: the
+per-view arithmetic and list order are the same), and the oracle.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2506_20202_gb300 import rara, scenes
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_20202_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _outputs(cam):
+    H, W = cam.height, cam.width
+    return (torch.full((3, H, W), -1.0, dtype=torch.float32, device="cuda"),
+            torch.full((H, W), -1.0, dtype=torch.float32, device="cuda"),
+            torch.zeros((H, W), dtype=torch.int32, device="cuda"))
+
+
+def _batch_case(seed=0):
+    rng = np.random.default_rng(seed)
+    sc = [scenes.uniform_scene(6000, seed=seed, sh_degree=1), scenes.general_scene(8000, seed=seed + 1, sh_degree=3)]
+    sizes = [(160, 120), (96, 200), (256, 144), (64, 64), (200, 136), (33, 47)]
+    views = []
+    for k, (w, h) in enumerate(sizes):
+        eye = rng.normal(0, 1, 3)
+        eye = 3.0 * eye / np.linalg.norm(eye)
+        cam = scenes.look_at_camera(eye, (0.0, 0.0, 0.0), w, h, 60.0)
+        nrm = np.float32(scenes.random_unit_normal(seed * 100 + k))
+        mode = [scenes.MODE_RARA, scenes.MODE_RARA, scenes.MODE_HARD, scenes.MODE_RARA_ALL, scenes.MODE_NONE,
+                scenes.MODE_RARA][k]
+        pl = scenes.Plane(nrm, float(rng.uniform(-0.2, 0.2)), 3.0, mode)
+        views.append((k % 2, cam, pl, tuple(rng.uniform(0, 0.3, 3))))
+    return sc, views
+
+
+def _render_batch(r, sc_t, views, graph=False):
+    vs = []
+    for (si, cam, pl, bg) in views:
+        img, T, nc = _outputs(cam)
+        vs.append(rara.View(si, cam, pl, img, T, nc, bg))
+    fn = rara.rara_render_batch_graph if graph else rara.rara_render_batch
+    fn(r.ctx, sc_t, vs)
+    rara.rara_ctx_sync(r.ctx)
+    return [(v.image.cpu().numpy(), v.final_T.cpu().numpy(), v.n_contrib.cpu().numpy()) for v in vs]
+
+
+def test_batch_views_equal_single_renders():
+    sc, views = _batch_case(0)
+    sc_t = [rara.GaussianTensors.from_scene(s) for s in sc]
+    r = rara.Renderer()
+    got = _render_batch(r, sc_t, views)
+    for (si, cam, pl, bg), (img, T, nc) in zip(views, got):
+        ref = parity.gpu_frame(sc[si], cam, pl, bg, export=False)
+        assert np.array_equal(img, ref["image"].astype(np.float32))
+        assert np.array_equal(T, ref["T"].astype(np.float32))
+        assert np.array_equal(nc, ref["n_contrib"])
+    r.close()
+
+
+def test_batch_views_against_oracle():
+    sc, views = _batch_case(1)
+    sc_t = [rara.GaussianTensors.from_scene(s) for s in sc]
+    r = rara.Renderer()
+    got = _render_batch(r, sc_t, views)
+    for k, ((si, cam, pl, bg), (img, T, nc)) in enumerate(zip(views, got)):
+        report = {}
+        fg = r.frame_gaussians(sc[si].n, view=k)
+        keys, vals, ranges, info = r.frame_pairs(view=k)
+        gpu = dict(image=img.astype(np.float64), T=T.astype(np.float64), n_contrib=nc,
+                   g={kk: v.cpu().numpy() for kk, v in fg.items()}, keys=keys.cpu().numpy().view(np.uint64),
+                   vals=vals.cpu().numpy().view(np.uint32), ranges=ranges.cpu().numpy())
+        pre = oracle.preprocess(sc[si], cam, pl)
+        kvr = oracle.build_keys(pre)
+        parity.check_gaussians(pre, gpu["g"], report)
+        parity.check_pairs(pre, kvr, gpu, report)
+        ref = oracle.render(sc[si], pre, cam, pl, bg, kvr)
+        parity.check_image(pre, ref, gpu, report, max_flag_frac=0.08)
+        assert info["n_pairs"] == report["pairs_gpu"]
+    r.close()
+
+
+def test_graph_replay_with_new_cameras_matches_exact():
+    sc, views = _batch_case(2)
+    sc_t = [rara.GaussianTensors.from_scene(s) for s in sc]
+    rg = rara.Renderer()
+    _render_batch(rg, sc_t, views, graph=True)                # renders exactly, then captures
+    _, views2 = _batch_case(3)                                 # same shape, new cameras and planes
+    views2 = [(views[k][0],) + tuple(views2[k][1:]) for k in range(len(views))]
+    l0 = rara.rara_ctx_launches(rg.ctx)
+    got = _render_batch(rg, sc_t, views2, graph=True)         # replay
+    assert rara.rara_ctx_launches(rg.ctx) - l0 >= 10           # the graph's kernels ran
+    re = rara.Renderer()
+    ref = _render_batch(re, sc_t, views2)
+    for (a, b) in zip(got, ref):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    rg.close()
+    re.close()
+
+
+def test_graph_overflow_is_reported_and_recovers():
+    """A replay whose pairs exceed the captured capacity writes none past it, is reported
+    as RARA_ERR_OVERFLOW, and the next call recaptures with room for them. Same shape
+    (same n and SH degree), but the second scene's Gaussians are about 7 times larger."""
+    small = scenes.uniform_scene(20000, seed=5, sh_degree=0)
+    big = scenes.uniform_scene(20000, seed=5, sh_degree=0)
+    big.log_scales = np.ascontiguousarray(big.log_scales + np.float32(2.0))
+    pl = scenes.Plane(np.float32([0, 0, 1]), 0.0, 3.0, scenes.MODE_RARA)
+    view = [(0, scenes.look_at_camera((0, 0, -3.0), (0, 0, 0), 128, 128, 60.0), pl, (0, 0, 0))]
+    r = rara.Renderer()
+    _render_batch(r, [rara.GaussianTensors.from_scene(small)], view, graph=True)
+    big_t = [rara.GaussianTensors.from_scene(big)]
+    with pytest.raises(rara.RaraError) as e:
+        _render_batch(r, big_t, view, graph=True)
+    assert e.value.code == rara.RARA_ERR_OVERFLOW
+    got = _render_batch(r, big_t, view, graph=True)            # recaptures with a larger capacity
+    got2 = _render_batch(r, big_t, view, graph=True)           # and replays it
+    ref = _render_batch(rara.Renderer(), big_t, view)
+    for a in (got, got2):
+        for x, y in zip(a[0], ref[0]):
+            assert np.array_equal(x, y)
+    r.close()
