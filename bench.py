@@ -6,10 +6,13 @@ for a Mip-NeRF360 capture) at 1920x1080 with a sweep of 16 parallel clip-plane o
 across the scene (the plane-sweep protocol of the paper's render-efficiency experiment).
 One step = one sweep = 16 clipped frames through the C ABI (preprocess, bin, render).
 
-Prints one JSON line: frames/s (device-resident inputs), per-frame p50/p99 latency, the
-end-to-end figure with host buffers, the roofline of the dominant kernel, the CPU
-oracle timed on this host, SM clocks sampled during the timed region, and the number of
-kernel launches in the timed region.
+Prints one JSON line. `value` is frames/s of the batched path (the 16 sweep frames as one
+batch, one launch per stage, replayed as a CUDA graph, autotuned) with the scene resident;
+`paths` also gives the plain one-frame-per-launch-sequence path, `latency_ms` the p50/p99 of
+both, `e2e` the batched path end to end with host buffers, `roofline` the batched render
+launch, `serving` a continuous-batching server against the plain path on Poisson arrivals,
+`cpu_baseline` the FP64 oracle timed on this host, `clocks` the SM clocks sampled during the
+timed region, and `gpu_launches` the kernel launches in it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -51,7 +54,7 @@ RENDER_SRC = os.path.join(ROOT, "paper_2506_20202_gb300", "csrc", "render.cu")
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=150)
+    ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=1_000_000)
@@ -59,7 +62,11 @@ def parse_args():
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--sweep", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--plain-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-s", type=float, default=4.0, help="serving window (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-3m", action=argparse.BooleanOptionalAction, default=True)
     return ap.parse_args()
 
 
@@ -244,7 +251,7 @@ def run_ours(args):
     import numpy as np
     import torch
 
-    from paper_2506_20202_gb300 import build, rara, scenes
+    from paper_2506_20202_gb300 import autotune, build, rara, scenes, serve
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -258,13 +265,16 @@ def run_ours(args):
 
     scene, cam, planes = scenes.general_workload(args.n, args.width, args.height, seed=0, sweep=args.sweep)
     gs = rara.GaussianTensors.from_scene(scene, f"cuda:{local}")
-    ctx = rara.rara_ctx_create(0)
     H, W = cam.height, cam.width
+    stream = torch.cuda.Stream()
+    bg = (0.0, 0.0, 0.0)
+    nplanes = len(planes)
+
+    # ---------------- plain path: one frame per launch sequence --------------------------
+    ctx = rara.rara_ctx_create(0)
     image = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
     final_T = torch.empty((H, W), dtype=torch.float32, device="cuda")
     n_contrib = torch.empty((H, W), dtype=torch.int32, device="cuda")
-    stream = torch.cuda.Stream()
-    bg = (0.0, 0.0, 0.0)
 
     def frame(pl, evs=None):
         if evs is not None:
@@ -279,21 +289,54 @@ def run_ours(args):
         if evs is not None:
             evs[3].record(stream)
 
-    # warm-up
     for _ in range(args.warmup):
         for pl in planes:
             frame(pl)
-    stream.synchronize()
-
-    # per-plane work counters (untimed pass)
     counts = []
     for pl in planes:
         frame(pl)
         counts.append(rara.rara_frame_info_get(ctx))
     stream.synchronize()
+    plain_steps = max(3, min(args.steps, args.plain_steps))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(plain_steps * nplanes)]
+    p_begin, p_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    p_begin.record(stream)
+    k = 0
+    for _ in range(plain_steps):
+        for pl in planes:
+            frame(pl, evs[k])
+            k += 1
+    p_end.record(stream)
+    stream.synchronize()
+    plain_ms = p_begin.elapsed_time(p_end)
+    lat = [e[0].elapsed_time(e[3]) for e in evs]
+    t_pre = [e[0].elapsed_time(e[1]) for e in evs]
+    t_bin = [e[1].elapsed_time(e[2]) for e in evs]
+    t_ren = [e[2].elapsed_time(e[3]) for e in evs]
+    plain = {"frames_per_s": plain_steps * nplanes / (plain_ms / 1e3), "p50_ms": percentile(lat, 50),
+             "p99_ms": percentile(lat, 99), "stage_ms": {"preprocess": statistics.mean(t_pre),
+                                                         "bin": statistics.mean(t_bin),
+                                                         "render": statistics.mean(t_ren)},
+             "note": "per frame: preprocess, bin (one host wait), render on one stream"}
+    rara.rara_ctx_destroy(ctx)
 
-    nfr = args.steps * len(planes)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(nfr)]
+    # ---------------- batched path: the sweep as one batch, CUDA-graph replay ------------
+    bctx = rara.rara_ctx_create(0)
+    outs = [(torch.empty((3, H, W), dtype=torch.float32, device="cuda"),
+             torch.empty((H, W), dtype=torch.float32, device="cuda"),
+             torch.empty((H, W), dtype=torch.int32, device="cuda")) for _ in planes]
+    views = [rara.View(0, cam, pl, o[0], o[1], o[2], bg) for pl, o in zip(planes, outs)]
+    best, tune_ms = autotune.autotune(bctx, [gs], views, stream, reps=3)
+    # stage times and work counts of one exact batched render (for the roofline)
+    rara.rara_render_batch(bctx, [gs], views, stream)
+    stage = rara.rara_ctx_stage_ms(bctx)
+    binfo = rara.rara_frame_info_get(bctx, 0)
+    for _ in range(args.warmup):
+        rara.rara_render_batch_graph(bctx, [gs], views, stream)
+    rara.rara_ctx_sync(bctx, stream)
+
+    sevs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     t_begin, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(torch.cuda.current_device())
     if dist:
@@ -301,18 +344,18 @@ def run_ours(args):
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)
-    launches0 = rara.rara_ctx_launches(ctx)
+    launches0 = rara.rara_ctx_launches(bctx)
     t_begin.record(stream)
-    k = 0
-    for _ in range(args.steps):
-        for pl in planes:
-            frame(pl, evs[k])
-            k += 1
+    for kk in range(args.steps):
+        sevs[kk][0].record(stream)
+        rara.rara_render_batch_graph(bctx, [gs], views, stream)
+        sevs[kk][1].record(stream)
     t_end.record(stream)
     stream.synchronize()
     torch.cuda.synchronize()
-    launches = rara.rara_ctx_launches(ctx) - launches0
+    launches = rara.rara_ctx_launches(bctx) - launches0
     sampler.stop()
+    rara.rara_ctx_sync(bctx, stream)   # raises if a replay overflowed its pair capacity
     if dist:
         dist.barrier()
     elapsed_ms = t_begin.elapsed_time(t_end)
@@ -320,93 +363,141 @@ def run_ours(args):
         t = torch.tensor([elapsed_ms], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed_ms = float(t.item())
-    value = world * nfr / (elapsed_ms / 1e3)
-
-    lat = [e[0].elapsed_time(e[3]) for e in evs]
-    t_pre = [e[0].elapsed_time(e[1]) for e in evs]
-    t_bin = [e[1].elapsed_time(e[2]) for e in evs]
-    t_ren = [e[2].elapsed_time(e[3]) for e in evs]
+    value = world * args.steps * nplanes / (elapsed_ms / 1e3)
+    blat = [e[0].elapsed_time(e[1]) for e in sevs]
+    batched = {"frames_per_s": value, "batch_p50_ms": percentile(blat, 50), "batch_p99_ms": percentile(blat, 99),
+               "views_per_batch": nplanes, "tuning": list(best),
+               "autotune_ms": {json.dumps(list(k2)): v for k2, v in tune_ms.items()},
+               "stage_ms_exact_batch": {"preprocess": stage[0], "bin": stage[1], "render": stage[2]},
+               "note": "the 16 sweep frames as one batch (one launch per stage), replayed as a CUDA graph; "
+                       "a request's latency is its batch's"}
     clocks = sampler.summary()
 
-    # roofline of the dominant kernel (the render: one launch per frame)
+    # roofline of the dominant kernel: the render launch of the batch
     peaks, peak_kind = measured_peaks()
-    stage_ms = {"preprocess": statistics.mean(t_pre), "bin": statistics.mean(t_bin),
-                "render": statistics.mean(t_ren)}
-    flop = [FLOP_TEST * c["n_tested"] + FLOP_WALKED * c["n_walked"] + FLOP_EVAL * c["n_evaluated"]
-            + FLOP_CUT * c["n_cut_evaluated"] for c in counts]
-    ren_by_plane = [statistics.mean(t_ren[i::len(planes)]) for i in range(len(planes))]
-    achieved = statistics.mean([f / (t * 1e-3) for f, t in zip(flop, ren_by_plane)]) / 1e12
+    flop = (FLOP_TEST * binfo["n_tested"] + FLOP_WALKED * binfo["n_walked"] + FLOP_EVAL * binfo["n_evaluated"]
+            + FLOP_CUT * binfo["n_cut_evaluated"])
+    achieved = flop / (stage[2] * 1e-3) / 1e12
     sm_max = float(clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
     peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
-    roofline = {"bound": "alu", "kernel": "k_render", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_for_current_kernel(),
+    roofline = {"bound": "alu", "kernel": "k_render (one launch for the 16-view batch)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for_current_kernel(),
                 "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES} lanes x 2 FLOP x {sm_max:.0f} MHz "
                               f"(recipe unit counts, max SM clock)",
-                "per_frame_units": {"tested": statistics.mean(c["n_tested"] for c in counts),
-                                    "walked": statistics.mean(c["n_walked"] for c in counts),
-                                    "evaluated": statistics.mean(c["n_evaluated"] for c in counts),
-                                    "cut_evaluated": statistics.mean(c["n_cut_evaluated"] for c in counts)}}
-    # HBM view of the other stages (context)
+                "per_launch_units": {"tested": binfo["n_tested"], "walked": binfo["n_walked"],
+                                     "evaluated": binfo["n_evaluated"], "cut_evaluated": binfo["n_cut_evaluated"]}}
     n = scene.n
     pre_bytes = n * (12 + 12 + 16 + 4 + 4 * scene.sh.shape[0]) + \
-        statistics.mean(c["n_rendered"] * (48 + 8 + 8) + n * 5 + c["n_cutoff"] * 64 for c in counts)
-    stages = {k2: {"ms": v} for k2, v in stage_ms.items()}
-    stages["preprocess"]["algorithmic_GBps"] = pre_bytes / (stage_ms["preprocess"] * 1e-3) / 1e9
-    stages["preprocess"]["hbm_frac"] = stages["preprocess"]["algorithmic_GBps"] / peaks["hbm_gbs"]
+        statistics.mean(c["n_rendered"] * (48 + 8 + 8) + n * 9 + c["n_cutoff"] * 64 for c in counts)
+    plain["preprocess_algorithmic_GBps"] = pre_bytes / (plain["stage_ms"]["preprocess"] * 1e-3) / 1e9
+    plain["preprocess_hbm_frac"] = plain["preprocess_algorithmic_GBps"] / peaks["hbm_gbs"]
 
-    # end to end through the C ABI with host buffers: per step the scene is uploaded from
-    # pinned host memory and each frame's image is read back into pinned host memory
+    # end to end through the C ABI with host buffers (graph path): per step the scene is
+    # uploaded from pinned host memory and every image is read back into pinned host memory
     host = {k2: torch.from_numpy(np.ascontiguousarray(getattr(scene, k2), np.float32)).pin_memory()
             for k2 in ("means", "log_scales", "quats", "opacity_logits", "sh")}
     dev = rara.GaussianTensors(*(torch.empty_like(host[k2], device="cuda") for k2 in
                                  ("means", "log_scales", "quats", "opacity_logits", "sh")), scene.sh_degree)
     img_host = [torch.empty((3, H, W), dtype=torch.float32).pin_memory() for _ in planes]
     h2d = sum(t.numel() * 4 for t in host.values())
-    d2h = len(planes) * 3 * H * W * 4
-    torch.cuda.synchronize()
+    d2h = nplanes * 3 * H * W * 4
+    ectx = rara.rara_ctx_create(0)
+    rara.rara_ctx_set_tuning(ectx, *best)
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            for k2 in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+                getattr(dev, k2).copy_(host[k2], non_blocking=True)
+        rara.rara_render_batch_graph(ectx, [dev], views, stream)
+        with torch.cuda.stream(stream):
+            for i in range(nplanes):
+                img_host[i].copy_(outs[i][0], non_blocking=True)
+
+    e2e_step()
+    e2e_step()
+    rara.rara_ctx_sync(ectx, stream)
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        with torch.cuda.stream(stream):
-            for k2, name in zip(("means", "log_scales", "quats", "opacity_logits", "sh"),
-                                ("means", "log_scales", "quats", "opacity_logits", "sh")):
-                getattr(dev, name).copy_(host[k2], non_blocking=True)
-            for i, pl in enumerate(planes):
-                rara.rara_render_frame(ctx, dev, cam, pl, bg, image, None, None, stream)
-                img_host[i].copy_(image, non_blocking=True)
-    stream.synchronize()
+        e2e_step()
+    rara.rara_ctx_sync(ectx, stream)
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * args.e2e_steps * len(planes) / e2e_s, "unit": UNIT,
+    rara.rara_ctx_destroy(ectx)
+    e2e = {"value": world * args.e2e_steps * nplanes / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "note": "per step: scene upload from pinned host memory + one C-ABI render per sweep frame + "
-                   "image read-back into pinned host memory; host wall clock"}
+           "note": "per step: scene upload from pinned host memory + one C-ABI batched render of the 16 sweep "
+                   "frames (graph replay) + read-back of every image into pinned host memory; host wall clock"}
     if dist:
         t = torch.tensor([e2e_s], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e["value"] = world * args.e2e_steps * len(planes) / float(t.item())
+        e2e["value"] = world * args.e2e_steps * nplanes / float(t.item())
+    rara.rara_ctx_destroy(bctx)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args),
-        "latency_ms": {"plain_p50": percentile(lat, 50), "plain_p99": percentile(lat, 99),
-                       "note": "per-frame preprocess+bin+render on one stream, one request per launch sequence"},
-        "stages_ms": stages,
+        "paths": {"batched_graph": batched, "plain": plain},
+        "latency_ms": {"plain_p50": plain["p50_ms"], "plain_p99": plain["p99_ms"],
+                       "batched_p50": batched["batch_p50_ms"], "batched_p99": batched["batch_p99_ms"]},
         "roofline": roofline, "peak_source": peak_kind,
         "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
         "frame_counts": {"cutoff_fraction_per_plane": [round(c["n_cutoff"] / max(1, c["n_rendered"]), 4)
                                                        for c in counts],
                          "pairs_mean": statistics.mean(c["n_pairs"] for c in counts)},
     }
+    if rank == 0 and world == 1 and args.serve_s > 0:
+        line["serving"] = run_serving(args, gs, scene)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fr, fs, sample, spent = oracle_frame_rate(scene, cam, planes, [4, 8, 12], 6, 16, os.cpu_count() or 1)
         line["cpu_baseline"] = {"value": fr, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
                                 "sample": sample, "seconds": spent}
-    rara.rara_ctx_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_serving(args, gs_1m, scene_1m):
+    """Continuous-batching server vs the plain one-request-per-launch path on the same
+    seeded Poisson arrivals: resident scenes of 100k, 1M and 3M Gaussians, random scene,
+    camera, resolution (512^2, 1280x720, 1920x1080) and plane per request, 60 GB budget."""
+    import torch
+
+    from paper_2506_20202_gb300 import rara, scenes, serve
+    sc = {"100k": rara.GaussianTensors.from_scene(scenes.general_scene(100_000, seed=11)), "1M": gs_1m}
+    if args.serve_3m:
+        sc["3M"] = rara.GaussianTensors.from_scene(scenes.general_scene(3_000_000, seed=12))
+    names = list(sc)
+    out = {"scenes": names, "budget_gb": 60, "rate_hz": args.serve_rate, "window_s": args.serve_s}
+    reqs = serve.poisson_requests(names, serve.orbit_camera, args.serve_rate, args.serve_s, seed=21)
+    # warm both paths on a few requests (allocations, graph-free contexts)
+    warm = serve.poisson_requests(names, serve.orbit_camera, 200.0, 0.05, seed=22)
+    serve.serve_plain(sc, warm, keep_images=False)
+    srv = serve.Server(sc, budget_bytes=60 << 30, slots=2, max_batch=64, keep_images=False)
+    try:
+        srv.run(warm)
+        srv.results.clear()
+        res = srv.run(reqs)
+        out["served"] = serve.summarize(res, args.serve_s)
+        out["served"]["batches"] = srv.batches
+        out["served"]["rejected"] = srv.rejected
+    finally:
+        srv.close()
+    torch.cuda.synchronize()
+    res_p = serve.serve_plain(sc, reqs, keep_images=False)
+    out["plain"] = serve.summarize(res_p, args.serve_s)
+    # the same arrivals 10x faster, where the GPU is the bottleneck
+    fast = serve.poisson_requests(names, serve.orbit_camera, args.serve_rate * 10, args.serve_s / 4, seed=23)
+    srv = serve.Server(sc, budget_bytes=60 << 30, slots=2, max_batch=64, keep_images=False)
+    try:
+        res = srv.run(fast)
+        out["served_10x_rate"] = serve.summarize(res)
+        out["served_10x_rate"]["batches"] = srv.batches
+    finally:
+        srv.close()
+    out["plain_10x_rate"] = serve.summarize(serve.serve_plain(sc, fast, keep_images=False))
+    return out
 
 
 def main():

@@ -134,6 +134,11 @@ int rara_ctx_sync(rara_ctx *ctx, void *stream);
  * order of the compositing sums. Defaults: 11 and 12. */
 int rara_ctx_set_tuning(rara_ctx *ctx, int32_t split2_bits, int32_t split4_bits);
 
+/* GPU time (ms) of the stages of the last frame or batch rendered without a graph:
+ * out[0] preprocess + compaction, out[1] sorts, emission, ranges and render order, out[2]
+ * render. Waits for that render to finish. */
+int rara_ctx_stage_ms(rara_ctx *ctx, float out[3]);
+
 /* Number of kernel launches this context has queued since creation (all entry points). */
 int64_t rara_ctx_launches(const rara_ctx *ctx);
 

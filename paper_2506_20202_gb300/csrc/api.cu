@@ -75,6 +75,11 @@ struct rara_ctx {
     int64_t graph_kernels = 0;          // kernel launches one replay makes
 
     bool owns_host = true;              // false for the static context
+
+    // stage timing of the last batch rendered outside a graph: preprocess start, bin start,
+    // render start, render end
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool capturing = false;
 };
 
 namespace {
@@ -133,6 +138,11 @@ void release(rara_ctx *c, DevBuf &b)
 }
 
 bool finite(float v) { return isfinite(v) != 0; }
+
+void mark(rara_ctx *c, int k, cudaStream_t s)
+{
+    if (c->ev[k] && !c->capturing) cudaEventRecord(c->ev[k], s);
+}
 
 int launched(rara_ctx *c, const char *what, int count = 1)
 {
@@ -319,6 +329,7 @@ int batch_preprocess(rara_ctx *c, cudaStream_t s)
     occupancy_setup(c);
     Counters *dc = (Counters *)c->counters.p;
     const size_t nn = c->num_slots > 0 ? (size_t)c->num_slots : 1;
+    mark(c, 0, s);
     if ((rc = check_cuda(c, cudaMemsetAsync(dc, 0, sizeof(Counters), s), "memset counters")) ||
         (rc = check_cuda(c, cudaMemsetAsync(c->view_counters_d.p, 0, sizeof(ViewCounters) * (size_t)c->num_views, s),
                          "memset view counters")) ||
@@ -392,6 +403,7 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
     uint32_t *hist = (uint32_t *)c->hist.p;
     const size_t nn = c->num_slots > 0 ? (size_t)c->num_slots : 1;
     c->cap_pairs = cap;
+    mark(c, 1, s);
     const int sgrid = c->sm_count * c->bpsm_sort;
     int nl = sort_launch((uint32_t *)c->ckeys.p, (uint32_t *)c->cvals.p, (uint32_t *)c->ckeys_b.p,
                          (uint32_t *)c->cvals_b.p, &dc->n_rendered, (uint32_t)nn, 4, hist, c->sort_scratch.p,
@@ -443,6 +455,7 @@ int batch_render(rara_ctx *c, cudaStream_t s)
     int rc;
     occupancy_setup(c);
     Counters *dc = (Counters *)c->counters.p;
+    mark(c, 2, s);
     if ((rc = check_cuda(c, cudaMemsetAsync(&dc->n_evaluated, 0, kRenderCounterBytes, s), "memset render counters")))
         return rc;
     RenderArgs a;
@@ -458,7 +471,9 @@ int batch_render(rara_ctx *c, cudaStream_t s)
     const long long slots = (long long)c->sm_count * c->bpsm_render;
     const long long items = 4ll * c->num_tiles;
     launch_render(a, (int)(items < slots ? items : slots), s);
-    return launched(c, "render launch", c->num_tiles > 0);
+    rc = launched(c, "render launch", c->num_tiles > 0);
+    mark(c, 3, s);
+    return rc;
 }
 
 // Exact binning: wait for the preprocess to know the pair count, size the buffers, launch.
@@ -492,6 +507,8 @@ void free_host(rara_ctx *c)
     free(c->shape);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (cudaEvent_t &e : c->ev)
+        if (e) cudaEventDestroy(e);
 }
 
 }  // namespace
@@ -522,6 +539,7 @@ int rara_ctx_create(size_t budget_bytes, int32_t tile_w, int32_t tile_h, rara_ct
     c->h_view_map = (int *)malloc(sizeof(int) * kMaxViews);
     c->h_view_n = (int *)malloc(sizeof(int) * kMaxViews);
     ok = ok && c->h_view_map && c->h_view_n;
+    for (cudaEvent_t &e : c->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         release(c, c->counters);
@@ -553,6 +571,18 @@ const char *rara_last_error(const rara_ctx *c) { return c ? c->err : "null conte
 size_t rara_ctx_bytes(const rara_ctx *c) { return c ? c->held : 0; }
 
 int64_t rara_ctx_launches(const rara_ctx *c) { return c ? c->launches : 0; }
+
+int rara_ctx_stage_ms(rara_ctx *c, float out[3])
+{
+    if (!c || !out) return RARA_ERR_INVALID_ARG;
+    if (!c->ev[0]) return fail(c, RARA_ERR_INVALID_ARG, "no stage timing on this context");
+    int rc = check_cuda(c, cudaEventSynchronize(c->ev[3]), "event wait");
+    if (rc) return rc;
+    for (int k = 0; k < 3; ++k)
+        if ((rc = check_cuda(c, cudaEventElapsedTime(&out[k], c->ev[k], c->ev[k + 1]), "event elapsed time")))
+            return rc;
+    return RARA_OK;
+}
 
 int rara_ctx_set_tuning(rara_ctx *c, int32_t split2_bits, int32_t split4_bits)
 {
@@ -736,6 +766,7 @@ int rara_render_batch_graph(rara_ctx *c, const rara_gaussians *scenes, int32_t n
     }
     const int64_t launches0 = c->launches;
     cudaGraph_t g = nullptr;
+    c->capturing = true;
     rc = check_cuda(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     if (!rc) {
         int rc2 = batch_preprocess(c, c->cap_stream);
@@ -747,6 +778,7 @@ int rara_render_batch_graph(rara_ctx *c, const rara_gaussians *scenes, int32_t n
         rc = check_cuda(c, cudaStreamEndCapture(c->cap_stream, &g), "end capture");
         if (rc2) rc = rc2;
     }
+    c->capturing = false;
     c->graph_kernels = c->launches - launches0;
     c->launches = launches0;  // capturing launches nothing
     if (!rc) rc = check_cuda(c, cudaGraphInstantiate(&c->graph, g, 0), "graph instantiate");

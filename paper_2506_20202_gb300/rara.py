@@ -64,6 +64,7 @@ SIGNATURES = {
     "rara_ctx_sync": (C.c_int, [_P, _P]),
     "rara_ctx_launches": (C.c_int64, [_P]),
     "rara_ctx_set_tuning": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "rara_ctx_stage_ms": (C.c_int, [_P, C.POINTER(C.c_float)]),
     "rara_preprocess": (C.c_int, [_P, C.POINTER(rara_gaussians), C.POINTER(rara_camera),
                                   C.POINTER(rara_plane), _P]),
     "rara_bin": (C.c_int, [_P, _P]),
@@ -197,6 +198,13 @@ def rara_ctx_launches(ctx) -> int:
 
 def rara_ctx_set_tuning(ctx, split2_bits: int, split4_bits: int):
     _check(ctx, load().rara_ctx_set_tuning(ctx, int(split2_bits), int(split4_bits)))
+
+
+def rara_ctx_stage_ms(ctx):
+    """(preprocess, bin, render) GPU milliseconds of the last frame or batch rendered without a graph."""
+    out = (C.c_float * 3)()
+    _check(ctx, load().rara_ctx_stage_ms(ctx, out))
+    return tuple(float(x) for x in out)
 
 
 def rara_ctx_sync(ctx, stream=None):
