@@ -14,6 +14,9 @@
  *   rara_render_batch   many views (cameras, planes, resolutions) of one or more scenes in
  *                    one launch per stage; rara_render_batch_graph replays the batch's stage
  *                    sequence as a captured CUDA graph
+ *   rara_render_backward   gradients of a loss on the rendered images with respect to the
+ *                    Gaussians' parameters and the clip planes (an extension: the paper
+ *                    renders only)
  *
  * Conventions
  *   - All device pointers are CUDA device memory on the current device; sizes are
@@ -185,6 +188,44 @@ int rara_render_batch(rara_ctx *ctx, const rara_gaussians *scenes, int32_t num_s
  * the capacity so the next call recaptures. */
 int rara_render_batch_graph(rara_ctx *ctx, const rara_gaussians *scenes, int32_t num_scenes,
                             const rara_view *views, int32_t num_views, void *stream);
+
+/* Gradients of one scene, device arrays in the layouts of rara_gaussians (means[3][n],
+ * log_scales[3][n], quats[4][n] with respect to the unnormalised input quaternion,
+ * opacity_logits[n], sh[(L+1)^2 * 3][n]). */
+typedef struct rara_gaussian_grads {
+    float *means;
+    float *log_scales;
+    float *quats;
+    float *opacity_logits;
+    float *sh;
+} rara_gaussian_grads;
+
+/* Backward of the last render on this context (rara_render / rara_render_frame,
+ * rara_render_batch, or rara_render_batch_graph): given dL/dimage for every view, writes
+ * the gradients of the Gaussians' parameters and of every view's clip plane. The paper
+ * renders only (the Discussion's limitations leave re-optimising Gaussians after clipping
+ * to future work); this differentiates the forward of Eq. 2, Eq. 9-12 and Algorithm 1 as
+ * the kernels compute it: where the weight w is 0 or 1 (the chord on one side of the
+ * plane, a ray that misses the ellipsoid), where alpha is clamped at 0.99 or the colour
+ * at 0, the gradient through that factor is 0; the class thresholds, the q <= 9 support, the 1/255 alpha
+ * cut-off and the 1e-4 transmittance stop are discontinuities and pass none.
+ *   dL_dimages   [num_views] device pointers, view v's dL/dimage [3][H][W] (the caller's
+ *                view order, as given to the forward)
+ *   grads        [num_scenes] gradient arrays, written (not accumulated): every Gaussian of
+ *                every scene gets its sum over the views that render it, 0 if none
+ *   plane_grads  device float[num_views][4] = dL/d(n.x, n.y, n.z, d) per view, written; or
+ *                NULL. k_sigma and the mode are not differentiated.
+ * The forward must have been given final_T and n_contrib buffers for every view, and its
+ * inputs and outputs must be unchanged. Returns RARA_ERR_INVALID_ARG if there is no
+ * rendered frame or batch on the context, a view lacks final_T / n_contrib, or a pointer is
+ * NULL. Asynchronous on `stream`; gradient sums use float atomics, so they are not
+ * bit-reproducible. */
+int rara_render_backward(rara_ctx *ctx, const float *const *dL_dimages, const rara_gaussian_grads *grads,
+                         float *plane_grads, void *stream);
+
+/* GPU milliseconds of the last rara_render_backward: [0] the per-tile render backward,
+ * [1] the per-Gaussian preprocess backward. Waits for them to finish. */
+int rara_ctx_backward_ms(rara_ctx *ctx, float out[2]);
 
 /* Counts of one view of the current frame or batch (view 0 for a single frame), valid after
  * rara_bin; the render counts are totals of the last rara_render over all views. Waits for

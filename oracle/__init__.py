@@ -70,8 +70,13 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
 
 
-def _f32(a):
-    return np.ascontiguousarray(np.asarray(a, np.float32))
+def _f64(a):
+    """Gaussian parameters as double: float32 arrays widen exactly, float64 arrays (finite-
+    difference perturbations) are passed through unrounded."""
+    a = np.asarray(a)
+    if a.dtype != np.float64:
+        a = np.asarray(a, np.float32).astype(np.float64)
+    return np.ascontiguousarray(a)
 
 
 def cam16(cam) -> np.ndarray:
@@ -82,6 +87,11 @@ def cam16(cam) -> np.ndarray:
 
 
 def plane4(plane) -> np.ndarray:
+    """(n, d) as the GPU receives them (float32), or unrounded when the plane carries an
+    attribute exact=True (finite-difference perturbations of the plane)."""
+    if getattr(plane, "exact", False):
+        n = np.asarray(plane.n, np.float64)
+        return np.array([n[0], n[1], n[2], float(plane.d)], np.float64)
     n = np.asarray(plane.n, np.float32).astype(np.float64)
     return np.array([n[0], n[1], n[2], float(np.float32(plane.d))], np.float64)
 
@@ -95,8 +105,8 @@ def preprocess(scene, cam, plane, tile=(16, 16)) -> dict:
         rect=np.zeros((n, 4), np.int32), tiles=np.zeros(n, np.int32), rgb=np.zeros((n, 3)),
         opacity=np.zeros(n), d_ep=np.zeros(n), radius=np.zeros(n), margin_class=np.zeros(n),
         margin_gauss=np.zeros(n), margin_rect=np.zeros(n))
-    sc = [_f32(scene.means), _f32(scene.log_scales), _f32(scene.quats),
-          _f32(scene.opacity_logits), _f32(scene.sh)]
+    sc = [_f64(scene.means), _f64(scene.log_scales), _f64(scene.quats),
+          _f64(scene.opacity_logits), _f64(scene.sh)]
     c16, p4 = cam16(cam), plane4(plane)
     rc = lib.orc_preprocess(n, *[_p(a) for a in sc], int(scene.sh_degree), _p(c16),
                             int(cam.width), int(cam.height), _p(p4), float(np.float32(plane.k_sigma)),
@@ -141,7 +151,7 @@ def render(scene, pre: dict, cam, plane, bg=(0.0, 0.0, 0.0), binned=None, tol=DE
     T = np.zeros((H, W))
     nc = np.zeros((H, W), np.int32)
     ev = np.zeros((H, W), np.uint8)
-    sc = [_f32(scene.means), _f32(scene.log_scales), _f32(scene.quats)]
+    sc = [_f64(scene.means), _f64(scene.log_scales), _f64(scene.quats)]
     c16, p4 = cam16(cam), plane4(plane)
     bgv = np.asarray(bg, np.float64).copy()
     tolv = np.asarray(tol, np.float64).copy()
@@ -184,7 +194,7 @@ def rara_weight(e, d, mu, quat, sigma, k_sigma, plane_n, plane_d):
 
 def sh_colour(degree: int, coeffs, direction):
     lib = _load()
-    cf = _f32(coeffs).reshape(-1)
+    cf = _f64(coeffs).reshape(-1)
     assert cf.size == 3 * (degree + 1) ** 2
     d = np.ascontiguousarray(np.asarray(direction, np.float64))
     rgb = np.zeros(3)

@@ -7,8 +7,9 @@
  * smoke test and by the benchmark's CPU-baseline leg; nothing on the product path links,
  * loads or calls it, and it shares no code with the CUDA library.
  *
- * Arithmetic is double precision throughout. Inputs arrive as the same float32 arrays the
- * GPU consumes and are widened on load. Every step follows the paper's order:
+ * Arithmetic is double precision throughout. The Gaussians' parameters arrive as double
+ * arrays: the float32 values the GPU consumes, widened exactly, or (for finite-difference
+ * gradients) any double values. Every step follows the paper's order:
  *   1. per Gaussian: covariance V = R S^2 R^T (Section 3.1), three-way classification
  *      against the plane (Section 3.2, Eq. 3; Algorithm 1 step 1), EWA projection of the
  *      covariance (Section 3.4, Eq. 9-10), colour from real spherical harmonics;
@@ -128,14 +129,14 @@ double orc_real_sh(int l, int m, const double *dir)
 }
 
 /* Colour of Gaussian i seen along unit direction dir: sum_k sh_k Y_k(dir) + 0.5, clamped at 0. */
-static void eval_colour(const float *sh, int64_t n, int64_t i, int degree, const double *dir, double rgb[3])
+static void eval_colour(const double *sh, int64_t n, int64_t i, int degree, const double *dir, double rgb[3])
 {
     for (int c = 0; c < 3; ++c) rgb[c] = 0.0;
     for (int l = 0; l <= degree; ++l)
         for (int m = -l; m <= l; ++m) {
             int k = l * l + l + m;
             double y = orc_real_sh(l, m, dir);
-            for (int c = 0; c < 3; ++c) rgb[c] += (double)sh[(int64_t)(k * 3 + c) * n + i] * y;
+            for (int c = 0; c < 3; ++c) rgb[c] += sh[(int64_t)(k * 3 + c) * n + i] * y;
         }
     for (int c = 0; c < 3; ++c) rgb[c] = fmax(rgb[c] + 0.5, 0.0);
 }
@@ -165,8 +166,8 @@ static void eval_colour(const float *sh, int64_t n, int64_t i, int degree, const
  * RARA is the paper's three-way rule; RARA_ALL uses the three-way rule but ray-traces
  * every non-invisible Gaussian (label cutoff for all of them).
  */
-int orc_preprocess(int64_t n, const float *means, const float *log_scales, const float *quats,
-                   const float *opacity_logits, const float *sh, int sh_degree,
+int orc_preprocess(int64_t n, const double *means, const double *log_scales, const double *quats,
+                   const double *opacity_logits, const double *sh, int sh_degree,
                    const double *cam16, int W, int H, const double *plane4, double k_sigma, int mode,
                    int tile_w, int tile_h,
                    uint8_t *label, uint8_t *culled, double *depth, double *mean2d, double *cov2d,
@@ -182,7 +183,7 @@ int orc_preprocess(int64_t n, const float *means, const float *log_scales, const
 
     for (int64_t i = 0; i < n; ++i) {
         double mu[3] = {means[i], means[n + i], means[2 * n + i]};
-        double sig[3] = {exp((double)log_scales[i]), exp((double)log_scales[n + i]), exp((double)log_scales[2 * n + i])};
+        double sig[3] = {exp(log_scales[i]), exp(log_scales[n + i]), exp(log_scales[2 * n + i])};
 
         /* Section 3.2 / Algorithm 1 step 1: signed distance of the centre and r = 3 max sigma. */
         double dep = dot3(pn, mu) + pd;
@@ -285,7 +286,7 @@ int orc_preprocess(int64_t n, const float *means, const float *log_scales, const
         tiles[i] = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
         culled[i] = 0;
 
-        opacity[i] = 1.0 / (1.0 + exp(-(double)opacity_logits[i]));
+        opacity[i] = 1.0 / (1.0 + exp(-opacity_logits[i]));
         double dir[3] = {mu[0] - cam.e[0], mu[1] - cam.e[1], mu[2] - cam.e[2]};
         double dl = sqrt(dot3(dir, dir));
         for (int k = 0; k < 3; ++k) dir[k] /= dl;
@@ -430,7 +431,7 @@ double orc_rara_weight(const double *e, const double *d, const double *mu, const
 }
 
 /* Colour evaluation exposed for tests (coefficients for one Gaussian, [(L+1)^2 * 3]). */
-void orc_sh_colour(int degree, const float *coeffs, const double *dir, double *rgb)
+void orc_sh_colour(int degree, const double *coeffs, const double *dir, double *rgb)
 {
     double dn = sqrt(dot3(dir, dir));
     double du[3] = {dir[0] / dn, dir[1] / dn, dir[2] / dn};
@@ -469,7 +470,7 @@ static int f32_ulp_close(float a, float b, int ulps)
  * (1 + list position of the last blended Gaussian in binned mode, the count of walked
  * candidates in brute mode), events [H, W].
  */
-int orc_render(int64_t n, const float *means, const float *log_scales, const float *quats,
+int orc_render(int64_t n, const double *means, const double *log_scales, const double *quats,
                const uint8_t *label, const uint8_t *culled, const double *depth,
                const double *mean2d, const double *conic, const double *rgb, const double *opacity,
                const double *margin_gauss,
@@ -544,7 +545,7 @@ int orc_render(int64_t n, const float *means, const float *log_scales, const flo
                 double w = 1.0;
                 if (label[i] == ORC_CUTOFF) {
                     double mu[3] = {means[i], means[n + i], means[2 * n + i]};
-                    double sig[3] = {exp((double)log_scales[i]), exp((double)log_scales[n + i]), exp((double)log_scales[2 * n + i])};
+                    double sig[3] = {exp(log_scales[i]), exp(log_scales[n + i]), exp(log_scales[2 * n + i])};
                     double Rg[3][3];
                     quat_to_rot(quats[i], quats[n + i], quats[2 * n + i], quats[3 * n + i], Rg);
                     w = orc_rara_weight_full(cam.e, dw, mu, Rg, sig, k_sigma, pn, pd, NULL, &ev, tol_disc);

@@ -75,6 +75,15 @@ struct rara_ctx {
     int64_t graph_kernels = 0;          // kernel launches one replay makes
 
     bool owns_host = true;              // false for the static context
+    bool rendered = false;              // the current batch has been rendered (backward may follow)
+
+    // backward: gradient records, tables of the dL/dimage and gradient pointers
+    DevBuf grec, bviews_d, bscenes_d;
+    BwdView *h_bviews = nullptr;        // pinned [max_views]
+    BwdScene *h_bscenes = nullptr;      // pinned [max_scenes]
+    cudaEvent_t bwd_uploaded = nullptr;
+    cudaEvent_t bev[3] = {nullptr, nullptr, nullptr};
+    int bpsm_render_bwd = 0;
 
     // stage timing of the last batch rendered outside a graph: preprocess start, bin start,
     // render start, render end
@@ -169,6 +178,7 @@ void occupancy_setup(rara_ctx *c)
     c->bpsm_sort = sort_blocks_per_sm();
     c->bpsm_emit = emit_blocks_per_sm();
     c->bpsm_compact = compact_blocks_per_sm();
+    c->bpsm_render_bwd = render_bwd_blocks_per_sm();
 }
 
 int check_gaussians(rara_ctx *c, const rara_gaussians *g)
@@ -247,6 +257,7 @@ int upload_tables(rara_ctx *c, cudaStream_t s)
 int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_view *views, int nv, cudaStream_t s)
 {
     c->stage = 0;
+    c->rendered = false;
     if (ns < 1 || ns > c->max_scenes) return fail(c, RARA_ERR_INVALID_ARG, "%d scenes (1..%d)", ns, c->max_scenes);
     if (nv < 1 || nv > c->max_views) return fail(c, RARA_ERR_INVALID_ARG, "%d views (1..%d)", nv, c->max_views);
     int rc;
@@ -500,6 +511,11 @@ void free_host(rara_ctx *c)
         if (st.scenes) cudaFreeHost(st.scenes);
         if (st.uploaded) cudaEventDestroy(st.uploaded);
     }
+    if (c->h_bviews) cudaFreeHost(c->h_bviews);
+    if (c->h_bscenes) cudaFreeHost(c->h_bscenes);
+    if (c->bwd_uploaded) cudaEventDestroy(c->bwd_uploaded);
+    for (cudaEvent_t &e : c->bev)
+        if (e) cudaEventDestroy(e);
     if (c->h_counters) cudaFreeHost(c->h_counters);
     if (c->h_view_counters) cudaFreeHost(c->h_view_counters);
     free(c->h_view_map);
@@ -540,6 +556,11 @@ int rara_ctx_create(size_t budget_bytes, int32_t tile_w, int32_t tile_h, rara_ct
     c->h_view_n = (int *)malloc(sizeof(int) * kMaxViews);
     ok = ok && c->h_view_map && c->h_view_n;
     for (cudaEvent_t &e : c->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+    ok = ok && cudaHostAlloc((void **)&c->h_bviews, sizeof(BwdView) * kMaxViews, cudaHostAllocDefault) == cudaSuccess;
+    ok = ok && cudaHostAlloc((void **)&c->h_bscenes, sizeof(BwdScene) * kMaxScenes, cudaHostAllocDefault) ==
+                   cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&c->bwd_uploaded, cudaEventDisableTiming) == cudaSuccess;
+    for (cudaEvent_t &e : c->bev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         release(c, c->counters);
@@ -559,7 +580,7 @@ int rara_ctx_destroy(rara_ctx *c)
     DevBuf *all[] = {&c->views_d, &c->scenes_d, &c->view_counters_d, &c->counters, &c->labels, &c->tiles,
                      &c->rect, &c->rec, &c->cut, &c->depth, &c->ckeys, &c->cvals, &c->ckeys_b, &c->cvals_b,
                      &c->lookback_c, &c->pkeys, &c->pvals, &c->pkeys_b, &c->pvals_b, &c->lookback_e, &c->hist,
-                     &c->ranges, &c->items, &c->sort_scratch};
+                     &c->ranges, &c->items, &c->sort_scratch, &c->grec, &c->bviews_d, &c->bscenes_d};
     for (DevBuf *b : all) release(c, *b);
     free_host(c);
     delete c;
@@ -673,6 +694,7 @@ int rara_render(rara_ctx *c, const float bg[3], float *image, float *final_T, ui
     if (st.uploaded && (rc = check_cuda(c, cudaEventRecord(st.uploaded, s), "staging event"))) return rc;
     if ((rc = batch_render(c, s))) return rc;
     c->last_stream = s;
+    c->rendered = true;
     return RARA_OK;
 }
 
@@ -701,6 +723,7 @@ int rara_render_batch(rara_ctx *c, const rara_gaussians *scenes, int32_t num_sce
     if ((rc = batch_render(c, s))) return rc;
     c->last_stream = s;
     c->stage = 2;
+    c->rendered = true;
     return RARA_OK;
 }
 
@@ -740,6 +763,7 @@ int rara_render_batch_graph(rara_ctx *c, const rara_gaussians *scenes, int32_t n
         c->launches += c->graph_kernels;
         c->last_stream = s;
         c->stage = 2;
+        c->rendered = true;
         return RARA_OK;
     }
     // First batch of this shape: render it exactly, then capture the stage sequence.
@@ -792,6 +816,131 @@ int rara_render_batch_graph(rara_ctx *c, const rara_gaussians *scenes, int32_t n
     c->shape = shape;
     c->shape_len = len;
     c->graph_cap_pairs = (uint32_t)cap;
+    // The pair buffers may have grown for the capture, which drops the exact render's pairs:
+    // replay once so the batch's intermediate state matches its outputs again (a backward
+    // may follow).
+    c->rendered = false;
+    if ((rc = check_cuda(c, cudaGraphLaunch(c->graph, s), "cudaGraphLaunch"))) return rc;
+    c->launches += c->graph_kernels;
+    c->cap_pairs = c->graph_cap_pairs;
+    c->rendered = true;
+    return RARA_OK;
+}
+
+int rara_render_backward(rara_ctx *c, const float *const *dL_dimages, const rara_gaussian_grads *grads,
+                         float *plane_grads, void *stream)
+{
+    if (!c) return RARA_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (!c->owns_host) return fail(c, RARA_ERR_INVALID_ARG, "the static context has no backward");
+    if (!c->rendered || c->stage < 2)
+        return fail(c, RARA_ERR_INVALID_ARG, "rara_render_backward needs a rendered frame or batch on this context");
+    if (!dL_dimages || !grads) return fail(c, RARA_ERR_INVALID_ARG, "null dL_dimages or grads");
+    for (int v = 0; v < c->num_views; ++v) {
+        if (!dL_dimages[v]) return fail(c, RARA_ERR_INVALID_ARG, "view %d has no dL/dimage", v);
+        const ViewDev &vd = c->h_views[c->h_view_map[v]];
+        if (!vd.final_T || !vd.n_contrib)
+            return fail(c, RARA_ERR_INVALID_ARG, "view %d was rendered without final_T and n_contrib", v);
+    }
+    for (int si = 0; si < c->num_scenes; ++si) {
+        const rara_gaussian_grads &g = grads[si];
+        if (c->h_scenes[si].n > 0 && (!g.means || !g.log_scales || !g.quats || !g.opacity_logits || !g.sh))
+            return fail(c, RARA_ERR_INVALID_ARG, "scene %d has a null gradient array", si);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    occupancy_setup(c);
+    // the pinned tables are refilled only after their last upload has been read
+    if ((rc = check_cuda(c, cudaEventSynchronize(c->bwd_uploaded), "backward table wait"))) return rc;
+    int max_degree = 0;
+    for (int v = 0; v < c->num_views; ++v) {
+        BwdView &b = c->h_bviews[c->h_view_map[v]];
+        b.dimage = dL_dimages[v];
+        b.plane_grad = plane_grads ? plane_grads + 4 * (size_t)v : nullptr;
+    }
+    for (int si = 0; si < c->num_scenes; ++si) {
+        const rara_gaussian_grads &g = grads[si];
+        BwdScene &b = c->h_bscenes[si];
+        b.means = g.means; b.log_scales = g.log_scales; b.quats = g.quats; b.logits = g.opacity_logits; b.sh = g.sh;
+        if (c->h_scenes[si].view_count > 0 && c->h_scenes[si].sh_degree > max_degree)
+            max_degree = c->h_scenes[si].sh_degree;
+    }
+    const size_t nn = c->num_slots > 0 ? (size_t)c->num_slots : 1;
+    if ((rc = ensure(c, c->grec, nn * sizeof(GradRec), "gradient records")) ||
+        (rc = ensure(c, c->bviews_d, sizeof(BwdView) * (size_t)c->num_views, "backward view table")) ||
+        (rc = ensure(c, c->bscenes_d, sizeof(BwdScene) * (size_t)c->num_scenes, "backward scene table")))
+        return rc;
+    if ((rc = check_cuda(c, cudaMemcpyAsync(c->bviews_d.p, c->h_bviews, sizeof(BwdView) * (size_t)c->num_views,
+                                            cudaMemcpyHostToDevice, s), "backward view table upload")) ||
+        (rc = check_cuda(c, cudaMemcpyAsync(c->bscenes_d.p, c->h_bscenes, sizeof(BwdScene) * (size_t)c->num_scenes,
+                                            cudaMemcpyHostToDevice, s), "backward scene table upload")) ||
+        (rc = check_cuda(c, cudaEventRecord(c->bwd_uploaded, s), "backward table event")))
+        return rc;
+    Counters *dc = (Counters *)c->counters.p;
+    if ((rc = check_cuda(c, cudaMemsetAsync(c->grec.p, 0, nn * sizeof(GradRec), s), "memset gradient records")) ||
+        (rc = check_cuda(c, cudaMemsetAsync(&dc->bwd_queue, 0, sizeof(unsigned int), s), "memset queue")))
+        return rc;
+    if (plane_grads &&
+        (rc = check_cuda(c, cudaMemsetAsync(plane_grads, 0, sizeof(float) * 4 * (size_t)c->num_views, s),
+                         "memset plane gradients")))
+        return rc;
+    cudaEventRecord(c->bev[0], s);
+    RenderBwdArgs ra;
+    ra.ranges = (const int2 *)c->ranges.p;
+    ra.tile_order = (const uint32_t *)c->items.p;
+    ra.vals_a = (const uint32_t *)c->pvals.p;
+    ra.vals_b = (const uint32_t *)c->pvals_b.p;
+    ra.rec = (const SplatRec *)c->rec.p;
+    ra.cut = (const CutRec *)c->cut.p;
+    ra.views = (const ViewDev *)c->views_d.p;
+    ra.bviews = (const BwdView *)c->bviews_d.p;
+    ra.num_views = c->num_views;
+    ra.grec = (GradRec *)c->grec.p;
+    ra.counters = dc;
+    const long long slots = (long long)c->sm_count * c->bpsm_render_bwd;
+    const long long items = 4ll * c->num_tiles;
+    launch_render_bwd(ra, (int)(items < slots ? items : slots), s);
+    if ((rc = launched(c, "render backward launch", c->num_tiles > 0))) return rc;
+    cudaEventRecord(c->bev[1], s);
+    PreprocessBwdArgs pa;
+    pa.scenes = (const SceneDev *)c->scenes_d.p;
+    pa.num_scenes = c->num_scenes;
+    pa.views = (const ViewDev *)c->views_d.p;
+    pa.bviews = (const BwdView *)c->bviews_d.p;
+    pa.bscenes = (const BwdScene *)c->bscenes_d.p;
+    pa.labels = (const uint8_t *)c->labels.p;
+    pa.tiles = (const uint32_t *)c->tiles.p;
+    pa.grec = (const GradRec *)c->grec.p;
+    if (launch_preprocess_bwd(pa, (int)c->num_units, max_degree, s))
+        return fail(c, RARA_ERR_CUDA, "preprocess backward: shared-memory size not accepted");
+    if ((rc = launched(c, "preprocess backward launch", c->num_units > 0))) return rc;
+    // Gaussians of scenes without views get zero gradients
+    for (int si = 0; si < c->num_scenes; ++si) {
+        const SceneDev &sd = c->h_scenes[si];
+        if (sd.view_count > 0 || sd.n == 0) continue;
+        const rara_gaussian_grads &g = grads[si];
+        const size_t n = (size_t)sd.n, K = (size_t)(sd.sh_degree + 1) * (sd.sh_degree + 1);
+        if ((rc = check_cuda(c, cudaMemsetAsync(g.means, 0, 12 * n, s), "memset gradients")) ||
+            (rc = check_cuda(c, cudaMemsetAsync(g.log_scales, 0, 12 * n, s), "memset gradients")) ||
+            (rc = check_cuda(c, cudaMemsetAsync(g.quats, 0, 16 * n, s), "memset gradients")) ||
+            (rc = check_cuda(c, cudaMemsetAsync(g.opacity_logits, 0, 4 * n, s), "memset gradients")) ||
+            (rc = check_cuda(c, cudaMemsetAsync(g.sh, 0, 12 * K * n, s), "memset gradients")))
+            return rc;
+    }
+    cudaEventRecord(c->bev[2], s);
+    c->last_stream = s;
+    return RARA_OK;
+}
+
+int rara_ctx_backward_ms(rara_ctx *c, float out[2])
+{
+    if (!c || !out) return RARA_ERR_INVALID_ARG;
+    if (!c->bev[0]) return fail(c, RARA_ERR_INVALID_ARG, "no backward timing on this context");
+    int rc = check_cuda(c, cudaEventSynchronize(c->bev[2]), "event wait");
+    if (rc) return rc;
+    for (int k = 0; k < 2; ++k)
+        if ((rc = check_cuda(c, cudaEventElapsedTime(&out[k], c->bev[k], c->bev[k + 1]), "event elapsed time")))
+            return rc;
     return RARA_OK;
 }
 

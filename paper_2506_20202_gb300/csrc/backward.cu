@@ -1,0 +1,568 @@
+// Backward of the clipped render: dL/dimage -> gradients of the Gaussians' parameters
+// (means, log-scales, quaternions, opacity logits, SH coefficients) and of every view's
+// clip plane (n, d). The paper renders only; this differentiates the forward exactly as
+// the forward kernels compute it, in two launches:
+//
+// Render backward (per tile, the reverse of Eq. 2): every pixel starts from its final
+// transmittance and the list position of its last blended entry (both written by the
+// forward) and walks its tile's list back to front. Entry alphas are re-evaluated with the
+// forward's own functions, so the set of blended entries is the forward's; the
+// transmittance before an entry is recovered as T / (1 - alpha), and the colour composited
+// behind it as a running sum, giving
+//   dC/dalpha_j = T_j (c_j - B_j) - T_final bg / (1 - alpha_j)
+//   B_{j-1}     = alpha_j c_j + (1 - alpha_j) B_j
+// Through alpha = min(0.99, o exp(-q/2) w) the pixel's contribution flows to the entry's
+// 2D mean, conic, opacity, colour and, for a cutoff Gaussian whose chord the plane splits,
+// to its ray-tracing record (G, P, m, d_ep) via the weight's closed form
+//   w = 1/2 + s_mid / (2 |h|)   (s_mid = d_ep + m.c, h = sqrt(1 - |c|^2) m.V / |V|).
+// Where w is 0 or 1 (chord on one side of the plane, ray missing or behind) it is constant
+// and passes no gradient; where 0.99 clamps alpha, alpha passes none either. Per entry the
+// warp's pixels are summed with shuffles and one lane adds the sums to the slot's gradient
+// record with vector atomics. Warps skip entries whose q <= 9 support misses their 8x4
+// rectangle, as in the forward.
+//
+// Preprocess backward (per Gaussian, looping over its scene's views like the forward):
+// the slot's gradient record is carried back through the projection (Eq. 9-10: conic ->
+// Sigma2 -> J W R S -> camera-space mean), the SH colour, the sigmoid opacity and the
+// ray-tracing record (G = M^-1 (mu - e), P, m = M^T n, d_ep = n.mu + d) to mu, sigma, R,
+// the opacity logit, the SH coefficients and the plane; the rotation's gradient goes
+// through the quaternion's normalisation once, after the views. Each Gaussian's gradients
+// have one writer (no atomics); each view's plane gradient is a sum over Gaussians
+// (warp sums + atomics).
+#include "rara_internal.cuh"
+#include "render_common.cuh"
+#include "sh.cuh"
+
+namespace rara {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Gradient of the decay weight where the plane splits the chord (0 < w < 1); returns false
+// (no gradient) where w is constant. The arithmetic repeats rara_weight's. Inputs: the
+// cutoff record c0..c3, the pixel offset (dx, dy) and gw = dL/dw; outputs dL/dG, dL/dp
+// (p = P (dx, dy)), dL/dm, dL/dd_ep.
+__device__ __forceinline__ bool rara_weight_grad(const float4 c0, const float4 c1, const float4 c2, const float4 c3,
+                                                 float dx, float dy, float gw, float gG[3], float gp[3], float gm[3],
+                                                 float &gdep)
+{
+    const float p[3] = {fmaf(c1.x, dx, c2.x * dy), fmaf(c1.y, dx, c2.y * dy), fmaf(c1.z, dx, c2.z * dy)};
+    const float V[3] = {c0.x + p[0], c0.y + p[1], c0.z + p[2]};
+    const float m[3] = {c1.w, c2.w, c3.x};
+    const float VV = fmaf(V[0], V[0], fmaf(V[1], V[1], V[2] * V[2]));
+    const float pV = fmaf(p[0], V[0], fmaf(p[1], V[1], p[2] * V[2]));
+    const float f = __fdividef(pV, VV);
+    const float c[3] = {fmaf(-f, V[0], p[0]), fmaf(-f, V[1], p[1]), fmaf(-f, V[2], p[2])};
+    const float cc = fmaf(c[0], c[0], fmaf(c[1], c[1], c[2] * c[2]));
+    if (cc >= 1.0f) return false;
+    const float h2 = 1.0f - cc;
+    const float GV = fmaf(c0.x, V[0], fmaf(c0.y, V[1], c0.z * V[2]));
+    if (!(GV > 0.0f && GV * GV > h2 * VV)) return false;
+    const float mc = fmaf(m[0], c[0], fmaf(m[1], c[1], m[2] * c[2]));
+    const float mV = fmaf(m[0], V[0], fmaf(m[1], V[1], m[2] * V[2]));
+    const float smid = c0.w + mc;
+    const float half = __fmul_rn(sqrtf(h2) * mV, rsqrtf(VV));
+    const float s1 = smid - half, s2 = smid + half;
+    if ((s1 >= 0.0f) == (s2 >= 0.0f)) return false;
+    // w = 1/2 + smid / (2 H), H = |half| = sqrt(h2) |mV| / |V|
+    const float Hh = fabsf(half);
+    const float g_smid = gw / (2.0f * Hh);
+    const float g_H = -gw * smid / (2.0f * Hh * Hh);
+    const float H_h2 = Hh / h2, H_mV = Hh / mV, H_VV = Hh / VV;
+    float gc[3], gV[3];
+    float gcV = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        gc[k] = g_smid * m[k] - g_H * H_h2 * c[k];
+        gm[k] = g_smid * c[k] + g_H * H_mV * V[k];
+        gV[k] = g_H * (H_mV * m[k] - H_VV * V[k]);
+        gcV = fmaf(gc[k], V[k], gcV);
+    }
+    gdep = g_smid;
+    // c = p - (p.V / V.V) V with V = G + p
+    const float gv = gcV / VV;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float gVt = gV[k] - gv * p[k] - f * gc[k] + 2.0f * f * gv * V[k];
+        gG[k] = gVt;
+        gp[k] = gc[k] - gv * V[k] + gVt;
+    }
+    return true;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// One 16x16 tile, one thread per pixel (warp rectangles of 8x4 pixels).
+__device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &vw, const BwdView &bv,
+                                         const uint32_t *pair_vals, Stage &st, uint32_t *s_slot, int *s_max,
+                                         int gtile, int tile)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int W = vw.cam.W, H = vw.cam.H;
+    const int tx = tile % vw.tiles_x, ty0 = tile / vw.tiles_x;
+    const int wx0 = (warp & 1) * 8, wy0 = (warp >> 1) * 4;
+    const int px = tx * kTile + wx0 + (lane & 7), py = ty0 * kTile + wy0 + (lane >> 3);
+    const bool inside = px < W && py < H;
+    const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
+    const float rx0 = (float)(tx * kTile + wx0) + 0.5f, rx1 = rx0 + 7.0f;
+    const float ry0 = (float)(ty0 * kTile + wy0) + 0.5f, ry1 = ry0 + 3.0f;
+    const int2 range = a.ranges[gtile];
+
+    float T = 1.0f, dC0 = 0.0f, dC1 = 0.0f, dC2 = 0.0f;
+    uint32_t last = 0;
+    if (inside) {
+        const size_t p = (size_t)py * W + px, plane = (size_t)W * H;
+        T = vw.final_T[p];
+        last = vw.n_contrib[p];
+        dC0 = bv.dimage[p];
+        dC1 = bv.dimage[plane + p];
+        dC2 = bv.dimage[2 * plane + p];
+    }
+    const float Tfin = T;
+    const float bgdot = vw.bg[0] * dC0 + vw.bg[1] * dC1 + vw.bg[2] * dC2;
+    float B0 = 0.0f, B1 = 0.0f, B2 = 0.0f;  // colour composited behind the current entry
+    const uint32_t wlast = __reduce_max_sync(kFull, last);
+    if (threadIdx.x == 0) *s_max = 0;
+    __syncthreads();
+    if (lane == 0 && wlast) atomicMax(s_max, (int)wlast);
+    __syncthreads();
+    const int end = range.x + *s_max;
+
+    for (int bend = end; bend > range.x; bend -= kBlock) {
+        const int bbeg = max(range.x, bend - kBlock);
+        const int cnt = bend - bbeg;
+        __syncthreads();  // the previous batch has been consumed
+        if ((int)threadIdx.x < cnt) {
+            const uint32_t g = __ldg(&pair_vals[bbeg + threadIdx.x]);
+            const SplatRec rec = a.rec[g];
+            st.r0[threadIdx.x] = rec.r0;
+            st.r1[threadIdx.x] = rec.r1;
+            st.r2[threadIdx.x] = rec.r2;
+            if (rec.r2.y != 0.0f) {
+                const CutRec c = a.cut[g];
+                st.c0[threadIdx.x] = c.c0;
+                st.c1[threadIdx.x] = c.c1;
+                st.c2[threadIdx.x] = c.c2;
+                st.c3[threadIdx.x] = c.c3;
+            }
+            s_slot[threadIdx.x] = g;
+        }
+        __syncthreads();
+        for (int hi = cnt; hi > 0; hi -= 32) {
+            const int lo = max(0, hi - 32);
+            const int jt = lo + lane;
+            bool keep = false;
+            if (jt < hi && (uint32_t)(bbeg - range.x + jt) < wlast) {
+                const float4 t0 = st.r0[jt];
+                const float4 t2 = st.r2[jt];
+                keep = box_min_q(rx0 - t0.x, rx1 - t0.x, ry0 - t0.y, ry1 - t0.y, t0.z, t0.w, st.r1[jt].x, t2.z,
+                                 t2.w) <= kCullQ;
+            }
+            unsigned m = __ballot_sync(kFull, keep);
+            while (m) {
+                const int b = 31 - __clz(m);
+                m &= ~(1u << b);
+                const int j = lo + b;
+                const uint32_t pos = (uint32_t)(bbeg - range.x + j);
+                const float4 r0 = st.r0[j], r1 = st.r1[j], r2 = st.r2[j];
+                const bool cut = r2.y != 0.0f;
+                bool contrib = false;
+                float gmx = 0.f, gmy = 0.f, gCa = 0.f, gCb = 0.f, gCc = 0.f, gop = 0.f;
+                float gr = 0.f, gg = 0.f, gb = 0.f;
+                float gdep = 0.f, gG[3] = {0.f, 0.f, 0.f}, gPx[3] = {0.f, 0.f, 0.f}, gPy[3] = {0.f, 0.f, 0.f};
+                float gm[3] = {0.f, 0.f, 0.f};
+                if (inside && pos < last) {
+                    const float dx = pxf - r0.x, dy = pyf - r0.y;
+                    const float q = splat_q(r0.z, r0.w, r1.x, dx, dy);
+                    if (q <= kSupportQ) {
+                        const float ex = __expf(-0.5f * q);
+                        const float a0 = r1.y * ex;
+                        if (a0 >= kAlphaMin) {
+                            float w = 1.0f;
+                            if (cut) w = rara_weight(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
+                            const float au = a0 * w;
+                            const float alpha = fminf(kAlphaMax, au);
+                            if (alpha >= kAlphaMin) {
+                                contrib = true;
+                                const float oma = 1.0f - alpha;
+                                const float Tj = T / oma;
+                                const float wgt = alpha * Tj;
+                                gr = dC0 * wgt;
+                                gg = dC1 * wgt;
+                                gb = dC2 * wgt;
+                                float ga = Tj * (dC0 * (r1.z - B0) + dC1 * (r1.w - B1) + dC2 * (r2.x - B2)) -
+                                           Tfin * bgdot / oma;
+                                B0 = fmaf(alpha, r1.z, oma * B0);
+                                B1 = fmaf(alpha, r1.w, oma * B1);
+                                B2 = fmaf(alpha, r2.x, oma * B2);
+                                T = Tj;
+                                if (au > kAlphaMax) ga = 0.0f;  // clamped at 0.99
+                                const float ga0 = ga * w;
+                                gop = ga0 * ex;
+                                const float gq = -0.5f * ga0 * a0;
+                                gCa = gq * dx * dx;
+                                gCb = 2.0f * gq * dx * dy;
+                                gCc = gq * dy * dy;
+                                float gdx = 2.0f * gq * fmaf(r0.z, dx, r0.w * dy);
+                                float gdy = 2.0f * gq * fmaf(r0.w, dx, r1.x * dy);
+                                if (cut) {
+                                    const float4 c1 = st.c1[j], c2 = st.c2[j];
+                                    float gp[3];
+                                    if (rara_weight_grad(st.c0[j], c1, c2, st.c3[j], dx, dy, ga * a0, gG, gp, gm,
+                                                         gdep)) {
+#pragma unroll
+                                        for (int k = 0; k < 3; ++k) {
+                                            gPx[k] = gp[k] * dx;
+                                            gPy[k] = gp[k] * dy;
+                                        }
+                                        gdx += gp[0] * c1.x + gp[1] * c1.y + gp[2] * c1.z;
+                                        gdy += gp[0] * c2.x + gp[1] * c2.y + gp[2] * c2.z;
+                                    }
+                                }
+                                gmx = -gdx;
+                                gmy = -gdy;
+                            }
+                        }
+                    }
+                }
+                const unsigned who = __ballot_sync(kFull, contrib);
+                if (!who) continue;
+                GradRec *dst = &a.grec[s_slot[j]];
+                bool writer = contrib;
+                if (__popc(who) > 1) {  // sum the warp's pixels; lane 0 writes
+                    gmx = warp_sum(gmx); gmy = warp_sum(gmy); gCa = warp_sum(gCa); gCb = warp_sum(gCb);
+                    gCc = warp_sum(gCc); gop = warp_sum(gop); gr = warp_sum(gr); gg = warp_sum(gg);
+                    gb = warp_sum(gb);
+                    if (cut) {
+                        gdep = warp_sum(gdep);
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            gG[k] = warp_sum(gG[k]);
+                            gPx[k] = warp_sum(gPx[k]);
+                            gPy[k] = warp_sum(gPy[k]);
+                            gm[k] = warp_sum(gm[k]);
+                        }
+                    }
+                    writer = lane == 0;
+                }
+                if (writer) {
+                    atomicAdd(&dst->g0, make_float4(gmx, gmy, gCa, gCb));
+                    atomicAdd(&dst->g1, make_float4(gCc, gop, gr, gg));
+                    if (cut) {
+                        atomicAdd(&dst->g2, make_float4(gb, gdep, gm[0], gm[1]));
+                        atomicAdd(&dst->g3, make_float4(gm[2], gG[0], gG[1], gG[2]));
+                        atomicAdd(&dst->g4, make_float4(gPx[0], gPx[1], gPx[2], gPy[0]));
+                        atomicAdd(reinterpret_cast<float2 *>(&dst->g5), make_float2(gPy[1], gPy[2]));
+                    } else {
+                        atomicAdd(&dst->g2.x, gb);
+                    }
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock, 2) k_render_bwd(RenderBwdArgs a)
+{
+    __shared__ Stage st;
+    __shared__ uint32_t s_slot[kBlock];
+    __shared__ unsigned s_item;
+    __shared__ int s_max;
+    const unsigned num_items = *(volatile unsigned *)&a.counters->num_items;
+    const uint32_t *pair_vals = a.counters->tile_in_b ? a.vals_b : a.vals_a;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned q = atomicAdd(&a.counters->bwd_queue, 1u);
+            s_item = q < num_items ? a.tile_order[q] : 0xffffffffu;
+        }
+        __syncthreads();
+        const unsigned item = s_item;
+        if (item == 0xffffffffu) break;
+        if ((item & 3u) == 0u) {  // part 0 of a split tile does the whole tile
+            const int gtile = (int)(item >> 4);
+            int lo = 0, hi = a.num_views - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.views[mid].tile_base <= (uint32_t)gtile) lo = mid;
+                else hi = mid - 1;
+            }
+            const ViewDev &vw = a.views[lo];
+            tile_bwd(a, vw, a.bviews[lo], pair_vals, st, s_slot, &s_max, gtile, gtile - (int)vw.tile_base);
+        }
+        __syncthreads();  // everyone has read s_item and the staged batch
+    }
+}
+
+// Per-Gaussian backward over the scene's views. Dynamic shared memory: the block's SH
+// coefficient gradients, [3 (degree+1)^2][kBlock].
+__global__ void __launch_bounds__(kBlock, 2) k_preprocess_bwd(PreprocessBwdArgs a)
+{
+    extern __shared__ float s_gsh[];
+    const int unit = blockIdx.x;
+    int si = 0;
+    while (si + 1 < a.num_scenes && (int)a.scenes[si + 1].unit_begin <= unit) ++si;
+    const SceneDev &sc = a.scenes[si];
+    const BwdScene &bs = a.bscenes[si];
+    const int n = sc.n;
+    const int i = (unit - (int)sc.unit_begin) * kBlock + threadIdx.x;
+    const bool valid = i < n;
+    const int K = sh_count(sc.sh_degree);
+    for (int k = 0; k < 3 * K; ++k) s_gsh[k * kBlock + threadIdx.x] = 0.0f;
+
+    float mu[3] = {0.f, 0.f, 0.f}, sg[3] = {1.f, 1.f, 1.f}, logit = 0.f;
+    float qv[4] = {1.f, 0.f, 0.f, 0.f}, qinv = 1.0f;
+    float Rg[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    if (valid) {
+        mu[0] = __ldg(&sc.means[i]); mu[1] = __ldg(&sc.means[n + i]); mu[2] = __ldg(&sc.means[2 * n + i]);
+        sg[0] = expf(__ldg(&sc.log_scales[i]));
+        sg[1] = expf(__ldg(&sc.log_scales[n + i]));
+        sg[2] = expf(__ldg(&sc.log_scales[2 * n + i]));
+        logit = __ldg(&sc.logits[i]);
+        float qw = __ldg(&sc.quats[i]), qx = __ldg(&sc.quats[n + i]);
+        float qy = __ldg(&sc.quats[2 * n + i]), qz = __ldg(&sc.quats[3 * n + i]);
+        qinv = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        qw *= qinv; qx *= qinv; qy *= qinv; qz *= qinv;
+        qv[0] = qw; qv[1] = qx; qv[2] = qy; qv[3] = qz;
+        Rg[0] = 1.f - 2.f * (qy * qy + qz * qz); Rg[1] = 2.f * (qx * qy - qw * qz); Rg[2] = 2.f * (qx * qz + qw * qy);
+        Rg[3] = 2.f * (qx * qy + qw * qz); Rg[4] = 1.f - 2.f * (qx * qx + qz * qz); Rg[5] = 2.f * (qy * qz - qw * qx);
+        Rg[6] = 2.f * (qx * qz - qw * qy); Rg[7] = 2.f * (qy * qz + qw * qx); Rg[8] = 1.f - 2.f * (qx * qx + qy * qy);
+    }
+    float gmu[3] = {0.f, 0.f, 0.f}, gsg[3] = {0.f, 0.f, 0.f}, gR[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float gopacity = 0.f;
+
+    for (int v = sc.view_begin; v < sc.view_begin + sc.view_count; ++v) {
+        const ViewDev &vw = a.views[v];
+        const CamDev &cam = vw.cam;
+        const PlaneDev &pl = vw.plane;
+        float gpn[4] = {0.f, 0.f, 0.f, 0.f};
+        bool has_plane = false;
+        const uint32_t slot = vw.slot_base + (uint32_t)i;
+        if (valid && a.tiles[slot] != 0u) {
+            const GradRec &grc = a.grec[slot];
+            const float4 g0 = grc.g0, g1 = grc.g1;
+            const bool cutoff = a.labels[slot] == RARA_CUTOFF;
+            const float4 g2 = grc.g2;  // (rgb.b, then zeros unless cutoff)
+            // ---- projection, as in the forward
+            const float tx = fmaf(cam.R[0], mu[0], fmaf(cam.R[1], mu[1], fmaf(cam.R[2], mu[2], cam.t[0])));
+            const float ty = fmaf(cam.R[3], mu[0], fmaf(cam.R[4], mu[1], fmaf(cam.R[5], mu[2], cam.t[1])));
+            const float tz = fmaf(cam.R[6], mu[0], fmaf(cam.R[7], mu[1], fmaf(cam.R[8], mu[2], cam.t[2])));
+            const float itz = 1.0f / tz;
+            const float limx = 1.3f * (0.5f * cam.W / cam.fx), limy = 1.3f * (0.5f * cam.H / cam.fy);
+            const float vx = tx * itz, vy = ty * itz;
+            const float txz = fminf(limx, fmaxf(-limx, vx));
+            const float tyz = fminf(limy, fmaxf(-limy, vy));
+            const float J00 = cam.fx * itz, J02 = -cam.fx * txz * itz;
+            const float J11 = cam.fy * itz, J12 = -cam.fy * tyz * itz;
+            float T0[3], T1[3], u0[3], u1[3], A0[3], A1[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                T0[k] = fmaf(J00, cam.R[k], J02 * cam.R[6 + k]);
+                T1[k] = fmaf(J11, cam.R[3 + k], J12 * cam.R[6 + k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                u0[k] = T0[0] * Rg[k] + T0[1] * Rg[3 + k] + T0[2] * Rg[6 + k];
+                u1[k] = T1[0] * Rg[k] + T1[1] * Rg[3 + k] + T1[2] * Rg[6 + k];
+                A0[k] = u0[k] * sg[k];
+                A1[k] = u1[k] * sg[k];
+            }
+            const float a0 = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2];
+            const float b0 = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
+            const float c0 = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2];
+            const float x0 = A0[1] * A1[2] - A0[2] * A1[1];
+            const float x1 = A0[2] * A1[0] - A0[0] * A1[2];
+            const float x2 = A0[0] * A1[1] - A0[1] * A1[0];
+            const float ca = a0 + kDilation, cb = b0, cc = c0 + kDilation;
+            const float det = (x0 * x0 + x1 * x1 + x2 * x2) + kDilation * (a0 + c0) + kDilation * kDilation;
+            const float idet = 1.0f / det;
+            // ---- conic (Ka, Kb, Kc) = (cc, -cb, ca) / det is the inverse of Sigma2:
+            // dL/dSigma2 = -K G K with G = [[gKa, gKb / 2], [gKb / 2, gKc]]
+            const float Ka = cc * idet, Kb = -cb * idet, Kc = ca * idet;
+            const float gKa = g0.z, gKb = 0.5f * g0.w, gKc = g1.x;
+            const float P00 = Ka * gKa + Kb * gKb, P01 = Ka * gKb + Kb * gKc;
+            const float P10 = Kb * gKa + Kc * gKb, P11 = Kb * gKb + Kc * gKc;
+            const float g_ca = -(P00 * Ka + P01 * Kb);
+            const float g_cb = -2.0f * (P00 * Kb + P01 * Kc);
+            const float g_cc = -(P10 * Kb + P11 * Kc);
+            // ---- Sigma2 = A A^T + 0.3 I, A = (J W) R S
+            float gT0[3] = {0.f, 0.f, 0.f}, gT1[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float gA0 = 2.0f * g_ca * A0[k] + g_cb * A1[k];
+                const float gA1 = 2.0f * g_cc * A1[k] + g_cb * A0[k];
+                gsg[k] += gA0 * u0[k] + gA1 * u1[k];
+                const float s0 = gA0 * sg[k], s1 = gA1 * sg[k];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    gR[3 * j + k] += s0 * T0[j] + s1 * T1[j];
+                    gT0[j] += s0 * Rg[3 * j + k];
+                    gT1[j] += s1 * Rg[3 * j + k];
+                }
+            }
+            const float gJ00 = gT0[0] * cam.R[0] + gT0[1] * cam.R[1] + gT0[2] * cam.R[2];
+            const float gJ02 = gT0[0] * cam.R[6] + gT0[1] * cam.R[7] + gT0[2] * cam.R[8];
+            const float gJ11 = gT1[0] * cam.R[3] + gT1[1] * cam.R[4] + gT1[2] * cam.R[5];
+            const float gJ12 = gT1[0] * cam.R[6] + gT1[1] * cam.R[7] + gT1[2] * cam.R[8];
+            // ---- J(t) with clamped x/z, y/z, and the 2D mean fx x/z + cx, fy y/z + cy
+            const float gmx2 = g0.x, gmy2 = g0.y;
+            float g_itz = cam.fx * (gJ00 - gJ02 * txz + gmx2 * tx) + cam.fy * (gJ11 - gJ12 * tyz + gmy2 * ty);
+            float gt[3] = {gmx2 * cam.fx * itz, gmy2 * cam.fy * itz, 0.0f};
+            if (vx > -limx && vx < limx) {
+                const float gv = -gJ02 * cam.fx * itz;
+                gt[0] += gv * itz;
+                g_itz += gv * tx;
+            }
+            if (vy > -limy && vy < limy) {
+                const float gv = -gJ12 * cam.fy * itz;
+                gt[1] += gv * itz;
+                g_itz += gv * ty;
+            }
+            gt[2] = -g_itz * itz * itz;
+            // ---- opacity
+            gopacity += g1.y;
+            // ---- colour at normalize(mu - e)
+            const float e[3] = {mu[0] - cam.eye[0], mu[1] - cam.eye[1], mu[2] - cam.eye[2]};
+            const float il = rsqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+            const float dir[3] = {e[0] * il, e[1] * il, e[2] * il};
+            {
+                float basis[16];
+                sh_basis(sc.sh_degree, dir[0], dir[1], dir[2], basis);
+                float grgb[3] = {g1.z, g1.w, g2.x};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        if (k < K) acc = fmaf(__ldg(&sc.sh[(size_t)(k * 3 + c) * n + i]), basis[k], acc);
+                    if (!(acc + 0.5f > 0.0f)) grgb[c] = 0.0f;  // clamped at 0
+                }
+                float s[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    s[k] = 0.0f;
+                    if (k < K) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            s[k] = fmaf(grgb[c], __ldg(&sc.sh[(size_t)(k * 3 + c) * n + i]), s[k]);
+                            s_gsh[(k * 3 + c) * kBlock + threadIdx.x] += grgb[c] * basis[k];
+                        }
+                    }
+                }
+                float gdir[3];
+                sh_basis_vjp(sc.sh_degree, dir[0], dir[1], dir[2], s, gdir);
+                const float dd = gdir[0] * dir[0] + gdir[1] * dir[1] + gdir[2] * dir[2];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) gmu[j] += (gdir[j] - dd * dir[j]) * il;
+            }
+            // ---- ray-tracing record of a cutoff Gaussian
+            if (cutoff) {
+                const float4 g3 = grc.g3, g4 = grc.g4, g5 = grc.g5;
+                const float gG[3] = {g3.y, g3.z, g3.w};
+                const float gPx[3] = {g4.x, g4.y, g4.z};
+                const float gPy[3] = {g4.w, g5.x, g5.y};
+                const float gm[3] = {g2.z, g2.w, g3.x};
+                const float gdep = g2.y;
+                const float kk = pl.k;
+                const float sx = tz / cam.fx, sy = tz / cam.fy;
+                float gtz_p = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float rk0 = Rg[k], rk1 = Rg[3 + k], rk2 = Rg[6 + k];
+                    const float iks = 1.0f / (kk * sg[k]);
+                    const float G = iks * (rk0 * e[0] + rk1 * e[1] + rk2 * e[2]);
+                    const float Px = iks * sx * (rk0 * cam.R[0] + rk1 * cam.R[1] + rk2 * cam.R[2]);
+                    const float Py = iks * sy * (rk0 * cam.R[3] + rk1 * cam.R[4] + rk2 * cam.R[5]);
+                    const float m = kk * sg[k] * (rk0 * pl.n[0] + rk1 * pl.n[1] + rk2 * pl.n[2]);
+                    gsg[k] += (-gG[k] * G - gPx[k] * Px - gPy[k] * Py + gm[k] * m) / sg[k];
+                    gtz_p += gPx[k] * Px + gPy[k] * Py;
+                    const float aG = iks * gG[k], aPx = iks * sx * gPx[k], aPy = iks * sy * gPy[k];
+                    const float am = kk * sg[k] * gm[k];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        gR[3 * j + k] += aG * e[j] + aPx * cam.R[j] + aPy * cam.R[3 + j] + am * pl.n[j];
+                        gmu[j] += aG * Rg[3 * j + k];
+                        gpn[j] += am * Rg[3 * j + k];
+                    }
+                }
+                gt[2] += gtz_p * itz;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    gmu[j] += gdep * pl.n[j];
+                    gpn[j] += gdep * mu[j];
+                }
+                gpn[3] = gdep;
+                has_plane = true;
+            }
+            // ---- camera-space mean t = W mu + t0
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gmu[j] += cam.R[j] * gt[0] + cam.R[3 + j] * gt[1] + cam.R[6 + j] * gt[2];
+        }
+        const BwdView &bv = a.bviews[v];
+        if (bv.plane_grad && __any_sync(kFull, has_plane)) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) gpn[j] = warp_sum(gpn[j]);
+            if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (gpn[j] != 0.0f) atomicAdd(&bv.plane_grad[j], gpn[j]);
+            }
+        }
+    }
+    if (!valid) return;
+    // rotation of the normalised quaternion (w, x, y, z), then the normalisation
+    const float w = qv[0], x = qv[1], y = qv[2], z = qv[3];
+    float gq[4];
+    gq[0] = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    gq[1] = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] -
+                   2.f * x * gR[8]);
+    gq[2] = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] -
+                   2.f * y * gR[8]);
+    gq[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] + x * gR[6] +
+                   y * gR[7]);
+    const float qd = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) bs.quats[(size_t)k * n + i] = (gq[k] - qd * qv[k]) * qinv;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        bs.means[(size_t)k * n + i] = gmu[k];
+        bs.log_scales[(size_t)k * n + i] = gsg[k] * sg[k];
+    }
+    const float op = 1.0f / (1.0f + expf(-logit));
+    bs.logits[i] = gopacity * op * (1.0f - op);
+    for (int k = 0; k < 3 * K; ++k) bs.sh[(size_t)k * n + i] = s_gsh[k * kBlock + threadIdx.x];
+}
+
+}  // namespace
+
+int render_bwd_blocks_per_sm()
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_render_bwd, kBlock, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return b;
+}
+
+void launch_render_bwd(const RenderBwdArgs &a, int grid, cudaStream_t s)
+{
+    if (grid > 0) k_render_bwd<<<grid, kBlock, 0, s>>>(a);
+}
+
+int launch_preprocess_bwd(const PreprocessBwdArgs &a, int grid, int max_sh_degree, cudaStream_t s)
+{
+    const int smem = 3 * (max_sh_degree + 1) * (max_sh_degree + 1) * kBlock * (int)sizeof(float);
+    if (grid <= 0) return 0;
+    if (cudaFuncSetAttribute(k_preprocess_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return -1;
+    k_preprocess_bwd<<<grid, kBlock, smem, s>>>(a);
+    return 0;
+}
+
+}  // namespace rara

@@ -9,66 +9,25 @@
 // scan across blocks so the order is deterministic.
 #include "chained_scan.cuh"
 #include "rara_internal.cuh"
+#include "sh.cuh"
 
 namespace rara {
 
 namespace {
 
-// Real spherical harmonics, orthonormal, standard (l, m) basis with positive polynomials:
-// Y_{1,-1} = c1 y, Y_{1,0} = c1 z, Y_{1,1} = c1 x, etc. Coefficient index k = l*l + l + m.
-constexpr float kY00 = 0.28209479177387814f;   // 1 / (2 sqrt(pi))
-constexpr float kY1 = 0.48860251190291992f;    // sqrt(3 / (4 pi))
-constexpr float kY2a = 1.0925484305920792f;    // (1/2) sqrt(15 / pi)
-constexpr float kY20 = 0.31539156525252005f;   // (1/4) sqrt(5 / pi)
-constexpr float kY22 = 0.54627421529603959f;   // (1/4) sqrt(15 / pi)
-constexpr float kY33 = 0.59004358992664352f;   // (1/4) sqrt(35 / (2 pi))
-constexpr float kY32 = 2.8906114426405538f;    // (1/2) sqrt(105 / pi)
-constexpr float kY31 = 0.45704579946446572f;   // (1/4) sqrt(21 / (2 pi))
-constexpr float kY30 = 0.37317633259011540f;   // (1/4) sqrt(7 / pi)
-constexpr float kY32b = 1.4453057213202769f;   // (1/4) sqrt(105 / pi)
-
-__device__ __forceinline__ float shc(const float *__restrict__ sh, int n, int i, int k, int c)
-{
-    return __ldg(&sh[(size_t)(k * 3 + c) * n + i]);
-}
-
-__device__ void sh_colour(const float *__restrict__ sh, int n, int i, int degree, float x, float y,
-                          float z, float rgb[3])
+// Colour of Gaussian i along the unit direction (x, y, z): sum_k sh_k Y_k + 0.5, clamped at 0.
+__device__ void sh_colour(const float *__restrict__ sh, int n, int i, int degree, float x, float y, float z,
+                          float rgb[3])
 {
     float basis[16];
-    basis[0] = kY00;
-    int kmax = 1;
-    if (degree >= 1) {
-        basis[1] = kY1 * y;
-        basis[2] = kY1 * z;
-        basis[3] = kY1 * x;
-        kmax = 4;
-    }
-    if (degree >= 2) {
-        const float xx = x * x, yy = y * y, zz = z * z;
-        basis[4] = kY2a * x * y;
-        basis[5] = kY2a * y * z;
-        basis[6] = kY20 * (3.0f * zz - 1.0f);
-        basis[7] = kY2a * x * z;
-        basis[8] = kY22 * (xx - yy);
-        kmax = 9;
-        if (degree >= 3) {
-            basis[9] = kY33 * y * (3.0f * xx - yy);
-            basis[10] = kY32 * x * y * z;
-            basis[11] = kY31 * y * (5.0f * zz - 1.0f);
-            basis[12] = kY30 * z * (5.0f * zz - 3.0f);
-            basis[13] = kY31 * x * (5.0f * zz - 1.0f);
-            basis[14] = kY32b * z * (xx - yy);
-            basis[15] = kY33 * x * (xx - 3.0f * yy);
-            kmax = 16;
-        }
-    }
+    sh_basis(degree, x, y, z, basis);
+    const int kmax = sh_count(degree);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         float acc = 0.0f;
 #pragma unroll
         for (int k = 0; k < 16; ++k)
-            if (k < kmax) acc = fmaf(shc(sh, n, i, k, c), basis[k], acc);
+            if (k < kmax) acc = fmaf(__ldg(&sh[(size_t)(k * 3 + c) * n + i]), basis[k], acc);
         rgb[c] = fmaxf(acc + 0.5f, 0.0f);
     }
 }

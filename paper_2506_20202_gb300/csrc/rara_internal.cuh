@@ -116,6 +116,7 @@ struct Counters {
     unsigned int status;
     unsigned int tile_in_b;              // 1 if the tile sort's result is in its B buffers
     unsigned int ticket[13];             // partition tickets of the persistent kernels
+    unsigned int bwd_queue;              // next entry of the item order (render backward)
 };
 constexpr size_t kRenderCounterBytes = 4 * sizeof(unsigned long long) + sizeof(unsigned int);
 // ticket slots
@@ -207,6 +208,56 @@ struct RenderArgs {
 };
 void launch_render(const RenderArgs &a, int grid, cudaStream_t s);
 int render_blocks_per_sm();
+
+// Backward. Per-slot gradient record, 6 x float4 = 96 bytes, accumulated (atomics) by the
+// render backward and read by the preprocess backward:
+//   g0 = (dL/dmean2d.x, dL/dmean2d.y, dL/dconic.a, dL/dconic.b)
+//   g1 = (dL/dconic.c, dL/dopacity, dL/drgb.r, dL/drgb.g)
+//   g2 = (dL/drgb.b, dL/dd_ep, dL/dm.x, dL/dm.y)
+//   g3 = (dL/dm.z, dL/dG.x, dL/dG.y, dL/dG.z)
+//   g4 = (dL/dP00, dL/dP10, dL/dP20, dL/dP01)
+//   g5 = (dL/dP11, dL/dP21, 0, 0)
+// with the fields of SplatRec / CutRec (conic.b is the off-diagonal entry, which q uses twice).
+struct __align__(16) GradRec {
+    float4 g0, g1, g2, g3, g4, g5;
+};
+
+struct BwdView {
+    const float *dimage;  // dL/dimage [3][H][W]
+    float *plane_grad;    // 4 floats (dL/dn, dL/dd) or null
+};
+
+struct BwdScene {
+    float *means, *log_scales, *quats, *logits, *sh;  // gradients, the scene's layouts
+};
+
+struct RenderBwdArgs {
+    const int2 *ranges;
+    const uint32_t *tile_order;
+    const uint32_t *vals_a, *vals_b;
+    const SplatRec *rec;
+    const CutRec *cut;
+    const ViewDev *views;
+    const BwdView *bviews;
+    int num_views;
+    GradRec *grec;        // [slots], zeroed before
+    Counters *counters;
+};
+void launch_render_bwd(const RenderBwdArgs &a, int grid, cudaStream_t s);
+int render_bwd_blocks_per_sm();
+
+struct PreprocessBwdArgs {
+    const SceneDev *scenes;
+    int num_scenes;
+    const ViewDev *views;
+    const BwdView *bviews;
+    const BwdScene *bscenes;
+    const uint8_t *labels;
+    const uint32_t *tiles;
+    const GradRec *grec;
+};
+// grid = preprocess units; max_sh_degree sizes the per-block SH gradient accumulators.
+int launch_preprocess_bwd(const PreprocessBwdArgs &a, int grid, int max_sh_degree, cudaStream_t s);
 
 // Debug exports of one view
 void launch_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_src, const uint32_t *tiles_src,

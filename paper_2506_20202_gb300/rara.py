@@ -47,6 +47,11 @@ class rara_view(C.Structure):
                 ("image", C.c_void_p), ("final_T", C.c_void_p), ("n_contrib", C.c_void_p)]
 
 
+class rara_gaussian_grads(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
+
+
 class rara_frame_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_rendered", C.c_int64), ("n_cutoff", C.c_int64),
                 ("n_pairs", C.c_int64), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
@@ -74,6 +79,8 @@ SIGNATURES = {
     "rara_render_batch": (C.c_int, [_P, C.POINTER(rara_gaussians), C.c_int32, C.POINTER(rara_view), C.c_int32, _P]),
     "rara_render_batch_graph": (C.c_int, [_P, C.POINTER(rara_gaussians), C.c_int32, C.POINTER(rara_view), C.c_int32,
                                           _P]),
+    "rara_render_backward": (C.c_int, [_P, C.POINTER(C.c_void_p), C.POINTER(rara_gaussian_grads), _P, _P]),
+    "rara_ctx_backward_ms": (C.c_int, [_P, C.POINTER(C.c_float)]),
     "rara_frame_info_get": (C.c_int, [_P, C.c_int32, C.POINTER(rara_frame_info)]),
     "rara_frame_gaussians": (C.c_int, [_P, C.c_int32] + [_P] * 9),
     "rara_frame_pairs": (C.c_int, [_P, C.c_int32] + [_P] * 4),
@@ -144,11 +151,25 @@ class GaussianTensors:
         return GaussianTensors(f(scene.means), f(scene.log_scales), f(scene.quats),
                                f(scene.opacity_logits), f(scene.sh), int(scene.sh_degree))
 
-    def c_struct(self) -> rara_gaussians:
+    def _check(self):
         for t in (self.means, self.log_scales, self.quats, self.opacity_logits, self.sh):
             assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"
+
+    def c_struct(self) -> rara_gaussians:
+        self._check()
         return rara_gaussians(self.means.data_ptr(), self.log_scales.data_ptr(), self.quats.data_ptr(),
                               self.opacity_logits.data_ptr(), self.sh.data_ptr(), self.n, self.sh_degree)
+
+    def grads_struct(self) -> rara_gaussian_grads:
+        """These tensors as the gradient arrays of rara_render_backward."""
+        self._check()
+        return rara_gaussian_grads(self.means.data_ptr(), self.log_scales.data_ptr(), self.quats.data_ptr(),
+                                   self.opacity_logits.data_ptr(), self.sh.data_ptr())
+
+    def empty_like(self) -> "GaussianTensors":
+        import torch
+        return GaussianTensors(*(torch.empty_like(t) for t in (self.means, self.log_scales, self.quats,
+                                                                 self.opacity_logits, self.sh)), self.sh_degree)
 
 
 def camera_struct(cam) -> rara_camera:
@@ -286,6 +307,26 @@ def rara_render_batch_graph(ctx, scenes, views, stream=None):
     _check(ctx, load().rara_render_batch_graph(ctx, sc, len(scenes), vw, len(views), _stream(stream)))
 
 
+def rara_render_backward(ctx, dL_dimages, grads, plane_grads=None, stream=None):
+    """Backward of the last render on ctx. dL_dimages: one [3, H, W] CUDA tensor per view
+    (the forward's view order); grads: one GaussianTensors of gradient buffers per scene
+    (written); plane_grads: [num_views, 4] CUDA tensor (written) or None."""
+    for t in dL_dimages:
+        assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"
+    ptrs = (C.c_void_p * len(dL_dimages))(*[t.data_ptr() for t in dL_dimages])
+    gs = (rara_gaussian_grads * len(grads))(*[g.grads_struct() for g in grads])
+    if plane_grads is not None:
+        assert plane_grads.is_cuda and plane_grads.is_contiguous() and plane_grads.shape[-1] == 4
+    _check(ctx, load().rara_render_backward(ctx, ptrs, gs, _ptr(plane_grads), _stream(stream)))
+
+
+def rara_ctx_backward_ms(ctx):
+    """(render backward, preprocess backward) GPU milliseconds of the last backward."""
+    out = (C.c_float * 2)()
+    _check(ctx, load().rara_ctx_backward_ms(ctx, out))
+    return tuple(float(x) for x in out)
+
+
 def rara_frame_info_get(ctx, view: int = 0) -> dict:
     info = rara_frame_info()
     _check(ctx, load().rara_frame_info_get(ctx, int(view), C.byref(info)))
@@ -311,6 +352,7 @@ class Renderer:
 
     def __init__(self, budget_bytes: int = 0, tuning=None):
         self.ctx = rara_ctx_create(budget_bytes)
+        self.generation = 0      # forwards run through this renderer (see autograd.py)
         if tuning is not None:
             rara_ctx_set_tuning(self.ctx, *tuning)
 
@@ -333,6 +375,7 @@ class Renderer:
                    torch.empty((H, W), dtype=torch.float32, device="cuda"),
                    torch.empty((H, W), dtype=torch.int32, device="cuda"))
         image, T, nc = out
+        self.generation += 1
         rara_render_frame(self.ctx, gaussians, cam, plane, bg, image, T, nc, stream)
         return image, T, nc
 

@@ -162,6 +162,24 @@ def uniform_scene(n: int = 10_000, seed: int = 0, sh_degree: int = 0) -> Scene:
     return Scene(_f32(means), _f32(log_scales), _f32(quats), _f32(logits), _f32(sh), sh_degree)
 
 
+def gradient_scene(n: int = 24, seed: int = 0, sh_degree: int = 1) -> Scene:
+    """Tiny scene for finite-difference gradient checks: centres uniform in [-0.6, 0.6]^3,
+    log-scales N(-1.9, 0.25) (splats of a few pixels at 64 px and distance 3, overlapping
+    about twice), uniform unit quaternions, opacity sigmoid(N(0, 1)), RGB uniform [0, 1]
+    at degree 0 and higher bands N(0, 0.3)."""
+    rng = np.random.default_rng(seed)
+    means = rng.uniform(-0.6, 0.6, size=(3, n))
+    log_scales = rng.normal(-1.9, 0.25, size=(3, n))
+    quats = random_unit_quats(rng, n)
+    logits = rng.normal(0.0, 1.0, size=n)
+    k = (sh_degree + 1) ** 2
+    sh = np.zeros((k * 3, n))
+    sh[0:3] = (rng.uniform(0.0, 1.0, size=(3, n)) - 0.5) / _Y00
+    if sh_degree > 0:
+        sh[3:] = rng.normal(0.0, 0.3, size=((k - 1) * 3, n))
+    return Scene(_f32(means), _f32(log_scales), _f32(quats), _f32(logits), _f32(sh), sh_degree)
+
+
 def _noisy_surface_points(rng, n, radius=0.8):
     """Points on a seeded radially perturbed sphere r(theta, phi) with N(0, 0.01) jitter."""
     v = rng.standard_normal((3, n))
