@@ -48,7 +48,7 @@ FLOP_TEST, FLOP_WALKED, FLOP_EVAL, FLOP_CUT = 36, 9, 12, 60
 SMS, FP32_LANES = 152, 128  # GB300: 152 SMs x 128 FP32 lanes, FMA = 2 FLOP
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "render_fwd_general_1080p.txt")
-RENDER_SRC = os.path.join(ROOT, "paper_2506_20202_gb300", "csrc", "render.cu")
+RENDER_SRCS = [os.path.join(ROOT, "paper_2506_20202_gb300", "csrc", f) for f in ("render.cu", "render_common.cuh")]
 
 
 def parse_args():
@@ -64,9 +64,14 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--plain-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", default="", help="split thresholds 'a,b' instead of autotuning")
     ap.add_argument("--serve-s", type=float, default=4.0, help="serving window (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-3m", action=argparse.BooleanOptionalAction, default=True)
+    ap.add_argument("--train-steps", type=int, default=6, help="forward+backward steps of the multi-layer "
+                    "differentiation workload (0: skip)")
+    ap.add_argument("--train-per-shell", type=int, default=700_000)
+    ap.add_argument("--train-views", type=int, default=64)
     return ap.parse_args()
 
 
@@ -145,18 +150,21 @@ class ClockSampler:
 
 
 def traffic_for_current_kernel():
-    """DRAM bytes per render launch from the committed ncu summary, if it was taken on the
-    current render.cu (matched by hash); otherwise None."""
+    """DRAM bytes of the benchmark's render launch from the committed ncu summary, if it was
+    taken on the current render sources (matched by hash); otherwise None."""
     try:
         text = open(TRAFFIC_FILE).read()
     except OSError:
         return None
-    m = re.search(r"render_cu_sha256:\s*([0-9a-f]{64})", text)
-    b = re.search(r"dram_bytes_per_launch_full_frame:\s*([0-9.eE+]+)", text)
-    if not m or not b:
+    b = re.search(r"dram_bytes_per_bench_launch:\s*([0-9.eE+]+)", text)
+    if not b:
         return None
-    cur = hashlib.sha256(open(RENDER_SRC, "rb").read()).hexdigest()
-    return float(b.group(1)) if m.group(1) == cur else None
+    for path in RENDER_SRCS:
+        key = os.path.basename(path).replace(".", "_") + "_sha256"
+        m = re.search(key + r":\s*([0-9a-f]{64})", text)
+        if not m or m.group(1) != hashlib.sha256(open(path, "rb").read()).hexdigest():
+            return None
+    return float(b.group(1))
 
 
 # --------------------------------------------------------------------------------------
@@ -271,55 +279,57 @@ def run_ours(args):
     nplanes = len(planes)
 
     # ---------------- plain path: one frame per launch sequence --------------------------
-    ctx = rara.rara_ctx_create(0)
-    image = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
-    final_T = torch.empty((H, W), dtype=torch.float32, device="cuda")
-    n_contrib = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    plain, counts = None, None
+    if args.plain_steps > 0:
+        ctx = rara.rara_ctx_create(0)
+        image = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
+        final_T = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        n_contrib = torch.empty((H, W), dtype=torch.int32, device="cuda")
 
-    def frame(pl, evs=None):
-        if evs is not None:
-            evs[0].record(stream)
-        rara.rara_preprocess(ctx, gs, cam, pl, stream)
-        if evs is not None:
-            evs[1].record(stream)
-        rara.rara_bin(ctx, stream)
-        if evs is not None:
-            evs[2].record(stream)
-        rara.rara_render(ctx, bg, image, final_T, n_contrib, stream)
-        if evs is not None:
-            evs[3].record(stream)
+        def frame(pl, evs=None):
+            if evs is not None:
+                evs[0].record(stream)
+            rara.rara_preprocess(ctx, gs, cam, pl, stream)
+            if evs is not None:
+                evs[1].record(stream)
+            rara.rara_bin(ctx, stream)
+            if evs is not None:
+                evs[2].record(stream)
+            rara.rara_render(ctx, bg, image, final_T, n_contrib, stream)
+            if evs is not None:
+                evs[3].record(stream)
 
-    for _ in range(args.warmup):
+        for _ in range(args.warmup):
+            for pl in planes:
+                frame(pl)
+        counts = []
         for pl in planes:
             frame(pl)
-    counts = []
-    for pl in planes:
-        frame(pl)
-        counts.append(rara.rara_frame_info_get(ctx))
-    stream.synchronize()
-    plain_steps = max(3, min(args.steps, args.plain_steps))
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(plain_steps * nplanes)]
-    p_begin, p_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    p_begin.record(stream)
-    k = 0
-    for _ in range(plain_steps):
-        for pl in planes:
-            frame(pl, evs[k])
-            k += 1
-    p_end.record(stream)
-    stream.synchronize()
-    plain_ms = p_begin.elapsed_time(p_end)
-    lat = [e[0].elapsed_time(e[3]) for e in evs]
-    t_pre = [e[0].elapsed_time(e[1]) for e in evs]
-    t_bin = [e[1].elapsed_time(e[2]) for e in evs]
-    t_ren = [e[2].elapsed_time(e[3]) for e in evs]
-    plain = {"frames_per_s": plain_steps * nplanes / (plain_ms / 1e3), "p50_ms": percentile(lat, 50),
-             "p99_ms": percentile(lat, 99), "stage_ms": {"preprocess": statistics.mean(t_pre),
-                                                         "bin": statistics.mean(t_bin),
-                                                         "render": statistics.mean(t_ren)},
-             "note": "per frame: preprocess, bin (one host wait), render on one stream"}
-    rara.rara_ctx_destroy(ctx)
+            counts.append(rara.rara_frame_info_get(ctx))
+        stream.synchronize()
+        plain_steps = max(3, min(args.steps, args.plain_steps))
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(plain_steps * nplanes)]
+        p_begin, p_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        p_begin.record(stream)
+        k = 0
+        for _ in range(plain_steps):
+            for pl in planes:
+                frame(pl, evs[k])
+                k += 1
+        p_end.record(stream)
+        stream.synchronize()
+        plain_ms = p_begin.elapsed_time(p_end)
+        lat = [e[0].elapsed_time(e[3]) for e in evs]
+        t_pre = [e[0].elapsed_time(e[1]) for e in evs]
+        t_bin = [e[1].elapsed_time(e[2]) for e in evs]
+        t_ren = [e[2].elapsed_time(e[3]) for e in evs]
+        plain = {"frames_per_s": plain_steps * nplanes / (plain_ms / 1e3), "p50_ms": percentile(lat, 50),
+                 "p99_ms": percentile(lat, 99), "stage_ms": {"preprocess": statistics.mean(t_pre),
+                                                             "bin": statistics.mean(t_bin),
+                                                             "render": statistics.mean(t_ren)},
+                 "note": "per frame: preprocess, bin (one host wait), render on one stream"}
+        rara.rara_ctx_destroy(ctx)
 
     # ---------------- batched path: the sweep as one batch, CUDA-graph replay ------------
     bctx = rara.rara_ctx_create(0)
@@ -327,11 +337,17 @@ def run_ours(args):
              torch.empty((H, W), dtype=torch.float32, device="cuda"),
              torch.empty((H, W), dtype=torch.int32, device="cuda")) for _ in planes]
     views = [rara.View(0, cam, pl, o[0], o[1], o[2], bg) for pl, o in zip(planes, outs)]
-    best, tune_ms = autotune.autotune(bctx, [gs], views, stream, reps=3)
+    if args.tuning:
+        best, tune_ms = tuple(int(x) for x in args.tuning.split(",")), {}
+        rara.rara_ctx_set_tuning(bctx, *best)
+    else:
+        best, tune_ms = autotune.autotune(bctx, [gs], views, stream, reps=3)
     # stage times and work counts of one exact batched render (for the roofline)
     rara.rara_render_batch(bctx, [gs], views, stream)
     stage = rara.rara_ctx_stage_ms(bctx)
     binfo = rara.rara_frame_info_get(bctx, 0)
+    if counts is None:
+        counts = [rara.rara_frame_info_get(bctx, v) for v in range(nplanes)]
     for _ in range(args.warmup):
         rara.rara_render_batch_graph(bctx, [gs], views, stream)
     rara.rara_ctx_sync(bctx, stream)
@@ -389,47 +405,50 @@ def run_ours(args):
     n = scene.n
     pre_bytes = n * (12 + 12 + 16 + 4 + 4 * scene.sh.shape[0]) + \
         statistics.mean(c["n_rendered"] * (48 + 8 + 8) + n * 9 + c["n_cutoff"] * 64 for c in counts)
-    plain["preprocess_algorithmic_GBps"] = pre_bytes / (plain["stage_ms"]["preprocess"] * 1e-3) / 1e9
-    plain["preprocess_hbm_frac"] = plain["preprocess_algorithmic_GBps"] / peaks["hbm_gbs"]
+    if plain:
+        plain["preprocess_algorithmic_GBps"] = pre_bytes / (plain["stage_ms"]["preprocess"] * 1e-3) / 1e9
+        plain["preprocess_hbm_frac"] = plain["preprocess_algorithmic_GBps"] / peaks["hbm_gbs"]
 
-    # end to end through the C ABI with host buffers (graph path): per step the scene is
-    # uploaded from pinned host memory and every image is read back into pinned host memory
-    host = {k2: torch.from_numpy(np.ascontiguousarray(getattr(scene, k2), np.float32)).pin_memory()
-            for k2 in ("means", "log_scales", "quats", "opacity_logits", "sh")}
-    dev = rara.GaussianTensors(*(torch.empty_like(host[k2], device="cuda") for k2 in
-                                 ("means", "log_scales", "quats", "opacity_logits", "sh")), scene.sh_degree)
-    img_host = [torch.empty((3, H, W), dtype=torch.float32).pin_memory() for _ in planes]
-    h2d = sum(t.numel() * 4 for t in host.values())
-    d2h = nplanes * 3 * H * W * 4
-    ectx = rara.rara_ctx_create(0)
-    rara.rara_ctx_set_tuning(ectx, *best)
+    e2e = None
+    if args.e2e_steps > 0:
+        # end to end through the C ABI with host buffers (graph path): per step the scene is
+        # uploaded from pinned host memory and every image is read back into pinned host memory
+        host = {k2: torch.from_numpy(np.ascontiguousarray(getattr(scene, k2), np.float32)).pin_memory()
+                for k2 in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+        dev = rara.GaussianTensors(*(torch.empty_like(host[k2], device="cuda") for k2 in
+                                     ("means", "log_scales", "quats", "opacity_logits", "sh")), scene.sh_degree)
+        img_host = [torch.empty((3, H, W), dtype=torch.float32).pin_memory() for _ in planes]
+        h2d = sum(t.numel() * 4 for t in host.values())
+        d2h = nplanes * 3 * H * W * 4
+        ectx = rara.rara_ctx_create(0)
+        rara.rara_ctx_set_tuning(ectx, *best)
 
-    def e2e_step():
-        with torch.cuda.stream(stream):
-            for k2 in ("means", "log_scales", "quats", "opacity_logits", "sh"):
-                getattr(dev, k2).copy_(host[k2], non_blocking=True)
-        rara.rara_render_batch_graph(ectx, [dev], views, stream)
-        with torch.cuda.stream(stream):
-            for i in range(nplanes):
-                img_host[i].copy_(outs[i][0], non_blocking=True)
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                for k2 in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+                    getattr(dev, k2).copy_(host[k2], non_blocking=True)
+            rara.rara_render_batch_graph(ectx, [dev], views, stream)
+            with torch.cuda.stream(stream):
+                for i in range(nplanes):
+                    img_host[i].copy_(outs[i][0], non_blocking=True)
 
-    e2e_step()
-    e2e_step()
-    rara.rara_ctx_sync(ectx, stream)
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
         e2e_step()
-    rara.rara_ctx_sync(ectx, stream)
-    e2e_s = time.perf_counter() - t0
-    rara.rara_ctx_destroy(ectx)
-    e2e = {"value": world * args.e2e_steps * nplanes / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "note": "per step: scene upload from pinned host memory + one C-ABI batched render of the 16 sweep "
-                   "frames (graph replay) + read-back of every image into pinned host memory; host wall clock"}
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e["value"] = world * args.e2e_steps * nplanes / float(t.item())
+        e2e_step()
+        rara.rara_ctx_sync(ectx, stream)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        rara.rara_ctx_sync(ectx, stream)
+        e2e_s = time.perf_counter() - t0
+        rara.rara_ctx_destroy(ectx)
+        e2e = {"value": world * args.e2e_steps * nplanes / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "note": "per step: scene upload from pinned host memory + one C-ABI batched render of the 16 sweep "
+                       "frames (graph replay) + read-back of every image into pinned host memory; host wall clock"}
+        if dist:
+            t = torch.tensor([e2e_s], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e["value"] = world * args.e2e_steps * nplanes / float(t.item())
     rara.rara_ctx_destroy(bctx)
 
     line = {
@@ -438,7 +457,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args),
         "paths": {"batched_graph": batched, "plain": plain},
-        "latency_ms": {"plain_p50": plain["p50_ms"], "plain_p99": plain["p99_ms"],
+        "latency_ms": {"plain_p50": plain and plain["p50_ms"], "plain_p99": plain and plain["p99_ms"],
                        "batched_p50": batched["batch_p50_ms"], "batched_p99": batched["batch_p99_ms"]},
         "roofline": roofline, "peak_source": peak_kind,
         "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
@@ -446,6 +465,8 @@ def run_ours(args):
                                                        for c in counts],
                          "pairs_mean": statistics.mean(c["n_pairs"] for c in counts)},
     }
+    if rank == 0 and world == 1 and args.train_steps > 0:
+        line["training"] = run_training(args)
     if rank == 0 and world == 1 and args.serve_s > 0:
         line["serving"] = run_serving(args, gs, scene)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -456,6 +477,122 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+# Algorithmic FP32 work of the render backward per unit, counted from the kernel's
+# arithmetic (the forward's pair counts of the same batch serve as unit counts):
+#   walked pair      dx, dy and q                                           10 FLOP
+#   in-support pair  alpha recomputed, T / (1 - alpha), colour and alpha
+#                    gradients, running colour, q -> conic and mean grads  50 FLOP + 2 MUFU
+#   cutoff pair      decay weight recomputed and its gradient             135 FLOP + 5 MUFU
+FLOP_BWD_WALKED, FLOP_BWD_EVAL, FLOP_BWD_CUT = 10, 50, 135
+
+
+def run_training(args):
+    """Multi-layer differentiation workload: 3 nested shells (3 x 700k Gaussians, SH degree
+    2), 64 views at 512^2 / 1024^2 / 1920x1080 with 64 planes cutting the shells. One step =
+    batched forward (CUDA-graph replay, autotuned) + L2 loss to target renders of a perturbed
+    copy of the scene + rara_render_backward + an Adam update of the Gaussians."""
+    import torch
+
+    from paper_2506_20202_gb300 import autotune, rara, scenes
+    t_setup = time.perf_counter()
+    scene, target, vp = scenes.shells_training_workload(args.train_per_shell, args.train_views, seed=3)
+    gs = rara.GaussianTensors.from_scene(scene)
+    tg = rara.GaussianTensors.from_scene(target)
+    stream = torch.cuda.Stream()
+    ctx = rara.rara_ctx_create(0)
+
+    def make_views():
+        out = []
+        for cam, pl in vp:
+            H, W = cam.height, cam.width
+            out.append(rara.View(0, cam, pl, torch.empty((3, H, W), device="cuda"),
+                                 torch.empty((H, W), device="cuda"),
+                                 torch.empty((H, W), dtype=torch.int32, device="cuda"), (0.0, 0.0, 0.0)))
+        return out
+
+    tviews = make_views()
+    rara.rara_render_batch(ctx, [tg], tviews, stream)
+    rara.rara_ctx_sync(ctx, stream)
+    targets = [v.image for v in tviews]
+    del tg
+    views = make_views()
+    if args.tuning:
+        best, tune_ms = tuple(int(x) for x in args.tuning.split(",")), {}
+        rara.rara_ctx_set_tuning(ctx, *best)
+    else:
+        best, tune_ms = autotune.autotune(ctx, [gs], views, stream, reps=2)
+    grads = gs.empty_like()
+    pg = torch.empty((len(views), 4), device="cuda")
+    dimgs = [torch.empty_like(v.image) for v in views]
+    # Adam on the Gaussians' own storage (nn.Parameter shares it), gradients from the backward
+    params = [torch.nn.Parameter(t) for t in (gs.means, gs.log_scales, gs.quats, gs.opacity_logits, gs.sh)]
+    for p_, g_ in zip(params, (grads.means, grads.log_scales, grads.quats, grads.opacity_logits, grads.sh)):
+        p_.grad = g_
+    opt = torch.optim.Adam(params, lr=1e-3, foreach=True)
+    losses = []
+
+    def step(evs):
+        evs[0].record(stream)
+        rara.rara_render_batch_graph(ctx, [gs], views, stream)
+        evs[1].record(stream)
+        with torch.cuda.stream(stream):
+            loss = torch.zeros((), device="cuda")
+            for v, t, d in zip(views, targets, dimgs):
+                torch.sub(v.image, t, out=d)
+                loss += (d * d).mean()
+                d.mul_(2.0 / d.numel())
+        evs[2].record(stream)
+        rara.rara_render_backward(ctx, dimgs, [grads], pg, stream)
+        evs[3].record(stream)
+        with torch.cuda.stream(stream):
+            opt.step()
+        evs[4].record(stream)
+        return loss
+
+    mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    for _ in range(2):
+        step(mk())
+    rara.rara_ctx_sync(ctx, stream)
+    info = rara.rara_frame_info_get(ctx, 0)
+    setup_s = time.perf_counter() - t_setup
+    evs = [mk() for _ in range(args.train_steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for k in range(args.train_steps):
+        losses.append(step(evs[k]))
+    t1.record(stream)
+    stream.synchronize()
+    rara.rara_ctx_sync(ctx, stream)
+    total_ms = t0.elapsed_time(t1)
+    bwd_ms = rara.rara_ctx_backward_ms(ctx)
+    med = lambda a, b: statistics.median(e[a].elapsed_time(e[b]) for e in evs)
+    pixels = sum(cam.width * cam.height for cam, _ in vp)
+    flop = (FLOP_BWD_WALKED * info["n_walked"] + FLOP_BWD_EVAL * info["n_evaluated"]
+            + FLOP_BWD_CUT * info["n_cut_evaluated"])
+    peak = SMS * FP32_LANES * 2 * 2070.0 * 1e6 / 1e12
+    achieved = flop / (bwd_ms[0] * 1e-3) / 1e12
+    out = {"workload": f"3 nested shells x {args.train_per_shell} Gaussians (SH 2), {len(vp)} views "
+                       f"(512^2 / 1024^2 / 1920x1080), 64 planes cutting the shells, L2 loss to renders of a "
+                       f"perturbed copy", "gaussians": scene.n, "views": len(vp), "pixels_per_step": pixels,
+           "steps": args.train_steps, "ms_per_step": total_ms / args.train_steps,
+           "views_per_s": args.train_steps * len(vp) / (total_ms * 1e-3),
+           "stage_ms_median": {"forward_graph": med(0, 1), "loss_grad": med(1, 2), "backward": med(2, 3),
+                               "adam_update": med(3, 4)},
+           "backward_kernels_ms_last": {"render_backward": bwd_ms[0], "preprocess_backward": bwd_ms[1]},
+           "tuning": list(best), "loss_per_step": [float(x) for x in losses],
+           "render_backward_roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                        "frac": achieved / peak,
+                                        "units": {"walked": info["n_walked"], "evaluated": info["n_evaluated"],
+                                                  "cut_evaluated": info["n_cut_evaluated"]}},
+           "pairs": sum(rara.rara_frame_info_get(ctx, v)["n_pairs"] for v in range(len(vp))),
+           "setup_s": setup_s}
+    rara.rara_ctx_destroy(ctx)
+    del gs, grads, dimgs, targets, tviews, views
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_serving(args, gs_1m, scene_1m):

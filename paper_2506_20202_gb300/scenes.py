@@ -331,3 +331,28 @@ def general_workload(n: int = 1_000_000, width: int = 1920, height: int = 1080, 
     nrm = random_unit_normal(seed + 1)
     planes = [Plane(_f32(nrm), float(d), 3.0, MODE_RARA) for d in sweep_offsets(scene, nrm, sweep)]
     return scene, cam, planes
+
+
+def shells_training_workload(per_shell: int = 700_000, views: int = 64, seed: int = 0,
+                             resolutions=((512, 512), (1024, 1024), (1920, 1080))):
+    """Multi-layer differentiation workload: the 3-shell scene (3 x per_shell Gaussians, SH
+    degree 2), a perturbed copy of it whose renders are the L2 targets (colours N(0, 0.1)
+    and opacity logits N(0, 0.3) added), and `views` seeded views at the resolutions in turn,
+    each a camera on a sphere of radius 3 looking at the centre and a plane with a random
+    unit normal and an offset uniform in [-0.5, 0.5] (cutting through the shells).
+    Returns (scene, target_scene, [(camera, plane)])."""
+    scene = shells_scene(per_shell, seed=seed)
+    rng = np.random.default_rng(seed + 1000)
+    target = Scene(scene.means, scene.log_scales, scene.quats,
+                   _f32(scene.opacity_logits + rng.normal(0.0, 0.3, size=scene.n)),
+                   _f32(scene.sh + rng.normal(0.0, 0.1, size=scene.sh.shape)), scene.sh_degree)
+    out = []
+    for v in range(views):
+        w, h = resolutions[v % len(resolutions)]
+        e = rng.standard_normal(3)
+        e = 3.0 * e / np.linalg.norm(e)
+        nrm = rng.standard_normal(3)
+        nrm /= np.linalg.norm(nrm)
+        out.append((look_at_camera(e, (0.0, 0.0, 0.0), w, h, 60.0),
+                    Plane(_f32(nrm), float(rng.uniform(-0.5, 0.5)), 3.0, MODE_RARA)))
+    return scene, target, out
