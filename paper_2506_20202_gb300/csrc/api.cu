@@ -179,6 +179,7 @@ void occupancy_setup(rara_ctx *c)
     c->bpsm_emit = emit_blocks_per_sm();
     c->bpsm_compact = compact_blocks_per_sm();
     c->bpsm_render_bwd = render_bwd_blocks_per_sm();
+    if (preprocess_configure()) cudaGetLastError();  // a launch that needs it then reports the error
 }
 
 int check_gaussians(rara_ctx *c, const rara_gaussians *g)
@@ -360,7 +361,11 @@ int batch_preprocess(rara_ctx *c, cudaStream_t s)
     a.depth = (float *)c->depth.p;
     a.view_counters = (ViewCounters *)c->view_counters_d.p;
     a.counters = dc;
-    launch_preprocess(a, (int)c->num_units, s);
+    int max_degree = 0;
+    for (int si = 0; si < c->num_scenes; ++si)
+        if (c->h_scenes[si].view_count > 0 && c->h_scenes[si].sh_degree > max_degree)
+            max_degree = c->h_scenes[si].sh_degree;
+    launch_preprocess(a, (int)c->num_units, max_degree, s);
     if ((rc = launched(c, "preprocess launch", c->num_units > 0))) return rc;
 
     CompactArgs ca;

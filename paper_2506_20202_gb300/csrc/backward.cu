@@ -171,7 +171,7 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
                 const int j = lo + b;
                 const uint32_t pos = (uint32_t)(bbeg - range.x + j);
                 const float4 r0 = st.r0[j], r1 = st.r1[j], r2 = st.r2[j];
-                const bool cut = r2.y != 0.0f;
+                const bool cut = r2.y == kWeightSplit;  // the weight varies with the inputs
                 bool contrib = false;
                 float gmx = 0.f, gmy = 0.f, gCa = 0.f, gCb = 0.f, gCc = 0.f, gop = 0.f;
                 float gr = 0.f, gg = 0.f, gb = 0.f;
@@ -185,7 +185,8 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
                         const float a0 = r1.y * ex;
                         if (a0 >= kAlphaMin) {
                             float w = 1.0f;
-                            if (cut) w = rara_weight(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
+                            if (r2.y != kWeightNone)
+                                w = decay_weight(r2.y, st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
                             const float au = a0 * w;
                             const float alpha = fminf(kAlphaMax, au);
                             if (alpha >= kAlphaMin) {

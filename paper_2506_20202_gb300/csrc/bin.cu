@@ -26,9 +26,18 @@ __device__ __forceinline__ int view_of_slot(const ViewDev *views, int num_views,
     return lo;
 }
 
+// Partitions of kEmitItems rows of kBlock depth-ordered slots: thread t takes slot
+// r * kBlock + t of each row r, so in every row adjacent threads emit adjacent slots' pairs
+// (the stores of a warp stay close together), while one chained-scan step serves
+// kBlock * kEmitItems slots. The partition's exclusive prefix is a block scan of the
+// row-major tile counts staged in shared memory.
+constexpr int kEmitItems = 8;
+constexpr uint32_t kEmitPart = kBlock * kEmitItems;
+
 __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
 {
     __shared__ uint32_t s_hist[4][256];
+    __shared__ uint32_t s_cnt[kEmitPart];          // tile counts, then exclusive offsets
     __shared__ unsigned s_part;
     __shared__ unsigned long long s_warp[kBlock / 32];
     __shared__ unsigned long long s_prefix;
@@ -36,7 +45,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t n = (uint32_t)a.counters->n_rendered;
     const uint32_t *vals = a.counters->depth_in_b ? a.vals_b : a.vals_a;
-    const uint32_t parts = (n + kBlock - 1) / kBlock;
+    const uint32_t parts = (n + kEmitPart - 1) / kEmitPart;
     bool overflow = false;
     for (;;) {
         __syncthreads();
@@ -44,14 +53,24 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
         __syncthreads();
         const uint32_t part = s_part;
         if (part >= parts) break;
-        const uint32_t j = part * kBlock + threadIdx.x;
-        uint32_t slot = 0, nt = 0;
-        if (j < n) {
-            slot = vals[j];
-            nt = a.tiles[slot];
+        const uint32_t first = part * kEmitPart + threadIdx.x;
+        uint32_t slot[kEmitItems];
+#pragma unroll
+        for (int r = 0; r < kEmitItems; ++r)
+            slot[r] = first + r * kBlock < n ? __ldg(&vals[first + r * kBlock]) : 0u;
+#pragma unroll
+        for (int r = 0; r < kEmitItems; ++r)
+            s_cnt[r * kBlock + threadIdx.x] = first + r * kBlock < n ? __ldg(&a.tiles[slot[r]]) : 0u;
+        __syncthreads();
+        // thread t scans the kEmitItems consecutive counts [t * kEmitItems, ...)
+        uint32_t c[kEmitItems];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int r = 0; r < kEmitItems; ++r) {
+            c[r] = s_cnt[threadIdx.x * kEmitItems + r];
+            sum += c[r];
         }
-        // block exclusive scan of nt
-        unsigned long long incl = nt;
+        unsigned long long incl = sum;
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += v;
@@ -71,17 +90,29 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
             if (lane == 0) s_prefix = prefix;
         }
         __syncthreads();
-        if (nt) {
-            unsigned long long off = s_prefix + s_warp[warp] + incl - nt;
-            const ViewDev &vw = a.views[view_of_slot(a.views, a.num_views, slot)];
-            const uint2 rc = a.rect[slot];
+        // offsets inside the partition (they fit 32 bits: a partition's pairs are < 2^32)
+        uint32_t run = (uint32_t)(s_warp[warp] + incl - sum);
+#pragma unroll
+        for (int r = 0; r < kEmitItems; ++r) {
+            s_cnt[threadIdx.x * kEmitItems + r] = run;
+            run += c[r];
+        }
+        __syncthreads();
+        const unsigned long long pbase = s_prefix;
+#pragma unroll
+        for (int r = 0; r < kEmitItems; ++r) {
+            if (first + r * kBlock >= n) break;
+            unsigned long long off = pbase + s_cnt[r * kBlock + threadIdx.x];
+            const uint2 rc = a.rect[slot[r]];
             const int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
+            if (x0 > x1 || y0 > y1) continue;
+            const ViewDev &vw = a.views[view_of_slot(a.views, a.num_views, slot[r])];
             for (int y = y0; y <= y1; ++y)
                 for (int x = x0; x <= x1; ++x) {
                     if (off < a.cap_pairs) {
                         const uint32_t t = vw.tile_base + (uint32_t)(y * vw.tiles_x + x);
                         a.pair_keys[off] = t;
-                        a.pair_vals[off] = slot;
+                        a.pair_vals[off] = slot[r];
                         for (int p = 0; p < a.tile_passes; ++p) atomicAdd(&s_hist[p][(t >> (8 * p)) & 0xffu], 1u);
                     } else {
                         overflow = true;

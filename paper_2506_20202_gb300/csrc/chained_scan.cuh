@@ -59,7 +59,10 @@ __device__ __forceinline__ unsigned long long warp_chained_prefix(unsigned long 
         const int idx = end - lane;
         unsigned long long v = idx >= 0 ? ld_relaxed_u64(&lookback[idx]) : kFlagIncl;
         const unsigned long long flag = v & ~kValueMask;
-        if (__any_sync(0xffffffffu, flag == 0)) {
+        const unsigned waiting = __ballot_sync(0xffffffffu, flag == 0);
+        const unsigned incl = __ballot_sync(0xffffffffu, flag == kFlagIncl);
+        // Only the predecessors up to the nearest inclusive prefix matter.
+        if (waiting && (!incl || __ffs(waiting) < __ffs(incl))) {
             if (++spins > kSpinLimit) {
                 if (lane == 0) atomicOr(status, kStatusLookbackTimeout);
                 break;
@@ -67,7 +70,6 @@ __device__ __forceinline__ unsigned long long warp_chained_prefix(unsigned long 
             __nanosleep(32);
             continue;
         }
-        const unsigned incl = __ballot_sync(0xffffffffu, flag == kFlagIncl);
         unsigned long long val = v & kValueMask;
         if (incl) {
             const int first = __ffs(incl) - 1;  // nearest predecessor with an inclusive prefix

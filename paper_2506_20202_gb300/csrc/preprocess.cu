@@ -15,9 +15,9 @@ namespace rara {
 
 namespace {
 
-// Colour of Gaussian i along the unit direction (x, y, z): sum_k sh_k Y_k + 0.5, clamped at 0.
-__device__ void sh_colour(const float *__restrict__ sh, int n, int i, int degree, float x, float y, float z,
-                          float rgb[3])
+// Colour along the unit direction (x, y, z): sum_k sh_k Y_k + 0.5, clamped at 0. The
+// thread's coefficients are staged in shared memory, s_sh[(k * 3 + c) * kBlock + thread].
+__device__ __forceinline__ void sh_colour(const float *s_sh, int degree, float x, float y, float z, float rgb[3])
 {
     float basis[16];
     sh_basis(degree, x, y, z, basis);
@@ -27,45 +27,24 @@ __device__ void sh_colour(const float *__restrict__ sh, int n, int i, int degree
         float acc = 0.0f;
 #pragma unroll
         for (int k = 0; k < 16; ++k)
-            if (k < kmax) acc = fmaf(__ldg(&sh[(size_t)(k * 3 + c) * n + i]), basis[k], acc);
+            if (k < kmax) acc = fmaf(s_sh[(k * 3 + c) * kBlock + threadIdx.x], basis[k], acc);
         rgb[c] = fmaxf(acc + 0.5f, 0.0f);
     }
 }
 
-__device__ __forceinline__ void block_add3(unsigned long long v0, unsigned long long v1, unsigned long long v2,
-                                           unsigned long long *s_red, unsigned long long *d0, unsigned long long *d1,
-                                           unsigned long long *d2, unsigned long long *t0, unsigned long long *t1,
-                                           unsigned long long *t2)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) {
-        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-    }
-    if (lane == 0) {
-        s_red[3 * warp] = v0;
-        s_red[3 * warp + 1] = v1;
-        s_red[3 * warp + 2] = v2;
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-        unsigned long long acc = 0;
-        for (int w = 0; w < kBlock / 32; ++w) acc += s_red[3 * w + threadIdx.x];
-        if (acc) {
-            atomicAdd(threadIdx.x == 0 ? d0 : (threadIdx.x == 1 ? d1 : d2), acc);
-            atomicAdd(threadIdx.x == 0 ? t0 : (threadIdx.x == 1 ? t1 : t2), acc);
-        }
-    }
-    __syncthreads();
-}
+constexpr int kViewChunk = 16;  // views staged in shared memory at a time
 
-// One block = one unit of 256 Gaussians of one scene; the Gaussians' attributes are read
-// once and every view of the scene is processed from registers (SH coefficients are re-read
-// per view, from L1/L2 after the first view).
+// One block = one unit of 256 Gaussians of one scene. The Gaussians' attributes are read
+// once (the SH coefficients into shared memory, all loads of a thread issued together) and
+// every view of the scene is processed from registers and shared memory; the views' tables
+// are staged kViewChunk at a time. Per-view counts are summed per warp and per block in
+// shared memory and added to the global counters once per chunk.
 __global__ void __launch_bounds__(kBlock, 4) k_preprocess(PreprocessArgs a)
 {
-    __shared__ unsigned long long s_red[3 * (kBlock / 32)];
+    extern __shared__ float s_sh[];  // [3 (degree+1)^2][kBlock]
+    __shared__ ViewDev s_views[kViewChunk];
+    __shared__ unsigned long long s_cnt[3][kViewChunk];
+    const int lane = threadIdx.x & 31;
     const int unit = blockIdx.x;
     int si = 0;
     while (si + 1 < a.num_scenes && (int)a.scenes[si + 1].unit_begin <= unit) ++si;
@@ -91,133 +70,179 @@ __global__ void __launch_bounds__(kBlock, 4) k_preprocess(PreprocessArgs a)
         Rg[3] = 2.f * (qx * qy + qw * qz); Rg[4] = 1.f - 2.f * (qx * qx + qz * qz); Rg[5] = 2.f * (qy * qz - qw * qx);
         Rg[6] = 2.f * (qx * qz - qw * qy); Rg[7] = 2.f * (qy * qz + qw * qx); Rg[8] = 1.f - 2.f * (qx * qx + qy * qy);
     }
+    {
+        const int q3 = 3 * sh_count(sc.sh_degree);
+        for (int q = 0; q < q3; ++q)
+            s_sh[q * kBlock + threadIdx.x] = valid ? __ldg(&sc.sh[(size_t)q * n + i]) : 0.0f;
+    }
     const float sg[3] = {s0, s1, s2};
     const float r = 3.0f * fmaxf(s0, fmaxf(s1, s2));
+    const float op = 1.0f / (1.0f + expf(-logit));
+    const int view_end = sc.view_begin + sc.view_count;
 
-    for (int v = sc.view_begin; v < sc.view_begin + sc.view_count; ++v) {
-        const ViewDev &vw = a.views[v];
-        const PlaneDev &pl = vw.plane;
-        const CamDev &cam = vw.cam;
-        bool rendered = false, cutoff = false;
-        uint32_t ntiles = 0;
-        if (valid) {
-            const uint32_t slot = vw.slot_base + (uint32_t)i;
-            // Section 3.2 / Algorithm 1 step 1: d_ep = n.mu + d, r = 3 max(sigma)
-            const float dep = fmaf(pl.n[0], mx, fmaf(pl.n[1], my, fmaf(pl.n[2], mz, pl.d)));
-            int label;
-            if (pl.mode == RARA_MODE_NONE) label = RARA_VISIBLE;
-            else if (pl.mode == RARA_MODE_HARD) label = dep < 0.0f ? RARA_INVISIBLE : RARA_VISIBLE;
-            else {
-                label = dep < -r ? RARA_INVISIBLE : (dep > r ? RARA_VISIBLE : RARA_CUTOFF);
-                if (pl.mode == RARA_MODE_RARA_ALL && label != RARA_INVISIBLE) label = RARA_CUTOFF;
-            }
-            a.labels[slot] = (uint8_t)label;
-
-            const float tx = fmaf(cam.R[0], mx, fmaf(cam.R[1], my, fmaf(cam.R[2], mz, cam.t[0])));
-            const float ty = fmaf(cam.R[3], mx, fmaf(cam.R[4], my, fmaf(cam.R[5], mz, cam.t[1])));
-            const float tz = fmaf(cam.R[6], mx, fmaf(cam.R[7], my, fmaf(cam.R[8], mz, cam.t[2])));
-
-            if (label != RARA_INVISIBLE && tz > kNearZ) {
-                // Eq. 9-10: Sigma2 = (J W M)(J W M)^T + 0.3 I with M = R S and J the affine
-                // approximation of the projection at the centre (x/z, y/z clamped).
-                const float itz = 1.0f / tz;
-                const float limx = 1.3f * (0.5f * cam.W / cam.fx), limy = 1.3f * (0.5f * cam.H / cam.fy);
-                const float txz = fminf(limx, fmaxf(-limx, tx * itz));
-                const float tyz = fminf(limy, fmaxf(-limy, ty * itz));
-                const float J00 = cam.fx * itz, J02 = -cam.fx * txz * itz;
-                const float J11 = cam.fy * itz, J12 = -cam.fy * tyz * itz;
-                float T0[3], T1[3];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    T0[k] = fmaf(J00, cam.R[k], J02 * cam.R[6 + k]);
-                    T1[k] = fmaf(J11, cam.R[3 + k], J12 * cam.R[6 + k]);
+    for (int vbase = sc.view_begin; vbase < view_end; vbase += kViewChunk) {
+        const int nv = min(kViewChunk, view_end - vbase);
+        __syncthreads();  // the previous chunk's tables and counts are no longer read
+        {
+            constexpr int kWords = (int)(sizeof(ViewDev) / sizeof(uint32_t));
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(a.views + vbase);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(s_views);
+            for (int t = threadIdx.x; t < nv * kWords; t += kBlock) dst[t] = __ldg(&src[t]);
+            if (threadIdx.x < 3 * kViewChunk) (&s_cnt[0][0])[threadIdx.x] = 0ull;
+        }
+        __syncthreads();
+        for (int vv = 0; vv < nv; ++vv) {
+            const ViewDev &vw = s_views[vv];
+            const PlaneDev &pl = vw.plane;
+            const CamDev &cam = vw.cam;
+            bool rendered = false, cutoff = false;
+            uint32_t ntiles = 0;
+            if (valid) {
+                const uint32_t slot = vw.slot_base + (uint32_t)i;
+                // Section 3.2 / Algorithm 1 step 1: d_ep = n.mu + d, r = 3 max(sigma)
+                const float dep = fmaf(pl.n[0], mx, fmaf(pl.n[1], my, fmaf(pl.n[2], mz, pl.d)));
+                int label;
+                if (pl.mode == RARA_MODE_NONE) label = RARA_VISIBLE;
+                else if (pl.mode == RARA_MODE_HARD) label = dep < 0.0f ? RARA_INVISIBLE : RARA_VISIBLE;
+                else {
+                    label = dep < -r ? RARA_INVISIBLE : (dep > r ? RARA_VISIBLE : RARA_CUTOFF);
+                    if (pl.mode == RARA_MODE_RARA_ALL && label != RARA_INVISIBLE) label = RARA_CUTOFF;
                 }
-                float A0[3], A1[3];  // rows of J W R S
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    A0[k] = (T0[0] * Rg[k] + T0[1] * Rg[3 + k] + T0[2] * Rg[6 + k]) * sg[k];
-                    A1[k] = (T1[0] * Rg[k] + T1[1] * Rg[3 + k] + T1[2] * Rg[6 + k]) * sg[k];
-                }
-                const float a0 = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2];
-                const float b0 = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
-                const float c0 = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2];
-                // det((A A^T) + 0.3 I) = |A0 x A1|^2 + 0.3 (a0 + c0) + 0.09: every term is
-                // non-negative, so elongated splats keep their precision.
-                const float x0 = A0[1] * A1[2] - A0[2] * A1[1];
-                const float x1 = A0[2] * A1[0] - A0[0] * A1[2];
-                const float x2 = A0[0] * A1[1] - A0[1] * A1[0];
-                const float ca = a0 + kDilation, cb = b0, cc = c0 + kDilation;
-                const float det = (x0 * x0 + x1 * x1 + x2 * x2) + kDilation * (a0 + c0) + kDilation * kDilation;
-                if (det > 0.0f) {
-                    const float idet = 1.0f / det;
-                    const float mx2 = fmaf(cam.fx, tx * itz, cam.cx);
-                    const float my2 = fmaf(cam.fy, ty * itz, cam.cy);
-                    // Tile rectangle: axis-aligned box of the q <= 9 ellipse
-                    const float hx = 3.0f * sqrtf(ca), hy = 3.0f * sqrtf(cc);
-                    const float inv_t = 1.0f / kTile;
-                    const float fx0 = floorf((mx2 - hx) * inv_t), fx1 = floorf((mx2 + hx) * inv_t);
-                    const float fy0 = floorf((my2 - hy) * inv_t), fy1 = floorf((my2 + hy) * inv_t);
-                    const int rx0 = (int)fmaxf(0.0f, fminf((float)vw.tiles_x, fx0));
-                    const int rx1 = (int)fmaxf(-1.0f, fminf((float)(vw.tiles_x - 1), fx1));
-                    const int ry0 = (int)fmaxf(0.0f, fminf((float)vw.tiles_y, fy0));
-                    const int ry1 = (int)fmaxf(-1.0f, fminf((float)(vw.tiles_y - 1), fy1));
-                    if (rx0 <= rx1 && ry0 <= ry1) {
-                        ntiles = (uint32_t)((rx1 - rx0 + 1) * (ry1 - ry0 + 1));
-                        rendered = true;
-                        cutoff = label == RARA_CUTOFF;
-                        a.rect[slot] = make_uint2((uint32_t)rx0 | ((uint32_t)ry0 << 16),
-                                                  (uint32_t)rx1 | ((uint32_t)ry1 << 16));
-                        const float op = 1.0f / (1.0f + expf(-logit));
-                        // colour at normalize(mu - e)
-                        const float ex = mx - cam.eye[0], ey = my - cam.eye[1], ez = mz - cam.eye[2];
-                        const float il = rsqrtf(ex * ex + ey * ey + ez * ez);
-                        float rgb[3];
-                        sh_colour(sc.sh, n, i, sc.sh_degree, ex * il, ey * il, ez * il, rgb);
-                        SplatRec rec;
-                        rec.r0 = make_float4(mx2, my2, cc * idet, -cb * idet);
-                        rec.r1 = make_float4(ca * idet, op, rgb[0], rgb[1]);
-                        rec.r2 = make_float4(rgb[2], cutoff ? 1.0f : 0.0f, cb / cc, cb / ca);
-                        a.rec[slot] = rec;
-                        // The sort key holds the depth rounded once from a double-precision
-                        // dot product: the correctly rounded float32 of the exact depth.
-                        a.depth[slot] = (float)fma((double)cam.R[6], (double)mx,
-                                                   fma((double)cam.R[7], (double)my,
-                                                       fma((double)cam.R[8], (double)mz, (double)cam.t[2])));
+                a.labels[slot] = (uint8_t)label;
 
-                        if (cutoff) {
-                            // Ray-tracing record in the unit-sphere frame of M = k R S
-                            // (Eq. 4): M^-1 = diag(1/(k sigma)) R^T. For the pixel ray with
-                            // offset (dx, dy) from the projected centre, the local ray is
-                            // o + tau V with o = -G, V = G + P (dx, dy): G = M^-1 (mu - e) and
-                            // P = z M^-1 W^T[:, 0:2] diag(1/fx, 1/fy). m = M^T n carries the
-                            // plane into the same frame: s(x) = d_ep + m . u for x = mu + M u.
-                            const float kk = pl.k;
-                            const float iks[3] = {1.0f / (kk * s0), 1.0f / (kk * s1), 1.0f / (kk * s2)};
-                            float G[3], Px[3], Py[3], m[3];
-                            const float sx = tz / cam.fx, sy = tz / cam.fy;
-#pragma unroll
-                            for (int k = 0; k < 3; ++k) {
-                                const float rk0 = Rg[k], rk1 = Rg[3 + k], rk2 = Rg[6 + k];  // column k of R
-                                G[k] = iks[k] * (rk0 * ex + rk1 * ey + rk2 * ez);
-                                Px[k] = iks[k] * sx * (rk0 * cam.R[0] + rk1 * cam.R[1] + rk2 * cam.R[2]);
-                                Py[k] = iks[k] * sy * (rk0 * cam.R[3] + rk1 * cam.R[4] + rk2 * cam.R[5]);
-                                m[k] = kk * sg[k] * (rk0 * pl.n[0] + rk1 * pl.n[1] + rk2 * pl.n[2]);
+                const float tx = fmaf(cam.R[0], mx, fmaf(cam.R[1], my, fmaf(cam.R[2], mz, cam.t[0])));
+                const float ty = fmaf(cam.R[3], mx, fmaf(cam.R[4], my, fmaf(cam.R[5], mz, cam.t[1])));
+                const float tz = fmaf(cam.R[6], mx, fmaf(cam.R[7], my, fmaf(cam.R[8], mz, cam.t[2])));
+
+                if (label != RARA_INVISIBLE && tz > kNearZ) {
+                    // Eq. 9-10: Sigma2 = (J W M)(J W M)^T + 0.3 I with M = R S and J the affine
+                    // approximation of the projection at the centre (x/z, y/z clamped).
+                    const float itz = 1.0f / tz;
+                    const float limx = 1.3f * (0.5f * cam.W / cam.fx), limy = 1.3f * (0.5f * cam.H / cam.fy);
+                    const float txz = fminf(limx, fmaxf(-limx, tx * itz));
+                    const float tyz = fminf(limy, fmaxf(-limy, ty * itz));
+                    const float J00 = cam.fx * itz, J02 = -cam.fx * txz * itz;
+                    const float J11 = cam.fy * itz, J12 = -cam.fy * tyz * itz;
+                    float T0[3], T1[3];
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        T0[k] = fmaf(J00, cam.R[k], J02 * cam.R[6 + k]);
+                        T1[k] = fmaf(J11, cam.R[3 + k], J12 * cam.R[6 + k]);
+                    }
+                    float A0[3], A1[3];  // rows of J W R S
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        A0[k] = (T0[0] * Rg[k] + T0[1] * Rg[3 + k] + T0[2] * Rg[6 + k]) * sg[k];
+                        A1[k] = (T1[0] * Rg[k] + T1[1] * Rg[3 + k] + T1[2] * Rg[6 + k]) * sg[k];
+                    }
+                    const float a0 = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2];
+                    const float b0 = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
+                    const float c0 = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2];
+                    // det((A A^T) + 0.3 I) = |A0 x A1|^2 + 0.3 (a0 + c0) + 0.09: every term is
+                    // non-negative, so elongated splats keep their precision.
+                    const float x0 = A0[1] * A1[2] - A0[2] * A1[1];
+                    const float x1 = A0[2] * A1[0] - A0[0] * A1[2];
+                    const float x2 = A0[0] * A1[1] - A0[1] * A1[0];
+                    const float ca = a0 + kDilation, cb = b0, cc = c0 + kDilation;
+                    const float det = (x0 * x0 + x1 * x1 + x2 * x2) + kDilation * (a0 + c0) + kDilation * kDilation;
+                    if (det > 0.0f) {
+                        const float idet = 1.0f / det;
+                        const float mx2 = fmaf(cam.fx, tx * itz, cam.cx);
+                        const float my2 = fmaf(cam.fy, ty * itz, cam.cy);
+                        // Tile rectangle: axis-aligned box of the q <= 9 ellipse
+                        const float hx = 3.0f * sqrtf(ca), hy = 3.0f * sqrtf(cc);
+                        const float inv_t = 1.0f / kTile;
+                        const float fx0 = floorf((mx2 - hx) * inv_t), fx1 = floorf((mx2 + hx) * inv_t);
+                        const float fy0 = floorf((my2 - hy) * inv_t), fy1 = floorf((my2 + hy) * inv_t);
+                        const int rx0 = (int)fmaxf(0.0f, fminf((float)vw.tiles_x, fx0));
+                        const int rx1 = (int)fmaxf(-1.0f, fminf((float)(vw.tiles_x - 1), fx1));
+                        const int ry0 = (int)fmaxf(0.0f, fminf((float)vw.tiles_y, fy0));
+                        const int ry1 = (int)fmaxf(-1.0f, fminf((float)(vw.tiles_y - 1), fy1));
+                        if (rx0 <= rx1 && ry0 <= ry1) {
+                            ntiles = (uint32_t)((rx1 - rx0 + 1) * (ry1 - ry0 + 1));
+                            rendered = true;
+                            cutoff = label == RARA_CUTOFF;
+                            a.rect[slot] = make_uint2((uint32_t)rx0 | ((uint32_t)ry0 << 16),
+                                                      (uint32_t)rx1 | ((uint32_t)ry1 << 16));
+                            // colour at normalize(mu - e)
+                            const float ex = mx - cam.eye[0], ey = my - cam.eye[1], ez = mz - cam.eye[2];
+                            const float il = rsqrtf(ex * ex + ey * ey + ez * ez);
+                            float rgb[3];
+                            sh_colour(s_sh, sc.sh_degree, ex * il, ey * il, ez * il, rgb);
+                            SplatRec rec;
+                            rec.r0 = make_float4(mx2, my2, cc * idet, -cb * idet);
+                            rec.r1 = make_float4(ca * idet, op, rgb[0], rgb[1]);
+                            float wmode = 0.0f;
+                            // The sort key holds the depth rounded once from a double-precision
+                            // dot product: the correctly rounded float32 of the exact depth.
+                            a.depth[slot] = (float)fma((double)cam.R[6], (double)mx,
+                                                       fma((double)cam.R[7], (double)my,
+                                                           fma((double)cam.R[8], (double)mz, (double)cam.t[2])));
+
+                            if (cutoff) {
+                                // Ray-tracing record in the unit-sphere frame of M = k R S
+                                // (Eq. 4): M^-1 = diag(1/(k sigma)) R^T. For the pixel ray with
+                                // offset (dx, dy) from the projected centre, the local ray is
+                                // o + tau V with o = -G, V = G + P (dx, dy): G = M^-1 (mu - e) and
+                                // P = z M^-1 W^T[:, 0:2] diag(1/fx, 1/fy). m = M^T n carries the
+                                // plane into the same frame: s(x) = d_ep + m . u for x = mu + M u.
+                                const float kk = pl.k;
+                                const float iks[3] = {1.0f / (kk * s0), 1.0f / (kk * s1), 1.0f / (kk * s2)};
+                                float G[3], Px[3], Py[3], m[3];
+                                const float sx = tz / cam.fx, sy = tz / cam.fy;
+    #pragma unroll
+                                for (int k = 0; k < 3; ++k) {
+                                    const float rk0 = Rg[k], rk1 = Rg[3 + k], rk2 = Rg[6 + k];  // column k of R
+                                    G[k] = iks[k] * (rk0 * ex + rk1 * ey + rk2 * ez);
+                                    Px[k] = iks[k] * sx * (rk0 * cam.R[0] + rk1 * cam.R[1] + rk2 * cam.R[2]);
+                                    Py[k] = iks[k] * sy * (rk0 * cam.R[3] + rk1 * cam.R[4] + rk2 * cam.R[5]);
+                                    m[k] = kk * sg[k] * (rk0 * pl.n[0] + rk1 * pl.n[1] + rk2 * pl.n[2]);
+                                }
+                                // The plane meets the ellipsoid only if |d_ep| <= |m| (s varies by
+                                // at most |m| over the unit ball). Beyond that (with a margin over
+                                // rounding) every chord lies on one side: w = 1 for every ray when
+                                // it is the visible side, and w = 0 for rays that hit the ellipsoid
+                                // in front (1 for the others) when it is the invisible side.
+                                const float mlen = sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+                                const float bound = mlen * (1.0f + 1e-4f);
+                                wmode = dep > bound ? kWeightNone : (dep < -bound ? kWeightHidden : kWeightSplit);
+                                if (wmode != kWeightNone) {
+                                    CutRec c;
+                                    c.c0 = make_float4(G[0], G[1], G[2], dep);
+                                    c.c1 = make_float4(Px[0], Px[1], Px[2], m[0]);
+                                    c.c2 = make_float4(Py[0], Py[1], Py[2], m[1]);
+                                    c.c3 = make_float4(m[2], 0.0f, 0.0f, 0.0f);
+                                    a.cut[slot] = c;
+                                }
                             }
-                            CutRec c;
-                            c.c0 = make_float4(G[0], G[1], G[2], dep);
-                            c.c1 = make_float4(Px[0], Px[1], Px[2], m[0]);
-                            c.c2 = make_float4(Py[0], Py[1], Py[2], m[1]);
-                            c.c3 = make_float4(m[2], 0.0f, 0.0f, 0.0f);
-                            a.cut[slot] = c;
+                            rec.r2 = make_float4(rgb[2], wmode, cb / cc, cb / ca);
+                            a.rec[slot] = rec;
                         }
                     }
                 }
+                a.tiles[slot] = ntiles;
             }
-            a.tiles[slot] = ntiles;
+            // per-view counts: warp sums, then one shared-memory add per warp
+            const unsigned nr = __reduce_add_sync(0xffffffffu, rendered ? 1u : 0u);
+            const unsigned nc = __reduce_add_sync(0xffffffffu, cutoff ? 1u : 0u);
+            unsigned long long np = ntiles;
+            for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(0xffffffffu, np, o);
+            if (lane == 0) {
+                if (nr) atomicAdd(&s_cnt[0][vv], (unsigned long long)nr);
+                if (np) atomicAdd(&s_cnt[1][vv], np);
+                if (nc) atomicAdd(&s_cnt[2][vv], (unsigned long long)nc);
+            }
         }
-        ViewCounters *vc = &a.view_counters[v];
-        block_add3(rendered ? 1ull : 0ull, ntiles, cutoff ? 1ull : 0ull, s_red, &vc->n_rendered, &vc->n_pairs,
-                   &vc->n_cutoff, &a.counters->n_rendered, &a.counters->n_pairs, &a.counters->n_cutoff);
+        __syncthreads();
+        if (threadIdx.x < 3 * nv) {
+            const int f = threadIdx.x / nv, vv = threadIdx.x % nv;
+            const unsigned long long c = s_cnt[f][vv];
+            if (c) {
+                ViewCounters *vc = &a.view_counters[vbase + vv];
+                atomicAdd(f == 0 ? &vc->n_rendered : (f == 1 ? &vc->n_pairs : &vc->n_cutoff), c);
+                atomicAdd(f == 0 ? &a.counters->n_rendered : (f == 1 ? &a.counters->n_pairs : &a.counters->n_cutoff), c);
+            }
+        }
     }
 }
 
@@ -296,9 +321,17 @@ __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
 
 }  // namespace
 
-void launch_preprocess(const PreprocessArgs &a, int grid, cudaStream_t s)
+int preprocess_configure()
 {
-    if (grid > 0) k_preprocess<<<grid, kBlock, 0, s>>>(a);
+    const int most = 3 * 16 * kBlock * (int)sizeof(float);  // SH degree 3
+    return cudaFuncSetAttribute(k_preprocess, cudaFuncAttributeMaxDynamicSharedMemorySize, most) == cudaSuccess ? 0
+                                                                                                              : -1;
+}
+
+void launch_preprocess(const PreprocessArgs &a, int grid, int max_sh_degree, cudaStream_t s)
+{
+    const int smem = 3 * (max_sh_degree + 1) * (max_sh_degree + 1) * kBlock * (int)sizeof(float);
+    if (grid > 0) k_preprocess<<<grid, kBlock, smem, s>>>(a);
 }
 
 int compact_blocks_per_sm()

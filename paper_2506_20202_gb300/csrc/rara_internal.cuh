@@ -43,12 +43,18 @@ constexpr uint32_t kStatusOverflow = 2u;         // a count exceeded its buffer'
 // render kernel: 3 x float4 = 48 bytes.
 //   r0 = (mean2d.x, mean2d.y, conic.a, conic.b)
 //   r1 = (conic.c, opacity, rgb.r, rgb.g)
-//   r2 = (rgb.b, cutoff flag as float (1 or 0), -b/a, -b/c)
+//   r2 = (rgb.b, decay-weight mode as float (kWeight*), -b/a, -b/c)
 // The last two are the minimisers of q along a horizontal / vertical line (dx* = -b/a dy,
 // dy* = -b/c dx), used by the render's exact rectangle test.
 struct __align__(16) SplatRec {
     float4 r0, r1, r2;
 };
+
+// Decay-weight mode of a rendered slot (SplatRec r2.y). Only cutoff Gaussians whose
+// ellipsoid the plane actually meets need the per-pixel weight; a cutoff Gaussian wholly on
+// the visible side has w = 1 for every ray, one wholly on the invisible side has w = 0 for
+// the rays that hit it in front and 1 for the others.
+constexpr float kWeightNone = 0.0f, kWeightSplit = 1.0f, kWeightHidden = 2.0f;
 
 // Per-cutoff-slot ray-tracing record, 4 x float4 = 64 bytes, relative to the Gaussian's own
 // frame (see preprocess.cu for the derivation):
@@ -138,7 +144,10 @@ struct PreprocessArgs {
     ViewCounters *view_counters;
     Counters *counters;
 };
-void launch_preprocess(const PreprocessArgs &a, int grid, cudaStream_t s);
+// max_sh_degree sizes the shared-memory staging of the SH coefficients (the largest degree
+// of a scene with views); preprocess_configure() must have succeeded once per device.
+void launch_preprocess(const PreprocessArgs &a, int grid, int max_sh_degree, cudaStream_t s);
+int preprocess_configure();
 
 // Stage 2: compaction of rendered slots (slot order) + histogram of the depth-key digits
 struct CompactArgs {

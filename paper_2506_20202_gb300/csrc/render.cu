@@ -31,7 +31,9 @@
 //   weight      both >= 0: 1; both < 0: 0; otherwise the visible share of the chord,
 //               max(s1, s2) / |s2 - s1|  (= (t2 - t_p)/(t2 - t1) or (t_p - t1)/(t2 - t1)).
 // Because w <= 1, an entry whose unweighted alpha is already below 1/255 is skipped before
-// the weight is computed (the weighted alpha could only be smaller).
+// the weight is computed (the weighted alpha could only be smaller). The preprocess marks
+// which cutoff Gaussians the plane actually meets (|d_ep| <= |m|); only those evaluate the
+// full weight, the others are w = 1 (visible side) or a hit test (invisible side).
 #include "rara_internal.cuh"
 #include "render_common.cuh"
 
@@ -56,9 +58,14 @@ __device__ __forceinline__ float entry_alpha(const Stage &st, int j, float pxf, 
     ++ty.evaluated;
     float alpha = r1.y * __expf(-0.5f * q);
     if (alpha < kAlphaMin) return 0.0f;
-    if (st.r2[j].y != 0.0f) {
-        alpha *= rara_weight(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
-        ++ty.cut;
+    const float mode = st.r2[j].y;
+    if (mode != kWeightNone) {
+        if (mode == kWeightSplit) {
+            alpha *= rara_weight(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
+            ++ty.cut;
+        } else {
+            alpha *= rara_weight_hidden(st.c0[j], st.c1[j], st.c2[j], dx, dy);
+        }
     }
     alpha = fminf(kAlphaMax, alpha);
     return alpha < kAlphaMin ? 0.0f : alpha;

@@ -21,8 +21,8 @@ constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kItems = 12;                       // keys per thread per partition
 constexpr int kPart = kSortThreads * kItems;     // keys per partition (3072)
-constexpr int kMaxPasses = 4;
 constexpr uint32_t kLbAgg = 1u << 30, kLbIncl = 2u << 30, kLbMask = (1u << 30) - 1u;
+constexpr int kLbWidth = 4;                      // predecessors read per look-back step
 
 // Exclusive scan of 256 values held one per thread, result per thread (block of 256).
 __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *s_tmp)
@@ -92,12 +92,21 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(uint32_t *keys_a, uin
 
         uint32_t key[kItems], val[kItems], rank[kItems];
         const unsigned lt = (1u << lane) - 1u;
+        // Issue every load of the partition before ranking, so they are in flight together.
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            const int idx = base + r * 32 + lane;
+            key[r] = idx < n ? __ldg(&keys_in[idx]) : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            const int idx = base + r * 32 + lane;
+            val[r] = idx < n ? __ldg(&vals_in[idx]) : 0u;
+        }
 #pragma unroll
         for (int r = 0; r < kItems; ++r) {
             const int idx = base + r * 32 + lane;
             const bool ok = idx < n;
-            key[r] = ok ? keys_in[idx] : 0u;
-            val[r] = ok ? vals_in[idx] : 0u;
             const uint32_t digit = ok ? ((key[r] >> shift) & 0xffu) : 0x100u;
             const unsigned peers = __match_any_sync(0xffffffffu, digit);
             const int leader = 31 - __clz(peers);
@@ -123,19 +132,33 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(uint32_t *keys_a, uin
         else st_relaxed_u32(lb, kLbAgg | total);
         uint32_t excl = 0;
         if (part > 0) {
+            // Walk back over the predecessors' words for this digit, kLbWidth at a time (the
+            // loads of one step are in flight together), summing aggregates up to the
+            // nearest inclusive prefix.
             int p = part - 1;
             int spins = 0;
             while (p >= 0) {
-                const uint32_t v = ld_relaxed_u32(lookback + (size_t)p * kRadix + tid);
-                const uint32_t flag = v & ~kLbMask;
-                if (flag == 0u) {
+                uint32_t v[kLbWidth];
+#pragma unroll
+                for (int k = 0; k < kLbWidth; ++k)
+                    v[k] = p - k >= 0 ? ld_relaxed_u32(lookback + (size_t)(p - k) * kRadix + tid) : kLbIncl;
+                int k = 0;
+                bool found = false;
+#pragma unroll
+                for (int u = 0; u < kLbWidth; ++u) {
+                    if (found || k < u) continue;        // stopped earlier in this step
+                    const uint32_t flag = v[u] & ~kLbMask;
+                    if (flag == 0u) continue;            // not published yet: retry from here
+                    excl += v[u] & kLbMask;
+                    k = u + 1;
+                    if (flag == kLbIncl) found = true;
+                }
+                if (found) break;
+                p -= k;
+                if (k < kLbWidth) {
                     if (++spins > kSpinLimit) { atomicOr(status, kStatusLookbackTimeout); break; }
                     __nanosleep(32);
-                    continue;
                 }
-                excl += v & kLbMask;
-                if (flag == kLbIncl) break;
-                --p;
             }
             st_relaxed_u32(lb, kLbIncl | (excl + total));
         }
