@@ -17,9 +17,10 @@
 //   w = 1/2 + s_mid / (2 |h|)   (s_mid = d_ep + m.c, h = sqrt(1 - |c|^2) m.V / |V|).
 // Where w is 0 or 1 (chord on one side of the plane, ray missing or behind) it is constant
 // and passes no gradient; where 0.99 clamps alpha, alpha passes none either. Per entry the
-// warp's pixels are summed with shuffles and one lane adds the sums to the slot's gradient
-// record with vector atomics. Warps skip entries whose q <= 9 support misses their 8x4
-// rectangle, as in the forward.
+// warp's pixels are summed with a shuffle reduce-scatter (9 or 22 components), after which
+// one lane per component adds its total to the slot's gradient record (a single
+// contributing pixel adds its own values with vector atomics). Warps skip entries whose
+// q <= 9 support misses their 8x4 rectangle, as in the forward.
 //
 // Preprocess backward (per Gaussian, looping over its scene's views like the forward):
 // the slot's gradient record is carried back through the projection (Eq. 9-10: conic ->
@@ -96,6 +97,28 @@ __device__ __forceinline__ float warp_sum(float v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
+}
+
+// Sums N = 16 or 32 values per lane over the warp and scatters the totals (reduce-scatter:
+// at each step a lane keeps half of its values and trades the other half with its partner,
+// N/2 + N/4 + ... shuffles instead of 5 N). Afterwards v[0] holds the total of component
+// `lane` (N = 32) or `lane >> 1` (N = 16, the pair of lanes 2c, 2c+1 both hold it).
+template <int N>
+__device__ __forceinline__ void warp_reduce_scatter(float (&v)[N])
+{
+    const int lane = threadIdx.x & 31;
+    int o = 16;
+#pragma unroll
+    for (int h = N / 2; h >= 1; h >>= 1, o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = upper ? v[i] : v[i + h];
+            const float keep = upper ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, o);
+        }
+    }
+    if (N == 16) v[0] += __shfl_xor_sync(kFull, v[0], 1);
 }
 
 // One 16x16 tile, one thread per pixel (warp rectangles of 8x4 pixels).
@@ -235,41 +258,37 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
                 const unsigned who = __ballot_sync(kFull, contrib);
                 if (!who) continue;
                 GradRec *dst = &a.grec[s_slot[j]];
-                bool writer = contrib;
-                if (__popc(who) > 1) {  // sum the warp's pixels; lane 0 writes
-                    gmx = warp_sum(gmx); gmy = warp_sum(gmy); gCa = warp_sum(gCa); gCb = warp_sum(gCb);
-                    gCc = warp_sum(gCc); gop = warp_sum(gop); gr = warp_sum(gr); gg = warp_sum(gg);
-                    gb = warp_sum(gb);
-                    if (cut) {
-                        gdep = warp_sum(gdep);
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            gG[k] = warp_sum(gG[k]);
-                            gPx[k] = warp_sum(gPx[k]);
-                            gPy[k] = warp_sum(gPy[k]);
-                            gm[k] = warp_sum(gm[k]);
+                if (__popc(who) == 1) {  // one pixel: it adds its own values
+                    if (contrib) {
+                        atomicAdd(&dst->g0, make_float4(gmx, gmy, gCa, gCb));
+                        atomicAdd(&dst->g1, make_float4(gCc, gop, gr, gg));
+                        if (cut) {
+                            atomicAdd(&dst->g2, make_float4(gb, gdep, gm[0], gm[1]));
+                            atomicAdd(&dst->g3, make_float4(gm[2], gG[0], gG[1], gG[2]));
+                            atomicAdd(&dst->g4, make_float4(gPx[0], gPx[1], gPx[2], gPy[0]));
+                            atomicAdd(reinterpret_cast<float2 *>(&dst->g5), make_float2(gPy[1], gPy[2]));
+                        } else {
+                            atomicAdd(&dst->g2.x, gb);
                         }
                     }
-                    writer = lane == 0;
-                }
-                if (writer) {
-                    atomicAdd(&dst->g0, make_float4(gmx, gmy, gCa, gCb));
-                    atomicAdd(&dst->g1, make_float4(gCc, gop, gr, gg));
-                    if (cut) {
-                        atomicAdd(&dst->g2, make_float4(gb, gdep, gm[0], gm[1]));
-                        atomicAdd(&dst->g3, make_float4(gm[2], gG[0], gG[1], gG[2]));
-                        atomicAdd(&dst->g4, make_float4(gPx[0], gPx[1], gPx[2], gPy[0]));
-                        atomicAdd(reinterpret_cast<float2 *>(&dst->g5), make_float2(gPy[1], gPy[2]));
-                    } else {
-                        atomicAdd(&dst->g2.x, gb);
-                    }
+                } else if (!cut) {  // components 0..8 of the record
+                    float v[16] = {gmx, gmy, gCa, gCb, gCc, gop, gr, gg, gb, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    warp_reduce_scatter<16>(v);
+                    if (!(lane & 1) && (lane >> 1) < 9) atomicAdd(reinterpret_cast<float *>(dst) + (lane >> 1), v[0]);
+                } else {  // components 0..21 of the record
+                    float v[32] = {gmx,    gmy,    gCa,    gCb,    gCc,    gop,    gr,     gg,
+                                   gb,     gdep,   gm[0],  gm[1],  gm[2],  gG[0],  gG[1],  gG[2],
+                                   gPx[0], gPx[1], gPx[2], gPy[0], gPy[1], gPy[2], 0.f,    0.f,
+                                   0.f,    0.f,    0.f,    0.f,    0.f,    0.f,    0.f,    0.f};
+                    warp_reduce_scatter<32>(v);
+                    if (lane < 22) atomicAdd(reinterpret_cast<float *>(dst) + lane, v[0]);
                 }
             }
         }
     }
 }
 
-__global__ void __launch_bounds__(kBlock, 2) k_render_bwd(RenderBwdArgs a)
+__global__ void __launch_bounds__(kBlock, 4) k_render_bwd(RenderBwdArgs a)
 {
     __shared__ Stage st;
     __shared__ uint32_t s_slot[kBlock];

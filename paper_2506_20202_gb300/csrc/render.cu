@@ -98,12 +98,15 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     bool done = !inside;
     uint32_t last = 0;
+    // slot of this thread's entry in the next batch, loaded one batch ahead
+    uint32_t g_next = range.x + (int)threadIdx.x < range.y ? __ldg(&pair_vals[range.x + threadIdx.x]) : 0u;
 
     for (int base = range.x; base < range.y; base += kBlock) {
         if (__syncthreads_count(done) == kBlock) break;
         const int k = base + threadIdx.x;
+        const uint32_t g = g_next;
+        if (k + kBlock < range.y) g_next = __ldg(&pair_vals[k + kBlock]);
         if (k < range.y) {
-            const uint32_t g = __ldg(&pair_vals[k]);
             const SplatRec rec = a.rec[g];
             st.r0[threadIdx.x] = rec.r0;
             st.r1[threadIdx.x] = rec.r1;
@@ -226,7 +229,7 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
     }
 }
 
-__global__ void __launch_bounds__(kBlock, 4) k_render(RenderArgs a)
+__global__ void __launch_bounds__(kBlock, 5) k_render(RenderArgs a)
 {
     __shared__ Stage st;
     __shared__ unsigned s_item;
