@@ -41,54 +41,59 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 // Gradient of the decay weight where the plane splits the chord (0 < w < 1); returns false
-// (no gradient) where w is constant. The arithmetic repeats rara_weight's. Inputs: the
-// cutoff record c0..c3, the pixel offset (dx, dy) and gw = dL/dw; outputs dL/dG, dL/dp
-// (p = P (dx, dy)), dL/dm, dL/dd_ep.
+// (no gradient) where w is constant. It repeats rara_weight's arithmetic; with
+// w = 1/2 + s_mid / (2 H), H = sqrt(h2) |m.V| / |V|, it goes back through
+// s_mid = d_ep + m.p - f (m.V), f = (G.p + p.p) / V.V, h2 = 1 - |u|^2 / V.V,
+// V.V = G.G + 2 G.p + p.p, m.V = m.G + m.p and the per-pixel polynomials G.p, p.p, m.p,
+// u = dx A + dy B. Outputs: dL/d(record products) in CutRec order (c0.x .. c3.w) in gc[16],
+// and dL/d(dx, dy) added to gdx, gdy.
 __device__ __forceinline__ bool rara_weight_grad(const float4 c0, const float4 c1, const float4 c2, const float4 c3,
-                                                 float dx, float dy, float gw, float gG[3], float gp[3], float gm[3],
-                                                 float &gdep)
+                                                 float dx, float dy, float gw, float gc[16], float &gdx, float &gdy)
 {
-    const float p[3] = {fmaf(c1.x, dx, c2.x * dy), fmaf(c1.y, dx, c2.y * dy), fmaf(c1.z, dx, c2.z * dy)};
-    const float V[3] = {c0.x + p[0], c0.y + p[1], c0.z + p[2]};
-    const float m[3] = {c1.w, c2.w, c3.x};
-    const float VV = fmaf(V[0], V[0], fmaf(V[1], V[1], V[2] * V[2]));
-    const float pV = fmaf(p[0], V[0], fmaf(p[1], V[1], p[2] * V[2]));
-    const float f = __fdividef(pV, VV);
-    const float c[3] = {fmaf(-f, V[0], p[0]), fmaf(-f, V[1], p[1]), fmaf(-f, V[2], p[2])};
-    const float cc = fmaf(c[0], c[0], fmaf(c[1], c[1], c[2] * c[2]));
-    if (cc >= 1.0f) return false;
-    const float h2 = 1.0f - cc;
-    const float GV = fmaf(c0.x, V[0], fmaf(c0.y, V[1], c0.z * V[2]));
-    if (!(GV > 0.0f && GV * GV > h2 * VV)) return false;
-    const float mc = fmaf(m[0], c[0], fmaf(m[1], c[1], m[2] * c[2]));
-    const float mV = fmaf(m[0], V[0], fmaf(m[1], V[1], m[2] * V[2]));
-    const float smid = c0.w + mc;
-    const float half = __fmul_rn(sqrtf(h2) * mV, rsqrtf(VV));
+    const RayTerms t = ray_terms(c0, c1, c2, c3, dx, dy);
+    if (t.cc >= 1.0f) return false;
+    const float h2 = 1.0f - t.cc;
+    if (!(t.GV > 0.0f && t.GV * t.GV > h2 * t.VV)) return false;
+    const float mp = fmaf(c2.x, dx, c2.y * dy);
+    const float mV = c1.w + mp;
+    const float f = __fmul_rn(t.Gp + t.pp, t.rVV);
+    const float smid = c0.w + fmaf(-f, mV, mp);
+    const float half = __fmul_rn(__fmul_rn(__fmul_rn(h2, rsqrtf(h2)), mV), rsqrtf(t.VV));
     const float s1 = smid - half, s2 = smid + half;
     if ((s1 >= 0.0f) == (s2 >= 0.0f)) return false;
-    // w = 1/2 + smid / (2 H), H = |half| = sqrt(h2) |mV| / |V|
-    const float Hh = fabsf(half);
-    const float g_smid = gw / (2.0f * Hh);
-    const float g_H = -gw * smid / (2.0f * Hh * Hh);
-    const float H_h2 = Hh / h2, H_mV = Hh / mV, H_VV = Hh / VV;
-    float gc[3], gV[3];
-    float gcV = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        gc[k] = g_smid * m[k] - g_H * H_h2 * c[k];
-        gm[k] = g_smid * c[k] + g_H * H_mV * V[k];
-        gV[k] = g_H * (H_mV * m[k] - H_VV * V[k]);
-        gcV = fmaf(gc[k], V[k], gcV);
-    }
-    gdep = g_smid;
-    // c = p - (p.V / V.V) V with V = G + p
-    const float gv = gcV / VV;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float gVt = gV[k] - gv * p[k] - f * gc[k] + 2.0f * f * gv * V[k];
-        gG[k] = gVt;
-        gp[k] = gc[k] - gv * V[k] + gVt;
-    }
+    const float H = fabsf(half);
+    const float g_smid = gw / (2.0f * H);
+    const float g_H = -gw * smid / (2.0f * H * H);
+    const float iVV = 1.0f / t.VV;
+    float g_VV = -g_H * H * 0.5f * iVV;
+    const float g_h2 = g_H * H * 0.5f / h2;
+    float g_mV = g_H * H / mV - g_smid * f;
+    const float g_f = -g_smid * mV;
+    float g_mp = g_smid + g_mV;
+    const float g_pV = g_f * iVV;
+    g_VV -= g_f * f * iVV;
+    const float g_cc = -g_h2;
+    const float g_uu = g_cc * iVV;
+    g_VV -= g_cc * t.cc * iVV;
+    const float g_Gp = 2.0f * g_VV + g_pV;
+    const float g_pp = g_VV + g_pV;
+    gc[0] = g_VV;                       // G.G
+    gc[1] = g_Gp * dx;                  // G.Px
+    gc[2] = g_Gp * dy;                  // G.Py
+    gc[3] = g_smid;                     // d_ep
+    gc[4] = g_pp * dx * dx;             // Px.Px
+    gc[5] = 2.0f * g_pp * dx * dy;      // Px.Py
+    gc[6] = g_pp * dy * dy;             // Py.Py
+    gc[7] = g_mV;                       // m.G
+    gc[8] = g_mp * dx;                  // m.Px
+    gc[9] = g_mp * dy;                  // m.Py
+    const float gu0 = 2.0f * g_uu * t.u0, gu1 = 2.0f * g_uu * t.u1, gu2 = 2.0f * g_uu * t.u2;
+    gc[10] = gu0 * dx; gc[11] = gu1 * dx; gc[12] = gu2 * dx;   // A
+    gc[13] = gu0 * dy; gc[14] = gu1 * dy; gc[15] = gu2 * dy;   // B
+    gdx += g_Gp * c0.y + 2.0f * g_pp * fmaf(dx, c1.x, dy * c1.y) + g_mp * c2.x +
+           (gu0 * c2.z + gu1 * c2.w + gu2 * c3.x);
+    gdy += g_Gp * c0.z + 2.0f * g_pp * fmaf(dx, c1.y, dy * c1.z) + g_mp * c2.y +
+           (gu0 * c3.y + gu1 * c3.z + gu2 * c3.w);
     return true;
 }
 
@@ -198,8 +203,9 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
                 bool contrib = false;
                 float gmx = 0.f, gmy = 0.f, gCa = 0.f, gCb = 0.f, gCc = 0.f, gop = 0.f;
                 float gr = 0.f, gg = 0.f, gb = 0.f;
-                float gdep = 0.f, gG[3] = {0.f, 0.f, 0.f}, gPx[3] = {0.f, 0.f, 0.f}, gPy[3] = {0.f, 0.f, 0.f};
-                float gm[3] = {0.f, 0.f, 0.f};
+                float gc[16];  // cutoff record products (split weights only)
+#pragma unroll
+                for (int k = 0; k < 16; ++k) gc[k] = 0.f;
                 if (inside && pos < last) {
                     const float dx = pxf - r0.x, dy = pyf - r0.y;
                     const float q = splat_q(r0.z, r0.w, r1.x, dx, dy);
@@ -235,20 +241,9 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
                                 gCc = gq * dy * dy;
                                 float gdx = 2.0f * gq * fmaf(r0.z, dx, r0.w * dy);
                                 float gdy = 2.0f * gq * fmaf(r0.w, dx, r1.x * dy);
-                                if (cut) {
-                                    const float4 c1 = st.c1[j], c2 = st.c2[j];
-                                    float gp[3];
-                                    if (rara_weight_grad(st.c0[j], c1, c2, st.c3[j], dx, dy, ga * a0, gG, gp, gm,
-                                                         gdep)) {
-#pragma unroll
-                                        for (int k = 0; k < 3; ++k) {
-                                            gPx[k] = gp[k] * dx;
-                                            gPy[k] = gp[k] * dy;
-                                        }
-                                        gdx += gp[0] * c1.x + gp[1] * c1.y + gp[2] * c1.z;
-                                        gdy += gp[0] * c2.x + gp[1] * c2.y + gp[2] * c2.z;
-                                    }
-                                }
+                                if (cut)
+                                    rara_weight_grad(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy, ga * a0, gc, gdx,
+                                                     gdy);
                                 gmx = -gdx;
                                 gmy = -gdy;
                             }
@@ -257,31 +252,33 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
                 }
                 const unsigned who = __ballot_sync(kFull, contrib);
                 if (!who) continue;
-                GradRec *dst = &a.grec[s_slot[j]];
+                float *dst = a.grec[s_slot[j]].v;
                 if (__popc(who) == 1) {  // one pixel: it adds its own values
                     if (contrib) {
-                        atomicAdd(&dst->g0, make_float4(gmx, gmy, gCa, gCb));
-                        atomicAdd(&dst->g1, make_float4(gCc, gop, gr, gg));
+                        float4 *d4 = reinterpret_cast<float4 *>(dst);
+                        atomicAdd(&d4[0], make_float4(gmx, gmy, gCa, gCb));
+                        atomicAdd(&d4[1], make_float4(gCc, gop, gr, gg));
                         if (cut) {
-                            atomicAdd(&dst->g2, make_float4(gb, gdep, gm[0], gm[1]));
-                            atomicAdd(&dst->g3, make_float4(gm[2], gG[0], gG[1], gG[2]));
-                            atomicAdd(&dst->g4, make_float4(gPx[0], gPx[1], gPx[2], gPy[0]));
-                            atomicAdd(reinterpret_cast<float2 *>(&dst->g5), make_float2(gPy[1], gPy[2]));
+                            atomicAdd(&d4[2], make_float4(gb, gc[0], gc[1], gc[2]));
+                            atomicAdd(&d4[3], make_float4(gc[3], gc[4], gc[5], gc[6]));
+                            atomicAdd(&d4[4], make_float4(gc[7], gc[8], gc[9], gc[10]));
+                            atomicAdd(&d4[5], make_float4(gc[11], gc[12], gc[13], gc[14]));
+                            atomicAdd(&dst[24], gc[15]);
                         } else {
-                            atomicAdd(&dst->g2.x, gb);
+                            atomicAdd(&dst[8], gb);
                         }
                     }
                 } else if (!cut) {  // components 0..8 of the record
                     float v[16] = {gmx, gmy, gCa, gCb, gCc, gop, gr, gg, gb, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                     warp_reduce_scatter<16>(v);
-                    if (!(lane & 1) && (lane >> 1) < 9) atomicAdd(reinterpret_cast<float *>(dst) + (lane >> 1), v[0]);
-                } else {  // components 0..21 of the record
+                    if (!(lane & 1) && (lane >> 1) < 9) atomicAdd(&dst[lane >> 1], v[0]);
+                } else {  // components 0..24 of the record
                     float v[32] = {gmx,    gmy,    gCa,    gCb,    gCc,    gop,    gr,     gg,
-                                   gb,     gdep,   gm[0],  gm[1],  gm[2],  gG[0],  gG[1],  gG[2],
-                                   gPx[0], gPx[1], gPx[2], gPy[0], gPy[1], gPy[2], 0.f,    0.f,
-                                   0.f,    0.f,    0.f,    0.f,    0.f,    0.f,    0.f,    0.f};
+                                   gb,     gc[0],  gc[1],  gc[2],  gc[3],  gc[4],  gc[5],  gc[6],
+                                   gc[7],  gc[8],  gc[9],  gc[10], gc[11], gc[12], gc[13], gc[14],
+                                   gc[15], 0.f,    0.f,    0.f,    0.f,    0.f,    0.f,    0.f};
                     warp_reduce_scatter<32>(v);
-                    if (lane < 22) atomicAdd(reinterpret_cast<float *>(dst) + lane, v[0]);
+                    if (lane < kGradCut + 16) atomicAdd(&dst[lane], v[0]);
                 }
             }
         }
@@ -364,10 +361,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_preprocess_bwd(PreprocessBwdArgs 
         bool has_plane = false;
         const uint32_t slot = vw.slot_base + (uint32_t)i;
         if (valid && a.tiles[slot] != 0u) {
-            const GradRec &grc = a.grec[slot];
-            const float4 g0 = grc.g0, g1 = grc.g1;
+            const float *grc = a.grec[slot].v;
+            const float4 g0 = reinterpret_cast<const float4 *>(grc)[0];
+            const float4 g1 = reinterpret_cast<const float4 *>(grc)[1];
+            const float gblue = grc[8];
             const bool cutoff = a.labels[slot] == RARA_CUTOFF;
-            const float4 g2 = grc.g2;  // (rgb.b, then zeros unless cutoff)
             // ---- projection, as in the forward
             const float tx = fmaf(cam.R[0], mu[0], fmaf(cam.R[1], mu[1], fmaf(cam.R[2], mu[2], cam.t[0])));
             const float ty = fmaf(cam.R[3], mu[0], fmaf(cam.R[4], mu[1], fmaf(cam.R[5], mu[2], cam.t[1])));
@@ -453,7 +451,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_preprocess_bwd(PreprocessBwdArgs 
             {
                 float basis[16];
                 sh_basis(sc.sh_degree, dir[0], dir[1], dir[2], basis);
-                float grgb[3] = {g1.z, g1.w, g2.x};
+                float grgb[3] = {g1.z, g1.w, gblue};
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     float acc = 0.0f;
@@ -482,25 +480,41 @@ __global__ void __launch_bounds__(kBlock, 2) k_preprocess_bwd(PreprocessBwdArgs 
             }
             // ---- ray-tracing record of a cutoff Gaussian
             if (cutoff) {
-                const float4 g3 = grc.g3, g4 = grc.g4, g5 = grc.g5;
-                const float gG[3] = {g3.y, g3.z, g3.w};
-                const float gPx[3] = {g4.x, g4.y, g4.z};
-                const float gPy[3] = {g4.w, g5.x, g5.y};
-                const float gm[3] = {g2.z, g2.w, g3.x};
-                const float gdep = g2.y;
+                // gradients of the record products -> G, Px, Py, m (A = Px x G, B = Py x G)
+                const float *gq = grc + kGradCut;
                 const float kk = pl.k;
                 const float sx = tz / cam.fx, sy = tz / cam.fy;
-                float gtz_p = 0.0f;
+                float G[3], Px[3], Py[3], m[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const float rk0 = Rg[k], rk1 = Rg[3 + k], rk2 = Rg[6 + k];
                     const float iks = 1.0f / (kk * sg[k]);
-                    const float G = iks * (rk0 * e[0] + rk1 * e[1] + rk2 * e[2]);
-                    const float Px = iks * sx * (rk0 * cam.R[0] + rk1 * cam.R[1] + rk2 * cam.R[2]);
-                    const float Py = iks * sy * (rk0 * cam.R[3] + rk1 * cam.R[4] + rk2 * cam.R[5]);
-                    const float m = kk * sg[k] * (rk0 * pl.n[0] + rk1 * pl.n[1] + rk2 * pl.n[2]);
-                    gsg[k] += (-gG[k] * G - gPx[k] * Px - gPy[k] * Py + gm[k] * m) / sg[k];
-                    gtz_p += gPx[k] * Px + gPy[k] * Py;
+                    G[k] = iks * (rk0 * e[0] + rk1 * e[1] + rk2 * e[2]);
+                    Px[k] = iks * sx * (rk0 * cam.R[0] + rk1 * cam.R[1] + rk2 * cam.R[2]);
+                    Py[k] = iks * sy * (rk0 * cam.R[3] + rk1 * cam.R[4] + rk2 * cam.R[5]);
+                    m[k] = kk * sg[k] * (rk0 * pl.n[0] + rk1 * pl.n[1] + rk2 * pl.n[2]);
+                }
+                const float gA[3] = {gq[10], gq[11], gq[12]}, gB[3] = {gq[13], gq[14], gq[15]};
+                float gG[3], gPx[3], gPy[3], gm[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+                    // d(Px x G): G gets gA x Px, Px gets G x gA (likewise for B = Py x G)
+                    gG[k] = 2.0f * gq[0] * G[k] + gq[1] * Px[k] + gq[2] * Py[k] + gq[7] * m[k] +
+                            (gA[k1] * Px[k2] - gA[k2] * Px[k1]) + (gB[k1] * Py[k2] - gB[k2] * Py[k1]);
+                    gPx[k] = gq[1] * G[k] + 2.0f * gq[4] * Px[k] + gq[5] * Py[k] + gq[8] * m[k] +
+                             (G[k1] * gA[k2] - G[k2] * gA[k1]);
+                    gPy[k] = gq[2] * G[k] + gq[5] * Px[k] + 2.0f * gq[6] * Py[k] + gq[9] * m[k] +
+                             (G[k1] * gB[k2] - G[k2] * gB[k1]);
+                    gm[k] = gq[7] * G[k] + gq[8] * Px[k] + gq[9] * Py[k];
+                }
+                const float gdep = gq[3];
+                float gtz_p = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float iks = 1.0f / (kk * sg[k]);
+                    gsg[k] += (-gG[k] * G[k] - gPx[k] * Px[k] - gPy[k] * Py[k] + gm[k] * m[k]) / sg[k];
+                    gtz_p += gPx[k] * Px[k] + gPy[k] * Py[k];
                     const float aG = iks * gG[k], aPx = iks * sx * gPx[k], aPy = iks * sy * gPy[k];
                     const float am = kk * sg[k] * gm[k];
 #pragma unroll

@@ -15,6 +15,18 @@ namespace rara {
 
 namespace {
 
+__device__ __forceinline__ float dot3(const float a[3], const float b[3])
+{
+    return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
+}
+
+__device__ __forceinline__ void cross3(const float a[3], const float b[3], float out[3])
+{
+    out[0] = fmaf(a[1], b[2], -a[2] * b[1]);
+    out[1] = fmaf(a[2], b[0], -a[0] * b[2]);
+    out[2] = fmaf(a[0], b[1], -a[1] * b[0]);
+}
+
 // Colour along the unit direction (x, y, z): sum_k sh_k Y_k + 0.5, clamped at 0. The
 // thread's coefficients are staged in shared memory, s_sh[(k * 3 + c) * kBlock + thread].
 __device__ __forceinline__ void sh_colour(const float *s_sh, int degree, float x, float y, float z, float rgb[3])
@@ -124,13 +136,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_preprocess(PreprocessArgs a)
                     const float J00 = cam.fx * itz, J02 = -cam.fx * txz * itz;
                     const float J11 = cam.fy * itz, J12 = -cam.fy * tyz * itz;
                     float T0[3], T1[3];
-    #pragma unroll
+#pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         T0[k] = fmaf(J00, cam.R[k], J02 * cam.R[6 + k]);
                         T1[k] = fmaf(J11, cam.R[3 + k], J12 * cam.R[6 + k]);
                     }
                     float A0[3], A1[3];  // rows of J W R S
-    #pragma unroll
+#pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         A0[k] = (T0[0] * Rg[k] + T0[1] * Rg[3 + k] + T0[2] * Rg[6 + k]) * sg[k];
                         A1[k] = (T1[0] * Rg[k] + T1[1] * Rg[3 + k] + T1[2] * Rg[6 + k]) * sg[k];
@@ -190,7 +202,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_preprocess(PreprocessArgs a)
                                 const float iks[3] = {1.0f / (kk * s0), 1.0f / (kk * s1), 1.0f / (kk * s2)};
                                 float G[3], Px[3], Py[3], m[3];
                                 const float sx = tz / cam.fx, sy = tz / cam.fy;
-    #pragma unroll
+#pragma unroll
                                 for (int k = 0; k < 3; ++k) {
                                     const float rk0 = Rg[k], rk1 = Rg[3 + k], rk2 = Rg[6 + k];  // column k of R
                                     G[k] = iks[k] * (rk0 * ex + rk1 * ey + rk2 * ez);
@@ -207,11 +219,17 @@ __global__ void __launch_bounds__(kBlock, 4) k_preprocess(PreprocessArgs a)
                                 const float bound = mlen * (1.0f + 1e-4f);
                                 wmode = dep > bound ? kWeightNone : (dep < -bound ? kWeightHidden : kWeightSplit);
                                 if (wmode != kWeightNone) {
+                                    // The render needs, per pixel, p = P (dx, dy) only through the
+                                    // dot products G.p, p.p, m.p and the cross product p x G: store
+                                    // the pairwise products of G, Px, Py, m and A = Px x G, B = Py x G.
                                     CutRec c;
-                                    c.c0 = make_float4(G[0], G[1], G[2], dep);
-                                    c.c1 = make_float4(Px[0], Px[1], Px[2], m[0]);
-                                    c.c2 = make_float4(Py[0], Py[1], Py[2], m[1]);
-                                    c.c3 = make_float4(m[2], 0.0f, 0.0f, 0.0f);
+                                    c.c0 = make_float4(dot3(G, G), dot3(G, Px), dot3(G, Py), dep);
+                                    c.c1 = make_float4(dot3(Px, Px), dot3(Px, Py), dot3(Py, Py), dot3(m, G));
+                                    float A[3], B[3];
+                                    cross3(Px, G, A);
+                                    cross3(Py, G, B);
+                                    c.c2 = make_float4(dot3(m, Px), dot3(m, Py), A[0], A[1]);
+                                    c.c3 = make_float4(A[2], B[0], B[1], B[2]);
                                     a.cut[slot] = c;
                                 }
                             }

@@ -57,11 +57,13 @@ struct __align__(16) SplatRec {
 constexpr float kWeightNone = 0.0f, kWeightSplit = 1.0f, kWeightHidden = 2.0f;
 
 // Per-cutoff-slot ray-tracing record, 4 x float4 = 64 bytes, relative to the Gaussian's own
-// frame (see preprocess.cu for the derivation):
-//   c0 = (G.x, G.y, G.z, d_ep)         G = M^-1 (mu - e), d_ep = n.mu + d
-//   c1 = (P00, P10, P20, m.x)          P: 3x2 map from a pixel offset to the local ray
-//   c2 = (P01, P11, P21, m.y)              offset, scaled by the centre depth
-//   c3 = (m.z, 0, 0, 0)                m = M^T n
+// frame (see preprocess.cu for the derivation). With G = M^-1 (mu - e), the columns Px, Py
+// of the 3x2 map P from a pixel offset to the local ray offset (scaled by the centre
+// depth), m = M^T n and d_ep = n.mu + d, the record holds their products:
+//   c0 = (G.G, G.Px, G.Py, d_ep)
+//   c1 = (Px.Px, Px.Py, Py.Py, m.G)
+//   c2 = (m.Px, m.Py, A.x, A.y)        A = Px x G
+//   c3 = (A.z, B.x, B.y, B.z)          B = Py x G
 struct __align__(16) CutRec {
     float4 c0, c1, c2, c3;
 };
@@ -218,17 +220,15 @@ struct RenderArgs {
 void launch_render(const RenderArgs &a, int grid, cudaStream_t s);
 int render_blocks_per_sm();
 
-// Backward. Per-slot gradient record, 6 x float4 = 96 bytes, accumulated (atomics) by the
+// Backward. Per-slot gradient record, 7 x float4 = 112 bytes, accumulated (atomics) by the
 // render backward and read by the preprocess backward:
-//   g0 = (dL/dmean2d.x, dL/dmean2d.y, dL/dconic.a, dL/dconic.b)
-//   g1 = (dL/dconic.c, dL/dopacity, dL/drgb.r, dL/drgb.g)
-//   g2 = (dL/drgb.b, dL/dd_ep, dL/dm.x, dL/dm.y)
-//   g3 = (dL/dm.z, dL/dG.x, dL/dG.y, dL/dG.z)
-//   g4 = (dL/dP00, dL/dP10, dL/dP20, dL/dP01)
-//   g5 = (dL/dP11, dL/dP21, 0, 0)
-// with the fields of SplatRec / CutRec (conic.b is the off-diagonal entry, which q uses twice).
+//   v[0..8]   dL/d(mean2d.x, mean2d.y, conic.a, conic.b, conic.c, opacity, rgb.r, rgb.g, rgb.b)
+//   v[9..24]  dL/d(the 16 products of the CutRec, in its order), split-weight slots only
+//   v[25..27] unused
+// conic.b is the off-diagonal entry, which q uses twice.
+constexpr int kGradCut = 9;
 struct __align__(16) GradRec {
-    float4 g0, g1, g2, g3, g4, g5;
+    float v[28];
 };
 
 struct BwdView {

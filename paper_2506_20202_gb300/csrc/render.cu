@@ -18,18 +18,18 @@
 // would have been skipped pixel by pixel.
 //
 // Decay weight (Eq. 4-8, Eq. 11, Algorithm 1 step 2), evaluated in the unit-sphere frame
-// of the ellipsoid M = k R S without forming t1, t2 or t_p explicitly:
+// of the ellipsoid M = k R S without forming t1, t2 or t_p explicitly (render_common.cuh):
 //   local ray   u(tau) = -G + tau V,  V = G + p,  p = P (dx, dy)   (tau = 1 at the centre
 //               depth for the central ray; dx, dy = pixel offset from the projected centre)
-//   chord       the closest point to the origin is c = p - (p.V / V.V) V (the component of
-//               p orthogonal to V: no cancellation between the large G and the small p);
-//               the ray meets the sphere iff |c| < 1, at tau_mid -/+ h with
-//               tau_mid = G.V / V.V and h = sqrt(1 - |c|^2) / |V|
-//   in front    t1 > 0  <=>  G.V > 0 and (G.V)^2 > (1 - |c|^2) V.V
+//   chord       the ray meets the sphere iff its squared distance from the centre,
+//               cc = |p x G|^2 / V.V, is below 1; the chord's midpoint is c = p - (p.V/V.V) V
+//   in front    t1 > 0  <=>  G.V > 0 and (G.V)^2 > (1 - cc) V.V
 //   plane       s(u) = d_ep + m . u with m = M^T n, linear along the ray:
-//               s1,2 = d_ep + m.c -/+ sqrt(1 - |c|^2) (m.V) / |V|
+//               s1,2 = d_ep + m.c -/+ sqrt(1 - cc) (m.V) / |V|
 //   weight      both >= 0: 1; both < 0: 0; otherwise the visible share of the chord,
 //               max(s1, s2) / |s2 - s1|  (= (t2 - t_p)/(t2 - t1) or (t_p - t1)/(t2 - t1)).
+// Everything is a polynomial in (dx, dy) with coefficients the products of G, P and m that
+// the preprocess stores, so a pixel needs about 50 instructions for the full weight.
 // Because w <= 1, an entry whose unweighted alpha is already below 1/255 is skipped before
 // the weight is computed (the weighted alpha could only be smaller). The preprocess marks
 // which cutoff Gaussians the plane actually meets (|d_ep| <= |m|); only those evaluate the
@@ -64,7 +64,7 @@ __device__ __forceinline__ float entry_alpha(const Stage &st, int j, float pxf, 
             alpha *= rara_weight(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
             ++ty.cut;
         } else {
-            alpha *= rara_weight_hidden(st.c0[j], st.c1[j], st.c2[j], dx, dy);
+            alpha *= rara_weight_hidden(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
         }
     }
     alpha = fminf(kAlphaMax, alpha);
