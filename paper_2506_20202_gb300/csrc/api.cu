@@ -461,8 +461,8 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
                   (int2 *)c->ranges.p, rgrid, s);
     if ((rc = launched(c, "ranges"))) return rc;
     launch_tile_order((const int2 *)c->ranges.p, (int)c->num_tiles, c->split2_bits, c->split4_bits,
-                      (uint32_t *)c->items.p, dc, s);
-    return launched(c, "tile order", c->num_tiles > 0);
+                      (uint32_t *)c->items.p, dc, c->sm_count * 2, s);
+    return launched(c, "tile order", c->num_tiles > 0 ? 2 : 0);
 }
 
 // Stages (c)+(d): the render of every view.

@@ -129,54 +129,99 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
     if (overflow) atomicOr(&a.counters->status, kStatusOverflow);
 }
 
+// Ranges: each thread takes 4 consecutive keys (one 16-byte load) and compares them with
+// their neighbours; a tile's range starts and ends where its id changes.
 __global__ void k_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const Counters *counters,
                          uint32_t cap_pairs, uint32_t num_tiles, int2 *__restrict__ ranges)
 {
     const unsigned long long np = counters->n_pairs;
     const uint32_t n = (uint32_t)(np < cap_pairs ? np : cap_pairs);
     const uint32_t *keys = counters->tile_in_b ? keys_b : keys_a;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t t = keys[i];
-        if (t >= num_tiles) continue;
-        if (i == 0 || keys[i - 1] != t) ranges[t].x = (int)i;
-        if (i == n - 1 || keys[i + 1] != t) ranges[t].y = (int)(i + 1);
+    const uint32_t nq = (n + 3) / 4;
+    constexpr uint32_t kNone = 0xffffffffu;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const uint32_t i0 = 4 * q;
+        uint32_t k[4];
+        if (i0 + 4 <= n) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(keys + i0));
+            k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) k[r] = i0 + r < n ? __ldg(&keys[i0 + r]) : kNone;
+        }
+        const uint32_t prev = i0 > 0 ? __ldg(&keys[i0 - 1]) : kNone;
+        const uint32_t next = i0 + 4 < n ? __ldg(&keys[i0 + 4]) : kNone;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint32_t t = k[r];
+            if (t >= num_tiles) continue;  // also the padding past n
+            const uint32_t before = r > 0 ? k[r - 1] : prev;
+            const uint32_t after = r < 3 ? k[r + 1] : next;
+            if (before != t) ranges[t].x = (int)(i0 + r);
+            if (after != t) ranges[t].y = (int)(i0 + r + 1);
+        }
     }
 }
 
-// One block: bucket the tiles by the bit length of their list length, longest first, and
-// expand heavy tiles into 2 or 4 work items. The order inside a bucket is whatever the
-// atomics give; it only affects scheduling, never the image.
-__global__ void __launch_bounds__(1024) k_tile_order(const int2 *__restrict__ ranges, int num_tiles, int split2_bits,
-                                                     int split4_bits, uint32_t *__restrict__ order,
-                                                     Counters *__restrict__ counters)
+// Render work order, heaviest first: tiles are bucketed by the bit length of their list
+// length (bucket 32 - bits), and a heavy tile becomes 2 or 4 items. Two launches over all
+// tiles: bucket counts, then each block reserves its run in every bucket and writes its
+// items there. The order inside a bucket follows the atomics; it only affects scheduling,
+// never the image.
+__device__ __forceinline__ unsigned items_of(int bits, int split2_bits, int split4_bits)
+{
+    return bits >= split4_bits ? 2u : (bits >= split2_bits ? 1u : 0u);  // log2 of the items
+}
+
+__global__ void __launch_bounds__(kBlock) k_order_hist(const int2 *__restrict__ ranges, int num_tiles,
+                                                       Counters *__restrict__ counters)
 {
     __shared__ unsigned s_cnt[33];
     if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (int t = threadIdx.x; t < num_tiles; t += blockDim.x) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < num_tiles; t += gridDim.x * blockDim.x) {
         const int2 r = ranges[t];
-        atomicAdd(&s_cnt[__clz((unsigned)(r.y - r.x))], 1u);  // bucket = 32 - bit length
+        atomicAdd(&s_cnt[__clz((unsigned)(r.y - r.x))], 1u);
     }
     __syncthreads();
+    if (threadIdx.x < 33 && s_cnt[threadIdx.x]) atomicAdd(&counters->order_hist[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(kBlock) k_order_scatter(const int2 *__restrict__ ranges, int num_tiles,
+                                                          int split2_bits, int split4_bits,
+                                                          uint32_t *__restrict__ order, Counters *__restrict__ counters)
+{
+    __shared__ unsigned s_base[33], s_cnt[33];
     if (threadIdx.x == 0) {
         unsigned acc = 0;
         for (int b = 0; b < 33; ++b) {
-            const int bits = 32 - b;
-            const unsigned per = bits >= split4_bits ? 4u : (bits >= split2_bits ? 2u : 1u);
-            const unsigned c = s_cnt[b];
-            s_cnt[b] = acc;
-            acc += c * per;
+            s_base[b] = acc;
+            acc += counters->order_hist[b] << items_of(32 - b, split2_bits, split4_bits);
         }
-        counters->num_items = acc;
+        if (blockIdx.x == 0) counters->num_items = acc;
     }
+    if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (int t = threadIdx.x; t < num_tiles; t += blockDim.x) {
+    const int chunk = (num_tiles + gridDim.x - 1) / gridDim.x;
+    const int t0 = blockIdx.x * chunk, t1 = min(num_tiles, t0 + chunk);
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
         const int2 r = ranges[t];
         const int b = __clz((unsigned)(r.y - r.x));
-        const int bits = 32 - b;
-        const unsigned lg = bits >= split4_bits ? 2u : (bits >= split2_bits ? 1u : 0u);
+        atomicAdd(&s_cnt[b], 1u << items_of(32 - b, split2_bits, split4_bits));
+    }
+    __syncthreads();
+    if (threadIdx.x < 33) {
+        const unsigned c = s_cnt[threadIdx.x];
+        s_base[threadIdx.x] += c ? atomicAdd(&counters->order_cursor[threadIdx.x], c) : 0u;
+        s_cnt[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        const int2 r = ranges[t];
+        const int b = __clz((unsigned)(r.y - r.x));
+        const unsigned lg = items_of(32 - b, split2_bits, split4_bits);
         const unsigned per = 1u << lg;
-        const unsigned pos = atomicAdd(&s_cnt[b], per);
+        const unsigned pos = s_base[b] + atomicAdd(&s_cnt[b], per);
         for (unsigned p = 0; p < per; ++p) order[pos + p] = ((uint32_t)t << 4) | (lg << 2) | p;
     }
 }
@@ -254,10 +299,13 @@ void launch_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const Counter
 }
 
 void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int split4_bits, uint32_t *order,
-                       Counters *counters, cudaStream_t s)
+                       Counters *counters, int grid, cudaStream_t s)
 {
-    if (num_tiles > 0)
-        k_tile_order<<<1, 1024, 0, s>>>(ranges, num_tiles, split2_bits, split4_bits, order, counters);
+    if (num_tiles <= 0) return;
+    const int want = (num_tiles + kBlock * 4 - 1) / (kBlock * 4);
+    const int g = want < grid ? want : grid;
+    k_order_hist<<<g, kBlock, 0, s>>>(ranges, num_tiles, counters);
+    k_order_scatter<<<g, kBlock, 0, s>>>(ranges, num_tiles, split2_bits, split4_bits, order, counters);
 }
 
 void launch_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_src, const uint32_t *tiles_src,

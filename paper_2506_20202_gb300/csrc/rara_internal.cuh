@@ -125,6 +125,8 @@ struct Counters {
     unsigned int tile_in_b;              // 1 if the tile sort's result is in its B buffers
     unsigned int ticket[13];             // partition tickets of the persistent kernels
     unsigned int bwd_queue;              // next entry of the item order (render backward)
+    unsigned int order_hist[33];         // tiles per list-length bucket (item order)
+    unsigned int order_cursor[33];       // items placed per bucket (item order)
 };
 constexpr size_t kRenderCounterBytes = 4 * sizeof(unsigned long long) + sizeof(unsigned int);
 // ticket slots
@@ -204,7 +206,7 @@ void launch_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const Counter
 // per pixel), otherwise 1 item. Item = tile << 4 | log2(lanes per pixel) << 2 | part.
 // order holds 4 * num_tiles entries; the item count goes to counters->num_items.
 void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int split4_bits, uint32_t *order,
-                       Counters *counters, cudaStream_t s);
+                       Counters *counters, int grid, cudaStream_t s);
 
 // Stage 8: render
 struct RenderArgs {
