@@ -45,7 +45,9 @@ struct rara_ctx {
     int stage = 0;  // 0 empty, 1 preprocessed, 2 binned
     int num_views = 0, num_scenes = 0;
     uint32_t num_slots = 0, num_tiles = 0, num_units = 0;
-    int tile_passes = 1;
+    int tile_bits = 0;                  // global tile id = internal view << tile_bits | local tile
+    int tile_passes = 1;                // digit passes of the tile sort
+    int view_passes = 0;                // view digit passes of the depth sort (several views)
     uint32_t cap_pairs = 0;             // pair capacity the binning kernels were launched with
     cudaStream_t last_stream = nullptr;
     int max_views = 0, max_scenes = 0;
@@ -63,7 +65,7 @@ struct rara_ctx {
     DevBuf labels, tiles, rect, rec, cut, depth;
     DevBuf ckeys, cvals, ckeys_b, cvals_b, lookback_c;
     DevBuf pkeys, pvals, pkeys_b, pvals_b, lookback_e;
-    DevBuf hist, ranges, items, sort_scratch;
+    DevBuf hist, ranges, items, sort_scratch, seg_base, export_off;
 
     // captured batch
     cudaStream_t cap_stream = nullptr;
@@ -271,6 +273,13 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
         if (!views[v].image) return fail(c, RARA_ERR_INVALID_ARG, "view %d has no image buffer", v);
     }
     if ((rc = next_staging(c))) return rc;
+    uint64_t max_tiles = 1;
+    for (int v = 0; v < nv; ++v) {
+        const uint64_t t = (uint64_t)((views[v].camera.width + kTile - 1) / kTile) *
+                           (uint64_t)((views[v].camera.height + kTile - 1) / kTile);
+        if (t > max_tiles) max_tiles = t;
+    }
+    const int tile_bits = ceil_bits((uint32_t)(max_tiles < 0xffffffffull ? max_tiles : 0xffffffffull));
     uint64_t slots = 0, tiles = 0;
     uint32_t units = 0;
     int k = 0;
@@ -288,7 +297,7 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
             ViewDev &vd = c->h_views[k];
             fill_view(vd, &views[v].camera, &views[v].plane);
             vd.scene = si;
-            vd.tile_base = (uint32_t)tiles;
+            vd.tile_base = (uint32_t)((uint64_t)k << tile_bits);
             vd.slot_base = (uint32_t)slots;
             for (int j = 0; j < 3; ++j) vd.bg[j] = views[v].bg[j];
             vd.image = views[v].image;
@@ -296,13 +305,13 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
             vd.n_contrib = views[v].n_contrib;
             c->h_view_map[v] = k;
             c->h_view_n[k] = (int)g.n;
-            tiles += (uint64_t)vd.tiles_x * vd.tiles_y;
             slots += (uint64_t)g.n;
             ++k;
         }
         sd.view_count = k - sd.view_begin;
         if (sd.view_count > 0) units += (uint32_t)((g.n + kBlock - 1) / kBlock);
     }
+    tiles = (uint64_t)nv << tile_bits;
     if (slots >= ((uint64_t)1 << 32) - 1)
         return fail(c, RARA_ERR_INVALID_ARG, "%llu slots exceed 2^32", (unsigned long long)slots);
     if (tiles >= ((uint64_t)1 << 28))
@@ -312,8 +321,10 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
     c->num_slots = (uint32_t)slots;
     c->num_tiles = (uint32_t)tiles;
     c->num_units = units;
-    c->tile_passes = (ceil_bits(c->num_tiles) + 7) / 8;
+    c->tile_bits = tile_bits;
+    c->tile_passes = (tile_bits + 7) / 8;
     if (c->tile_passes < 1) c->tile_passes = 1;
+    c->view_passes = nv > 256 ? 2 : (nv > 1 ? 1 : 0);
     const size_t nn = slots > 0 ? (size_t)slots : 1;
     const size_t nt = tiles > 0 ? (size_t)tiles : 1;
     if ((rc = ensure(c, c->views_d, sizeof(ViewDev) * (size_t)nv, "view table")) ||
@@ -327,7 +338,8 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
         (rc = ensure(c, c->cvals_b, nn * 4, "depth values B")) ||
         (rc = ensure(c, c->lookback_c, (nn / 1024 + 2) * 8, "compaction scan words")) ||
         (rc = ensure(c, c->lookback_e, (nn / kBlock + 2) * 8, "emission scan words")) ||
-        (rc = ensure(c, c->hist, 8 * 256 * 4, "digit histograms")) ||
+        (rc = ensure(c, c->hist, kHistPasses * 256 * 4, "digit histograms")) ||
+        (rc = ensure(c, c->seg_base, sizeof(uint32_t) * (size_t)nv, "view slot bases")) ||
         (rc = ensure(c, c->ranges, nt * sizeof(int2), "ranges")) ||
         (rc = ensure(c, c->items, nt * 16, "render items")))
         return rc;
@@ -345,7 +357,7 @@ int batch_preprocess(rara_ctx *c, cudaStream_t s)
     if ((rc = check_cuda(c, cudaMemsetAsync(dc, 0, sizeof(Counters), s), "memset counters")) ||
         (rc = check_cuda(c, cudaMemsetAsync(c->view_counters_d.p, 0, sizeof(ViewCounters) * (size_t)c->num_views, s),
                          "memset view counters")) ||
-        (rc = check_cuda(c, cudaMemsetAsync(c->hist.p, 0, 8 * 256 * 4, s), "memset histograms")) ||
+        (rc = check_cuda(c, cudaMemsetAsync(c->hist.p, 0, kHistPasses * 256 * 4, s), "memset histograms")) ||
         (rc = check_cuda(c, cudaMemsetAsync(c->lookback_c.p, 0, (nn / 1024 + 2) * 8, s), "memset scan")))
         return rc;
     PreprocessArgs a;
@@ -375,6 +387,10 @@ int batch_preprocess(rara_ctx *c, cudaStream_t s)
     ca.keys = (uint32_t *)c->ckeys.p;
     ca.vals = (uint32_t *)c->cvals.p;
     ca.hist = (uint32_t *)c->hist.p;
+    ca.views = (const ViewDev *)c->views_d.p;
+    ca.view_counters = (const ViewCounters *)c->view_counters_d.p;
+    ca.num_views = c->num_views;
+    ca.seg_base = (uint32_t *)c->seg_base.p;
     ca.lookback = (unsigned long long *)c->lookback_c.p;
     ca.counters = dc;
     const uint32_t parts = (c->num_slots + 1023) / 1024;
@@ -400,7 +416,8 @@ int ensure_pairs(rara_ctx *c, uint32_t cap)
 {
     const size_t pp = cap > 0 ? (size_t)cap : 1;
     const size_t nn = c->num_slots > 0 ? (size_t)c->num_slots : 1;
-    const size_t sb1 = sort_scratch_bytes((int64_t)nn, 4), sb2 = sort_scratch_bytes((int64_t)pp, c->tile_passes);
+    const size_t sb1 = sort_scratch_bytes((int64_t)nn, 4 + c->view_passes);
+    const size_t sb2 = sort_scratch_bytes((int64_t)pp, c->tile_passes);
     int rc;
     if ((rc = ensure(c, c->pkeys, pp * 4, "pair keys")) || (rc = ensure(c, c->pvals, pp * 4, "pair values")) ||
         (rc = ensure(c, c->pkeys_b, pp * 4, "pair keys B")) || (rc = ensure(c, c->pvals_b, pp * 4, "pair values B")) ||
@@ -422,8 +439,10 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
     mark(c, 1, s);
     const int sgrid = c->sm_count * c->bpsm_sort;
     int nl = sort_launch((uint32_t *)c->ckeys.p, (uint32_t *)c->cvals.p, (uint32_t *)c->ckeys_b.p,
-                         (uint32_t *)c->cvals_b.p, &dc->n_rendered, (uint32_t)nn, 4, hist, c->sort_scratch.p,
-                         &dc->ticket[kTicketSortDepth], &dc->status, &dc->depth_in_b, sgrid, s);
+                         (uint32_t *)c->cvals_b.p, &dc->n_rendered, (uint32_t)nn, 4 + c->view_passes,
+                         hist + kHistDepth * 256, c->sort_scratch.p, &dc->ticket[kTicketSortDepth], &dc->status,
+                         &dc->depth_in_b, sgrid, s, (const uint32_t *)c->seg_base.p,
+                         c->view_passes ? c->num_views : 0, 4);
     if ((rc = launched(c, "depth sort", nl))) return rc;
 
     if ((rc = check_cuda(c, cudaMemsetAsync(c->lookback_e.p, 0, (nn / kBlock + 2) * 8, s), "memset emit")))
@@ -441,14 +460,14 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
     e.tile_passes = c->tile_passes;
     e.pair_keys = (uint32_t *)c->pkeys.p;
     e.pair_vals = (uint32_t *)c->pvals.p;
-    e.tile_hist = hist + 4 * 256;
+    e.tile_hist = hist + kHistTile * 256;
     e.lookback = (unsigned long long *)c->lookback_e.p;
     e.counters = dc;
     launch_emit(e, c->sm_count * c->bpsm_emit, s);
     if ((rc = launched(c, "emit"))) return rc;
 
     nl = sort_launch((uint32_t *)c->pkeys.p, (uint32_t *)c->pvals.p, (uint32_t *)c->pkeys_b.p,
-                     (uint32_t *)c->pvals_b.p, &dc->n_pairs, cap, c->tile_passes, hist + 4 * 256, c->sort_scratch.p,
+                     (uint32_t *)c->pvals_b.p, &dc->n_pairs, cap, c->tile_passes, hist + kHistTile * 256, c->sort_scratch.p,
                      &dc->ticket[kTicketSortTile], &dc->status, &dc->tile_in_b, sgrid, s);
     if ((rc = launched(c, "tile sort", nl))) return rc;
 
@@ -461,7 +480,7 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
                   (int2 *)c->ranges.p, rgrid, s);
     if ((rc = launched(c, "ranges"))) return rc;
     launch_tile_order((const int2 *)c->ranges.p, (int)c->num_tiles, c->split2_bits, c->split4_bits,
-                      (uint32_t *)c->items.p, dc, c->sm_count * 2, s);
+                      (uint32_t *)c->items.p, dc, (const ViewDev *)c->views_d.p, c->tile_bits, c->sm_count * 2, s);
     return launched(c, "tile order", c->num_tiles > 0 ? 2 : 0);
 }
 
@@ -585,7 +604,8 @@ int rara_ctx_destroy(rara_ctx *c)
     DevBuf *all[] = {&c->views_d, &c->scenes_d, &c->view_counters_d, &c->counters, &c->labels, &c->tiles,
                      &c->rect, &c->rec, &c->cut, &c->depth, &c->ckeys, &c->cvals, &c->ckeys_b, &c->cvals_b,
                      &c->lookback_c, &c->pkeys, &c->pvals, &c->pkeys_b, &c->pvals_b, &c->lookback_e, &c->hist,
-                     &c->ranges, &c->items, &c->sort_scratch, &c->grec, &c->bviews_d, &c->bscenes_d};
+                     &c->ranges, &c->items, &c->sort_scratch, &c->grec, &c->bviews_d, &c->bscenes_d,
+                     &c->seg_base, &c->export_off};
     for (DevBuf *b : all) release(c, *b);
     free_host(c);
     delete c;
@@ -999,24 +1019,31 @@ int rara_frame_pairs(rara_ctx *c, int32_t view, uint64_t *keys, uint32_t *values
     const int nt = v.tiles_x * v.tiles_y;
     int rc = rara_ctx_sync(c, c->last_stream);
     if (rc) return rc;
-    // the view's pairs are contiguous (its tile ids are contiguous): find their span
+    // the view's lists, in local tile order: output offsets from the list lengths
     int2 *hr = (int2 *)malloc(sizeof(int2) * (size_t)(nt > 0 ? nt : 1));
-    if (!hr) return fail(c, RARA_ERR_BUDGET, "host allocation failed");
+    uint32_t *ho = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(nt > 0 ? nt : 1));
+    if (!hr || !ho) {
+        free(hr);
+        free(ho);
+        return fail(c, RARA_ERR_BUDGET, "host allocation failed");
+    }
     rc = check_cuda(c, cudaMemcpy(hr, (const int2 *)c->ranges.p + v.tile_base, sizeof(int2) * (size_t)nt,
                                   cudaMemcpyDeviceToHost), "ranges copy");
-    uint32_t lo = 0xffffffffu, hi = 0;
-    for (int t = 0; t < nt && !rc; ++t)
-        if (hr[t].y > hr[t].x) {
-            if ((uint32_t)hr[t].x < lo) lo = (uint32_t)hr[t].x;
-            if ((uint32_t)hr[t].y > hi) hi = (uint32_t)hr[t].y;
-        }
+    uint32_t acc = 0;
+    for (int t = 0; t < nt && !rc; ++t) {
+        ho[t] = acc;
+        if (hr[t].y > hr[t].x) acc += (uint32_t)(hr[t].y - hr[t].x);
+    }
+    if (!rc) rc = ensure(c, c->export_off, sizeof(uint32_t) * (size_t)(nt > 0 ? nt : 1), "export offsets");
+    if (!rc)
+        rc = check_cuda(c, cudaMemcpy(c->export_off.p, ho, sizeof(uint32_t) * (size_t)nt, cudaMemcpyHostToDevice),
+                        "offsets upload");
     free(hr);
+    free(ho);
     if (rc) return rc;
-    if (lo > hi) lo = hi = 0;
-    launch_export_pairs((const uint32_t *)c->pkeys.p, (const uint32_t *)c->pvals.p, (const uint32_t *)c->pkeys_b.p,
-                        (const uint32_t *)c->pvals_b.p, (const Counters *)c->counters.p, (const float *)c->depth.p,
-                        (const int2 *)c->ranges.p, v.tile_base, v.slot_base, nt, lo, hi, keys, values, ranges,
-                        (cudaStream_t)stream);
+    launch_export_pairs((const uint32_t *)c->pvals.p, (const uint32_t *)c->pvals_b.p, (const Counters *)c->counters.p,
+                        (const float *)c->depth.p, (const int2 *)c->ranges.p, v.tile_base, v.slot_base, nt,
+                        (const uint32_t *)c->export_off.p, keys, values, ranges, (cudaStream_t)stream);
     return launched(c, "export pairs", 1);
 }
 
@@ -1054,7 +1081,8 @@ constexpr size_t kSzCut = align256((size_t)kStaticMaxGaussians * sizeof(CutRec))
 constexpr size_t kSzLookC = align256((size_t)(kStaticMaxGaussians / 1024 + 2) * 8);
 constexpr size_t kSzLookE = align256((size_t)(kStaticMaxGaussians / kBlock + 2) * 8);
 constexpr size_t kSzU32P = align256((size_t)kStaticMaxPairs * 4);
-constexpr size_t kSzHist = align256(8 * 256 * 4);
+constexpr size_t kSzHist = align256(kHistPasses * 256 * 4);
+constexpr size_t kSzSeg = align256(sizeof(uint32_t));
 constexpr size_t kSzRanges = align256((size_t)kStaticMaxTiles * sizeof(int2));
 constexpr size_t kSzOrder = align256((size_t)kStaticMaxTiles * 16);
 // sort scratch for 4 digit passes over kStaticMaxPairs keys, sized for partitions as small as
@@ -1062,7 +1090,7 @@ constexpr size_t kSzOrder = align256((size_t)kStaticMaxTiles * 16);
 constexpr size_t kSzSort = align256(4 * (4 * (size_t)((kStaticMaxPairs + 1023) / 1024) * 256));
 constexpr size_t kStaticBytes = kSzCounters + kSzViews + kSzScenes + kSzViewCounters + kSzLabels + 2 * kSzU32G +
                                 kSzRect + kSzRec + kSzCut + 4 * kSzU32G + kSzLookC + kSzLookE + 4 * kSzU32P +
-                                kSzHist + kSzRanges + kSzOrder + kSzSort;
+                                kSzHist + kSzSeg + kSzRanges + kSzOrder + kSzSort;
 
 static __device__ __align__(256) unsigned char g_rara_static_scratch[kStaticBytes];
 
@@ -1110,6 +1138,7 @@ int static_setup(int dev)
     take(c->pkeys_b, kSzU32P);
     take(c->pvals_b, kSzU32P);
     take(c->hist, kSzHist);
+    take(c->seg_base, kSzSeg);
     take(c->ranges, kSzRanges);
     take(c->items, kSzOrder);
     take(c->sort_scratch, kSzSort);

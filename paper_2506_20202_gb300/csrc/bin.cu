@@ -6,7 +6,9 @@
 // build sorts the rendered slots by depth once (one entry per slot instead of one per
 // pair), emits each slot's pairs in that order, and finishes with the tile-id digit passes
 // over the pairs. The result is the same list as the full stable key sort. Tile ids are
-// global over the batch (view tile base + ty * tiles_x + tx), so one sort serves all views.
+// global over the batch (view << tile_bits | ty * tiles_x + tx); with several views the
+// slots are ordered by (view, depth) before the emission, so each view's pairs are
+// contiguous and the tile sort only needs the local tile bits.
 #include "chained_scan.cuh"
 #include "rara_internal.cuh"
 
@@ -173,13 +175,22 @@ __device__ __forceinline__ unsigned items_of(int bits, int split2_bits, int spli
     return bits >= split4_bits ? 2u : (bits >= split2_bits ? 1u : 0u);  // log2 of the items
 }
 
+// A global tile id is a real tile unless it is a hole past its view's last tile.
+__device__ __forceinline__ bool real_tile(const ViewDev *views, int tile_bits, int t)
+{
+    const ViewDev &v = views[t >> tile_bits];
+    return (t & ((1 << tile_bits) - 1)) < v.tiles_x * v.tiles_y;
+}
+
 __global__ void __launch_bounds__(kBlock) k_order_hist(const int2 *__restrict__ ranges, int num_tiles,
-                                                       Counters *__restrict__ counters)
+                                                       Counters *__restrict__ counters, const ViewDev *views,
+                                                       int tile_bits)
 {
     __shared__ unsigned s_cnt[33];
     if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < num_tiles; t += gridDim.x * blockDim.x) {
+        if (!real_tile(views, tile_bits, t)) continue;
         const int2 r = ranges[t];
         atomicAdd(&s_cnt[__clz((unsigned)(r.y - r.x))], 1u);
     }
@@ -189,7 +200,8 @@ __global__ void __launch_bounds__(kBlock) k_order_hist(const int2 *__restrict__ 
 
 __global__ void __launch_bounds__(kBlock) k_order_scatter(const int2 *__restrict__ ranges, int num_tiles,
                                                           int split2_bits, int split4_bits,
-                                                          uint32_t *__restrict__ order, Counters *__restrict__ counters)
+                                                          uint32_t *__restrict__ order, Counters *__restrict__ counters,
+                                                          const ViewDev *views, int tile_bits)
 {
     __shared__ unsigned s_base[33], s_cnt[33];
     if (threadIdx.x == 0) {
@@ -205,6 +217,7 @@ __global__ void __launch_bounds__(kBlock) k_order_scatter(const int2 *__restrict
     const int chunk = (num_tiles + gridDim.x - 1) / gridDim.x;
     const int t0 = blockIdx.x * chunk, t1 = min(num_tiles, t0 + chunk);
     for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        if (!real_tile(views, tile_bits, t)) continue;
         const int2 r = ranges[t];
         const int b = __clz((unsigned)(r.y - r.x));
         atomicAdd(&s_cnt[b], 1u << items_of(32 - b, split2_bits, split4_bits));
@@ -217,6 +230,7 @@ __global__ void __launch_bounds__(kBlock) k_order_scatter(const int2 *__restrict
     }
     __syncthreads();
     for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        if (!real_tile(views, tile_bits, t)) continue;
         const int2 r = ranges[t];
         const int b = __clz((unsigned)(r.y - r.x));
         const unsigned lg = items_of(32 - b, split2_bits, split4_bits);
@@ -251,27 +265,24 @@ __global__ void k_export_gaussians(int n, uint32_t slot_base, const uint8_t *lab
     }
 }
 
-__global__ void k_export_pairs(const uint32_t *keys_a, const uint32_t *vals_a, const uint32_t *keys_b,
-                               const uint32_t *vals_b, const Counters *counters, const float *depth,
-                               const int2 *ranges, uint32_t tile_base, uint32_t slot_base, int num_tiles,
-                               uint32_t pair_begin, uint32_t pair_end, uint64_t *keys, uint32_t *values,
-                               int64_t *ranges_out)
+// One block per local tile of the view: its list, in order, at out_offset[t].
+__global__ void k_export_pairs(const uint32_t *vals_a, const uint32_t *vals_b, const Counters *counters,
+                               const float *depth, const int2 *ranges, uint32_t tile_base, uint32_t slot_base,
+                               const uint32_t *out_offset, uint64_t *keys, uint32_t *values, int64_t *ranges_out)
 {
-    const bool in_b = counters->tile_in_b != 0u;
-    const uint32_t *tk = in_b ? keys_b : keys_a;
-    const uint32_t *tv = in_b ? vals_b : vals_a;
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t np = pair_end - pair_begin;
-    if (i < np) {
-        const uint32_t slot = tv[pair_begin + i];
-        if (keys) keys[i] = ((uint64_t)(tk[pair_begin + i] - tile_base) << 32) | __float_as_uint(depth[slot]);
-        if (values) values[i] = slot - slot_base;
+    const uint32_t *tv = counters->tile_in_b ? vals_b : vals_a;
+    const int t = blockIdx.x;
+    const int2 r = ranges[tile_base + t];
+    const int len = r.y > r.x ? r.y - r.x : 0;
+    const uint32_t off = out_offset[t];
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
+        const uint32_t slot = tv[r.x + k];
+        if (keys) keys[off + k] = ((uint64_t)t << 32) | __float_as_uint(depth[slot]);
+        if (values) values[off + k] = slot - slot_base;
     }
-    if (ranges_out && i < (uint32_t)num_tiles) {
-        const int2 r = ranges[tile_base + i];
-        const bool empty = r.y <= r.x;
-        ranges_out[2 * i] = empty ? 0 : (int64_t)r.x - pair_begin;
-        ranges_out[2 * i + 1] = empty ? 0 : (int64_t)r.y - pair_begin;
+    if (ranges_out && threadIdx.x == 0) {
+        ranges_out[2 * t] = len ? (int64_t)off : 0;
+        ranges_out[2 * t + 1] = len ? (int64_t)off + len : 0;
     }
 }
 
@@ -299,13 +310,14 @@ void launch_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const Counter
 }
 
 void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int split4_bits, uint32_t *order,
-                       Counters *counters, int grid, cudaStream_t s)
+                       Counters *counters, const ViewDev *views, int tile_bits, int grid, cudaStream_t s)
 {
     if (num_tiles <= 0) return;
     const int want = (num_tiles + kBlock * 4 - 1) / (kBlock * 4);
     const int g = want < grid ? want : grid;
-    k_order_hist<<<g, kBlock, 0, s>>>(ranges, num_tiles, counters);
-    k_order_scatter<<<g, kBlock, 0, s>>>(ranges, num_tiles, split2_bits, split4_bits, order, counters);
+    k_order_hist<<<g, kBlock, 0, s>>>(ranges, num_tiles, counters, views, tile_bits);
+    k_order_scatter<<<g, kBlock, 0, s>>>(ranges, num_tiles, split2_bits, split4_bits, order, counters, views,
+                                         tile_bits);
 }
 
 void launch_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_src, const uint32_t *tiles_src,
@@ -319,17 +331,14 @@ void launch_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_sr
                                                            rect, tiles);
 }
 
-void launch_export_pairs(const uint32_t *keys_a, const uint32_t *vals_a, const uint32_t *keys_b,
-                         const uint32_t *vals_b, const Counters *counters, const float *depth, const int2 *ranges,
-                         uint32_t tile_base, uint32_t slot_base, int num_tiles, uint32_t pair_begin,
-                         uint32_t pair_end, uint64_t *keys, uint32_t *values, int64_t *ranges_out, cudaStream_t s)
+void launch_export_pairs(const uint32_t *vals_a, const uint32_t *vals_b, const Counters *counters, const float *depth,
+                         const int2 *ranges, uint32_t tile_base, uint32_t slot_base, int num_tiles,
+                         const uint32_t *out_offset, uint64_t *keys, uint32_t *values, int64_t *ranges_out,
+                         cudaStream_t s)
 {
-    const uint32_t np = pair_end - pair_begin;
-    const uint32_t m = np > (uint32_t)num_tiles ? np : (uint32_t)num_tiles;
-    if (m > 0)
-        k_export_pairs<<<(m + 255) / 256, 256, 0, s>>>(keys_a, vals_a, keys_b, vals_b, counters, depth, ranges,
-                                                       tile_base, slot_base, num_tiles, pair_begin, pair_end, keys,
-                                                       values, ranges_out);
+    if (num_tiles > 0)
+        k_export_pairs<<<num_tiles, 128, 0, s>>>(vals_a, vals_b, counters, depth, ranges, tile_base, slot_base,
+                                                 out_offset, keys, values, ranges_out);
 }
 
 }  // namespace rara

@@ -333,7 +333,19 @@ __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
     __syncthreads();
     for (int t = threadIdx.x; t < 4 * 256; t += kBlock) {
         const uint32_t v = (&s_hist[0][0])[t];
-        if (v) atomicAdd(&a.hist[t], v);
+        if (v) atomicAdd(&a.hist[kHistDepth * 256 + t], v);
+    }
+    // view passes of the depth sort (several views): digit histograms of the view index of
+    // the rendered slots (its low and high byte), and the views' first slots
+    if (blockIdx.x == 0 && a.num_views > 1) {
+        for (int v = threadIdx.x; v < a.num_views; v += kBlock) {
+            a.seg_base[v] = a.views[v].slot_base;
+            const uint32_t nr = (uint32_t)a.view_counters[v].n_rendered;
+            if (nr) {
+                atomicAdd(&a.hist[kHistView * 256 + (v & 0xff)], nr);
+                atomicAdd(&a.hist[(kHistView + 1) * 256 + (v >> 8)], nr);
+            }
+        }
     }
 }
 

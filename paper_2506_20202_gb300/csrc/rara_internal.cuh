@@ -7,11 +7,18 @@
 //                fills dense per-(view, Gaussian) slots: label, tiles touched, rectangle,
 //                splat record, depth, ray-tracing record
 //   compact      rendered slots in slot order -> (depth bits, slot), depth-digit histogram
-//   depth sort   one-sweep radix sort of those pairs
-//   emit         one (global tile id, slot) pair per touched tile, in depth order, plus the
-//                tile-id digit histogram
-//   tile sort    one-sweep radix sort of the pairs on the tile-id bits
+//   depth sort   one-sweep radix sort of those pairs by depth, then (batches of several
+//                views) by view: slots in (view, depth) order
+//   emit         one (global tile id, slot) pair per touched tile in that order (so each
+//                view's pairs are contiguous and in depth order), plus the tile-digit
+//                histogram
+//   tile sort    one-sweep radix sort of the pairs on the local tile bits only
 //   ranges       [start, end) of every global tile
+// Global tile ids are view << tile_bits | local tile, tile_bits the bit length of the
+// largest view's tile count: sorting the view-grouped pairs stably by the local bits leaves
+// every (view, tile) list contiguous and in depth order with ceil(tile_bits / 8) digit
+// passes, however many views the batch has. Ids past a view's last tile are holes (no
+// pairs, no work items).
 //   item order   render work items, heaviest first
 //   render       compositing of every view's pixels
 // Element counts after the preprocess live in device memory (Counters), so the sequence
@@ -88,7 +95,7 @@ struct ViewDev {
     PlaneDev plane;
     int scene;
     int tiles_x, tiles_y;
-    uint32_t tile_base;   // first global tile id of the view
+    uint32_t tile_base;   // first global tile id of the view (view << tile_bits)
     uint32_t slot_base;   // first dense (view, Gaussian) slot of the view
     float bg[3];
     float *image;         // [3][H][W]
@@ -130,7 +137,10 @@ struct Counters {
 };
 constexpr size_t kRenderCounterBytes = 4 * sizeof(unsigned long long) + sizeof(unsigned int);
 // ticket slots
-constexpr int kTicketPre = 0, kTicketCompact = 1, kTicketEmit = 2, kTicketSortDepth = 3, kTicketSortTile = 7;
+// (the depth sort has up to 4 depth + 2 view passes, the tile sort up to 4 passes)
+constexpr int kTicketPre = 0, kTicketCompact = 1, kTicketEmit = 2, kTicketSortDepth = 3, kTicketSortTile = 9;
+// digit histograms: [0, 4) depth passes, [4, 6) view passes, [6, 10) tile passes (256 each)
+constexpr int kHistDepth = 0, kHistView = 4, kHistTile = 6, kHistPasses = 10;
 
 // Stage 1: preprocess
 struct PreprocessArgs {
@@ -160,9 +170,14 @@ struct CompactArgs {
     uint32_t num_slots;
     uint32_t *keys;        // depth bits
     uint32_t *vals;        // slot
-    uint32_t *hist;        // [4][256] digit histogram of the keys, zeroed before
+    uint32_t *hist;        // [kHistPasses][256] digit histograms, zeroed before
     unsigned long long *lookback;
     Counters *counters;
+    // view passes of the depth sort: the views' first slots and rendered counts
+    const ViewDev *views;
+    const ViewCounters *view_counters;
+    int num_views;
+    uint32_t *seg_base;    // [num_views] first slot of each view (written)
 };
 void launch_compact(const CompactArgs &a, int grid, cudaStream_t s);
 int compact_blocks_per_sm();
@@ -173,9 +188,13 @@ int compact_blocks_per_sm();
 // digit is the same for every key is skipped; *result_in_b is set on the device to 1 when
 // the result ends in the B buffers. scratch: sort_scratch_bytes(cap, passes) bytes.
 size_t sort_scratch_bytes(int64_t cap, int passes);
+// Passes from first_seg_pass on (if num_segs > 0) sort by the segment of the value instead
+// of the key: the index of the last seg_base entry <= value (seg_base ascending), 8 bits
+// per pass; the keys those passes write out are the segment indices.
 int sort_launch(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, const unsigned long long *n,
                 uint32_t cap, int passes, const uint32_t *hist, void *scratch, unsigned int *tickets,
-                unsigned int *status, unsigned int *result_in_b, int grid, cudaStream_t s);
+                unsigned int *status, unsigned int *result_in_b, int grid, cudaStream_t s,
+                const uint32_t *seg_base = nullptr, int num_segs = 0, int first_seg_pass = 0);
 int sort_blocks_per_sm();
 
 // Stage 4: emission of (global tile, slot) pairs in depth order + tile-digit histogram
@@ -206,7 +225,7 @@ void launch_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const Counter
 // per pixel), otherwise 1 item. Item = tile << 4 | log2(lanes per pixel) << 2 | part.
 // order holds 4 * num_tiles entries; the item count goes to counters->num_items.
 void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int split4_bits, uint32_t *order,
-                       Counters *counters, int grid, cudaStream_t s);
+                       Counters *counters, const ViewDev *views, int tile_bits, int grid, cudaStream_t s);
 
 // Stage 8: render
 struct RenderArgs {
@@ -275,9 +294,11 @@ void launch_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_sr
                              const uint2 *rect_src, const SplatRec *rec, const float *depth_src, uint8_t *labels,
                              float *depth, float *mean2d, float *conic, float *rgb, float *opacity, int32_t *rect,
                              uint32_t *tiles, cudaStream_t s);
-void launch_export_pairs(const uint32_t *keys_a, const uint32_t *vals_a, const uint32_t *keys_b,
-                         const uint32_t *vals_b, const Counters *counters, const float *depth, const int2 *ranges,
-                         uint32_t tile_base, uint32_t slot_base, int num_tiles, uint32_t pair_begin,
-                         uint32_t pair_end, uint64_t *keys, uint32_t *values, int64_t *ranges_out, cudaStream_t s);
+// Pairs of one view in (local tile, depth) order: tile t's list goes to out_offset[t]
+// (exclusive prefix of the view's list lengths, computed by the caller).
+void launch_export_pairs(const uint32_t *vals_a, const uint32_t *vals_b, const Counters *counters, const float *depth,
+                         const int2 *ranges, uint32_t tile_base, uint32_t slot_base, int num_tiles,
+                         const uint32_t *out_offset, uint64_t *keys, uint32_t *values, int64_t *ranges_out,
+                         cudaStream_t s);
 
 }  // namespace rara

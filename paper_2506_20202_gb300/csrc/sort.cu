@@ -46,7 +46,9 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(uint32_t *keys_a, 
                                                            uint32_t cap, int pass, int passes,
                                                            const uint32_t *__restrict__ hist, uint32_t *lookback,
                                                            unsigned int *ticket, unsigned int *status,
-                                                           unsigned int *result_in_b)
+                                                           unsigned int *result_in_b,
+                                                           const uint32_t *__restrict__ seg_base, int num_segs,
+                                                           int first_seg_pass)
 {
     __shared__ uint32_t s_warp_hist[kSortWarps][kRadix];
     __shared__ uint32_t s_keys[kPart];
@@ -78,7 +80,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(uint32_t *keys_a, 
     const uint32_t *vals_in = (flips_before & 1) ? vals_b : vals_a;
     uint32_t *keys_out = (flips_before & 1) ? keys_a : keys_b;
     uint32_t *vals_out = (flips_before & 1) ? vals_a : vals_b;
-    const int shift = 8 * pass;
+    const bool seg_pass = num_segs > 0 && pass >= first_seg_pass;
+    const int shift = seg_pass ? 8 * (pass - first_seg_pass) : 8 * pass;
     const int parts = (n + kPart - 1) / kPart;
     s_gstart[tid] = block_excl_scan_256(hist[pass * kRadix + tid], s_tmp);
 
@@ -102,6 +105,18 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(uint32_t *keys_a, 
         for (int r = 0; r < kItems; ++r) {
             const int idx = base + r * 32 + lane;
             val[r] = idx < n ? __ldg(&vals_in[idx]) : 0u;
+        }
+        if (seg_pass) {  // key = segment of the value (binary search over the segment starts)
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                int lo = 0, hi = num_segs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (__ldg(&seg_base[mid]) <= val[r]) lo = mid;
+                    else hi = mid - 1;
+                }
+                key[r] = (uint32_t)lo;
+            }
         }
 #pragma unroll
         for (int r = 0; r < kItems; ++r) {
@@ -212,7 +227,8 @@ int sort_blocks_per_sm()
 
 int sort_launch(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, const unsigned long long *n,
                 uint32_t cap, int passes, const uint32_t *hist, void *scratch, unsigned int *tickets,
-                unsigned int *status, unsigned int *result_in_b, int grid, cudaStream_t s)
+                unsigned int *status, unsigned int *result_in_b, int grid, cudaStream_t s,
+                const uint32_t *seg_base, int num_segs, int first_seg_pass)
 {
     if (passes <= 0 || grid <= 0) return 0;
     const int64_t parts = ((int64_t)cap + kPart - 1) / kPart;
@@ -220,7 +236,8 @@ int sort_launch(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *
     for (int p = 0; p < passes; ++p) {
         uint32_t *lb = (uint32_t *)scratch + (size_t)p * (size_t)(parts > 0 ? parts : 1) * kRadix;
         k_onesweep<<<grid, kSortThreads, 0, s>>>(keys_a, vals_a, keys_b, vals_b, n, cap, p, passes, hist, lb,
-                                                 tickets + p, status, result_in_b);
+                                                 tickets + p, status, result_in_b, seg_base, num_segs,
+                                                 first_seg_pass);
     }
     return passes;
 }
