@@ -891,7 +891,8 @@ int rara_render_backward(rara_ctx *c, const float *const *dL_dimages, const rara
             max_degree = c->h_scenes[si].sh_degree;
     }
     const size_t nn = c->num_slots > 0 ? (size_t)c->num_slots : 1;
-    if ((rc = ensure(c, c->grec, nn * sizeof(GradRec), "gradient records")) ||
+    rc = ensure(c, c->grec, nn * sizeof(GradRec), "gradient records");
+    if (rc ||
         (rc = ensure(c, c->bviews_d, sizeof(BwdView) * (size_t)c->num_views, "backward view table")) ||
         (rc = ensure(c, c->bscenes_d, sizeof(BwdScene) * (size_t)c->num_scenes, "backward scene table")))
         return rc;

@@ -318,9 +318,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_render_bwd(RenderBwdArgs a)
 
 // Per-Gaussian backward over the scene's views. Dynamic shared memory: the block's SH
 // coefficient gradients, [3 (degree+1)^2][kBlock].
+constexpr int kViewChunkBwd = 16;  // views staged in shared memory at a time
+
 __global__ void __launch_bounds__(kBlock, 2) k_preprocess_bwd(PreprocessBwdArgs a)
 {
+    // dynamic shared memory: SH coefficient gradients, then the SH coefficients themselves,
+    // each [3 (max degree+1)^2][kBlock]
     extern __shared__ float s_gsh[];
+    float *s_shc = s_gsh + a.sh_stride;
+    __shared__ ViewDev s_views[kViewChunkBwd];
     const int unit = blockIdx.x;
     int si = 0;
     while (si + 1 < a.num_scenes && (int)a.scenes[si + 1].unit_begin <= unit) ++si;
@@ -330,7 +336,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_preprocess_bwd(PreprocessBwdArgs 
     const int i = (unit - (int)sc.unit_begin) * kBlock + threadIdx.x;
     const bool valid = i < n;
     const int K = sh_count(sc.sh_degree);
-    for (int k = 0; k < 3 * K; ++k) s_gsh[k * kBlock + threadIdx.x] = 0.0f;
+    for (int k = 0; k < 3 * K; ++k) {
+        s_gsh[k * kBlock + threadIdx.x] = 0.0f;
+        s_shc[k * kBlock + threadIdx.x] = valid ? __ldg(&sc.sh[(size_t)k * n + i]) : 0.0f;
+    }
 
     float mu[3] = {0.f, 0.f, 0.f}, sg[3] = {1.f, 1.f, 1.f}, logit = 0.f;
     float qv[4] = {1.f, 0.f, 0.f, 0.f}, qinv = 1.0f;
@@ -353,198 +362,211 @@ __global__ void __launch_bounds__(kBlock, 2) k_preprocess_bwd(PreprocessBwdArgs 
     float gmu[3] = {0.f, 0.f, 0.f}, gsg[3] = {0.f, 0.f, 0.f}, gR[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float gopacity = 0.f;
 
-    for (int v = sc.view_begin; v < sc.view_begin + sc.view_count; ++v) {
-        const ViewDev &vw = a.views[v];
-        const CamDev &cam = vw.cam;
-        const PlaneDev &pl = vw.plane;
-        float gpn[4] = {0.f, 0.f, 0.f, 0.f};
-        bool has_plane = false;
-        const uint32_t slot = vw.slot_base + (uint32_t)i;
-        if (valid && a.tiles[slot] != 0u) {
-            const float *grc = a.grec[slot].v;
-            const float4 g0 = reinterpret_cast<const float4 *>(grc)[0];
-            const float4 g1 = reinterpret_cast<const float4 *>(grc)[1];
-            const float gblue = grc[8];
-            const bool cutoff = a.labels[slot] == RARA_CUTOFF;
-            // ---- projection, as in the forward
-            const float tx = fmaf(cam.R[0], mu[0], fmaf(cam.R[1], mu[1], fmaf(cam.R[2], mu[2], cam.t[0])));
-            const float ty = fmaf(cam.R[3], mu[0], fmaf(cam.R[4], mu[1], fmaf(cam.R[5], mu[2], cam.t[1])));
-            const float tz = fmaf(cam.R[6], mu[0], fmaf(cam.R[7], mu[1], fmaf(cam.R[8], mu[2], cam.t[2])));
-            const float itz = 1.0f / tz;
-            const float limx = 1.3f * (0.5f * cam.W / cam.fx), limy = 1.3f * (0.5f * cam.H / cam.fy);
-            const float vx = tx * itz, vy = ty * itz;
-            const float txz = fminf(limx, fmaxf(-limx, vx));
-            const float tyz = fminf(limy, fmaxf(-limy, vy));
-            const float J00 = cam.fx * itz, J02 = -cam.fx * txz * itz;
-            const float J11 = cam.fy * itz, J12 = -cam.fy * tyz * itz;
-            float T0[3], T1[3], u0[3], u1[3], A0[3], A1[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                T0[k] = fmaf(J00, cam.R[k], J02 * cam.R[6 + k]);
-                T1[k] = fmaf(J11, cam.R[3 + k], J12 * cam.R[6 + k]);
-            }
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                u0[k] = T0[0] * Rg[k] + T0[1] * Rg[3 + k] + T0[2] * Rg[6 + k];
-                u1[k] = T1[0] * Rg[k] + T1[1] * Rg[3 + k] + T1[2] * Rg[6 + k];
-                A0[k] = u0[k] * sg[k];
-                A1[k] = u1[k] * sg[k];
-            }
-            const float a0 = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2];
-            const float b0 = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
-            const float c0 = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2];
-            const float x0 = A0[1] * A1[2] - A0[2] * A1[1];
-            const float x1 = A0[2] * A1[0] - A0[0] * A1[2];
-            const float x2 = A0[0] * A1[1] - A0[1] * A1[0];
-            const float ca = a0 + kDilation, cb = b0, cc = c0 + kDilation;
-            const float det = (x0 * x0 + x1 * x1 + x2 * x2) + kDilation * (a0 + c0) + kDilation * kDilation;
-            const float idet = 1.0f / det;
-            // ---- conic (Ka, Kb, Kc) = (cc, -cb, ca) / det is the inverse of Sigma2:
-            // dL/dSigma2 = -K G K with G = [[gKa, gKb / 2], [gKb / 2, gKc]]
-            const float Ka = cc * idet, Kb = -cb * idet, Kc = ca * idet;
-            const float gKa = g0.z, gKb = 0.5f * g0.w, gKc = g1.x;
-            const float P00 = Ka * gKa + Kb * gKb, P01 = Ka * gKb + Kb * gKc;
-            const float P10 = Kb * gKa + Kc * gKb, P11 = Kb * gKb + Kc * gKc;
-            const float g_ca = -(P00 * Ka + P01 * Kb);
-            const float g_cb = -2.0f * (P00 * Kb + P01 * Kc);
-            const float g_cc = -(P10 * Kb + P11 * Kc);
-            // ---- Sigma2 = A A^T + 0.3 I, A = (J W) R S
-            float gT0[3] = {0.f, 0.f, 0.f}, gT1[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float gA0 = 2.0f * g_ca * A0[k] + g_cb * A1[k];
-                const float gA1 = 2.0f * g_cc * A1[k] + g_cb * A0[k];
-                gsg[k] += gA0 * u0[k] + gA1 * u1[k];
-                const float s0 = gA0 * sg[k], s1 = gA1 * sg[k];
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    gR[3 * j + k] += s0 * T0[j] + s1 * T1[j];
-                    gT0[j] += s0 * Rg[3 * j + k];
-                    gT1[j] += s1 * Rg[3 * j + k];
-                }
-            }
-            const float gJ00 = gT0[0] * cam.R[0] + gT0[1] * cam.R[1] + gT0[2] * cam.R[2];
-            const float gJ02 = gT0[0] * cam.R[6] + gT0[1] * cam.R[7] + gT0[2] * cam.R[8];
-            const float gJ11 = gT1[0] * cam.R[3] + gT1[1] * cam.R[4] + gT1[2] * cam.R[5];
-            const float gJ12 = gT1[0] * cam.R[6] + gT1[1] * cam.R[7] + gT1[2] * cam.R[8];
-            // ---- J(t) with clamped x/z, y/z, and the 2D mean fx x/z + cx, fy y/z + cy
-            const float gmx2 = g0.x, gmy2 = g0.y;
-            float g_itz = cam.fx * (gJ00 - gJ02 * txz + gmx2 * tx) + cam.fy * (gJ11 - gJ12 * tyz + gmy2 * ty);
-            float gt[3] = {gmx2 * cam.fx * itz, gmy2 * cam.fy * itz, 0.0f};
-            if (vx > -limx && vx < limx) {
-                const float gv = -gJ02 * cam.fx * itz;
-                gt[0] += gv * itz;
-                g_itz += gv * tx;
-            }
-            if (vy > -limy && vy < limy) {
-                const float gv = -gJ12 * cam.fy * itz;
-                gt[1] += gv * itz;
-                g_itz += gv * ty;
-            }
-            gt[2] = -g_itz * itz * itz;
-            // ---- opacity
-            gopacity += g1.y;
-            // ---- colour at normalize(mu - e)
-            const float e[3] = {mu[0] - cam.eye[0], mu[1] - cam.eye[1], mu[2] - cam.eye[2]};
-            const float il = rsqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
-            const float dir[3] = {e[0] * il, e[1] * il, e[2] * il};
-            {
-                float basis[16];
-                sh_basis(sc.sh_degree, dir[0], dir[1], dir[2], basis);
-                float grgb[3] = {g1.z, g1.w, gblue};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        if (k < K) acc = fmaf(__ldg(&sc.sh[(size_t)(k * 3 + c) * n + i]), basis[k], acc);
-                    if (!(acc + 0.5f > 0.0f)) grgb[c] = 0.0f;  // clamped at 0
-                }
-                float s[16];
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    s[k] = 0.0f;
-                    if (k < K) {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            s[k] = fmaf(grgb[c], __ldg(&sc.sh[(size_t)(k * 3 + c) * n + i]), s[k]);
-                            s_gsh[(k * 3 + c) * kBlock + threadIdx.x] += grgb[c] * basis[k];
-                        }
-                    }
-                }
-                float gdir[3];
-                sh_basis_vjp(sc.sh_degree, dir[0], dir[1], dir[2], s, gdir);
-                const float dd = gdir[0] * dir[0] + gdir[1] * dir[1] + gdir[2] * dir[2];
-#pragma unroll
-                for (int j = 0; j < 3; ++j) gmu[j] += (gdir[j] - dd * dir[j]) * il;
-            }
-            // ---- ray-tracing record of a cutoff Gaussian
-            if (cutoff) {
-                // gradients of the record products -> G, Px, Py, m (A = Px x G, B = Py x G)
-                const float *gq = grc + kGradCut;
-                const float kk = pl.k;
-                const float sx = tz / cam.fx, sy = tz / cam.fy;
-                float G[3], Px[3], Py[3], m[3];
+    const int view_end = sc.view_begin + sc.view_count;
+    for (int vbase = sc.view_begin; vbase < view_end; vbase += kViewChunkBwd) {
+        const int nv = min(kViewChunkBwd, view_end - vbase);
+        __syncthreads();  // the previous chunk's tables are no longer read
+        {
+            constexpr int kWords = (int)(sizeof(ViewDev) / sizeof(uint32_t));
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(a.views + vbase);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(s_views);
+            for (int t = threadIdx.x; t < nv * kWords; t += kBlock) dst[t] = __ldg(&src[t]);
+        }
+        __syncthreads();
+        for (int vv = 0; vv < nv; ++vv) {
+            const int v = vbase + vv;
+            const ViewDev &vw = s_views[vv];
+            const CamDev &cam = vw.cam;
+            const PlaneDev &pl = vw.plane;
+            float gpn[4] = {0.f, 0.f, 0.f, 0.f};
+            bool has_plane = false;
+            const uint32_t slot = vw.slot_base + (uint32_t)i;
+            if (valid && a.tiles[slot] != 0u) {
+                const float *grc = a.grec[slot].v;
+                const float4 g0 = reinterpret_cast<const float4 *>(grc)[0];
+                const float4 g1 = reinterpret_cast<const float4 *>(grc)[1];
+                const float gblue = grc[8];
+                const bool cutoff = a.labels[slot] == RARA_CUTOFF;
+                // ---- projection, as in the forward
+                const float tx = fmaf(cam.R[0], mu[0], fmaf(cam.R[1], mu[1], fmaf(cam.R[2], mu[2], cam.t[0])));
+                const float ty = fmaf(cam.R[3], mu[0], fmaf(cam.R[4], mu[1], fmaf(cam.R[5], mu[2], cam.t[1])));
+                const float tz = fmaf(cam.R[6], mu[0], fmaf(cam.R[7], mu[1], fmaf(cam.R[8], mu[2], cam.t[2])));
+                const float itz = 1.0f / tz;
+                const float limx = 1.3f * (0.5f * cam.W / cam.fx), limy = 1.3f * (0.5f * cam.H / cam.fy);
+                const float vx = tx * itz, vy = ty * itz;
+                const float txz = fminf(limx, fmaxf(-limx, vx));
+                const float tyz = fminf(limy, fmaxf(-limy, vy));
+                const float J00 = cam.fx * itz, J02 = -cam.fx * txz * itz;
+                const float J11 = cam.fy * itz, J12 = -cam.fy * tyz * itz;
+                float T0[3], T1[3], u0[3], u1[3], A0[3], A1[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const float rk0 = Rg[k], rk1 = Rg[3 + k], rk2 = Rg[6 + k];
-                    const float iks = 1.0f / (kk * sg[k]);
-                    G[k] = iks * (rk0 * e[0] + rk1 * e[1] + rk2 * e[2]);
-                    Px[k] = iks * sx * (rk0 * cam.R[0] + rk1 * cam.R[1] + rk2 * cam.R[2]);
-                    Py[k] = iks * sy * (rk0 * cam.R[3] + rk1 * cam.R[4] + rk2 * cam.R[5]);
-                    m[k] = kk * sg[k] * (rk0 * pl.n[0] + rk1 * pl.n[1] + rk2 * pl.n[2]);
+                    T0[k] = fmaf(J00, cam.R[k], J02 * cam.R[6 + k]);
+                    T1[k] = fmaf(J11, cam.R[3 + k], J12 * cam.R[6 + k]);
                 }
-                const float gA[3] = {gq[10], gq[11], gq[12]}, gB[3] = {gq[13], gq[14], gq[15]};
-                float gG[3], gPx[3], gPy[3], gm[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
-                    // d(Px x G): G gets gA x Px, Px gets G x gA (likewise for B = Py x G)
-                    gG[k] = 2.0f * gq[0] * G[k] + gq[1] * Px[k] + gq[2] * Py[k] + gq[7] * m[k] +
-                            (gA[k1] * Px[k2] - gA[k2] * Px[k1]) + (gB[k1] * Py[k2] - gB[k2] * Py[k1]);
-                    gPx[k] = gq[1] * G[k] + 2.0f * gq[4] * Px[k] + gq[5] * Py[k] + gq[8] * m[k] +
-                             (G[k1] * gA[k2] - G[k2] * gA[k1]);
-                    gPy[k] = gq[2] * G[k] + gq[5] * Px[k] + 2.0f * gq[6] * Py[k] + gq[9] * m[k] +
-                             (G[k1] * gB[k2] - G[k2] * gB[k1]);
-                    gm[k] = gq[7] * G[k] + gq[8] * Px[k] + gq[9] * Py[k];
+                    u0[k] = T0[0] * Rg[k] + T0[1] * Rg[3 + k] + T0[2] * Rg[6 + k];
+                    u1[k] = T1[0] * Rg[k] + T1[1] * Rg[3 + k] + T1[2] * Rg[6 + k];
+                    A0[k] = u0[k] * sg[k];
+                    A1[k] = u1[k] * sg[k];
                 }
-                const float gdep = gq[3];
-                float gtz_p = 0.0f;
+                const float a0 = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2];
+                const float b0 = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
+                const float c0 = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2];
+                const float x0 = A0[1] * A1[2] - A0[2] * A1[1];
+                const float x1 = A0[2] * A1[0] - A0[0] * A1[2];
+                const float x2 = A0[0] * A1[1] - A0[1] * A1[0];
+                const float ca = a0 + kDilation, cb = b0, cc = c0 + kDilation;
+                const float det = (x0 * x0 + x1 * x1 + x2 * x2) + kDilation * (a0 + c0) + kDilation * kDilation;
+                const float idet = 1.0f / det;
+                // ---- conic (Ka, Kb, Kc) = (cc, -cb, ca) / det is the inverse of Sigma2:
+                // dL/dSigma2 = -K G K with G = [[gKa, gKb / 2], [gKb / 2, gKc]]
+                const float Ka = cc * idet, Kb = -cb * idet, Kc = ca * idet;
+                const float gKa = g0.z, gKb = 0.5f * g0.w, gKc = g1.x;
+                const float P00 = Ka * gKa + Kb * gKb, P01 = Ka * gKb + Kb * gKc;
+                const float P10 = Kb * gKa + Kc * gKb, P11 = Kb * gKb + Kc * gKc;
+                const float g_ca = -(P00 * Ka + P01 * Kb);
+                const float g_cb = -2.0f * (P00 * Kb + P01 * Kc);
+                const float g_cc = -(P10 * Kb + P11 * Kc);
+                // ---- Sigma2 = A A^T + 0.3 I, A = (J W) R S
+                float gT0[3] = {0.f, 0.f, 0.f}, gT1[3] = {0.f, 0.f, 0.f};
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const float iks = 1.0f / (kk * sg[k]);
-                    gsg[k] += (-gG[k] * G[k] - gPx[k] * Px[k] - gPy[k] * Py[k] + gm[k] * m[k]) / sg[k];
-                    gtz_p += gPx[k] * Px[k] + gPy[k] * Py[k];
-                    const float aG = iks * gG[k], aPx = iks * sx * gPx[k], aPy = iks * sy * gPy[k];
-                    const float am = kk * sg[k] * gm[k];
+                    const float gA0 = 2.0f * g_ca * A0[k] + g_cb * A1[k];
+                    const float gA1 = 2.0f * g_cc * A1[k] + g_cb * A0[k];
+                    gsg[k] += gA0 * u0[k] + gA1 * u1[k];
+                    const float s0 = gA0 * sg[k], s1 = gA1 * sg[k];
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
-                        gR[3 * j + k] += aG * e[j] + aPx * cam.R[j] + aPy * cam.R[3 + j] + am * pl.n[j];
-                        gmu[j] += aG * Rg[3 * j + k];
-                        gpn[j] += am * Rg[3 * j + k];
+                        gR[3 * j + k] += s0 * T0[j] + s1 * T1[j];
+                        gT0[j] += s0 * Rg[3 * j + k];
+                        gT1[j] += s1 * Rg[3 * j + k];
                     }
                 }
-                gt[2] += gtz_p * itz;
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    gmu[j] += gdep * pl.n[j];
-                    gpn[j] += gdep * mu[j];
+                const float gJ00 = gT0[0] * cam.R[0] + gT0[1] * cam.R[1] + gT0[2] * cam.R[2];
+                const float gJ02 = gT0[0] * cam.R[6] + gT0[1] * cam.R[7] + gT0[2] * cam.R[8];
+                const float gJ11 = gT1[0] * cam.R[3] + gT1[1] * cam.R[4] + gT1[2] * cam.R[5];
+                const float gJ12 = gT1[0] * cam.R[6] + gT1[1] * cam.R[7] + gT1[2] * cam.R[8];
+                // ---- J(t) with clamped x/z, y/z, and the 2D mean fx x/z + cx, fy y/z + cy
+                const float gmx2 = g0.x, gmy2 = g0.y;
+                float g_itz = cam.fx * (gJ00 - gJ02 * txz + gmx2 * tx) + cam.fy * (gJ11 - gJ12 * tyz + gmy2 * ty);
+                float gt[3] = {gmx2 * cam.fx * itz, gmy2 * cam.fy * itz, 0.0f};
+                if (vx > -limx && vx < limx) {
+                    const float gv = -gJ02 * cam.fx * itz;
+                    gt[0] += gv * itz;
+                    g_itz += gv * tx;
                 }
-                gpn[3] = gdep;
-                has_plane = true;
+                if (vy > -limy && vy < limy) {
+                    const float gv = -gJ12 * cam.fy * itz;
+                    gt[1] += gv * itz;
+                    g_itz += gv * ty;
+                }
+                gt[2] = -g_itz * itz * itz;
+                // ---- opacity
+                gopacity += g1.y;
+                // ---- colour at normalize(mu - e)
+                const float e[3] = {mu[0] - cam.eye[0], mu[1] - cam.eye[1], mu[2] - cam.eye[2]};
+                const float il = rsqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+                const float dir[3] = {e[0] * il, e[1] * il, e[2] * il};
+                {
+                    float basis[16];
+                    sh_basis(sc.sh_degree, dir[0], dir[1], dir[2], basis);
+                    float grgb[3] = {g1.z, g1.w, gblue};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        float acc = 0.0f;
+#pragma unroll
+                        for (int k = 0; k < 16; ++k)
+                            if (k < K) acc = fmaf(s_shc[(k * 3 + c) * kBlock + threadIdx.x], basis[k], acc);
+                        if (!(acc + 0.5f > 0.0f)) grgb[c] = 0.0f;  // clamped at 0
+                    }
+                    float s[16];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        s[k] = 0.0f;
+                        if (k < K) {
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                s[k] = fmaf(grgb[c], s_shc[(k * 3 + c) * kBlock + threadIdx.x], s[k]);
+                                s_gsh[(k * 3 + c) * kBlock + threadIdx.x] += grgb[c] * basis[k];
+                            }
+                        }
+                    }
+                    float gdir[3];
+                    sh_basis_vjp(sc.sh_degree, dir[0], dir[1], dir[2], s, gdir);
+                    const float dd = gdir[0] * dir[0] + gdir[1] * dir[1] + gdir[2] * dir[2];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) gmu[j] += (gdir[j] - dd * dir[j]) * il;
+                }
+                // ---- ray-tracing record of a cutoff Gaussian
+                if (cutoff) {
+                    // gradients of the record products -> G, Px, Py, m (A = Px x G, B = Py x G)
+                    const float *gq = grc + kGradCut;
+                    const float kk = pl.k;
+                    const float sx = tz / cam.fx, sy = tz / cam.fy;
+                    float G[3], Px[3], Py[3], m[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const float rk0 = Rg[k], rk1 = Rg[3 + k], rk2 = Rg[6 + k];
+                        const float iks = 1.0f / (kk * sg[k]);
+                        G[k] = iks * (rk0 * e[0] + rk1 * e[1] + rk2 * e[2]);
+                        Px[k] = iks * sx * (rk0 * cam.R[0] + rk1 * cam.R[1] + rk2 * cam.R[2]);
+                        Py[k] = iks * sy * (rk0 * cam.R[3] + rk1 * cam.R[4] + rk2 * cam.R[5]);
+                        m[k] = kk * sg[k] * (rk0 * pl.n[0] + rk1 * pl.n[1] + rk2 * pl.n[2]);
+                    }
+                    const float gA[3] = {gq[10], gq[11], gq[12]}, gB[3] = {gq[13], gq[14], gq[15]};
+                    float gG[3], gPx[3], gPy[3], gm[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+                        // d(Px x G): G gets gA x Px, Px gets G x gA (likewise for B = Py x G)
+                        gG[k] = 2.0f * gq[0] * G[k] + gq[1] * Px[k] + gq[2] * Py[k] + gq[7] * m[k] +
+                                (gA[k1] * Px[k2] - gA[k2] * Px[k1]) + (gB[k1] * Py[k2] - gB[k2] * Py[k1]);
+                        gPx[k] = gq[1] * G[k] + 2.0f * gq[4] * Px[k] + gq[5] * Py[k] + gq[8] * m[k] +
+                                 (G[k1] * gA[k2] - G[k2] * gA[k1]);
+                        gPy[k] = gq[2] * G[k] + gq[5] * Px[k] + 2.0f * gq[6] * Py[k] + gq[9] * m[k] +
+                                 (G[k1] * gB[k2] - G[k2] * gB[k1]);
+                        gm[k] = gq[7] * G[k] + gq[8] * Px[k] + gq[9] * Py[k];
+                    }
+                    const float gdep = gq[3];
+                    float gtz_p = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const float iks = 1.0f / (kk * sg[k]);
+                        gsg[k] += (-gG[k] * G[k] - gPx[k] * Px[k] - gPy[k] * Py[k] + gm[k] * m[k]) / sg[k];
+                        gtz_p += gPx[k] * Px[k] + gPy[k] * Py[k];
+                        const float aG = iks * gG[k], aPx = iks * sx * gPx[k], aPy = iks * sy * gPy[k];
+                        const float am = kk * sg[k] * gm[k];
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            gR[3 * j + k] += aG * e[j] + aPx * cam.R[j] + aPy * cam.R[3 + j] + am * pl.n[j];
+                            gmu[j] += aG * Rg[3 * j + k];
+                            gpn[j] += am * Rg[3 * j + k];
+                        }
+                    }
+                    gt[2] += gtz_p * itz;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        gmu[j] += gdep * pl.n[j];
+                        gpn[j] += gdep * mu[j];
+                    }
+                    gpn[3] = gdep;
+                    has_plane = true;
+                }
+                // ---- camera-space mean t = W mu + t0
+#pragma unroll
+                for (int j = 0; j < 3; ++j) gmu[j] += cam.R[j] * gt[0] + cam.R[3 + j] * gt[1] + cam.R[6 + j] * gt[2];
             }
-            // ---- camera-space mean t = W mu + t0
+            const BwdView &bv = a.bviews[v];
+            if (bv.plane_grad && __any_sync(kFull, has_plane)) {
 #pragma unroll
-            for (int j = 0; j < 3; ++j) gmu[j] += cam.R[j] * gt[0] + cam.R[3 + j] * gt[1] + cam.R[6 + j] * gt[2];
-        }
-        const BwdView &bv = a.bviews[v];
-        if (bv.plane_grad && __any_sync(kFull, has_plane)) {
+                for (int j = 0; j < 4; ++j) gpn[j] = warp_sum(gpn[j]);
+                if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) gpn[j] = warp_sum(gpn[j]);
-            if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (gpn[j] != 0.0f) atomicAdd(&bv.plane_grad[j], gpn[j]);
+                    for (int j = 0; j < 4; ++j)
+                        if (gpn[j] != 0.0f) atomicAdd(&bv.plane_grad[j], gpn[j]);
+                }
             }
         }
     }
@@ -589,9 +611,11 @@ void launch_render_bwd(const RenderBwdArgs &a, int grid, cudaStream_t s)
     if (grid > 0) k_render_bwd<<<grid, kBlock, 0, s>>>(a);
 }
 
-int launch_preprocess_bwd(const PreprocessBwdArgs &a, int grid, int max_sh_degree, cudaStream_t s)
+int launch_preprocess_bwd(const PreprocessBwdArgs &a_in, int grid, int max_sh_degree, cudaStream_t s)
 {
-    const int smem = 3 * (max_sh_degree + 1) * (max_sh_degree + 1) * kBlock * (int)sizeof(float);
+    PreprocessBwdArgs a = a_in;
+    a.sh_stride = 3 * (max_sh_degree + 1) * (max_sh_degree + 1) * kBlock;
+    const int smem = 2 * a.sh_stride * (int)sizeof(float);
     if (grid <= 0) return 0;
     if (cudaFuncSetAttribute(k_preprocess_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return -1;

@@ -285,6 +285,7 @@ struct PreprocessBwdArgs {
     const uint8_t *labels;
     const uint32_t *tiles;
     const GradRec *grec;
+    int sh_stride;         // set by the launcher
 };
 // grid = preprocess units; max_sh_degree sizes the per-block SH gradient accumulators.
 int launch_preprocess_bwd(const PreprocessBwdArgs &a, int grid, int max_sh_degree, cudaStream_t s);

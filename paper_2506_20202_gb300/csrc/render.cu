@@ -47,7 +47,8 @@ struct Tally {
 
 // Alpha of list entry j (in the staged batch) at pixel offset (dx, dy); 0 when the entry
 // does not contribute (outside the q <= 9 support or below 1/255 after the weight).
-__device__ __forceinline__ float entry_alpha(const Stage &st, int j, float pxf, float pyf, Tally &ty)
+template <class StageT>
+__device__ __forceinline__ float entry_alpha(const StageT &st, int j, float pxf, float pyf, Tally &ty)
 {
     const float4 r0 = st.r0[j];
     const float dx = pxf - r0.x, dy = pyf - r0.y;
