@@ -47,6 +47,7 @@ struct rara_ctx {
     uint32_t num_slots = 0, num_tiles = 0, num_units = 0;
     int tile_bits = 0;                  // global tile id = internal view << tile_bits | local tile
     int tile_passes = 1;                // digit passes of the tile sort
+    int tile_digit_bits = 8;            // bits per tile-sort pass (the tile bits split evenly)
     int view_passes = 0;                // view digit passes of the depth sort (several views)
     uint32_t cap_pairs = 0;             // pair capacity the binning kernels were launched with
     cudaStream_t last_stream = nullptr;
@@ -324,6 +325,7 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
     c->tile_bits = tile_bits;
     c->tile_passes = (tile_bits + 7) / 8;
     if (c->tile_passes < 1) c->tile_passes = 1;
+    c->tile_digit_bits = tile_bits > 0 ? (tile_bits + c->tile_passes - 1) / c->tile_passes : 1;
     c->view_passes = nv > 256 ? 2 : (nv > 1 ? 1 : 0);
     const size_t nn = slots > 0 ? (size_t)slots : 1;
     const size_t nt = tiles > 0 ? (size_t)tiles : 1;
@@ -458,6 +460,7 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
     e.num_views = c->num_views;
     e.cap_pairs = cap;
     e.tile_passes = c->tile_passes;
+    e.tile_digit_bits = c->tile_digit_bits;
     e.pair_keys = (uint32_t *)c->pkeys.p;
     e.pair_vals = (uint32_t *)c->pvals.p;
     e.tile_hist = hist + kHistTile * 256;
@@ -468,7 +471,8 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
 
     nl = sort_launch((uint32_t *)c->pkeys.p, (uint32_t *)c->pvals.p, (uint32_t *)c->pkeys_b.p,
                      (uint32_t *)c->pvals_b.p, &dc->n_pairs, cap, c->tile_passes, hist + kHistTile * 256, c->sort_scratch.p,
-                     &dc->ticket[kTicketSortTile], &dc->status, &dc->tile_in_b, sgrid, s);
+                     &dc->ticket[kTicketSortTile], &dc->status, &dc->tile_in_b, sgrid, s, nullptr, 0, 0,
+                     c->tile_digit_bits);
     if ((rc = launched(c, "tile sort", nl))) return rc;
 
     const size_t nt = c->num_tiles > 0 ? (size_t)c->num_tiles : 1;

@@ -53,7 +53,7 @@ __device__ __forceinline__ bool rara_weight_grad(const float4 c0, const float4 c
     const RayTerms t = ray_terms(c0, c1, c2, c3, dx, dy);
     if (t.cc >= 1.0f) return false;
     const float h2 = 1.0f - t.cc;
-    if (!(t.GV > 0.0f && t.GV * t.GV > h2 * t.VV)) return false;
+    if (!(t.GV > 0.0f && __fmul_rn(t.GV, t.GV) > __fmul_rn(h2, t.VV))) return false;
     const float mp = fmaf(c2.x, dx, c2.y * dy);
     const float mV = c1.w + mp;
     const float f = __fmul_rn(t.Gp + t.pp, t.rVV);
@@ -169,10 +169,8 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
         if ((int)threadIdx.x < cnt) {
             const uint32_t g = __ldg(&pair_vals[bbeg + threadIdx.x]);
             const SplatRec rec = a.rec[g];
-            st.r0[threadIdx.x] = rec.r0;
-            st.r1[threadIdx.x] = rec.r1;
-            st.r2[threadIdx.x] = rec.r2;
-            if (rec.r2.y != 0.0f) {
+            stage_splat(st, threadIdx.x, rec);
+            if (rec.r2.y != kWeightNone) {
                 const CutRec c = a.cut[g];
                 st.c0[threadIdx.x] = c.c0;
                 st.c1[threadIdx.x] = c.c1;
@@ -186,20 +184,17 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
             const int lo = max(0, hi - 32);
             const int jt = lo + lane;
             bool keep = false;
-            if (jt < hi && (uint32_t)(bbeg - range.x + jt) < wlast) {
-                const float4 t0 = st.r0[jt];
-                const float4 t2 = st.r2[jt];
-                keep = box_min_q(rx0 - t0.x, rx1 - t0.x, ry0 - t0.y, ry1 - t0.y, t0.z, t0.w, st.r1[jt].x, t2.z,
-                                 t2.w) <= kCullQ;
-            }
+            if (jt < hi && (uint32_t)(bbeg - range.x + jt) < wlast) keep = entry_reaches(st, jt, rx0, rx1, ry0, ry1);
             unsigned m = __ballot_sync(kFull, keep);
             while (m) {
                 const int b = 31 - __clz(m);
                 m &= ~(1u << b);
                 const int j = lo + b;
                 const uint32_t pos = (uint32_t)(bbeg - range.x + j);
-                const float4 r0 = st.r0[j], r1 = st.r1[j], r2 = st.r2[j];
-                const bool cut = r2.y == kWeightSplit;  // the weight varies with the inputs
+                const float4 s0 = st.s0[j], s1 = st.s1[j], s2 = st.s2[j];
+                const float ca = s0.z, cb = 0.5f * s0.w, cc = s1.x;  // conic (a, b, c)
+                const float mode = s1.w;
+                const bool cut = mode == kWeightSplit;  // the weight varies with the inputs
                 bool contrib = false;
                 float gmx = 0.f, gmy = 0.f, gCa = 0.f, gCb = 0.f, gCc = 0.f, gop = 0.f;
                 float gr = 0.f, gg = 0.f, gb = 0.f;
@@ -207,16 +202,15 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
 #pragma unroll
                 for (int k = 0; k < 16; ++k) gc[k] = 0.f;
                 if (inside && pos < last) {
-                    const float dx = pxf - r0.x, dy = pyf - r0.y;
-                    const float q = splat_q(r0.z, r0.w, r1.x, dx, dy);
-                    if (q <= kSupportQ) {
-                        const float ex = __expf(-0.5f * q);
-                        const float a0 = r1.y * ex;
+                    const float dx = pxf - s0.x, dy = pyf - s0.y;
+                    const float q = splat_q(s0.z, s0.w, s1.x, dx, dy);
+                    if (q <= s1.z) {
+                        const float a0 = splat_alpha0(q, s1.y);
                         if (a0 >= kAlphaMin) {
                             float w = 1.0f;
-                            if (r2.y != kWeightNone)
-                                w = decay_weight(r2.y, st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
-                            const float au = a0 * w;
+                            if (mode != kWeightNone)
+                                w = decay_weight(mode, st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
+                            const float au = __fmul_rn(a0, w);
                             const float alpha = fminf(kAlphaMax, au);
                             if (alpha >= kAlphaMin) {
                                 contrib = true;
@@ -226,21 +220,21 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
                                 gr = dC0 * wgt;
                                 gg = dC1 * wgt;
                                 gb = dC2 * wgt;
-                                float ga = Tj * (dC0 * (r1.z - B0) + dC1 * (r1.w - B1) + dC2 * (r2.x - B2)) -
+                                float ga = Tj * (dC0 * (s2.x - B0) + dC1 * (s2.y - B1) + dC2 * (s2.z - B2)) -
                                            Tfin * bgdot / oma;
-                                B0 = fmaf(alpha, r1.z, oma * B0);
-                                B1 = fmaf(alpha, r1.w, oma * B1);
-                                B2 = fmaf(alpha, r2.x, oma * B2);
+                                B0 = fmaf(alpha, s2.x, oma * B0);
+                                B1 = fmaf(alpha, s2.y, oma * B1);
+                                B2 = fmaf(alpha, s2.z, oma * B2);
                                 T = Tj;
                                 if (au > kAlphaMax) ga = 0.0f;  // clamped at 0.99
                                 const float ga0 = ga * w;
-                                gop = ga0 * ex;
+                                gop = ga0 * (a0 / s2.w);        // d alpha0 / d opacity = exp(-q/2)
                                 const float gq = -0.5f * ga0 * a0;
                                 gCa = gq * dx * dx;
                                 gCb = 2.0f * gq * dx * dy;
                                 gCc = gq * dy * dy;
-                                float gdx = 2.0f * gq * fmaf(r0.z, dx, r0.w * dy);
-                                float gdy = 2.0f * gq * fmaf(r0.w, dx, r1.x * dy);
+                                float gdx = 2.0f * gq * fmaf(ca, dx, cb * dy);
+                                float gdy = 2.0f * gq * fmaf(cb, dx, cc * dy);
                                 if (cut)
                                     rara_weight_grad(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy, ga * a0, gc, gdx,
                                                      gdy);

@@ -28,18 +28,24 @@ __device__ __forceinline__ int view_of_slot(const ViewDev *views, int num_views,
     return lo;
 }
 
-// Partitions of kEmitItems rows of kBlock depth-ordered slots: thread t takes slot
-// r * kBlock + t of each row r, so in every row adjacent threads emit adjacent slots' pairs
-// (the stores of a warp stay close together), while one chained-scan step serves
-// kBlock * kEmitItems slots. The partition's exclusive prefix is a block scan of the
-// row-major tile counts staged in shared memory.
-constexpr int kEmitItems = 8;
+// Emission, persistent over partitions of kEmitPart consecutive depth-ordered slots. A
+// partition loads its slots (thread t takes slot r * kBlock + t of row r, coalesced), scans
+// their tile counts into per-slot offsets, gets its first pair position from a chained scan,
+// and then writes its pairs striped over the block: output k of the partition goes to
+// thread k mod kBlock, which finds the slot owning k by binary search over the offsets and
+// the tile from k's position inside the slot's rectangle (row-major). Consecutive threads
+// thus store consecutive pairs (full 128-byte lines per warp), however uneven the
+// rectangles, and a slot with many tiles is spread over the whole block.
+constexpr int kEmitItems = 4;
 constexpr uint32_t kEmitPart = kBlock * kEmitItems;
 
 __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
 {
     __shared__ uint32_t s_hist[4][256];
-    __shared__ uint32_t s_cnt[kEmitPart];          // tile counts, then exclusive offsets
+    __shared__ uint32_t s_off[kEmitPart + 1];      // tile counts, then exclusive offsets
+    __shared__ uint32_t s_slot[kEmitPart];
+    __shared__ uint32_t s_t0[kEmitPart];           // global tile id of the rectangle's first tile
+    __shared__ uint32_t s_geo[kEmitPart];          // rectangle width | view's tiles_x << 16
     __shared__ unsigned s_part;
     __shared__ unsigned long long s_warp[kBlock / 32];
     __shared__ unsigned long long s_prefix;
@@ -48,6 +54,8 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
     const uint32_t n = (uint32_t)a.counters->n_rendered;
     const uint32_t *vals = a.counters->depth_in_b ? a.vals_b : a.vals_a;
     const uint32_t parts = (n + kEmitPart - 1) / kEmitPart;
+    const int passes = a.tile_passes, dbits = a.tile_digit_bits;
+    const uint32_t dmask = (1u << dbits) - 1u;
     bool overflow = false;
     for (;;) {
         __syncthreads();
@@ -55,21 +63,39 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
         __syncthreads();
         const uint32_t part = s_part;
         if (part >= parts) break;
-        const uint32_t first = part * kEmitPart + threadIdx.x;
+        const uint32_t first = part * kEmitPart;
         uint32_t slot[kEmitItems];
 #pragma unroll
-        for (int r = 0; r < kEmitItems; ++r)
-            slot[r] = first + r * kBlock < n ? __ldg(&vals[first + r * kBlock]) : 0u;
+        for (int r = 0; r < kEmitItems; ++r) {
+            const uint32_t i = first + r * kBlock + threadIdx.x;
+            slot[r] = i < n ? __ldg(&vals[i]) : 0u;
+        }
 #pragma unroll
-        for (int r = 0; r < kEmitItems; ++r)
-            s_cnt[r * kBlock + threadIdx.x] = first + r * kBlock < n ? __ldg(&a.tiles[slot[r]]) : 0u;
+        for (int r = 0; r < kEmitItems; ++r) {
+            const int j = r * kBlock + threadIdx.x;
+            uint32_t cnt = 0, t0 = 0, geo = 0;
+            if (first + j < n) {
+                const uint2 rc = __ldg(&a.rect[slot[r]]);
+                const int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
+                if (x0 <= x1 && y0 <= y1) {
+                    const ViewDev &vw = a.views[view_of_slot(a.views, a.num_views, slot[r])];
+                    cnt = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+                    t0 = vw.tile_base + (uint32_t)(y0 * vw.tiles_x + x0);
+                    geo = (uint32_t)(x1 - x0 + 1) | ((uint32_t)vw.tiles_x << 16);
+                }
+            }
+            s_off[j] = cnt;
+            s_slot[j] = slot[r];
+            s_t0[j] = t0;
+            s_geo[j] = geo;
+        }
         __syncthreads();
         // thread t scans the kEmitItems consecutive counts [t * kEmitItems, ...)
         uint32_t c[kEmitItems];
         uint32_t sum = 0;
 #pragma unroll
         for (int r = 0; r < kEmitItems; ++r) {
-            c[r] = s_cnt[threadIdx.x * kEmitItems + r];
+            c[r] = s_off[threadIdx.x * kEmitItems + r];
             sum += c[r];
         }
         unsigned long long incl = sum;
@@ -89,38 +115,44 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
             const unsigned long long total = __shfl_sync(0xffffffffu, wi, 31);
             if (lane < kBlock / 32) s_warp[lane] = wi - w;
             const unsigned long long prefix = warp_chained_prefix(a.lookback, (int)part, total, &a.counters->status);
-            if (lane == 0) s_prefix = prefix;
+            if (lane == 0) {
+                s_prefix = prefix;
+                s_off[kEmitPart] = (uint32_t)total;  // a partition's pairs are < 2^32
+            }
         }
         __syncthreads();
-        // offsets inside the partition (they fit 32 bits: a partition's pairs are < 2^32)
         uint32_t run = (uint32_t)(s_warp[warp] + incl - sum);
 #pragma unroll
         for (int r = 0; r < kEmitItems; ++r) {
-            s_cnt[threadIdx.x * kEmitItems + r] = run;
+            s_off[threadIdx.x * kEmitItems + r] = run;
             run += c[r];
         }
         __syncthreads();
         const unsigned long long pbase = s_prefix;
-#pragma unroll
-        for (int r = 0; r < kEmitItems; ++r) {
-            if (first + r * kBlock >= n) break;
-            unsigned long long off = pbase + s_cnt[r * kBlock + threadIdx.x];
-            const uint2 rc = a.rect[slot[r]];
-            const int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
-            if (x0 > x1 || y0 > y1) continue;
-            const ViewDev &vw = a.views[view_of_slot(a.views, a.num_views, slot[r])];
-            for (int y = y0; y <= y1; ++y)
-                for (int x = x0; x <= x1; ++x) {
-                    if (off < a.cap_pairs) {
-                        const uint32_t t = vw.tile_base + (uint32_t)(y * vw.tiles_x + x);
-                        a.pair_keys[off] = t;
-                        a.pair_vals[off] = slot[r];
-                        for (int p = 0; p < a.tile_passes; ++p) atomicAdd(&s_hist[p][(t >> (8 * p)) & 0xffu], 1u);
-                    } else {
-                        overflow = true;
-                    }
-                    ++off;
-                }
+        const uint32_t total = s_off[kEmitPart];
+        int j = 0;  // owner of the previous output of this thread (owners never decrease)
+        for (uint32_t k = threadIdx.x; k < total; k += kBlock) {
+            // last j with s_off[j] <= k (empty slots share their successor's offset)
+            int lo = j, hi = (int)kEmitPart - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= k) lo = mid;
+                else hi = mid - 1;
+            }
+            j = lo;
+            const uint32_t r = k - s_off[j];
+            const uint32_t geo = s_geo[j];
+            const uint32_t w = geo & 0xffffu;
+            const uint32_t y = r / w, x = r - y * w;
+            const uint32_t t = s_t0[j] + y * (geo >> 16) + x;
+            const unsigned long long off = pbase + k;
+            if (off < a.cap_pairs) {
+                a.pair_keys[off] = t;
+                a.pair_vals[off] = s_slot[j];
+                for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(t >> (dbits * p)) & dmask], 1u);
+            } else {
+                overflow = true;
+            }
         }
     }
     __syncthreads();

@@ -182,7 +182,8 @@ struct CompactArgs {
 void launch_compact(const CompactArgs &a, int grid, cudaStream_t s);
 int compact_blocks_per_sm();
 
-// One-sweep LSD radix sort of (uint32 key, uint32 value) over bits [0, 8 * passes).
+// One-sweep LSD radix sort of (uint32 key, uint32 value) over bits [0, digit_bits * passes),
+// digit_bits <= 8 bits per pass.
 // The element count is read from device memory (*n, clamped to cap). hist holds the
 // 8-bit digit histograms of all passes (built by the producer of the keys). A pass whose
 // digit is the same for every key is skipped; *result_in_b is set on the device to 1 when
@@ -194,7 +195,7 @@ size_t sort_scratch_bytes(int64_t cap, int passes);
 int sort_launch(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, const unsigned long long *n,
                 uint32_t cap, int passes, const uint32_t *hist, void *scratch, unsigned int *tickets,
                 unsigned int *status, unsigned int *result_in_b, int grid, cudaStream_t s,
-                const uint32_t *seg_base = nullptr, int num_segs = 0, int first_seg_pass = 0);
+                const uint32_t *seg_base = nullptr, int num_segs = 0, int first_seg_pass = 0, int digit_bits = 8);
 int sort_blocks_per_sm();
 
 // Stage 4: emission of (global tile, slot) pairs in depth order + tile-digit histogram
@@ -206,6 +207,7 @@ struct EmitArgs {
     int num_views;
     uint32_t cap_pairs;
     int tile_passes;
+    int tile_digit_bits;     // bits per tile-sort pass
     uint32_t *pair_keys;     // global tile id
     uint32_t *pair_vals;     // slot
     uint32_t *tile_hist;     // [tile_passes][256], zeroed before

@@ -45,28 +45,24 @@ struct Tally {
     uint32_t evaluated = 0, walked = 0, cut = 0, tested = 0;
 };
 
-// Alpha of list entry j (in the staged batch) at pixel offset (dx, dy); 0 when the entry
-// does not contribute (outside the q <= 9 support or below 1/255 after the weight).
-template <class StageT>
-__device__ __forceinline__ float entry_alpha(const StageT &st, int j, float pxf, float pyf, Tally &ty)
+// Alpha of staged entry j at pixel offset (dx, dy) from its centre; 0 when the entry does
+// not contribute (q > q_cut, alpha0 < 1/255, or below 1/255 after the weight). Used by the
+// multi-lane pixel paths, where the lanes of a warp look at different entries.
+__device__ __forceinline__ float entry_alpha(const Stage &st, int j, float pxf, float pyf, Tally &ty)
 {
-    const float4 r0 = st.r0[j];
-    const float dx = pxf - r0.x, dy = pyf - r0.y;
-    const float4 r1 = st.r1[j];
-    const float q = splat_q(r0.z, r0.w, r1.x, dx, dy);
+    const float4 s0 = st.s0[j];
+    const float4 s1 = st.s1[j];
+    const float dx = pxf - s0.x, dy = pyf - s0.y;
+    const float q = splat_q(s0.z, s0.w, s1.x, dx, dy);
     ++ty.walked;
-    if (q > kSupportQ) return 0.0f;
-    ++ty.evaluated;
-    float alpha = r1.y * __expf(-0.5f * q);
+    if (!(q <= s1.z)) return 0.0f;
+    float alpha = splat_alpha0(q, s1.y);
     if (alpha < kAlphaMin) return 0.0f;
-    const float mode = st.r2[j].y;
+    ++ty.evaluated;
+    const float mode = s1.w;
     if (mode != kWeightNone) {
-        if (mode == kWeightSplit) {
-            alpha *= rara_weight(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
-            ++ty.cut;
-        } else {
-            alpha *= rara_weight_hidden(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
-        }
+        if (mode == kWeightSplit) ++ty.cut;
+        alpha = __fmul_rn(alpha, decay_weight(mode, st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy));
     }
     alpha = fminf(kAlphaMax, alpha);
     return alpha < kAlphaMin ? 0.0f : alpha;
@@ -109,10 +105,8 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
         if (k + kBlock < range.y) g_next = __ldg(&pair_vals[k + kBlock]);
         if (k < range.y) {
             const SplatRec rec = a.rec[g];
-            st.r0[threadIdx.x] = rec.r0;
-            st.r1[threadIdx.x] = rec.r1;
-            st.r2[threadIdx.x] = rec.r2;
-            if (rec.r2.y != 0.0f) {
+            stage_splat(st, threadIdx.x, rec);
+            if (rec.r2.y != kWeightNone) {
                 const CutRec c = a.cut[g];
                 st.c0[threadIdx.x] = c.c0;
                 st.c1[threadIdx.x] = c.c1;
@@ -122,37 +116,53 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
         }
         __syncthreads();
         const int cnt = min(kBlock, range.y - base);
+        const int pos0 = base - range.x + 1;  // list position (1-based) of batch entry 0
         for (int chunk = 0; chunk < cnt; chunk += 32) {
             if (__all_sync(0xffffffffu, done)) break;
-            bool keep = false;
+            bool keep = false, weighted = false;
             const int jt = chunk + lane;
             if (jt < cnt) {
-                const float4 t0 = st.r0[jt];
-                const float cq = st.r1[jt].x;
-                const float4 t2 = st.r2[jt];
-                keep = box_min_q(rx0 - t0.x, rx1 - t0.x, ry0 - t0.y, ry1 - t0.y, t0.z, t0.w, cq, t2.z, t2.w) <= kCullQ;
+                keep = entry_reaches(st, jt, rx0, rx1, ry0, ry1);
+                weighted = st.s1[jt].w != kWeightNone;
                 ++ty.tested;
             }
             unsigned m = __ballot_sync(0xffffffffu, keep);
             if (LPP == 1) {
+                const unsigned mw = __ballot_sync(0xffffffffu, keep && weighted);
+                // Entries in list order; every lane runs the same straight-line step (the
+                // only branch, on the entry's weight mode, is uniform across the warp), with
+                // lanes that are done or outside the support contributing alpha = 0.
                 while (m) {
-                    const int j = chunk + __ffs(m) - 1;
+                    const int bit = __ffs(m) - 1;
                     m &= m - 1;
-                    if (done) continue;
-                    const float alpha = entry_alpha(st, j, pxf, pyf, ty);
-                    if (alpha == 0.0f) continue;
-                    const float Tn = T * (1.0f - alpha);
-                    if (Tn < kTMin) {
-                        done = true;
-                        continue;
+                    const int j = chunk + bit;
+                    const float4 s0 = st.s0[j];
+                    const float4 s1 = st.s1[j];
+                    const float dx = pxf - s0.x, dy = pyf - s0.y;
+                    const float q = splat_q(s0.z, s0.w, s1.x, dx, dy);
+                    ty.walked += done ? 0u : 1u;
+                    const float a0 = splat_alpha0(q, s1.y);
+                    const bool live = !done && q <= s1.z && a0 >= kAlphaMin;
+                    ty.evaluated += live ? 1u : 0u;
+                    float alpha = a0;
+                    if ((mw >> bit) & 1u) {
+                        const float mode = s1.w;
+                        ty.cut += live && mode == kWeightSplit ? 1u : 0u;
+                        alpha = __fmul_rn(a0, decay_weight(mode, st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy));
                     }
-                    const float wgt = alpha * T;
-                    const float4 r1 = st.r1[j];
-                    C0 = fmaf(r1.z, wgt, C0);
-                    C1 = fmaf(r1.w, wgt, C1);
-                    C2 = fmaf(st.r2[j].x, wgt, C2);
-                    T = Tn;
-                    last = (uint32_t)(base - range.x + j + 1);
+                    alpha = fminf(kAlphaMax, alpha);
+                    const bool valid = live && alpha >= kAlphaMin;
+                    const float Tn = T * (1.0f - alpha);
+                    const bool stop = valid && Tn < kTMin;
+                    const bool blend = valid && !stop;
+                    const float wgt = blend ? alpha * T : 0.0f;
+                    const float4 s2 = st.s2[j];
+                    C0 = fmaf(s2.x, wgt, C0);
+                    C1 = fmaf(s2.y, wgt, C1);
+                    C2 = fmaf(s2.z, wgt, C2);
+                    T = blend ? Tn : T;
+                    last = blend ? (uint32_t)(pos0 + j) : last;
+                    done = done || stop;
                 }
             } else {
                 const int group = pix * LPP;          // first lane of this pixel's group
@@ -190,11 +200,11 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
                     float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
                     uint32_t lp = 0;
                     if (blend) {
-                        const float4 r1 = st.r1[j];
-                        s0 = r1.z * wgt;
-                        s1 = r1.w * wgt;
-                        s2 = st.r2[j].x * wgt;
-                        lp = (uint32_t)(base - range.x + j + 1);
+                        const float4 c = st.s2[j];
+                        s0 = c.x * wgt;
+                        s1 = c.y * wgt;
+                        s2 = c.z * wgt;
+                        lp = (uint32_t)(pos0 + j);
                     }
 #pragma unroll
                     for (int o = 1; o < LPP; o <<= 1) {

@@ -6,10 +6,27 @@
 
 namespace rara {
 
-// q(dx, dy) = a dx^2 + 2 b dx dy + c dy^2 of a splat with conic (a, b, c).
-__device__ __forceinline__ float splat_q(float a, float b, float c, float dx, float dy)
+// q(dx, dy) = a dx^2 + 2 b dx dy + c dy^2 of a splat with conic (a, b, c), given b2 = 2 b.
+__device__ __forceinline__ float splat_q(float a, float b2, float c, float dx, float dy)
 {
-    return fmaf(dx, fmaf(a, dx, 2.0f * b * dy), c * dy * dy);
+    return fmaf(dx, fmaf(a, dx, b2 * dy), c * dy * dy);
+}
+
+constexpr float kHalfLog2e = 0.72134752044448170f;  // log2(e) / 2
+constexpr float kLog2_255 = 7.99435343685885793f;   // -log2(kAlphaMin)
+
+// 2^x (the special function unit's base-2 exponential).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// alpha0 = opacity exp(-q/2) (Eq. 10 without the normalisation) from log2(opacity).
+__device__ __forceinline__ float splat_alpha0(float q, float lo)
+{
+    return ex2_approx(fmaf(q, -kHalfLog2e, lo));
 }
 
 // Per-pixel quantities of the ray through pixel offset (dx, dy) in the unit-sphere frame
@@ -50,10 +67,12 @@ __device__ __forceinline__ RayTerms ray_terms(const float4 c0, const float4 c1, 
 __device__ __forceinline__ float rara_weight(const float4 c0, const float4 c1, const float4 c2, const float4 c3,
                                              float dx, float dy)
 {
+    // Every lane evaluates the whole expression and the cases are selected at the end, so a
+    // warp whose pixels fall into different cases does not diverge; the values are the ones
+    // the case-by-case form gives (the unselected ones may be NaN and are never used).
     const RayTerms t = ray_terms(c0, c1, c2, c3, dx, dy);
-    if (t.cc >= 1.0f) return 1.0f;                    // misses or grazes: keep rasterization
     const float h2 = 1.0f - t.cc;
-    if (!(t.GV > 0.0f && t.GV * t.GV > h2 * t.VV)) return 1.0f;  // camera inside or behind
+    const bool hit = t.cc < 1.0f && t.GV > 0.0f && __fmul_rn(t.GV, t.GV) > __fmul_rn(h2, t.VV);  // roots in front
     const float mp = fmaf(c2.x, dx, c2.y * dy);
     const float mV = c1.w + mp;
     const float f = __fmul_rn(t.Gp + t.pp, t.rVV);
@@ -61,9 +80,9 @@ __device__ __forceinline__ float rara_weight(const float4 c0, const float4 c1, c
     const float half = __fmul_rn(__fmul_rn(__fmul_rn(h2, rsqrtf(h2)), mV), rsqrtf(t.VV));
     const float s1 = smid - half, s2 = smid + half;
     const bool v1 = s1 >= 0.0f, v2 = s2 >= 0.0f;
-    if (v1 && v2) return 1.0f;
-    if (!v1 && !v2) return 0.0f;
-    return fminf(1.0f, __fdividef(fmaxf(s1, s2), fabsf(s2 - s1)));
+    const float part = fminf(1.0f, __fdividef(fmaxf(s1, s2), fabsf(s2 - s1)));
+    const float w = v1 == v2 ? (v1 ? 1.0f : 0.0f) : part;
+    return hit ? w : 1.0f;  // a ray that misses, grazes or starts inside keeps rasterization
 }
 
 // The weight of a Gaussian wholly on the invisible side of the plane (kWeightHidden): 0 when
@@ -72,9 +91,8 @@ __device__ __forceinline__ float rara_weight_hidden(const float4 c0, const float
                                                     const float4 c3, float dx, float dy)
 {
     const RayTerms t = ray_terms(c0, c1, c2, c3, dx, dy);
-    if (t.cc >= 1.0f) return 1.0f;
     const float h2 = 1.0f - t.cc;
-    return (t.GV > 0.0f && t.GV * t.GV > h2 * t.VV) ? 0.0f : 1.0f;
+    return (t.cc < 1.0f && t.GV > 0.0f && __fmul_rn(t.GV, t.GV) > __fmul_rn(h2, t.VV)) ? 0.0f : 1.0f;
 }
 
 // Decay weight of a slot with weight mode `mode` (kWeightSplit or kWeightHidden).
@@ -88,36 +106,67 @@ __device__ __forceinline__ float decay_weight(float mode, const float4 c0, const
 // offsets from the projected centre. q is convex, so when the centre lies outside the box
 // the minimum is on an edge, at the edge's 1D minimiser clamped to the edge
 // (dx* = nba dy on a horizontal edge, dy* = nbc dx on a vertical one).
-__device__ __forceinline__ float box_min_q(float ax, float bx, float ay, float by, float a, float b, float c,
+__device__ __forceinline__ float box_min_q(float ax, float bx, float ay, float by, float a, float b2, float c,
                                            float nba, float nbc)
 {
     if (ax <= 0.0f && bx >= 0.0f && ay <= 0.0f && by >= 0.0f) return 0.0f;
     float best;
     {
         const float dx = fminf(bx, fmaxf(ax, nba * ay));
-        best = fmaf(dx, fmaf(a, dx, 2.0f * b * ay), c * ay * ay);
+        best = splat_q(a, b2, c, dx, ay);
     }
     {
         const float dx = fminf(bx, fmaxf(ax, nba * by));
-        best = fminf(best, fmaf(dx, fmaf(a, dx, 2.0f * b * by), c * by * by));
+        best = fminf(best, splat_q(a, b2, c, dx, by));
     }
     {
         const float dy = fminf(by, fmaxf(ay, nbc * ax));
-        best = fminf(best, fmaf(ax, fmaf(a, ax, 2.0f * b * dy), c * dy * dy));
+        best = fminf(best, splat_q(a, b2, c, ax, dy));
     }
     {
         const float dy = fminf(by, fmaxf(ay, nbc * bx));
-        best = fminf(best, fmaf(bx, fmaf(a, bx, 2.0f * b * dy), c * dy * dy));
+        best = fminf(best, splat_q(a, b2, c, bx, dy));
     }
     return best;
 }
 
-constexpr float kCullQ = kSupportQ * 1.0001f;  // margin over float32 rounding of the test
+// Margin of the rectangle test over the float32 rounding of the minimum.
+constexpr float kCullMargin = 1.0001f;
 
-// Shared-memory staging of one batch of list entries.
+// Shared-memory staging of one batch of list entries, as the per-pixel loops read them:
+//   s0 = (mean2d.x, mean2d.y, conic.a, 2 conic.b)
+//   s1 = (conic.c, log2(opacity), q_cut, decay-weight mode)
+//   s2 = (rgb.r, rgb.g, rgb.b, opacity)
+//   nb = (-b/a, -b/c), the rectangle test's line minimisers
+// q_cut = min(9, the q at which alpha0 = opacity exp(-q/2) falls to 1/255, plus a margin
+// over its float32 rounding): a pixel with q > q_cut is outside the 3-sigma support or has
+// alpha0 < 1/255, so it is skipped before the exponential; alpha0 itself is still compared
+// with 1/255 afterwards, so q_cut only saves work and never decides.
 struct Stage {
-    float4 r0[kBlock], r1[kBlock], r2[kBlock];
+    float4 s0[kBlock], s1[kBlock], s2[kBlock];
+    float2 nb[kBlock];
     float4 c0[kBlock], c1[kBlock], c2[kBlock], c3[kBlock];
 };
+
+__device__ __forceinline__ void stage_splat(Stage &st, int i, const SplatRec &rec)
+{
+    const float lo = __log2f(rec.r1.y);
+    const float qa = fmaf(lo + kLog2_255, 1.0f / kHalfLog2e, 1e-4f);
+    st.s0[i] = make_float4(rec.r0.x, rec.r0.y, rec.r0.z, 2.0f * rec.r0.w);
+    st.s1[i] = make_float4(rec.r1.x, lo, fminf(kSupportQ, qa), rec.r2.y);
+    st.s2[i] = make_float4(rec.r1.z, rec.r1.w, rec.r2.x, rec.r1.y);
+    st.nb[i] = make_float2(rec.r2.z, rec.r2.w);
+}
+
+// Exact rectangle test of staged entry j against the box [rx0, rx1] x [ry0, ry1] of pixel
+// centres: whether some pixel of the box can have q <= q_cut.
+__device__ __forceinline__ bool entry_reaches(const Stage &st, int j, float rx0, float rx1, float ry0, float ry1)
+{
+    const float4 s0 = st.s0[j];
+    const float4 s1 = st.s1[j];
+    const float2 nb = st.nb[j];
+    return box_min_q(rx0 - s0.x, rx1 - s0.x, ry0 - s0.y, ry1 - s0.y, s0.z, s0.w, s1.x, nb.x, nb.y) <=
+           s1.z * kCullMargin;
+}
 
 }  // namespace rara

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(uint32_t *keys_a, 
                                                            unsigned int *ticket, unsigned int *status,
                                                            unsigned int *result_in_b,
                                                            const uint32_t *__restrict__ seg_base, int num_segs,
-                                                           int first_seg_pass)
+                                                           int first_seg_pass, int digit_bits)
 {
     __shared__ uint32_t s_warp_hist[kSortWarps][kRadix];
     __shared__ uint32_t s_keys[kPart];
@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(uint32_t *keys_a, 
     uint32_t *keys_out = (flips_before & 1) ? keys_a : keys_b;
     uint32_t *vals_out = (flips_before & 1) ? vals_a : vals_b;
     const bool seg_pass = num_segs > 0 && pass >= first_seg_pass;
-    const int shift = seg_pass ? 8 * (pass - first_seg_pass) : 8 * pass;
+    const int shift = seg_pass ? 8 * (pass - first_seg_pass) : digit_bits * pass;
+    const uint32_t dmask = seg_pass ? 0xffu : (1u << digit_bits) - 1u;
     const int parts = (n + kPart - 1) / kPart;
     s_gstart[tid] = block_excl_scan_256(hist[pass * kRadix + tid], s_tmp);
 
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(uint32_t *keys_a, 
         for (int r = 0; r < kItems; ++r) {
             const int idx = base + r * 32 + lane;
             const bool ok = idx < n;
-            const uint32_t digit = ok ? ((key[r] >> shift) & 0xffu) : 0x100u;
+            const uint32_t digit = ok ? ((key[r] >> shift) & dmask) : 0x100u;
             const unsigned peers = __match_any_sync(0xffffffffu, digit);
             const int leader = 31 - __clz(peers);
             uint32_t prev = 0;
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(uint32_t *keys_a, 
         for (int r = 0; r < kItems; ++r) {
             const int idx = base + r * 32 + lane;
             if (idx < n) {
-                const uint32_t digit = (key[r] >> shift) & 0xffu;
+                const uint32_t digit = (key[r] >> shift) & dmask;
                 const uint32_t pos = s_local_excl[digit] + s_warp_hist[warp][digit] + rank[r];
                 s_keys[pos] = key[r];
                 s_vals[pos] = val[r];
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(uint32_t *keys_a, 
         const int count = min(kPart, n - part * kPart);
         for (int j = tid; j < count; j += kSortThreads) {
             const uint32_t k = s_keys[j];
-            const uint32_t dst = s_out_base[(k >> shift) & 0xffu] + j;
+            const uint32_t dst = s_out_base[(k >> shift) & dmask] + j;
             if (dst < (uint32_t)n) {  // always true unless a bounded wait gave up
                 keys_out[dst] = k;
                 vals_out[dst] = s_vals[j];
@@ -228,7 +229,7 @@ int sort_blocks_per_sm()
 int sort_launch(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, const unsigned long long *n,
                 uint32_t cap, int passes, const uint32_t *hist, void *scratch, unsigned int *tickets,
                 unsigned int *status, unsigned int *result_in_b, int grid, cudaStream_t s,
-                const uint32_t *seg_base, int num_segs, int first_seg_pass)
+                const uint32_t *seg_base, int num_segs, int first_seg_pass, int digit_bits)
 {
     if (passes <= 0 || grid <= 0) return 0;
     const int64_t parts = ((int64_t)cap + kPart - 1) / kPart;
@@ -237,7 +238,7 @@ int sort_launch(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *
         uint32_t *lb = (uint32_t *)scratch + (size_t)p * (size_t)(parts > 0 ? parts : 1) * kRadix;
         k_onesweep<<<grid, kSortThreads, 0, s>>>(keys_a, vals_a, keys_b, vals_b, n, cap, p, passes, hist, lb,
                                                  tickets + p, status, result_in_b, seg_base, num_segs,
-                                                 first_seg_pass);
+                                                 first_seg_pass, digit_bits);
     }
     return passes;
 }
