@@ -45,29 +45,6 @@ struct Tally {
     uint32_t evaluated = 0, walked = 0, cut = 0, tested = 0;
 };
 
-// Alpha of staged entry j at pixel offset (dx, dy) from its centre; 0 when the entry does
-// not contribute (q > q_cut, alpha0 < 1/255, or below 1/255 after the weight). Used by the
-// multi-lane pixel paths, where the lanes of a warp look at different entries.
-__device__ __forceinline__ float entry_alpha(const Stage &st, int j, float pxf, float pyf, Tally &ty)
-{
-    const float4 s0 = st.s0[j];
-    const float4 s1 = st.s1[j];
-    const float dx = pxf - s0.x, dy = pyf - s0.y;
-    const float q = splat_q(s0.z, s0.w, s1.x, dx, dy);
-    ++ty.walked;
-    if (!(q <= s1.z)) return 0.0f;
-    float alpha = splat_alpha0(q, s1.y);
-    if (alpha < kAlphaMin) return 0.0f;
-    ++ty.evaluated;
-    const float mode = s1.w;
-    if (mode != kWeightNone) {
-        if (mode == kWeightSplit) ++ty.cut;
-        alpha = __fmul_rn(alpha, decay_weight(mode, st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy));
-    }
-    alpha = fminf(kAlphaMax, alpha);
-    return alpha < kAlphaMin ? 0.0f : alpha;
-}
-
 // One work item: LPP lanes per pixel. Item geometry (inside the 16x16 tile):
 //   LPP 1: the whole tile, warp rectangles 8x4
 //   LPP 2: rows [8 part, 8 part + 8), warp rectangles 8x2
@@ -165,67 +142,71 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
                     done = done || stop;
                 }
             } else {
+                // LPP lanes per pixel: in each step the lanes of a pixel take the next LPP
+                // kept entries (sub-lane s the (s+1)-th), evaluate their alphas, exchange
+                // (1 - alpha) with shuffles, and every lane of the pixel applies the same
+                // steps of the front-to-back recursion in list order, so all of them agree on
+                // T, on which entries blend and on where the pixel stops. Each lane adds only
+                // its own entry's colour to its partial sums, which are added up at the end.
                 const int group = pix * LPP;          // first lane of this pixel's group
-                const unsigned gmask = ((1u << LPP) - 1u) << group;
                 while (m) {
-                    // sub-lane s takes the (s+1)-th remaining entry of the chunk
-                    unsigned mine = m;
-                    for (int r = 0; r < sub; ++r) mine &= mine - 1u;
-                    unsigned rest = m;
+                    const unsigned m1 = m & (m - 1u), m2 = m1 & (m1 - 1u), m3 = m2 & (m2 - 1u);
+                    const unsigned mine = sub == 0 ? m : (sub == 1 ? m1 : (sub == 2 ? m2 : m3));
+                    m = LPP == 2 ? m2 : (m3 & (m3 - 1u));
+                    const bool has = mine != 0u && !done;
+                    const int j = chunk + (mine ? __ffs(mine) - 1 : 0);
+                    const float4 s0 = st.s0[j];
+                    const float4 s1 = st.s1[j];
+                    const float dx = pxf - s0.x, dy = pyf - s0.y;
+                    const float q = splat_q(s0.z, s0.w, s1.x, dx, dy);
+                    ty.walked += has ? 1u : 0u;
+                    const float a0 = splat_alpha0(q, s1.y);
+                    const bool live = has && q <= s1.z && a0 >= kAlphaMin;
+                    ty.evaluated += live ? 1u : 0u;
+                    float alpha = a0;
+                    const bool wt = live && s1.w != kWeightNone;
+                    if (__any_sync(0xffffffffu, wt)) {
+                        ty.cut += live && s1.w == kWeightSplit ? 1u : 0u;
+                        const float w = decay_weight_any(wt ? s1.w : kWeightNone, st.c0[j], st.c1[j], st.c2[j],
+                                                         st.c3[j], dx, dy);
+                        alpha = __fmul_rn(a0, w);
+                    }
+                    alpha = fminf(kAlphaMax, alpha);
+                    const bool valid = live && alpha >= kAlphaMin;
+                    const float om = valid ? 1.0f - alpha : 1.0f;
+                    // the recursion over the group's entries, identical in its lanes: an entry
+                    // with alpha > 0 (1 - alpha < 1) that would take T below 1e-4 stops the pixel
+                    float t = T, tb = T;
+                    int first = LPP;
 #pragma unroll
-                    for (int r = 0; r < LPP; ++r) rest &= rest - 1u;
-                    m = rest;
-                    float alpha = 0.0f;
-                    int j = 0;
-                    if (!done && mine) {
-                        j = chunk + __ffs(mine) - 1;
-                        alpha = entry_alpha(st, j, pxf, pyf, ty);
+                    for (int k = 0; k < LPP; ++k) {
+                        const float ok = __shfl_sync(0xffffffffu, om, group + k);
+                        if (sub == k) tb = t;
+                        const float tn = t * ok;
+                        if (first == LPP && ok < 1.0f && tn < kTMin) first = k;
+                        if (first == LPP) t = tn;
                     }
-                    // prefix products of (1 - alpha) over the pixel's lanes, in list order
-                    const float om = 1.0f - alpha;
-                    float incl = om;
-#pragma unroll
-                    for (int o = 1; o < LPP; o <<= 1) {
-                        const float v = __shfl_up_sync(0xffffffffu, incl, o, LPP);
-                        if (sub >= o) incl *= v;
-                    }
-                    float excl = __shfl_up_sync(0xffffffffu, incl, 1, LPP);
-                    if (sub == 0) excl = 1.0f;
-                    // the first entry that would take T below 1e-4 stops the pixel, unblended
-                    const bool stop = alpha > 0.0f && T * incl < kTMin;
-                    const unsigned sb = (__ballot_sync(0xffffffffu, stop) & gmask) >> group;
-                    const int first = sb ? __ffs(sb) - 1 : LPP;
-                    const bool blend = alpha > 0.0f && sub < first;
-                    const float wgt = blend ? alpha * excl : 0.0f;
-                    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
-                    uint32_t lp = 0;
-                    if (blend) {
-                        const float4 c = st.s2[j];
-                        s0 = c.x * wgt;
-                        s1 = c.y * wgt;
-                        s2 = c.z * wgt;
-                        lp = (uint32_t)(pos0 + j);
-                    }
-#pragma unroll
-                    for (int o = 1; o < LPP; o <<= 1) {
-                        s0 += __shfl_xor_sync(0xffffffffu, s0, o, LPP);
-                        s1 += __shfl_xor_sync(0xffffffffu, s1, o, LPP);
-                        s2 += __shfl_xor_sync(0xffffffffu, s2, o, LPP);
-                        lp = max(lp, __shfl_xor_sync(0xffffffffu, lp, o, LPP));
-                    }
-                    // transmittance after the group: before the stopping entry, or after all
-                    const float e_first = __shfl_sync(0xffffffffu, excl, group + (first < LPP ? first : 0));
-                    const float i_last = __shfl_sync(0xffffffffu, incl, group + LPP - 1);
-                    if (!done) {
-                        C0 = fmaf(T, s0, C0);
-                        C1 = fmaf(T, s1, C1);
-                        C2 = fmaf(T, s2, C2);
-                        if (lp) last = lp;
-                        T = T * (first < LPP ? e_first : i_last);
-                        done = first < LPP;
-                    }
+                    const bool blend = valid && sub < first;
+                    const float wgt = blend ? alpha * tb : 0.0f;
+                    const float4 s2 = st.s2[j];
+                    C0 = fmaf(s2.x, wgt, C0);
+                    C1 = fmaf(s2.y, wgt, C1);
+                    C2 = fmaf(s2.z, wgt, C2);
+                    last = blend ? (uint32_t)(pos0 + j) : last;
+                    if (!done) T = t;
+                    done = done || first < LPP;
                 }
             }
+        }
+    }
+
+    if (LPP > 1) {  // partial colour sums and last blended position over the pixel's lanes
+#pragma unroll
+        for (int o = 1; o < LPP; o <<= 1) {
+            C0 += __shfl_xor_sync(0xffffffffu, C0, o, LPP);
+            C1 += __shfl_xor_sync(0xffffffffu, C1, o, LPP);
+            C2 += __shfl_xor_sync(0xffffffffu, C2, o, LPP);
+            last = max(last, __shfl_xor_sync(0xffffffffu, last, o, LPP));
         }
     }
 

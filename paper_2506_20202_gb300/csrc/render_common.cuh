@@ -102,6 +102,16 @@ __device__ __forceinline__ float decay_weight(float mode, const float4 c0, const
     return mode == kWeightSplit ? rara_weight(c0, c1, c2, c3, dx, dy) : rara_weight_hidden(c0, c1, c2, c3, dx, dy);
 }
 
+// decay_weight for lanes that may hold entries of different modes (kWeightNone gives 1):
+// both cases are evaluated and selected, with the same values as decay_weight.
+__device__ __forceinline__ float decay_weight_any(float mode, const float4 c0, const float4 c1, const float4 c2,
+                                                  const float4 c3, float dx, float dy)
+{
+    const float ws = rara_weight(c0, c1, c2, c3, dx, dy);
+    const float wh = rara_weight_hidden(c0, c1, c2, c3, dx, dy);
+    return mode == kWeightSplit ? ws : (mode == kWeightHidden ? wh : 1.0f);
+}
+
 // Minimum of q(dx, dy) = a dx^2 + 2 b dx dy + c dy^2 over the box [ax, bx] x [ay, by] of
 // offsets from the projected centre. q is convex, so when the centre lies outside the box
 // the minimum is on an edge, at the edge's 1D minimiser clamped to the edge
