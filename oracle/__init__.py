@@ -48,9 +48,12 @@ def _load():
         lib.orc_preprocess.argtypes = [C.c_int64, P, P, P, P, P, C.c_int, P, C.c_int, C.c_int, P,
                                        C.c_double, C.c_int, C.c_int, C.c_int] + [P] * 15
         lib.orc_count_pairs.restype = C.c_int64
-        lib.orc_count_pairs.argtypes = [C.c_int64, P, P]
+        lib.orc_count_pairs.argtypes = [C.c_int64, P, P, P, P, P, C.c_int, C.c_int, C.c_int, C.c_int]
         lib.orc_build_keys.restype = C.c_int
-        lib.orc_build_keys.argtypes = [C.c_int64, P, P, P, C.c_int, C.c_int, P, P, P]
+        lib.orc_build_keys.argtypes = [C.c_int64, P, P, P, P, P, P, C.c_int, C.c_int, C.c_int, C.c_int,
+                                       P, P, P]
+        lib.orc_box_min_q.restype = C.c_double
+        lib.orc_box_min_q.argtypes = [C.c_double] * 7
         lib.orc_render.restype = C.c_int
         lib.orc_render.argtypes = ([C.c_int64, P, P, P, P, P, P, P, P, P, P, P, P, C.c_int, C.c_int,
                                     P, C.c_double, C.c_int, C.c_int, P, P, P, P, P, C.c_int,
@@ -116,6 +119,7 @@ def preprocess(scene, cam, plane, tile=(16, 16)) -> dict:
                                                    "d_ep", "radius", "margin_class", "margin_gauss",
                                                    "margin_rect")])
     assert rc == 0
+    out["W"], out["H"] = int(cam.width), int(cam.height)
     out["tiles_x"] = (cam.width + tile[0] - 1) // tile[0]
     out["tiles_y"] = (cam.height + tile[1] - 1) // tile[1]
     out["tile"] = tuple(tile)
@@ -126,15 +130,35 @@ def build_keys(pre: dict):
     """Sorted (key, value) pairs and per-tile [start, end) ranges (see orc_build_keys)."""
     lib = _load()
     n = pre["label"].shape[0]
-    p = int(lib.orc_count_pairs(n, _p(pre["culled"]), _p(pre["tiles"])))
+    geo = (_p(pre["rect"]), _p(pre["mean2d"]), _p(pre["conic"]), _p(pre["opacity"]),
+           pre["W"], pre["H"], pre["tile"][0], pre["tile"][1])
+    p = int(lib.orc_count_pairs(n, _p(pre["culled"]), *geo))
     keys = np.zeros(max(p, 1), np.uint64)
     vals = np.zeros(max(p, 1), np.uint32)
     nt = pre["tiles_x"] * pre["tiles_y"]
     ranges = np.zeros((nt, 2), np.int64)
-    rc = lib.orc_build_keys(n, _p(pre["culled"]), _p(pre["rect"]), _p(pre["depth"]),
-                            pre["tiles_x"], pre["tiles_y"], _p(keys), _p(vals), _p(ranges))
+    rc = lib.orc_build_keys(n, _p(pre["culled"]), _p(pre["rect"]), _p(pre["depth"]), *geo[1:],
+                            _p(keys), _p(vals), _p(ranges))
     assert rc == 0
     return keys[:p], vals[:p], ranges
+
+
+def box_min_q(conic, x0, x1, y0, y1) -> float:
+    """Smallest q over the box [x0, x1] x [y0, y1] of offsets (see orc_box_min_q)."""
+    a, b, c = (float(v) for v in conic)
+    return float(_load().orc_box_min_q(a, b, c, float(x0), float(x1), float(y0), float(y1)))
+
+
+def tile_margin(pre: dict, i: int, t: int) -> float:
+    """|smallest q over tile t's pixel-centre rectangle - q_cut| for Gaussian i: how close the
+    tile-listing decision of orc_build_keys is to its threshold."""
+    tw, th = pre["tile"]
+    tx, ty = t % pre["tiles_x"], t // pre["tiles_x"]
+    mx, my = pre["mean2d"][i]
+    x0, x1 = tx * tw + 0.5 - mx, min((tx + 1) * tw, pre["W"]) - 0.5 - mx
+    y0, y1 = ty * th + 0.5 - my, min((ty + 1) * th, pre["H"]) - 0.5 - my
+    qc = min(9.0, 2.0 * np.log(255.0 * pre["opacity"][i]))
+    return abs(box_min_q(pre["conic"][i], x0, x1, y0, y1) - qc)
 
 
 def render(scene, pre: dict, cam, plane, bg=(0.0, 0.0, 0.0), binned=None, tol=DEFAULT_TOL,

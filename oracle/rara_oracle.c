@@ -319,27 +319,83 @@ static int cmp_kv(const void *a, const void *b)
     return 0;
 }
 
-/* Total number of (Gaussian, tile) pairs. */
-int64_t orc_count_pairs(int64_t n, const uint8_t *culled, const int32_t *tiles)
+/* Smallest value of q(dx, dy) = a dx^2 + 2 b dx dy + c dy^2 (a positive definite conic) over
+ * the box [x0, x1] x [y0, y1] of offsets from the projected centre. q is convex: the minimum
+ * is 0 when the box holds the centre, and otherwise lies on the boundary, so it is the
+ * smallest of the four edge minima; along an edge q is a 1D quadratic whose vertex is
+ * clamped to the edge. */
+double orc_box_min_q(double a, double b, double c, double x0, double x1, double y0, double y1)
+{
+    if (x0 <= 0.0 && x1 >= 0.0 && y0 <= 0.0 && y1 >= 0.0) return 0.0;
+    double best = INFINITY;
+    const double ys[2] = {y0, y1}, xs[2] = {x0, x1};
+    for (int k = 0; k < 2; ++k) {
+        /* horizontal edge dy = ys[k]: q = a dx^2 + 2 b ys dx + c ys^2, vertex dx = -b ys / a */
+        double dy = ys[k];
+        double dx = fmin(x1, fmax(x0, -b * dy / a));
+        best = fmin(best, a * dx * dx + 2.0 * b * dx * dy + c * dy * dy);
+        /* vertical edge dx = xs[k]: vertex dy = -b xs / c */
+        dx = xs[k];
+        dy = fmin(y1, fmax(y0, -b * dx / c));
+        best = fmin(best, a * dx * dx + 2.0 * b * dx * dy + c * dy * dy);
+    }
+    return best;
+}
+
+/* q up to which Gaussian i can blend: alpha0 = opacity exp(-q/2) >= 1/255 and q <= 9, so
+ * q_cut = min(9, 2 ln(255 opacity)). Beyond it a pixel skips the Gaussian (Algorithm 1
+ * step 3 skips alpha < 1/255, and the decay weight w <= 1 only lowers alpha). */
+static double q_cut(double opacity)
+{
+    return fmin(9.0, 2.0 * log(255.0 * opacity));
+}
+
+/* Whether tile (tx, ty) lists Gaussian i: the smallest q over the rectangle spanned by the
+ * tile's pixel centres (those inside the W x H image) is at most q_cut. Every pixel centre
+ * of the tile lies in that rectangle, so a pixel where the Gaussian can blend is never in a
+ * tile that does not list it. */
+static int tile_lists(const double *mean2d, const double *conic, const double *opacity, int64_t i, int tx, int ty,
+                      int W, int H, int tile_w, int tile_h)
+{
+    double px0 = tx * tile_w + 0.5, px1 = fmin((double)(tx + 1) * tile_w, (double)W) - 0.5;
+    double py0 = ty * tile_h + 0.5, py1 = fmin((double)(ty + 1) * tile_h, (double)H) - 0.5;
+    double mx = mean2d[2 * i], my = mean2d[2 * i + 1];
+    double m = orc_box_min_q(conic[3 * i], conic[3 * i + 1], conic[3 * i + 2], px0 - mx, px1 - mx, py0 - my,
+                             py1 - my);
+    return m <= q_cut(opacity[i]);
+}
+
+/* Number of (Gaussian, tile) pairs: the tiles of each rendered Gaussian's rectangle that
+ * list it (tile_lists). */
+int64_t orc_count_pairs(int64_t n, const uint8_t *culled, const int32_t *rect, const double *mean2d,
+                        const double *conic, const double *opacity, int W, int H, int tile_w, int tile_h)
 {
     int64_t p = 0;
-    for (int64_t i = 0; i < n; ++i) if (!culled[i]) p += tiles[i];
+    for (int64_t i = 0; i < n; ++i) {
+        if (culled[i]) continue;
+        for (int ty = rect[4 * i + 1]; ty <= rect[4 * i + 3]; ++ty)
+            for (int tx = rect[4 * i]; tx <= rect[4 * i + 2]; ++tx)
+                p += tile_lists(mean2d, conic, opacity, i, tx, ty, W, H, tile_w, tile_h);
+    }
     return p;
 }
 
-/* One key per touched tile: key = tile_id << 32 | bits(float32(depth)), value = Gaussian
+/* One key per listing tile: key = tile_id << 32 | bits(float32(depth)), value = Gaussian
  * index, tile_id = ty * tiles_x + tx. Sorted ascending by (key, index), which is the
  * stable sort of the index-ordered emission. ranges[2t], ranges[2t+1] = [start, end) of
  * tile t in the sorted list (zero-length when empty). */
 int orc_build_keys(int64_t n, const uint8_t *culled, const int32_t *rect, const double *depth,
-                   int tiles_x, int tiles_y, uint64_t *keys, uint32_t *vals, int64_t *ranges)
+                   const double *mean2d, const double *conic, const double *opacity, int W, int H,
+                   int tile_w, int tile_h, uint64_t *keys, uint32_t *vals, int64_t *ranges)
 {
+    const int tiles_x = (W + tile_w - 1) / tile_w, tiles_y = (H + tile_h - 1) / tile_h;
     int64_t p = 0;
     for (int64_t i = 0; i < n; ++i) {
         if (culled[i]) continue;
         uint32_t db = f32_bits(depth[i]);
         for (int ty = rect[4 * i + 1]; ty <= rect[4 * i + 3]; ++ty)
             for (int tx = rect[4 * i]; tx <= rect[4 * i + 2]; ++tx) {
+                if (!tile_lists(mean2d, conic, opacity, i, tx, ty, W, H, tile_w, tile_h)) continue;
                 keys[p] = ((uint64_t)(uint32_t)(ty * tiles_x + tx) << 32) | db;
                 vals[p] = (uint32_t)i;
                 ++p;

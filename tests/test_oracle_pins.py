@@ -568,24 +568,81 @@ def test_single_gaussian_coverage_monotone_in_offset(orc):
 # ------------------------------------------------------------------------------------
 
 def test_keys_single_gaussian_by_hand(orc):
+    """One isotropic Gaussian: q = |d|^2 / var, so a tile lists it iff the squared distance
+    from the centre to the tile's rectangle of pixel centres is at most var q_cut, with
+    q_cut = min(9, 2 ln(255 opacity)); the candidates are the tiles of the 3-sigma box."""
     cam = axis_camera(64, 64, 64.0)
     z = 2.0
-    sc = make_scene([[0.1, -0.2, z]], [[0.03] * 3])
-    pre = orc.preprocess(sc, cam, plane([0, 0, 1], 1e20, scenes.MODE_NONE))
-    keys, vals, ranges = orc.build_keys(pre)
-    s32 = float(np.exp(np.float64(np.float32(math.log(0.03)))))
-    var = (64 * s32 / z) ** 2 + 0.3
-    h = 3 * math.sqrt(var)
-    mx = 64 * float(np.float32(0.1)) / z + 32
-    my = 64 * float(np.float32(-0.2)) / z + 32
-    tx = range(max(0, math.floor((mx - h) / 16)), min(3, math.floor((mx + h) / 16)) + 1)
-    ty = range(max(0, math.floor((my - h) / 16)), min(3, math.floor((my + h) / 16)) + 1)
-    dbits = int(np.float32(z).view(np.uint32))
-    exp = sorted(((y * 4 + x) << 32) | dbits for y in ty for x in tx)
-    assert list(keys) == exp and list(vals) == [0] * len(exp)
-    for k, key in enumerate(exp):
-        t = key >> 32
-        assert tuple(ranges[t]) == (k, k + 1)
+    for op in (0.5, 0.02):
+        sc = make_scene([[0.1, -0.2, z]], [[0.03] * 3], opacity=[op])
+        pre = orc.preprocess(sc, cam, plane([0, 0, 1], 1e20, scenes.MODE_NONE))
+        keys, vals, ranges = orc.build_keys(pre)
+        s32 = float(np.exp(np.float64(np.float32(math.log(0.03)))))
+        var = (64 * s32 / z) ** 2 + 0.3
+        h = 3 * math.sqrt(var)
+        mx = 64 * float(np.float32(0.1)) / z + 32
+        my = 64 * float(np.float32(-0.2)) / z + 32
+        lg = float(np.float32(math.log(op / (1 - op))))
+        qc = min(9.0, 2 * math.log(255 / (1 + math.exp(-lg))))
+        tx = range(max(0, math.floor((mx - h) / 16)), min(3, math.floor((mx + h) / 16)) + 1)
+        ty = range(max(0, math.floor((my - h) / 16)), min(3, math.floor((my + h) / 16)) + 1)
+
+        def dist2(x, y):
+            ddx = max(x * 16 + 0.5 - mx, 0.0, mx - (x * 16 + 15.5))
+            ddy = max(y * 16 + 0.5 - my, 0.0, my - (y * 16 + 15.5))
+            return ddx * ddx + ddy * ddy
+
+        dbits = int(np.float32(z).view(np.uint32))
+        exp = sorted(((y * 4 + x) << 32) | dbits for y in ty for x in tx if dist2(x, y) <= var * qc)
+        assert exp
+        assert list(keys) == exp and list(vals) == [0] * len(exp)
+        for k, key in enumerate(exp):
+            t = key >> 32
+            assert tuple(ranges[t]) == (k, k + 1)
+
+
+def _box_min_q_lsq(conic, x0, x1, y0, y1):
+    """Smallest q over a box by bounded least squares (scipy): q = |L^T d|^2, conic = L L^T."""
+    from scipy.optimize import lsq_linear
+    a, b, c = conic
+    L = np.linalg.cholesky(np.array([[a, b], [b, c]]))
+    r = lsq_linear(L.T, np.zeros(2), bounds=([x0, y0], [x1, y1]), tol=1e-14, method="bvls")
+    return float(r.cost * 2.0)
+
+
+def test_box_min_q_against_bounded_least_squares(orc):
+    rng = np.random.default_rng(31)
+    for _ in range(300):
+        A = rng.standard_normal((2, 2)) * rng.uniform(0.05, 2.0)
+        C = A @ A.T + 0.05 * np.eye(2)
+        conic = (C[0, 0], C[0, 1], C[1, 1])
+        x0, y0 = rng.uniform(-12, 8, 2)
+        x1, y1 = x0 + rng.uniform(0, 15), y0 + rng.uniform(0, 15)
+        got = orc.box_min_q(conic, x0, x1, y0, y1)
+        ref = _box_min_q_lsq(conic, x0, x1, y0, y1)
+        assert got == pytest.approx(ref, rel=1e-9, abs=1e-12)
+    assert orc.box_min_q((1.0, 0.2, 2.0), -1.0, 3.0, -2.0, 0.5) == 0.0   # centre inside
+
+
+def _numpy_tile_lists(pre, i, x, y):
+    """Tile-listing rule restated in numpy: the minimum of the convex q over the tile's
+    pixel-centre rectangle, 0 if it holds the centre, else the smallest edge minimum."""
+    a, b, c = pre["conic"][i]
+    mx, my = pre["mean2d"][i]
+    x0, x1 = x * 16 + 0.5 - mx, min(x * 16 + 16, pre["W"]) - 0.5 - mx
+    y0, y1 = y * 16 + 0.5 - my, min(y * 16 + 16, pre["H"]) - 0.5 - my
+    if x0 <= 0 <= x1 and y0 <= 0 <= y1:
+        m = 0.0
+    else:
+        cand = []
+        for dy in (y0, y1):
+            dx = np.clip(-b * dy / a, x0, x1)
+            cand.append(a * dx * dx + 2 * b * dx * dy + c * dy * dy)
+        for dx in (x0, x1):
+            dy = np.clip(-b * dx / c, y0, y1)
+            cand.append(a * dx * dx + 2 * b * dx * dy + c * dy * dy)
+        m = min(cand)
+    return m <= min(9.0, 2 * np.log(255 * pre["opacity"][i]))
 
 
 def test_keys_match_numpy_stable_sort(orc):
@@ -594,6 +651,7 @@ def test_keys_match_numpy_stable_sort(orc):
     keys, vals, ranges = orc.build_keys(pre)
     ek, ev = [], []
     tx = pre["tiles_x"]
+    dropped = 0
     for i in range(sc.n):
         if pre["culled"][i]:
             continue
@@ -601,8 +659,12 @@ def test_keys_match_numpy_stable_sort(orc):
         db = int(np.float32(pre["depth"][i]).view(np.uint32))
         for y in range(y0, y1 + 1):
             for x in range(x0, x1 + 1):
+                if not _numpy_tile_lists(pre, i, x, y):
+                    dropped += 1
+                    continue
                 ek.append(((y * tx + x) << 32) | db)
                 ev.append(i)
+    assert dropped > 0
     ek, ev = np.array(ek, np.uint64), np.array(ev, np.uint32)
     order = np.argsort(ek, kind="stable")
     assert np.array_equal(keys, ek[order]) and np.array_equal(vals, ev[order])
@@ -612,3 +674,23 @@ def test_keys_match_numpy_stable_sort(orc):
         s, e = ranges[t]
         assert np.all(tiles[s:e] == t)
     assert (ranges[:, 1] - ranges[:, 0]).sum() == len(keys)
+
+
+def test_every_blending_pixel_is_in_a_listing_tile(orc):
+    """Brute force over pixels: wherever alpha0 = opacity exp(-q/2) >= 1/255 with q <= 9,
+    the pixel's tile lists the Gaussian (so the tiles left out cannot change a pixel)."""
+    sc, cam, pl = scenes.small_uniform_workload(n=1500, width=80, height=64, seed=8)
+    pre = orc.preprocess(sc, cam, pl)
+    keys, vals, ranges = orc.build_keys(pre)
+    listed = set(zip((keys >> np.uint64(32)).astype(np.int64).tolist(), vals.tolist()))
+    ys, xs = np.mgrid[0:64, 0:80]
+    checked = 0
+    for i in np.nonzero(pre["culled"] == 0)[0]:
+        a, b, c = pre["conic"][i]
+        dx, dy = xs + 0.5 - pre["mean2d"][i][0], ys + 0.5 - pre["mean2d"][i][1]
+        q = a * dx * dx + 2 * b * dx * dy + c * dy * dy
+        hit = (q <= 9.0) & (pre["opacity"][i] * np.exp(-0.5 * q) >= 1.0 / 255.0)
+        for y, x in zip(*np.nonzero(hit)):
+            assert ((y // 16) * pre["tiles_x"] + x // 16, int(i)) in listed
+            checked += 1
+    assert checked > 1000
