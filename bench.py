@@ -42,7 +42,8 @@ UNIT = "frames/s"
 # Algorithmic FP32 work of the render kernel per unit (see the design notes):
 #   rectangle test   min of q over a warp's 8x4 pixel box (4 edges)  36 FLOP (one per warp and entry)
 #   walked pair      dx, dy and the conic quadratic form q            9 FLOP
-#   in-support pair  alpha = delta exp(-q/2), clamp, T update, RGB   12 FLOP + 1 MUFU (ex2)
+#   blending pair    alpha0 = delta exp(-q/2) >= 1/255 with q <= 9:
+#                    alpha0, clamp, T update, RGB                     12 FLOP + 1 MUFU (ex2)
 #   cutoff pair      ray-traced decay weight (Eq. 4-8, 11)           60 FLOP + 3 MUFU
 FLOP_TEST, FLOP_WALKED, FLOP_EVAL, FLOP_CUT = 36, 9, 12, 60
 SMS, FP32_LANES = 152, 128  # GB300: 152 SMs x 128 FP32 lanes, FMA = 2 FLOP

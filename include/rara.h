@@ -5,8 +5,10 @@
  *   rara_preprocess  per-Gaussian three-way classification against the clip plane
  *                    (Section 3.2, Eq. 3; Algorithm 1 step 1), EWA projection to a 2D
  *                    conic (Section 3.4, Eq. 9-10), SH colour, tile rectangle
- *   rara_bin         one (tile id | depth) key per touched tile, radix-sorted so every tile
- *                    holds its Gaussians front to back (Section 3.1, "sorted by depth")
+ *   rara_bin         one (tile id | depth) key per listing tile, radix-sorted so every tile
+ *                    holds its Gaussians front to back (Section 3.1, "sorted by depth"); a
+ *                    tile of the 3-sigma rectangle lists a Gaussian where some pixel centre
+ *                    of the tile can blend it (alpha0 >= 1/255, Algorithm 1 step 3)
  *   rara_render      per pixel, front-to-back compositing (Eq. 2) of alpha from Eq. 10,
  *                    with the ray-ellipsoid decay weight (Eq. 4-8, Eq. 11, Eq. 12;
  *                    Algorithm 1 steps 2-3) for cutoff Gaussians and early termination
@@ -151,8 +153,10 @@ int64_t rara_ctx_launches(const rara_ctx *ctx);
 int rara_preprocess(rara_ctx *ctx, const rara_gaussians *g, const rara_camera *cam,
                     const rara_plane *plane, void *stream);
 
-/* Step (b): emit one pair per (Gaussian, touched tile), radix-sort by (tile id, depth),
- * and build per-tile ranges. Must follow rara_preprocess on the same context. Blocks the
+/* Step (b): emit one pair per (Gaussian, listing tile): a tile of the Gaussian's rectangle
+ * whose box of pixel centres reaches q <= q_cut = min(9, 2 ln(255 opacity)), the pixels
+ * where alpha0 = opacity exp(-q/2) can reach 1/255 (no other pixel can blend the Gaussian);
+ * radix-sort by (tile id, depth), and build per-tile ranges. Must follow rara_preprocess on the same context. Blocks the
  * host once (stream synchronisation) to size the pair buffers. */
 int rara_bin(rara_ctx *ctx, void *stream);
 
@@ -234,10 +238,12 @@ typedef struct rara_frame_info {
     int64_t n;            /* Gaussians in the frame */
     int64_t n_rendered;   /* not invisible, not culled, at least one tile */
     int64_t n_cutoff;     /* rendered and labelled cutoff */
-    int64_t n_pairs;      /* (Gaussian, tile) pairs */
+    int64_t n_pairs;      /* (Gaussian, tile) pairs listed: a tile of the Gaussian's 3-sigma
+                             rectangle lists it where some pixel centre of the tile can have
+                             alpha0 = opacity exp(-q/2) >= 1/255 with q <= 9 */
     int32_t tiles_x, tiles_y;
-    int64_t n_evaluated;  /* (pixel, Gaussian) pairs of the last rara_render inside the
-                             q <= 9 support (alpha computed) */
+    int64_t n_evaluated;  /* (pixel, Gaussian) pairs of the last rara_render with
+                             alpha0 >= 1/255 inside the q <= 9 support */
     int64_t n_walked;     /* (pixel, Gaussian) pairs whose q was computed, i.e. tile-list
                              entries visited by pixels still compositing */
     int64_t n_cut_evaluated; /* evaluated pairs that needed the ray-traced weight */
@@ -250,7 +256,8 @@ int rara_frame_info_get(rara_ctx *ctx, int32_t view, rara_frame_info *out);
  * NULL; n is the view's scene size):
  * labels uint8[n]; depth float[n] (camera z); mean2d float[2][n]; conic float[3][n]
  * (a, b, c of [[a,b],[b,c]], the inverse 2D covariance); rgb float[3][n]; opacity float[n];
- * rect int32[4][n] (inclusive tx0, ty0, tx1, ty1); tiles uint32[n] (0 when culled).
+ * rect int32[4][n] (inclusive tx0, ty0, tx1, ty1); tiles uint32[n] (tiles of the rectangle,
+ * 0 when culled).
  * Fields other than labels are defined only where tiles > 0. */
 int rara_frame_gaussians(rara_ctx *ctx, int32_t view, uint8_t *labels, float *depth, float *mean2d,
                          float *conic, float *rgb, float *opacity, int32_t *rect,

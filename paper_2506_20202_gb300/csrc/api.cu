@@ -456,6 +456,7 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
     e.vals_b = (const uint32_t *)c->cvals_b.p;
     e.tiles = (const uint32_t *)c->tiles.p;
     e.rect = (const uint2 *)c->rect.p;
+    e.rec = (const SplatRec *)c->rec.p;
     e.views = (const ViewDev *)c->views_d.p;
     e.num_views = c->num_views;
     e.cap_pairs = cap;
@@ -990,7 +991,18 @@ int rara_frame_info_get(rara_ctx *c, int32_t view, rara_frame_info *out)
     out->n = c->h_view_n[k];
     out->n_rendered = (int64_t)c->h_view_counters[k].n_rendered;
     out->n_cutoff = (int64_t)c->h_view_counters[k].n_cutoff;
-    out->n_pairs = (int64_t)c->h_view_counters[k].n_pairs;
+    // pairs the binning listed: the sum of the view's tile-list lengths
+    const int nt = v.tiles_x * v.tiles_y;
+    int2 *hr = (int2 *)malloc(sizeof(int2) * (size_t)(nt > 0 ? nt : 1));
+    if (!hr) return fail(c, RARA_ERR_BUDGET, "host allocation failed");
+    rc = check_cuda(c, cudaMemcpy(hr, (const int2 *)c->ranges.p + v.tile_base, sizeof(int2) * (size_t)nt,
+                                  cudaMemcpyDeviceToHost), "ranges copy");
+    int64_t np = 0;
+    for (int t = 0; t < nt && !rc; ++t)
+        if (hr[t].y > hr[t].x) np += hr[t].y - hr[t].x;
+    free(hr);
+    if (rc) return rc;
+    out->n_pairs = np;
     out->tiles_x = v.tiles_x;
     out->tiles_y = v.tiles_y;
     out->n_evaluated = (int64_t)c->h_counters->n_evaluated;

@@ -11,6 +11,7 @@
 // contiguous and the tile sort only needs the local tile bits.
 #include "chained_scan.cuh"
 #include "rara_internal.cuh"
+#include "render_common.cuh"
 
 namespace rara {
 
@@ -28,24 +29,117 @@ __device__ __forceinline__ int view_of_slot(const ViewDev *views, int num_views,
     return lo;
 }
 
-// Emission, persistent over partitions of kEmitPart consecutive depth-ordered slots. A
-// partition loads its slots (thread t takes slot r * kBlock + t of row r, coalesced), scans
-// their tile counts into per-slot offsets, gets its first pair position from a chained scan,
-// and then writes its pairs striped over the block: output k of the partition goes to
-// thread k mod kBlock, which finds the slot owning k by binary search over the offsets and
-// the tile from k's position inside the slot's rectangle (row-major). Consecutive threads
-// thus store consecutive pairs (full 128-byte lines per warp), however uneven the
-// rectangles, and a slot with many tiles is spread over the whole block.
-constexpr int kEmitItems = 4;
+// Emission, persistent over partitions of kEmitPart consecutive depth-ordered slots.
+//
+// A tile of a slot's rectangle lists the slot when some pixel centre of the tile can have
+// q <= q_cut (elsewhere alpha0 = opacity exp(-q/2) < 1/255 or q > 9, and the pixel would skip
+// the Gaussian). In tile row ty the pixel centres span the band y in [py0, py1]; the part of
+// the ellipse q <= q_cut inside the band is convex, so its x-extent is one interval [XL, XR]
+// and the listing tiles of the row are the contiguous columns whose pixel centres reach it.
+// With the conic (a, b, c) and D = ac - b^2, the ellipse's left boundary
+// x_l(y) = (-b y - sqrt(a q_cut - D y^2)) / a is convex with its minimum at the leftmost point
+// y_L = b sqrt(q_cut / (c D)), so XL = x_l(y_L clamped to the band); XR mirrors it
+// (row_span below; offsets relative to the projected centre).
+//
+// A partition loads its slots and reserves room for their rectangles' rows in a
+// shared-memory row pool (block scan of the rectangle heights); thread t owns slots 2t and
+// 2t + 1. Each thread computes its slots' row spans into the pool (first column and the
+// slot's pairs before the row) and their listed-pair counts; the block scans the counts into
+// per-slot offsets and a chained scan places the partition. Each warp then writes the pairs
+// of its own 64 slots, 32 consecutive pairs at a time (coalesced stores): the slots starting
+// in the window mark their first position in a warp-private array, a shuffle prefix maximum
+// gives every lane the slot owning its pair, and a binary search over the slot's pooled rows
+// gives the tile. A slot whose rows do not fit the pool recomputes its spans when it writes.
+constexpr int kEmitItems = 2;
 constexpr uint32_t kEmitPart = kBlock * kEmitItems;
+constexpr uint32_t kRowPool = 4096;
+constexpr uint32_t kNoPool = 0xffffffffu;
+
+// Per-splat constants of the listing spans: conic (a, b, c), q_cut and their derived terms.
+struct SpanGeo {
+    float mx, my, aq, D, ia, b, ymax, yl;
+    int x0, x1, y0, W, H;
+    bool ok;
+};
+
+// r0, r1: the first two float4 of the slot's splat record (centre, conic, opacity).
+__device__ __forceinline__ SpanGeo span_geo(const float4 r0, const float4 r1, uint2 rc, const ViewDev &vw)
+{
+    SpanGeo g;
+    const float a = r0.z, b = r0.w, c = r1.x;
+    const float qc = splat_qcut(__log2f(r1.y));
+    g.mx = r0.x; g.my = r0.y; g.b = b;
+    g.D = fmaf(a, c, -__fmul_rn(b, b));
+    g.aq = __fmul_rn(a, qc);
+    g.ia = 1.0f / a;
+    g.ok = qc >= 0.0f && g.D > 0.0f;
+    g.ymax = g.ok ? sqrtf(g.aq / g.D) : 0.0f;
+    g.yl = g.ok ? __fmul_rn(b, sqrtf(qc / __fmul_rn(c, g.D))) : 0.0f;
+    g.x0 = rc.x & 0xffff; g.y0 = rc.x >> 16; g.x1 = rc.y & 0xffff;
+    g.W = vw.cam.W; g.H = vw.cam.H;
+    return g;
+}
+
+// Listing columns [lo, lo + count) of tile row ty (count 0 when none). Every product that
+// feeds a sum is rounded on its own (__fmul_rn), so each call site computes the same spans.
+__device__ __forceinline__ void row_span(const SpanGeo &g, int ty, int &lo, int &count)
+{
+    const float by0 = __fsub_rn((float)(ty * kTile) + 0.5f, g.my);
+    const float by1 = __fsub_rn((float)min((ty + 1) * kTile, g.H) - 0.5f, g.my);
+    const float y0 = fmaxf(by0, -g.ymax), y1 = fminf(by1, g.ymax);
+    count = 0;
+    lo = g.x0;
+    if (!(g.ok && y0 <= y1)) return;
+    const float ya = fminf(y1, fmaxf(y0, g.yl)), yb = fminf(y1, fmaxf(y0, -g.yl));
+    const float ra = sqrtf(fmaxf(0.0f, fmaf(-__fmul_rn(g.D, ya), ya, g.aq)));
+    const float rb = sqrtf(fmaxf(0.0f, fmaf(-__fmul_rn(g.D, yb), yb, g.aq)));
+    const float XL = __fmul_rn(__fsub_rn(-__fmul_rn(g.b, ya), ra), g.ia);
+    const float XR = __fmul_rn(__fadd_rn(-__fmul_rn(g.b, yb), rb), g.ia);
+    if (XL > __fsub_rn((float)g.W - 0.5f, g.mx)) return;  // right of the image's last pixel centres
+    // column tx reaches the interval iff tx 16 + 15.5 - mx >= XL and tx 16 + 0.5 - mx <= XR
+    const int c0 = max(g.x0, (int)ceilf(__fmul_rn(__fsub_rn(__fadd_rn(XL, g.mx), 15.5f), 1.0f / kTile)));
+    const int c1 = min(g.x1, (int)floorf(__fmul_rn(__fsub_rn(__fadd_rn(XR, g.mx), 0.5f), 1.0f / kTile)));
+    lo = c0;
+    count = max(0, c1 - c0 + 1);
+}
+
+// Exclusive block scan (256 threads) of per-thread sums; returns this thread's prefix and
+// the block total in *total. Uses s_w[8].
+__device__ __forceinline__ uint32_t block_scan_u32(uint32_t v, uint32_t *s_w, uint32_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+    for (int w = 0; w < kBlock / 32; ++w) {
+        const uint32_t u = s_w[w];
+        if (w < warp) before += u;
+        all += u;
+    }
+    __syncthreads();
+    *total = all;
+    return before + incl - v;
+}
 
 __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
 {
     __shared__ uint32_t s_hist[4][256];
-    __shared__ uint32_t s_off[kEmitPart + 1];      // tile counts, then exclusive offsets
+    __shared__ uint32_t s_off[kEmitPart + 1];       // pair offsets of the slots, then the total
+    __shared__ uint32_t s_roff[kEmitPart];          // first pooled row of the slot, or kNoPool
+    __shared__ uint32_t s_nrows[kEmitPart];         // rows of the rectangle
     __shared__ uint32_t s_slot[kEmitPart];
-    __shared__ uint32_t s_t0[kEmitPart];           // global tile id of the rectangle's first tile
-    __shared__ uint32_t s_geo[kEmitPart];          // rectangle width | view's tiles_x << 16
+    __shared__ uint32_t s_view[kEmitPart];
+    __shared__ uint32_t s_t0[kEmitPart];            // global tile id of the rectangle's origin
+    __shared__ uint32_t s_tx[kEmitPart];            // the view's tiles per row
+    __shared__ uint16_t s_rcol[kRowPool];           // first listing column of a pooled row (from x0)
+    __shared__ uint32_t s_rcum[kRowPool];           // the slot's pairs before the row
+    __shared__ int s_mark[kBlock / 32][32];
+    __shared__ uint32_t s_w[kBlock / 32];
     __shared__ unsigned s_part;
     __shared__ unsigned long long s_warp[kBlock / 32];
     __shared__ unsigned long long s_prefix;
@@ -64,40 +158,56 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
         const uint32_t part = s_part;
         if (part >= parts) break;
         const uint32_t first = part * kEmitPart;
-        uint32_t slot[kEmitItems];
+        uint32_t slot[kEmitItems], rows[kEmitItems];
+        uint2 rc[kEmitItems];
+        uint32_t nrows = 0;
 #pragma unroll
         for (int r = 0; r < kEmitItems; ++r) {
-            const uint32_t i = first + r * kBlock + threadIdx.x;
+            const uint32_t i = first + threadIdx.x * kEmitItems + r;
             slot[r] = i < n ? __ldg(&vals[i]) : 0u;
+            rc[r] = i < n ? __ldg(&a.rect[slot[r]]) : make_uint2(0u, 0u);
+            const int y0 = rc[r].x >> 16, y1 = rc[r].y >> 16;
+            const int x0 = rc[r].x & 0xffff, x1 = rc[r].y & 0xffff;
+            rows[r] = (i < n && x0 <= x1 && y0 <= y1) ? (uint32_t)(y1 - y0 + 1) : 0u;
+            nrows += rows[r];
         }
-#pragma unroll
-        for (int r = 0; r < kEmitItems; ++r) {
-            const int j = r * kBlock + threadIdx.x;
-            uint32_t cnt = 0, t0 = 0, geo = 0;
-            if (first + j < n) {
-                const uint2 rc = __ldg(&a.rect[slot[r]]);
-                const int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
-                if (x0 <= x1 && y0 <= y1) {
-                    const ViewDev &vw = a.views[view_of_slot(a.views, a.num_views, slot[r])];
-                    cnt = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
-                    t0 = vw.tile_base + (uint32_t)(y0 * vw.tiles_x + x0);
-                    geo = (uint32_t)(x1 - x0 + 1) | ((uint32_t)vw.tiles_x << 16);
-                }
-            }
-            s_off[j] = cnt;
-            s_slot[j] = slot[r];
-            s_t0[j] = t0;
-            s_geo[j] = geo;
-        }
-        __syncthreads();
-        // thread t scans the kEmitItems consecutive counts [t * kEmitItems, ...)
-        uint32_t c[kEmitItems];
+        uint32_t allrows;
+        uint32_t rbase = block_scan_u32(nrows, s_w, &allrows);
+        uint32_t cnt[kEmitItems];
         uint32_t sum = 0;
 #pragma unroll
         for (int r = 0; r < kEmitItems; ++r) {
-            c[r] = s_off[threadIdx.x * kEmitItems + r];
-            sum += c[r];
+            const int j = threadIdx.x * kEmitItems + r;
+            cnt[r] = 0;
+            uint32_t v = 0, roff = kNoPool, t0 = 0, txs = 0;
+            if (rows[r]) {
+                v = (uint32_t)view_of_slot(a.views, a.num_views, slot[r]);
+                const ViewDev &vw = a.views[v];
+                const SpanGeo g = span_geo(a.rec[slot[r]].r0, a.rec[slot[r]].r1, rc[r], vw);
+                t0 = vw.tile_base + (uint32_t)(g.y0 * vw.tiles_x + g.x0);
+                txs = (uint32_t)vw.tiles_x;
+                const bool pooled = rbase + rows[r] <= kRowPool;
+                if (pooled) roff = rbase;
+                for (uint32_t k = 0; k < rows[r]; ++k) {
+                    int lo, c;
+                    row_span(g, g.y0 + (int)k, lo, c);
+                    if (pooled) {
+                        s_rcol[rbase + k] = (uint16_t)(lo - g.x0);
+                        s_rcum[rbase + k] = cnt[r];
+                    }
+                    cnt[r] += (uint32_t)c;
+                }
+            }
+            rbase += rows[r];
+            s_roff[j] = roff;
+            s_nrows[j] = rows[r];
+            s_slot[j] = slot[r];
+            s_view[j] = v;
+            s_t0[j] = t0;
+            s_tx[j] = txs;
+            sum += cnt[r];
         }
+        // pair offsets of the slots, and the partition's place among all pairs
         unsigned long long incl = sum;
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
@@ -118,6 +228,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
             if (lane == 0) {
                 s_prefix = prefix;
                 s_off[kEmitPart] = (uint32_t)total;  // a partition's pairs are < 2^32
+                if (part == parts - 1) a.counters->n_pairs = prefix + total;  // all listed pairs
             }
         }
         __syncthreads();
@@ -125,26 +236,66 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
 #pragma unroll
         for (int r = 0; r < kEmitItems; ++r) {
             s_off[threadIdx.x * kEmitItems + r] = run;
-            run += c[r];
+            run += cnt[r];
         }
         __syncthreads();
+        // this warp's slots [jw, jw + 64) and pairs [ws, we)
         const unsigned long long pbase = s_prefix;
-        const uint32_t total = s_off[kEmitPart];
-        int j = 0;  // owner of the previous output of this thread (owners never decrease)
-        for (uint32_t k = threadIdx.x; k < total; k += kBlock) {
-            // last j with s_off[j] <= k (empty slots share their successor's offset)
-            int lo = j, hi = (int)kEmitPart - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_off[mid] <= k) lo = mid;
-                else hi = mid - 1;
+        const int jw = warp * 32 * kEmitItems;
+        const uint32_t ws = s_off[jw], we = s_off[jw + 32 * kEmitItems];
+        int carry = -1;
+        for (uint32_t c0 = ws; c0 < we; c0 += 32) {
+            s_mark[warp][lane] = -1;
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < kEmitItems; ++r) {
+                const int j = jw + lane * kEmitItems + r;
+                const uint32_t st = s_off[j];
+                if (s_off[j + 1] > st && st >= c0 && st < c0 + 32u) s_mark[warp][st - c0] = j;
             }
-            j = lo;
+            __syncwarp();
+            int owner = s_mark[warp][lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, owner, o);
+                if (lane >= o) owner = max(owner, u);
+            }
+            owner = max(owner, carry);
+            carry = __shfl_sync(0xffffffffu, owner, 31);
+            __syncwarp();
+            const uint32_t k = c0 + (uint32_t)lane;
+            if (k >= we || owner < 0) continue;
+            const int j = owner;
             const uint32_t r = k - s_off[j];
-            const uint32_t geo = s_geo[j];
-            const uint32_t w = geo & 0xffffu;
-            const uint32_t y = r / w, x = r - y * w;
-            const uint32_t t = s_t0[j] + y * (geo >> 16) + x;
+            int dy = 0, dx = 0;
+            const uint32_t roff = s_roff[j];
+            if (roff != kNoPool) {
+                // last pooled row of the slot with s_rcum <= r (rows without pairs share the
+                // next row's value, so the row found has pairs)
+                int rl = (int)roff, rh = (int)roff + (int)s_nrows[j] - 1;
+                while (rl < rh) {
+                    const int mid = (rl + rh + 1) >> 1;
+                    if (s_rcum[mid] <= r) rl = mid;
+                    else rh = mid - 1;
+                }
+                dy = rl - (int)roff;
+                dx = (int)s_rcol[rl] + (int)(r - s_rcum[rl]);
+            } else {
+                const uint32_t sl = s_slot[j];
+                const SpanGeo g = span_geo(a.rec[sl].r0, a.rec[sl].r1, a.rect[sl], a.views[s_view[j]]);
+                uint32_t rr = r;
+                for (int k2 = 0; k2 < (int)s_nrows[j]; ++k2) {  // the spans of the count phase
+                    int lo2, c2;
+                    row_span(g, g.y0 + k2, lo2, c2);
+                    if (rr < (uint32_t)c2) {
+                        dy = k2;
+                        dx = lo2 - g.x0 + (int)rr;
+                        break;
+                    }
+                    rr -= (uint32_t)c2;
+                }
+            }
+            const uint32_t t = s_t0[j] + (uint32_t)dy * s_tx[j] + (uint32_t)dx;
             const unsigned long long off = pbase + k;
             if (off < a.cap_pairs) {
                 a.pair_keys[off] = t;

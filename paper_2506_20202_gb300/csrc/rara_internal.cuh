@@ -111,6 +111,8 @@ struct SceneDev {
     uint32_t unit_begin;         // first preprocess unit (256-Gaussian block) of the scene
 };
 
+// n_pairs counts candidate pairs (the tiles of the rendered slots' rectangles), an upper
+// bound of the pairs the emission lists; it sizes the pair buffers.
 struct ViewCounters {
     unsigned long long n_rendered, n_pairs, n_cutoff;
 };
@@ -118,7 +120,8 @@ struct ViewCounters {
 // Counters written by the kernels (device), copied to pinned host memory in one block.
 struct Counters {
     unsigned long long n_rendered;       // rendered slots (all views)
-    unsigned long long n_pairs;          // pairs (all views)
+    unsigned long long n_pairs;          // candidate pairs after the preprocess; the emission
+                                         // replaces them with the pairs it lists (all views)
     unsigned long long n_cutoff;
     unsigned int num_items;              // render work items (written by the item-order kernel)
     unsigned int depth_in_b;             // 1 if the depth sort's result is in its B buffers
@@ -203,6 +206,7 @@ struct EmitArgs {
     const uint32_t *keys_a, *vals_a, *keys_b, *vals_b;  // the depth sort's two buffers
     const uint32_t *tiles;
     const uint2 *rect;
+    const SplatRec *rec;     // the splats (the per-tile listing test)
     const ViewDev *views;
     int num_views;
     uint32_t cap_pairs;

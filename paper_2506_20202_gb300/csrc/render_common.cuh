@@ -158,12 +158,17 @@ struct Stage {
     float4 c0[kBlock], c1[kBlock], c2[kBlock], c3[kBlock];
 };
 
+// q_cut of a splat from log2(opacity) (see Stage).
+__device__ __forceinline__ float splat_qcut(float lo)
+{
+    return fminf(kSupportQ, fmaf(lo + kLog2_255, 1.0f / kHalfLog2e, 1e-4f));
+}
+
 __device__ __forceinline__ void stage_splat(Stage &st, int i, const SplatRec &rec)
 {
     const float lo = __log2f(rec.r1.y);
-    const float qa = fmaf(lo + kLog2_255, 1.0f / kHalfLog2e, 1e-4f);
     st.s0[i] = make_float4(rec.r0.x, rec.r0.y, rec.r0.z, 2.0f * rec.r0.w);
-    st.s1[i] = make_float4(rec.r1.x, lo, fminf(kSupportQ, qa), rec.r2.y);
+    st.s1[i] = make_float4(rec.r1.x, lo, splat_qcut(lo), rec.r2.y);
     st.s2[i] = make_float4(rec.r1.z, rec.r1.w, rec.r2.x, rec.r1.y);
     st.nb[i] = make_float2(rec.r2.z, rec.r2.w);
 }

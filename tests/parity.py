@@ -14,6 +14,7 @@ IMG_MAX_ABS = 2e-3
 IMG_MEAN_ABS = 1e-4
 CLASS_EXEMPT = 1e-6   # world units from a class threshold
 RECT_EXEMPT = 2e-3    # pixels from a tile edge (float32 position + footprint error)
+TILE_EXEMPT = 0.03    # |smallest q over a tile - q_cut| under which float32 may list differently
 
 
 def gpu_frame(scene, cam, plane, bg=(0.0, 0.0, 0.0), renderer=None, export=True, tuning=None):
@@ -96,6 +97,7 @@ def check_pairs(pre, kvr, gpu, report):
     exact_tiles = 0
     tie_swaps = 0
     odepth32 = pre["depth"].astype(np.float32).view(np.int32).astype(np.int64)
+    listing_exempt = 0
     for t in range(nt):
         o = ovals[oranges[t, 0]:oranges[t, 1]]
         g = gvals[granges[t, 0]:granges[t, 1]]
@@ -103,6 +105,16 @@ def check_pairs(pre, kvr, gpu, report):
         g = g[~ex[g]]
         if np.array_equal(o, g):
             exact_tiles += 1
+            continue
+        # a Gaussian listed on one side only must be at the listing threshold of that tile
+        only = np.setxor1d(o, g)
+        for i in only:
+            m = oracle.tile_margin(pre, int(i), t)
+            assert m <= TILE_EXEMPT, f"tile {t}: Gaussian {i} listed on one side only (margin {m:.3g})"
+        listing_exempt += only.size
+        o = o[~np.isin(o, only)]
+        g = g[~np.isin(g, only)]
+        if np.array_equal(o, g):
             continue
         assert np.array_equal(np.sort(o), np.sort(g)), f"tile {t}: member sets differ"
         # order may differ only among Gaussians whose float32 depths are within 2 ulp
@@ -114,6 +126,8 @@ def check_pairs(pre, kvr, gpu, report):
     report["tiles_exact"] = exact_tiles
     report["tiles"] = nt
     report["tie_swaps"] = tie_swaps
+    report["listing_exempt"] = listing_exempt
+    assert listing_exempt <= 1e-3 * max(1, okeys.size) + 5, "too many pairs at the listing threshold"
 
 
 def check_image(pre, ref, gpu, report, rows=None, max_flag_frac=0.05, extra_mask=None):

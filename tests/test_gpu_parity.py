@@ -167,6 +167,24 @@ def test_hair_strand_scene(tuning):
     assert 0.2 <= frac <= 0.6, frac
 
 
+def test_large_splats_tall_rectangles():
+    """Splats tens of tiles tall: a partition's rectangle rows overflow the emission's
+    shared-memory row pool, so part of the pairs come from recomputed row spans."""
+    rng = np.random.default_rng(41)
+    n = 900
+    means = np.column_stack([rng.uniform(-0.9, 0.9, n), rng.uniform(-0.7, 0.7, n), rng.uniform(2.0, 3.2, n)])
+    sc = make_scene(means, np.exp(rng.normal(-1.6, 0.3, (n, 3))), quats=rng.standard_normal((n, 4)),
+                    opacity=rng.uniform(0.02, 0.6, n), rgb=rng.uniform(0, 1, (n, 3)))
+    cam = axis_camera(480, 352, 300.0)
+    nrm = rng.standard_normal(3)
+    nrm /= np.linalg.norm(nrm)
+    pl = plane(nrm, -float(nrm @ [0.0, 0.0, 2.6]))
+    rep, gpu, ref = full_check(sc, cam, pl, bg=(0.1, 0.1, 0.1), max_flag_frac=0.1)
+    g = gpu["g"]
+    rows = (g["rect"][3] - g["rect"][1] + 1)[g["tiles"] > 0]
+    assert rows[:512].sum() > 4096  # the first partition's rows exceed the pool
+
+
 def test_shell_scene():
     scene = scenes.shells_scene(per_shell=30_000, seed=1)
     cam = scenes.look_at_camera((0.5, -0.4, -2.6), (0.0, 0.0, 0.0), 192, 160, 60.0)
