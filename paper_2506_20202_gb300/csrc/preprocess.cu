@@ -27,6 +27,31 @@ __device__ __forceinline__ void cross3(const float a[3], const float b[3], float
     out[2] = fmaf(a[0], b[1], -a[1] * b[0]);
 }
 
+// r0 x + r1 y + r2 z + t in doubled float32 precision, rounded once: the compensated dot
+// product "Dot2" of Ogita, Rump and Oishi (Accurate sum and dot product, SIAM J. Sci.
+// Comput. 26(6), 2005), with each product split exactly by an FMA (p + e = a b) and each
+// sum by Knuth's TwoSum (s + e = a + b); the rounding errors are added up and folded in
+// at the end. Every operation is explicitly rounded, so no contraction changes it.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ float dot2_depth(float r0, float r1, float r2, float t, float x, float y, float z)
+{
+    const float p0 = __fmul_rn(r0, x), e0 = fmaf(r0, x, -p0);
+    const float p1 = __fmul_rn(r1, y), e1 = fmaf(r1, y, -p1);
+    const float p2 = __fmul_rn(r2, z), e2 = fmaf(r2, z, -p2);
+    float s, f0, f1, f2;
+    two_sum(p0, p1, s, f0);
+    two_sum(s, p2, s, f1);
+    two_sum(s, t, s, f2);
+    const float err = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, f0)), __fadd_rn(f1, f2));
+    return __fadd_rn(s, err);
+}
+
 // Colour along the unit direction (x, y, z): sum_k sh_k Y_k + 0.5, clamped at 0. The
 // thread's coefficients are staged in shared memory, s_sh[(k * 3 + c) * kBlock + thread].
 __device__ __forceinline__ void sh_colour(const float *s_sh, int degree, float x, float y, float z, float rgb[3])
@@ -185,11 +210,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_preprocess(PreprocessArgs a)
                             rec.r0 = make_float4(mx2, my2, cc * idet, -cb * idet);
                             rec.r1 = make_float4(ca * idet, op, rgb[0], rgb[1]);
                             float wmode = 0.0f;
-                            // The sort key holds the depth rounded once from a double-precision
-                            // dot product: the correctly rounded float32 of the exact depth.
-                            a.depth[slot] = (float)fma((double)cam.R[6], (double)mx,
-                                                       fma((double)cam.R[7], (double)my,
-                                                           fma((double)cam.R[8], (double)mz, (double)cam.t[2])));
+                            // The sort key holds the depth rounded once from a dot product
+                            // carried in doubled float32 precision (dot2), i.e. the correctly
+                            // rounded float32 of the exact depth except within about 2^-48 of
+                            // a rounding midpoint.
+                            a.depth[slot] = dot2_depth(cam.R[6], cam.R[7], cam.R[8], cam.t[2], mx, my, mz);
 
                             if (cutoff) {
                                 // Ray-tracing record in the unit-sphere frame of M = k R S
