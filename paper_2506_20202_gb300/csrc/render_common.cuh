@@ -173,15 +173,39 @@ __device__ __forceinline__ void stage_splat(Stage &st, int i, const SplatRec &re
     st.nb[i] = make_float2(rec.r2.z, rec.r2.w);
 }
 
+// A cutoff Gaussian wholly on the invisible side (kWeightHidden) has w = 0, hence alpha = 0,
+// at every pixel whose ray hits its ellipsoid in front of the camera. With the camera outside
+// the ellipsoid those pixels form a convex region of the image (the central projection of the
+// ellipsoid's part in front of the camera), and so do the pixels whose rays pass within
+// sqrt(0.999) of its centre (in the unit-sphere frame) with G.V above a margin. If the four
+// corners of a box of pixel centres (offsets [ax, bx] x [ay, by] from the projected centre)
+// lie in that smaller region, every pixel of the box does, and its float32 hit test (cc < 1,
+// G.V > 0, (G.V)^2 > (1 - cc) V.V, whose margin is (G.G - 1) V.V) cannot fail: the entry is
+// nothing to the box.
+__device__ __forceinline__ bool hidden_covers_box(const Stage &st, int j, float ax, float bx, float ay, float by)
+{
+    const float4 c0 = st.c0[j], c1 = st.c1[j], c2 = st.c2[j], c3 = st.c3[j];
+    if (!(c0.x >= 1.001f)) return false;  // camera outside the ellipsoid, with a margin
+    bool all = true;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const RayTerms t = ray_terms(c0, c1, c2, c3, k & 1 ? bx : ax, k & 2 ? by : ay);
+        all = all && t.cc <= 0.999f && t.GV >= 1e-4f * (c0.x + fabsf(t.Gp));
+    }
+    return all;
+}
+
 // Exact rectangle test of staged entry j against the box [rx0, rx1] x [ry0, ry1] of pixel
-// centres: whether some pixel of the box can have q <= q_cut.
+// centres: whether some pixel of the box can have q <= q_cut and, for a Gaussian wholly on
+// the invisible side, can miss its ellipsoid (elsewhere its alpha is 0).
 __device__ __forceinline__ bool entry_reaches(const Stage &st, int j, float rx0, float rx1, float ry0, float ry1)
 {
     const float4 s0 = st.s0[j];
     const float4 s1 = st.s1[j];
     const float2 nb = st.nb[j];
-    return box_min_q(rx0 - s0.x, rx1 - s0.x, ry0 - s0.y, ry1 - s0.y, s0.z, s0.w, s1.x, nb.x, nb.y) <=
-           s1.z * kCullMargin;
+    const float ax = rx0 - s0.x, bx = rx1 - s0.x, ay = ry0 - s0.y, by = ry1 - s0.y;
+    const bool reach = box_min_q(ax, bx, ay, by, s0.z, s0.w, s1.x, nb.x, nb.y) <= s1.z * kCullMargin;
+    return reach && !(s1.w == kWeightHidden && hidden_covers_box(st, j, ax, bx, ay, by));
 }
 
 }  // namespace rara
