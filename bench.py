@@ -247,6 +247,23 @@ def run_reference(args):
 # our arm
 # --------------------------------------------------------------------------------------
 
+def max_over_ranks(value: float, dist) -> float:
+    """The largest of a per-rank float over all ranks (the slowest rank's time), through the
+    host process group; the value itself with one rank (dist None)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units per second of the whole job: every rank processed units_per_rank (weak scaling)
+    and the job took the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def percentile(xs, p):
     xs = sorted(xs)
     if not xs:
@@ -375,12 +392,8 @@ def run_ours(args):
     rara.rara_ctx_sync(bctx, stream)   # raises if a replay overflowed its pair capacity
     if dist:
         dist.barrier()
-    elapsed_ms = t_begin.elapsed_time(t_end)
-    if dist:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = world * args.steps * nplanes / (elapsed_ms / 1e3)
+    elapsed_ms = max_over_ranks(t_begin.elapsed_time(t_end), dist)
+    value = whole_job_rate(args.steps * nplanes, world, elapsed_ms / 1e3)
     blat = [e[0].elapsed_time(e[1]) for e in sevs]
     batched = {"frames_per_s": value, "batch_p50_ms": percentile(blat, 50), "batch_p99_ms": percentile(blat, 99),
                "views_per_batch": nplanes, "tuning": list(best),
@@ -442,14 +455,11 @@ def run_ours(args):
         rara.rara_ctx_sync(ectx, stream)
         e2e_s = time.perf_counter() - t0
         rara.rara_ctx_destroy(ectx)
-        e2e = {"value": world * args.e2e_steps * nplanes / e2e_s, "unit": UNIT,
+        e2e_s = max_over_ranks(e2e_s, dist)
+        e2e = {"value": whole_job_rate(args.e2e_steps * nplanes, world, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "note": "per step: scene upload from pinned host memory + one C-ABI batched render of the 16 sweep "
                        "frames (graph replay) + read-back of every image into pinned host memory; host wall clock"}
-        if dist:
-            t = torch.tensor([e2e_s], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e["value"] = world * args.e2e_steps * nplanes / float(t.item())
     rara.rara_ctx_destroy(bctx)
 
     line = {
