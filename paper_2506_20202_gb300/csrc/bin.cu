@@ -63,6 +63,13 @@ struct SpanGeo {
 };
 
 // r0, r1: the first two float4 of the slot's splat record (centre, conic, opacity).
+// sqrt(x) for x >= 0 from the special function unit's reciprocal square root (0 at 0);
+// the listing needs the spans only to within the float32 tolerance of its threshold.
+__device__ __forceinline__ float fast_sqrt(float x)
+{
+    return x > 0.0f ? __fmul_rn(x, rsqrtf(x)) : 0.0f;
+}
+
 __device__ __forceinline__ SpanGeo span_geo(const float4 r0, const float4 r1, uint2 rc, const ViewDev &vw)
 {
     SpanGeo g;
@@ -71,10 +78,10 @@ __device__ __forceinline__ SpanGeo span_geo(const float4 r0, const float4 r1, ui
     g.mx = r0.x; g.my = r0.y; g.b = b;
     g.D = fmaf(a, c, -__fmul_rn(b, b));
     g.aq = __fmul_rn(a, qc);
-    g.ia = 1.0f / a;
+    g.ia = __fdividef(1.0f, a);
     g.ok = qc >= 0.0f && g.D > 0.0f;
-    g.ymax = g.ok ? sqrtf(g.aq / g.D) : 0.0f;
-    g.yl = g.ok ? __fmul_rn(b, sqrtf(qc / __fmul_rn(c, g.D))) : 0.0f;
+    g.ymax = g.ok ? fast_sqrt(__fdividef(g.aq, g.D)) : 0.0f;
+    g.yl = g.ok ? __fmul_rn(b, fast_sqrt(__fdividef(qc, __fmul_rn(c, g.D)))) : 0.0f;
     g.x0 = rc.x & 0xffff; g.y0 = rc.x >> 16; g.x1 = rc.y & 0xffff;
     g.W = vw.cam.W; g.H = vw.cam.H;
     return g;
@@ -91,8 +98,8 @@ __device__ __forceinline__ void row_span(const SpanGeo &g, int ty, int &lo, int 
     lo = g.x0;
     if (!(g.ok && y0 <= y1)) return;
     const float ya = fminf(y1, fmaxf(y0, g.yl)), yb = fminf(y1, fmaxf(y0, -g.yl));
-    const float ra = sqrtf(fmaxf(0.0f, fmaf(-__fmul_rn(g.D, ya), ya, g.aq)));
-    const float rb = sqrtf(fmaxf(0.0f, fmaf(-__fmul_rn(g.D, yb), yb, g.aq)));
+    const float ra = fast_sqrt(fmaxf(0.0f, fmaf(-__fmul_rn(g.D, ya), ya, g.aq)));
+    const float rb = fast_sqrt(fmaxf(0.0f, fmaf(-__fmul_rn(g.D, yb), yb, g.aq)));
     const float XL = __fmul_rn(__fsub_rn(-__fmul_rn(g.b, ya), ra), g.ia);
     const float XR = __fmul_rn(__fadd_rn(-__fmul_rn(g.b, yb), rb), g.ia);
     if (XL > __fsub_rn((float)g.W - 0.5f, g.mx)) return;  // right of the image's last pixel centres
