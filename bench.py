@@ -72,6 +72,8 @@ def parse_args():
     ap.add_argument("--train-steps", type=int, default=6, help="forward+backward steps of the multi-layer "
                     "differentiation workload (0: skip)")
     ap.add_argument("--train-per-shell", type=int, default=700_000)
+    ap.add_argument("--hair-steps", type=int, default=20, help="frames of the hair-strand workload per path "
+                    "(0: skip)")
     ap.add_argument("--train-views", type=int, default=64)
     return ap.parse_args()
 
@@ -476,6 +478,8 @@ def run_ours(args):
                                                        for c in counts],
                          "pairs_mean": statistics.mean(c["n_pairs"] for c in counts)},
     }
+    if rank == 0 and world == 1 and args.hair_steps > 0:
+        line["hair"] = run_hair(args)
     if rank == 0 and world == 1 and args.train_steps > 0:
         line["training"] = run_training(args)
     if rank == 0 and world == 1 and args.serve_s > 0:
@@ -602,6 +606,96 @@ def run_training(args):
            "setup_s": setup_s}
     rara.rara_ctx_destroy(ctx)
     del gs, grads, dimgs, targets, tviews, views
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_hair(args):
+    """Hair-strand workload: 500k strand Gaussians (10,000 cubic curves x 50 segments, axis
+    scales 1:1:40 along the tangent, SH 1) at 1024x1024 with an oblique plane cutting 30-50%
+    of them. The plain path renders one frame per launch sequence from a fixed camera; the
+    batched path renders 16 views on an orbit around the head as one graph replay."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_2506_20202_gb300 import autotune, rara, scenes
+    scene, nrm, d = scenes.hair_scene(curves=10_000, segments=50, seed=0)
+    gs = rara.GaussianTensors.from_scene(scene)
+    pl = scenes.Plane(np.asarray(nrm, np.float32), float(d), 3.0, scenes.MODE_RARA)
+    W = H = 1024
+    cam = scenes.look_at_camera((0.2, -0.3, -3.2), (0.0, 0.3, 0.0), W, H, 60.0)
+    stream = torch.cuda.Stream()
+    out = {"workload": "hair strands: 500,000 Gaussians (10,000 curves x 50 segments, scales 1:1:40, SH 1), "
+                       "1024x1024, one oblique plane"}
+    ctx = rara.rara_ctx_create(0)
+    img = torch.empty((3, H, W), device="cuda")
+    T = torch.empty((H, W), device="cuda")
+    nc = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.hair_steps)]
+
+    def frame(e=None):
+        if e is not None:
+            e[0].record(stream)
+        rara.rara_preprocess(ctx, gs, cam, pl, stream)
+        rara.rara_bin(ctx, stream)
+        rara.rara_render(ctx, (0.0, 0.0, 0.0), img, T, nc, stream)
+        if e is not None:
+            e[1].record(stream)
+
+    for _ in range(3):
+        frame()
+    info = rara.rara_frame_info_get(ctx)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for e in ev:
+        frame(e)
+    t1.record(stream)
+    stream.synchronize()
+    lat = [e[0].elapsed_time(e[1]) for e in ev]
+    out["plain"] = {"frames_per_s": args.hair_steps / (t0.elapsed_time(t1) / 1e3), "p50_ms": percentile(lat, 50),
+                    "p99_ms": percentile(lat, 99)}
+    out["cutoff_fraction_of_rendered"] = info["n_cutoff"] / max(1, info["n_rendered"])
+    out["cutoff_fraction_of_all"] = info["n_cutoff"] / scene.n
+    out["pairs"] = info["n_pairs"]
+    rara.rara_ctx_destroy(ctx)
+    # batched: 16 views on an orbit of radius 3.2 around the head, one graph replay per step
+    bctx = rara.rara_ctx_create(0)
+    views = []
+    for k in range(16):
+        a = 2.0 * math.pi * k / 16
+        c = scenes.look_at_camera((3.2 * math.sin(a), -0.3, -3.2 * math.cos(a)), (0.0, 0.3, 0.0), W, H, 60.0)
+        views.append(rara.View(0, c, pl, torch.empty((3, H, W), device="cuda"), torch.empty((H, W), device="cuda"),
+                               torch.empty((H, W), dtype=torch.int32, device="cuda"), (0.0, 0.0, 0.0)))
+    if args.tuning:
+        best = tuple(int(x) for x in args.tuning.split(","))
+        rara.rara_ctx_set_tuning(bctx, *best)
+    else:
+        best, _ = autotune.autotune(bctx, [gs], views, stream, reps=2)
+    rara.rara_render_batch(bctx, [gs], views, stream)
+    stage = rara.rara_ctx_stage_ms(bctx)
+    for _ in range(3):
+        rara.rara_render_batch_graph(bctx, [gs], views, stream)
+    rara.rara_ctx_sync(bctx, stream)
+    bev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.hair_steps)]
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for e in bev:
+        e[0].record(stream)
+        rara.rara_render_batch_graph(bctx, [gs], views, stream)
+        e[1].record(stream)
+    t1.record(stream)
+    stream.synchronize()
+    rara.rara_ctx_sync(bctx, stream)
+    blat = [e[0].elapsed_time(e[1]) for e in bev]
+    out["batched_graph"] = {"frames_per_s": 16 * args.hair_steps / (t0.elapsed_time(t1) / 1e3),
+                            "batch_p50_ms": percentile(blat, 50), "batch_p99_ms": percentile(blat, 99),
+                            "views_per_batch": 16, "tuning": list(best),
+                            "stage_ms_exact_batch": {"preprocess": stage[0], "bin": stage[1], "render": stage[2]}}
+    rara.rara_ctx_destroy(bctx)
+    del gs, views
     torch.cuda.empty_cache()
     return out
 
