@@ -567,10 +567,13 @@ def run_training(args):
         return loss
 
     mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    # the forward's work counts (the backward's roofline units) from an exact render: graph
+    # replays run the render without its counters
+    rara.rara_render_batch(ctx, [gs], views, stream)
+    info = rara.rara_frame_info_get(ctx, 0)
     for _ in range(2):
         step(mk())
     rara.rara_ctx_sync(ctx, stream)
-    info = rara.rara_frame_info_get(ctx, 0)
     setup_s = time.perf_counter() - t_setup
     evs = [mk() for _ in range(args.train_steps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

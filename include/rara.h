@@ -232,8 +232,9 @@ int rara_render_backward(rara_ctx *ctx, const float *const *dL_dimages, const ra
 int rara_ctx_backward_ms(rara_ctx *ctx, float out[2]);
 
 /* Counts of one view of the current frame or batch (view 0 for a single frame), valid after
- * rara_bin; the render counts are totals of the last rara_render over all views. Waits for
- * the context's last stream to read them. */
+ * rara_bin; the render counts are totals over all views of the last render launched outside
+ * a CUDA graph (rara_render, rara_render_batch): graph replays render without the work
+ * counters and leave them 0. Waits for the context's last stream to read them. */
 typedef struct rara_frame_info {
     int64_t n;            /* Gaussians in the frame */
     int64_t n_rendered;   /* not invisible, not culled, at least one tile */

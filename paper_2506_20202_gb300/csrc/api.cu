@@ -510,7 +510,8 @@ int batch_render(rara_ctx *c, cudaStream_t s)
     a.counters = dc;
     const long long slots = (long long)c->sm_count * c->bpsm_render;
     const long long items = 4ll * c->num_tiles;
-    launch_render(a, (int)(items < slots ? items : slots), s);
+    // graph captures run without the work counters (their replays are not read for them)
+    launch_render(a, (int)(items < slots ? items : slots), s, !c->capturing);
     rc = launched(c, "render launch", c->num_tiles > 0);
     mark(c, 3, s);
     return rc;

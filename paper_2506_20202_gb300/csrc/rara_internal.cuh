@@ -244,7 +244,8 @@ struct RenderArgs {
     int num_views;
     Counters *counters;
 };
-void launch_render(const RenderArgs &a, int grid, cudaStream_t s);
+// count: accumulate the work counters (n_evaluated .. n_tested) of the launch.
+void launch_render(const RenderArgs &a, int grid, cudaStream_t s, bool count = true);
 int render_blocks_per_sm();
 
 // Backward. Per-slot gradient record, 7 x float4 = 112 bytes, accumulated (atomics) by the

@@ -41,17 +41,24 @@ namespace rara {
 
 namespace {
 
+// Work counters of a render launch (the units of its roofline). COUNT = false drops them:
+// the graph replays of a batch, which nothing reads them from, run without them.
+template <bool COUNT>
 struct Tally {
     uint32_t evaluated = 0, walked = 0, cut = 0, tested = 0;
+    __device__ __forceinline__ void add(uint32_t &c, bool v)
+    {
+        if (COUNT) c += v ? 1u : 0u;
+    }
 };
 
 // One work item: LPP lanes per pixel. Item geometry (inside the 16x16 tile):
 //   LPP 1: the whole tile, warp rectangles 8x4
 //   LPP 2: rows [8 part, 8 part + 8), warp rectangles 8x2
 //   LPP 4: rows [4 part, 4 part + 4), warp rectangles 4x2
-template <int LPP>
+template <int LPP, bool COUNT>
 __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &vw, const uint32_t *pair_vals,
-                                            Stage &st, int gtile, int tile, int part, Tally &ty)
+                                            Stage &st, int gtile, int tile, int part, Tally<COUNT> &ty)
 {
     constexpr int RW = LPP == 4 ? 4 : 8;     // warp rectangle width
     constexpr int RH = LPP == 1 ? 4 : 2;     // warp rectangle height
@@ -101,7 +108,7 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
             if (jt < cnt) {
                 keep = entry_reaches(st, jt, rx0, rx1, ry0, ry1);
                 weighted = st.s1[jt].w != kWeightNone;
-                ++ty.tested;
+                ty.add(ty.tested, true);
             }
             unsigned m = __ballot_sync(0xffffffffu, keep);
             if (LPP == 1) {
@@ -117,14 +124,14 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
                     const float4 s1 = st.s1[j];
                     const float dx = pxf - s0.x, dy = pyf - s0.y;
                     const float q = splat_q(s0.z, s0.w, s1.x, dx, dy);
-                    ty.walked += done ? 0u : 1u;
+                    ty.add(ty.walked, !done);
                     const float a0 = splat_alpha0(q, s1.y);
                     const bool live = !done && q <= s1.z && a0 >= kAlphaMin;
-                    ty.evaluated += live ? 1u : 0u;
+                    ty.add(ty.evaluated, live);
                     float alpha = a0;
                     if ((mw >> bit) & 1u) {
                         const float mode = s1.w;
-                        ty.cut += live && mode == kWeightSplit ? 1u : 0u;
+                        ty.add(ty.cut, live && mode == kWeightSplit);
                         alpha = __fmul_rn(a0, decay_weight(mode, st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy));
                     }
                     alpha = fminf(kAlphaMax, alpha);
@@ -159,14 +166,14 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
                     const float4 s1 = st.s1[j];
                     const float dx = pxf - s0.x, dy = pyf - s0.y;
                     const float q = splat_q(s0.z, s0.w, s1.x, dx, dy);
-                    ty.walked += has ? 1u : 0u;
+                    ty.add(ty.walked, has);
                     const float a0 = splat_alpha0(q, s1.y);
                     const bool live = has && q <= s1.z && a0 >= kAlphaMin;
-                    ty.evaluated += live ? 1u : 0u;
+                    ty.add(ty.evaluated, live);
                     float alpha = a0;
                     const bool wt = live && s1.w != kWeightNone;
                     if (__any_sync(0xffffffffu, wt)) {
-                        ty.cut += live && s1.w == kWeightSplit ? 1u : 0u;
+                        ty.add(ty.cut, live && s1.w == kWeightSplit);
                         const float w = decay_weight_any(wt ? s1.w : kWeightNone, st.c0[j], st.c1[j], st.c2[j],
                                                          st.c3[j], dx, dy);
                         alpha = __fmul_rn(a0, w);
@@ -221,11 +228,12 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
     }
 }
 
+template <bool COUNT>
 __global__ void __launch_bounds__(kBlock, 5) k_render(RenderArgs a)
 {
     __shared__ Stage st;
     __shared__ unsigned s_item;
-    Tally ty;
+    Tally<COUNT> ty;
     const unsigned num_items = *(volatile unsigned *)&a.counters->num_items;
     const uint32_t *pair_vals = a.counters->tile_in_b ? a.vals_b : a.vals_a;
     for (;;) {
@@ -246,12 +254,13 @@ __global__ void __launch_bounds__(kBlock, 5) k_render(RenderArgs a)
         }
         const ViewDev &vw = a.views[lo];
         const int tile = gtile - (int)vw.tile_base;
-        if (lpp_log2 == 0) render_item<1>(a, vw, pair_vals, st, gtile, tile, 0, ty);
-        else if (lpp_log2 == 1) render_item<2>(a, vw, pair_vals, st, gtile, tile, part, ty);
-        else render_item<4>(a, vw, pair_vals, st, gtile, tile, part, ty);
+        if (lpp_log2 == 0) render_item<1, COUNT>(a, vw, pair_vals, st, gtile, tile, 0, ty);
+        else if (lpp_log2 == 1) render_item<2, COUNT>(a, vw, pair_vals, st, gtile, tile, part, ty);
+        else render_item<4, COUNT>(a, vw, pair_vals, st, gtile, tile, part, ty);
         __syncthreads();  // everyone has read s_item and the staged batch
     }
 
+    if (!COUNT) return;
     unsigned long long ev = ty.evaluated, wk = ty.walked, ce = ty.cut, ts = ty.tested;
     for (int o = 16; o > 0; o >>= 1) {
         ev += __shfl_xor_sync(0xffffffffu, ev, o);
@@ -272,16 +281,18 @@ __global__ void __launch_bounds__(kBlock, 5) k_render(RenderArgs a)
 int render_blocks_per_sm()
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_render, kBlock, 0) != cudaSuccess || b < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_render<true>, kBlock, 0) != cudaSuccess || b < 1) {
         cudaGetLastError();
         b = 1;
     }
     return b;
 }
 
-void launch_render(const RenderArgs &a, int grid, cudaStream_t s)
+void launch_render(const RenderArgs &a, int grid, cudaStream_t s, bool count)
 {
-    if (grid > 0) k_render<<<grid, kBlock, 0, s>>>(a);
+    if (grid <= 0) return;
+    if (count) k_render<true><<<grid, kBlock, 0, s>>>(a);
+    else k_render<false><<<grid, kBlock, 0, s>>>(a);
 }
 
 }  // namespace rara
