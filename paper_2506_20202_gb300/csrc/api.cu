@@ -375,11 +375,13 @@ int batch_preprocess(rara_ctx *c, cudaStream_t s)
     a.depth = (float *)c->depth.p;
     a.view_counters = (ViewCounters *)c->view_counters_d.p;
     a.counters = dc;
-    int max_degree = 0;
-    for (int si = 0; si < c->num_scenes; ++si)
+    int max_degree = 0, max_views = 0;
+    for (int si = 0; si < c->num_scenes; ++si) {
         if (c->h_scenes[si].view_count > 0 && c->h_scenes[si].sh_degree > max_degree)
             max_degree = c->h_scenes[si].sh_degree;
-    launch_preprocess(a, (int)c->num_units, max_degree, s);
+        if (c->h_scenes[si].view_count > max_views) max_views = c->h_scenes[si].view_count;
+    }
+    launch_preprocess(a, (int)c->num_units, max_degree, max_views, s);
     if ((rc = launched(c, "preprocess launch", c->num_units > 0))) return rc;
 
     CompactArgs ca;

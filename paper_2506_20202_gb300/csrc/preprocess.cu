@@ -76,7 +76,11 @@ constexpr int kViewChunk = 16;  // views staged in shared memory at a time
 // every view of the scene is processed from registers and shared memory; the views' tables
 // are staged kViewChunk at a time. Per-view counts are summed per warp and per block in
 // shared memory and added to the global counters once per chunk.
-__global__ void __launch_bounds__(kBlock, 4) k_preprocess(PreprocessArgs a)
+// MINB: blocks per SM the register budget is sized for. With many views per Gaussian the
+// per-view loop is arithmetic and wants every register (3 blocks); with few views the kernel
+// streams the scene and wants warps in flight (4 blocks).
+template <int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
 {
     extern __shared__ float s_sh[];  // [3 (degree+1)^2][kBlock]
     __shared__ ViewDev s_views[kViewChunk];
@@ -379,14 +383,19 @@ __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
 int preprocess_configure()
 {
     const int most = 3 * 16 * kBlock * (int)sizeof(float);  // SH degree 3
-    return cudaFuncSetAttribute(k_preprocess, cudaFuncAttributeMaxDynamicSharedMemorySize, most) == cudaSuccess ? 0
-                                                                                                              : -1;
+    const bool ok = cudaFuncSetAttribute(k_preprocess<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) ==
+                        cudaSuccess &&
+                    cudaFuncSetAttribute(k_preprocess<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) ==
+                        cudaSuccess;
+    return ok ? 0 : -1;
 }
 
-void launch_preprocess(const PreprocessArgs &a, int grid, int max_sh_degree, cudaStream_t s)
+void launch_preprocess(const PreprocessArgs &a, int grid, int max_sh_degree, int max_views, cudaStream_t s)
 {
     const int smem = 3 * (max_sh_degree + 1) * (max_sh_degree + 1) * kBlock * (int)sizeof(float);
-    if (grid > 0) k_preprocess<<<grid, kBlock, smem, s>>>(a);
+    if (grid <= 0) return;
+    if (max_views >= 4) k_preprocess<3><<<grid, kBlock, smem, s>>>(a);
+    else k_preprocess<4><<<grid, kBlock, smem, s>>>(a);
 }
 
 int compact_blocks_per_sm()

@@ -163,7 +163,8 @@ struct PreprocessArgs {
 };
 // max_sh_degree sizes the shared-memory staging of the SH coefficients (the largest degree
 // of a scene with views); preprocess_configure() must have succeeded once per device.
-void launch_preprocess(const PreprocessArgs &a, int grid, int max_sh_degree, cudaStream_t s);
+// max_views: the most views of one scene in the batch (picks the register budget).
+void launch_preprocess(const PreprocessArgs &a, int grid, int max_sh_degree, int max_views, cudaStream_t s);
 int preprocess_configure();
 
 // Stage 2: compaction of rendered slots (slot order) + histogram of the depth-key digits
