@@ -52,6 +52,56 @@ __device__ __forceinline__ float dot2_depth(float r0, float r1, float r2, float 
     return __fadd_rn(s, err);
 }
 
+// One-dimensional bulk copies (TMA) of the block's SH coefficient slices into shared memory,
+// completed on an mbarrier. The planar layout makes the unit's slice of each coefficient
+// plane one contiguous run of floats; a bulk copy needs both addresses 16-byte aligned and a
+// size that is a multiple of 16 bytes, which holds when the scene size is a multiple of 4 and
+// the array is 16-byte aligned (bulk_sh_ok).
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Waits for phase 0 of the mbarrier, at most kSpinLimit polls; false if it gave up.
+__device__ __forceinline__ bool mbar_wait0(uint64_t *bar)
+{
+    for (int spin = 0; spin < kSpinLimit; ++spin) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(bar))
+            : "memory");
+        if (done) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool bulk_sh_ok(const float *sh, int n)
+{
+    return (n & 3) == 0 && ((uintptr_t)sh & 15u) == 0;
+}
+
 // Colour along the unit direction (x, y, z): sum_k sh_k Y_k + 0.5, clamped at 0. The
 // thread's coefficients are staged in shared memory, s_sh[(k * 3 + c) * kBlock + thread].
 __device__ __forceinline__ void sh_colour(const float *s_sh, int degree, float x, float y, float z, float rgb[3])
@@ -82,7 +132,8 @@ constexpr int kViewChunk = 16;  // views staged in shared memory at a time
 template <int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
 {
-    extern __shared__ float s_sh[];  // [3 (degree+1)^2][kBlock]
+    extern __shared__ __align__(16) float s_sh[];  // [3 (degree+1)^2][kBlock]
+    __shared__ __align__(8) uint64_t s_bar;
     __shared__ ViewDev s_views[kViewChunk];
     __shared__ unsigned long long s_cnt[3][kViewChunk];
     const int lane = threadIdx.x & 31;
@@ -112,9 +163,28 @@ __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
         Rg[6] = 2.f * (qx * qz - qw * qy); Rg[7] = 2.f * (qy * qz + qw * qx); Rg[8] = 1.f - 2.f * (qx * qx + qy * qy);
     }
     {
+        // the unit's SH coefficients: bulk copies of its slice of each plane when aligned
         const int q3 = 3 * sh_count(sc.sh_degree);
-        for (int q = 0; q < q3; ++q)
-            s_sh[q * kBlock + threadIdx.x] = valid ? __ldg(&sc.sh[(size_t)q * n + i]) : 0.0f;
+        const int first = (unit - (int)sc.unit_begin) * kBlock;
+        const uint32_t bytes = (uint32_t)(min(kBlock, n - first) * (int)sizeof(float));
+        bool staged = false;
+        if (bulk_sh_ok(sc.sh, n)) {
+            if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                mbar_expect_tx(&s_bar, bytes * (uint32_t)q3);
+                for (int q = 0; q < q3; ++q)
+                    bulk_copy_g2s(&s_sh[q * kBlock], sc.sh + (size_t)q * n + first, bytes, &s_bar);
+            }
+            staged = mbar_wait0(&s_bar);
+            if (!staged) {  // report, let the copies land (bounded), then load directly
+                atomicOr(&a.counters->status, kStatusLookbackTimeout);
+                mbar_wait0(&s_bar);
+            }
+        }
+        if (!staged)
+            for (int q = 0; q < q3; ++q)
+                s_sh[q * kBlock + threadIdx.x] = valid ? __ldg(&sc.sh[(size_t)q * n + i]) : 0.0f;
     }
     const float sg[3] = {s0, s1, s2};
     const float r = 3.0f * fmaxf(s0, fmaxf(s1, s2));

@@ -43,7 +43,7 @@ constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
 // Device status word bits.
-constexpr uint32_t kStatusLookbackTimeout = 1u;  // a bounded chained-scan wait gave up
+constexpr uint32_t kStatusLookbackTimeout = 1u;  // a bounded wait (chained scan, bulk copy) gave up
 constexpr uint32_t kStatusOverflow = 2u;         // a count exceeded its buffer's capacity
 
 // Per-slot splat record, written by preprocess for rendered slots and gathered by the
