@@ -266,6 +266,43 @@ def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
+def stage_hbm(kms, vinfo, scene, W, H, hbm_gbs):
+    """Algorithmic bytes of each preprocess and binning stage of an exact batched render, their
+    GB/s over the stage's GPU time (rara_ctx_kernel_ms) and the fraction of the measured HBM
+    copy bandwidth. Bytes per unit (the design notes list them):
+      preprocess   the scene once (44 B of geometry + 12 (L+1)^2 B of SH per Gaussian), 5 B per
+                   (view, Gaussian) slot (label, tiles), 60 B per rendered slot (rectangle,
+                   splat record, depth), 64 B per cutoff slot (ray-tracing record)
+      compaction   8 B per slot read (tiles, depth), 8 B per rendered slot written
+      depth sort   16 B per rendered slot per digit pass launched (4 depth + 1 view pass)
+      emission     44 B per rendered slot read (slot, rectangle, centre and conic), 8 B per pair
+      tile sort    16 B per pair per digit pass
+      ranges       4 B per pair read, 8 B per tile written"""
+    views = len(vinfo)
+    n = scene.n
+    slots = views * n
+    rendered = sum(v["n_rendered"] for v in vinfo)
+    cutoff = sum(v["n_cutoff"] for v in vinfo)
+    pairs = sum(v["n_pairs"] for v in vinfo)
+    tiles = sum(v["tiles_x"] * v["tiles_y"] for v in vinfo)
+    tile_bits = max(1, (max(v["tiles_x"] * v["tiles_y"] for v in vinfo) - 1).bit_length())
+    tile_passes = (tile_bits + 7) // 8
+    view_passes = 0 if views == 1 else (1 if views <= 256 else 2)
+    bytes_ = {
+        "preprocess": n * (44 + 4 * scene.sh.shape[0]) + 5 * slots + 60 * rendered + 64 * cutoff,
+        "compaction": 8 * slots + 8 * rendered,
+        "depth_sort": 16 * rendered * (4 + view_passes),
+        "emission": 44 * rendered + 8 * pairs,
+        "tile_sort": 16 * pairs * tile_passes,
+        "ranges": 4 * pairs + 8 * tiles,
+    }
+    out = {}
+    for (name, b), ms in zip(bytes_.items(), kms):
+        gbs = b / (ms * 1e-3) / 1e9 if ms > 0 else None
+        out[name] = {"ms": ms, "bytes": int(b), "GBps": gbs, "hbm_frac": gbs / hbm_gbs if gbs else None}
+    return out
+
+
 def percentile(xs, p):
     xs = sorted(xs)
     if not xs:
@@ -365,7 +402,9 @@ def run_ours(args):
     # stage times and work counts of one exact batched render (for the roofline)
     rara.rara_render_batch(bctx, [gs], views, stream)
     stage = rara.rara_ctx_stage_ms(bctx)
+    kms = rara.rara_ctx_kernel_ms(bctx)
     binfo = rara.rara_frame_info_get(bctx, 0)
+    vinfo = [rara.rara_frame_info_get(bctx, v) for v in range(nplanes)]
     if counts is None:
         counts = [rara.rara_frame_info_get(bctx, v) for v in range(nplanes)]
     for _ in range(args.warmup):
@@ -404,9 +443,10 @@ def run_ours(args):
                "note": "the 16 sweep frames as one batch (one launch per stage), replayed as a CUDA graph; "
                        "a request's latency is its batch's"}
     clocks = sampler.summary()
+    peaks, peak_kind = measured_peaks()
+    batched["stage_hbm"] = stage_hbm(kms, vinfo, scene, W, H, peaks["hbm_gbs"])
 
     # roofline of the dominant kernel: the render launch of the batch
-    peaks, peak_kind = measured_peaks()
     flop = (FLOP_TEST * binfo["n_tested"] + FLOP_WALKED * binfo["n_walked"] + FLOP_EVAL * binfo["n_evaluated"]
             + FLOP_CUT * binfo["n_cut_evaluated"])
     achieved = flop / (stage[2] * 1e-3) / 1e12

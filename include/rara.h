@@ -144,6 +144,12 @@ int rara_ctx_set_tuning(rara_ctx *ctx, int32_t split2_bits, int32_t split4_bits)
  * render. Waits for that render to finish. */
 int rara_ctx_stage_ms(rara_ctx *ctx, float out[3]);
 
+/* The same, finer: out[0] k_preprocess (with the counter memsets before it), out[1] the
+ * compaction, out[2] the depth sort, out[3] the pair emission, out[4] the tile sort,
+ * out[5] the ranges and the render work order. Measurement only (the paper times whole
+ * frames). Waits for the last render to finish. */
+int rara_ctx_kernel_ms(rara_ctx *ctx, float out[6]);
+
 /* Number of kernel launches this context has queued since creation (all entry points). */
 int64_t rara_ctx_launches(const rara_ctx *ctx);
 

@@ -89,8 +89,9 @@ struct rara_ctx {
     int bpsm_render_bwd = 0;
 
     // stage timing of the last batch rendered outside a graph: preprocess start, bin start,
-    // render start, render end
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // render start, render end, then inside the stages: after the depth sort, after the
+    // emission, after the tile sort, after k_preprocess (before the compaction)
+    cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool capturing = false;
 };
 
@@ -383,6 +384,7 @@ int batch_preprocess(rara_ctx *c, cudaStream_t s)
     }
     launch_preprocess(a, (int)c->num_units, max_degree, max_views, s);
     if ((rc = launched(c, "preprocess launch", c->num_units > 0))) return rc;
+    mark(c, 7, s);
 
     CompactArgs ca;
     ca.tiles = (const uint32_t *)c->tiles.p;
@@ -448,6 +450,7 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
                          &dc->depth_in_b, sgrid, s, (const uint32_t *)c->seg_base.p,
                          c->view_passes ? c->num_views : 0, 4);
     if ((rc = launched(c, "depth sort", nl))) return rc;
+    mark(c, 4, s);
 
     if ((rc = check_cuda(c, cudaMemsetAsync(c->lookback_e.p, 0, (nn / kBlock + 2) * 8, s), "memset emit")))
         return rc;
@@ -471,12 +474,14 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
     e.counters = dc;
     launch_emit(e, c->sm_count * c->bpsm_emit, s);
     if ((rc = launched(c, "emit"))) return rc;
+    mark(c, 5, s);
 
     nl = sort_launch((uint32_t *)c->pkeys.p, (uint32_t *)c->pvals.p, (uint32_t *)c->pkeys_b.p,
                      (uint32_t *)c->pvals_b.p, &dc->n_pairs, cap, c->tile_passes, hist + kHistTile * 256, c->sort_scratch.p,
                      &dc->ticket[kTicketSortTile], &dc->status, &dc->tile_in_b, sgrid, s, nullptr, 0, 0,
                      c->tile_digit_bits);
     if ((rc = launched(c, "tile sort", nl))) return rc;
+    mark(c, 6, s);
 
     const size_t nt = c->num_tiles > 0 ? (size_t)c->num_tiles : 1;
     if ((rc = check_cuda(c, cudaMemsetAsync(c->ranges.p, 0, nt * sizeof(int2), s), "memset ranges"))) return rc;
@@ -974,6 +979,20 @@ int rara_ctx_backward_ms(rara_ctx *c, float out[2])
     if (rc) return rc;
     for (int k = 0; k < 2; ++k)
         if ((rc = check_cuda(c, cudaEventElapsedTime(&out[k], c->bev[k], c->bev[k + 1]), "event elapsed time")))
+            return rc;
+    return RARA_OK;
+}
+
+int rara_ctx_kernel_ms(rara_ctx *c, float out[6])
+{
+    if (!c || !out) return RARA_ERR_INVALID_ARG;
+    if (!c->ev[0]) return fail(c, RARA_ERR_INVALID_ARG, "no stage timing on this context");
+    int rc = check_cuda(c, cudaEventSynchronize(c->ev[3]), "event wait");
+    if (rc) return rc;
+    // preprocess, compaction, depth sort, emission, tile sort, ranges and render order
+    const int from[6] = {0, 7, 1, 4, 5, 6}, to[6] = {7, 1, 4, 5, 6, 2};
+    for (int k = 0; k < 6; ++k)
+        if ((rc = check_cuda(c, cudaEventElapsedTime(&out[k], c->ev[from[k]], c->ev[to[k]]), "event elapsed time")))
             return rc;
     return RARA_OK;
 }

@@ -70,6 +70,7 @@ SIGNATURES = {
     "rara_ctx_launches": (C.c_int64, [_P]),
     "rara_ctx_set_tuning": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "rara_ctx_stage_ms": (C.c_int, [_P, C.POINTER(C.c_float)]),
+    "rara_ctx_kernel_ms": (C.c_int, [_P, C.POINTER(C.c_float)]),
     "rara_preprocess": (C.c_int, [_P, C.POINTER(rara_gaussians), C.POINTER(rara_camera),
                                   C.POINTER(rara_plane), _P]),
     "rara_bin": (C.c_int, [_P, _P]),
@@ -226,6 +227,14 @@ def rara_ctx_stage_ms(ctx):
     out = (C.c_float * 3)()
     _check(ctx, load().rara_ctx_stage_ms(ctx, out))
     return tuple(float(x) for x in out)
+
+
+def rara_ctx_kernel_ms(ctx):
+    """[preprocess, compaction, depth sort, emission, tile sort, ranges + order] GPU ms of the
+    last render launched outside a graph."""
+    out = (C.c_float * 6)()
+    _check(ctx, load().rara_ctx_kernel_ms(ctx, out))
+    return [float(v) for v in out]
 
 
 def rara_ctx_sync(ctx, stream=None):
