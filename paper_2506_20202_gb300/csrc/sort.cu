@@ -19,8 +19,8 @@ namespace {
 constexpr int kRadix = 256;
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kItems = 12;                       // keys per thread per partition
-constexpr int kPart = kSortThreads * kItems;     // keys per partition (3072)
+constexpr int kItems = 16;                       // keys per thread per partition
+constexpr int kPart = kSortThreads * kItems;     // keys per partition (4096)
 constexpr uint32_t kLbAgg = 1u << 30, kLbIncl = 2u << 30, kLbMask = (1u << 30) - 1u;
 constexpr int kLbWidth = 8;                      // predecessors read per look-back step
 
@@ -41,7 +41,7 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *s_
     return wbase + incl - v;
 }
 
-__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b,
+__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b,
                                                            uint32_t *vals_b, const unsigned long long *n_ptr,
                                                            uint32_t cap, int pass, int passes,
                                                            const uint32_t *__restrict__ hist, uint32_t *lookback,
