@@ -61,13 +61,14 @@ __device__ __forceinline__ bool rara_weight_grad(const float4 c0, const float4 c
     const float half = __fmul_rn(__fmul_rn(__fmul_rn(h2, rsqrtf(h2)), mV), rsqrtf(t.VV));
     const float s1 = smid - half, s2 = smid + half;
     if ((s1 >= 0.0f) == (s2 >= 0.0f)) return false;
+    // H > 0 and mV != 0 here (s1, s2 of opposite signs), h2 > 0 (cc < 1)
     const float H = fabsf(half);
-    const float g_smid = gw / (2.0f * H);
-    const float g_H = -gw * smid / (2.0f * H * H);
-    const float iVV = 1.0f / t.VV;
-    float g_VV = -g_H * H * 0.5f * iVV;
-    const float g_h2 = g_H * H * 0.5f / h2;
-    float g_mV = g_H * H / mV - g_smid * f;
+    const float g_smid = __fdividef(0.5f * gw, H);
+    const float gHH = -g_smid * smid;   // dL/dH * H
+    const float iVV = t.rVV;
+    float g_VV = -0.5f * gHH * iVV;
+    const float g_h2 = __fdividef(0.5f * gHH, h2);
+    float g_mV = __fdividef(gHH, mV) - g_smid * f;
     const float g_f = -g_smid * mV;
     float g_mp = g_smid + g_mV;
     const float g_pV = g_f * iVV;
@@ -214,21 +215,22 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
                             const float alpha = fminf(kAlphaMax, au);
                             if (alpha >= kAlphaMin) {
                                 contrib = true;
-                                const float oma = 1.0f - alpha;
-                                const float Tj = T / oma;
+                                const float oma = 1.0f - alpha;   // in [0.01, 1)
+                                const float roma = __fdividef(1.0f, oma);
+                                const float Tj = T * roma;
                                 const float wgt = alpha * Tj;
                                 gr = dC0 * wgt;
                                 gg = dC1 * wgt;
                                 gb = dC2 * wgt;
                                 float ga = Tj * (dC0 * (s2.x - B0) + dC1 * (s2.y - B1) + dC2 * (s2.z - B2)) -
-                                           Tfin * bgdot / oma;
+                                           Tfin * bgdot * roma;
                                 B0 = fmaf(alpha, s2.x, oma * B0);
                                 B1 = fmaf(alpha, s2.y, oma * B1);
                                 B2 = fmaf(alpha, s2.z, oma * B2);
                                 T = Tj;
                                 if (au > kAlphaMax) ga = 0.0f;  // clamped at 0.99
                                 const float ga0 = ga * w;
-                                gop = ga0 * (a0 / s2.w);        // d alpha0 / d opacity = exp(-q/2)
+                                gop = ga0 * __fdividef(a0, s2.w);        // d alpha0 / d opacity = exp(-q/2)
                                 const float gq = -0.5f * ga0 * a0;
                                 gCa = gq * dx * dx;
                                 gCb = 2.0f * gq * dx * dy;
