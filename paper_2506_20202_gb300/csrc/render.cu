@@ -27,7 +27,8 @@
 //   plane       s(u) = d_ep + m . u with m = M^T n, linear along the ray:
 //               s1,2 = d_ep + m.c -/+ sqrt(1 - cc) (m.V) / |V|
 //   weight      both >= 0: 1; both < 0: 0; otherwise the visible share of the chord,
-//               max(s1, s2) / |s2 - s1|  (= (t2 - t_p)/(t2 - t1) or (t_p - t1)/(t2 - t1)).
+//               max(s1, s2) / |s2 - s1|  (= (t2 - t_p)/(t2 - t1) or (t_p - t1)/(t2 - t1));
+//               all three cases are clamp(1/2 + (d_ep + m.c) / (2 |h|), 0, 1), h = s2 - s_mid.
 // Everything is a polynomial in (dx, dy) with coefficients the products of G, P and m that
 // the preprocess stores, so a pixel needs about 50 instructions for the full weight.
 // Because w <= 1, an entry whose unweighted alpha is already below 1/255 is skipped before

@@ -61,7 +61,8 @@ __device__ __forceinline__ RayTerms ray_terms(const float4 c0, const float4 c1, 
 // plane s(u) = d_ep + m.u is linear along the chord, with values at its ends
 //   s1,2 = s_mid -/+ h,  s_mid = d_ep + m.c,  h = sqrt(1 - cc) (m.V) / |V|,
 // where c is the chord's midpoint, m.c = m.p - (p.V / V.V)(m.V). w = 1 if both ends are on
-// the visible side, 0 if both are not, else the visible share max(s1, s2) / |s2 - s1|.
+// the visible side, 0 if both are not, else the visible share max(s1, s2) / |s2 - s1|
+// (together: clamp(1/2 + s_mid / (2 |h|), 0, 1)).
 // Products that feed a sum are written with __fmul_rn so the forward and the backward,
 // which re-evaluates this function, round identically.
 __device__ __forceinline__ float rara_weight(const float4 c0, const float4 c1, const float4 c2, const float4 c3,
@@ -77,11 +78,11 @@ __device__ __forceinline__ float rara_weight(const float4 c0, const float4 c1, c
     const float mV = c1.w + mp;
     const float f = __fmul_rn(t.Gp + t.pp, t.rVV);
     const float smid = c0.w + fmaf(-f, mV, mp);
-    const float half = __fmul_rn(__fmul_rn(__fmul_rn(h2, rsqrtf(h2)), mV), rsqrtf(t.VV));
-    const float s1 = smid - half, s2 = smid + half;
-    const bool v1 = s1 >= 0.0f, v2 = s2 >= 0.0f;
-    const float part = fminf(1.0f, __fdividef(fmaxf(s1, s2), fabsf(s2 - s1)));
-    const float w = v1 == v2 ? (v1 ? 1.0f : 0.0f) : part;
+    // With H = |h| the chord's ends are s_mid -/+ H and the visible share is
+    // (s_mid + H) / (2 H) = 1/2 + s_mid / (2 H), which reaches 1 (or 0) exactly when both ends
+    // are on the visible (or the invisible) side: clamped to [0, 1] it is w in every case.
+    const float iH = rsqrtf(__fmul_rn(__fmul_rn(h2, __fmul_rn(mV, mV)), t.rVV));  // 1 / H
+    const float w = __saturatef(fmaf(__fmul_rn(smid, iH), 0.5f, 0.5f));
     return hit ? w : 1.0f;  // a ray that misses, grazes or starts inside keeps rasterization
 }
 
