@@ -127,20 +127,22 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
                     const float q = splat_q(s0.z, s0.w, s1.x, dx, dy);
                     ty.add(ty.walked, !done);
                     const float a0 = splat_alpha0(q, s1.y);
-                    const bool live = !done && q <= s1.z && a0 >= kAlphaMin;
-                    ty.add(ty.evaluated, live);
+                    // alpha <= alpha0, so alpha >= 1/255 below also stands for alpha0 >= 1/255
+                    const bool inq = !done && q <= s1.z;
+                    ty.add(ty.evaluated, inq && a0 >= kAlphaMin);
                     float alpha = a0;
                     if ((mw >> bit) & 1u) {
                         const float mode = s1.w;
-                        ty.add(ty.cut, live && mode == kWeightSplit);
+                        ty.add(ty.cut, inq && a0 >= kAlphaMin && mode == kWeightSplit);
                         alpha = __fmul_rn(a0, decay_weight(mode, st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy));
                     }
                     alpha = fminf(kAlphaMax, alpha);
-                    const bool valid = live && alpha >= kAlphaMin;
-                    const float Tn = T * (1.0f - alpha);
+                    const bool valid = inq && alpha >= kAlphaMin;
+                    const float aT = alpha * T;
+                    const float Tn = T - aT;  // T (1 - alpha)
                     const bool stop = valid && Tn < kTMin;
                     const bool blend = valid && !stop;
-                    const float wgt = blend ? alpha * T : 0.0f;
+                    const float wgt = blend ? aT : 0.0f;
                     const float4 s2 = st.s2[j];
                     C0 = fmaf(s2.x, wgt, C0);
                     C1 = fmaf(s2.y, wgt, C1);
