@@ -51,18 +51,20 @@ __device__ __forceinline__ bool rara_weight_grad(const float4 c0, const float4 c
                                                  float dx, float dy, float gw, float gc[16], float &gdx, float &gdy)
 {
     const RayTerms t = ray_terms(c0, c1, c2, c3, dx, dy);
-    if (t.cc >= 1.0f) return false;
-    const float h2 = 1.0f - t.cc;
-    if (!(t.GV > 0.0f && __fmul_rn(t.GV, t.GV) > __fmul_rn(h2, t.VV))) return false;
+    if (!ray_hits_front(t)) return false;
     const float mp = fmaf(c2.x, dx, c2.y * dy);
     const float mV = c1.w + mp;
+    {   // w is constant (0 or 1) unless rara_weight's unclamped share lies strictly inside (0, 1)
+        const float num = fmaf(c0.w + mp, t.VV, -__fmul_rn(t.Gp + t.pp, mV));
+        const float den2 = __fmul_rn(t.VV - t.uu, __fmul_rn(mV, mV));
+        const float v = fmaf(__fmul_rn(num, rsqrtf(den2)), 0.5f, 0.5f);
+        if (!(v > 0.0f && v < 1.0f)) return false;
+    }
+    const float h2 = 1.0f - t.cc;
     const float f = __fmul_rn(t.Gp + t.pp, t.rVV);
     const float smid = c0.w + fmaf(-f, mV, mp);
-    const float half = __fmul_rn(__fmul_rn(__fmul_rn(h2, rsqrtf(h2)), mV), rsqrtf(t.VV));
-    const float s1 = smid - half, s2 = smid + half;
-    if ((s1 >= 0.0f) == (s2 >= 0.0f)) return false;
-    // H > 0 and mV != 0 here (s1, s2 of opposite signs), h2 > 0 (cc < 1)
-    const float H = fabsf(half);
+    // H > 0 and mV != 0 here (the share is finite and strictly inside (0, 1)), h2 > 0 (cc < 1)
+    const float H = fabsf(__fmul_rn(__fmul_rn(__fmul_rn(h2, rsqrtf(h2)), mV), rsqrtf(t.VV)));
     const float g_smid = __fdividef(0.5f * gw, H);
     const float gHH = -g_smid * smid;   // dL/dH * H
     const float iVV = t.rVV;

@@ -36,7 +36,7 @@ __device__ __forceinline__ float splat_alpha0(float q, float lo)
 //   cc = |p x V|^2 / V.V = |dx A + dy B|^2 / V.V, the squared distance of the ray from the
 //        centre (a sum of squares: no cancellation between the large G and the small p)
 struct RayTerms {
-    float Gp, pp, VV, rVV, GV, cc, u0, u1, u2;
+    float Gp, pp, VV, rVV, GV, cc, uu, u0, u1, u2;
 };
 
 __device__ __forceinline__ RayTerms ray_terms(const float4 c0, const float4 c1, const float4 c2, const float4 c3,
@@ -48,12 +48,19 @@ __device__ __forceinline__ RayTerms ray_terms(const float4 c0, const float4 c1, 
     t.u0 = fmaf(c2.z, dx, c3.y * dy);
     t.u1 = fmaf(c2.w, dx, c3.z * dy);
     t.u2 = fmaf(c3.x, dx, c3.w * dy);
-    const float uu = fmaf(t.u0, t.u0, fmaf(t.u1, t.u1, t.u2 * t.u2));
+    t.uu = fmaf(t.u0, t.u0, fmaf(t.u1, t.u1, t.u2 * t.u2));
     t.VV = c0.x + fmaf(2.0f, t.Gp, t.pp);
     t.rVV = __fdividef(1.0f, t.VV);
-    t.cc = __fmul_rn(uu, t.rVV);
+    t.cc = __fmul_rn(t.uu, t.rVV);
     t.GV = c0.x + t.Gp;
     return t;
+}
+
+// The ray meets the unit sphere (cc < 1) with both roots in front of the camera (G.V > 0 and
+// (G.V)^2 > (1 - cc) V.V), written with cc V.V = |u|^2 so that no reciprocal is needed.
+__device__ __forceinline__ bool ray_hits_front(const RayTerms &t)
+{
+    return t.uu < t.VV && t.GV > 0.0f && __fmul_rn(t.GV, t.GV) > t.VV - t.uu;
 }
 
 // Decay weight (Eq. 4-8, Eq. 11) of a Gaussian that the plane splits (kWeightSplit): the ray
@@ -72,17 +79,17 @@ __device__ __forceinline__ float rara_weight(const float4 c0, const float4 c1, c
     // warp whose pixels fall into different cases does not diverge; the values are the ones
     // the case-by-case form gives (the unselected ones may be NaN and are never used).
     const RayTerms t = ray_terms(c0, c1, c2, c3, dx, dy);
-    const float h2 = 1.0f - t.cc;
-    const bool hit = t.cc < 1.0f && t.GV > 0.0f && __fmul_rn(t.GV, t.GV) > __fmul_rn(h2, t.VV);  // roots in front
+    const bool hit = ray_hits_front(t);
     const float mp = fmaf(c2.x, dx, c2.y * dy);
     const float mV = c1.w + mp;
-    const float f = __fmul_rn(t.Gp + t.pp, t.rVV);
-    const float smid = c0.w + fmaf(-f, mV, mp);
     // With H = |h| the chord's ends are s_mid -/+ H and the visible share is
     // (s_mid + H) / (2 H) = 1/2 + s_mid / (2 H), which reaches 1 (or 0) exactly when both ends
     // are on the visible (or the invisible) side: clamped to [0, 1] it is w in every case.
-    const float iH = rsqrtf(__fmul_rn(__fmul_rn(h2, __fmul_rn(mV, mV)), t.rVV));  // 1 / H
-    const float w = __saturatef(fmaf(__fmul_rn(smid, iH), 0.5f, 0.5f));
+    // Multiplied through by V.V: s_mid / H = num / sqrt(den2) with
+    //   num = (d_ep + m.p) V.V - (G.p + p.p) m.V,  den2 = (V.V - |u|^2) (m.V)^2.
+    const float num = fmaf(c0.w + mp, t.VV, -__fmul_rn(t.Gp + t.pp, mV));
+    const float den2 = __fmul_rn(t.VV - t.uu, __fmul_rn(mV, mV));
+    const float w = __saturatef(fmaf(__fmul_rn(num, rsqrtf(den2)), 0.5f, 0.5f));
     return hit ? w : 1.0f;  // a ray that misses, grazes or starts inside keeps rasterization
 }
 
@@ -91,9 +98,7 @@ __device__ __forceinline__ float rara_weight(const float4 c0, const float4 c1, c
 __device__ __forceinline__ float rara_weight_hidden(const float4 c0, const float4 c1, const float4 c2,
                                                     const float4 c3, float dx, float dy)
 {
-    const RayTerms t = ray_terms(c0, c1, c2, c3, dx, dy);
-    const float h2 = 1.0f - t.cc;
-    return (t.cc < 1.0f && t.GV > 0.0f && __fmul_rn(t.GV, t.GV) > __fmul_rn(h2, t.VV)) ? 0.0f : 1.0f;
+    return ray_hits_front(ray_terms(c0, c1, c2, c3, dx, dy)) ? 0.0f : 1.0f;
 }
 
 // Decay weight of a slot with weight mode `mode` (kWeightSplit or kWeightHidden).
@@ -182,7 +187,8 @@ __device__ __forceinline__ void stage_splat(Stage &st, int i, const SplatRec &re
 // corners of a box of pixel centres (offsets [ax, bx] x [ay, by] from the projected centre)
 // lie in that smaller region, every pixel of the box does, and its float32 hit test (cc < 1,
 // G.V > 0, (G.V)^2 > (1 - cc) V.V, whose margin is (G.G - 1) V.V) cannot fail: the entry is
-// nothing to the box.
+// nothing to the box. (The test is evaluated as |u|^2 < V.V, G.V > 0, (G.V)^2 > V.V - |u|^2,
+// the same inequalities times V.V, with the same margin.)
 __device__ __forceinline__ bool hidden_covers_box(const Stage &st, int j, float ax, float bx, float ay, float by)
 {
     const float4 c0 = st.c0[j], c1 = st.c1[j], c2 = st.c2[j], c3 = st.c3[j];
