@@ -45,10 +45,12 @@ constexpr unsigned kFull = 0xffffffffu;
 // w = 1/2 + s_mid / (2 H), H = sqrt(h2) |m.V| / |V|, it goes back through
 // s_mid = d_ep + m.p - f (m.V), f = (G.p + p.p) / V.V, h2 = 1 - |u|^2 / V.V,
 // V.V = G.G + 2 G.p + p.p, m.V = m.G + m.p and the per-pixel polynomials G.p, p.p, m.p,
-// u = dx A + dy B. Outputs: dL/d(record products) in CutRec order (c0.x .. c3.w) in gc[16],
-// and dL/d(dx, dy) added to gdx, gdy.
+// u = dx A + dy B. c0..c3 is the record's staged form (stage_cut), r2, r3 its own c2, c3
+// (which hold A and B). Outputs: dL/d(record products) in CutRec order (c0.x .. c3.w) in
+// gc[16], and dL/d(dx, dy) added to gdx, gdy.
 __device__ __forceinline__ bool rara_weight_grad(const float4 c0, const float4 c1, const float4 c2, const float4 c3,
-                                                 float dx, float dy, float gw, float gc[16], float &gdx, float &gdy)
+                                                 const float4 r2, const float4 r3, float dx, float dy, float gw,
+                                                 float gc[16], float &gdx, float &gdy)
 {
     const RayTerms t = ray_terms(c0, c1, c2, c3, dx, dy);
     if (!ray_hits_front(t)) return false;
@@ -90,13 +92,15 @@ __device__ __forceinline__ bool rara_weight_grad(const float4 c0, const float4 c
     gc[7] = g_mV;                       // m.G
     gc[8] = g_mp * dx;                  // m.Px
     gc[9] = g_mp * dy;                  // m.Py
-    const float gu0 = 2.0f * g_uu * t.u0, gu1 = 2.0f * g_uu * t.u1, gu2 = 2.0f * g_uu * t.u2;
+    // u = dx A + dy B from the stored A = (r2.z, r2.w, r3.x), B = (r3.y, r3.z, r3.w)
+    const float u0 = fmaf(r2.z, dx, r3.y * dy), u1 = fmaf(r2.w, dx, r3.z * dy), u2 = fmaf(r3.x, dx, r3.w * dy);
+    const float gu0 = 2.0f * g_uu * u0, gu1 = 2.0f * g_uu * u1, gu2 = 2.0f * g_uu * u2;
     gc[10] = gu0 * dx; gc[11] = gu1 * dx; gc[12] = gu2 * dx;   // A
     gc[13] = gu0 * dy; gc[14] = gu1 * dy; gc[15] = gu2 * dy;   // B
-    gdx += g_Gp * c0.y + 2.0f * g_pp * fmaf(dx, c1.x, dy * c1.y) + g_mp * c2.x +
-           (gu0 * c2.z + gu1 * c2.w + gu2 * c3.x);
-    gdy += g_Gp * c0.z + 2.0f * g_pp * fmaf(dx, c1.y, dy * c1.z) + g_mp * c2.y +
-           (gu0 * c3.y + gu1 * c3.z + gu2 * c3.w);
+    gdx += g_Gp * c0.y + g_pp * fmaf(2.0f * dx, c1.x, dy * c1.y) + g_mp * c2.x +
+           (gu0 * r2.z + gu1 * r2.w + gu2 * r3.x);
+    gdy += g_Gp * c0.z + g_pp * fmaf(dx, c1.y, 2.0f * dy * c1.z) + g_mp * c2.y +
+           (gu0 * r3.y + gu1 * r3.z + gu2 * r3.w);
     return true;
 }
 
@@ -131,7 +135,8 @@ __device__ __forceinline__ void warp_reduce_scatter(float (&v)[N])
 
 // One 16x16 tile, one thread per pixel (warp rectangles of 8x4 pixels).
 __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &vw, const BwdView &bv,
-                                         const uint32_t *pair_vals, Stage &st, uint32_t *s_slot, int *s_max,
+                                         const uint32_t *pair_vals, Stage &st, float4 (*s_ab)[kBlock],
+                                         uint32_t *s_slot, int *s_max,
                                          int gtile, int tile)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -175,10 +180,9 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
             stage_splat(st, threadIdx.x, rec);
             if (rec.r2.y != kWeightNone) {
                 const CutRec c = a.cut[g];
-                st.c0[threadIdx.x] = c.c0;
-                st.c1[threadIdx.x] = c.c1;
-                st.c2[threadIdx.x] = c.c2;
-                st.c3[threadIdx.x] = c.c3;
+                stage_cut(st, threadIdx.x, c);
+                s_ab[0][threadIdx.x] = c.c2;  // A, B as stored, for the gradient
+                s_ab[1][threadIdx.x] = c.c3;
             }
             s_slot[threadIdx.x] = g;
         }
@@ -240,7 +244,7 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
                                 float gdx = 2.0f * gq * fmaf(ca, dx, cb * dy);
                                 float gdy = 2.0f * gq * fmaf(cb, dx, cc * dy);
                                 if (cut)
-                                    rara_weight_grad(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy, ga * a0, gc, gdx,
+                                    rara_weight_grad(st.c0[j], st.c1[j], st.c2[j], st.c3[j], s_ab[0][j], s_ab[1][j], dx, dy, ga * a0, gc, gdx,
                                                      gdy);
                                 gmx = -gdx;
                                 gmy = -gdy;
@@ -286,6 +290,7 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
 __global__ void __launch_bounds__(kBlock, 4) k_render_bwd(RenderBwdArgs a)
 {
     __shared__ Stage st;
+    __shared__ float4 s_ab[2][kBlock];  // stored c2, c3 (A, B) of the staged cutoff entries
     __shared__ uint32_t s_slot[kBlock];
     __shared__ unsigned s_item;
     __shared__ int s_max;
@@ -308,7 +313,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_render_bwd(RenderBwdArgs a)
                 else hi = mid - 1;
             }
             const ViewDev &vw = a.views[lo];
-            tile_bwd(a, vw, a.bviews[lo], pair_vals, st, s_slot, &s_max, gtile, gtile - (int)vw.tile_base);
+            tile_bwd(a, vw, a.bviews[lo], pair_vals, st, s_ab, s_slot, &s_max, gtile, gtile - (int)vw.tile_base);
         }
         __syncthreads();  // everyone has read s_item and the staged batch
     }

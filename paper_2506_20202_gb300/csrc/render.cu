@@ -92,11 +92,7 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
             const SplatRec rec = a.rec[g];
             stage_splat(st, threadIdx.x, rec);
             if (rec.r2.y != kWeightNone) {
-                const CutRec c = a.cut[g];
-                st.c0[threadIdx.x] = c.c0;
-                st.c1[threadIdx.x] = c.c1;
-                st.c2[threadIdx.x] = c.c2;
-                st.c3[threadIdx.x] = c.c3;
+                stage_cut(st, threadIdx.x, a.cut[g]);
             }
         }
         __syncthreads();

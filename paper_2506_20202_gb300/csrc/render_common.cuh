@@ -31,12 +31,13 @@ __device__ __forceinline__ float splat_alpha0(float q, float lo)
 
 // Per-pixel quantities of the ray through pixel offset (dx, dy) in the unit-sphere frame
 // of a cutoff Gaussian (the local ray is -G + tau V, V = G + p, p = P (dx, dy)), from the
-// products stored in its CutRec:
+// staged form of its CutRec (stage_cut):
 //   Gp = G.p, pp = p.p, VV = V.V = G.G + 2 Gp + pp, GV = G.V = G.G + Gp,
-//   cc = |p x V|^2 / V.V = |dx A + dy B|^2 / V.V, the squared distance of the ray from the
-//        centre (a sum of squares: no cancellation between the large G and the small p)
+//   uu = |p x V|^2 = |dx A + dy B|^2 = A.A dx^2 + 2 A.B dx dy + B.B dy^2 (p x V = p x G, so
+//        no difference of the large G and the small p enters), cc = uu / V.V, the squared
+//        distance of the ray from the centre
 struct RayTerms {
-    float Gp, pp, VV, rVV, GV, cc, uu, u0, u1, u2;
+    float Gp, pp, VV, rVV, GV, cc, uu;
 };
 
 __device__ __forceinline__ RayTerms ray_terms(const float4 c0, const float4 c1, const float4 c2, const float4 c3,
@@ -44,11 +45,9 @@ __device__ __forceinline__ RayTerms ray_terms(const float4 c0, const float4 c1, 
 {
     RayTerms t;
     t.Gp = fmaf(c0.y, dx, c0.z * dy);
-    t.pp = fmaf(dx, fmaf(c1.x, dx, 2.0f * c1.y * dy), c1.z * dy * dy);
-    t.u0 = fmaf(c2.z, dx, c3.y * dy);
-    t.u1 = fmaf(c2.w, dx, c3.z * dy);
-    t.u2 = fmaf(c3.x, dx, c3.w * dy);
-    t.uu = fmaf(t.u0, t.u0, fmaf(t.u1, t.u1, t.u2 * t.u2));
+    const float yy = dy * dy;
+    t.pp = fmaf(dx, fmaf(c1.x, dx, c1.y * dy), c1.z * yy);
+    t.uu = fmaf(dx, fmaf(c2.z, dx, c2.w * dy), c3.x * yy);
     t.VV = c0.x + fmaf(2.0f, t.Gp, t.pp);
     t.rVV = __fdividef(1.0f, t.VV);
     t.cc = __fmul_rn(t.uu, t.rVV);
@@ -154,6 +153,7 @@ constexpr float kCullMargin = 1.0001f;
 //   s1 = (conic.c, log2(opacity), q_cut, decay-weight mode)
 //   s2 = (rgb.r, rgb.g, rgb.b, opacity)
 //   nb = (-b/a, -b/c), the rectangle test's line minimisers
+//   c0..c3 = a cutoff entry's CutRec in the staged form of stage_cut
 // q_cut = min(9, the q at which alpha0 = opacity exp(-q/2) falls to 1/255, plus a margin
 // over its float32 rounding): a pixel with q > q_cut is outside the 3-sigma support or has
 // alpha0 < 1/255, so it is skipped before the exponential; alpha0 itself is still compared
@@ -163,6 +163,20 @@ struct Stage {
     float2 nb[kBlock];
     float4 c0[kBlock], c1[kBlock], c2[kBlock], c3[kBlock];
 };
+
+// Staged form of a CutRec: the quadratic forms p.p and |dx A + dy B|^2 in (dx, dy) take
+// their coefficients directly,
+//   c0 = (G.G, G.Px, G.Py, d_ep), c1 = (Px.Px, 2 Px.Py, Py.Py, m.G),
+//   c2 = (m.Px, m.Py, A.A, 2 A.B), c3 = (B.B, 0, 0, 0).
+__device__ __forceinline__ void stage_cut(Stage &st, int i, const CutRec &c)
+{
+    const float ax = c.c2.z, ay = c.c2.w, az = c.c3.x, bx = c.c3.y, by = c.c3.z, bz = c.c3.w;
+    st.c0[i] = c.c0;
+    st.c1[i] = make_float4(c.c1.x, 2.0f * c.c1.y, c.c1.z, c.c1.w);
+    st.c2[i] = make_float4(c.c2.x, c.c2.y, fmaf(ax, ax, fmaf(ay, ay, az * az)),
+                           2.0f * fmaf(ax, bx, fmaf(ay, by, az * bz)));
+    st.c3[i] = make_float4(fmaf(bx, bx, fmaf(by, by, bz * bz)), 0.0f, 0.0f, 0.0f);
+}
 
 // q_cut of a splat from log2(opacity) (see Stage).
 __device__ __forceinline__ float splat_qcut(float lo)
