@@ -317,12 +317,17 @@ __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
                                 const float mlen = sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
                                 const float bound = mlen * (1.0f + 1e-4f);
                                 wmode = dep > bound ? kWeightNone : (dep < -bound ? kWeightHidden : kWeightSplit);
+                                // With the camera inside (or on) the ellipsoid, G.G <= 1, the
+                                // roots of every ray have product (G.G - 1) / V.V <= 0: no ray
+                                // meets it twice in front, so w = 1 for every ray.
+                                const float GG = dot3(G, G);
+                                if (!(GG > 1.0f)) wmode = kWeightNone;
                                 if (wmode != kWeightNone) {
                                     // The render needs, per pixel, p = P (dx, dy) only through the
                                     // dot products G.p, p.p, m.p and the cross product p x G: store
                                     // the pairwise products of G, Px, Py, m and A = Px x G, B = Py x G.
                                     CutRec c;
-                                    c.c0 = make_float4(dot3(G, G), dot3(G, Px), dot3(G, Py), dep);
+                                    c.c0 = make_float4(GG, dot3(G, Px), dot3(G, Py), dep);
                                     c.c1 = make_float4(dot3(Px, Px), dot3(Px, Py), dot3(Py, Py), dot3(m, G));
                                     float A[3], B[3];
                                     cross3(Px, G, A);

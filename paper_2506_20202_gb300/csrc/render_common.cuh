@@ -55,11 +55,15 @@ __device__ __forceinline__ RayTerms ray_terms(const float4 c0, const float4 c1, 
     return t;
 }
 
-// The ray meets the unit sphere (cc < 1) with both roots in front of the camera (G.V > 0 and
-// (G.V)^2 > (1 - cc) V.V), written with cc V.V = |u|^2 so that no reciprocal is needed.
+// The ray meets the unit sphere with both roots in front of the camera. The roots of
+// |-G + tau V|^2 = 1 are real iff cc < 1 (|u|^2 < V.V), their sum is 2 G.V / V.V and their
+// product (G.G - 1) / V.V, so both are positive iff G.V > 0 and G.G > 1. (Equivalently
+// (G.V)^2 > (1 - cc) V.V: by Lagrange's identity (G.V)^2 = G.G V.V - |u|^2.) G.G > 1 is a
+// property of the Gaussian, not of the ray: the preprocess gives the Gaussians with
+// G.G <= 1 no weight (kWeightNone), so only the two per-ray conditions remain here.
 __device__ __forceinline__ bool ray_hits_front(const RayTerms &t)
 {
-    return t.uu < t.VV && t.GV > 0.0f && __fmul_rn(t.GV, t.GV) > t.VV - t.uu;
+    return t.uu < t.VV && t.GV > 0.0f;
 }
 
 // Decay weight (Eq. 4-8, Eq. 11) of a Gaussian that the plane splits (kWeightSplit): the ray
@@ -199,10 +203,9 @@ __device__ __forceinline__ void stage_splat(Stage &st, int i, const SplatRec &re
 // ellipsoid's part in front of the camera), and so do the pixels whose rays pass within
 // sqrt(0.999) of its centre (in the unit-sphere frame) with G.V above a margin. If the four
 // corners of a box of pixel centres (offsets [ax, bx] x [ay, by] from the projected centre)
-// lie in that smaller region, every pixel of the box does, and its float32 hit test (cc < 1,
-// G.V > 0, (G.V)^2 > (1 - cc) V.V, whose margin is (G.G - 1) V.V) cannot fail: the entry is
-// nothing to the box. (The test is evaluated as |u|^2 < V.V, G.V > 0, (G.V)^2 > V.V - |u|^2,
-// the same inequalities times V.V, with the same margin.)
+// lie in that smaller region, every pixel of the box does, and its float32 hit test
+// (|u|^2 < V.V and G.V > 0, ray_hits_front; margins 1e-3 V.V and 1e-4 (G.G + |G.p|), far
+// above the rounding) cannot fail: the entry is nothing to the box.
 __device__ __forceinline__ bool hidden_covers_box(const Stage &st, int j, float ax, float bx, float ay, float by)
 {
     const float4 c0 = st.c0[j], c1 = st.c1[j], c2 = st.c2[j], c3 = st.c3[j];
