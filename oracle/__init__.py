@@ -46,7 +46,7 @@ def _load():
         P = C.c_void_p
         lib.orc_preprocess.restype = C.c_int
         lib.orc_preprocess.argtypes = [C.c_int64, P, P, P, P, P, C.c_int, P, C.c_int, C.c_int, P,
-                                       C.c_double, C.c_int, C.c_int, C.c_int] + [P] * 15
+                                       C.c_int, C.c_double, C.c_int, C.c_int, C.c_int] + [P] * 15
         lib.orc_count_pairs.restype = C.c_int64
         lib.orc_count_pairs.argtypes = [C.c_int64, P, P, P, P, P, C.c_int, C.c_int, C.c_int, C.c_int]
         lib.orc_build_keys.restype = C.c_int
@@ -56,10 +56,12 @@ def _load():
         lib.orc_box_min_q.argtypes = [C.c_double] * 7
         lib.orc_render.restype = C.c_int
         lib.orc_render.argtypes = ([C.c_int64, P, P, P, P, P, P, P, P, P, P, P, P, C.c_int, C.c_int,
-                                    P, C.c_double, C.c_int, C.c_int, P, P, P, P, P, C.c_int,
+                                    P, C.c_int, C.c_double, C.c_int, C.c_int, P, P, P, P, P, C.c_int,
                                     C.c_int, C.c_int, P, P, P, P])
         lib.orc_rara_weight.restype = C.c_double
         lib.orc_rara_weight.argtypes = [P, P, P, P, P, C.c_double, P, P]
+        lib.orc_rara_weight_vol.restype = C.c_double
+        lib.orc_rara_weight_vol.argtypes = [P, P, P, P, P, C.c_double, P, C.c_int]
         lib.orc_sh_colour.restype = None
         lib.orc_sh_colour.argtypes = [C.c_int, P, P, P]
         lib.orc_real_sh.restype = C.c_double
@@ -90,13 +92,16 @@ def cam16(cam) -> np.ndarray:
 
 
 def plane4(plane) -> np.ndarray:
-    """(n, d) as the GPU receives them (float32), or unrounded when the plane carries an
-    attribute exact=True (finite-difference perturbations of the plane)."""
-    if getattr(plane, "exact", False):
-        n = np.asarray(plane.n, np.float64)
-        return np.array([n[0], n[1], n[2], float(plane.d)], np.float64)
-    n = np.asarray(plane.n, np.float32).astype(np.float64)
-    return np.array([n[0], n[1], n[2], float(np.float32(plane.d))], np.float64)
+    """The clip planes (n, d), four doubles each: the plane's own, then its extra planes
+    (plane.extra, rows (nx, ny, nz, d)) of a convex clip volume. As the GPU receives them
+    (float32), or unrounded when the plane carries an attribute exact=True (finite-difference
+    perturbations of the plane)."""
+    rows = [list(np.asarray(plane.n).reshape(3)) + [plane.d]]
+    rows += [list(np.asarray(e).reshape(4)) for e in getattr(plane, "extra", ())]
+    a = np.asarray(rows, np.float64)
+    if not getattr(plane, "exact", False):
+        a = np.asarray(rows, np.float32).astype(np.float64)
+    return np.ascontiguousarray(a.reshape(-1))
 
 
 def preprocess(scene, cam, plane, tile=(16, 16)) -> dict:
@@ -112,7 +117,8 @@ def preprocess(scene, cam, plane, tile=(16, 16)) -> dict:
           _f64(scene.opacity_logits), _f64(scene.sh)]
     c16, p4 = cam16(cam), plane4(plane)
     rc = lib.orc_preprocess(n, *[_p(a) for a in sc], int(scene.sh_degree), _p(c16),
-                            int(cam.width), int(cam.height), _p(p4), float(np.float32(plane.k_sigma)),
+                            int(cam.width), int(cam.height), _p(p4), p4.size // 4,
+                            float(np.float32(plane.k_sigma)),
                             int(plane.mode), int(tile[0]), int(tile[1]),
                             *[_p(out[k]) for k in ("label", "culled", "depth", "mean2d", "cov2d",
                                                    "conic", "rect", "tiles", "rgb", "opacity",
@@ -188,7 +194,7 @@ def render(scene, pre: dict, cam, plane, bg=(0.0, 0.0, 0.0), binned=None, tol=DE
     threads = threads or (os.cpu_count() or 1)
     rc = lib.orc_render(n, *[_p(a) for a in sc], _p(pre["label"]), _p(pre["culled"]),
                         _p(pre["depth"]), _p(pre["mean2d"]), _p(pre["conic"]), _p(pre["rgb"]),
-                        _p(pre["opacity"]), _p(pre["margin_gauss"]), _p(c16), W, H, _p(p4),
+                        _p(pre["opacity"]), _p(pre["margin_gauss"]), _p(c16), W, H, _p(p4), p4.size // 4,
                         float(np.float32(plane.k_sigma)), pre["tile"][0], pre["tile"][1], _p(bgv),
                         kp, vp, rp, _p(tolv), int(threads), int(rows[0] if rows else 0),
                         int(rows[1] if rows else H), _p(image), _p(T), _p(nc), _p(ev))
@@ -214,6 +220,17 @@ def rara_weight(e, d, mu, quat, sigma, k_sigma, plane_n, plane_d):
     tout = np.zeros(3)
     w = lib.orc_rara_weight(*[_p(a) for a in arrs], float(k_sigma), _p(p4), _p(tout))
     return float(w), tuple(float(x) for x in tout)
+
+
+def rara_weight_volume(e, d, mu, quat, sigma, k_sigma, planes):
+    """Decay weight against the convex clip volume of `planes` (rows (nx, ny, nz, d)): the
+    share of the chord of the ray e + t d through the ellipsoid k R S that lies on the
+    visible side of every plane (1 when the ray meets the ellipsoid fewer than twice in
+    front)."""
+    lib = _load()
+    arrs = [np.ascontiguousarray(np.asarray(x, np.float64)) for x in (e, d, mu, quat, sigma)]
+    pl = np.ascontiguousarray(np.asarray(planes, np.float64).reshape(-1))
+    return float(lib.orc_rara_weight_vol(*[_p(a) for a in arrs], float(k_sigma), _p(pl), pl.size // 4))
 
 
 def sh_colour(degree: int, coeffs, direction):

@@ -165,11 +165,17 @@ static void eval_colour(const double *sh, int64_t n, int64_t i, int degree, cons
  * Modes: NONE labels all visible; HARD labels invisible iff d_ep < 0 (centre test);
  * RARA is the paper's three-way rule; RARA_ALL uses the three-way rule but ray-traces
  * every non-invisible Gaussian (label cutoff for all of them).
+ * plane4 holds nplanes >= 1 planes (n, d), four doubles each; the visible region is the
+ * intersection of their visible sides (a convex clip volume). The three-way rule then
+ * reads: invisible if the Gaussian's sphere of radius r lies wholly behind some plane
+ * (d_ep,k < -r for some k), visible if it lies wholly in front of all of them (d_ep,k > r
+ * for every k), cutoff otherwise; hard clipping: invisible iff the centre is behind some
+ * plane. With one plane these are the rules above. d_ep[i] reports the first plane's.
  */
 int orc_preprocess(int64_t n, const double *means, const double *log_scales, const double *quats,
                    const double *opacity_logits, const double *sh, int sh_degree,
-                   const double *cam16, int W, int H, const double *plane4, double k_sigma, int mode,
-                   int tile_w, int tile_h,
+                   const double *cam16, int W, int H, const double *plane4, int nplanes, double k_sigma,
+                   int mode, int tile_w, int tile_h,
                    uint8_t *label, uint8_t *culled, double *depth, double *mean2d, double *cov2d,
                    double *conic, int32_t *rect, int32_t *tiles, double *rgb, double *opacity,
                    double *d_ep, double *radius, double *margin_class, double *margin_gauss,
@@ -197,14 +203,28 @@ int orc_preprocess(int64_t n, const double *means, const double *log_scales, con
         if (mode == ORC_MODE_NONE) {
             lab = ORC_VISIBLE;
         } else if (mode == ORC_MODE_HARD) {
-            lab = dep < 0.0 ? ORC_INVISIBLE : ORC_VISIBLE;
-            mc = mg = fabs(dep);
+            int behind = 0;
+            mc = INFINITY;
+            for (int k = 0; k < nplanes; ++k) {
+                double dk = dot3(&plane4[4 * k], mu) + plane4[4 * k + 3];
+                behind = behind || dk < 0.0;
+                mc = fmin(mc, fabs(dk));
+            }
+            lab = behind ? ORC_INVISIBLE : ORC_VISIBLE;
+            mg = mc;
         } else {
-            if (dep < -r) lab = ORC_INVISIBLE;
-            else if (dep > r) lab = ORC_VISIBLE;
+            int behind = 0, front = 1;
+            mc = INFINITY;
+            for (int k = 0; k < nplanes; ++k) {
+                double dk = dot3(&plane4[4 * k], mu) + plane4[4 * k + 3];
+                behind = behind || dk < -r;
+                front = front && dk > r;
+                mc = fmin(mc, fmin(fabs(dk - r), fabs(dk + r)));
+            }
+            if (behind) lab = ORC_INVISIBLE;
+            else if (front) lab = ORC_VISIBLE;
             else lab = ORC_CUTOFF;
             if (mode == ORC_MODE_RARA_ALL && lab != ORC_INVISIBLE) lab = ORC_CUTOFF;
-            mc = fmin(fabs(dep - r), fabs(dep + r));
             /* With k_sigma <= 3 the traced ellipsoid lies inside the radius-r sphere, so at
              * d_ep = +r every chord is visible (w = 1) and at d_ep = -r none is (w = 0): the
              * labels change there but the image does not jump. A larger ellipsoid pokes out. */
@@ -475,6 +495,68 @@ double orc_rara_weight_full(const double *e, const double *d, const double *mu, 
     return fmin(1.0, fmax(0.0, w));
 }
 
+/*
+ * The decay weight against a convex clip volume: the intersection of the half-spaces
+ * n_k.x + d_k >= 0, k < K (planes[4k..4k+3] = n_k, d_k). The paper clips by one plane and
+ * names other clipping primitives as an extension wherever a ray-primitive intersection is
+ * available (Discussion, Limitations); for a convex volume Eq. 11 keeps its meaning: w is
+ * the share of the chord [t1, t2] (Eq. 4-7) that lies inside the volume. Each plane is
+ * linear along the ray, s_k(t) = (n_k.e + d_k) + t (n_k.d), so its visible part of the
+ * chord is one interval (Eq. 8 gives its end t_p); the visible part of the chord is their
+ * intersection, and w = its length / (t2 - t1). Rays that meet the ellipsoid fewer than
+ * twice in front of the camera keep w = 1, as for one plane.
+ */
+double orc_rara_weight_volume(const double *e, const double *d, const double *mu, double Rg[3][3],
+                              const double *sig, double k_sigma, const double *planes, int nplanes,
+                              unsigned *events, double tol_disc)
+{
+    double em[3] = {e[0] - mu[0], e[1] - mu[1], e[2] - mu[2]};
+    double et[3], dt[3];
+    for (int a = 0; a < 3; ++a) {
+        double inv = 1.0 / (k_sigma * sig[a]);
+        et[a] = inv * (Rg[0][a] * em[0] + Rg[1][a] * em[1] + Rg[2][a] * em[2]);
+        dt[a] = inv * (Rg[0][a] * d[0] + Rg[1][a] * d[1] + Rg[2][a] * d[2]);
+    }
+    double A = dot3(dt, dt);
+    double B = 2.0 * dot3(et, dt);
+    double C = dot3(et, et) - 1.0;
+    double disc = B * B - 4.0 * A * C;
+    if (events && fabs(disc) <= tol_disc * 4.0 * A) {
+        /* grazing ray: w jumps between the miss value 1 and ~0 when the tangent point is
+         * outside the volume (on or behind one of its planes) */
+        double tm = -B / (2.0 * A);
+        double xm[3] = {e[0] + tm * d[0], e[1] + tm * d[1], e[2] + tm * d[2]};
+        for (int k = 0; k < nplanes; ++k)
+            if (dot3(&planes[4 * k], xm) + planes[4 * k + 3] <= 1e-6) *events |= EV_DISC;
+    }
+    if (disc <= 0.0) return 1.0;
+    double sq = sqrt(disc);
+    double t1 = (-B - sq) / (2.0 * A), t2 = (-B + sq) / (2.0 * A);
+    if (events && fabs(t1) <= 1e-6 * (t2 - t1)) *events |= EV_T1;
+    if (!(t1 > 0.0 && t2 > 0.0)) return 1.0;
+    double lo = t1, hi = t2;
+    for (int k = 0; k < nplanes; ++k) {
+        const double *pk = &planes[4 * k];
+        double a0 = dot3(pk, e) + pk[3];  /* s_k at t = 0 */
+        double b = dot3(pk, d);           /* ds_k / dt */
+        if (b > 0.0) lo = fmax(lo, -a0 / b);       /* visible for t >= t_p */
+        else if (b < 0.0) hi = fmin(hi, -a0 / b);  /* visible for t <= t_p */
+        else if (a0 < 0.0) return 0.0;             /* parallel, chord wholly behind it */
+    }
+    return hi > lo ? (hi - lo) / (t2 - t1) : 0.0;
+}
+
+/* ctypes-friendly wrapper of the volume weight (quaternion (w,x,y,z), sigma). */
+double orc_rara_weight_vol(const double *e, const double *d, const double *mu, const double *quat,
+                           const double *sig, double k_sigma, const double *planes, int nplanes)
+{
+    double Rg[3][3];
+    quat_to_rot(quat[0], quat[1], quat[2], quat[3], Rg);
+    double dn = sqrt(dot3(d, d));
+    double du[3] = {d[0] / dn, d[1] / dn, d[2] / dn};
+    return orc_rara_weight_volume(e, du, mu, Rg, sig, k_sigma, planes, nplanes, NULL, 0.0);
+}
+
 /* ctypes-friendly wrapper: quaternion (w,x,y,z) and log-free sigma. */
 double orc_rara_weight(const double *e, const double *d, const double *mu, const double *quat,
                        const double *sig, double k_sigma, const double *plane4, double *tout)
@@ -530,7 +612,7 @@ int orc_render(int64_t n, const double *means, const double *log_scales, const d
                const uint8_t *label, const uint8_t *culled, const double *depth,
                const double *mean2d, const double *conic, const double *rgb, const double *opacity,
                const double *margin_gauss,
-               const double *cam16, int W, int H, const double *plane4, double k_sigma,
+               const double *cam16, int W, int H, const double *plane4, int nplanes, double k_sigma,
                int tile_w, int tile_h, const double *bg,
                const uint64_t *keys, const uint32_t *vals, const int64_t *ranges,
                const double *tol, int nthreads, int row_begin, int row_end,
@@ -604,7 +686,11 @@ int orc_render(int64_t n, const double *means, const double *log_scales, const d
                     double sig[3] = {exp(log_scales[i]), exp(log_scales[n + i]), exp(log_scales[2 * n + i])};
                     double Rg[3][3];
                     quat_to_rot(quats[i], quats[n + i], quats[2 * n + i], quats[3 * n + i], Rg);
-                    w = orc_rara_weight_full(cam.e, dw, mu, Rg, sig, k_sigma, pn, pd, NULL, &ev, tol_disc);
+                    if (nplanes == 1)
+                        w = orc_rara_weight_full(cam.e, dw, mu, Rg, sig, k_sigma, pn, pd, NULL, &ev, tol_disc);
+                    else
+                        w = orc_rara_weight_volume(cam.e, dw, mu, Rg, sig, k_sigma, plane4, nplanes, &ev,
+                                                   tol_disc);
                 }
                 /* Eq. 12 and Algorithm 1 step 3 */
                 double alpha = fmin(0.99, a0 * w);

@@ -85,6 +85,9 @@ class Plane:
     d: float
     k_sigma: float = 3.0
     mode: int = MODE_RARA
+    # further planes (nx, ny, nz, d) of a convex clip volume, at most 3: the visible region
+    # is the intersection of the visible sides of this plane and these
+    extra: tuple = ()
 
 
 def _f32(a) -> np.ndarray:
