@@ -89,11 +89,28 @@ typedef struct rara_camera {
     int32_t width, height;
 } rara_camera;
 
+#define RARA_MAX_EXTRA_PLANES 3
+
+/* The clip plane n.x + d = 0 (visible side n.x + d >= 0), or a convex clip volume: with
+ * n_extra > 0, the planes extra[k] = (n.x, n.y, n.z, d) for k < n_extra are added and the
+ * visible region is the intersection of the visible sides of all 1 + n_extra planes. The
+ * paper clips by one plane and names other clipping primitives, wherever the ray meets
+ * them cheaply, as its extension (Discussion, Limitations); for a convex volume its rules
+ * read: a Gaussian is invisible if its sphere of radius 3 max(sigma) lies wholly behind
+ * some plane, visible if it lies wholly in front of every plane, cutoff otherwise
+ * (Section 3.2, Algorithm 1 step 1 per plane); the decay weight is the share of the pixel
+ * ray's chord through the ellipsoid that lies inside the volume (Eq. 11 with the chord
+ * clipped by every plane, Eq. 8 per plane); hard clipping removes a Gaussian whose centre
+ * is behind some plane. Zero-initialise the struct: n_extra = 0 is the single plane.
+ * rara_render_backward and rara_render_frame_noalloc accept single planes only
+ * (RARA_ERR_INVALID_ARG for n_extra > 0). */
 typedef struct rara_plane {
     float n[3];
     float d;
-    float k_sigma; /* > 0 */
-    int32_t mode;  /* rara_mode */
+    float k_sigma;   /* > 0 */
+    int32_t mode;    /* rara_mode */
+    int32_t n_extra; /* 0..RARA_MAX_EXTRA_PLANES further planes of a convex clip volume */
+    float extra[RARA_MAX_EXTRA_PLANES][4];
 } rara_plane;
 
 /* One view of a batch: a camera, a clip plane and output buffers over one of the batch's

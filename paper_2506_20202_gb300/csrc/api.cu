@@ -64,6 +64,9 @@ struct rara_ctx {
     // device
     DevBuf views_d, scenes_d, view_counters_d, counters;
     DevBuf labels, tiles, rect, rec, cut, depth;
+    DevBuf cut_x;                       // further planes of clip-volume cutoff slots
+    bool multi = false;                 // the batch has a view with a convex clip volume
+    bool extra_planes = false;          // the batch has a view with further planes
     DevBuf ckeys, cvals, ckeys_b, cvals_b, lookback_c;
     DevBuf pkeys, pvals, pkeys_b, pvals_b, lookback_e;
     DevBuf hist, ranges, items, sort_scratch, seg_base, export_off;
@@ -210,6 +213,11 @@ int check_view(rara_ctx *c, const rara_camera *cam, const rara_plane *pl)
     if (!(finite(pl->k_sigma) && pl->k_sigma > 0)) return fail(c, RARA_ERR_INVALID_ARG, "k_sigma must be > 0");
     if (pl->mode < RARA_MODE_NONE || pl->mode > RARA_MODE_RARA_ALL)
         return fail(c, RARA_ERR_INVALID_ARG, "unknown mode %d", pl->mode);
+    if (pl->n_extra < 0 || pl->n_extra > RARA_MAX_EXTRA_PLANES)
+        return fail(c, RARA_ERR_INVALID_ARG, "n_extra %d outside [0, %d]", pl->n_extra, RARA_MAX_EXTRA_PLANES);
+    for (int e = 0; e < pl->n_extra; ++e)
+        for (int k = 0; k < 4; ++k)
+            if (!finite(pl->extra[e][k])) return fail(c, RARA_ERR_INVALID_ARG, "non-finite clip-volume plane");
     return RARA_OK;
 }
 
@@ -225,6 +233,9 @@ void fill_view(ViewDev &v, const rara_camera *cam, const rara_plane *pl)
     v.plane.d = pl->d;
     v.plane.k = pl->k_sigma;
     v.plane.mode = pl->mode;
+    v.plane.n_extra = pl->n_extra;
+    for (int e = 0; e < RARA_MAX_EXTRA_PLANES; ++e)
+        for (int k = 0; k < 4; ++k) v.plane.ex[e][k] = e < pl->n_extra ? pl->extra[e][k] : 0.0f;
     v.tiles_x = (cam->width + kTile - 1) / kTile;
     v.tiles_y = (cam->height + kTile - 1) / kTile;
 }
@@ -275,6 +286,13 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
         if (!views[v].image) return fail(c, RARA_ERR_INVALID_ARG, "view %d has no image buffer", v);
     }
     if ((rc = next_staging(c))) return rc;
+    c->multi = false;
+    c->extra_planes = false;
+    for (int v = 0; v < nv; ++v) {
+        const rara_plane &pl = views[v].plane;
+        c->extra_planes = c->extra_planes || pl.n_extra > 0;
+        c->multi = c->multi || (pl.n_extra > 0 && (pl.mode == RARA_MODE_RARA || pl.mode == RARA_MODE_RARA_ALL));
+    }
     uint64_t max_tiles = 1;
     for (int v = 0; v < nv; ++v) {
         const uint64_t t = (uint64_t)((views[v].camera.width + kTile - 1) / kTile) *
@@ -344,7 +362,8 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
         (rc = ensure(c, c->hist, kHistPasses * 256 * 4, "digit histograms")) ||
         (rc = ensure(c, c->seg_base, sizeof(uint32_t) * (size_t)nv, "view slot bases")) ||
         (rc = ensure(c, c->ranges, nt * sizeof(int2), "ranges")) ||
-        (rc = ensure(c, c->items, nt * 16, "render items")))
+        (rc = ensure(c, c->items, nt * 16, "render items")) ||
+        (c->multi && (rc = ensure(c, c->cut_x, nn * sizeof(CutExtra), "clip-volume records"))))
         return rc;
     return upload_tables(c, s);
 }
@@ -373,6 +392,7 @@ int batch_preprocess(rara_ctx *c, cudaStream_t s)
     a.rect = (uint2 *)c->rect.p;
     a.rec = (SplatRec *)c->rec.p;
     a.cut = (CutRec *)c->cut.p;
+    a.cut_x = c->multi ? (CutExtra *)c->cut_x.p : nullptr;
     a.depth = (float *)c->depth.p;
     a.view_counters = (ViewCounters *)c->view_counters_d.p;
     a.counters = dc;
@@ -512,13 +532,14 @@ int batch_render(rara_ctx *c, cudaStream_t s)
     a.vals_b = (const uint32_t *)c->pvals_b.p;
     a.rec = (const SplatRec *)c->rec.p;
     a.cut = (const CutRec *)c->cut.p;
+    a.cut_x = c->multi ? (const CutExtra *)c->cut_x.p : nullptr;
     a.views = (const ViewDev *)c->views_d.p;
     a.num_views = c->num_views;
     a.counters = dc;
     const long long slots = (long long)c->sm_count * c->bpsm_render;
     const long long items = 4ll * c->num_tiles;
     // graph captures run without the work counters (their replays are not read for them)
-    launch_render(a, (int)(items < slots ? items : slots), s, !c->capturing);
+    launch_render(a, (int)(items < slots ? items : slots), s, !c->capturing, c->multi);
     rc = launched(c, "render launch", c->num_tiles > 0);
     mark(c, 3, s);
     return rc;
@@ -615,7 +636,7 @@ int rara_ctx_destroy(rara_ctx *c)
     if (!c) return RARA_OK;
     cudaDeviceSynchronize();
     DevBuf *all[] = {&c->views_d, &c->scenes_d, &c->view_counters_d, &c->counters, &c->labels, &c->tiles,
-                     &c->rect, &c->rec, &c->cut, &c->depth, &c->ckeys, &c->cvals, &c->ckeys_b, &c->cvals_b,
+                     &c->rect, &c->rec, &c->cut, &c->cut_x, &c->depth, &c->ckeys, &c->cvals, &c->ckeys_b, &c->cvals_b,
                      &c->lookback_c, &c->pkeys, &c->pvals, &c->pkeys_b, &c->pvals_b, &c->lookback_e, &c->hist,
                      &c->ranges, &c->items, &c->sort_scratch, &c->grec, &c->bviews_d, &c->bscenes_d,
                      &c->seg_base, &c->export_off};
@@ -774,13 +795,19 @@ int rara_render_batch_graph(rara_ctx *c, const rara_gaussians *scenes, int32_t n
         num_views > c->max_views)
         return fail(c, RARA_ERR_INVALID_ARG, "bad batch (%d scenes, %d views)", num_scenes, num_views);
     if (!c->owns_host) return fail(c, RARA_ERR_INVALID_ARG, "graph batches need a regular context");
-    // batch shape: scene sizes and degrees, views' scene and resolution
-    const size_t len = 2 + 2 * (size_t)num_scenes + 3 * (size_t)num_views;
+    // batch shape: scene sizes and degrees, views' scene and resolution, and whether a view
+    // clips by a convex volume (the render kernel's variant and buffers depend on it)
+    const size_t len = 3 + 2 * (size_t)num_scenes + 3 * (size_t)num_views;
     int *shape = (int *)malloc(sizeof(int) * len);
     if (!shape) return fail(c, RARA_ERR_BUDGET, "host allocation failed");
     size_t k = 0;
     shape[k++] = num_scenes;
     shape[k++] = num_views;
+    int multi = 0;
+    for (int v = 0; v < num_views; ++v)
+        multi |= views[v].plane.n_extra > 0 &&
+                 (views[v].plane.mode == RARA_MODE_RARA || views[v].plane.mode == RARA_MODE_RARA_ALL);
+    shape[k++] = multi;
     for (int i = 0; i < num_scenes; ++i) {
         shape[k++] = (int)scenes[i].n;
         shape[k++] = scenes[i].sh_degree;
@@ -874,6 +901,8 @@ int rara_render_backward(rara_ctx *c, const float *const *dL_dimages, const rara
     if (!c->rendered || c->stage < 2)
         return fail(c, RARA_ERR_INVALID_ARG, "rara_render_backward needs a rendered frame or batch on this context");
     if (!dL_dimages || !grads) return fail(c, RARA_ERR_INVALID_ARG, "null dL_dimages or grads");
+    if (c->extra_planes)
+        return fail(c, RARA_ERR_INVALID_ARG, "the backward supports single clip planes (a view has n_extra > 0)");
     for (int v = 0; v < c->num_views; ++v) {
         if (!dL_dimages[v]) return fail(c, RARA_ERR_INVALID_ARG, "view %d has no dL/dimage", v);
         const ViewDev &vd = c->h_views[c->h_view_map[v]];
@@ -1206,6 +1235,7 @@ extern "C" int rara_render_frame_noalloc(const rara_gaussians *g, const rara_cam
                                          void *stream)
 {
     if (!g || !cam || !plane || !bg || !image) return RARA_ERR_INVALID_ARG;
+    if (plane->n_extra != 0) return RARA_ERR_INVALID_ARG;  // single planes only: no clip-volume scratch
     if (g->n < 0 || g->n > kStaticMaxGaussians) return RARA_ERR_BUDGET;
     if (cam->width <= 0 || cam->height <= 0) return RARA_ERR_INVALID_ARG;
     const int64_t tiles = (int64_t)((cam->width + kTile - 1) / kTile) * ((cam->height + kTile - 1) / kTile);

@@ -219,6 +219,19 @@ __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
                     label = dep < -r ? RARA_INVISIBLE : (dep > r ? RARA_VISIBLE : RARA_CUTOFF);
                     if (pl.mode == RARA_MODE_RARA_ALL && label != RARA_INVISIBLE) label = RARA_CUTOFF;
                 }
+                // A convex clip volume: the rule of each further plane joins the first's.
+                // Invisible if behind any plane (the centre for hard clipping, the radius-r
+                // sphere otherwise), visible only if in front of all of them.
+                for (int e = 0; e < pl.n_extra && pl.mode != RARA_MODE_NONE; ++e) {
+                    const float de = fmaf(pl.ex[e][0], mx, fmaf(pl.ex[e][1], my, fmaf(pl.ex[e][2], mz, pl.ex[e][3])));
+                    if (pl.mode == RARA_MODE_HARD) {
+                        if (de < 0.0f) label = RARA_INVISIBLE;
+                    } else if (de < -r) {
+                        label = RARA_INVISIBLE;
+                    } else if (de <= r && label == RARA_VISIBLE) {
+                        label = RARA_CUTOFF;
+                    }
+                }
                 a.labels[slot] = (uint8_t)label;
 
                 const float tx = fmaf(cam.R[0], mx, fmaf(cam.R[1], my, fmaf(cam.R[2], mz, cam.t[0])));
@@ -317,6 +330,40 @@ __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
                                 const float mlen = sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
                                 const float bound = mlen * (1.0f + 1e-4f);
                                 wmode = dep > bound ? kWeightNone : (dep < -bound ? kWeightHidden : kWeightSplit);
+                                // Convex clip volume: a plane wholly in front of the ellipsoid
+                                // constrains no chord and drops out; one wholly behind it hides
+                                // it (w = 0 where a ray hits it in front); the splitting planes
+                                // clip the chord. The first splitting plane takes the CutRec's
+                                // plane terms, the others the slot's CutExtra.
+                                float xs[3][4] = {};
+                                int nsplit = wmode == kWeightSplit ? 1 : 0;
+                                float sdep = dep;
+                                for (int e = 0; e < pl.n_extra; ++e) {
+                                    float me[3];
+#pragma unroll
+                                    for (int k = 0; k < 3; ++k)
+                                        me[k] = kk * sg[k] * (Rg[k] * pl.ex[e][0] + Rg[3 + k] * pl.ex[e][1] +
+                                                              Rg[6 + k] * pl.ex[e][2]);
+                                    const float de = fmaf(pl.ex[e][0], mx,
+                                                          fmaf(pl.ex[e][1], my, fmaf(pl.ex[e][2], mz, pl.ex[e][3])));
+                                    const float be = sqrtf(me[0] * me[0] + me[1] * me[1] + me[2] * me[2]) * (1.0f + 1e-4f);
+                                    if (de < -be) {
+                                        wmode = kWeightHidden;
+                                    } else if (de <= be) {
+                                        if (nsplit == 0) {
+                                            sdep = de;
+#pragma unroll
+                                            for (int k = 0; k < 3; ++k) m[k] = me[k];
+                                        } else {
+                                            xs[nsplit - 1][0] = de;
+#pragma unroll
+                                            for (int k = 0; k < 3; ++k) xs[nsplit - 1][1 + k] = me[k];
+                                        }
+                                        ++nsplit;
+                                    }
+                                }
+                                if (pl.n_extra > 0 && wmode != kWeightHidden)
+                                    wmode = nsplit == 0 ? kWeightNone : (nsplit == 1 ? kWeightSplit : kWeightMulti);
                                 // With the camera inside (or on) the ellipsoid, G.G <= 1, the
                                 // roots of every ray have product (G.G - 1) / V.V <= 0: no ray
                                 // meets it twice in front, so w = 1 for every ray.
@@ -327,7 +374,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
                                     // dot products G.p, p.p, m.p and the cross product p x G: store
                                     // the pairwise products of G, Px, Py, m and A = Px x G, B = Py x G.
                                     CutRec c;
-                                    c.c0 = make_float4(GG, dot3(G, Px), dot3(G, Py), dep);
+                                    c.c0 = make_float4(GG, dot3(G, Px), dot3(G, Py), sdep);
                                     c.c1 = make_float4(dot3(Px, Px), dot3(Px, Py), dot3(Py, Py), dot3(m, G));
                                     float A[3], B[3];
                                     cross3(Px, G, A);
@@ -335,6 +382,17 @@ __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
                                     c.c2 = make_float4(dot3(m, Px), dot3(m, Py), A[0], A[1]);
                                     c.c3 = make_float4(A[2], B[0], B[1], B[2]);
                                     a.cut[slot] = c;
+                                    if (wmode == kWeightMulti) {
+                                        CutExtra x;
+#pragma unroll
+                                        for (int e = 0; e < 3; ++e) {
+                                            const float *me = &xs[e][1];
+                                            x.p[e] = e + 1 < nsplit
+                                                         ? make_float4(xs[e][0], dot3(me, G), dot3(me, Px), dot3(me, Py))
+                                                         : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+                                        }
+                                        a.cut_x[slot] = x;
+                                    }
                                 }
                             }
                             rec.r2 = make_float4(rgb[2], wmode, cb / cc, cb / ca);

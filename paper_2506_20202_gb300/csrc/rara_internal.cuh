@@ -62,6 +62,9 @@ struct __align__(16) SplatRec {
 // the visible side has w = 1 for every ray, one wholly on the invisible side has w = 0 for
 // the rays that hit it in front and 1 for the others.
 constexpr float kWeightNone = 0.0f, kWeightSplit = 1.0f, kWeightHidden = 2.0f;
+// A cutoff Gaussian that two or more planes of a convex clip volume split (and none hides):
+// its CutRec holds the first splitting plane, CutExtra the others.
+constexpr float kWeightMulti = 3.0f;
 
 // Per-cutoff-slot ray-tracing record, 4 x float4 = 64 bytes, relative to the Gaussian's own
 // frame (see preprocess.cu for the derivation). With G = M^-1 (mu - e), the columns Px, Py
@@ -73,6 +76,13 @@ constexpr float kWeightNone = 0.0f, kWeightSplit = 1.0f, kWeightHidden = 2.0f;
 //   c3 = (A.z, B.x, B.y, B.z)          B = Py x G
 struct __align__(16) CutRec {
     float4 c0, c1, c2, c3;
+};
+
+// The further splitting planes of a kWeightMulti slot, in the CutRec's terms:
+// p[k] = (d_ep, m.G, m.Px, m.Py) of the plane; unused entries are (1, 0, 0, 0), a plane with
+// s = 1 everywhere, which constrains nothing.
+struct __align__(16) CutExtra {
+    float4 p[3];
 };
 
 struct CamDev {
@@ -88,6 +98,8 @@ struct PlaneDev {
     float d;
     float k;
     int mode;
+    int n_extra;      // further planes of a convex clip volume (0..3)
+    float ex[3][4];   // their (n, d)
 };
 
 struct ViewDev {
@@ -157,6 +169,7 @@ struct PreprocessArgs {
     uint2 *rect;           // (tx0 | ty0 << 16, tx1 | ty1 << 16), tile coordinates in the view
     SplatRec *rec;
     CutRec *cut;
+    CutExtra *cut_x;  // per slot, only for batches with clip volumes (else null)
     float *depth;          // camera-space depth (the float32 sort key) of rendered slots
     ViewCounters *view_counters;
     Counters *counters;
@@ -241,12 +254,13 @@ struct RenderArgs {
     const uint32_t *vals_a, *vals_b;  // the tile sort's value buffers (slots)
     const SplatRec *rec;
     const CutRec *cut;
+    const CutExtra *cut_x;  // per slot, only for batches with clip volumes (else null)
     const ViewDev *views;
     int num_views;
     Counters *counters;
 };
 // count: accumulate the work counters (n_evaluated .. n_tested) of the launch.
-void launch_render(const RenderArgs &a, int grid, cudaStream_t s, bool count = true);
+void launch_render(const RenderArgs &a, int grid, cudaStream_t s, bool count = true, bool multi = false);
 int render_blocks_per_sm();
 
 // Backward. Per-slot gradient record, 7 x float4 = 112 bytes, accumulated (atomics) by the

@@ -57,7 +57,7 @@ struct Tally {
 //   LPP 1: the whole tile, warp rectangles 8x4
 //   LPP 2: rows [8 part, 8 part + 8), warp rectangles 8x2
 //   LPP 4: rows [4 part, 4 part + 4), warp rectangles 4x2
-template <int LPP, bool COUNT>
+template <int LPP, bool COUNT, bool MULTI>
 __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &vw, const uint32_t *pair_vals,
                                             Stage &st, int gtile, int tile, int part, Tally<COUNT> &ty)
 {
@@ -93,6 +93,9 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
             stage_splat(st, threadIdx.x, rec);
             if (rec.r2.y != kWeightNone) {
                 stage_cut(st, threadIdx.x, a.cut[g]);
+                // a Gaussian split by several planes of a clip volume: its slot, for the
+                // further planes (the staged c3.y is otherwise unused)
+                if (MULTI && rec.r2.y == kWeightMulti) st.c3[threadIdx.x].y = __uint_as_float(g);
             }
         }
         __syncthreads();
@@ -129,8 +132,14 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
                     float alpha = a0;
                     if ((mw >> bit) & 1u) {
                         const float mode = s1.w;
-                        ty.add(ty.cut, inq && a0 >= kAlphaMin && mode == kWeightSplit);
-                        alpha = __fmul_rn(a0, decay_weight(mode, st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy));
+                        ty.add(ty.cut, inq && a0 >= kAlphaMin && (mode == kWeightSplit || (MULTI && mode == kWeightMulti)));
+                        if (MULTI && mode == kWeightMulti) {
+                            const float4 c3 = st.c3[j];
+                            alpha = __fmul_rn(a0, rara_weight_multi(st.c0[j], st.c1[j], st.c2[j], c3,
+                                                                    a.cut_x[__float_as_uint(c3.y)], dx, dy));
+                        } else {
+                            alpha = __fmul_rn(a0, decay_weight(mode, st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy));
+                        }
                     }
                     alpha = fminf(kAlphaMax, alpha);
                     const bool valid = inq && alpha >= kAlphaMin;
@@ -172,9 +181,18 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
                     float alpha = a0;
                     const bool wt = live && s1.w != kWeightNone;
                     if (__any_sync(0xffffffffu, wt)) {
-                        ty.add(ty.cut, live && s1.w == kWeightSplit);
-                        const float w = decay_weight_any(wt ? s1.w : kWeightNone, st.c0[j], st.c1[j], st.c2[j],
-                                                         st.c3[j], dx, dy);
+                        ty.add(ty.cut, live && (s1.w == kWeightSplit || (MULTI && s1.w == kWeightMulti)));
+                        float w = decay_weight_any(wt ? s1.w : kWeightNone, st.c0[j], st.c1[j], st.c2[j],
+                                                   st.c3[j], dx, dy);
+                        if (MULTI) {
+                            const bool wm = wt && s1.w == kWeightMulti;
+                            if (__any_sync(0xffffffffu, wm)) {
+                                const float4 c3 = st.c3[j];
+                                const uint32_t xs = wm ? __float_as_uint(c3.y) : 0u;  // slot 0 exists
+                                const float w2 = rara_weight_multi(st.c0[j], st.c1[j], st.c2[j], c3, a.cut_x[xs], dx, dy);
+                                if (wm) w = w2;
+                            }
+                        }
                         alpha = __fmul_rn(a0, w);
                     }
                     alpha = fminf(kAlphaMax, alpha);
@@ -227,7 +245,7 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
     }
 }
 
-template <bool COUNT>
+template <bool COUNT, bool MULTI>
 __global__ void __launch_bounds__(kBlock, 5) k_render(RenderArgs a)
 {
     __shared__ Stage st;
@@ -253,9 +271,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_render(RenderArgs a)
         }
         const ViewDev &vw = a.views[lo];
         const int tile = gtile - (int)vw.tile_base;
-        if (lpp_log2 == 0) render_item<1, COUNT>(a, vw, pair_vals, st, gtile, tile, 0, ty);
-        else if (lpp_log2 == 1) render_item<2, COUNT>(a, vw, pair_vals, st, gtile, tile, part, ty);
-        else render_item<4, COUNT>(a, vw, pair_vals, st, gtile, tile, part, ty);
+        if (lpp_log2 == 0) render_item<1, COUNT, MULTI>(a, vw, pair_vals, st, gtile, tile, 0, ty);
+        else if (lpp_log2 == 1) render_item<2, COUNT, MULTI>(a, vw, pair_vals, st, gtile, tile, part, ty);
+        else render_item<4, COUNT, MULTI>(a, vw, pair_vals, st, gtile, tile, part, ty);
         __syncthreads();  // everyone has read s_item and the staged batch
     }
 
@@ -280,18 +298,23 @@ __global__ void __launch_bounds__(kBlock, 5) k_render(RenderArgs a)
 int render_blocks_per_sm()
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_render<true>, kBlock, 0) != cudaSuccess || b < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_render<true, false>, kBlock, 0) != cudaSuccess || b < 1) {
         cudaGetLastError();
         b = 1;
     }
     return b;
 }
 
-void launch_render(const RenderArgs &a, int grid, cudaStream_t s, bool count)
+void launch_render(const RenderArgs &a, int grid, cudaStream_t s, bool count, bool multi)
 {
     if (grid <= 0) return;
-    if (count) k_render<true><<<grid, kBlock, 0, s>>>(a);
-    else k_render<false><<<grid, kBlock, 0, s>>>(a);
+    if (multi) {  // batches with a convex clip volume
+        if (count) k_render<true, true><<<grid, kBlock, 0, s>>>(a);
+        else k_render<false, true><<<grid, kBlock, 0, s>>>(a);
+    } else {
+        if (count) k_render<true, false><<<grid, kBlock, 0, s>>>(a);
+        else k_render<false, false><<<grid, kBlock, 0, s>>>(a);
+    }
 }
 
 }  // namespace rara

@@ -96,6 +96,39 @@ __device__ __forceinline__ float rara_weight(const float4 c0, const float4 c1, c
     return hit ? w : 1.0f;  // a ray that misses, grazes or starts inside keeps rasterization
 }
 
+// Decay weight of a Gaussian that several planes of a convex clip volume split
+// (kWeightMulti): the share of the chord inside every half-space (Eq. 11 with the chord
+// clipped by each plane, Eq. 8 per plane). Along the chord, with x in [-1, 1] from one end
+// to the other, plane k is s_mid,k + x h_k, visible for x >= -g_k when h_k > 0 and for
+// x <= g_k' = -(-g_k) when h_k < 0, with g_k = s_mid,k / |h_k| (rara_weight's ratio, here
+// num_k / (sqrt(V.V - |u|^2) |m_k.V|)). The visible part is [lo, hi] = the intersection of
+// those intervals with [-1, 1]; w = (hi - lo) / 2, clamped at 0. A plane with m_k.V = 0 is
+// parallel to the ray: g_k = +-inf keeps everything or nothing by the sign of s, and the
+// padding entries (1, 0, 0, 0) of a CutExtra keep everything. The planes are the CutRec's
+// (c0.w, c1.w, c2.x, c2.y) and x[0..2].
+__device__ __forceinline__ float rara_weight_multi(const float4 c0, const float4 c1, const float4 c2, const float4 c3,
+                                                   const CutExtra &x, float dx, float dy)
+{
+    const RayTerms t = ray_terms(c0, c1, c2, c3, dx, dy);
+    const bool hit = ray_hits_front(t);
+    const float rs = rsqrtf(t.VV - t.uu);  // NaN when the ray misses; then w = 1 below
+    const float GT = t.Gp + t.pp;
+    float lo = -1.0f, hi = 1.0f;
+    auto clip = [&](float dep, float mG, float mPx, float mPy) {
+        const float mp = fmaf(mPx, dx, mPy * dy);
+        const float mV = mG + mp;
+        const float num = fmaf(dep + mp, t.VV, -__fmul_rn(GT, mV));
+        const float g = __fmul_rn(num, rs) / fabsf(mV);
+        if (mV >= 0.0f) lo = fmaxf(lo, -g);
+        else hi = fminf(hi, g);
+    };
+    clip(c0.w, c1.w, c2.x, c2.y);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) clip(x.p[k].x, x.p[k].y, x.p[k].z, x.p[k].w);
+    const float w = __saturatef(0.5f * (hi - lo));
+    return hit ? w : 1.0f;
+}
+
 // The weight of a Gaussian wholly on the invisible side of the plane (kWeightHidden): 0 when
 // the ray hits the ellipsoid in front of the camera, else 1 (rara_weight's hit test).
 __device__ __forceinline__ float rara_weight_hidden(const float4 c0, const float4 c1, const float4 c2,

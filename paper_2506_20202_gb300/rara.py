@@ -39,7 +39,8 @@ class rara_camera(C.Structure):
 
 
 class rara_plane(C.Structure):
-    _fields_ = [("n", C.c_float * 3), ("d", C.c_float), ("k_sigma", C.c_float), ("mode", C.c_int32)]
+    _fields_ = [("n", C.c_float * 3), ("d", C.c_float), ("k_sigma", C.c_float), ("mode", C.c_int32),
+                ("n_extra", C.c_int32), ("extra", (C.c_float * 4) * 3)]
 
 
 class rara_view(C.Structure):
@@ -190,6 +191,11 @@ def plane_struct(plane) -> rara_plane:
     p.d = float(plane.d)
     p.k_sigma = float(plane.k_sigma)
     p.mode = int(plane.mode)
+    extra = getattr(plane, "extra", ())
+    p.n_extra = len(extra)
+    for e, row in enumerate(extra[:3]):
+        for k in range(4):
+            p.extra[e][k] = float(row[k])
     return p
 
 
