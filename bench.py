@@ -75,6 +75,7 @@ def parse_args():
     ap.add_argument("--hair-steps", type=int, default=20, help="frames of the hair-strand workload per path "
                     "(0: skip)")
     ap.add_argument("--train-views", type=int, default=64)
+    ap.add_argument("--volume-steps", type=int, default=20, help="batches of the clip-volume sweep (0: skip)")
     return ap.parse_args()
 
 
@@ -557,6 +558,8 @@ def run_ours(args):
                                                        for c in counts],
                          "pairs_mean": statistics.mean(c["n_pairs"] for c in counts)},
     }
+    if rank == 0 and world == 1 and args.volume_steps > 0:
+        line["volume"] = run_volume(args, gs, cam, planes)
     if rank == 0 and world == 1 and args.hair_steps > 0:
         line["hair"] = run_hair(args)
     if rank == 0 and world == 1 and args.train_steps > 0:
@@ -692,6 +695,59 @@ def run_training(args):
     del gs, grads, dimgs, targets, tviews, views
     torch.cuda.empty_cache()
     return out
+
+
+def run_volume(args, gs, cam, planes):
+    """Clip-volume sweep: the general scene's 16 sweep planes, each joined by a second fixed
+    plane through the scene centre (normal n x (0, 1, 0), so the two planes meet along a line
+    through the image) into a wedge, rendered as one batch of 16 frames, graph-replayed and
+    autotuned like the single-plane sweep."""
+    import numpy as np
+    import torch
+
+    from paper_2506_20202_gb300 import autotune, rara, scenes
+    H, W = cam.height, cam.width
+    stream = torch.cuda.Stream()
+    m = np.cross(np.asarray(planes[0].n, np.float64), [0.0, 1.0, 0.0])
+    m = np.float32(m / np.linalg.norm(m))
+    extra = ((float(m[0]), float(m[1]), float(m[2]), 0.05),)
+    vols = [scenes.Plane(p.n, p.d, p.k_sigma, p.mode, extra) for p in planes]
+    ctx = rara.rara_ctx_create(0)
+    views = [rara.View(0, cam, v, torch.empty((3, H, W), device="cuda"), torch.empty((H, W), device="cuda"),
+                       torch.empty((H, W), dtype=torch.int32, device="cuda"), (0.0, 0.0, 0.0)) for v in vols]
+    if args.tuning:
+        best = tuple(int(x) for x in args.tuning.split(","))
+        rara.rara_ctx_set_tuning(ctx, *best)
+    else:
+        best, _ = autotune.autotune(ctx, [gs], views, stream, reps=2)
+    rara.rara_render_batch(ctx, [gs], views, stream)
+    stage = rara.rara_ctx_stage_ms(ctx)
+    info = [rara.rara_frame_info_get(ctx, v) for v in range(len(views))]
+    for _ in range(3):
+        rara.rara_render_batch_graph(ctx, [gs], views, stream)
+    rara.rara_ctx_sync(ctx, stream)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.volume_steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for e in ev:
+        e[0].record(stream)
+        rara.rara_render_batch_graph(ctx, [gs], views, stream)
+        e[1].record(stream)
+    t1.record(stream)
+    stream.synchronize()
+    rara.rara_ctx_sync(ctx, stream)
+    lat = [e[0].elapsed_time(e[1]) for e in ev]
+    rara.rara_ctx_destroy(ctx)
+    del views
+    torch.cuda.empty_cache()
+    n = gs.n
+    return {"workload": "general scene 1M SH3, 1920x1080, 16-offset sweep, each plane joined by a second plane "
+                        "(a wedge)",
+            "frames_per_s": len(vols) * args.volume_steps / (t0.elapsed_time(t1) / 1e3),
+            "batch_p50_ms": percentile(lat, 50), "batch_p99_ms": percentile(lat, 99), "tuning": list(best),
+            "stage_ms_exact_batch": {"preprocess": stage[0], "bin": stage[1], "render": stage[2]},
+            "cutoff_fraction_per_frame": [round(i["n_cutoff"] / n, 4) for i in info]}
 
 
 def run_hair(args):
