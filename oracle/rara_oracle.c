@@ -50,7 +50,7 @@
 #define EV_Q 1u        /* q near the support bound 9 */
 #define EV_ALPHA 2u    /* final alpha near 1/255 */
 #define EV_T 4u        /* transmittance near the 1e-4 stop */
-#define EV_GAUSS 8u    /* candidate Gaussian flagged near a class or cull threshold */
+#define EV_GAUSS 8u    /* a candidate, or the footprint of an invisible Gaussian, near a threshold where the image jumps */
 #define EV_DISC 16u    /* ray grazing a cutoff ellipsoid (discriminant near 0) */
 #define EV_DEPTH 32u   /* two candidates whose float32 depths differ by a few ulp */
 #define EV_T1 64u      /* camera on the surface of a cutoff ellipsoid */
@@ -159,8 +159,9 @@ static void eval_colour(const double *sh, int64_t n, int64_t i, int degree, cons
  *   rgb[3i..], opacity[i], d_ep[i], radius[i] (= 3 max sigma)
  *   margin_class[i]  distance of d_ep to the nearest label threshold (world units)
  *   margin_gauss[i]  distance to the nearest threshold across which the image is
- *                    discontinuous: the near cull (z) and, for hard clipping or k_sigma > 3,
- *                    the label thresholds
+ *                    discontinuous: the near cull (z); for hard clipping the centre test;
+ *                    for the three-way rule the invisible threshold d_ep = -r of every
+ *                    plane (and, with k_sigma > 3, the visible threshold d_ep = +r too)
  *   margin_rect[i]   distance (pixels) of the rectangle bounds to the nearest tile edge
  * Modes: NONE labels all visible; HARD labels invisible iff d_ep < 0 (centre test);
  * RARA is the paper's three-way rule; RARA_ALL uses the three-way rule but ray-traces
@@ -214,21 +215,29 @@ int orc_preprocess(int64_t n, const double *means, const double *log_scales, con
             mg = mc;
         } else {
             int behind = 0, front = 1;
+            double m_inv = INFINITY;  /* distance to the invisible thresholds d_ep,k = -r */
             mc = INFINITY;
             for (int k = 0; k < nplanes; ++k) {
                 double dk = dot3(&plane4[4 * k], mu) + plane4[4 * k + 3];
                 behind = behind || dk < -r;
                 front = front && dk > r;
                 mc = fmin(mc, fmin(fabs(dk - r), fabs(dk + r)));
+                m_inv = fmin(m_inv, fabs(dk + r));
             }
             if (behind) lab = ORC_INVISIBLE;
             else if (front) lab = ORC_VISIBLE;
             else lab = ORC_CUTOFF;
             if (mode == ORC_MODE_RARA_ALL && lab != ORC_INVISIBLE) lab = ORC_CUTOFF;
-            /* With k_sigma <= 3 the traced ellipsoid lies inside the radius-r sphere, so at
-             * d_ep = +r every chord is visible (w = 1) and at d_ep = -r none is (w = 0): the
-             * labels change there but the image does not jump. A larger ellipsoid pokes out. */
-            if (k_sigma > 3.0) mg = mc;
+            /* Where the image jumps. At d_ep = +r (k_sigma <= 3) the traced ellipsoid lies
+             * inside the radius-r sphere, so every chord is already wholly visible (w = 1)
+             * when the label turns visible: no jump. At d_ep = -r it is not so: a ray that
+             * hits the ellipsoid has w = 0 just before the Gaussian turns invisible, but the
+             * pixels of the q <= 9 footprint whose rays miss the ellipsoid (the footprint is
+             * the EWA approximation widened by the 0.3 px^2 dilation, so it reaches past the
+             * ellipsoid's silhouette) keep w = 1 up to the threshold and drop to nothing
+             * after it. With k_sigma > 3 the ellipsoid pokes out of the sphere and +r jumps
+             * as well. */
+            mg = k_sigma > 3.0 ? mc : m_inv;
         }
         label[i] = (uint8_t)lab;
         margin_class[i] = mc;
@@ -639,6 +648,17 @@ int orc_render(int64_t n, const double *means, const double *log_scales, const d
         qsort(all, (size_t)nall, sizeof(cand_t), cmp_cand);
     }
 
+    /* Gaussians labelled invisible within tol_g of a threshold where the image jumps: a
+     * float32 renderer may label them cutoff and blend them, so every pixel of their
+     * q <= 9 footprint is flagged (they are in no tile list, so the walk below never sees
+     * them). Their projection fields are filled by the preprocess. */
+    int64_t *haz = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t nhaz = 0;
+    if (!haz) { free(all); return -1; }
+    for (int64_t i = 0; i < n; ++i)
+        if (label[i] == ORC_INVISIBLE && margin_gauss[i] <= tol_g && conic[3 * i] > 0.0 && conic[3 * i + 2] > 0.0)
+            haz[nhaz++] = i;
+
     if (row_begin < 0) row_begin = 0;
     if (row_end > H) row_end = H;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
@@ -662,6 +682,13 @@ int orc_render(int64_t n, const double *means, const double *log_scales, const d
             double T = 1.0, C[3] = {0.0, 0.0, 0.0};
             int32_t last = 0;
             unsigned ev = 0;
+            for (int64_t h = 0; h < nhaz; ++h) {
+                const int64_t i = haz[h];
+                double dx = pxc - mean2d[2 * i], dy = pyc - mean2d[2 * i + 1];
+                double q = conic[3 * i] * dx * dx + 2.0 * conic[3 * i + 1] * dx * dy + conic[3 * i + 2] * dy * dy;
+                double tq = tol_q * 9.0 + 6.0 * tol_pos * sqrt(fabs(conic[3 * i]) + fabs(conic[3 * i + 2]));
+                if (q <= 9.0 + tq) ev |= EV_GAUSS;
+            }
             float prev_depth = 0.0f;
             int have_prev = 0;
             for (int64_t k = start; k < end; ++k) {
@@ -711,6 +738,7 @@ int orc_render(int64_t n, const double *means, const double *log_scales, const d
             events[p] = (uint8_t)ev;
         }
     }
+    free(haz);
     free(all);
     return 0;
 }

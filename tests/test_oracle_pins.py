@@ -694,3 +694,56 @@ def test_every_blending_pixel_is_in_a_listing_tile(orc):
             assert ((y // 16) * pre["tiles_x"] + x // 16, int(i)) in listed
             checked += 1
     assert checked > 1000
+
+
+# ------------------------------------------------------------------------------------
+# The class thresholds where the image jumps (Section 3.2, Algorithm 1 step 1, Eq. 11)
+# ------------------------------------------------------------------------------------
+
+def _threshold_frames(orc, side, eps, mode=scenes.MODE_RARA):
+    """One isotropic Gaussian (sigma 0.01 at depth 2 on the axis camera: 0.32 px, so its
+    dilated q <= 9 footprint reaches 1.9 px while the 3-sigma ellipsoid's silhouette is
+    0.96 px) and the plane x = -d whose offset puts the centre at d_ep = side * r + eps."""
+    mu = _at_pixel(32, 32, 2.0)
+    sc = make_scene([mu], [[0.01] * 3], opacity=[0.9], rgb=[[1.0, 1.0, 1.0]])
+    r = 3.0 * math.exp(float(np.float32(math.log(0.01))))
+    d = float(np.float32(side * r + eps - np.float32(mu[0])))
+    pre, _, out = _render(orc, sc, plane([1, 0, 0], d, mode))
+    return pre, out, float(np.float32(mu[0])) + d - side * r
+
+
+@pytest.mark.parametrize("mode", [scenes.MODE_RARA, scenes.MODE_RARA_ALL])
+def test_invisible_threshold_is_an_image_jump_and_flagged(orc, mode):
+    # Pixel (33, 32) is 1 px from the projected centre: inside the footprint (q = 2.5,
+    # alpha0 = 0.26) but its ray misses the ellipsoid, so w = 1 while the Gaussian is
+    # cutoff and 0 once it turns invisible at d_ep = -r.
+    pre_c, out_c, off_c = _threshold_frames(orc, -1.0, +1e-7, mode)
+    pre_i, out_i, off_i = _threshold_frames(orc, -1.0, -1e-7, mode)
+    assert 0 < off_c < 1e-6 and -1e-6 < off_i < 0
+    assert pre_c["label"][0] == orc.CUTOFF and pre_i["label"][0] == orc.INVISIBLE
+    assert out_c["image"][0, 32, 33] > 0.2          # blended with w = 1 just inside
+    assert out_i["image"][0, 32, 33] == 0.0         # background just outside
+    assert out_c["image"][0, 32, 32] < 1e-3         # the central ray hits: w ~ 0 already
+    # the oracle marks the jump: the Gaussian's margin and the footprint's pixels, on both
+    # sides (as a candidate when cutoff, as a hazard when invisible)
+    for pre, out in ((pre_c, out_c), (pre_i, out_i)):
+        assert pre["margin_gauss"][0] <= 1e-6
+        assert out["events"][32, 33] & orc.EV_GAUSS
+        assert out["events"][32, 31] & orc.EV_GAUSS
+        assert out["events"][10, 10] == 0           # far outside the footprint
+    # away from the threshold nothing is flagged
+    pre_f, out_f, _ = _threshold_frames(orc, -1.0, -1e-3, mode)
+    assert pre_f["margin_gauss"][0] > 1e-4 and not (out_f["events"][32, 33] & orc.EV_GAUSS)
+
+
+def test_visible_threshold_is_continuous(orc):
+    # At d_ep = +r (k_sigma = 3) the traced ellipsoid lies inside the radius-r sphere: every
+    # chord is visible on both sides of the threshold, so the image does not jump there and
+    # the oracle does not flag it.
+    pre_c, out_c, _ = _threshold_frames(orc, +1.0, -1e-7)
+    pre_v, out_v, _ = _threshold_frames(orc, +1.0, +1e-7)
+    assert pre_c["label"][0] == orc.CUTOFF and pre_v["label"][0] == orc.VISIBLE
+    assert np.abs(out_c["image"] - out_v["image"]).max() < 1e-5
+    assert out_v["image"][0, 32, 32] > 0.5
+    assert pre_c["margin_gauss"][0] > 1e-4 and pre_v["margin_gauss"][0] > 1e-4
+    assert not (out_c["events"] & orc.EV_GAUSS).any()
