@@ -39,14 +39,25 @@ sys.path.insert(0, ROOT)
 METRIC = "clipped frames/sec at 1080p/1M Gaussians + p50/p99 latency, batched vs plain, same GB300"
 UNIT = "frames/s"
 
-# Algorithmic FP32 work of the render kernel per unit (see the design notes):
+# Algorithmic FP32 work of the render per unit, the method's own arithmetic (the units the
+# roofline is stated in): an evaluated (pixel, Gaussian) pair, alpha0 = delta exp(-q/2) >= 1/255
+# inside the q <= 9 support (Eq. 2, Eq. 10, Algorithm 1 step 3: offset, q, alpha, clamp,
+# transmittance and colour update) costs 15 FLOP + 1 exp; a cutoff pair adds the ray-traced
+# decay weight (Eq. 4-8, Eq. 11: chord, front test, plane split) for 30 FLOP + sqrt + rcp.
+FLOP_EVAL, FLOP_CUT = 15, 30
+# The kernel's own work per unit, counted from its instructions (context: it includes the
+# culling the method does not define):
 #   rectangle test   min of q over a warp's 8x4 pixel box (4 edges)  36 FLOP (one per warp and entry)
 #   walked pair      dx, dy and the conic quadratic form q            9 FLOP
-#   blending pair    alpha0 = delta exp(-q/2) >= 1/255 with q <= 9:
-#                    alpha0, clamp, T update, RGB                     12 FLOP + 1 MUFU (ex2)
-#   cutoff pair      ray-traced decay weight (Eq. 4-8, 11)           60 FLOP + 3 MUFU
-FLOP_TEST, FLOP_WALKED, FLOP_EVAL, FLOP_CUT = 36, 9, 12, 60
-SMS, FP32_LANES = 152, 128  # GB300: 152 SMs x 128 FP32 lanes, FMA = 2 FLOP
+#   blending pair    alpha0, clamp, T update, RGB                     12 FLOP + 1 MUFU (ex2)
+#   cutoff pair      decay weight as the kernel evaluates it          60 FLOP + 3 MUFU
+KFLOP_TEST, KFLOP_WALKED, KFLOP_EVAL, KFLOP_CUT = 36, 9, 12, 60
+FP32_LANES = 128  # FP32 lanes per SM on GB300 (an FMA counts 2 FLOP)
+
+
+def sm_count():
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "render_fwd_general_1080p.txt")
 RENDER_SRCS = [os.path.join(ROOT, "paper_2506_20202_gb300", "csrc", f) for f in ("render.cu", "render_common.cuh")]
@@ -66,16 +77,21 @@ def parse_args():
     ap.add_argument("--plain-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tuning", default="", help="split thresholds 'a,b' instead of autotuning")
-    ap.add_argument("--serve-s", type=float, default=4.0, help="serving window (0: skip)")
+    ap.add_argument("--serve-s", type=float, default=30.0, help="serving window (0: skip)")
+    ap.add_argument("--serve-fast-s", type=float, default=2.0, help="window of the 10x-rate serving leg")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-3m", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--train-steps", type=int, default=6, help="forward+backward steps of the multi-layer "
                     "differentiation workload (0: skip)")
     ap.add_argument("--train-per-shell", type=int, default=700_000)
+    ap.add_argument("--train-multi", action="store_true", help="with several ranks, run the differentiation "
+                    "leg data-parallel over all of them (views sharded, gradients all-reduced over NCCL)")
     ap.add_argument("--hair-steps", type=int, default=20, help="frames of the hair-strand workload per path "
                     "(0: skip)")
     ap.add_argument("--train-views", type=int, default=64)
     ap.add_argument("--volume-steps", type=int, default=20, help="batches of the clip-volume sweep (0: skip)")
+    ap.add_argument("--mode-steps", type=int, default=20, help="batches per clipping mode of the Table 1 "
+                    "comparison on the sweep and hair workloads (0: skip)")
     return ap.parse_args()
 
 
@@ -153,6 +169,29 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
+def issue_slots_for_current_kernel():
+    """The render kernel's issue-slot use from the committed ncu summary (issue active % of
+    its active cycles), if it was taken on the current render sources; otherwise None."""
+    try:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    m = re.search(r"issue active %\s+([0-9.]+)", text)
+    if not m or not _profile_matches_sources(text):
+        return None
+    return {"issue_active_frac": float(m.group(1)) / 100.0, "source": os.path.relpath(TRAFFIC_FILE, ROOT),
+            "note": "the kernel issues on this share of its SMs' active cycles (ncu, 4-view capture)"}
+
+
+def _profile_matches_sources(text):
+    for path in RENDER_SRCS:
+        key = os.path.basename(path).replace(".", "_") + "_sha256"
+        m = re.search(key + r":\s*([0-9a-f]{64})", text)
+        if not m or m.group(1) != hashlib.sha256(open(path, "rb").read()).hexdigest():
+            return False
+    return True
+
+
 def traffic_for_current_kernel():
     """DRAM bytes of the benchmark's render launch from the committed ncu summary, if it was
     taken on the current render sources (matched by hash); otherwise None."""
@@ -222,8 +261,10 @@ def run_reference(args):
     import oracle as orc
     cache = {}
     total_steps = args.warmup + args.steps
+    step_t = []
     for s in range(total_steps):
         pid = s % args.sweep
+        t_step = time.perf_counter()
         if pid not in cache:
             t0 = time.perf_counter()
             pre = orc.preprocess(scene, cam, planes[pid])
@@ -236,14 +277,19 @@ def run_reference(args):
         orc.render(scene, pre, cam, planes[pid], (0.0, 0.0, 0.0), kvr, threads=threads, rows=(y0, y0 + band_rows))
         if s >= args.warmup:
             band_t.append(time.perf_counter() - t0)
+            step_t.append(time.perf_counter() - t_step)
     frame_s = statistics.mean(pre_t.values()) + statistics.mean(band_t) * cam.height / band_rows
     value = 1.0 / frame_s
+    step_ms = 1e3 * (sum(step_t) / len(step_t))
     sample = (f"each step renders {band_rows} rows (one eighth) of one sweep frame (plane cycling over {args.sweep}); the full "
               f"per-plane preprocess + key sort is timed once per plane; frame time = mean(preprocess+sort) + "
               f"mean(band) x {cam.height}/{band_rows}")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": frame_s * args.sweep * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "frame_ms_extrapolated": frame_s * 1e3,
+        "step_note": "ms_per_step is the measured mean of a timed step (one band, plus the plane's preprocess and "
+                     "key sort on the step that first meets it); value extrapolates whole frames from those parts",
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
@@ -331,7 +377,8 @@ def run_ours(args):
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("gloo")
+        # host-side timing reductions over gloo; gradient all-reduces of CUDA tensors over NCCL
+        dist.init_process_group("cpu:gloo,cuda:nccl")
     torch.cuda.set_device(local)
     build.build()
 
@@ -402,12 +449,14 @@ def run_ours(args):
              torch.empty((H, W), dtype=torch.int32, device="cuda")) for _ in planes]
     views = [rara.View(0, cam, pl, o[0], o[1], o[2], bg) for pl, o in zip(planes, outs)]
     if args.tuning:
-        best, tune_ms = tuple(int(x) for x in args.tuning.split(",")), {}
-        rara.rara_ctx_set_tuning(bctx, *best)
+        best, tune_ms = autotune.parse(args.tuning), {}
+        autotune.apply(bctx, best)
     else:
         best, tune_ms = autotune.autotune(bctx, [gs], views, stream, reps=3)
     # stage times and work counts of one exact batched render (for the roofline)
+    rara.rara_ctx_count_work(bctx, True)
     rara.rara_render_batch(bctx, [gs], views, stream)
+    rara.rara_ctx_count_work(bctx, False)
     stage = rara.rara_ctx_stage_ms(bctx)
     kms = rara.rara_ctx_kernel_ms(bctx)
     binfo = rara.rara_frame_info_get(bctx, 0)
@@ -451,20 +500,41 @@ def run_ours(args):
                        "a request's latency is its batch's"}
     clocks = sampler.summary()
     peaks, peak_kind = measured_peaks()
-    batched["stage_hbm"] = stage_hbm(kms, vinfo, scene, W, H, peaks["hbm_gbs"])
 
-    # roofline of the dominant kernel: the render launch of the batch
-    flop = (FLOP_TEST * binfo["n_tested"] + FLOP_WALKED * binfo["n_walked"] + FLOP_EVAL * binfo["n_evaluated"]
-            + FLOP_CUT * binfo["n_cut_evaluated"])
-    achieved = flop / (stage[2] * 1e-3) / 1e12
+    # roofline of the dominant kernel: the render launch of the batch, timed by the events the
+    # captured graph records around it (the replays the timed region ran); units from the
+    # exact render of the same batch (the same work, counted on the device)
+    replay_kms, replay_render = [], []
+    for _ in range(10):
+        rara.rara_render_batch_graph(bctx, [gs], views, stream)
+        replay_render.append(rara.rara_ctx_stage_ms(bctx)[2])
+        replay_kms.append(rara.rara_ctx_kernel_ms(bctx))
+    t_render = statistics.mean(replay_render)
+    sms = sm_count()
+    flop = FLOP_EVAL * binfo["n_evaluated"] + FLOP_CUT * binfo["n_cut_evaluated"]
+    kflop = (KFLOP_TEST * binfo["n_tested"] + KFLOP_WALKED * binfo["n_walked"] + KFLOP_EVAL * binfo["n_evaluated"]
+             + KFLOP_CUT * binfo["n_cut_evaluated"])
+    achieved = flop / (t_render * 1e-3) / 1e12
     sm_max = float(clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
-    peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    peak = sms * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    issue = issue_slots_for_current_kernel()
     roofline = {"bound": "alu", "kernel": "k_render (one launch for the 16-view batch)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for_current_kernel(),
-                "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES} lanes x 2 FLOP x {sm_max:.0f} MHz "
-                              f"(recipe unit counts, max SM clock)",
+                "launch_ms": t_render, "launch_ms_exact_render": stage[2],
+                "flop_per_launch": flop,
+                "units": "15 FLOP per evaluated (pixel, Gaussian) pair + 30 per cutoff pair (the method's arithmetic)",
+                "peak_basis": f"FP32 FMA: {sms} SMs (device) x {FP32_LANES} lanes x 2 FLOP x {sm_max:.0f} MHz "
+                              f"(max SM clock; of measured clocks)",
+                "kernel_work": {"flop_per_launch": kflop, "achieved": kflop / (t_render * 1e-3) / 1e12,
+                                "frac": kflop / (t_render * 1e-3) / 1e12 / peak,
+                                "note": "the kernel's own arithmetic incl. its culling tests (36/9/12/60 FLOP per "
+                                        "test/walked/blending/cutoff unit)"},
+                "issue_slots": issue,
                 "per_launch_units": {"tested": binfo["n_tested"], "walked": binfo["n_walked"],
                                      "evaluated": binfo["n_evaluated"], "cut_evaluated": binfo["n_cut_evaluated"]}}
+    kms = [statistics.mean(k[j] for k in replay_kms) for j in range(6)]
+    batched["stage_hbm"] = stage_hbm(kms, vinfo, scene, W, H, peaks["hbm_gbs"])
+    batched["stage_hbm_note"] = "stage times: mean of 10 graph replays (events recorded by the graph)"
     n = scene.n
     pre_bytes = n * (12 + 12 + 16 + 4 + 4 * scene.sh.shape[0]) + \
         statistics.mean(c["n_rendered"] * (48 + 8 + 8) + n * 9 + c["n_cutoff"] * 64 for c in counts)
@@ -493,7 +563,7 @@ def run_ours(args):
         h2d = sum(t.numel() * 4 for t in host.values())
         d2h = nplanes * 3 * H * W * 4
         ectx = rara.rara_ctx_create(0)
-        rara.rara_ctx_set_tuning(ectx, *best)
+        autotune.apply(ectx, best)
         up_stream, down_stream = torch.cuda.Stream(), torch.cuda.Stream()
         ev_up = [torch.cuda.Event() for _ in range(2)]
         ev_ren = [torch.cuda.Event() for _ in range(2)]
@@ -558,12 +628,19 @@ def run_ours(args):
                                                        for c in counts],
                          "pairs_mean": statistics.mean(c["n_pairs"] for c in counts)},
     }
+    if rank == 0 and world == 1 and args.mode_steps > 0:
+        line["paths"]["modes"] = {"general_sweep": run_modes(args, gs, cam, planes, best),
+                                  "paper_table1_rtx4090": PAPER_TABLE1}
     if rank == 0 and world == 1 and args.volume_steps > 0:
         line["volume"] = run_volume(args, gs, cam, planes)
     if rank == 0 and world == 1 and args.hair_steps > 0:
         line["hair"] = run_hair(args)
-    if rank == 0 and world == 1 and args.train_steps > 0:
-        line["training"] = run_training(args)
+        if "modes" in line["hair"] and "modes" in line["paths"]:
+            line["paths"]["modes"]["hair"] = line["hair"]["modes"]
+    if args.train_steps > 0 and (world == 1 or args.train_multi):
+        tr = run_training(args, rank, world)
+        if rank == 0:
+            line["training"] = tr
     if rank == 0 and world == 1 and args.serve_s > 0:
         line["serving"] = run_serving(args, gs, scene)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -587,44 +664,47 @@ def run_ours(args):
 FLOP_BWD_WALKED, FLOP_BWD_EVAL, FLOP_BWD_CUT = 10, 50, 135
 
 
-def run_training(args):
+def run_training(args, rank=0, world=1):
     """Multi-layer differentiation workload: 3 nested shells (3 x 700k Gaussians, SH degree
     2), 64 views at 512^2 / 1024^2 / 1920x1080 with 64 planes cutting the shells. One step =
     batched forward (CUDA-graph replay, autotuned) + L2 loss to target renders of a perturbed
-    copy of the scene + rara_render_backward + an Adam update of the Gaussians."""
+    copy of the scene + rara_render_backward + an Adam update of the Gaussians, as a
+    data-parallel step (dp.data_parallel_gradients): with several ranks each renders and
+    differentiates every world-th view and one all-reduce sums the parameter gradients."""
     import torch
 
-    from paper_2506_20202_gb300 import autotune, rara, scenes
+    from paper_2506_20202_gb300 import autotune, dp, rara, scenes
     t_setup = time.perf_counter()
     scene, target, vp = scenes.shells_training_workload(args.train_per_shell, args.train_views, seed=3)
     gs = rara.GaussianTensors.from_scene(scene)
     tg = rara.GaussianTensors.from_scene(target)
     stream = torch.cuda.Stream()
     ctx = rara.rara_ctx_create(0)
+    mine = dp.shard_views(len(vp), rank, world)
 
-    def make_views():
+    def make_views(idx):
         out = []
-        for cam, pl in vp:
+        for k in idx:
+            cam, pl = vp[k]
             H, W = cam.height, cam.width
             out.append(rara.View(0, cam, pl, torch.empty((3, H, W), device="cuda"),
                                  torch.empty((H, W), device="cuda"),
                                  torch.empty((H, W), dtype=torch.int32, device="cuda"), (0.0, 0.0, 0.0)))
         return out
 
-    tviews = make_views()
+    tviews = make_views(mine)
     rara.rara_render_batch(ctx, [tg], tviews, stream)
     rara.rara_ctx_sync(ctx, stream)
-    targets = [v.image for v in tviews]
+    targets = {k: v.image for k, v in zip(mine, tviews)}
     del tg
-    views = make_views()
+    local = dp.GpuViews(ctx, gs, vp, targets, stream)
+    views = local._views(mine)[0]
     if args.tuning:
-        best, tune_ms = tuple(int(x) for x in args.tuning.split(",")), {}
-        rara.rara_ctx_set_tuning(ctx, *best)
+        best, tune_ms = autotune.parse(args.tuning), {}
+        autotune.apply(ctx, best)
     else:
         best, tune_ms = autotune.autotune(ctx, [gs], views, stream, reps=2)
-    grads = gs.empty_like()
-    pg = torch.empty((len(views), 4), device="cuda")
-    dimgs = [torch.empty_like(v.image) for v in views]
+    grads = local.grads
     # Adam on the Gaussians' own storage (nn.Parameter shares it), gradients from the backward
     params = [torch.nn.Parameter(t) for t in (gs.means, gs.log_scales, gs.quats, gs.opacity_logits, gs.sh)]
     for p_, g_ in zip(params, (grads.means, grads.log_scales, grads.quats, grads.opacity_logits, grads.sh)):
@@ -633,27 +713,19 @@ def run_training(args):
     losses = []
 
     def step(evs):
+        cur = torch.cuda.current_stream()
         evs[0].record(stream)
-        rara.rara_render_batch_graph(ctx, [gs], views, stream)
-        evs[1].record(stream)
-        with torch.cuda.stream(stream):
-            loss = torch.zeros((), device="cuda")
-            for v, t, d in zip(views, targets, dimgs):
-                torch.sub(v.image, t, out=d)
-                loss += (d * d).mean()
-                d.mul_(2.0 / d.numel())
-        evs[2].record(stream)
-        rara.rara_render_backward(ctx, dimgs, [grads], pg, stream)
-        evs[3].record(stream)
-        with torch.cuda.stream(stream):
-            opt.step()
-        evs[4].record(stream)
-        return loss
+        res = dp.data_parallel_gradients(lambda idx: local(idx, evs[1:4]), len(vp), rank, world)
+        opt.step()
+        evs[4].record(cur)
+        return res.loss
 
     mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     # the forward's work counts (the backward's roofline units) from an exact render: graph
     # replays run the render without its counters
+    rara.rara_ctx_count_work(ctx, True)
     rara.rara_render_batch(ctx, [gs], views, stream)
+    rara.rara_ctx_count_work(ctx, False)
     info = rara.rara_frame_info_get(ctx, 0)
     for _ in range(2):
         step(mk())
@@ -665,36 +737,98 @@ def run_training(args):
     t0.record(stream)
     for k in range(args.train_steps):
         losses.append(step(evs[k]))
-    t1.record(stream)
-    stream.synchronize()
+    t1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
     rara.rara_ctx_sync(ctx, stream)
     total_ms = t0.elapsed_time(t1)
     bwd_ms = rara.rara_ctx_backward_ms(ctx)
     med = lambda a, b: statistics.median(e[a].elapsed_time(e[b]) for e in evs)
-    pixels = sum(cam.width * cam.height for cam, _ in vp)
+    pixels = sum(vp[k][0].width * vp[k][0].height for k in mine)
     flop = (FLOP_BWD_WALKED * info["n_walked"] + FLOP_BWD_EVAL * info["n_evaluated"]
             + FLOP_BWD_CUT * info["n_cut_evaluated"])
-    peak = SMS * FP32_LANES * 2 * 2070.0 * 1e6 / 1e12
+    peak = sm_count() * FP32_LANES * 2 * 2070.0 * 1e6 / 1e12
     achieved = flop / (bwd_ms[0] * 1e-3) / 1e12
     out = {"workload": f"3 nested shells x {args.train_per_shell} Gaussians (SH 2), {len(vp)} views "
                        f"(512^2 / 1024^2 / 1920x1080), 64 planes cutting the shells, L2 loss to renders of a "
-                       f"perturbed copy", "gaussians": scene.n, "views": len(vp), "pixels_per_step": pixels,
+                       f"perturbed copy", "gaussians": scene.n, "views": len(vp), "views_this_rank": len(mine),
+           "ranks": world, "pixels_per_step": pixels,
            "steps": args.train_steps, "ms_per_step": total_ms / args.train_steps,
-           "views_per_s": args.train_steps * len(vp) / (total_ms * 1e-3),
+           "views_per_s": args.train_steps * len(mine) / (total_ms * 1e-3),
            "stage_ms_median": {"forward_graph": med(0, 1), "loss_grad": med(1, 2), "backward": med(2, 3),
-                               "adam_update": med(3, 4)},
+                               "allreduce_and_adam": med(3, 4)},
            "backward_kernels_ms_last": {"render_backward": bwd_ms[0], "preprocess_backward": bwd_ms[1]},
            "tuning": list(best), "loss_per_step": [float(x) for x in losses],
            "render_backward_roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                                         "frac": achieved / peak,
                                         "units": {"walked": info["n_walked"], "evaluated": info["n_evaluated"],
                                                   "cut_evaluated": info["n_cut_evaluated"]}},
-           "pairs": sum(rara.rara_frame_info_get(ctx, v)["n_pairs"] for v in range(len(vp))),
-           "setup_s": setup_s}
+           "pairs": sum(rara.rara_frame_info_get(ctx, v)["n_pairs"] for v in range(len(views))),
+           "setup_s": setup_s,
+           "note": "a data-parallel step (views dealt round-robin over ranks, one all-reduce of the parameter "
+                   "gradients; at one rank the all-reduce is skipped)"}
     rara.rara_ctx_destroy(ctx)
-    del gs, grads, dimgs, targets, tviews, views
+    del gs, grads, targets, tviews, views, local
     torch.cuda.empty_cache()
     return out
+
+
+# The paper's render-efficiency comparison (Section 4.2, Table 1, RTX 4090, real captures at
+# an unstated resolution; context only): frames/s without clipping, with hard clipping and
+# with RaRa clipping over a plane sweep.
+PAPER_TABLE1 = {"360garden (~4M Gaussians)": {"original": 77.82, "hard": 81.49, "rara": 81.47},
+                "Hair (~3M Gaussians)": {"original": 128.02, "hard": 146.88, "rara": 145.46}}
+
+
+def time_modes(gs, views_for_mode, steps, tuning, stream):
+    """frames/s of one batched, graph-replayed batch per clipping mode (no clipping, hard
+    clipping, RaRa), each on its own context (the pair capacity depends on the mode)."""
+    import torch
+
+    from paper_2506_20202_gb300 import autotune, rara, scenes
+    out = {}
+    for name, mode in (("original", scenes.MODE_NONE), ("hard", scenes.MODE_HARD), ("rara", scenes.MODE_RARA)):
+        views = views_for_mode(mode)
+        ctx = rara.rara_ctx_create(0)
+        autotune.apply(ctx, tuning)
+        for _ in range(3):
+            rara.rara_render_batch_graph(ctx, [gs], views, stream)
+        rara.rara_ctx_sync(ctx, stream)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for _ in range(steps):
+            rara.rara_render_batch_graph(ctx, [gs], views, stream)
+        t1.record(stream)
+        stream.synchronize()
+        rara.rara_ctx_sync(ctx, stream)
+        render_ms = rara.rara_ctx_stage_ms(ctx)[2]
+        rara.rara_ctx_destroy(ctx)
+        out[name] = {"frames_per_s": steps * len(views) / (t0.elapsed_time(t1) / 1e3),
+                     "render_ms_last_batch": render_ms}
+    out["rara_over_hard"] = out["rara"]["frames_per_s"] / out["hard"]["frames_per_s"]
+    out["rara_over_original"] = out["rara"]["frames_per_s"] / out["original"]["frames_per_s"]
+    return out
+
+
+def run_modes(args, gs, cam, planes, tuning):
+    """Table 1's protocol on the general-scene sweep: the 16 sweep planes rendered without
+    clipping, with hard clipping and with RaRa, each as one graph-replayed batch."""
+    import torch
+
+    from paper_2506_20202_gb300 import rara, scenes
+    H, W = cam.height, cam.width
+    stream = torch.cuda.Stream()
+    outs = [(torch.empty((3, H, W), device="cuda"), torch.empty((H, W), device="cuda"),
+             torch.empty((H, W), dtype=torch.int32, device="cuda")) for _ in planes]
+
+    def views_for(mode):
+        return [rara.View(0, cam, scenes.Plane(p.n, p.d, p.k_sigma, mode), o[0], o[1], o[2]) for p, o in zip(planes, outs)]
+
+    res = time_modes(gs, views_for, args.mode_steps, tuning, stream)
+    del outs
+    torch.cuda.empty_cache()
+    res["workload"] = "general scene 1M SH3, 1920x1080, the 16-offset plane sweep as one batch per mode"
+    return res
 
 
 def run_volume(args, gs, cam, planes):
@@ -716,8 +850,8 @@ def run_volume(args, gs, cam, planes):
     views = [rara.View(0, cam, v, torch.empty((3, H, W), device="cuda"), torch.empty((H, W), device="cuda"),
                        torch.empty((H, W), dtype=torch.int32, device="cuda"), (0.0, 0.0, 0.0)) for v in vols]
     if args.tuning:
-        best = tuple(int(x) for x in args.tuning.split(","))
-        rara.rara_ctx_set_tuning(ctx, *best)
+        best = autotune.parse(args.tuning)
+        autotune.apply(ctx, best)
     else:
         best, _ = autotune.autotune(ctx, [gs], views, stream, reps=2)
     rara.rara_render_batch(ctx, [gs], views, stream)
@@ -810,8 +944,8 @@ def run_hair(args):
         views.append(rara.View(0, c, pl, torch.empty((3, H, W), device="cuda"), torch.empty((H, W), device="cuda"),
                                torch.empty((H, W), dtype=torch.int32, device="cuda"), (0.0, 0.0, 0.0)))
     if args.tuning:
-        best = tuple(int(x) for x in args.tuning.split(","))
-        rara.rara_ctx_set_tuning(bctx, *best)
+        best = autotune.parse(args.tuning)
+        autotune.apply(bctx, best)
     else:
         best, _ = autotune.autotune(bctx, [gs], views, stream, reps=2)
     rara.rara_render_batch(bctx, [gs], views, stream)
@@ -835,6 +969,12 @@ def run_hair(args):
                             "views_per_batch": 16, "tuning": list(best),
                             "stage_ms_exact_batch": {"preprocess": stage[0], "bin": stage[1], "render": stage[2]}}
     rara.rara_ctx_destroy(bctx)
+    if args.mode_steps > 0:
+        def views_for(mode):
+            return [rara.View(0, v.camera, scenes.Plane(pl.n, pl.d, pl.k_sigma, mode), v.image, v.final_T, v.n_contrib)
+                    for v in views]
+        out["modes"] = time_modes(gs, views_for, args.mode_steps, best, stream)
+        out["modes"]["workload"] = "hair strands, the 16 orbit views as one batch per mode"
     del gs, views
     torch.cuda.empty_cache()
     return out
@@ -843,7 +983,9 @@ def run_hair(args):
 def run_serving(args, gs_1m, scene_1m):
     """Continuous-batching server vs the plain one-request-per-launch path on the same
     seeded Poisson arrivals: resident scenes of 100k, 1M and 3M Gaussians, random scene,
-    camera, resolution (512^2, 1280x720, 1920x1080) and plane per request, 60 GB budget."""
+    camera, resolution (512^2, 1280x720, 1920x1080) and plane per request, 60 GB budget.
+    Both paths start warm: every scene x resolution rendered beforehand on their own
+    contexts (kernels loaded, buffers grown / reserved) and pinned image pools filled."""
     import torch
 
     from paper_2506_20202_gb300 import rara, scenes, serve
@@ -853,32 +995,31 @@ def run_serving(args, gs_1m, scene_1m):
     names = list(sc)
     out = {"scenes": names, "budget_gb": 60, "rate_hz": args.serve_rate, "window_s": args.serve_s}
     reqs = serve.poisson_requests(names, serve.orbit_camera, args.serve_rate, args.serve_s, seed=21)
-    # warm both paths on a few requests (allocations, graph-free contexts)
-    warm = serve.poisson_requests(names, serve.orbit_camera, 200.0, 0.05, seed=22)
-    serve.serve_plain(sc, warm, keep_images=False)
     srv = serve.Server(sc, budget_bytes=60 << 30, slots=2, max_batch=64, keep_images=False)
     try:
-        srv.run(warm)
-        srv.results.clear()
+        srv.warm(serve.orbit_camera, seed=22)
+        out["reserved"] = srv.reserved
         res = srv.run(reqs)
         out["served"] = serve.summarize(res, args.serve_s)
         out["served"]["batches"] = srv.batches
         out["served"]["rejected"] = srv.rejected
-    finally:
-        srv.close()
-    torch.cuda.synchronize()
-    res_p = serve.serve_plain(sc, reqs, keep_images=False)
-    out["plain"] = serve.summarize(res_p, args.serve_s)
-    # the same arrivals 10x faster, where the GPU is the bottleneck
-    fast = serve.poisson_requests(names, serve.orbit_camera, args.serve_rate * 10, args.serve_s / 4, seed=23)
-    srv = serve.Server(sc, budget_bytes=60 << 30, slots=2, max_batch=64, keep_images=False)
-    try:
+        # the same arrivals 10x faster (a shorter window), where the GPU is the bottleneck
+        fast = serve.poisson_requests(names, serve.orbit_camera, args.serve_rate * 10, args.serve_fast_s, seed=23)
+        srv.batches = srv.rejected = 0
         res = srv.run(fast)
         out["served_10x_rate"] = serve.summarize(res)
         out["served_10x_rate"]["batches"] = srv.batches
     finally:
         srv.close()
-    out["plain_10x_rate"] = serve.summarize(serve.serve_plain(sc, fast, keep_images=False))
+    torch.cuda.synchronize()
+    ctx, pool = serve.warm_plain(sc, serve.orbit_camera, seed=22)
+    try:
+        out["plain"] = serve.summarize(serve.serve_plain(sc, reqs, keep_images=False, ctx=ctx, pool=pool),
+                                       args.serve_s)
+        out["plain_10x_rate"] = serve.summarize(serve.serve_plain(sc, fast, keep_images=False, ctx=ctx, pool=pool))
+    finally:
+        rara.rara_ctx_destroy(ctx)
+    out["p99_served_over_plain"] = out["served"]["p99_ms"] / out["plain"]["p99_ms"]
     return out
 
 

@@ -54,7 +54,12 @@ extern "C" {
 typedef enum rara_status {
     RARA_OK = 0,
     RARA_ERR_INVALID_ARG = 1, /* null pointer, n < 0, sh_degree outside [0,3], W or H <= 0,
-                                 non-finite camera/plane, unknown mode, call out of order */
+                                 non-finite camera/plane, unknown mode, call out of order;
+                                 and, detected on the device and reported at the next host
+                                 wait, a Gaussian with a non-finite mean, log-scale (a zero
+                                 scale is log-scale -inf), quaternion, opacity logit or SH
+                                 colour, or a zero quaternion (such Gaussians are not
+                                 rendered and the frame is invalid) */
     RARA_ERR_BUDGET = 2,      /* the context's device-memory budget cannot hold this frame */
     RARA_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
     RARA_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (results invalid) */
@@ -129,10 +134,20 @@ typedef struct rara_view {
 typedef struct rara_ctx rara_ctx;
 
 /* Create a context on the current CUDA device. budget_bytes caps the device scratch the
- * context may hold (0 = no cap). tile_w x tile_h is the screen tile (16 x 16; the render
- * kernel uses one 256-thread block per tile, so tile_w * tile_h must be 256).
- * Returns RARA_ERR_INVALID_ARG for other tile shapes. */
+ * context may hold (0 = no cap). tile_w x tile_h is the screen tile the binning and the
+ * render use: 16 x 16, 32 x 8, 8 x 32 (256 pixels), 8 x 8 (64) or 32 x 16, 16 x 32 (512);
+ * RARA_ERR_INVALID_ARG for other shapes. Images do not depend on the tile (a tile lists a
+ * Gaussian wherever one of its pixels can blend it); n_contrib, a position in the pixel's
+ * tile list, does. The blend batch depth starts at 256 (rara_ctx_set_tiling). */
 int rara_ctx_create(size_t budget_bytes, int32_t tile_w, int32_t tile_h, rara_ctx **out);
+
+/* Tile shape (as for rara_ctx_create) and blend batch depth (128, 256 or 512 list entries
+ * staged in shared memory per render batch) of the context's next frames and batches; the
+ * autotuner's knobs (the paper renders 16 x 16 tiles; the batch depth is this build's). The
+ * current frame's state is dropped when the tile changes, and a captured graph is
+ * recaptured on the next rara_render_batch_graph. RARA_ERR_INVALID_ARG for unsupported
+ * values. */
+int rara_ctx_set_tiling(rara_ctx *ctx, int32_t tile_w, int32_t tile_h, int32_t blend_depth);
 
 /* Free every device and pinned buffer the context owns. Waits for the device first.
  * NULL is accepted. */
@@ -144,19 +159,42 @@ const char *rara_last_error(const rara_ctx *ctx);
 /* Bytes of device scratch currently held by the context. */
 size_t rara_ctx_bytes(const rara_ctx *ctx);
 
+/* Allocate the context's scratch up front (serving: no allocation, and so no device-wide
+ * synchronisation of cudaFree / cudaMalloc, inside the request loop; the paper has no
+ * counterpart). Later frames and batches of up to `slots` (view, Gaussian) slots (the sum
+ * over the views of their scenes' sizes), `pairs` listed (Gaussian, tile) pairs, `views`
+ * views and `max_view_tiles` tiles in the largest view use these buffers without
+ * allocating; larger ones grow them as usual. Counts within the budget of
+ * rara_ctx_create, else RARA_ERR_BUDGET (what was reserved before the refusal stays
+ * held). Convex clip volumes and the backward allocate their own extra buffers on first
+ * use. Synchronous (it allocates). */
+int rara_ctx_reserve(rara_ctx *ctx, int64_t slots, int64_t pairs, int32_t views, int32_t max_view_tiles);
+
 /* Wait for `stream` and report a device-side wait failure of earlier work. */
 int rara_ctx_sync(rara_ctx *ctx, void *stream);
 
-/* Render scheduling knobs of the context. The render splits a tile whose list holds at
- * least 2^(split2_bits - 1) entries into 2 work items of 16x8 pixels with 2 lanes per
- * pixel, and one with at least 2^(split4_bits - 1) entries into 4 items of 16x4 pixels with 4
- * lanes per pixel (split4 wins when both apply); the lanes of a pixel combine consecutive
- * entries, which shortens the pixel's dependent chain. Values are clamped to [0, 33]
- * (0: always split, 33: never). Images do not depend on them beyond the float rounding
- * order of the compositing sums. Defaults: 11 and 12. */
+/* Render scheduling knobs of the context. The render gives a tile whose list holds at
+ * least 2^(split2_bits - 1) entries 2 lanes per pixel (a 16x16 tile becomes 2 work items of
+ * 16x8 pixels), and one with at least 2^(split4_bits - 1) entries 4 lanes per pixel (4 items
+ * of 16x4; split4 wins when both apply); the lanes of a pixel combine consecutive entries,
+ * which shortens the pixel's dependent chain. 8x8 tiles always take 4 lanes per pixel and
+ * 512-pixel tiles at most 2. Values are clamped to [0, 33] (0: always split, 33: never).
+ * Images do not depend on them beyond the float rounding order of the compositing sums.
+ * Defaults: 11 and 12. */
 int rara_ctx_set_tuning(rara_ctx *ctx, int32_t split2_bits, int32_t split4_bits);
 
-/* GPU time (ms) of the stages of the last frame or batch rendered without a graph:
+/* Test hook of the bounded device-side waits (the paper has no counterpart: its renderer
+ * has no multi-block scans). It applies to the next rara_preprocess / rara_render_batch on
+ * this context only, and only outside a graph capture: the compaction's look-back waits
+ * give up after spin_limit polls (0 = the default bound of about a second), and with
+ * orphan_first_partition != 0 its partition tickets start at 1, so partition 0 is never
+ * processed and every later partition's wait on its look-back word runs out. The kernel
+ * then records the time-out in the context's status word and returns; the next host wait
+ * (rara_bin, rara_render_batch, rara_ctx_sync) reports RARA_ERR_TIMEOUT and the frame is
+ * invalid. The context stays usable: the next call clears the status. */
+int rara_ctx_debug_waits(rara_ctx *ctx, int32_t spin_limit, int32_t orphan_first_partition);
+
+/* GPU time (ms) of the stages of the last frame or batch (a graph replay included):
  * out[0] preprocess + compaction, out[1] sorts, emission, ranges and render order, out[2]
  * render. Waits for that render to finish. */
 int rara_ctx_stage_ms(rara_ctx *ctx, float out[3]);
@@ -254,9 +292,15 @@ int rara_render_backward(rara_ctx *ctx, const float *const *dL_dimages, const ra
  * [1] the per-Gaussian preprocess backward. Waits for them to finish. */
 int rara_ctx_backward_ms(rara_ctx *ctx, float out[2]);
 
+/* Measurement: with on != 0 the renders of this context launched outside a CUDA graph
+ * (rara_render, rara_render_batch) count their work in the device counters that
+ * rara_frame_info_get reports (n_evaluated, n_walked, n_cut_evaluated, n_tested); the
+ * counting costs the render a few percent, so it is off by default. */
+int rara_ctx_count_work(rara_ctx *ctx, int32_t on);
+
 /* Counts of one view of the current frame or batch (view 0 for a single frame), valid after
  * rara_bin; the render counts are totals over all views of the last render launched outside
- * a CUDA graph (rara_render, rara_render_batch): graph replays render without the work
+ * a CUDA graph with counting on (rara_ctx_count_work): graph replays render without the work
  * counters and leave them 0. Waits for the context's last stream to read them. */
 typedef struct rara_frame_info {
     int64_t n;            /* Gaussians in the frame */
@@ -267,11 +311,14 @@ typedef struct rara_frame_info {
                              alpha0 = opacity exp(-q/2) >= 1/255 with q <= 9 */
     int32_t tiles_x, tiles_y;
     int64_t n_evaluated;  /* (pixel, Gaussian) pairs of the last rara_render with
-                             alpha0 >= 1/255 inside the q <= 9 support */
+                             alpha0 >= 1/255 inside the q <= 9 support (this and the next
+                             three: only with rara_ctx_count_work on, else 0) */
     int64_t n_walked;     /* (pixel, Gaussian) pairs whose q was computed, i.e. tile-list
                              entries visited by pixels still compositing */
     int64_t n_cut_evaluated; /* evaluated pairs that needed the ray-traced weight */
     int64_t n_tested;     /* (warp rectangle, Gaussian) culling tests of the last render */
+    int64_t n_pair_candidates; /* tiles of the view's rendered rectangles: the upper bound of
+                                  n_pairs the preprocess sizes the pair buffers by */
 } rara_frame_info;
 
 int rara_frame_info_get(rara_ctx *ctx, int32_t view, rara_frame_info *out);
@@ -301,8 +348,8 @@ int rara_frame_pairs(rara_ctx *ctx, int32_t view, uint64_t *keys, uint32_t *valu
  * frame loop or a host callback, where an allocation would block or is not allowed, or a
  * process whose device memory belongs to another allocator. The call allocates nothing
  * (no cudaMalloc, cudaFree, pinned or heap memory): every scratch buffer is carved from one
- * file-scope static __device__ array of about 18 MB, which each GPU that loads the library
- * holds until the process exits. The caller passes inputs and outputs as for
+ * file-scope static __device__ array of about 20.4 MB (19.5 MiB), which each GPU that loads
+ * the library holds until the process exits. The caller passes inputs and outputs as for
  * rara_render_frame, with the same layouts and results.
  *
  * Limits: n <= 65536 Gaussians, at most 2^19 (Gaussian, tile) pairs and 16384 tiles (for
@@ -315,8 +362,9 @@ int rara_frame_pairs(rara_ctx *ctx, int32_t view, uint64_t *keys, uint32_t *valu
  * device, with that device current); make that first call before any stream capture.
  * Every call on a device shares the one array and leaves the last call's contents in it:
  * calls that overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller. The call waits for the stream twice (to read the pair count).
- * It is not thread-safe. */
+ * serialised by the caller. The call waits for the stream three times (once to read the pair
+ * count, then twice more inside the binning, where the stream is already idle). It is not
+ * thread-safe. */
 int rara_render_frame_noalloc(const rara_gaussians *g, const rara_camera *cam, const rara_plane *plane,
                               const float bg[3], float *image, float *final_T, uint32_t *n_contrib,
                               void *stream);

@@ -1,11 +1,20 @@
-"""Autotuner for the render's work granularity.
+"""Autotuner for the render's tile shape, blend batch depth and work granularity.
 
-The render splits a tile with a long list into 2 or 4 work items with 2 or 4 lanes per
-pixel (rara_ctx_set_tuning). Where the split pays depends on the workload (list lengths,
-share of cutoff Gaussians, resolution mix), so the tuner times candidate thresholds on the
-actual batch, through the captured-graph path, and keeps the fastest. Images do not depend
-on the choice beyond float rounding order. Results can be cached in a JSON file keyed by
-the device name and the batch shape.
+Three knobs set how the render maps onto the GPU, none of which changes the image beyond
+float rounding order (with one lane per pixel, not even that):
+  - the screen tile (rara_ctx_set_tiling): 8x8, 16x16, 32x8, 8x32, 32x16 or 16x32 pixels;
+    smaller tiles give shorter lists and more (Gaussian, tile) pairs to sort;
+  - the blend batch depth: list entries staged in shared memory at a time (128, 256, 512);
+    deeper batches mean fewer block barriers and more staged entries a saturated pixel
+    never reads;
+  - the split thresholds (rara_ctx_set_tuning): a tile with a long list is split into work
+    items with 2 or 4 lanes per pixel.
+Where each pays depends on the workload (list lengths, share of cutoff Gaussians,
+resolution mix), so the tuner times candidates on the actual batch, through the captured-
+graph path, by coordinate descent: split thresholds (16x16 tiles, depth 256), then tile
+shapes, then depths, then the split thresholds again for the chosen tile and depth,
+keeping the fastest of each. Results can be cached in a JSON
+file keyed by the device name and the batch shape.
 """
 from __future__ import annotations
 
@@ -15,8 +24,28 @@ import statistics
 
 from . import rara
 
+TILES = [(16, 16), (32, 8), (8, 32), (8, 8), (32, 16), (16, 32)]
+DEPTHS = [256, 128, 512]
 # (split2_bits, split4_bits): a tile with >= 2^(bits-1) list entries is split
 CANDIDATES = [(33, 33), (13, 14), (12, 13), (11, 12), (10, 11), (11, 13), (10, 12), (9, 11)]
+DEFAULT = (16, 16, 256, 11, 12)
+
+
+def apply(ctx, setting):
+    """Set a (tile_w, tile_h, depth, split2_bits, split4_bits) setting on ctx."""
+    tw, th, depth, s2, s4 = setting
+    rara.rara_ctx_set_tiling(ctx, tw, th, depth)
+    rara.rara_ctx_set_tuning(ctx, s2, s4)
+
+
+def parse(text: str):
+    """A setting from 'split2,split4' (16x16 tiles, depth 256) or 'tw,th,depth,split2,split4'."""
+    v = tuple(int(x) for x in text.split(","))
+    if len(v) == 2:
+        return DEFAULT[:3] + v
+    if len(v) == 5:
+        return v
+    raise ValueError(f"tuning '{text}': give split2,split4 or tile_w,tile_h,depth,split2,split4")
 
 
 def _shape_key(scenes, views) -> str:
@@ -44,11 +73,13 @@ def time_batch(ctx, scenes, views, stream, reps: int = 5) -> float:
     return statistics.median(times)
 
 
-def autotune(ctx, scenes, views, stream=None, reps: int = 5, candidates=None, cache_path: str | None = None):
-    """Pick the fastest split thresholds for this batch and set them on ctx.
+def autotune(ctx, scenes, views, stream=None, reps: int = 5, tiles=None, depths=None, candidates=None,
+             cache_path: str | None = None):
+    """Pick the fastest (tile_w, tile_h, depth, split2_bits, split4_bits) for this batch and
+    set it on ctx.
 
-    Returns (best, {candidate: ms}). With cache_path, a stored choice for the same device
-    and batch shape is reused without timing, and a new choice is stored."""
+    Returns (best, {setting: ms}). With cache_path, a stored choice for the same device and
+    batch shape is reused without timing, and a new choice is stored."""
     import torch
     stream = stream or torch.cuda.current_stream()
     key = _shape_key(scenes, views)
@@ -58,14 +89,38 @@ def autotune(ctx, scenes, views, stream=None, reps: int = 5, candidates=None, ca
             cache = json.load(fh)
         if key in cache:
             best = tuple(cache[key]["best"])
-            rara.rara_ctx_set_tuning(ctx, *best)
+            apply(ctx, best)
             return best, {tuple(json.loads(k)): v for k, v in cache[key]["ms"].items()}
     results = {}
-    for cand in candidates or CANDIDATES:
-        rara.rara_ctx_set_tuning(ctx, *cand)
-        results[tuple(cand)] = time_batch(ctx, scenes, views, stream, reps)
-    best = min(results, key=results.get)
-    rara.rara_ctx_set_tuning(ctx, *best)
+
+    def trial(setting):
+        if setting not in results:
+            apply(ctx, setting)
+            results[setting] = time_batch(ctx, scenes, views, stream, reps)
+        return results[setting]
+
+    best = DEFAULT
+
+    def splits():
+        nonlocal best
+        for s2, s4 in candidates or CANDIDATES:
+            cand = best[:3] + (s2, s4)
+            if trial(cand) < trial(best):
+                best = cand
+
+    splits()                          # at the default tile, so tiles are compared at a good split
+    first = best
+    for tw, th in tiles or TILES:
+        cand = (tw, th) + best[2:]
+        if trial(cand) < trial(best):
+            best = cand
+    for depth in depths or DEPTHS:
+        cand = best[:2] + (depth,) + best[3:]
+        if trial(cand) < trial(best):
+            best = cand
+    if best[:3] != first[:3]:
+        splits()                      # the split that suits the chosen tile and depth
+    apply(ctx, best)
     if cache_path:
         cache[key] = {"best": list(best), "ms": {json.dumps(list(k)): v for k, v in results.items()}}
         tmp = cache_path + ".tmp"

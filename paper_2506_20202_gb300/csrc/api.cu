@@ -38,8 +38,12 @@ struct rara_ctx {
     int device = 0;
     char err[512] = {0};
     int64_t launches = 0;
-    int sm_count = 0, bpsm_render = 0, bpsm_sort = 0, bpsm_emit = 0, bpsm_compact = 0;
+    int sm_count = 0, bpsm_sort = 0, bpsm_emit = 0, bpsm_compact = 0;
+    int bpsm_render[3] = {0, 0, 0};     // render blocks per SM for batch depths 128, 256, 512
     int split2_bits = 11, split4_bits = 12;  // heavy-tile split thresholds (list length bit counts)
+    int tile_w = kTile, tile_h = kTile;      // screen tile of the next batch
+    int blend_depth = kBlock;                // list entries staged per render batch
+    bool count_work = false;                 // renders outside graphs fill the work counters
 
     // current batch
     int stage = 0;  // 0 empty, 1 preprocessed, 2 binned
@@ -91,6 +95,12 @@ struct rara_ctx {
     cudaEvent_t bev[3] = {nullptr, nullptr, nullptr};
     int bpsm_render_bwd = 0;
 
+    // test hook of the bounded waits (rara_ctx_debug_waits), applied to the next batch's
+    // compaction only: its look-back poll limit, and whether its first partition is left
+    // unprocessed (its look-back word is then never written)
+    int debug_spin_limit = 0;
+    bool debug_orphan = false;
+
     // stage timing of the last batch rendered outside a graph: preprocess start, bin start,
     // render start, render end, then inside the stages: after the depth sort, after the
     // emission, after the tile sort, after k_preprocess (before the compaction)
@@ -115,10 +125,25 @@ int check_cuda(rara_ctx *c, cudaError_t e, const char *what)
     return fail(c, RARA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Errors the kernels record in the device status word (read after a host wait).
+int device_status(rara_ctx *c, uint32_t status)
+{
+    if (status & kStatusLookbackTimeout)
+        return fail(c, RARA_ERR_TIMEOUT, "a bounded device-side wait gave up; the frame is invalid");
+    if (status & kStatusBadInput)
+        return fail(c, RARA_ERR_INVALID_ARG,
+                    "a Gaussian has a non-finite mean, log-scale, quaternion, opacity logit or colour, or a zero "
+                    "quaternion; the frame is invalid");
+    return RARA_OK;
+}
+
 // Grow-only device buffer within the context budget.
 int ensure(rara_ctx *c, DevBuf &b, size_t bytes, const char *name)
 {
     if (bytes <= b.cap) return RARA_OK;
+    // the static context's buffers are carved from a fixed array: never freed or replaced
+    if (!c->owns_host)
+        return fail(c, RARA_ERR_BUDGET, "buffer %s needs %zu bytes; the static scratch holds %zu", name, bytes, b.cap);
     size_t want = bytes + bytes / 4;  // headroom so small growth does not reallocate
     want = (want + 255) & ~(size_t)255;
     if (c->budget && c->held - b.cap + want > c->budget) {
@@ -155,9 +180,13 @@ void release(rara_ctx *c, DevBuf &b)
 
 bool finite(float v) { return isfinite(v) != 0; }
 
+// Stage events. Inside a graph capture they become event-record nodes of the graph, so a
+// replay records them too and the stage times of the last replay can be read.
 void mark(rara_ctx *c, int k, cudaStream_t s)
 {
-    if (c->ev[k] && !c->capturing) cudaEventRecord(c->ev[k], s);
+    if (!c->ev[k]) return;
+    if (c->capturing) cudaEventRecordWithFlags(c->ev[k], s, cudaEventRecordExternal);
+    else cudaEventRecord(c->ev[k], s);
 }
 
 int launched(rara_ctx *c, const char *what, int count = 1)
@@ -181,7 +210,7 @@ void occupancy_setup(rara_ctx *c)
         cudaGetLastError();
         c->sm_count = 1;
     }
-    c->bpsm_render = render_blocks_per_sm();
+    for (int k = 0; k < 3; ++k) c->bpsm_render[k] = render_blocks_per_sm(128 << k);
     c->bpsm_sort = sort_blocks_per_sm();
     c->bpsm_emit = emit_blocks_per_sm();
     c->bpsm_compact = compact_blocks_per_sm();
@@ -202,7 +231,7 @@ int check_gaussians(rara_ctx *c, const rara_gaussians *g)
 int check_view(rara_ctx *c, const rara_camera *cam, const rara_plane *pl)
 {
     if (!cam || !pl) return fail(c, RARA_ERR_INVALID_ARG, "null camera or plane");
-    if (cam->width <= 0 || cam->height <= 0 || cam->width > 65535 * kTile || cam->height > 65535 * kTile)
+    if (cam->width <= 0 || cam->height <= 0 || cam->width / c->tile_w >= 65535 || cam->height / c->tile_h >= 65535)
         return fail(c, RARA_ERR_INVALID_ARG, "image size %dx%d", cam->width, cam->height);
     for (int k = 0; k < 12; ++k)
         if (!finite(cam->world_to_cam[k])) return fail(c, RARA_ERR_INVALID_ARG, "non-finite camera pose");
@@ -221,7 +250,7 @@ int check_view(rara_ctx *c, const rara_camera *cam, const rara_plane *pl)
     return RARA_OK;
 }
 
-void fill_view(ViewDev &v, const rara_camera *cam, const rara_plane *pl)
+void fill_view(ViewDev &v, const rara_camera *cam, const rara_plane *pl, int tile_w, int tile_h)
 {
     for (int k = 0; k < 9; ++k) v.cam.R[k] = cam->world_to_cam[(k / 3) * 4 + (k % 3)];
     for (int k = 0; k < 3; ++k) v.cam.t[k] = cam->world_to_cam[k * 4 + 3];
@@ -236,8 +265,10 @@ void fill_view(ViewDev &v, const rara_camera *cam, const rara_plane *pl)
     v.plane.n_extra = pl->n_extra;
     for (int e = 0; e < RARA_MAX_EXTRA_PLANES; ++e)
         for (int k = 0; k < 4; ++k) v.plane.ex[e][k] = e < pl->n_extra ? pl->extra[e][k] : 0.0f;
-    v.tiles_x = (cam->width + kTile - 1) / kTile;
-    v.tiles_y = (cam->height + kTile - 1) / kTile;
+    v.tile_w = tile_w;
+    v.tile_h = tile_h;
+    v.tiles_x = (cam->width + tile_w - 1) / tile_w;
+    v.tiles_y = (cam->height + tile_h - 1) / tile_h;
 }
 
 // Take the next staging copy, waiting for the upload that last read it.
@@ -295,8 +326,8 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
     }
     uint64_t max_tiles = 1;
     for (int v = 0; v < nv; ++v) {
-        const uint64_t t = (uint64_t)((views[v].camera.width + kTile - 1) / kTile) *
-                           (uint64_t)((views[v].camera.height + kTile - 1) / kTile);
+        const uint64_t t = (uint64_t)((views[v].camera.width + c->tile_w - 1) / c->tile_w) *
+                           (uint64_t)((views[v].camera.height + c->tile_h - 1) / c->tile_h);
         if (t > max_tiles) max_tiles = t;
     }
     const int tile_bits = ceil_bits((uint32_t)(max_tiles < 0xffffffffull ? max_tiles : 0xffffffffull));
@@ -315,7 +346,7 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
         for (int v = 0; v < nv; ++v) {
             if (views[v].scene != si) continue;
             ViewDev &vd = c->h_views[k];
-            fill_view(vd, &views[v].camera, &views[v].plane);
+            fill_view(vd, &views[v].camera, &views[v].plane, c->tile_w, c->tile_h);
             vd.scene = si;
             vd.tile_base = (uint32_t)((uint64_t)k << tile_bits);
             vd.slot_base = (uint32_t)slots;
@@ -419,6 +450,12 @@ int batch_preprocess(rara_ctx *c, cudaStream_t s)
     ca.seg_base = (uint32_t *)c->seg_base.p;
     ca.lookback = (unsigned long long *)c->lookback_c.p;
     ca.counters = dc;
+    ca.spin_limit = c->debug_spin_limit > 0 ? c->debug_spin_limit : kSpinLimit;
+    if (c->debug_orphan && !c->capturing &&
+        (rc = check_cuda(c, cudaMemsetAsync(&dc->ticket[kTicketCompact], 1, 1, s), "debug ticket")))
+        return rc;  // tickets then start at 1: partition 0 is never taken
+    c->debug_spin_limit = 0;
+    c->debug_orphan = false;
     const uint32_t parts = (c->num_slots + 1023) / 1024;
     const uint32_t slots = (uint32_t)(c->sm_count * c->bpsm_compact);
     const int cgrid = (int)(parts < slots ? parts : slots);
@@ -511,7 +548,9 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
     launch_ranges((const uint32_t *)c->pkeys.p, (const uint32_t *)c->pkeys_b.p, dc, cap, c->num_tiles,
                   (int2 *)c->ranges.p, rgrid, s);
     if ((rc = launched(c, "ranges"))) return rc;
-    launch_tile_order((const int2 *)c->ranges.p, (int)c->num_tiles, c->split2_bits, c->split4_bits,
+    const int area = c->tile_w * c->tile_h;
+    const int area_log2 = area == 64 ? 0 : (area == 256 ? 2 : 3);
+    launch_tile_order((const int2 *)c->ranges.p, (int)c->num_tiles, c->split2_bits, c->split4_bits, area_log2,
                       (uint32_t *)c->items.p, dc, (const ViewDev *)c->views_d.p, c->tile_bits, c->sm_count * 2, s);
     return launched(c, "tile order", c->num_tiles > 0 ? 2 : 0);
 }
@@ -536,10 +575,13 @@ int batch_render(rara_ctx *c, cudaStream_t s)
     a.views = (const ViewDev *)c->views_d.p;
     a.num_views = c->num_views;
     a.counters = dc;
-    const long long slots = (long long)c->sm_count * c->bpsm_render;
+    const int di = c->blend_depth == 128 ? 0 : (c->blend_depth == 512 ? 2 : 1);
+    const long long slots = (long long)c->sm_count * c->bpsm_render[di];
     const long long items = 4ll * c->num_tiles;
     // graph captures run without the work counters (their replays are not read for them)
-    launch_render(a, (int)(items < slots ? items : slots), s, !c->capturing, c->multi);
+    if (launch_render(a, (int)(items < slots ? items : slots), s, c->count_work && !c->capturing, c->multi,
+                      c->blend_depth))
+        return fail(c, RARA_ERR_CUDA, "render: shared-memory size not accepted");
     rc = launched(c, "render launch", c->num_tiles > 0);
     mark(c, 3, s);
     return rc;
@@ -550,9 +592,9 @@ int bin_exact(rara_ctx *c, cudaStream_t s)
 {
     int rc;
     if ((rc = check_cuda(c, cudaStreamSynchronize(s), "cudaStreamSynchronize"))) return rc;
-    if (c->h_counters->status & kStatusLookbackTimeout) {
+    if ((rc = device_status(c, c->h_counters->status))) {
         c->stage = 0;
-        return fail(c, RARA_ERR_TIMEOUT, "a chained-scan wait exceeded its bound; the frame is invalid");
+        return rc;
     }
     const unsigned long long np = c->h_counters->n_pairs;
     if (np >= (1ull << 30)) return fail(c, RARA_ERR_BUDGET, "%llu pairs exceed 2^30", np);
@@ -593,10 +635,12 @@ int rara_ctx_create(size_t budget_bytes, int32_t tile_w, int32_t tile_h, rara_ct
 {
     if (!out) return RARA_ERR_INVALID_ARG;
     *out = nullptr;
-    if (tile_w != kTile || tile_h != kTile) return RARA_ERR_INVALID_ARG;
+    if (!tile_shape_ok(tile_w, tile_h)) return RARA_ERR_INVALID_ARG;
     rara_ctx *c = new (std::nothrow) rara_ctx();
     if (!c) return RARA_ERR_BUDGET;
     c->budget = budget_bytes;
+    c->tile_w = tile_w;
+    c->tile_h = tile_h;
     cudaGetDevice(&c->device);
     c->max_views = kMaxViews;
     c->max_scenes = kMaxScenes;
@@ -664,6 +708,80 @@ int rara_ctx_stage_ms(rara_ctx *c, float out[3])
     return RARA_OK;
 }
 
+int rara_ctx_reserve(rara_ctx *c, int64_t slots, int64_t pairs, int32_t views, int32_t max_view_tiles)
+{
+    if (!c) return RARA_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (!c->owns_host) return fail(c, RARA_ERR_INVALID_ARG, "the static context cannot reserve");
+    if (slots < 0 || slots >= ((int64_t)1 << 32) - 1 || pairs < 0 || pairs >= ((int64_t)1 << 30) || views < 1 ||
+        views > c->max_views || max_view_tiles < 1)
+        return fail(c, RARA_ERR_INVALID_ARG, "reserve(%lld slots, %lld pairs, %d views, %d tiles) out of range",
+                    (long long)slots, (long long)pairs, views, max_view_tiles);
+    const uint64_t tiles = (uint64_t)views << ceil_bits((uint32_t)max_view_tiles);
+    if (tiles >= ((uint64_t)1 << 28)) return fail(c, RARA_ERR_INVALID_ARG, "%llu tiles exceed 2^28",
+                                                   (unsigned long long)tiles);
+    const size_t nn = slots > 0 ? (size_t)slots : 1, pp = pairs > 0 ? (size_t)pairs : 1, nt = (size_t)tiles;
+    const size_t sb1 = sort_scratch_bytes((int64_t)nn, 6), sb2 = sort_scratch_bytes((int64_t)pp, 4);
+    int rc;
+    if ((rc = ensure(c, c->views_d, sizeof(ViewDev) * (size_t)views, "view table")) ||
+        (rc = ensure(c, c->scenes_d, sizeof(SceneDev) * (size_t)c->max_scenes, "scene table")) ||
+        (rc = ensure(c, c->view_counters_d, sizeof(ViewCounters) * (size_t)views, "view counters")) ||
+        (rc = ensure(c, c->labels, nn, "labels")) || (rc = ensure(c, c->tiles, nn * 4, "tiles")) ||
+        (rc = ensure(c, c->rect, nn * 8, "rect")) || (rc = ensure(c, c->rec, nn * sizeof(SplatRec), "records")) ||
+        (rc = ensure(c, c->cut, nn * sizeof(CutRec), "cutoff records")) ||
+        (rc = ensure(c, c->depth, nn * 4, "depth")) || (rc = ensure(c, c->ckeys, nn * 4, "depth keys")) ||
+        (rc = ensure(c, c->cvals, nn * 4, "depth values")) || (rc = ensure(c, c->ckeys_b, nn * 4, "depth keys B")) ||
+        (rc = ensure(c, c->cvals_b, nn * 4, "depth values B")) ||
+        (rc = ensure(c, c->lookback_c, (nn / 1024 + 2) * 8, "compaction scan words")) ||
+        (rc = ensure(c, c->lookback_e, (nn / kBlock + 2) * 8, "emission scan words")) ||
+        (rc = ensure(c, c->hist, kHistPasses * 256 * 4, "digit histograms")) ||
+        (rc = ensure(c, c->seg_base, sizeof(uint32_t) * (size_t)views, "view slot bases")) ||
+        (rc = ensure(c, c->ranges, nt * sizeof(int2), "ranges")) || (rc = ensure(c, c->items, nt * 16, "render items")) ||
+        (rc = ensure(c, c->pkeys, pp * 4, "pair keys")) || (rc = ensure(c, c->pvals, pp * 4, "pair values")) ||
+        (rc = ensure(c, c->pkeys_b, pp * 4, "pair keys B")) || (rc = ensure(c, c->pvals_b, pp * 4, "pair values B")) ||
+        (rc = ensure(c, c->sort_scratch, sb1 > sb2 ? sb1 : sb2, "sort scratch")))
+        return rc;
+    return RARA_OK;
+}
+
+int rara_ctx_debug_waits(rara_ctx *c, int32_t spin_limit, int32_t orphan_first_partition)
+{
+    if (!c) return RARA_ERR_INVALID_ARG;
+    if (spin_limit < 0) return fail(c, RARA_ERR_INVALID_ARG, "spin_limit %d < 0", spin_limit);
+    c->debug_spin_limit = spin_limit;
+    c->debug_orphan = orphan_first_partition != 0;
+    return RARA_OK;
+}
+
+int rara_ctx_count_work(rara_ctx *c, int32_t on)
+{
+    if (!c) return RARA_ERR_INVALID_ARG;
+    c->count_work = on != 0;
+    return RARA_OK;
+}
+
+int rara_ctx_set_tiling(rara_ctx *c, int32_t tile_w, int32_t tile_h, int32_t blend_depth)
+{
+    if (!c) return RARA_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (!tile_shape_ok(tile_w, tile_h))
+        return fail(c, RARA_ERR_INVALID_ARG, "tile %dx%d is not one of 8x8, 16x16, 32x8, 8x32, 32x16, 16x32", tile_w,
+                    tile_h);
+    if (!batch_depth_ok(blend_depth))
+        return fail(c, RARA_ERR_INVALID_ARG, "blend batch depth %d is not 128, 256 or 512", blend_depth);
+    if (!c->owns_host && (tile_w != kTile || tile_h != kTile || blend_depth != kBlock))
+        return fail(c, RARA_ERR_INVALID_ARG, "the static context keeps 16x16 tiles and 256-entry batches");
+    if (tile_w != c->tile_w || tile_h != c->tile_h) {
+        c->stage = 0;          // the current frame's tiles no longer apply
+        c->rendered = false;
+    }
+    c->tile_w = tile_w;
+    c->tile_h = tile_h;
+    c->blend_depth = blend_depth;
+    c->shape_len = 0;          // a captured graph holds the old tiling: recapture
+    return RARA_OK;
+}
+
 int rara_ctx_set_tuning(rara_ctx *c, int32_t split2_bits, int32_t split4_bits)
 {
     if (!c) return RARA_ERR_INVALID_ARG;
@@ -682,8 +800,7 @@ int rara_ctx_sync(rara_ctx *c, void *stream)
     if (rc) return rc;
     rc = check_cuda(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
     if (rc) return rc;
-    if (c->h_counters->status & kStatusLookbackTimeout)
-        return fail(c, RARA_ERR_TIMEOUT, "a chained-scan wait exceeded its bound; the frame is invalid");
+    if ((rc = device_status(c, c->h_counters->status))) return rc;
     if (c->h_counters->status & kStatusOverflow) {
         const unsigned long long np = c->h_counters->n_pairs;
         const unsigned long long want = np + np / 4 + 4096;
@@ -1060,6 +1177,7 @@ int rara_frame_info_get(rara_ctx *c, int32_t view, rara_frame_info *out)
     out->n_walked = (int64_t)c->h_counters->n_walked;
     out->n_cut_evaluated = (int64_t)c->h_counters->n_cut_evaluated;
     out->n_tested = (int64_t)c->h_counters->n_tested;
+    out->n_pair_candidates = (int64_t)c->h_view_counters[k].n_pairs;
     return RARA_OK;
 }
 
@@ -1159,6 +1277,9 @@ constexpr size_t kSzSort = align256(4 * (4 * (size_t)((kStaticMaxPairs + 1023) /
 constexpr size_t kStaticBytes = kSzCounters + kSzViews + kSzScenes + kSzViewCounters + kSzLabels + 2 * kSzU32G +
                                 kSzRect + kSzRec + kSzCut + 4 * kSzU32G + kSzLookC + kSzLookE + 4 * kSzU32P +
                                 kSzHist + kSzSeg + kSzRanges + kSzOrder + kSzSort;
+
+// 20,396,544 bytes with the current record sizes; the header states "about 20.4 MB"
+static_assert(kStaticBytes <= 20500000, "the static scratch outgrew the size the header states");
 
 static __device__ __align__(256) unsigned char g_rara_static_scratch[kStaticBytes];
 

@@ -133,21 +133,26 @@ __device__ __forceinline__ void warp_reduce_scatter(float (&v)[N])
     if (N == 16) v[0] += __shfl_xor_sync(kFull, v[0], 1);
 }
 
-// One 16x16 tile, one thread per pixel (warp rectangles of 8x4 pixels).
+// One band of up to 256 pixels of a tile (rows [band * rows, (band + 1) * rows), rows =
+// min(tile_h, 256 / tile_w)), one thread per pixel, warp rectangles of 8x4 pixels; the warps
+// past a 64-pixel tile's rows have no pixels.
 __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &vw, const BwdView &bv,
                                          const uint32_t *pair_vals, Stage &st, float4 (*s_ab)[kBlock],
                                          uint32_t *s_slot, int *s_max,
-                                         int gtile, int tile)
+                                         int gtile, int tile, int band)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int W = vw.cam.W, H = vw.cam.H;
+    const int TW = vw.tile_w, TH = vw.tile_h;
+    const int rows = min(TH, kBlock / TW), wpr = TW / 8;
     const int tx = tile % vw.tiles_x, ty0 = tile / vw.tiles_x;
-    const int wx0 = (warp & 1) * 8, wy0 = (warp >> 1) * 4;
-    const int px = tx * kTile + wx0 + (lane & 7), py = ty0 * kTile + wy0 + (lane >> 3);
-    const bool inside = px < W && py < H;
+    const int wx0 = (warp % wpr) * 8, wy0 = (warp / wpr) * 4;   // within the band
+    const int px = tx * TW + wx0 + (lane & 7);
+    const int py = ty0 * TH + band * rows + wy0 + (lane >> 3);
+    const bool inside = px < W && py < H && wy0 + (lane >> 3) < rows;
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-    const float rx0 = (float)(tx * kTile + wx0) + 0.5f, rx1 = rx0 + 7.0f;
-    const float ry0 = (float)(ty0 * kTile + wy0) + 0.5f, ry1 = ry0 + 3.0f;
+    const float rx0 = (float)(tx * TW + wx0) + 0.5f, rx1 = rx0 + 7.0f;
+    const float ry0 = (float)(ty0 * TH + band * rows + wy0) + 0.5f, ry1 = ry0 + 3.0f;
     const int2 range = a.ranges[gtile];
 
     float T = 1.0f, dC0 = 0.0f, dC1 = 0.0f, dC2 = 0.0f;
@@ -304,17 +309,21 @@ __global__ void __launch_bounds__(kBlock, 4) k_render_bwd(RenderBwdArgs a)
         __syncthreads();
         const unsigned item = s_item;
         if (item == 0xffffffffu) break;
-        if ((item & 3u) == 0u) {  // part 0 of a split tile does the whole tile
-            const int gtile = (int)(item >> 4);
-            int lo = 0, hi = a.num_views - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (a.views[mid].tile_base <= (uint32_t)gtile) lo = mid;
-                else hi = mid - 1;
-            }
-            const ViewDev &vw = a.views[lo];
-            tile_bwd(a, vw, a.bviews[lo], pair_vals, st, s_ab, s_slot, &s_max, gtile, gtile - (int)vw.tile_base);
+        const int gtile = (int)(item >> 4), part = (int)(item & 3u);
+        int lo = 0, hi = a.num_views - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.views[mid].tile_base <= (uint32_t)gtile) lo = mid;
+            else hi = mid - 1;
         }
+        const ViewDev &vw = a.views[lo];
+        // the forward's items of a tile are bands of its rows with 1, 2 or 4 lanes per pixel;
+        // the backward walks bands of 256 pixels with one lane each: the first bands' items
+        // take them, the others have nothing to do
+        const int bands = max(1, vw.tile_w * vw.tile_h / kBlock);
+        if (part < bands)
+            tile_bwd(a, vw, a.bviews[lo], pair_vals, st, s_ab, s_slot, &s_max, gtile, gtile - (int)vw.tile_base,
+                     part);
         __syncthreads();  // everyone has read s_item and the staged batch
     }
 }

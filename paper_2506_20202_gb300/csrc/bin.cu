@@ -58,7 +58,7 @@ constexpr uint32_t kNoPool = 0xffffffffu;
 // Per-splat constants of the listing spans: conic (a, b, c), q_cut and their derived terms.
 struct SpanGeo {
     float mx, my, aq, D, ia, b, ymax, yl;
-    int x0, x1, y0, W, H;
+    int x0, x1, y0, W, H, tw, th;
     bool ok;
 };
 
@@ -84,6 +84,7 @@ __device__ __forceinline__ SpanGeo span_geo(const float4 r0, const float4 r1, ui
     g.yl = g.ok ? __fmul_rn(b, fast_sqrt(__fdividef(qc, __fmul_rn(c, g.D)))) : 0.0f;
     g.x0 = rc.x & 0xffff; g.y0 = rc.x >> 16; g.x1 = rc.y & 0xffff;
     g.W = vw.cam.W; g.H = vw.cam.H;
+    g.tw = vw.tile_w; g.th = vw.tile_h;
     return g;
 }
 
@@ -91,8 +92,8 @@ __device__ __forceinline__ SpanGeo span_geo(const float4 r0, const float4 r1, ui
 // feeds a sum is rounded on its own (__fmul_rn), so each call site computes the same spans.
 __device__ __forceinline__ void row_span(const SpanGeo &g, int ty, int &lo, int &count)
 {
-    const float by0 = __fsub_rn((float)(ty * kTile) + 0.5f, g.my);
-    const float by1 = __fsub_rn((float)min((ty + 1) * kTile, g.H) - 0.5f, g.my);
+    const float by0 = __fsub_rn((float)(ty * g.th) + 0.5f, g.my);
+    const float by1 = __fsub_rn((float)min((ty + 1) * g.th, g.H) - 0.5f, g.my);
     const float y0 = fmaxf(by0, -g.ymax), y1 = fminf(by1, g.ymax);
     count = 0;
     lo = g.x0;
@@ -103,9 +104,11 @@ __device__ __forceinline__ void row_span(const SpanGeo &g, int ty, int &lo, int 
     const float XL = __fmul_rn(__fsub_rn(-__fmul_rn(g.b, ya), ra), g.ia);
     const float XR = __fmul_rn(__fadd_rn(-__fmul_rn(g.b, yb), rb), g.ia);
     if (XL > __fsub_rn((float)g.W - 0.5f, g.mx)) return;  // right of the image's last pixel centres
-    // column tx reaches the interval iff tx 16 + 15.5 - mx >= XL and tx 16 + 0.5 - mx <= XR
-    const int c0 = max(g.x0, (int)ceilf(__fmul_rn(__fsub_rn(__fadd_rn(XL, g.mx), 15.5f), 1.0f / kTile)));
-    const int c1 = min(g.x1, (int)floorf(__fmul_rn(__fsub_rn(__fadd_rn(XR, g.mx), 0.5f), 1.0f / kTile)));
+    // column tx reaches the interval iff tx tw + (tw - 0.5) - mx >= XL and tx tw + 0.5 - mx <= XR
+    // (tile widths are powers of two, so 1 / tw is exact and the products are the quotients)
+    const float itw = 1.0f / (float)g.tw;
+    const int c0 = max(g.x0, (int)ceilf(__fmul_rn(__fsub_rn(__fadd_rn(XL, g.mx), (float)g.tw - 0.5f), itw)));
+    const int c1 = min(g.x1, (int)floorf(__fmul_rn(__fsub_rn(__fadd_rn(XR, g.mx), 0.5f), itw)));
     lo = c0;
     count = max(0, c1 - c0 + 1);
 }
@@ -360,9 +363,19 @@ __global__ void k_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const C
 // tiles: bucket counts, then each block reserves its run in every bucket and writes its
 // items there. The order inside a bucket follows the atomics; it only affects scheduling,
 // never the image.
-__device__ __forceinline__ unsigned items_of(int bits, int split2_bits, int split4_bits)
+// log2 of the lanes per pixel of a tile whose list length has `bits` bits, clamped to what
+// the tile's area allows (at least 1 and at most 4 items of 256 lanes: area_log2 =
+// log2(pixels / 64) gives log2(L) in [2 - area_log2, 4 - area_log2]).
+__device__ __forceinline__ unsigned lpp_of(int bits, int split2_bits, int split4_bits, int area_log2)
 {
-    return bits >= split4_bits ? 2u : (bits >= split2_bits ? 1u : 0u);  // log2 of the items
+    const int l = bits >= split4_bits ? 2 : (bits >= split2_bits ? 1 : 0);
+    return (unsigned)min(min(2, 4 - area_log2), max(2 - area_log2, l));
+}
+
+// log2 of the items of such a tile: L pixels-worth of lanes / 256 = L * 2^area_log2 / 4.
+__device__ __forceinline__ unsigned items_of(int bits, int split2_bits, int split4_bits, int area_log2)
+{
+    return lpp_of(bits, split2_bits, split4_bits, area_log2) + (unsigned)area_log2 - 2u;
 }
 
 // A global tile id is a real tile unless it is a hole past its view's last tile.
@@ -389,7 +402,7 @@ __global__ void __launch_bounds__(kBlock) k_order_hist(const int2 *__restrict__ 
 }
 
 __global__ void __launch_bounds__(kBlock) k_order_scatter(const int2 *__restrict__ ranges, int num_tiles,
-                                                          int split2_bits, int split4_bits,
+                                                          int split2_bits, int split4_bits, int area_log2,
                                                           uint32_t *__restrict__ order, Counters *__restrict__ counters,
                                                           const ViewDev *views, int tile_bits)
 {
@@ -398,7 +411,7 @@ __global__ void __launch_bounds__(kBlock) k_order_scatter(const int2 *__restrict
         unsigned acc = 0;
         for (int b = 0; b < 33; ++b) {
             s_base[b] = acc;
-            acc += counters->order_hist[b] << items_of(32 - b, split2_bits, split4_bits);
+            acc += counters->order_hist[b] << items_of(32 - b, split2_bits, split4_bits, area_log2);
         }
         if (blockIdx.x == 0) counters->num_items = acc;
     }
@@ -410,7 +423,7 @@ __global__ void __launch_bounds__(kBlock) k_order_scatter(const int2 *__restrict
         if (!real_tile(views, tile_bits, t)) continue;
         const int2 r = ranges[t];
         const int b = __clz((unsigned)(r.y - r.x));
-        atomicAdd(&s_cnt[b], 1u << items_of(32 - b, split2_bits, split4_bits));
+        atomicAdd(&s_cnt[b], 1u << items_of(32 - b, split2_bits, split4_bits, area_log2));
     }
     __syncthreads();
     if (threadIdx.x < 33) {
@@ -423,8 +436,8 @@ __global__ void __launch_bounds__(kBlock) k_order_scatter(const int2 *__restrict
         if (!real_tile(views, tile_bits, t)) continue;
         const int2 r = ranges[t];
         const int b = __clz((unsigned)(r.y - r.x));
-        const unsigned lg = items_of(32 - b, split2_bits, split4_bits);
-        const unsigned per = 1u << lg;
+        const unsigned lg = lpp_of(32 - b, split2_bits, split4_bits, area_log2);
+        const unsigned per = 1u << items_of(32 - b, split2_bits, split4_bits, area_log2);
         const unsigned pos = s_base[b] + atomicAdd(&s_cnt[b], per);
         for (unsigned p = 0; p < per; ++p) order[pos + p] = ((uint32_t)t << 4) | (lg << 2) | p;
     }
@@ -499,15 +512,16 @@ void launch_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const Counter
     if (grid > 0) k_ranges<<<grid, 256, 0, s>>>(keys_a, keys_b, counters, cap_pairs, num_tiles, ranges);
 }
 
-void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int split4_bits, uint32_t *order,
-                       Counters *counters, const ViewDev *views, int tile_bits, int grid, cudaStream_t s)
+void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int split4_bits, int area_log2,
+                       uint32_t *order, Counters *counters, const ViewDev *views, int tile_bits, int grid,
+                       cudaStream_t s)
 {
     if (num_tiles <= 0) return;
     const int want = (num_tiles + kBlock * 4 - 1) / (kBlock * 4);
     const int g = want < grid ? want : grid;
     k_order_hist<<<g, kBlock, 0, s>>>(ranges, num_tiles, counters, views, tile_bits);
-    k_order_scatter<<<g, kBlock, 0, s>>>(ranges, num_tiles, split2_bits, split4_bits, order, counters, views,
-                                         tile_bits);
+    k_order_scatter<<<g, kBlock, 0, s>>>(ranges, num_tiles, split2_bits, split4_bits, area_log2, order, counters,
+                                         views, tile_bits);
 }
 
 void launch_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_src, const uint32_t *tiles_src,

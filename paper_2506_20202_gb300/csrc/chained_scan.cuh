@@ -14,7 +14,6 @@ namespace rara {
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagIncl = 2ull << 62;
 constexpr unsigned long long kValueMask = (1ull << 62) - 1;
-constexpr int kSpinLimit = 1 << 22;
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
 {
@@ -41,10 +40,12 @@ __device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v)
 }
 
 // Exclusive prefix of `total` over partitions 0..part-1. Must be called by all 32 lanes
-// of ONE warp of the block; returns the prefix in every lane.
+// of ONE warp of the block; returns the prefix in every lane. spin_limit bounds the polls
+// of one wait (kSpinLimit unless a test lowers it).
 __device__ __forceinline__ unsigned long long warp_chained_prefix(unsigned long long *lookback, int part,
                                                                   unsigned long long total,
-                                                                  unsigned int *status)
+                                                                  unsigned int *status,
+                                                                  int spin_limit = kSpinLimit)
 {
     const int lane = threadIdx.x & 31;
     if (part == 0) {
@@ -63,7 +64,7 @@ __device__ __forceinline__ unsigned long long warp_chained_prefix(unsigned long 
         const unsigned incl = __ballot_sync(0xffffffffu, flag == kFlagIncl);
         // Only the predecessors up to the nearest inclusive prefix matter.
         if (waiting && (!incl || __ffs(waiting) < __ffs(incl))) {
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 if (lane == 0) atomicOr(status, kStatusLookbackTimeout);
                 break;
             }

@@ -147,16 +147,24 @@ __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
 
     float mx = 0.f, my = 0.f, mz = 0.f, s0 = 1.f, s1 = 1.f, s2 = 1.f, logit = 0.f;
     float Rg[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    bool bad = false;  // a non-finite parameter or a zero quaternion: not rendered, reported
     if (valid) {
         mx = __ldg(&sc.means[i]); my = __ldg(&sc.means[n + i]); mz = __ldg(&sc.means[2 * n + i]);
-        s0 = expf(__ldg(&sc.log_scales[i]));
-        s1 = expf(__ldg(&sc.log_scales[n + i]));
-        s2 = expf(__ldg(&sc.log_scales[2 * n + i]));
+        const float l0 = __ldg(&sc.log_scales[i]), l1 = __ldg(&sc.log_scales[n + i]);
+        const float l2 = __ldg(&sc.log_scales[2 * n + i]);
+        s0 = expf(l0);
+        s1 = expf(l1);
+        s2 = expf(l2);
         logit = __ldg(&sc.logits[i]);
         // rotation of the normalised quaternion (w, x, y, z)
         float qw = __ldg(&sc.quats[i]), qx = __ldg(&sc.quats[n + i]);
         float qy = __ldg(&sc.quats[2 * n + i]), qz = __ldg(&sc.quats[3 * n + i]);
-        const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        const float qq = qw * qw + qx * qx + qy * qy + qz * qz;
+        // a NaN or an infinity anywhere makes the sum non-finite (so does a sum that
+        // overflows, which only inputs near the float range can cause: treated as bad too)
+        bad = !isfinite(mx + my + mz + l0 + l1 + l2 + logit) || !isfinite(qq) || !(qq > 0.0f);
+        if (bad) atomicOr(&a.counters->status, kStatusBadInput);
+        const float qn = rsqrtf(qq);
         qw *= qn; qx *= qn; qy *= qn; qz *= qn;
         Rg[0] = 1.f - 2.f * (qy * qy + qz * qz); Rg[1] = 2.f * (qx * qy - qw * qz); Rg[2] = 2.f * (qx * qz + qw * qy);
         Rg[3] = 2.f * (qx * qy + qw * qz); Rg[4] = 1.f - 2.f * (qx * qx + qz * qz); Rg[5] = 2.f * (qy * qz - qw * qx);
@@ -219,6 +227,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
                     label = dep < -r ? RARA_INVISIBLE : (dep > r ? RARA_VISIBLE : RARA_CUTOFF);
                     if (pl.mode == RARA_MODE_RARA_ALL && label != RARA_INVISIBLE) label = RARA_CUTOFF;
                 }
+                if (bad) label = RARA_INVISIBLE;
                 // A convex clip volume: the rule of each further plane joins the first's.
                 // Invisible if behind any plane (the centre for hard clipping, the radius-r
                 // sphere otherwise), visible only if in front of all of them.
@@ -275,9 +284,10 @@ __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
                         const float my2 = fmaf(cam.fy, ty * itz, cam.cy);
                         // Tile rectangle: axis-aligned box of the q <= 9 ellipse
                         const float hx = 3.0f * sqrtf(ca), hy = 3.0f * sqrtf(cc);
-                        const float inv_t = 1.0f / kTile;
-                        const float fx0 = floorf((mx2 - hx) * inv_t), fx1 = floorf((mx2 + hx) * inv_t);
-                        const float fy0 = floorf((my2 - hy) * inv_t), fy1 = floorf((my2 + hy) * inv_t);
+                        // tile edges are powers of two: the products are the exact quotients
+                        const float itw = 1.0f / (float)vw.tile_w, ith = 1.0f / (float)vw.tile_h;
+                        const float fx0 = floorf((mx2 - hx) * itw), fx1 = floorf((mx2 + hx) * itw);
+                        const float fy0 = floorf((my2 - hy) * ith), fy1 = floorf((my2 + hy) * ith);
                         const int rx0 = (int)fmaxf(0.0f, fminf((float)vw.tiles_x, fx0));
                         const int rx1 = (int)fmaxf(-1.0f, fminf((float)(vw.tiles_x - 1), fx1));
                         const int ry0 = (int)fmaxf(0.0f, fminf((float)vw.tiles_y, fy0));
@@ -293,6 +303,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
                             const float il = rsqrtf(ex * ex + ey * ey + ez * ez);
                             float rgb[3];
                             sh_colour(s_sh, sc.sh_degree, ex * il, ey * il, ez * il, rgb);
+                            if (!isfinite(rgb[0] + rgb[1] + rgb[2])) atomicOr(&a.counters->status, kStatusBadInput);
                             SplatRec rec;
                             rec.r0 = make_float4(mx2, my2, cc * idet, -cb * idet);
                             rec.r1 = make_float4(ca * idet, op, rgb[0], rgb[1]);
@@ -479,7 +490,8 @@ __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
             }
             const unsigned total = __shfl_sync(0xffffffffu, wi, 31);
             if (lane < kBlock / 32) s_warp[lane] = wi - w;
-            const unsigned long long prefix = warp_chained_prefix(a.lookback, (int)part, total, &a.counters->status);
+            const unsigned long long prefix =
+                warp_chained_prefix(a.lookback, (int)part, total, &a.counters->status, a.spin_limit);
             if (lane == 0) s_prefix = prefix;
         }
         __syncthreads();

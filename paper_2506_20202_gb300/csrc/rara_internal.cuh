@@ -33,7 +33,7 @@
 
 namespace rara {
 
-constexpr int kTile = 16;              // screen tile edge (pixels); one 256-thread block per tile
+constexpr int kTile = 16;              // default screen tile edge (pixels), 16 x 16
 constexpr int kBlock = 256;            // threads per block for per-Gaussian and per-pixel kernels
 constexpr float kNearZ = 0.2f;         // near-plane cull (camera z)
 constexpr float kDilation = 0.3f;      // low-pass dilation added to the 2D covariance (px^2)
@@ -42,9 +42,14 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
+// Polls of a bounded device-side wait (chained-scan look-back, bulk-copy barrier) before it
+// gives up and records kStatusLookbackTimeout.
+constexpr int kSpinLimit = 1 << 22;
+
 // Device status word bits.
 constexpr uint32_t kStatusLookbackTimeout = 1u;  // a bounded wait (chained scan, bulk copy) gave up
 constexpr uint32_t kStatusOverflow = 2u;         // a count exceeded its buffer's capacity
+constexpr uint32_t kStatusBadInput = 4u;         // a Gaussian had a non-finite parameter or colour
 
 // Per-slot splat record, written by preprocess for rendered slots and gathered by the
 // render kernel: 3 x float4 = 48 bytes.
@@ -106,6 +111,7 @@ struct ViewDev {
     CamDev cam;
     PlaneDev plane;
     int scene;
+    int tile_w, tile_h;   // screen tile (the batch's tile shape: 64, 256 or 512 pixels)
     int tiles_x, tiles_y;
     uint32_t tile_base;   // first global tile id of the view (view << tile_bits)
     uint32_t slot_base;   // first dense (view, Gaussian) slot of the view
@@ -195,6 +201,7 @@ struct CompactArgs {
     const ViewCounters *view_counters;
     int num_views;
     uint32_t *seg_base;    // [num_views] first slot of each view (written)
+    int spin_limit;        // polls of a look-back wait before it gives up
 };
 void launch_compact(const CompactArgs &a, int grid, cudaStream_t s);
 int compact_blocks_per_sm();
@@ -240,12 +247,16 @@ void launch_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const Counter
                    uint32_t num_tiles, int2 *ranges, int grid, cudaStream_t s);
 
 // Stage 7: render work items ordered by descending list length (log2 buckets), heaviest
-// first. A tile whose list has at least 2^(split4_bits-1) entries becomes 4 items (16x4
-// pixels, 4 lanes per pixel), at least 2^(split2_bits-1) entries 2 items (16x8, 2 lanes
-// per pixel), otherwise 1 item. Item = tile << 4 | log2(lanes per pixel) << 2 | part.
+// first. A work item is 256 lanes over a band of a tile's rows with L = 1, 2 or 4 lanes per
+// pixel (256 / L pixels). A tile whose list has at least 2^(split4_bits-1) entries gets
+// L = 4, at least 2^(split2_bits-1) entries L = 2, otherwise L = 1, clamped so that an item
+// holds at most the tile's pixels and a tile is at most 4 items: 64-pixel tiles always take
+// L = 4, 512-pixel tiles at most L = 2. The tile then becomes L * pixels / 256 items.
+// Item = tile << 4 | log2(L) << 2 | part. area_log2 = log2(tile pixels / 64) (0, 2 or 3).
 // order holds 4 * num_tiles entries; the item count goes to counters->num_items.
-void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int split4_bits, uint32_t *order,
-                       Counters *counters, const ViewDev *views, int tile_bits, int grid, cudaStream_t s);
+void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int split4_bits, int area_log2,
+                       uint32_t *order, Counters *counters, const ViewDev *views, int tile_bits, int grid,
+                       cudaStream_t s);
 
 // Stage 8: render
 struct RenderArgs {
@@ -259,9 +270,13 @@ struct RenderArgs {
     int num_views;
     Counters *counters;
 };
-// count: accumulate the work counters (n_evaluated .. n_tested) of the launch.
-void launch_render(const RenderArgs &a, int grid, cudaStream_t s, bool count = true, bool multi = false);
-int render_blocks_per_sm();
+// count: accumulate the work counters (n_evaluated .. n_tested) of the launch. depth: the
+// blend batch depth (entries staged in shared memory per batch: 128, 256 or 512).
+int launch_render(const RenderArgs &a, int grid, cudaStream_t s, bool count, bool multi, int depth);
+int render_blocks_per_sm(int depth);
+// Tile shapes and blend batch depths the kernels support.
+bool tile_shape_ok(int tile_w, int tile_h);
+bool batch_depth_ok(int depth);
 
 // Backward. Per-slot gradient record, 7 x float4 = 112 bytes, accumulated (atomics) by the
 // render backward and read by the preprocess backward:

@@ -1,16 +1,19 @@
 // Steps (c)+(d): per-tile front-to-back compositing with the RaRa decay weight.
 //
-// Work items come from a queue ordered heaviest first (by tile-list length). A light tile
-// is one item: a 256-thread block composites its 16x16 pixels, one lane per pixel. A heavy
-// tile is split into 2 or 4 items of 16x8 or 16x4 pixels with 2 or 4 lanes per pixel: the
-// lanes of a pixel take consecutive list entries and combine them with a prefix product of
-// (1 - alpha), so the pixel's chain of dependent steps is 2 or 4 times shorter. That
+// Work items come from a queue ordered heaviest first (by tile-list length). An item is a
+// 256-thread block over a band of a tile's rows with L = 1, 2 or 4 lanes per pixel (256 / L
+// pixels): a light 16x16 tile is one item of one lane per pixel, a heavy one 2 or 4 items of
+// 16x8 or 16x4 pixels with 2 or 4 lanes per pixel (an 8x8 tile is always one item of 4 lanes
+// per pixel, a 32x16 tile 2 or 4 items). The lanes of a pixel take consecutive list entries
+// and combine them with a prefix product of (1 - alpha), so the pixel's chain of dependent
+// steps is 2 or 4 times shorter. That
 // matters because a pixel that never saturates (for example one that looks through the
 // clipped region, where cutoff Gaussians get w ~ 0) walks its whole list, and the longest
 // such walk bounds the launch.
 //
-// The tile's depth-sorted list is walked in batches of 256 entries: each thread gathers one
-// splat record (and, for a cutoff Gaussian, its ray-tracing record) into shared memory.
+// The tile's depth-sorted list is walked in batches of D entries (the blend batch depth, 128,
+// 256 or 512, chosen by the autotuner): the threads gather the batch's splat records (and,
+// for cutoff Gaussians, their ray-tracing records) into shared memory.
 // Each warp owns a rectangle of the item's pixels; before walking a 32-entry chunk of the
 // batch, its lanes test one entry each against the rectangle (exact minimum of q over the
 // rectangle of pixel centres) and the warp walks only the entries whose q <= 9 support
@@ -53,60 +56,72 @@ struct Tally {
     }
 };
 
-// One work item: LPP lanes per pixel. Item geometry (inside the 16x16 tile):
-//   LPP 1: the whole tile, warp rectangles 8x4
-//   LPP 2: rows [8 part, 8 part + 8), warp rectangles 8x2
-//   LPP 4: rows [4 part, 4 part + 4), warp rectangles 4x2
-template <int LPP, bool COUNT, bool MULTI>
+// One work item: LPP lanes per pixel over rows [part * rows, (part + 1) * rows) of a
+// tile_w x tile_h tile, rows = 256 / (LPP tile_w). Warp rectangles of RW x RH pixels:
+//   LPP 1: 8x4, LPP 2: 8x2, LPP 4: 4x2 (32 lanes each), tile_w / RW of them per row.
+// The batch depth D is the number of list entries staged in shared memory at a time.
+template <int LPP, int D, bool COUNT, bool MULTI>
 __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &vw, const uint32_t *pair_vals,
-                                            Stage &st, int gtile, int tile, int part, Tally<COUNT> &ty)
+                                            StageT<D> &st, int gtile, int tile, int part, Tally<COUNT> &ty)
 {
     constexpr int RW = LPP == 4 ? 4 : 8;     // warp rectangle width
     constexpr int RH = LPP == 1 ? 4 : 2;     // warp rectangle height
-    constexpr int WPR = kTile / RW;          // warp rectangles per row
+    constexpr int NB = (D + kBlock - 1) / kBlock;  // entries a thread stages per batch
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane % LPP, pix = lane / LPP;
     const int W = vw.cam.W, H = vw.cam.H;
+    const int TW = vw.tile_w, TH = vw.tile_h;
+    const int wpr = TW / RW;                 // warp rectangles per row
+    const int rows = (kBlock / LPP) / TW;    // rows of the item
     const int tx = tile % vw.tiles_x, ty0 = tile / vw.tiles_x;
-    const int wx0 = (warp % WPR) * RW;
-    const int wy0 = part * (kTile / LPP) + (warp / WPR) * RH;
-    const int px = tx * kTile + wx0 + pix % RW, py = ty0 * kTile + wy0 + pix / RW;
-    const bool inside = px < W && py < H;
+    const int wx0 = (warp % wpr) * RW;
+    const int wy0 = part * rows + (warp / wpr) * RH;
+    const int px = tx * TW + wx0 + pix % RW, py = ty0 * TH + wy0 + pix / RW;
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-    const float rx0 = (float)(tx * kTile + wx0) + 0.5f, rx1 = rx0 + (float)(RW - 1);
-    const float ry0 = (float)(ty0 * kTile + wy0) + 0.5f, ry1 = ry0 + (float)(RH - 1);
+    // the warp's rectangle of pixel centres is [rx0, rx0 + RW - 1] x [ry0, ry0 + RH - 1]
+    const float rx0 = (float)(tx * TW + wx0) + 0.5f;
+    const float ry0 = (float)(ty0 * TH + wy0) + 0.5f;
     const int2 range = a.ranges[gtile];
 
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    bool done = !inside;
+    bool done = !(px < W && py < H);
     uint32_t last = 0;
-    // slot of this thread's entry in the next batch, loaded one batch ahead
-    uint32_t g_next = range.x + (int)threadIdx.x < range.y ? __ldg(&pair_vals[range.x + threadIdx.x]) : 0u;
+    // slots of this thread's entries in the next batch, loaded one batch ahead
+    uint32_t g_next[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+        const int e = (int)threadIdx.x + r * kBlock;
+        g_next[r] = e < D && range.x + e < range.y ? __ldg(&pair_vals[range.x + e]) : 0u;
+    }
 
-    for (int base = range.x; base < range.y; base += kBlock) {
+    for (int base = range.x; base < range.y; base += D) {
         if (__syncthreads_count(done) == kBlock) break;
-        const int k = base + threadIdx.x;
-        const uint32_t g = g_next;
-        if (k + kBlock < range.y) g_next = __ldg(&pair_vals[k + kBlock]);
-        if (k < range.y) {
-            const SplatRec rec = a.rec[g];
-            stage_splat(st, threadIdx.x, rec);
-            if (rec.r2.y != kWeightNone) {
-                stage_cut(st, threadIdx.x, a.cut[g]);
-                // a Gaussian split by several planes of a clip volume: its slot, for the
-                // further planes (the staged c3.y is otherwise unused)
-                if (MULTI && rec.r2.y == kWeightMulti) st.c3[threadIdx.x].y = __uint_as_float(g);
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+            const int e = (int)threadIdx.x + r * kBlock;  // entry of the batch this thread stages
+            const int k = base + e;
+            const uint32_t g = g_next[r];
+            if (e < D && k + D < range.y) g_next[r] = __ldg(&pair_vals[k + D]);
+            if (e < D && k < range.y) {
+                const SplatRec rec = a.rec[g];
+                stage_splat(st, e, rec);
+                if (rec.r2.y != kWeightNone) {
+                    stage_cut(st, e, a.cut[g]);
+                    // a Gaussian split by several planes of a clip volume: its slot, for the
+                    // further planes (the staged c3.y is otherwise unused)
+                    if (MULTI && rec.r2.y == kWeightMulti) st.c3[e].y = __uint_as_float(g);
+                }
             }
         }
         __syncthreads();
-        const int cnt = min(kBlock, range.y - base);
+        const int cnt = min(D, range.y - base);
         const int pos0 = base - range.x + 1;  // list position (1-based) of batch entry 0
         for (int chunk = 0; chunk < cnt; chunk += 32) {
             if (__all_sync(0xffffffffu, done)) break;
             bool keep = false, weighted = false;
             const int jt = chunk + lane;
             if (jt < cnt) {
-                keep = entry_reaches(st, jt, rx0, rx1, ry0, ry1);
+                keep = entry_reaches(st, jt, rx0, rx0 + (float)(RW - 1), ry0, ry0 + (float)(RH - 1));
                 weighted = st.s1[jt].w != kWeightNone;
                 ty.add(ty.tested, true);
             }
@@ -234,9 +249,11 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
         }
     }
 
-    if (inside && sub == 0) {
-        const size_t p = (size_t)py * W + px;
-        const size_t plane = (size_t)W * H;
+    // the pixel again from its centre (fewer values live across the loop)
+    const int W2 = vw.cam.W, H2 = vw.cam.H, px2 = (int)pxf, py2 = (int)pyf;
+    if (px2 < W2 && py2 < H2 && sub == 0) {
+        const size_t p = (size_t)py2 * W2 + px2;
+        const size_t plane = (size_t)W2 * H2;
         vw.image[p] = fmaf(T, vw.bg[0], C0);
         vw.image[plane + p] = fmaf(T, vw.bg[1], C1);
         vw.image[2 * plane + p] = fmaf(T, vw.bg[2], C2);
@@ -245,10 +262,19 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
     }
 }
 
-template <bool COUNT, bool MULTI>
-__global__ void __launch_bounds__(kBlock, 5) k_render(RenderArgs a)
+// Blocks per SM the register budget is sized for: the shared memory of a 512-entry batch
+// (61 KB) allows 3 blocks per SM, the others 5.
+template <int D>
+constexpr int render_minb() { return D >= 512 ? 3 : 5; }
+
+template <int D>
+constexpr size_t render_smem() { return sizeof(StageT<D>); }
+
+template <int D, bool COUNT, bool MULTI>
+__global__ void __launch_bounds__(kBlock, render_minb<D>()) k_render(RenderArgs a)
 {
-    __shared__ Stage st;
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    StageT<D> &st = *reinterpret_cast<StageT<D> *>(s_dyn);
     __shared__ unsigned s_item;
     Tally<COUNT> ty;
     const unsigned num_items = *(volatile unsigned *)&a.counters->num_items;
@@ -271,9 +297,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_render(RenderArgs a)
         }
         const ViewDev &vw = a.views[lo];
         const int tile = gtile - (int)vw.tile_base;
-        if (lpp_log2 == 0) render_item<1, COUNT, MULTI>(a, vw, pair_vals, st, gtile, tile, 0, ty);
-        else if (lpp_log2 == 1) render_item<2, COUNT, MULTI>(a, vw, pair_vals, st, gtile, tile, part, ty);
-        else render_item<4, COUNT, MULTI>(a, vw, pair_vals, st, gtile, tile, part, ty);
+        if (lpp_log2 == 0) render_item<1, D, COUNT, MULTI>(a, vw, pair_vals, st, gtile, tile, part, ty);
+        else if (lpp_log2 == 1) render_item<2, D, COUNT, MULTI>(a, vw, pair_vals, st, gtile, tile, part, ty);
+        else render_item<4, D, COUNT, MULTI>(a, vw, pair_vals, st, gtile, tile, part, ty);
         __syncthreads();  // everyone has read s_item and the staged batch
     }
 
@@ -293,28 +319,78 @@ __global__ void __launch_bounds__(kBlock, 5) k_render(RenderArgs a)
     }
 }
 
-}  // namespace
+template <int D, bool COUNT, bool MULTI>
+int configure_render()
+{
+    return cudaFuncSetAttribute(k_render<D, COUNT, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)render_smem<D>()) == cudaSuccess ? 0 : -1;
+}
 
-int render_blocks_per_sm()
+template <int D>
+int launch_render_d(const RenderArgs &a, int grid, cudaStream_t s, bool count, bool multi)
+{
+    // the shared-memory opt-in is set once per device and instance (512 entries exceed the
+    // 48 KB default); a failure is reported like a launch failure
+    static bool configured[64][4] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int k = (count ? 1 : 0) + (multi ? 2 : 0);
+    if (dev >= 0 && dev < 64 && !configured[dev][k]) {
+        const int rc = count ? (multi ? configure_render<D, true, true>() : configure_render<D, true, false>())
+                             : (multi ? configure_render<D, false, true>() : configure_render<D, false, false>());
+        if (rc) return -1;
+        configured[dev][k] = true;
+    }
+    const size_t smem = render_smem<D>();
+    if (multi) {  // batches with a convex clip volume
+        if (count) k_render<D, true, true><<<grid, kBlock, smem, s>>>(a);
+        else k_render<D, false, true><<<grid, kBlock, smem, s>>>(a);
+    } else {
+        if (count) k_render<D, true, false><<<grid, kBlock, smem, s>>>(a);
+        else k_render<D, false, false><<<grid, kBlock, smem, s>>>(a);
+    }
+    return 0;
+}
+
+template <int D>
+int render_bpsm_d()
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_render<true, false>, kBlock, 0) != cudaSuccess || b < 1) {
+    if (configure_render<D, true, false>() ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_render<D, true, false>, kBlock, render_smem<D>()) !=
+            cudaSuccess ||
+        b < 1) {
         cudaGetLastError();
         b = 1;
     }
     return b;
 }
 
-void launch_render(const RenderArgs &a, int grid, cudaStream_t s, bool count, bool multi)
+}  // namespace
+
+bool tile_shape_ok(int tile_w, int tile_h)
 {
-    if (grid <= 0) return;
-    if (multi) {  // batches with a convex clip volume
-        if (count) k_render<true, true><<<grid, kBlock, 0, s>>>(a);
-        else k_render<false, true><<<grid, kBlock, 0, s>>>(a);
-    } else {
-        if (count) k_render<true, false><<<grid, kBlock, 0, s>>>(a);
-        else k_render<false, false><<<grid, kBlock, 0, s>>>(a);
-    }
+    // 64, 256 or 512 pixels whose rows split evenly into the warp rectangles of every
+    // lane count an item of that tile may use
+    const int a = tile_w * tile_h;
+    return (a == 64 && tile_w == 8 && tile_h == 8) ||
+           (a == 256 && (tile_w == 16 || tile_w == 32 || tile_w == 8)) ||
+           (a == 512 && (tile_w == 32 || tile_w == 16));
+}
+
+bool batch_depth_ok(int depth) { return depth == 128 || depth == 256 || depth == 512; }
+
+int render_blocks_per_sm(int depth)
+{
+    return depth == 128 ? render_bpsm_d<128>() : (depth == 512 ? render_bpsm_d<512>() : render_bpsm_d<256>());
+}
+
+int launch_render(const RenderArgs &a, int grid, cudaStream_t s, bool count, bool multi, int depth)
+{
+    if (grid <= 0) return 0;
+    if (depth == 128) return launch_render_d<128>(a, grid, s, count, multi);
+    if (depth == 512) return launch_render_d<512>(a, grid, s, count, multi);
+    return launch_render_d<256>(a, grid, s, count, multi);
 }
 
 }  // namespace rara

@@ -195,17 +195,21 @@ constexpr float kCullMargin = 1.0001f;
 // over its float32 rounding): a pixel with q > q_cut is outside the 3-sigma support or has
 // alpha0 < 1/255, so it is skipped before the exponential; alpha0 itself is still compared
 // with 1/255 afterwards, so q_cut only saves work and never decides.
-struct Stage {
-    float4 s0[kBlock], s1[kBlock], s2[kBlock];
-    float2 nb[kBlock];
-    float4 c0[kBlock], c1[kBlock], c2[kBlock], c3[kBlock];
+// D entries per batch (the blend batch depth: 128, 256 or 512; 120 bytes per entry).
+template <int D>
+struct StageT {
+    float4 s0[D], s1[D], s2[D];
+    float2 nb[D];
+    float4 c0[D], c1[D], c2[D], c3[D];
 };
+using Stage = StageT<kBlock>;
 
 // Staged form of a CutRec: the quadratic forms p.p and |dx A + dy B|^2 in (dx, dy) take
 // their coefficients directly,
 //   c0 = (G.G, G.Px, G.Py, d_ep), c1 = (Px.Px, 2 Px.Py, Py.Py, m.G),
 //   c2 = (m.Px, m.Py, A.A, 2 A.B), c3 = (B.B, 0, 0, 0).
-__device__ __forceinline__ void stage_cut(Stage &st, int i, const CutRec &c)
+template <int D>
+__device__ __forceinline__ void stage_cut(StageT<D> &st, int i, const CutRec &c)
 {
     const float ax = c.c2.z, ay = c.c2.w, az = c.c3.x, bx = c.c3.y, by = c.c3.z, bz = c.c3.w;
     st.c0[i] = c.c0;
@@ -221,7 +225,8 @@ __device__ __forceinline__ float splat_qcut(float lo)
     return fminf(kSupportQ, fmaf(lo + kLog2_255, 1.0f / kHalfLog2e, 1e-4f));
 }
 
-__device__ __forceinline__ void stage_splat(Stage &st, int i, const SplatRec &rec)
+template <int D>
+__device__ __forceinline__ void stage_splat(StageT<D> &st, int i, const SplatRec &rec)
 {
     const float lo = __log2f(rec.r1.y);
     st.s0[i] = make_float4(rec.r0.x, rec.r0.y, rec.r0.z, 2.0f * rec.r0.w);
@@ -239,7 +244,8 @@ __device__ __forceinline__ void stage_splat(Stage &st, int i, const SplatRec &re
 // lie in that smaller region, every pixel of the box does, and its float32 hit test
 // (|u|^2 < V.V and G.V > 0, ray_hits_front; margins 1e-3 V.V and 1e-4 (G.G + |G.p|), far
 // above the rounding) cannot fail: the entry is nothing to the box.
-__device__ __forceinline__ bool hidden_covers_box(const Stage &st, int j, float ax, float bx, float ay, float by)
+template <int D>
+__device__ __forceinline__ bool hidden_covers_box(const StageT<D> &st, int j, float ax, float bx, float ay, float by)
 {
     const float4 c0 = st.c0[j], c1 = st.c1[j], c2 = st.c2[j], c3 = st.c3[j];
     if (!(c0.x >= 1.001f)) return false;  // camera outside the ellipsoid, with a margin
@@ -255,7 +261,8 @@ __device__ __forceinline__ bool hidden_covers_box(const Stage &st, int j, float 
 // Exact rectangle test of staged entry j against the box [rx0, rx1] x [ry0, ry1] of pixel
 // centres: whether some pixel of the box can have q <= q_cut and, for a Gaussian wholly on
 // the invisible side, can miss its ellipsoid (elsewhere its alpha is 0).
-__device__ __forceinline__ bool entry_reaches(const Stage &st, int j, float rx0, float rx1, float ry0, float ry1)
+template <int D>
+__device__ __forceinline__ bool entry_reaches(const StageT<D> &st, int j, float rx0, float rx1, float ry0, float ry1)
 {
     const float4 s0 = st.s0[j];
     const float4 s1 = st.s1[j];

@@ -57,7 +57,7 @@ class rara_frame_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_rendered", C.c_int64), ("n_cutoff", C.c_int64),
                 ("n_pairs", C.c_int64), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
                 ("n_evaluated", C.c_int64), ("n_walked", C.c_int64), ("n_cut_evaluated", C.c_int64),
-                ("n_tested", C.c_int64)]
+                ("n_tested", C.c_int64), ("n_pair_candidates", C.c_int64)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/rara.h
@@ -67,9 +67,13 @@ SIGNATURES = {
     "rara_ctx_destroy": (C.c_int, [_P]),
     "rara_last_error": (C.c_char_p, [_P]),
     "rara_ctx_bytes": (C.c_size_t, [_P]),
+    "rara_ctx_reserve": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int32, C.c_int32]),
     "rara_ctx_sync": (C.c_int, [_P, _P]),
     "rara_ctx_launches": (C.c_int64, [_P]),
     "rara_ctx_set_tuning": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "rara_ctx_set_tiling": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32]),
+    "rara_ctx_count_work": (C.c_int, [_P, C.c_int32]),
+    "rara_ctx_debug_waits": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "rara_ctx_stage_ms": (C.c_int, [_P, C.POINTER(C.c_float)]),
     "rara_ctx_kernel_ms": (C.c_int, [_P, C.POINTER(C.c_float)]),
     "rara_preprocess": (C.c_int, [_P, C.POINTER(rara_gaussians), C.POINTER(rara_camera),
@@ -220,12 +224,31 @@ def rara_ctx_bytes(ctx) -> int:
     return int(load().rara_ctx_bytes(ctx))
 
 
+def rara_ctx_reserve(ctx, slots: int, pairs: int, views: int, max_view_tiles: int):
+    """Allocate scratch up front for batches up to these sizes (see include/rara.h)."""
+    _check(ctx, load().rara_ctx_reserve(ctx, int(slots), int(pairs), int(views), int(max_view_tiles)))
+
+
 def rara_ctx_launches(ctx) -> int:
     return int(load().rara_ctx_launches(ctx))
 
 
 def rara_ctx_set_tuning(ctx, split2_bits: int, split4_bits: int):
     _check(ctx, load().rara_ctx_set_tuning(ctx, int(split2_bits), int(split4_bits)))
+
+
+def rara_ctx_set_tiling(ctx, tile_w: int, tile_h: int, blend_depth: int = 256):
+    _check(ctx, load().rara_ctx_set_tiling(ctx, int(tile_w), int(tile_h), int(blend_depth)))
+
+
+def rara_ctx_count_work(ctx, on: bool = True):
+    _check(ctx, load().rara_ctx_count_work(ctx, int(bool(on))))
+
+
+def rara_ctx_debug_waits(ctx, spin_limit: int, orphan_first_partition: bool):
+    """Test hook: lower the next compaction's look-back poll limit and optionally leave its
+    first partition unprocessed (see include/rara.h)."""
+    _check(ctx, load().rara_ctx_debug_waits(ctx, int(spin_limit), int(bool(orphan_first_partition))))
 
 
 def rara_ctx_stage_ms(ctx):
@@ -365,11 +388,13 @@ def rara_frame_pairs(ctx, view: int = 0, keys=None, values=None, ranges=None, st
 class Renderer:
     """Owns a context and output buffers; render() runs the three stages on a stream."""
 
-    def __init__(self, budget_bytes: int = 0, tuning=None):
+    def __init__(self, budget_bytes: int = 0, tuning=None, tiling=None):
         self.ctx = rara_ctx_create(budget_bytes)
         self.generation = 0      # forwards run through this renderer (see autograd.py)
         if tuning is not None:
             rara_ctx_set_tuning(self.ctx, *tuning)
+        if tiling is not None:   # (tile_w, tile_h[, blend_depth])
+            rara_ctx_set_tiling(self.ctx, *tiling)
 
     def close(self):
         if self.ctx is not None:

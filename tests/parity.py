@@ -17,8 +17,8 @@ RECT_EXEMPT = 2e-3    # pixels from a tile edge (float32 position + footprint er
 TILE_EXEMPT = 0.03    # |smallest q over a tile - q_cut| under which float32 may list differently
 
 
-def gpu_frame(scene, cam, plane, bg=(0.0, 0.0, 0.0), renderer=None, export=True, tuning=None):
-    r = renderer or rara.Renderer(tuning=tuning)
+def gpu_frame(scene, cam, plane, bg=(0.0, 0.0, 0.0), renderer=None, export=True, tuning=None, tiling=None):
+    r = renderer or rara.Renderer(tuning=tuning, tiling=tiling)
     gs = rara.GaussianTensors.from_scene(scene)
     img, T, nc = r.render(gs, cam, plane, bg)
     torch.cuda.synchronize()
@@ -155,7 +155,7 @@ def check_image(pre, ref, gpu, report, rows=None, max_flag_frac=0.05, extra_mask
             report[f"mean_abs_c{c}"] = float(dc.mean())
             assert dc.max() <= IMG_MAX_ABS, f"channel {c}: max abs {dc.max():.3e}"
             assert dc.mean() <= IMG_MEAN_ABS, f"channel {c}: mean abs {dc.mean():.3e}"
-    dT = np.abs(gpu["T"] - ref["T"])[ok]
+    dT = np.abs(gpu["T"] - ref["T"])[ok] if "T" in gpu else np.zeros(0)
     if dT.size:
         report["T_max_abs"] = float(dT.max())
         assert dT.max() <= IMG_MAX_ABS

@@ -1,10 +1,14 @@
-"""Serving loop: continuous batching gives each request the same image as rendering it alone."""
+"""Serving loop: continuous batching gives each request the same image as rendering it
+alone, and that image matches the FP64 oracle; the slots' contexts stay within their
+share of the budget and, once warmed, allocate nothing while serving."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle
 from paper_2506_20202_gb300 import rara, scenes, serve
+from tests import parity
 
 pytestmark = pytest.mark.gpu
 
@@ -34,6 +38,14 @@ def test_each_result_equals_the_request_rendered_alone():
         srv.close()
     assert len(results) == len(reqs) and srv.rejected == 0
     assert srv.batches < len(reqs)                       # requests were batched
+    # a seeded sample of the served images against the FP64 oracle at the image bars
+    host = {"a": scenes.uniform_scene(5000, seed=1, sh_degree=1), "b": scenes.general_scene(12000, seed=2, sh_degree=3)}
+    rng = np.random.default_rng(5)
+    for k in rng.choice(len(reqs), size=8, replace=False):
+        req, res = reqs[int(k)], results[int(k)]
+        pre, kvr, ref = oracle.render_frame(host[req.scene], req.camera, req.plane, req.bg)
+        report = {}
+        parity.check_image(pre, ref, {"image": res.image.numpy().astype(np.float64)}, report, max_flag_frac=0.08)
     ctx = rara.rara_ctx_create(0)
     try:
         for req, res in zip(reqs, results):
@@ -70,3 +82,20 @@ def test_plain_baseline_serves_in_order():
     assert [r.rid for r in res] == [r.rid for r in reqs]
     s = serve.summarize(res)
     assert s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_warmed_server_reserves_within_its_share_and_allocates_nothing_while_serving():
+    sc = _scenes()
+    res_list = ((128, 128), (200, 120))
+    srv = serve.Server(sc, budget_bytes=2 << 30, slots=2, max_batch=8, resolutions=res_list, reserve_batch=4)
+    try:
+        srv.warm(serve.orbit_camera, seed=1, per_shape=1, pinned_per_res=4)
+        held = [rara.rara_ctx_bytes(s.ctx) for s in srv.slots]
+        assert all(0 < h <= srv.share for h in held)
+        reqs = serve.poisson_requests(["a", "b"], serve.orbit_camera, rate_hz=3000.0, duration_s=0.02, seed=9,
+                                      resolutions=res_list)
+        results = srv.run(reqs)
+        assert len(results) == len(reqs) and srv.rejected == 0
+        assert [rara.rara_ctx_bytes(s.ctx) for s in srv.slots] == held
+    finally:
+        srv.close()

@@ -6,6 +6,8 @@ rara_render_frame_noalloc keeps all scratch in a static device array; it must pr
 same frame as rara_render_frame. This file is collected last so that a run stopping at the
 first failure has run every other test; it also passes alone in a fresh process.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -72,3 +74,43 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     with pytest.raises(rara.RaraError) as e:
         rara.rara_render_frame_noalloc(rara.GaussianTensors.from_scene(small), big, pl, (0, 0, 0), img, T, nc)
     assert e.value.code == rara.RARA_ERR_BUDGET
+
+
+def _case(seed, plane_seed):
+    scene = scenes.uniform_scene(20_000, seed=seed, sh_degree=2)
+    cam = scenes.look_at_camera((0.3, -0.4, -3.0), (0.0, 0.0, 0.0), 320, 240, 60.0)
+    pl = scenes.Plane(np.float32(scenes.random_unit_normal(plane_seed)), 0.05, 3.0, scenes.MODE_RARA)
+    return rara.GaussianTensors.from_scene(scene), cam, pl
+
+
+def test_noalloc_allocates_nothing_and_recovers_after_the_pair_limit():
+    gs, cam, pl = _case(3, 4)
+    ref = _outputs(cam)
+    r = rara.Renderer()
+    r.render(gs, cam, pl, (0.0, 0.0, 0.0), out=ref)
+    r.close()
+    out = _outputs(cam)
+    # 3000 wide splats (sigma 0.1 at distance 3, about 500 rectangle tiles each) at 2048^2:
+    # within the Gaussian and tile limits, but 1.5M pairs, above the 2^19 pair limit, which
+    # is found only after the preprocess has run on the shared array
+    wide = scenes.uniform_scene(3000, seed=6)
+    wide = dataclasses.replace(wide, log_scales=np.full_like(wide.log_scales, np.log(0.1)))
+    gw = rara.GaussianTensors.from_scene(wide)
+    big = scenes.look_at_camera((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), 2048, 2048, 60.0)
+    bimg, bT, bnc = _outputs(big)
+    rara.rara_render_frame_noalloc(gs, cam, pl, (0, 0, 0), *out)   # set-up done before measuring
+    torch.cuda.synchronize()
+    free0, allocated0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    with pytest.raises(rara.RaraError) as e:
+        rara.rara_render_frame_noalloc(gw, big, pl, (0, 0, 0), bimg, bT, bnc)
+    assert e.value.code == rara.RARA_ERR_BUDGET
+    for _ in range(2):          # the next calls render normally, over what the refused one left
+        out[0].fill_(-1.0)
+        rara.rara_render_frame_noalloc(gs, cam, pl, (0, 0, 0), *out)
+        torch.cuda.synchronize()
+        assert torch.equal(out[2], ref[2])
+        assert float((out[0] - ref[0]).abs().max()) <= IMG_MAX_ABS
+        assert float((out[1] - ref[1]).abs().max()) <= IMG_MAX_ABS
+    # nothing was allocated on the device across the calls, by the library or through torch
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == allocated0
