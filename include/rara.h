@@ -141,8 +141,10 @@ typedef struct rara_ctx rara_ctx;
  * tile list, does. The blend batch depth starts at 256 (rara_ctx_set_tiling). */
 int rara_ctx_create(size_t budget_bytes, int32_t tile_w, int32_t tile_h, rara_ctx **out);
 
-/* Tile shape (as for rara_ctx_create) and blend batch depth (128, 256 or 512 list entries
- * staged in shared memory per render batch) of the context's next frames and batches; the
+/* Tile shape (as for rara_ctx_create) and blend batch depth of the context's next frames and
+ * batches: 128, 256 or 512 list entries staged in shared memory by the whole block per render
+ * batch, or 32 for each warp staging and walking its own 32-entry chunks (no block barrier
+ * inside a work item); the
  * autotuner's knobs (the paper renders 16 x 16 tiles; the batch depth is this build's). The
  * current frame's state is dropped when the tile changes, and a captured graph is
  * recaptured on the next rara_render_batch_graph. RARA_ERR_INVALID_ARG for unsupported

@@ -4,9 +4,9 @@ Three knobs set how the render maps onto the GPU, none of which changes the imag
 float rounding order (with one lane per pixel, not even that):
   - the screen tile (rara_ctx_set_tiling): 8x8, 16x16, 32x8, 8x32, 32x16 or 16x32 pixels;
     smaller tiles give shorter lists and more (Gaussian, tile) pairs to sort;
-  - the blend batch depth: list entries staged in shared memory at a time (128, 256, 512);
-    deeper batches mean fewer block barriers and more staged entries a saturated pixel
-    never reads;
+  - the blend batch depth: list entries staged in shared memory at a time (128, 256, 512
+    by the whole block; deeper batches mean fewer block barriers and more staged entries a
+    saturated pixel never reads), or 32 per warp, each warp walking the list on its own;
   - the split thresholds (rara_ctx_set_tuning): a tile with a long list is split into work
     items with 2 or 4 lanes per pixel.
 Where each pays depends on the workload (list lengths, share of cutoff Gaussians,
@@ -25,7 +25,7 @@ import statistics
 from . import rara
 
 TILES = [(16, 16), (32, 8), (8, 32), (8, 8), (32, 16), (16, 32)]
-DEPTHS = [256, 128, 512]
+DEPTHS = [256, 32, 128, 512]
 # (split2_bits, split4_bits): a tile with >= 2^(bits-1) list entries is split
 CANDIDATES = [(33, 33), (13, 14), (12, 13), (11, 12), (10, 11), (11, 13), (10, 12), (9, 11)]
 DEFAULT = (16, 16, 256, 11, 12)

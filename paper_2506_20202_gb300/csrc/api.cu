@@ -39,7 +39,7 @@ struct rara_ctx {
     char err[512] = {0};
     int64_t launches = 0;
     int sm_count = 0, bpsm_sort = 0, bpsm_emit = 0, bpsm_compact = 0;
-    int bpsm_render[3] = {0, 0, 0};     // render blocks per SM for batch depths 128, 256, 512
+    int bpsm_render[4] = {0, 0, 0, 0};  // render blocks per SM for batch depths 32, 128, 256, 512
     int split2_bits = 11, split4_bits = 12;  // heavy-tile split thresholds (list length bit counts)
     int tile_w = kTile, tile_h = kTile;      // screen tile of the next batch
     int blend_depth = kBlock;                // list entries staged per render batch
@@ -210,7 +210,8 @@ void occupancy_setup(rara_ctx *c)
         cudaGetLastError();
         c->sm_count = 1;
     }
-    for (int k = 0; k < 3; ++k) c->bpsm_render[k] = render_blocks_per_sm(128 << k);
+    const int depths[4] = {32, 128, 256, 512};
+    for (int k = 0; k < 4; ++k) c->bpsm_render[k] = render_blocks_per_sm(depths[k]);
     c->bpsm_sort = sort_blocks_per_sm();
     c->bpsm_emit = emit_blocks_per_sm();
     c->bpsm_compact = compact_blocks_per_sm();
@@ -575,7 +576,7 @@ int batch_render(rara_ctx *c, cudaStream_t s)
     a.views = (const ViewDev *)c->views_d.p;
     a.num_views = c->num_views;
     a.counters = dc;
-    const int di = c->blend_depth == 128 ? 0 : (c->blend_depth == 512 ? 2 : 1);
+    const int di = c->blend_depth == 32 ? 0 : (c->blend_depth == 128 ? 1 : (c->blend_depth == 512 ? 3 : 2));
     const long long slots = (long long)c->sm_count * c->bpsm_render[di];
     const long long items = 4ll * c->num_tiles;
     // graph captures run without the work counters (their replays are not read for them)
@@ -768,7 +769,7 @@ int rara_ctx_set_tiling(rara_ctx *c, int32_t tile_w, int32_t tile_h, int32_t ble
         return fail(c, RARA_ERR_INVALID_ARG, "tile %dx%d is not one of 8x8, 16x16, 32x8, 8x32, 32x16, 16x32", tile_w,
                     tile_h);
     if (!batch_depth_ok(blend_depth))
-        return fail(c, RARA_ERR_INVALID_ARG, "blend batch depth %d is not 128, 256 or 512", blend_depth);
+        return fail(c, RARA_ERR_INVALID_ARG, "blend batch depth %d is not 32, 128, 256 or 512", blend_depth);
     if (!c->owns_host && (tile_w != kTile || tile_h != kTile || blend_depth != kBlock))
         return fail(c, RARA_ERR_INVALID_ARG, "the static context keeps 16x16 tiles and 256-entry batches");
     if (tile_w != c->tile_w || tile_h != c->tile_h) {

@@ -151,8 +151,9 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
     const int py = ty0 * TH + band * rows + wy0 + (lane >> 3);
     const bool inside = px < W && py < H && wy0 + (lane >> 3) < rows;
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-    const float rx0 = (float)(tx * TW + wx0) + 0.5f, rx1 = rx0 + 7.0f;
-    const float ry0 = (float)(ty0 * TH + band * rows + wy0) + 0.5f, ry1 = ry0 + 3.0f;
+    // the warp's rectangle of pixel centres: [rx0, rx0 + 7] x [ry0, ry0 + 3]
+    const float rx0 = (float)(tx * TW + wx0) + 0.5f;
+    const float ry0 = (float)(ty0 * TH + band * rows + wy0) + 0.5f;
     const int2 range = a.ranges[gtile];
 
     float T = 1.0f, dC0 = 0.0f, dC1 = 0.0f, dC2 = 0.0f;
@@ -196,7 +197,7 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
             const int lo = max(0, hi - 32);
             const int jt = lo + lane;
             bool keep = false;
-            if (jt < hi && (uint32_t)(bbeg - range.x + jt) < wlast) keep = entry_reaches(st, jt, rx0, rx1, ry0, ry1);
+            if (jt < hi && (uint32_t)(bbeg - range.x + jt) < wlast) keep = entry_reaches(st, jt, rx0, rx0 + 7.0f, ry0, ry0 + 3.0f);
             unsigned m = __ballot_sync(kFull, keep);
             while (m) {
                 const int b = 31 - __clz(m);
@@ -213,7 +214,7 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
                 float gc[16];  // cutoff record products (split weights only)
 #pragma unroll
                 for (int k = 0; k < 16; ++k) gc[k] = 0.f;
-                if (inside && pos < last) {
+                if (pos < last) {  // (last = 0 outside the image)
                     const float dx = pxf - s0.x, dy = pyf - s0.y;
                     const float q = splat_q(s0.z, s0.w, s1.x, dx, dy);
                     if (q <= s1.z) {

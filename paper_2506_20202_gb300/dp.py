@@ -44,7 +44,7 @@ def allreduce_sum(tensors, group=None):
 
 @dataclasses.dataclass
 class StepResult:
-    loss: float                 # summed over all ranks' views
+    loss: "torch.Tensor"        # [1], summed over all ranks' views (left on the device: no host wait)
     grads: dict                 # parameter name -> gradient, summed over all ranks (identical on every rank)
     plane_grads: dict           # view index -> dL/d(n, d) of this rank's views
     views: list                 # the view indices this rank rendered
@@ -59,7 +59,7 @@ def data_parallel_gradients(local_fn, num_views: int, rank: int, world: int, gro
     loss, grads, plane_grads = local_fn(mine)
     loss_t = torch.as_tensor(loss, dtype=grads[PARAMS[0]].dtype, device=grads[PARAMS[0]].device).reshape(1).clone()
     allreduce_sum([loss_t] + [grads[k] for k in PARAMS], group)
-    return StepResult(float(loss_t.item()), grads, plane_grads, mine)
+    return StepResult(loss_t, grads, plane_grads, mine)
 
 
 class GpuViews:
@@ -99,11 +99,14 @@ class GpuViews:
 
     def __call__(self, idx, events=None):
         """Loss and gradients of views idx; events (3 CUDA events or None) are recorded
-        after the forward, the loss gradient and the backward. The caller's current stream
-        is made to wait for the work (the all-reduce and the optimiser run there)."""
+        after the forward, the loss gradient and the backward. The work waits for the caller's
+        current stream first (the previous optimiser step ran there), and the caller's stream
+        is made to wait for it (the all-reduce and the optimiser run there)."""
         import torch
         rara = self.rara
         views, dimgs, pg = self._views(idx)
+        # the render reads the parameters the caller's stream last updated (the optimiser step)
+        self.stream.wait_stream(torch.cuda.current_stream())
         if not views:
             return torch.zeros((), device="cuda"), {k: getattr(self.grads, k).zero_() for k in PARAMS}, {}
         rara.rara_render_batch_graph(self.ctx, [self.scene], views, self.stream)

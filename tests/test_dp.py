@@ -61,7 +61,7 @@ def _rank(rank, world, port, q):
         from paper_2506_20202_gb300 import dp
         sc, views, weights = _workload()
         res = dp.data_parallel_gradients(_local_fn(sc, views, weights), len(views), rank, world)
-        q.put((rank, res.loss, {k: v.numpy() for k, v in res.grads.items()}, res.plane_grads, res.views))
+        q.put((rank, float(res.loss), {k: v.numpy() for k, v in res.grads.items()}, res.plane_grads, res.views))
         dist.barrier()
     finally:
         dist.destroy_process_group()

@@ -200,3 +200,59 @@ def test_general_scene_full_size_sampled_rows():
     rep, gpu, ref = full_check(scene, cam, pl, rows=(520, 552), max_flag_frac=0.05)
     assert rep["pixels"] == 32 * 1920
     assert gpu["info"]["n_cutoff"] > 1000
+
+
+def test_hair_workload_full_size_sampled_rows():
+    """The hair-strand workload at full size (500k strand Gaussians, 1024x1024, 40% of them
+    cutoff): every label, tile count and list checked; the image on a band of rows."""
+    sc, nrm, d = scenes.hair_scene(curves=10_000, segments=50, seed=0)
+    pl = scenes.Plane(np.asarray(nrm, np.float32), float(d), 3.0, scenes.MODE_RARA)
+    cam = scenes.look_at_camera((0.2, -0.3, -3.2), (0.0, 0.3, 0.0), 1024, 1024, 60.0)
+    rep, gpu, ref = full_check(sc, cam, pl, rows=(480, 512), max_flag_frac=0.08)
+    assert rep["pixels"] == 32 * 1024
+    assert gpu["info"]["n_cutoff"] > 0.3 * gpu["info"]["n_rendered"]
+
+
+def _batch_view(ctx, view, n):
+    """The exported state of one view of the context's last batch, as parity.gpu_frame gives it."""
+    from paper_2506_20202_gb300 import rara
+    r = rara.Renderer.__new__(rara.Renderer)
+    r.ctx = ctx
+    out = {"g": {k: v.cpu().numpy() for k, v in rara.Renderer.frame_gaussians(r, n, view).items()}}
+    keys, vals, ranges, info = rara.Renderer.frame_pairs(r, view)
+    out.update(keys=keys.cpu().numpy().view(np.uint64), vals=vals.cpu().numpy().view(np.uint32),
+               ranges=ranges.cpu().numpy(), info=info)
+    return out
+
+
+def test_shells_batch_full_size_two_views_sampled_rows():
+    """Two views of the 64-view differentiation batch over the 2.1M-Gaussian shell scene,
+    rendered as one batch: labels, tiles and lists of both views, and a band of each image."""
+    from paper_2506_20202_gb300 import rara
+    sc, _, vp = scenes.shells_training_workload(700_000, 64, seed=3)
+    gs = rara.GaussianTensors.from_scene(sc)
+    ctx = rara.rara_ctx_create(0)
+    try:
+        views = [rara.View(0, c, p, torch.empty((3, c.height, c.width), device="cuda"),
+                           torch.empty((c.height, c.width), device="cuda"),
+                           torch.empty((c.height, c.width), dtype=torch.int32, device="cuda")) for c, p in vp]
+        rara.rara_render_batch(ctx, [gs], views)
+        torch.cuda.synchronize()
+        for k in (1, 2):          # a 1024^2 and a 1920x1080 view
+            cam, pl = vp[k]
+            gpu = _batch_view(ctx, k, sc.n)
+            gpu["image"] = views[k].image.cpu().numpy().astype(np.float64)
+            gpu["T"] = views[k].final_T.cpu().numpy().astype(np.float64)
+            report = {}
+            pre = oracle.preprocess(sc, cam, pl)
+            kvr = oracle.build_keys(pre)
+            parity.check_gaussians(pre, gpu["g"], report)
+            parity.check_pairs(pre, kvr, gpu, report)
+            rows = (cam.height // 2 - 16, cam.height // 2 + 16)
+            ref = oracle.render(sc, pre, cam, pl, (0.0, 0.0, 0.0), kvr, rows=rows)
+            parity.check_image(pre, ref, gpu, report, rows=rows, max_flag_frac=0.05)
+            print(k, report)
+            assert report["pixels"] == 32 * cam.width
+            assert gpu["info"]["n_cutoff"] > 1000
+    finally:
+        rara.rara_ctx_destroy(ctx)

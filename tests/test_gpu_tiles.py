@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 # (tile_w, tile_h, blend batch depth)
 TILINGS = [(16, 16, 256), (32, 8, 256), (8, 32, 128), (8, 8, 512), (32, 16, 256), (16, 32, 512),
-           (16, 16, 128), (16, 16, 512)]
+           (16, 16, 128), (16, 16, 512), (16, 16, 32), (16, 32, 32), (8, 8, 32)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -76,7 +76,7 @@ def test_backward_is_the_same_for_every_tiling():
     rng = np.random.default_rng(1)
     dimgs = [torch.from_numpy(np.float32(rng.standard_normal((3, c.height, c.width)))).cuda() for c in cams]
     out = {}
-    for tiling in ((16, 16, 256), (8, 8, 128), (32, 16, 512), (8, 32, 256)):
+    for tiling in ((16, 16, 256), (8, 8, 128), (32, 16, 512), (8, 32, 256), (16, 32, 32)):
         ctx = rara.rara_ctx_create(0)
         try:
             rara.rara_ctx_set_tiling(ctx, *tiling)
@@ -124,7 +124,7 @@ def test_autotune_picks_a_supported_setting_that_matches_the_oracle():
 def test_unsupported_tilings_are_refused():
     ctx = rara.rara_ctx_create(0)
     try:
-        for bad in ((16, 8, 256), (64, 4, 256), (12, 12, 256), (16, 16, 64), (16, 16, 1024)):
+        for bad in ((16, 8, 256), (64, 4, 256), (12, 12, 256), (16, 16, 64), (16, 16, 1024), (16, 16, 16)):
             with pytest.raises(rara.RaraError) as e:
                 rara.rara_ctx_set_tiling(ctx, *bad)
             assert e.value.code == rara.RARA_ERR_INVALID_ARG

@@ -7,6 +7,7 @@ same frame as rara_render_frame. This file is collected last so that a run stopp
 first failure has run every other test; it also passes alone in a fresh process.
 """
 import dataclasses
+import gc
 
 import numpy as np
 import pytest
@@ -99,18 +100,29 @@ def test_noalloc_allocates_nothing_and_recovers_after_the_pair_limit():
     big = scenes.look_at_camera((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), 2048, 2048, 60.0)
     bimg, bT, bnc = _outputs(big)
     rara.rara_render_frame_noalloc(gs, cam, pl, (0, 0, 0), *out)   # set-up done before measuring
+    first = [torch.empty_like(t) for t in out]
+    gc.collect()
     torch.cuda.synchronize()
-    free0, allocated0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    free0 = torch.cuda.mem_get_info()[0]
+    count0 = torch.cuda.memory_stats()["allocation.all.allocated"]   # allocations made through torch
     with pytest.raises(rara.RaraError) as e:
         rara.rara_render_frame_noalloc(gw, big, pl, (0, 0, 0), bimg, bT, bnc)
     assert e.value.code == rara.RARA_ERR_BUDGET
-    for _ in range(2):          # the next calls render normally, over what the refused one left
-        out[0].fill_(-1.0)
-        rara.rara_render_frame_noalloc(gs, cam, pl, (0, 0, 0), *out)
-        torch.cuda.synchronize()
-        assert torch.equal(out[2], ref[2])
-        assert float((out[0] - ref[0]).abs().max()) <= IMG_MAX_ABS
-        assert float((out[1] - ref[1]).abs().max()) <= IMG_MAX_ABS
+    # the next calls render normally, over what the refused one left (in-place copies only, so
+    # nothing in this span allocates through torch either)
+    for t in out:
+        t.fill_(-1)
+    rara.rara_render_frame_noalloc(gs, cam, pl, (0, 0, 0), *out)
+    for a, b in zip(first, out):
+        a.copy_(b)
+    for t in out:
+        t.fill_(-1)
+    rara.rara_render_frame_noalloc(gs, cam, pl, (0, 0, 0), *out)
+    torch.cuda.synchronize()
     # nothing was allocated on the device across the calls, by the library or through torch
     assert torch.cuda.mem_get_info()[0] == free0
-    assert torch.cuda.memory_allocated() == allocated0
+    assert torch.cuda.memory_stats()["allocation.all.allocated"] == count0
+    for got in (first, out):
+        assert torch.equal(got[2], ref[2])
+        assert float((got[0] - ref[0]).abs().max()) <= IMG_MAX_ABS
+        assert float((got[1] - ref[1]).abs().max()) <= IMG_MAX_ABS
