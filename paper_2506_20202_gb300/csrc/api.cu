@@ -355,6 +355,17 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
             vd.image = views[v].image;
             vd.final_T = views[v].final_T;
             vd.n_contrib = views[v].n_contrib;
+            // views of one scene with the same camera share the preprocess's projection
+            const rara_camera &cm = views[v].camera;
+            vd.same_cam = 0;
+            if (k > sd.view_begin) {
+                const ViewDev &pv = c->h_views[k - 1];
+                bool same = pv.cam.W == cm.width && pv.cam.H == cm.height && pv.cam.fx == cm.fx &&
+                            pv.cam.fy == cm.fy && pv.cam.cx == cm.cx && pv.cam.cy == cm.cy;
+                for (int q = 0; q < 9 && same; ++q) same = pv.cam.R[q] == vd.cam.R[q];
+                for (int q = 0; q < 3 && same; ++q) same = pv.cam.t[q] == vd.cam.t[q];
+                vd.same_cam = same ? 1 : 0;
+            }
             c->h_view_map[v] = k;
             c->h_view_n[k] = (int)g.n;
             slots += (uint64_t)g.n;

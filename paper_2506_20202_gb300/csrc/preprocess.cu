@@ -121,6 +121,119 @@ __device__ __forceinline__ void sh_colour(const float *s_sh, int degree, float x
 
 constexpr int kViewChunk = 16;  // views staged in shared memory at a time
 
+// The camera's part of a rendered slot: rectangle, splat-record terms, colour and depth key.
+// ntiles = 0 when the projection culls the Gaussian (centre behind the near plane, singular 2D
+// covariance, no tile of the image in its rectangle).
+struct Proj {
+    uint32_t ntiles;
+    uint2 rect;
+    float4 r0;            // (mean2d.x, mean2d.y, conic.a, conic.b)
+    float r1x;            // conic.c
+    float rgb0, rgb1, rgb2;
+    float nbc, nba;       // b / c and b / a of the dilated covariance (the record's line minimisers)
+    float depth;
+};
+constexpr int kProjWords = 14;
+
+// Eq. 9-10 for one Gaussian and camera: Sigma2 = (J W M)(J W M)^T + 0.3 I with M = R S and J
+// the affine approximation of the projection at the centre (x/z, y/z clamped); the tile
+// rectangle of the q <= 9 ellipse; the SH colour at normalize(mu - e); the depth key.
+__device__ __forceinline__ void project(Proj &pj, const ViewDev &vw, const CamDev &cam, float mx, float my, float mz,
+                                        const float Rg[9], const float sg[3], const float *s_sh, int sh_degree,
+                                        Counters *counters)
+{
+    pj.ntiles = 0;
+    const float tx = fmaf(cam.R[0], mx, fmaf(cam.R[1], my, fmaf(cam.R[2], mz, cam.t[0])));
+    const float ty = fmaf(cam.R[3], mx, fmaf(cam.R[4], my, fmaf(cam.R[5], mz, cam.t[1])));
+    const float tz = fmaf(cam.R[6], mx, fmaf(cam.R[7], my, fmaf(cam.R[8], mz, cam.t[2])));
+    if (!(tz > kNearZ)) return;
+    const float itz = 1.0f / tz;
+    const float limx = 1.3f * (0.5f * cam.W / cam.fx), limy = 1.3f * (0.5f * cam.H / cam.fy);
+    const float txz = fminf(limx, fmaxf(-limx, tx * itz));
+    const float tyz = fminf(limy, fmaxf(-limy, ty * itz));
+    const float J00 = cam.fx * itz, J02 = -cam.fx * txz * itz;
+    const float J11 = cam.fy * itz, J12 = -cam.fy * tyz * itz;
+    float T0[3], T1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T0[k] = fmaf(J00, cam.R[k], J02 * cam.R[6 + k]);
+        T1[k] = fmaf(J11, cam.R[3 + k], J12 * cam.R[6 + k]);
+    }
+    float A0[3], A1[3];  // rows of J W R S
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        A0[k] = (T0[0] * Rg[k] + T0[1] * Rg[3 + k] + T0[2] * Rg[6 + k]) * sg[k];
+        A1[k] = (T1[0] * Rg[k] + T1[1] * Rg[3 + k] + T1[2] * Rg[6 + k]) * sg[k];
+    }
+    const float a0 = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2];
+    const float b0 = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
+    const float c0 = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2];
+    // det((A A^T) + 0.3 I) = |A0 x A1|^2 + 0.3 (a0 + c0) + 0.09: every term is non-negative,
+    // so elongated splats keep their precision.
+    const float x0 = A0[1] * A1[2] - A0[2] * A1[1];
+    const float x1 = A0[2] * A1[0] - A0[0] * A1[2];
+    const float x2 = A0[0] * A1[1] - A0[1] * A1[0];
+    const float ca = a0 + kDilation, cb = b0, cc = c0 + kDilation;
+    const float det = (x0 * x0 + x1 * x1 + x2 * x2) + kDilation * (a0 + c0) + kDilation * kDilation;
+    if (!(det > 0.0f)) return;
+    const float idet = 1.0f / det;
+    const float mx2 = fmaf(cam.fx, tx * itz, cam.cx);
+    const float my2 = fmaf(cam.fy, ty * itz, cam.cy);
+    // Tile rectangle: axis-aligned box of the q <= 9 ellipse; tile edges are powers of two, so
+    // the products are the exact quotients
+    const float hx = 3.0f * sqrtf(ca), hy = 3.0f * sqrtf(cc);
+    const float itw = 1.0f / (float)vw.tile_w, ith = 1.0f / (float)vw.tile_h;
+    const float fx0 = floorf((mx2 - hx) * itw), fx1 = floorf((mx2 + hx) * itw);
+    const float fy0 = floorf((my2 - hy) * ith), fy1 = floorf((my2 + hy) * ith);
+    const int rx0 = (int)fmaxf(0.0f, fminf((float)vw.tiles_x, fx0));
+    const int rx1 = (int)fmaxf(-1.0f, fminf((float)(vw.tiles_x - 1), fx1));
+    const int ry0 = (int)fmaxf(0.0f, fminf((float)vw.tiles_y, fy0));
+    const int ry1 = (int)fmaxf(-1.0f, fminf((float)(vw.tiles_y - 1), fy1));
+    if (!(rx0 <= rx1 && ry0 <= ry1)) return;
+    pj.ntiles = (uint32_t)((rx1 - rx0 + 1) * (ry1 - ry0 + 1));
+    pj.rect = make_uint2((uint32_t)rx0 | ((uint32_t)ry0 << 16), (uint32_t)rx1 | ((uint32_t)ry1 << 16));
+    // colour at normalize(mu - e)
+    const float ex = mx - cam.eye[0], ey = my - cam.eye[1], ez = mz - cam.eye[2];
+    const float il = rsqrtf(ex * ex + ey * ey + ez * ez);
+    float rgb[3];
+    sh_colour(s_sh, sh_degree, ex * il, ey * il, ez * il, rgb);
+    if (!isfinite(rgb[0] + rgb[1] + rgb[2])) atomicOr(&counters->status, kStatusBadInput);
+    pj.r0 = make_float4(mx2, my2, cc * idet, -cb * idet);
+    pj.r1x = ca * idet;
+    pj.rgb0 = rgb[0];
+    pj.rgb1 = rgb[1];
+    pj.rgb2 = rgb[2];
+    pj.nbc = cb / cc;
+    pj.nba = cb / ca;
+    // The sort key holds the depth rounded once from a dot product carried in doubled
+    // float32 precision (dot2), i.e. the correctly rounded float32 of the exact depth except
+    // within about 2^-48 of a rounding midpoint.
+    pj.depth = dot2_depth(cam.R[6], cam.R[7], cam.R[8], cam.t[2], mx, my, mz);
+}
+
+// This thread's column of the projection cache (kProjWords words, stride kBlock).
+__device__ __forceinline__ void store_proj(float (*c)[kBlock], const Proj &p)
+{
+    const int t = threadIdx.x;
+    c[0][t] = __uint_as_float(p.ntiles);
+    if (!p.ntiles) return;
+    c[1][t] = __uint_as_float(p.rect.x); c[2][t] = __uint_as_float(p.rect.y);
+    c[3][t] = p.r0.x; c[4][t] = p.r0.y; c[5][t] = p.r0.z; c[6][t] = p.r0.w;
+    c[7][t] = p.r1x; c[8][t] = p.rgb0; c[9][t] = p.rgb1; c[10][t] = p.rgb2;
+    c[11][t] = p.nbc; c[12][t] = p.nba; c[13][t] = p.depth;
+}
+
+__device__ __forceinline__ void load_proj(float (*c)[kBlock], Proj &p)
+{
+    const int t = threadIdx.x;
+    p.ntiles = __float_as_uint(c[0][t]);
+    if (!p.ntiles) return;
+    p.rect = make_uint2(__float_as_uint(c[1][t]), __float_as_uint(c[2][t]));
+    p.r0 = make_float4(c[3][t], c[4][t], c[5][t], c[6][t]);
+    p.r1x = c[7][t]; p.rgb0 = c[8][t]; p.rgb1 = c[9][t]; p.rgb2 = c[10][t];
+    p.nbc = c[11][t]; p.nba = c[12][t]; p.depth = c[13][t];
+}
+
 // One block = one unit of 256 Gaussians of one scene. The Gaussians' attributes are read
 // once (the SH coefficients into shared memory, all loads of a thread issued together) and
 // every view of the scene is processed from registers and shared memory; the views' tables
@@ -129,10 +242,14 @@ constexpr int kViewChunk = 16;  // views staged in shared memory at a time
 // MINB: blocks per SM the register budget is sized for. With many views per Gaussian the
 // per-view loop is arithmetic and wants every register (3 blocks); with few views the kernel
 // streams the scene and wants warps in flight (4 blocks).
-template <int MINB>
+// CACHE: keep the camera's part of each slot in shared memory across consecutive views with
+// the same camera (the batches of many views use it; a single view has nothing to reuse).
+template <int MINB, bool CACHE>
 __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
 {
     extern __shared__ __align__(16) float s_sh[];  // [3 (degree+1)^2][kBlock]
+    __shared__ float s_pc[CACHE ? kProjWords : 1][kBlock];
+    bool cam_ok = false;                            // s_pc holds this thread's slot for the view's camera
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ ViewDev s_views[kViewChunk];
     __shared__ unsigned long long s_cnt[3][kViewChunk];
@@ -216,6 +333,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
             const CamDev &cam = vw.cam;
             bool rendered = false, cutoff = false;
             uint32_t ntiles = 0;
+            if (CACHE && !vw.same_cam) cam_ok = false;
             if (valid) {
                 const uint32_t slot = vw.slot_base + (uint32_t)i;
                 // Section 3.2 / Algorithm 1 step 1: d_ep = n.mu + d, r = 3 max(sigma)
@@ -243,172 +361,128 @@ __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
                 }
                 a.labels[slot] = (uint8_t)label;
 
-                const float tx = fmaf(cam.R[0], mx, fmaf(cam.R[1], my, fmaf(cam.R[2], mz, cam.t[0])));
-                const float ty = fmaf(cam.R[3], mx, fmaf(cam.R[4], my, fmaf(cam.R[5], mz, cam.t[1])));
-                const float tz = fmaf(cam.R[6], mx, fmaf(cam.R[7], my, fmaf(cam.R[8], mz, cam.t[2])));
-
-                if (label != RARA_INVISIBLE && tz > kNearZ) {
-                    // Eq. 9-10: Sigma2 = (J W M)(J W M)^T + 0.3 I with M = R S and J the affine
-                    // approximation of the projection at the centre (x/z, y/z clamped).
-                    const float itz = 1.0f / tz;
-                    const float limx = 1.3f * (0.5f * cam.W / cam.fx), limy = 1.3f * (0.5f * cam.H / cam.fy);
-                    const float txz = fminf(limx, fmaxf(-limx, tx * itz));
-                    const float tyz = fminf(limy, fmaxf(-limy, ty * itz));
-                    const float J00 = cam.fx * itz, J02 = -cam.fx * txz * itz;
-                    const float J11 = cam.fy * itz, J12 = -cam.fy * tyz * itz;
-                    float T0[3], T1[3];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        T0[k] = fmaf(J00, cam.R[k], J02 * cam.R[6 + k]);
-                        T1[k] = fmaf(J11, cam.R[3 + k], J12 * cam.R[6 + k]);
-                    }
-                    float A0[3], A1[3];  // rows of J W R S
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        A0[k] = (T0[0] * Rg[k] + T0[1] * Rg[3 + k] + T0[2] * Rg[6 + k]) * sg[k];
-                        A1[k] = (T1[0] * Rg[k] + T1[1] * Rg[3 + k] + T1[2] * Rg[6 + k]) * sg[k];
-                    }
-                    const float a0 = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2];
-                    const float b0 = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
-                    const float c0 = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2];
-                    // det((A A^T) + 0.3 I) = |A0 x A1|^2 + 0.3 (a0 + c0) + 0.09: every term is
-                    // non-negative, so elongated splats keep their precision.
-                    const float x0 = A0[1] * A1[2] - A0[2] * A1[1];
-                    const float x1 = A0[2] * A1[0] - A0[0] * A1[2];
-                    const float x2 = A0[0] * A1[1] - A0[1] * A1[0];
-                    const float ca = a0 + kDilation, cb = b0, cc = c0 + kDilation;
-                    const float det = (x0 * x0 + x1 * x1 + x2 * x2) + kDilation * (a0 + c0) + kDilation * kDilation;
-                    if (det > 0.0f) {
-                        const float idet = 1.0f / det;
-                        const float mx2 = fmaf(cam.fx, tx * itz, cam.cx);
-                        const float my2 = fmaf(cam.fy, ty * itz, cam.cy);
-                        // Tile rectangle: axis-aligned box of the q <= 9 ellipse
-                        const float hx = 3.0f * sqrtf(ca), hy = 3.0f * sqrtf(cc);
-                        // tile edges are powers of two: the products are the exact quotients
-                        const float itw = 1.0f / (float)vw.tile_w, ith = 1.0f / (float)vw.tile_h;
-                        const float fx0 = floorf((mx2 - hx) * itw), fx1 = floorf((mx2 + hx) * itw);
-                        const float fy0 = floorf((my2 - hy) * ith), fy1 = floorf((my2 + hy) * ith);
-                        const int rx0 = (int)fmaxf(0.0f, fminf((float)vw.tiles_x, fx0));
-                        const int rx1 = (int)fmaxf(-1.0f, fminf((float)(vw.tiles_x - 1), fx1));
-                        const int ry0 = (int)fmaxf(0.0f, fminf((float)vw.tiles_y, fy0));
-                        const int ry1 = (int)fmaxf(-1.0f, fminf((float)(vw.tiles_y - 1), fy1));
-                        if (rx0 <= rx1 && ry0 <= ry1) {
-                            ntiles = (uint32_t)((rx1 - rx0 + 1) * (ry1 - ry0 + 1));
-                            rendered = true;
-                            cutoff = label == RARA_CUTOFF;
-                            a.rect[slot] = make_uint2((uint32_t)rx0 | ((uint32_t)ry0 << 16),
-                                                      (uint32_t)rx1 | ((uint32_t)ry1 << 16));
-                            // colour at normalize(mu - e)
-                            const float ex = mx - cam.eye[0], ey = my - cam.eye[1], ez = mz - cam.eye[2];
-                            const float il = rsqrtf(ex * ex + ey * ey + ez * ez);
-                            float rgb[3];
-                            sh_colour(s_sh, sc.sh_degree, ex * il, ey * il, ez * il, rgb);
-                            if (!isfinite(rgb[0] + rgb[1] + rgb[2])) atomicOr(&a.counters->status, kStatusBadInput);
-                            SplatRec rec;
-                            rec.r0 = make_float4(mx2, my2, cc * idet, -cb * idet);
-                            rec.r1 = make_float4(ca * idet, op, rgb[0], rgb[1]);
-                            float wmode = 0.0f;
-                            // The sort key holds the depth rounded once from a dot product
-                            // carried in doubled float32 precision (dot2), i.e. the correctly
-                            // rounded float32 of the exact depth except within about 2^-48 of
-                            // a rounding midpoint.
-                            a.depth[slot] = dot2_depth(cam.R[6], cam.R[7], cam.R[8], cam.t[2], mx, my, mz);
-
-                            if (cutoff) {
-                                // Ray-tracing record in the unit-sphere frame of M = k R S
-                                // (Eq. 4): M^-1 = diag(1/(k sigma)) R^T. For the pixel ray with
-                                // offset (dx, dy) from the projected centre, the local ray is
-                                // o + tau V with o = -G, V = G + P (dx, dy): G = M^-1 (mu - e) and
-                                // P = z M^-1 W^T[:, 0:2] diag(1/fx, 1/fy). m = M^T n carries the
-                                // plane into the same frame: s(x) = d_ep + m . u for x = mu + M u.
-                                const float kk = pl.k;
-                                const float iks[3] = {1.0f / (kk * s0), 1.0f / (kk * s1), 1.0f / (kk * s2)};
-                                float G[3], Px[3], Py[3], m[3];
-                                const float sx = tz / cam.fx, sy = tz / cam.fy;
-#pragma unroll
-                                for (int k = 0; k < 3; ++k) {
-                                    const float rk0 = Rg[k], rk1 = Rg[3 + k], rk2 = Rg[6 + k];  // column k of R
-                                    G[k] = iks[k] * (rk0 * ex + rk1 * ey + rk2 * ez);
-                                    Px[k] = iks[k] * sx * (rk0 * cam.R[0] + rk1 * cam.R[1] + rk2 * cam.R[2]);
-                                    Py[k] = iks[k] * sy * (rk0 * cam.R[3] + rk1 * cam.R[4] + rk2 * cam.R[5]);
-                                    m[k] = kk * sg[k] * (rk0 * pl.n[0] + rk1 * pl.n[1] + rk2 * pl.n[2]);
-                                }
-                                // The plane meets the ellipsoid only if |d_ep| <= |m| (s varies by
-                                // at most |m| over the unit ball). Beyond that (with a margin over
-                                // rounding) every chord lies on one side: w = 1 for every ray when
-                                // it is the visible side, and w = 0 for rays that hit the ellipsoid
-                                // in front (1 for the others) when it is the invisible side.
-                                const float mlen = sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
-                                const float bound = mlen * (1.0f + 1e-4f);
-                                wmode = dep > bound ? kWeightNone : (dep < -bound ? kWeightHidden : kWeightSplit);
-                                // Convex clip volume: a plane wholly in front of the ellipsoid
-                                // constrains no chord and drops out; one wholly behind it hides
-                                // it (w = 0 where a ray hits it in front); the splitting planes
-                                // clip the chord. The first splitting plane takes the CutRec's
-                                // plane terms, the others the slot's CutExtra.
-                                float xs[3][4] = {};
-                                int nsplit = wmode == kWeightSplit ? 1 : 0;
-                                float sdep = dep;
-                                for (int e = 0; e < pl.n_extra; ++e) {
-                                    float me[3];
-#pragma unroll
-                                    for (int k = 0; k < 3; ++k)
-                                        me[k] = kk * sg[k] * (Rg[k] * pl.ex[e][0] + Rg[3 + k] * pl.ex[e][1] +
-                                                              Rg[6 + k] * pl.ex[e][2]);
-                                    const float de = fmaf(pl.ex[e][0], mx,
-                                                          fmaf(pl.ex[e][1], my, fmaf(pl.ex[e][2], mz, pl.ex[e][3])));
-                                    const float be = sqrtf(me[0] * me[0] + me[1] * me[1] + me[2] * me[2]) * (1.0f + 1e-4f);
-                                    if (de < -be) {
-                                        wmode = kWeightHidden;
-                                    } else if (de <= be) {
-                                        if (nsplit == 0) {
-                                            sdep = de;
-#pragma unroll
-                                            for (int k = 0; k < 3; ++k) m[k] = me[k];
-                                        } else {
-                                            xs[nsplit - 1][0] = de;
-#pragma unroll
-                                            for (int k = 0; k < 3; ++k) xs[nsplit - 1][1 + k] = me[k];
-                                        }
-                                        ++nsplit;
-                                    }
-                                }
-                                if (pl.n_extra > 0 && wmode != kWeightHidden)
-                                    wmode = nsplit == 0 ? kWeightNone : (nsplit == 1 ? kWeightSplit : kWeightMulti);
-                                // With the camera inside (or on) the ellipsoid, G.G <= 1, the
-                                // roots of every ray have product (G.G - 1) / V.V <= 0: no ray
-                                // meets it twice in front, so w = 1 for every ray.
-                                const float GG = dot3(G, G);
-                                if (!(GG > 1.0f)) wmode = kWeightNone;
-                                if (wmode != kWeightNone) {
-                                    // The render needs, per pixel, p = P (dx, dy) only through the
-                                    // dot products G.p, p.p, m.p and the cross product p x G: store
-                                    // the pairwise products of G, Px, Py, m and A = Px x G, B = Py x G.
-                                    CutRec c;
-                                    c.c0 = make_float4(GG, dot3(G, Px), dot3(G, Py), sdep);
-                                    c.c1 = make_float4(dot3(Px, Px), dot3(Px, Py), dot3(Py, Py), dot3(m, G));
-                                    float A[3], B[3];
-                                    cross3(Px, G, A);
-                                    cross3(Py, G, B);
-                                    c.c2 = make_float4(dot3(m, Px), dot3(m, Py), A[0], A[1]);
-                                    c.c3 = make_float4(A[2], B[0], B[1], B[2]);
-                                    a.cut[slot] = c;
-                                    if (wmode == kWeightMulti) {
-                                        CutExtra x;
-#pragma unroll
-                                        for (int e = 0; e < 3; ++e) {
-                                            const float *me = &xs[e][1];
-                                            x.p[e] = e + 1 < nsplit
-                                                         ? make_float4(xs[e][0], dot3(me, G), dot3(me, Px), dot3(me, Py))
-                                                         : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
-                                        }
-                                        a.cut_x[slot] = x;
-                                    }
-                                }
-                            }
-                            rec.r2 = make_float4(rgb[2], wmode, cb / cc, cb / ca);
-                            a.rec[slot] = rec;
+                if (label != RARA_INVISIBLE) {
+                    // The camera's part of the slot (projection, rectangle, colour, depth key)
+                    // does not depend on the plane: with CACHE it is computed once per run of
+                    // views with the same camera (a plane sweep from one viewpoint) and kept in
+                    // this thread's column of the shared cache; the values are the same either way.
+                    Proj pj;
+                    if (!CACHE || !cam_ok) {
+                        project(pj, vw, cam, mx, my, mz, Rg, sg, s_sh, sc.sh_degree, a.counters);
+                        if (CACHE) {
+                            store_proj(s_pc, pj);
+                            cam_ok = true;
                         }
+                    } else {
+                        load_proj(s_pc, pj);
+                    }
+                    if (pj.ntiles) {
+                        ntiles = pj.ntiles;
+                        rendered = true;
+                        cutoff = label == RARA_CUTOFF;
+                        a.rect[slot] = pj.rect;
+                        SplatRec rec;
+                        rec.r0 = pj.r0;
+                        rec.r1 = make_float4(pj.r1x, op, pj.rgb0, pj.rgb1);
+                        float wmode = 0.0f;
+                        a.depth[slot] = pj.depth;
+                    if (cutoff) {
+                        // the camera-space centre and the eye offset again (not cached)
+                        const float tz = fmaf(cam.R[6], mx, fmaf(cam.R[7], my, fmaf(cam.R[8], mz, cam.t[2])));
+                        const float ex = mx - cam.eye[0], ey = my - cam.eye[1], ez = mz - cam.eye[2];
+                        // Ray-tracing record in the unit-sphere frame of M = k R S
+                        // (Eq. 4): M^-1 = diag(1/(k sigma)) R^T. For the pixel ray with
+                        // offset (dx, dy) from the projected centre, the local ray is
+                        // o + tau V with o = -G, V = G + P (dx, dy): G = M^-1 (mu - e) and
+                        // P = z M^-1 W^T[:, 0:2] diag(1/fx, 1/fy). m = M^T n carries the
+                        // plane into the same frame: s(x) = d_ep + m . u for x = mu + M u.
+                        const float kk = pl.k;
+                        const float iks[3] = {1.0f / (kk * s0), 1.0f / (kk * s1), 1.0f / (kk * s2)};
+                        float G[3], Px[3], Py[3], m[3];
+                        const float sx = tz / cam.fx, sy = tz / cam.fy;
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const float rk0 = Rg[k], rk1 = Rg[3 + k], rk2 = Rg[6 + k];  // column k of R
+                            G[k] = iks[k] * (rk0 * ex + rk1 * ey + rk2 * ez);
+                            Px[k] = iks[k] * sx * (rk0 * cam.R[0] + rk1 * cam.R[1] + rk2 * cam.R[2]);
+                            Py[k] = iks[k] * sy * (rk0 * cam.R[3] + rk1 * cam.R[4] + rk2 * cam.R[5]);
+                            m[k] = kk * sg[k] * (rk0 * pl.n[0] + rk1 * pl.n[1] + rk2 * pl.n[2]);
+                        }
+                        // The plane meets the ellipsoid only if |d_ep| <= |m| (s varies by
+                        // at most |m| over the unit ball). Beyond that (with a margin over
+                        // rounding) every chord lies on one side: w = 1 for every ray when
+                        // it is the visible side, and w = 0 for rays that hit the ellipsoid
+                        // in front (1 for the others) when it is the invisible side.
+                        const float mlen = sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+                        const float bound = mlen * (1.0f + 1e-4f);
+                        wmode = dep > bound ? kWeightNone : (dep < -bound ? kWeightHidden : kWeightSplit);
+                        // Convex clip volume: a plane wholly in front of the ellipsoid
+                        // constrains no chord and drops out; one wholly behind it hides
+                        // it (w = 0 where a ray hits it in front); the splitting planes
+                        // clip the chord. The first splitting plane takes the CutRec's
+                        // plane terms, the others the slot's CutExtra.
+                        float xs[3][4] = {};
+                        int nsplit = wmode == kWeightSplit ? 1 : 0;
+                        float sdep = dep;
+                        for (int e = 0; e < pl.n_extra; ++e) {
+                            float me[3];
+#pragma unroll
+                            for (int k = 0; k < 3; ++k)
+                                me[k] = kk * sg[k] * (Rg[k] * pl.ex[e][0] + Rg[3 + k] * pl.ex[e][1] +
+                                                      Rg[6 + k] * pl.ex[e][2]);
+                            const float de = fmaf(pl.ex[e][0], mx,
+                                                  fmaf(pl.ex[e][1], my, fmaf(pl.ex[e][2], mz, pl.ex[e][3])));
+                            const float be = sqrtf(me[0] * me[0] + me[1] * me[1] + me[2] * me[2]) * (1.0f + 1e-4f);
+                            if (de < -be) {
+                                wmode = kWeightHidden;
+                            } else if (de <= be) {
+                                if (nsplit == 0) {
+                                    sdep = de;
+#pragma unroll
+                                    for (int k = 0; k < 3; ++k) m[k] = me[k];
+                                } else {
+                                    xs[nsplit - 1][0] = de;
+#pragma unroll
+                                    for (int k = 0; k < 3; ++k) xs[nsplit - 1][1 + k] = me[k];
+                                }
+                                ++nsplit;
+                            }
+                        }
+                        if (pl.n_extra > 0 && wmode != kWeightHidden)
+                            wmode = nsplit == 0 ? kWeightNone : (nsplit == 1 ? kWeightSplit : kWeightMulti);
+                        // With the camera inside (or on) the ellipsoid, G.G <= 1, the
+                        // roots of every ray have product (G.G - 1) / V.V <= 0: no ray
+                        // meets it twice in front, so w = 1 for every ray.
+                        const float GG = dot3(G, G);
+                        if (!(GG > 1.0f)) wmode = kWeightNone;
+                        if (wmode != kWeightNone) {
+                            // The render needs, per pixel, p = P (dx, dy) only through the
+                            // dot products G.p, p.p, m.p and the cross product p x G: store
+                            // the pairwise products of G, Px, Py, m and A = Px x G, B = Py x G.
+                            CutRec c;
+                            c.c0 = make_float4(GG, dot3(G, Px), dot3(G, Py), sdep);
+                            c.c1 = make_float4(dot3(Px, Px), dot3(Px, Py), dot3(Py, Py), dot3(m, G));
+                            float A[3], B[3];
+                            cross3(Px, G, A);
+                            cross3(Py, G, B);
+                            c.c2 = make_float4(dot3(m, Px), dot3(m, Py), A[0], A[1]);
+                            c.c3 = make_float4(A[2], B[0], B[1], B[2]);
+                            a.cut[slot] = c;
+                            if (wmode == kWeightMulti) {
+                                CutExtra x;
+#pragma unroll
+                                for (int e = 0; e < 3; ++e) {
+                                    const float *me = &xs[e][1];
+                                    x.p[e] = e + 1 < nsplit
+                                                 ? make_float4(xs[e][0], dot3(me, G), dot3(me, Px), dot3(me, Py))
+                                                 : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+                                }
+                                a.cut_x[slot] = x;
+                            }
+                        }
+                    }
+                        rec.r2 = make_float4(pj.rgb2, wmode, pj.nbc, pj.nba);
+                        a.rec[slot] = rec;
                     }
                 }
                 a.tiles[slot] = ntiles;
@@ -528,9 +602,9 @@ __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
 int preprocess_configure()
 {
     const int most = 3 * 16 * kBlock * (int)sizeof(float);  // SH degree 3
-    const bool ok = cudaFuncSetAttribute(k_preprocess<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) ==
+    const bool ok = cudaFuncSetAttribute(k_preprocess<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) ==
                         cudaSuccess &&
-                    cudaFuncSetAttribute(k_preprocess<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) ==
+                    cudaFuncSetAttribute(k_preprocess<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) ==
                         cudaSuccess;
     return ok ? 0 : -1;
 }
@@ -539,8 +613,8 @@ void launch_preprocess(const PreprocessArgs &a, int grid, int max_sh_degree, int
 {
     const int smem = 3 * (max_sh_degree + 1) * (max_sh_degree + 1) * kBlock * (int)sizeof(float);
     if (grid <= 0) return;
-    if (max_views >= 4) k_preprocess<3><<<grid, kBlock, smem, s>>>(a);
-    else k_preprocess<4><<<grid, kBlock, smem, s>>>(a);
+    if (max_views >= 4) k_preprocess<3, true><<<grid, kBlock, smem, s>>>(a);
+    else k_preprocess<4, false><<<grid, kBlock, smem, s>>>(a);
 }
 
 int compact_blocks_per_sm()

@@ -112,6 +112,7 @@ struct ViewDev {
     PlaneDev plane;
     int scene;
     int tile_w, tile_h;   // screen tile (the batch's tile shape: 64, 256 or 512 pixels)
+    int same_cam;         // 1 if the previous view of the same scene has the same camera
     int tiles_x, tiles_y;
     uint32_t tile_base;   // first global tile id of the view (view << tile_bits)
     uint32_t slot_base;   // first dense (view, Gaussian) slot of the view

@@ -136,3 +136,31 @@ def test_graph_overflow_is_reported_and_recovers():
         for x, y in zip(a[0], ref[0]):
             assert np.array_equal(x, y)
     r.close()
+
+
+def test_plane_sweep_from_one_camera_equals_single_renders():
+    """Views that share a camera reuse the preprocess's projection (a plane sweep from one
+    viewpoint): every view must still equal the view rendered alone bit for bit, including a
+    view with another camera in the middle of the run and views whose mode labels a Gaussian
+    invisible for one plane and visible for the next."""
+    sc = scenes.general_scene(20_000, seed=7, sh_degree=3)
+    cam = scenes.look_at_camera((0.4, -0.6, -2.8), (0.0, 0.0, 0.0), 200, 136, 60.0)
+    other = scenes.look_at_camera((-1.5, 0.3, -2.5), (0.0, 0.0, 0.0), 200, 136, 60.0)
+    nrm = np.float32(scenes.random_unit_normal(5))
+    offs = np.linspace(-0.8, 0.8, 9)
+    modes = [scenes.MODE_RARA, scenes.MODE_HARD, scenes.MODE_RARA, scenes.MODE_NONE, scenes.MODE_RARA_ALL,
+             scenes.MODE_RARA, scenes.MODE_RARA, scenes.MODE_HARD, scenes.MODE_RARA]
+    views = [(0, other if k == 4 else cam, scenes.Plane(nrm, float(d), 3.0, m), (0.1, 0.0, 0.2))
+             for k, (d, m) in enumerate(zip(offs, modes))]
+    gs = [rara.GaussianTensors.from_scene(sc)]
+    r = rara.Renderer()
+    try:
+        got = _render_batch(r, gs, views)
+        for (si, c, pl, bg), (img, T, nc) in zip(views, got):
+            i0, T0, n0 = _outputs(c)
+            r.render(gs[0], c, pl, bg, out=(i0, T0, n0))
+            torch.cuda.synchronize()
+            assert np.array_equal(img, i0.cpu().numpy()) and np.array_equal(T, T0.cpu().numpy())
+            assert np.array_equal(nc, n0.cpu().numpy())
+    finally:
+        r.close()

@@ -217,15 +217,24 @@ def test_hair_workload_full_size_sampled_rows():
 
 
 def _batch_view(ctx, view, n):
-    """The exported state of one view of the context's last batch, as parity.gpu_frame gives it."""
+    """The exported state of one view of the context's last batch, as parity.gpu_frame gives it
+    (the context stays owned by the caller)."""
     from paper_2506_20202_gb300 import rara
-    r = rara.Renderer.__new__(rara.Renderer)
-    r.ctx = ctx
-    out = {"g": {k: v.cpu().numpy() for k, v in rara.Renderer.frame_gaussians(r, n, view).items()}}
-    keys, vals, ranges, info = rara.Renderer.frame_pairs(r, view)
-    out.update(keys=keys.cpu().numpy().view(np.uint64), vals=vals.cpu().numpy().view(np.uint32),
-               ranges=ranges.cpu().numpy(), info=info)
-    return out
+    dev = "cuda"
+    g = dict(labels=torch.zeros(n, dtype=torch.uint8, device=dev), depth=torch.zeros(n, device=dev),
+             mean2d=torch.zeros((2, n), device=dev), conic=torch.zeros((3, n), device=dev),
+             rgb=torch.zeros((3, n), device=dev), opacity=torch.zeros(n, device=dev),
+             rect=torch.zeros((4, n), dtype=torch.int32, device=dev), tiles=torch.zeros(n, dtype=torch.int32, device=dev))
+    rara.rara_frame_gaussians(ctx, view, **g)
+    info = rara.rara_frame_info_get(ctx, view)
+    p, nt = int(info["n_pairs"]), info["tiles_x"] * info["tiles_y"]
+    keys = torch.zeros(max(p, 1), dtype=torch.int64, device=dev)
+    vals = torch.zeros(max(p, 1), dtype=torch.int32, device=dev)
+    ranges = torch.zeros((nt, 2), dtype=torch.int64, device=dev)
+    rara.rara_frame_pairs(ctx, view, keys, vals, ranges)
+    torch.cuda.synchronize()
+    return {"g": {k: v.cpu().numpy() for k, v in g.items()}, "keys": keys[:p].cpu().numpy().view(np.uint64),
+            "vals": vals[:p].cpu().numpy().view(np.uint32), "ranges": ranges.cpu().numpy(), "info": info}
 
 
 def test_shells_batch_full_size_two_views_sampled_rows():
