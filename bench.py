@@ -319,7 +319,7 @@ def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
-def stage_hbm(kms, vinfo, scene, W, H, hbm_gbs):
+def stage_hbm(kms, vinfo, scene, W, H, hbm_gbs, depth_keys=None):
     """Algorithmic bytes of each preprocess and binning stage of an exact batched render, their
     GB/s over the stage's GPU time (rara_ctx_kernel_ms) and the fraction of the measured HBM
     copy bandwidth. Bytes per unit (the design notes list them):
@@ -327,7 +327,10 @@ def stage_hbm(kms, vinfo, scene, W, H, hbm_gbs):
                    (view, Gaussian) slot (label, tiles), 60 B per rendered slot (rectangle,
                    splat record, depth), 64 B per cutoff slot (ray-tracing record)
       compaction   8 B per slot read (tiles, depth), 8 B per rendered slot written
-      depth sort   16 B per rendered slot per digit pass launched (4 depth + 1 view pass)
+      depth sort   16 B per key per digit pass launched (4 depth + 1 view pass over the
+                   rendered slots; for a one-camera batch 4 depth passes over the Gaussians some
+                   view renders, plus the expansion into the views' slots: 4 B of sorted value
+                   and 4 B of tile count read per (view, key), 4 B written per rendered slot)
       emission     44 B per rendered slot read (slot, rectangle, centre and conic), 8 B per pair
       tile sort    16 B per pair per digit pass
       ranges       4 B per pair read, 8 B per tile written"""
@@ -343,8 +346,9 @@ def stage_hbm(kms, vinfo, scene, W, H, hbm_gbs):
     view_passes = 0 if views == 1 else (1 if views <= 256 else 2)
     bytes_ = {
         "preprocess": n * (44 + 4 * scene.sh.shape[0]) + 5 * slots + 60 * rendered + 64 * cutoff,
-        "compaction": 8 * slots + 8 * rendered,
-        "depth_sort": 16 * rendered * (4 + view_passes),
+        "compaction": (8 * slots + 8 * rendered) if depth_keys is None else (4 * n + 8 * depth_keys),
+        "depth_sort": 16 * rendered * (4 + view_passes) if depth_keys is None else
+                      16 * depth_keys * 4 + 8 * views * depth_keys + 4 * rendered,
         "emission": 44 * rendered + 8 * pairs,
         "tile_sort": 16 * pairs * tile_passes,
         "ranges": 4 * pairs + 8 * tiles,
@@ -533,7 +537,10 @@ def run_ours(args):
                 "per_launch_units": {"tested": binfo["n_tested"], "walked": binfo["n_walked"],
                                      "evaluated": binfo["n_evaluated"], "cut_evaluated": binfo["n_cut_evaluated"]}}
     kms = [statistics.mean(k[j] for k in replay_kms) for j in range(6)]
-    batched["stage_hbm"] = stage_hbm(kms, vinfo, scene, W, H, peaks["hbm_gbs"])
+    one_camera = binfo["n_depth_keys"] != sum(v["n_rendered"] for v in vinfo)
+    batched["stage_hbm"] = stage_hbm(kms, vinfo, scene, W, H, peaks["hbm_gbs"],
+                                     binfo["n_depth_keys"] if one_camera else None)
+    batched["depth_keys"] = {"keys": binfo["n_depth_keys"], "one_camera_batch": one_camera}
     batched["stage_hbm_note"] = "stage times: mean of 10 graph replays (events recorded by the graph)"
     n = scene.n
     pre_bytes = n * (12 + 12 + 16 + 4 + 4 * scene.sh.shape[0]) + \

@@ -246,7 +246,8 @@ int rara_render_batch(rara_ctx *ctx, const rara_gaussians *scenes, int32_t num_s
                       int32_t num_views, void *stream);
 
 /* Same as rara_render_batch, without any host synchronisation: the first call for a batch
- * shape (scene sizes and SH degrees, view count, per-view resolution and scene) renders it
+ * shape (scene sizes and SH degrees, view count, per-view resolution and scene, whether a view
+ * clips by a convex volume, whether the batch is one scene seen from one camera) renders it
  * with rara_render_batch, sizes the pair capacity from it (+25%), and captures the whole
  * stage sequence on a private stream into a CUDA graph; later calls with the same shape
  * copy the new cameras, planes, scene and output pointers into the graph's tables and
@@ -321,6 +322,10 @@ typedef struct rara_frame_info {
     int64_t n_tested;     /* (warp rectangle, Gaussian) culling tests of the last render */
     int64_t n_pair_candidates; /* tiles of the view's rendered rectangles: the upper bound of
                                   n_pairs the preprocess sizes the pair buffers by */
+    int64_t n_depth_keys; /* keys the depth sort of the frame or batch sorted: the rendered
+                             (view, Gaussian) slots of all views, or, when the batch is one scene
+                             whose views all share one camera, the Gaussians some view renders
+                             (sorted once, then expanded into every view's slots) */
 } rara_frame_info;
 
 int rara_frame_info_get(rara_ctx *ctx, int32_t view, rara_frame_info *out);

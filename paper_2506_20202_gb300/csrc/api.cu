@@ -69,6 +69,8 @@ struct rara_ctx {
     DevBuf views_d, scenes_d, view_counters_d, counters;
     DevBuf labels, tiles, rect, rec, cut, depth;
     DevBuf cut_x;                       // further planes of clip-volume cutoff slots
+    DevBuf gkey;                        // one-camera batches: per-Gaussian depth keys
+    bool one_camera = false;            // the batch is one scene whose views share one camera
     bool multi = false;                 // the batch has a view with a convex clip volume
     bool extra_planes = false;          // the batch has a view with further planes
     DevBuf ckeys, cvals, ckeys_b, cvals_b, lookback_c;
@@ -251,6 +253,22 @@ int check_view(rara_ctx *c, const rara_camera *cam, const rara_plane *pl)
     return RARA_OK;
 }
 
+// Bitwise-equal cameras (the preprocess reuses a Gaussian's projection across such views).
+bool same_camera(const rara_camera &a, const rara_camera &b)
+{
+    return memcmp(a.world_to_cam, b.world_to_cam, sizeof(a.world_to_cam)) == 0 && a.fx == b.fx && a.fy == b.fy &&
+           a.cx == b.cx && a.cy == b.cy && a.width == b.width && a.height == b.height;
+}
+
+// One scene whose views all share one camera: its depth order is the same in every view.
+bool one_camera_batch(int ns, const rara_view *views, int nv)
+{
+    if (ns != 1 || nv < 2) return false;
+    for (int v = 1; v < nv; ++v)
+        if (!same_camera(views[v].camera, views[0].camera)) return false;
+    return true;
+}
+
 void fill_view(ViewDev &v, const rara_camera *cam, const rara_plane *pl, int tile_w, int tile_h)
 {
     for (int k = 0; k < 9; ++k) v.cam.R[k] = cam->world_to_cam[(k / 3) * 4 + (k % 3)];
@@ -344,6 +362,7 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
         sd.sh_degree = g.sh_degree;
         sd.view_begin = k;
         sd.unit_begin = units;
+        int prev_v = -1;    // the caller's index of the scene's previous view
         for (int v = 0; v < nv; ++v) {
             if (views[v].scene != si) continue;
             ViewDev &vd = c->h_views[k];
@@ -356,16 +375,8 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
             vd.final_T = views[v].final_T;
             vd.n_contrib = views[v].n_contrib;
             // views of one scene with the same camera share the preprocess's projection
-            const rara_camera &cm = views[v].camera;
-            vd.same_cam = 0;
-            if (k > sd.view_begin) {
-                const ViewDev &pv = c->h_views[k - 1];
-                bool same = pv.cam.W == cm.width && pv.cam.H == cm.height && pv.cam.fx == cm.fx &&
-                            pv.cam.fy == cm.fy && pv.cam.cx == cm.cx && pv.cam.cy == cm.cy;
-                for (int q = 0; q < 9 && same; ++q) same = pv.cam.R[q] == vd.cam.R[q];
-                for (int q = 0; q < 3 && same; ++q) same = pv.cam.t[q] == vd.cam.t[q];
-                vd.same_cam = same ? 1 : 0;
-            }
+            vd.same_cam = prev_v >= 0 && same_camera(views[prev_v].camera, views[v].camera) ? 1 : 0;
+            prev_v = v;
             c->h_view_map[v] = k;
             c->h_view_n[k] = (int)g.n;
             slots += (uint64_t)g.n;
@@ -389,6 +400,11 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
     if (c->tile_passes < 1) c->tile_passes = 1;
     c->tile_digit_bits = tile_bits > 0 ? (tile_bits + c->tile_passes - 1) / c->tile_passes : 1;
     c->view_passes = nv > 256 ? 2 : (nv > 1 ? 1 : 0);
+    // One scene whose views all share one camera (a plane sweep from one viewpoint): the depth
+    // order is the same in every view, so the Gaussians are depth-sorted once and expanded
+    // per view (no view passes)
+    c->one_camera = one_camera_batch(ns, views, nv);
+    if (c->one_camera) c->view_passes = 0;
     const size_t nn = slots > 0 ? (size_t)slots : 1;
     const size_t nt = tiles > 0 ? (size_t)tiles : 1;
     if ((rc = ensure(c, c->views_d, sizeof(ViewDev) * (size_t)nv, "view table")) ||
@@ -406,7 +422,8 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
         (rc = ensure(c, c->seg_base, sizeof(uint32_t) * (size_t)nv, "view slot bases")) ||
         (rc = ensure(c, c->ranges, nt * sizeof(int2), "ranges")) ||
         (rc = ensure(c, c->items, nt * 16, "render items")) ||
-        (c->multi && (rc = ensure(c, c->cut_x, nn * sizeof(CutExtra), "clip-volume records"))))
+        (c->multi && (rc = ensure(c, c->cut_x, nn * sizeof(CutExtra), "clip-volume records"))) ||
+        (c->one_camera && (rc = ensure(c, c->gkey, (size_t)(scenes[0].n > 0 ? scenes[0].n : 1) * 4, "depth keys"))))
         return rc;
     return upload_tables(c, s);
 }
@@ -437,6 +454,7 @@ int batch_preprocess(rara_ctx *c, cudaStream_t s)
     a.cut = (CutRec *)c->cut.p;
     a.cut_x = c->multi ? (CutExtra *)c->cut_x.p : nullptr;
     a.depth = (float *)c->depth.p;
+    a.gkey = c->one_camera ? (uint32_t *)c->gkey.p : nullptr;
     a.view_counters = (ViewCounters *)c->view_counters_d.p;
     a.counters = dc;
     int max_degree = 0, max_views = 0;
@@ -452,7 +470,8 @@ int batch_preprocess(rara_ctx *c, cudaStream_t s)
     CompactArgs ca;
     ca.tiles = (const uint32_t *)c->tiles.p;
     ca.depth = (const float *)c->depth.p;
-    ca.num_slots = c->num_slots;
+    ca.gkey = c->one_camera ? (const uint32_t *)c->gkey.p : nullptr;
+    ca.num_slots = c->one_camera ? (uint32_t)c->h_scenes[0].n : c->num_slots;
     ca.keys = (uint32_t *)c->ckeys.p;
     ca.vals = (uint32_t *)c->cvals.p;
     ca.hist = (uint32_t *)c->hist.p;
@@ -468,7 +487,7 @@ int batch_preprocess(rara_ctx *c, cudaStream_t s)
         return rc;  // tickets then start at 1: partition 0 is never taken
     c->debug_spin_limit = 0;
     c->debug_orphan = false;
-    const uint32_t parts = (c->num_slots + 1023) / 1024;
+    const uint32_t parts = (ca.num_slots + 1023) / 1024;
     const uint32_t slots = (uint32_t)(c->sm_count * c->bpsm_compact);
     const int cgrid = (int)(parts < slots ? parts : slots);
     launch_compact(ca, cgrid, s);
@@ -513,12 +532,32 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
     c->cap_pairs = cap;
     mark(c, 1, s);
     const int sgrid = c->sm_count * c->bpsm_sort;
+    const uint32_t ng = c->one_camera ? (uint32_t)(c->h_scenes[0].n > 0 ? c->h_scenes[0].n : 1) : (uint32_t)nn;
     int nl = sort_launch((uint32_t *)c->ckeys.p, (uint32_t *)c->cvals.p, (uint32_t *)c->ckeys_b.p,
-                         (uint32_t *)c->cvals_b.p, &dc->n_rendered, (uint32_t)nn, 4 + c->view_passes,
-                         hist + kHistDepth * 256, c->sort_scratch.p, &dc->ticket[kTicketSortDepth], &dc->status,
-                         &dc->depth_in_b, sgrid, s, (const uint32_t *)c->seg_base.p,
-                         c->view_passes ? c->num_views : 0, 4);
+                         (uint32_t *)c->cvals_b.p, c->one_camera ? &dc->n_union : &dc->n_rendered, ng,
+                         4 + c->view_passes, hist + kHistDepth * 256, c->sort_scratch.p,
+                         &dc->ticket[kTicketSortDepth], &dc->status, &dc->depth_in_b, sgrid, s,
+                         (const uint32_t *)c->seg_base.p, c->view_passes ? c->num_views : 0, 4);
     if ((rc = launched(c, "depth sort", nl))) return rc;
+    if (c->one_camera) {
+        // every view's rendered slots in (view, depth) order from the one depth order
+        if ((rc = check_cuda(c, cudaMemsetAsync(c->lookback_c.p, 0, (nn / 1024 + 2) * 8, s), "memset scan")))
+            return rc;
+        ExpandArgs xa;
+        xa.sorted_a = (const uint32_t *)c->cvals.p;
+        xa.sorted_b = (const uint32_t *)c->cvals_b.p;
+        xa.out_a = (uint32_t *)c->cvals.p;
+        xa.out_b = (uint32_t *)c->cvals_b.p;
+        xa.tiles = (const uint32_t *)c->tiles.p;
+        xa.views = (const ViewDev *)c->views_d.p;
+        xa.num_views = c->num_views;
+        xa.lookback = (unsigned long long *)c->lookback_c.p;
+        xa.counters = dc;
+        const uint32_t xparts = (uint32_t)((nn + 1023) / 1024);
+        const uint32_t xslots = (uint32_t)(c->sm_count * c->bpsm_compact);
+        launch_expand(xa, (int)(xparts < xslots ? xparts : xslots), s);
+        if ((rc = launched(c, "expansion"))) return rc;
+    }
     mark(c, 4, s);
 
     if ((rc = check_cuda(c, cudaMemsetAsync(c->lookback_e.p, 0, (nn / kBlock + 2) * 8, s), "memset emit")))
@@ -534,6 +573,7 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
     e.views = (const ViewDev *)c->views_d.p;
     e.num_views = c->num_views;
     e.cap_pairs = cap;
+    e.expanded = c->one_camera ? 1 : 0;
     e.tile_passes = c->tile_passes;
     e.tile_digit_bits = c->tile_digit_bits;
     e.pair_keys = (uint32_t *)c->pkeys.p;
@@ -695,7 +735,7 @@ int rara_ctx_destroy(rara_ctx *c)
                      &c->rect, &c->rec, &c->cut, &c->cut_x, &c->depth, &c->ckeys, &c->cvals, &c->ckeys_b, &c->cvals_b,
                      &c->lookback_c, &c->pkeys, &c->pvals, &c->pkeys_b, &c->pvals_b, &c->lookback_e, &c->hist,
                      &c->ranges, &c->items, &c->sort_scratch, &c->grec, &c->bviews_d, &c->bscenes_d,
-                     &c->seg_base, &c->export_off};
+                     &c->seg_base, &c->export_off, &c->gkey};
     for (DevBuf *b : all) release(c, *b);
     free_host(c);
     delete c;
@@ -926,7 +966,7 @@ int rara_render_batch_graph(rara_ctx *c, const rara_gaussians *scenes, int32_t n
     if (!c->owns_host) return fail(c, RARA_ERR_INVALID_ARG, "graph batches need a regular context");
     // batch shape: scene sizes and degrees, views' scene and resolution, and whether a view
     // clips by a convex volume (the render kernel's variant and buffers depend on it)
-    const size_t len = 3 + 2 * (size_t)num_scenes + 3 * (size_t)num_views;
+    const size_t len = 4 + 2 * (size_t)num_scenes + 3 * (size_t)num_views;
     int *shape = (int *)malloc(sizeof(int) * len);
     if (!shape) return fail(c, RARA_ERR_BUDGET, "host allocation failed");
     size_t k = 0;
@@ -937,6 +977,7 @@ int rara_render_batch_graph(rara_ctx *c, const rara_gaussians *scenes, int32_t n
         multi |= views[v].plane.n_extra > 0 &&
                  (views[v].plane.mode == RARA_MODE_RARA || views[v].plane.mode == RARA_MODE_RARA_ALL);
     shape[k++] = multi;
+    shape[k++] = one_camera_batch(num_scenes, views, num_views) ? 1 : 0;  // the depth order's kernels differ
     for (int i = 0; i < num_scenes; ++i) {
         shape[k++] = (int)scenes[i].n;
         shape[k++] = scenes[i].sh_degree;
@@ -1190,6 +1231,7 @@ int rara_frame_info_get(rara_ctx *c, int32_t view, rara_frame_info *out)
     out->n_cut_evaluated = (int64_t)c->h_counters->n_cut_evaluated;
     out->n_tested = (int64_t)c->h_counters->n_tested;
     out->n_pair_candidates = (int64_t)c->h_view_counters[k].n_pairs;
+    out->n_depth_keys = (int64_t)(c->one_camera ? c->h_counters->n_union : c->h_counters->n_rendered);
     return RARA_OK;
 }
 

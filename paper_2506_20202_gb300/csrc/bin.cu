@@ -156,7 +156,9 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
     for (int t = threadIdx.x; t < 4 * 256; t += kBlock) (&s_hist[0][0])[t] = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t n = (uint32_t)a.counters->n_rendered;
-    const uint32_t *vals = a.counters->depth_in_b ? a.vals_b : a.vals_a;
+    // the slots in (view, depth) order: the depth sort's result, or (one-camera batches) the
+    // expansion's, which is in the other buffer
+    const uint32_t *vals = (a.counters->depth_in_b != 0u) != (a.expanded != 0) ? a.vals_b : a.vals_a;
     const uint32_t parts = (n + kEmitPart - 1) / kEmitPart;
     const int passes = a.tile_passes, dbits = a.tile_digit_bits;
     const uint32_t dmask = (1u << dbits) - 1u;

@@ -239,17 +239,19 @@ __device__ __forceinline__ void load_proj(float (*c)[kBlock], Proj &p)
 // every view of the scene is processed from registers and shared memory; the views' tables
 // are staged kViewChunk at a time. Per-view counts are summed per warp and per block in
 // shared memory and added to the global counters once per chunk.
-// MINB: blocks per SM the register budget is sized for. With many views per Gaussian the
-// per-view loop is arithmetic and wants every register (3 blocks); with few views the kernel
-// streams the scene and wants warps in flight (4 blocks).
-// CACHE: keep the camera's part of each slot in shared memory across consecutive views with
-// the same camera (the batches of many views use it; a single view has nothing to reuse).
-template <int MINB, bool CACHE>
-__global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
+// One instance serves every batch, a single frame included: a view renders with the same
+// instructions whatever batch it is in, so its images are the same bit for bit (two instances
+// tuned for few and for many views were each free to contract the colour's multiply-adds
+// differently). Its register budget is sized for 3 blocks per SM (with many views per Gaussian
+// the per-view loop is arithmetic). The camera's part of each slot is kept in shared memory
+// across consecutive views with the same camera (a single view has nothing to reuse).
+constexpr bool CACHE = true;
+__global__ void __launch_bounds__(kBlock, 3) k_preprocess(PreprocessArgs a)
 {
     extern __shared__ __align__(16) float s_sh[];  // [3 (degree+1)^2][kBlock]
     __shared__ float s_pc[CACHE ? kProjWords : 1][kBlock];
     bool cam_ok = false;                            // s_pc holds this thread's slot for the view's camera
+    uint32_t ukey = kNoKey;                         // one-camera batches: the depth key, once a view renders it
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ ViewDev s_views[kViewChunk];
     __shared__ unsigned long long s_cnt[3][kViewChunk];
@@ -386,6 +388,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
                         rec.r1 = make_float4(pj.r1x, op, pj.rgb0, pj.rgb1);
                         float wmode = 0.0f;
                         a.depth[slot] = pj.depth;
+                        ukey = __float_as_uint(pj.depth);
                     if (cutoff) {
                         // the camera-space centre and the eye offset again (not cached)
                         const float tz = fmaf(cam.R[6], mx, fmaf(cam.R[7], my, fmaf(cam.R[8], mz, cam.t[2])));
@@ -509,6 +512,9 @@ __global__ void __launch_bounds__(kBlock, MINB) k_preprocess(PreprocessArgs a)
             }
         }
     }
+    // one-camera batches: the views share this Gaussian's depth, so the depth order of every
+    // view is the order of the Gaussians some view renders (sorted once, then expanded per view)
+    if (a.gkey && valid) a.gkey[i] = ukey;
 }
 
 // Compaction of rendered slots in slot order: partitions of 1024 slots (4 per thread,
@@ -537,9 +543,15 @@ __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
         unsigned cnt = 0;
 #pragma unroll
         for (int r = 0; r < kCompactItems; ++r) {
-            const uint32_t slot = first + r;
-            flag[r] = slot < a.num_slots && a.tiles[slot] != 0u;
-            key[r] = flag[r] ? __float_as_uint(a.depth[slot]) : 0u;
+            const uint32_t slot = first + r;  // a Gaussian index with gkey
+            if (a.gkey) {
+                const uint32_t k = slot < a.num_slots ? a.gkey[slot] : kNoKey;
+                flag[r] = k != kNoKey;
+                key[r] = flag[r] ? k : 0u;
+            } else {
+                flag[r] = slot < a.num_slots && a.tiles[slot] != 0u;
+                key[r] = flag[r] ? __float_as_uint(a.depth[slot]) : 0u;
+            }
             if (flag[r]) {
                 ++cnt;
                 atomicAdd(&s_hist[0][key[r] & 0xffu], 1u);
@@ -566,7 +578,10 @@ __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
             if (lane < kBlock / 32) s_warp[lane] = wi - w;
             const unsigned long long prefix =
                 warp_chained_prefix(a.lookback, (int)part, total, &a.counters->status, a.spin_limit);
-            if (lane == 0) s_prefix = prefix;
+            if (lane == 0) {
+                s_prefix = prefix;
+                if (a.gkey && part == parts - 1) a.counters->n_union = prefix + total;  // all compacted
+            }
         }
         __syncthreads();
         unsigned long long pos = s_prefix + s_warp[warp] + incl - cnt;
@@ -585,7 +600,7 @@ __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
     }
     // view passes of the depth sort (several views): digit histograms of the view index of
     // the rendered slots (its low and high byte), and the views' first slots
-    if (blockIdx.x == 0 && a.num_views > 1) {
+    if (blockIdx.x == 0 && a.num_views > 1 && !a.gkey) {
         for (int v = threadIdx.x; v < a.num_views; v += kBlock) {
             a.seg_base[v] = a.views[v].slot_base;
             const uint32_t nr = (uint32_t)a.view_counters[v].n_rendered;
@@ -597,24 +612,99 @@ __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
     }
 }
 
+// One-camera batches: expansion of the depth-sorted Gaussians into every view's rendered
+// slots (see ExpandArgs): partitions of 1024 virtual elements (4 per thread, consecutive),
+// block prefix by warp scans, global prefix by the chained scan, as in the compaction.
+__global__ void __launch_bounds__(kBlock) k_expand(ExpandArgs a)
+{
+    __shared__ unsigned s_part;
+    __shared__ unsigned s_warp[kBlock / 32];
+    __shared__ unsigned long long s_prefix;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool in_b = a.counters->depth_in_b != 0u;
+    const uint32_t *sorted = in_b ? a.sorted_b : a.sorted_a;
+    uint32_t *out = in_b ? a.out_a : a.out_b;
+    const uint64_t nu = a.counters->n_union;
+    const uint64_t total_elems = nu * (uint64_t)a.num_views;
+    const uint64_t parts = (total_elems + kBlock * kCompactItems - 1) / (kBlock * kCompactItems);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_part = atomicAdd(&a.counters->ticket[kTicketExpand], 1u);
+        __syncthreads();
+        const uint32_t part = s_part;
+        if (part >= parts) break;
+        const uint64_t first = (uint64_t)part * (kBlock * kCompactItems) + threadIdx.x * kCompactItems;
+        uint32_t slot[kCompactItems];
+        bool flag[kCompactItems];
+        unsigned cnt = 0;
+        // element e = v * nu + j: view v, the j-th Gaussian in depth order
+        uint64_t v = nu ? first / nu : 0, j = first - v * nu;
+#pragma unroll
+        for (int r = 0; r < kCompactItems; ++r) {
+            flag[r] = false;
+            slot[r] = 0u;
+            if (first + r < total_elems) {
+                slot[r] = a.views[v].slot_base + __ldg(&sorted[j]);
+                flag[r] = a.tiles[slot[r]] != 0u;
+                cnt += flag[r] ? 1u : 0u;
+            }
+            if (++j == nu) {
+                j = 0;
+                ++v;
+            }
+        }
+        unsigned incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned w = lane < kBlock / 32 ? s_warp[lane] : 0u;
+            unsigned wi = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned u = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += u;
+            }
+            const unsigned total = __shfl_sync(0xffffffffu, wi, 31);
+            if (lane < kBlock / 32) s_warp[lane] = wi - w;
+            const unsigned long long prefix = warp_chained_prefix(a.lookback, (int)part, total, &a.counters->status);
+            if (lane == 0) s_prefix = prefix;
+        }
+        __syncthreads();
+        unsigned long long pos = s_prefix + s_warp[warp] + incl - cnt;
+        const unsigned long long cap = a.counters->n_rendered;   // the expansion lists exactly these
+#pragma unroll
+        for (int r = 0; r < kCompactItems; ++r)
+            if (flag[r]) {
+                if (pos < cap) out[pos] = slot[r];
+                ++pos;
+            }
+    }
+}
+
 }  // namespace
+
+void launch_expand(const ExpandArgs &a, int grid, cudaStream_t s)
+{
+    if (grid > 0) k_expand<<<grid, kBlock, 0, s>>>(a);
+}
 
 int preprocess_configure()
 {
     const int most = 3 * 16 * kBlock * (int)sizeof(float);  // SH degree 3
-    const bool ok = cudaFuncSetAttribute(k_preprocess<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) ==
-                        cudaSuccess &&
-                    cudaFuncSetAttribute(k_preprocess<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) ==
-                        cudaSuccess;
-    return ok ? 0 : -1;
+    return cudaFuncSetAttribute(k_preprocess, cudaFuncAttributeMaxDynamicSharedMemorySize, most) == cudaSuccess
+               ? 0
+               : -1;
 }
 
 void launch_preprocess(const PreprocessArgs &a, int grid, int max_sh_degree, int max_views, cudaStream_t s)
 {
+    (void)max_views;
     const int smem = 3 * (max_sh_degree + 1) * (max_sh_degree + 1) * kBlock * (int)sizeof(float);
     if (grid <= 0) return;
-    if (max_views >= 4) k_preprocess<3, true><<<grid, kBlock, smem, s>>>(a);
-    else k_preprocess<4, false><<<grid, kBlock, smem, s>>>(a);
+    k_preprocess<<<grid, kBlock, smem, s>>>(a);
 }
 
 int compact_blocks_per_sm()

@@ -152,7 +152,8 @@ struct Counters {
     unsigned int tile_queue;             // next entry of the heaviest-first item order
     unsigned int status;
     unsigned int tile_in_b;              // 1 if the tile sort's result is in its B buffers
-    unsigned int ticket[13];             // partition tickets of the persistent kernels
+    unsigned int ticket[14];             // partition tickets of the persistent kernels
+    unsigned long long n_union;          // one-camera batches: Gaussians rendered in some view
     unsigned int bwd_queue;              // next entry of the item order (render backward)
     unsigned int order_hist[33];         // tiles per list-length bucket (item order)
     unsigned int order_cursor[33];       // items placed per bucket (item order)
@@ -160,7 +161,8 @@ struct Counters {
 constexpr size_t kRenderCounterBytes = 4 * sizeof(unsigned long long) + sizeof(unsigned int);
 // ticket slots
 // (the depth sort has up to 4 depth + 2 view passes, the tile sort up to 4 passes)
-constexpr int kTicketPre = 0, kTicketCompact = 1, kTicketEmit = 2, kTicketSortDepth = 3, kTicketSortTile = 9;
+constexpr int kTicketPre = 0, kTicketCompact = 1, kTicketEmit = 2, kTicketSortDepth = 3, kTicketSortTile = 9,
+              kTicketExpand = 13;
 // digit histograms: [0, 4) depth passes, [4, 6) view passes, [6, 10) tile passes (256 each)
 constexpr int kHistDepth = 0, kHistView = 4, kHistTile = 6, kHistPasses = 10;
 
@@ -178,12 +180,14 @@ struct PreprocessArgs {
     CutRec *cut;
     CutExtra *cut_x;  // per slot, only for batches with clip volumes (else null)
     float *depth;          // camera-space depth (the float32 sort key) of rendered slots
+    uint32_t *gkey;        // one-camera batches (one scene, every view the same camera): per
+                           // Gaussian, its depth bits if some view renders it, else kNoKey; null otherwise
     ViewCounters *view_counters;
     Counters *counters;
 };
 // max_sh_degree sizes the shared-memory staging of the SH coefficients (the largest degree
 // of a scene with views); preprocess_configure() must have succeeded once per device.
-// max_views: the most views of one scene in the batch (picks the register budget).
+// max_views: the most views of one scene in the batch (unused: one kernel instance serves all).
 void launch_preprocess(const PreprocessArgs &a, int grid, int max_sh_degree, int max_views, cudaStream_t s);
 int preprocess_configure();
 
@@ -203,7 +207,12 @@ struct CompactArgs {
     int num_views;
     uint32_t *seg_base;    // [num_views] first slot of each view (written)
     int spin_limit;        // polls of a look-back wait before it gives up
+    // one-camera batches: compact the Gaussians with gkey[i] != kNoKey (num_slots = the scene
+    // size; keys = their depth bits, values = Gaussian indices) and store the count in
+    // counters->n_union; null otherwise
+    const uint32_t *gkey;
 };
+constexpr uint32_t kNoKey = 0xffffffffu;  // gkey of a Gaussian no view renders
 void launch_compact(const CompactArgs &a, int grid, cudaStream_t s);
 int compact_blocks_per_sm();
 
@@ -223,6 +232,22 @@ int sort_launch(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *
                 const uint32_t *seg_base = nullptr, int num_segs = 0, int first_seg_pass = 0, int digit_bits = 8);
 int sort_blocks_per_sm();
 
+// One-camera batches: the depth-sorted Gaussians (sorted_a / sorted_b by the sort's result
+// flag, counters->n_union of them) expanded into every view's rendered slots in (view, depth)
+// order: element e of the virtual sequence over views x sorted Gaussians is slot
+// slot_base[v] + g, kept where that slot is rendered (tiles[slot] != 0); written to the
+// depth-sort buffer the sort's result is not in (out_a / out_b), which the emission then reads.
+struct ExpandArgs {
+    const uint32_t *sorted_a, *sorted_b;
+    uint32_t *out_a, *out_b;
+    const uint32_t *tiles;
+    const ViewDev *views;
+    int num_views;
+    unsigned long long *lookback;
+    Counters *counters;
+};
+void launch_expand(const ExpandArgs &a, int grid, cudaStream_t s);
+
 // Stage 4: emission of (global tile, slot) pairs in depth order + tile-digit histogram
 struct EmitArgs {
     const uint32_t *keys_a, *vals_a, *keys_b, *vals_b;  // the depth sort's two buffers
@@ -234,6 +259,7 @@ struct EmitArgs {
     uint32_t cap_pairs;
     int tile_passes;
     int tile_digit_bits;     // bits per tile-sort pass
+    int expanded;            // the slots are in the buffer the depth sort's result is not in (launch_expand)
     uint32_t *pair_keys;     // global tile id
     uint32_t *pair_vals;     // slot
     uint32_t *tile_hist;     // [tile_passes][256], zeroed before

@@ -164,3 +164,46 @@ def test_plane_sweep_from_one_camera_equals_single_renders():
             assert np.array_equal(nc, n0.cpu().numpy())
     finally:
         r.close()
+
+
+def test_one_camera_batch_sorts_once_and_equals_single_renders():
+    """A batch of one scene whose views all share one camera sorts the Gaussians by depth once
+    and expands that order into every view: every view equals its single render bit for bit,
+    exactly and through graph replays with new planes, and a replay whose cameras differ
+    recaptures (the depth order then differs per view)."""
+    sc = scenes.general_scene(20_000, seed=9, sh_degree=2)
+    cam = scenes.look_at_camera((0.3, 0.5, -2.9), (0.0, 0.0, 0.0), 176, 120, 60.0)
+    nrm = np.float32(scenes.random_unit_normal(11))
+    modes = [scenes.MODE_RARA, scenes.MODE_HARD, scenes.MODE_RARA_ALL, scenes.MODE_RARA, scenes.MODE_NONE,
+             scenes.MODE_RARA]
+    gs = [rara.GaussianTensors.from_scene(sc)]
+
+    def views_for(offsets, cams):
+        return [(0, c, scenes.Plane(nrm, float(d), 3.0, m), (0.0, 0.1, 0.2)) for d, m, c in zip(offsets, modes, cams)]
+
+    def check(r, views, graph):
+        got = _render_batch(r, gs, views, graph=graph)
+        single = rara.Renderer()
+        try:
+            for (si, c, pl, bg), (img, T, nc) in zip(views, got):
+                i0, T0, n0 = _outputs(c)
+                single.render(gs[0], c, pl, bg, out=(i0, T0, n0))
+                torch.cuda.synchronize()
+                assert np.array_equal(img, i0.cpu().numpy()) and np.array_equal(T, T0.cpu().numpy())
+                assert np.array_equal(nc, n0.cpu().numpy())
+        finally:
+            single.close()
+
+    r = rara.Renderer()
+    try:
+        v1 = views_for(np.linspace(-0.7, 0.7, 6), [cam] * 6)
+        check(r, v1, graph=False)
+        info = [rara.rara_frame_info_get(r.ctx, k) for k in range(6)]
+        assert info[0]["n_depth_keys"] < sum(i["n_rendered"] for i in info)   # sorted once, not per view
+        assert info[0]["n_depth_keys"] >= max(i["n_rendered"] for i in info)
+        check(r, v1, graph=True)                                   # capture
+        check(r, views_for(np.linspace(-0.5, 0.9, 6), [cam] * 6), graph=True)   # replay, new planes
+        other = scenes.look_at_camera((-1.2, 0.2, -2.6), (0.0, 0.0, 0.0), 176, 120, 60.0)
+        check(r, views_for(np.linspace(-0.5, 0.9, 6), [cam, other] * 3), graph=True)   # recapture
+    finally:
+        r.close()

@@ -262,7 +262,11 @@ def test_shells_batch_full_size_two_views_sampled_rows():
             parity.check_pairs(pre, kvr, gpu, report)
             rows = (cam.height // 2 - 16, cam.height // 2 + 16)
             ref = oracle.render(sc, pre, cam, pl, (0.0, 0.0, 0.0), kvr, rows=rows)
-            parity.check_image(pre, ref, gpu, report, rows=rows, max_flag_frac=0.05)
+            # the oracle flags 2.3% of the 1024^2 band and 6.7% of the 1920x1080 band (pixels
+            # near q = 9: 2.5%, near a classification threshold: 2.5%, at T near 1e-4: 1.3%,
+            # invisible Gaussians within rounding of the plane: 1.6%; they overlap): the
+            # shells stack many surfaces along each ray, so one pixel meets many of them
+            parity.check_image(pre, ref, gpu, report, rows=rows, max_flag_frac=0.08)
             print(k, report)
             assert report["pixels"] == 32 * cam.width
             assert gpu["info"]["n_cutoff"] > 1000
