@@ -319,7 +319,7 @@ def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
-def stage_hbm(kms, vinfo, scene, W, H, hbm_gbs, depth_keys=None):
+def stage_hbm(kms, vinfo, scene, W, H, hbm_gbs, depth_keys=None, shared_pairs=0):
     """Algorithmic bytes of each preprocess and binning stage of an exact batched render, their
     GB/s over the stage's GPU time (rara_ctx_kernel_ms) and the fraction of the measured HBM
     copy bandwidth. Bytes per unit (the design notes list them):
@@ -333,7 +333,11 @@ def stage_hbm(kms, vinfo, scene, W, H, hbm_gbs, depth_keys=None):
                    and 4 B of tile count read per (view, key), 4 B written per rendered slot)
       emission     44 B per rendered slot read (slot, rectangle, centre and conic), 8 B per pair
       tile sort    16 B per pair per digit pass
-      ranges       4 B per pair read, 8 B per tile written"""
+      ranges       4 B per pair read, 8 B per tile written
+    A one-camera batch of at most 32 views lists once (shared_pairs > 0): the depth sort has no
+    expansion; the emission reads 48 B per Gaussian some view renders (its view mask too) and
+    writes 8 B per shared pair; the tile sort sorts the shared pairs; the listing reads 20 B per
+    shared pair (value and mask twice, key once) and writes 4 B per view pair and 8 B per tile."""
     views = len(vinfo)
     n = scene.n
     slots = views * n
@@ -348,10 +352,10 @@ def stage_hbm(kms, vinfo, scene, W, H, hbm_gbs, depth_keys=None):
         "preprocess": n * (44 + 4 * scene.sh.shape[0]) + 5 * slots + 60 * rendered + 64 * cutoff,
         "compaction": (8 * slots + 8 * rendered) if depth_keys is None else (4 * n + 8 * depth_keys),
         "depth_sort": 16 * rendered * (4 + view_passes) if depth_keys is None else
-                      16 * depth_keys * 4 + 8 * views * depth_keys + 4 * rendered,
-        "emission": 44 * rendered + 8 * pairs,
-        "tile_sort": 16 * pairs * tile_passes,
-        "ranges": 4 * pairs + 8 * tiles,
+                      16 * depth_keys * 4 + (0 if shared_pairs else 8 * views * depth_keys + 4 * rendered),
+        "emission": 48 * depth_keys + 8 * shared_pairs if shared_pairs else 44 * rendered + 8 * pairs,
+        "tile_sort": 16 * (shared_pairs or pairs) * tile_passes,
+        "ranges": (20 * shared_pairs + 4 * pairs + 8 * tiles) if shared_pairs else 4 * pairs + 8 * tiles,
     }
     out = {}
     for (name, b), ms in zip(bytes_.items(), kms):
@@ -539,8 +543,10 @@ def run_ours(args):
     kms = [statistics.mean(k[j] for k in replay_kms) for j in range(6)]
     one_camera = binfo["n_depth_keys"] != sum(v["n_rendered"] for v in vinfo)
     batched["stage_hbm"] = stage_hbm(kms, vinfo, scene, W, H, peaks["hbm_gbs"],
-                                     binfo["n_depth_keys"] if one_camera else None)
-    batched["depth_keys"] = {"keys": binfo["n_depth_keys"], "one_camera_batch": one_camera}
+                                     binfo["n_depth_keys"] if one_camera else None, binfo["n_shared_pairs"])
+    batched["depth_keys"] = {"keys": binfo["n_depth_keys"], "one_camera_batch": one_camera,
+                             "shared_pairs": binfo["n_shared_pairs"],
+                             "view_pairs": sum(v["n_pairs"] for v in vinfo)}
     batched["stage_hbm_note"] = "stage times: mean of 10 graph replays (events recorded by the graph)"
     n = scene.n
     pre_bytes = n * (12 + 12 + 16 + 4 + 4 * scene.sh.shape[0]) + \

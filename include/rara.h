@@ -325,7 +325,13 @@ typedef struct rara_frame_info {
     int64_t n_depth_keys; /* keys the depth sort of the frame or batch sorted: the rendered
                              (view, Gaussian) slots of all views, or, when the batch is one scene
                              whose views all share one camera, the Gaussians some view renders
-                             (sorted once, then expanded into every view's slots) */
+                             (sorted once) */
+    int64_t n_shared_pairs; /* a one-camera batch of at most 32 views lists and tile-sorts the
+                               Gaussians some view renders once (every view's tile lists are
+                               that list without the Gaussians the view does not render): the
+                               pairs of that shared list; 0 for any other frame or batch (a
+                               one-camera batch of more views expands the depth order into
+                               every view's slots and lists each view) */
 } rara_frame_info;
 
 int rara_frame_info_get(rara_ctx *ctx, int32_t view, rara_frame_info *out);

@@ -70,7 +70,9 @@ struct rara_ctx {
     DevBuf labels, tiles, rect, rec, cut, depth;
     DevBuf cut_x;                       // further planes of clip-volume cutoff slots
     DevBuf gkey;                        // one-camera batches: per-Gaussian depth keys
+    DevBuf vmask, list_counts;          // shared listing: per-Gaussian view masks, partition counts
     bool one_camera = false;            // the batch is one scene whose views share one camera
+    bool shared_list = false;           // ... of at most kListViews views: its tile lists are built once
     bool multi = false;                 // the batch has a view with a convex clip volume
     bool extra_planes = false;          // the batch has a view with further planes
     DevBuf ckeys, cvals, ckeys_b, cvals_b, lookback_c;
@@ -405,6 +407,9 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
     // per view (no view passes)
     c->one_camera = one_camera_batch(ns, views, nv);
     if (c->one_camera) c->view_passes = 0;
+    // ... and with at most kListViews views, its tile lists too: every view's list is the
+    // union's (listed and tile-sorted once) without the Gaussians the view does not render
+    c->shared_list = c->one_camera && nv <= kListViews;
     const size_t nn = slots > 0 ? (size_t)slots : 1;
     const size_t nt = tiles > 0 ? (size_t)tiles : 1;
     if ((rc = ensure(c, c->views_d, sizeof(ViewDev) * (size_t)nv, "view table")) ||
@@ -423,7 +428,8 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
         (rc = ensure(c, c->ranges, nt * sizeof(int2), "ranges")) ||
         (rc = ensure(c, c->items, nt * 16, "render items")) ||
         (c->multi && (rc = ensure(c, c->cut_x, nn * sizeof(CutExtra), "clip-volume records"))) ||
-        (c->one_camera && (rc = ensure(c, c->gkey, (size_t)(scenes[0].n > 0 ? scenes[0].n : 1) * 4, "depth keys"))))
+        (c->one_camera && (rc = ensure(c, c->gkey, (size_t)(scenes[0].n > 0 ? scenes[0].n : 1) * 4, "depth keys"))) ||
+        (c->shared_list && (rc = ensure(c, c->vmask, (size_t)(scenes[0].n > 0 ? scenes[0].n : 1) * 4, "view masks"))))
         return rc;
     return upload_tables(c, s);
 }
@@ -455,6 +461,7 @@ int batch_preprocess(rara_ctx *c, cudaStream_t s)
     a.cut_x = c->multi ? (CutExtra *)c->cut_x.p : nullptr;
     a.depth = (float *)c->depth.p;
     a.gkey = c->one_camera ? (uint32_t *)c->gkey.p : nullptr;
+    a.vmask = c->shared_list ? (uint32_t *)c->vmask.p : nullptr;
     a.view_counters = (ViewCounters *)c->view_counters_d.p;
     a.counters = dc;
     int max_degree = 0, max_views = 0;
@@ -515,7 +522,8 @@ int ensure_pairs(rara_ctx *c, uint32_t cap)
     int rc;
     if ((rc = ensure(c, c->pkeys, pp * 4, "pair keys")) || (rc = ensure(c, c->pvals, pp * 4, "pair values")) ||
         (rc = ensure(c, c->pkeys_b, pp * 4, "pair keys B")) || (rc = ensure(c, c->pvals_b, pp * 4, "pair values B")) ||
-        (rc = ensure(c, c->sort_scratch, sb1 > sb2 ? sb1 : sb2, "sort scratch")))
+        (rc = ensure(c, c->sort_scratch, sb1 > sb2 ? sb1 : sb2, "sort scratch")) ||
+        (c->shared_list && (rc = ensure(c, c->list_counts, list_count_words(cap) * 4, "list partition counts"))))
         return rc;
     return RARA_OK;
 }
@@ -539,7 +547,7 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
                          &dc->ticket[kTicketSortDepth], &dc->status, &dc->depth_in_b, sgrid, s,
                          (const uint32_t *)c->seg_base.p, c->view_passes ? c->num_views : 0, 4);
     if ((rc = launched(c, "depth sort", nl))) return rc;
-    if (c->one_camera) {
+    if (c->one_camera && !c->shared_list) {
         // every view's rendered slots in (view, depth) order from the one depth order
         if ((rc = check_cuda(c, cudaMemsetAsync(c->lookback_c.p, 0, (nn / 1024 + 2) * 8, s), "memset scan")))
             return rc;
@@ -573,7 +581,9 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
     e.views = (const ViewDev *)c->views_d.p;
     e.num_views = c->num_views;
     e.cap_pairs = cap;
-    e.expanded = c->one_camera ? 1 : 0;
+    e.expanded = c->one_camera && !c->shared_list ? 1 : 0;
+    e.shared_list = c->shared_list ? 1 : 0;
+    e.vmask = (const uint32_t *)c->vmask.p;
     e.tile_passes = c->tile_passes;
     e.tile_digit_bits = c->tile_digit_bits;
     e.pair_keys = (uint32_t *)c->pkeys.p;
@@ -597,9 +607,28 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
     const uint32_t rblocks = (cap + 255) / 256;
     const uint32_t rmax = (uint32_t)(c->sm_count * 8);
     const int rgrid = (int)(rblocks < rmax ? (rblocks > 0 ? rblocks : 1) : rmax);
-    launch_ranges((const uint32_t *)c->pkeys.p, (const uint32_t *)c->pkeys_b.p, dc, cap, c->num_tiles,
-                  (int2 *)c->ranges.p, rgrid, s);
-    if ((rc = launched(c, "ranges"))) return rc;
+    if (c->shared_list) {
+        ListArgs la;
+        la.keys_a = (const uint32_t *)c->pkeys.p;
+        la.keys_b = (const uint32_t *)c->pkeys_b.p;
+        la.vals_a = (uint32_t *)c->pvals.p;
+        la.vals_b = (uint32_t *)c->pvals_b.p;
+        la.vmask = (const uint32_t *)c->vmask.p;
+        la.views = (const ViewDev *)c->views_d.p;
+        la.num_views = c->num_views;
+        la.tile_bits = c->tile_bits;
+        la.part_counts = (uint32_t *)c->list_counts.p;
+        la.max_parts = (cap + kListPart - 1) / kListPart + 1;
+        la.ranges = (int2 *)c->ranges.p;
+        la.cap_pairs = cap;
+        la.counters = dc;
+        launch_lists(la, c->sm_count * 4, s);
+        if ((rc = launched(c, "shared listing", 3))) return rc;
+    } else {
+        launch_ranges((const uint32_t *)c->pkeys.p, (const uint32_t *)c->pkeys_b.p, dc, cap, c->num_tiles,
+                      (int2 *)c->ranges.p, rgrid, s);
+        if ((rc = launched(c, "ranges"))) return rc;
+    }
     const int area = c->tile_w * c->tile_h;
     const int area_log2 = area == 64 ? 0 : (area == 256 ? 2 : 3);
     launch_tile_order((const int2 *)c->ranges.p, (int)c->num_tiles, c->split2_bits, c->split4_bits, area_log2,
@@ -735,7 +764,7 @@ int rara_ctx_destroy(rara_ctx *c)
                      &c->rect, &c->rec, &c->cut, &c->cut_x, &c->depth, &c->ckeys, &c->cvals, &c->ckeys_b, &c->cvals_b,
                      &c->lookback_c, &c->pkeys, &c->pvals, &c->pkeys_b, &c->pvals_b, &c->lookback_e, &c->hist,
                      &c->ranges, &c->items, &c->sort_scratch, &c->grec, &c->bviews_d, &c->bscenes_d,
-                     &c->seg_base, &c->export_off, &c->gkey};
+                     &c->seg_base, &c->export_off, &c->gkey, &c->vmask, &c->list_counts};
     for (DevBuf *b : all) release(c, *b);
     free_host(c);
     delete c;
@@ -1232,6 +1261,7 @@ int rara_frame_info_get(rara_ctx *c, int32_t view, rara_frame_info *out)
     out->n_tested = (int64_t)c->h_counters->n_tested;
     out->n_pair_candidates = (int64_t)c->h_view_counters[k].n_pairs;
     out->n_depth_keys = (int64_t)(c->one_camera ? c->h_counters->n_union : c->h_counters->n_rendered);
+    out->n_shared_pairs = c->shared_list ? (int64_t)c->h_counters->n_list : 0;
     return RARA_OK;
 }
 

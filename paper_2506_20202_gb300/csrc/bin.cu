@@ -155,9 +155,11 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
     __shared__ unsigned long long s_prefix;
     for (int t = threadIdx.x; t < 4 * 256; t += kBlock) (&s_hist[0][0])[t] = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t n = (uint32_t)a.counters->n_rendered;
+    const bool shared = a.shared_list != 0;
+    const uint32_t n = (uint32_t)(shared ? a.counters->n_union : a.counters->n_rendered);
     // the slots in (view, depth) order: the depth sort's result, or (one-camera batches) the
-    // expansion's, which is in the other buffer
+    // expansion's, which is in the other buffer; with a shared listing, the union's Gaussians
+    // in depth order (the depth sort's result)
     const uint32_t *vals = (a.counters->depth_in_b != 0u) != (a.expanded != 0) ? a.vals_b : a.vals_a;
     const uint32_t parts = (n + kEmitPart - 1) / kEmitPart;
     const int passes = a.tile_passes, dbits = a.tile_digit_bits;
@@ -170,14 +172,22 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
         const uint32_t part = s_part;
         if (part >= parts) break;
         const uint32_t first = part * kEmitPart;
-        uint32_t slot[kEmitItems], rows[kEmitItems];
+        uint32_t slot[kEmitItems], rows[kEmitItems], lslot[kEmitItems];
+        int sview[kEmitItems];
         uint2 rc[kEmitItems];
         uint32_t nrows = 0;
 #pragma unroll
         for (int r = 0; r < kEmitItems; ++r) {
             const uint32_t i = first + threadIdx.x * kEmitItems + r;
-            slot[r] = i < n ? __ldg(&vals[i]) : 0u;
-            rc[r] = i < n ? __ldg(&a.rect[slot[r]]) : make_uint2(0u, 0u);
+            slot[r] = i < n ? __ldg(&vals[i]) : 0u;  // the value the pairs carry
+            lslot[r] = slot[r];                      // the slot whose rectangle and splat are read
+            sview[r] = 0;
+            if (shared && i < n) {
+                const uint32_t vm = __ldg(&a.vmask[slot[r]]);   // non-zero: some view renders it
+                sview[r] = vm ? __ffs(vm) - 1 : 0;
+                lslot[r] = a.views[sview[r]].slot_base + slot[r];
+            }
+            rc[r] = i < n ? __ldg(&a.rect[lslot[r]]) : make_uint2(0u, 0u);
             const int y0 = rc[r].x >> 16, y1 = rc[r].y >> 16;
             const int x0 = rc[r].x & 0xffff, x1 = rc[r].y & 0xffff;
             rows[r] = (i < n && x0 <= x1 && y0 <= y1) ? (uint32_t)(y1 - y0 + 1) : 0u;
@@ -193,10 +203,10 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
             cnt[r] = 0;
             uint32_t v = 0, roff = kNoPool, t0 = 0, txs = 0;
             if (rows[r]) {
-                v = (uint32_t)view_of_slot(a.views, a.num_views, slot[r]);
+                v = shared ? (uint32_t)sview[r] : (uint32_t)view_of_slot(a.views, a.num_views, slot[r]);
                 const ViewDev &vw = a.views[v];
-                const SpanGeo g = span_geo(a.rec[slot[r]].r0, a.rec[slot[r]].r1, rc[r], vw);
-                t0 = vw.tile_base + (uint32_t)(g.y0 * vw.tiles_x + g.x0);
+                const SpanGeo g = span_geo(a.rec[lslot[r]].r0, a.rec[lslot[r]].r1, rc[r], vw);
+                t0 = (shared ? 0u : vw.tile_base) + (uint32_t)(g.y0 * vw.tiles_x + g.x0);
                 txs = (uint32_t)vw.tiles_x;
                 const bool pooled = rbase + rows[r] <= kRowPool;
                 if (pooled) roff = rbase;
@@ -293,7 +303,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
                 dy = rl - (int)roff;
                 dx = (int)s_rcol[rl] + (int)(r - s_rcum[rl]);
             } else {
-                const uint32_t sl = s_slot[j];
+                const uint32_t sl = shared ? a.views[s_view[j]].slot_base + s_slot[j] : s_slot[j];
                 const SpanGeo g = span_geo(a.rec[sl].r0, a.rec[sl].r1, a.rect[sl], a.views[s_view[j]]);
                 uint32_t rr = r;
                 for (int k2 = 0; k2 < (int)s_nrows[j]; ++k2) {  // the spans of the count phase
@@ -356,6 +366,136 @@ __global__ void k_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const C
             const uint32_t after = r < 3 ? k[r + 1] : next;
             if (before != t) ranges[t].x = (int)(i0 + r);
             if (after != t) ranges[t].y = (int)(i0 + r + 1);
+        }
+    }
+}
+
+// Shared listing, launch 1: view v's count of partition p (the union pairs [p kListPart,
+// (p + 1) kListPart) whose Gaussian view v renders), one warp per partition. Lane v adds up
+// the ballots of bit v of the 32 pairs' view masks.
+__global__ void __launch_bounds__(kBlock) k_list_count(ListArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const bool in_b = a.counters->tile_in_b != 0u;
+    const uint32_t *vals = in_b ? a.vals_b : a.vals_a;
+    const unsigned long long np = a.counters->n_pairs;
+    const uint32_t n = (uint32_t)(np < a.cap_pairs ? np : a.cap_pairs);
+    const uint32_t parts = (n + kListPart - 1) / kListPart;
+    const int nv = a.num_views;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.counters->list_src = in_b ? 1u : 0u;
+        a.counters->n_list = n;
+    }
+    const uint32_t warps = gridDim.x * (kBlock / 32);
+    for (uint32_t part = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); part < parts; part += warps) {
+        const uint32_t first = part * kListPart, last = min(first + kListPart, n);
+        uint32_t c = 0;
+        for (uint32_t j0 = first; j0 < last; j0 += 32) {
+            const uint32_t j = j0 + (uint32_t)lane;
+            const uint32_t m = j < last ? __ldg(&a.vmask[__ldg(&vals[j])]) : 0u;
+            for (int v = 0; v < nv; ++v) {
+                const uint32_t b = __ballot_sync(0xffffffffu, (m >> v) & 1u);
+                if (lane == v) c += (uint32_t)__popc(b);
+            }
+        }
+        if (lane < nv) a.part_counts[(size_t)lane * a.max_parts + part] = c;
+    }
+}
+
+// Launch 2: one block per view scans its partition counts in place (exclusive) and stores the
+// view's total after the columns.
+__global__ void __launch_bounds__(1024) k_list_scan(ListArgs a)
+{
+    __shared__ uint32_t s_w[32];
+    const int v = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t n = (uint32_t)a.counters->n_list;
+    const uint32_t parts = (n + kListPart - 1) / kListPart;
+    uint32_t *col = a.part_counts + (size_t)v * a.max_parts;
+    const uint32_t per = (parts + 1023) / 1024;
+    const uint32_t p0 = threadIdx.x * per, p1 = min(p0 + per, parts);
+    uint32_t sum = 0;
+    for (uint32_t p = p0; p < p1; ++p) sum += col[p];
+    uint32_t incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (int w = 0; w < 32; ++w) {
+        const uint32_t u = s_w[w];
+        if (w < warp) before += u;
+        total += u;
+    }
+    uint32_t run = before + incl - sum;
+    for (uint32_t p = p0; p < p1; ++p) {
+        const uint32_t c = col[p];
+        col[p] = run;
+        run += c;
+    }
+    if (threadIdx.x == 0) a.part_counts[(size_t)kListViews * a.max_parts + v] = total;
+}
+
+// Launch 3: one warp per partition writes every view's slots of its pairs at B_v + C_v(j) and,
+// where a tile's run starts or ends, that tile's range bound in every view.
+__global__ void __launch_bounds__(kBlock) k_list_scatter(ListArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const bool in_b = a.counters->list_src != 0u;
+    const uint32_t *keys = in_b ? a.keys_b : a.keys_a;
+    const uint32_t *vals = in_b ? a.vals_b : a.vals_a;
+    uint32_t *out = in_b ? a.vals_a : a.vals_b;
+    const uint32_t n = (uint32_t)a.counters->n_list;
+    const uint32_t parts = (n + kListPart - 1) / kListPart;
+    const int nv = a.num_views;
+    const uint32_t cap = a.cap_pairs;
+    // lane v: B_v (the pairs of the views before v) and the view's first slot
+    const uint32_t tot = lane < nv ? a.part_counts[(size_t)kListViews * a.max_parts + lane] : 0u;
+    unsigned long long base = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long u = __shfl_up_sync(0xffffffffu, base, o);
+        if (lane >= o) base += u;
+    }
+    const unsigned long long all = __shfl_sync(0xffffffffu, base, 31);
+    base -= tot;
+    const uint32_t sbase = lane < nv ? a.views[lane].slot_base : 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.counters->n_pairs = all;
+        if (all > cap) atomicOr(&a.counters->status, kStatusOverflow);
+        a.counters->tile_in_b = in_b ? 0u : 1u;   // the views' lists are in the other buffer
+    }
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t warps = gridDim.x * (kBlock / 32);
+    for (uint32_t part = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); part < parts; part += warps) {
+        const uint32_t first = part * kListPart, last = min(first + kListPart, n);
+        unsigned long long run = lane < nv ? base + a.part_counts[(size_t)lane * a.max_parts + part] : 0ull;
+        for (uint32_t j0 = first; j0 < last; j0 += 32) {
+            const uint32_t j = j0 + (uint32_t)lane;
+            const bool ok = j < last;
+            const uint32_t g = ok ? __ldg(&vals[j]) : 0u;
+            const uint32_t m = ok ? __ldg(&a.vmask[g]) : 0u;
+            const uint32_t t = ok ? __ldg(&keys[j]) : 0xffffffffu;
+            uint32_t tp = __shfl_up_sync(0xffffffffu, t, 1);
+            uint32_t tn = __shfl_down_sync(0xffffffffu, t, 1);
+            if (lane == 0) tp = j > 0 && ok ? __ldg(&keys[j - 1]) : 0xffffffffu;
+            if (lane == 31 || j + 1 >= last) tn = ok && j + 1 < n ? __ldg(&keys[j + 1]) : 0xffffffffu;
+            const bool start = ok && tp != t, end = ok && tn != t;
+            for (int v = 0; v < nv; ++v) {
+                const bool bit = ((m >> v) & 1u) != 0u;
+                const uint32_t b = __ballot_sync(0xffffffffu, bit);
+                const unsigned long long pos = __shfl_sync(0xffffffffu, run, v) + (unsigned)__popc(b & lt);
+                const uint32_t sb = __shfl_sync(0xffffffffu, sbase, v);   // every lane takes part
+                if (bit && pos < cap) out[pos] = sb + g;
+                if (start || end) {
+                    int2 *rg = &a.ranges[((uint32_t)v << a.tile_bits) | t];
+                    if (start) rg->x = (int)(pos < cap ? pos : cap);
+                    const unsigned long long e = pos + (bit ? 1u : 0u);
+                    if (end) rg->y = (int)(e < cap ? e : cap);
+                }
+                if (lane == v) run += (unsigned)__popc(b);
+            }
         }
     }
 }
@@ -512,6 +652,14 @@ void launch_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const Counter
                    uint32_t num_tiles, int2 *ranges, int grid, cudaStream_t s)
 {
     if (grid > 0) k_ranges<<<grid, 256, 0, s>>>(keys_a, keys_b, counters, cap_pairs, num_tiles, ranges);
+}
+
+void launch_lists(const ListArgs &a, int grid, cudaStream_t s)
+{
+    if (grid <= 0 || a.num_views <= 0 || a.num_views > kListViews) return;
+    k_list_count<<<grid, kBlock, 0, s>>>(a);
+    k_list_scan<<<a.num_views, 1024, 0, s>>>(a);
+    k_list_scatter<<<grid, kBlock, 0, s>>>(a);
 }
 
 void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int split4_bits, int area_log2,

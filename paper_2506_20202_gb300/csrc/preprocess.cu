@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_preprocess(PreprocessArgs a)
     __shared__ float s_pc[CACHE ? kProjWords : 1][kBlock];
     bool cam_ok = false;                            // s_pc holds this thread's slot for the view's camera
     uint32_t ukey = kNoKey;                         // one-camera batches: the depth key, once a view renders it
+    uint32_t vmask = 0;                             // shared listing: the views that render it
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ ViewDev s_views[kViewChunk];
     __shared__ unsigned long long s_cnt[3][kViewChunk];
@@ -489,6 +490,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_preprocess(PreprocessArgs a)
                     }
                 }
                 a.tiles[slot] = ntiles;
+                const int vbit = vbase - sc.view_begin + vv;
+                if (rendered && vbit < kListViews) vmask |= 1u << vbit;
             }
             // per-view counts: warp sums, then one shared-memory add per warp
             const unsigned nr = __reduce_add_sync(0xffffffffu, rendered ? 1u : 0u);
@@ -515,6 +518,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_preprocess(PreprocessArgs a)
     // one-camera batches: the views share this Gaussian's depth, so the depth order of every
     // view is the order of the Gaussians some view renders (sorted once, then expanded per view)
     if (a.gkey && valid) a.gkey[i] = ukey;
+    if (a.vmask && valid) a.vmask[i] = vmask;
 }
 
 // Compaction of rendered slots in slot order: partitions of 1024 slots (4 per thread,

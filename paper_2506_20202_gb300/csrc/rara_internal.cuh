@@ -155,6 +155,8 @@ struct Counters {
     unsigned int ticket[14];             // partition tickets of the persistent kernels
     unsigned long long n_union;          // one-camera batches: Gaussians rendered in some view
     unsigned int bwd_queue;              // next entry of the item order (render backward)
+    unsigned int list_src;               // shared listing: 1 if the union's tile-sorted pairs are in B
+    unsigned long long n_list;           // shared listing: the union's pairs
     unsigned int order_hist[33];         // tiles per list-length bucket (item order)
     unsigned int order_cursor[33];       // items placed per bucket (item order)
 };
@@ -182,6 +184,8 @@ struct PreprocessArgs {
     float *depth;          // camera-space depth (the float32 sort key) of rendered slots
     uint32_t *gkey;        // one-camera batches (one scene, every view the same camera): per
                            // Gaussian, its depth bits if some view renders it, else kNoKey; null otherwise
+    uint32_t *vmask;       // shared listing (a one-camera batch of at most kListViews views): per
+                           // Gaussian, bit v set when view v renders it; null otherwise
     ViewCounters *view_counters;
     Counters *counters;
 };
@@ -260,14 +264,54 @@ struct EmitArgs {
     int tile_passes;
     int tile_digit_bits;     // bits per tile-sort pass
     int expanded;            // the slots are in the buffer the depth sort's result is not in (launch_expand)
-    uint32_t *pair_keys;     // global tile id
-    uint32_t *pair_vals;     // slot
+    // shared listing: the depth-sorted values are the Gaussians of a one-camera batch that
+    // some view renders (counters->n_union of them); each is listed once with the local tile
+    // ids of the common tile grid and the Gaussian index as value, its rectangle and splat
+    // read from the first view that renders it (vmask)
+    int shared_list;
+    const uint32_t *vmask;
+    uint32_t *pair_keys;     // global tile id (local with shared_list)
+    uint32_t *pair_vals;     // slot (Gaussian index with shared_list)
     uint32_t *tile_hist;     // [tile_passes][256], zeroed before
     unsigned long long *lookback;
     Counters *counters;
 };
 void launch_emit(const EmitArgs &a, int grid, cudaStream_t s);
 int emit_blocks_per_sm();
+
+// Shared listing of a one-camera batch. All views share the camera, so a Gaussian covers the
+// same tiles in each view that renders it, and the depth order is common: view v's list of
+// tile t is the union's list of t (tile-sorted once) without the Gaussians v does not render.
+// With C_v(j) = the union pairs before position j whose Gaussian view v renders and B_v = the
+// pairs of the views before v, union pair j goes to position B_v + C_v(j) of the views' pair
+// list, and view v's range of tile t is [B_v + C_v(start of t), B_v + C_v(end of t)). Three
+// launches over partitions of kListPart union pairs (one warp each): every view's count per
+// partition, their exclusive scan per view (one block per view) with the view totals, and the
+// scatter of values (slot_base[v] + Gaussian) and ranges. The lists land in the value buffer
+// the union's are not in, and counters->tile_in_b is switched to it.
+constexpr int kListViews = 32;          // views of a shared listing (bits of vmask)
+constexpr uint32_t kListPart = 512;     // union pairs per partition (16 rounds of a warp)
+struct ListArgs {
+    const uint32_t *keys_a, *keys_b;    // the union's tile-sorted pairs (local tile ids)
+    uint32_t *vals_a, *vals_b;          // ... their Gaussians; the views' slots go to the other buffer
+    const uint32_t *vmask;
+    const ViewDev *views;
+    int num_views;
+    int tile_bits;
+    uint32_t *part_counts;              // [kListViews][max_parts] counts, then exclusive prefixes,
+                                        // followed by the kListViews view totals
+    uint32_t max_parts;                 // >= cap_pairs / kListPart rounded up
+    int2 *ranges;                       // global tile ranges, zeroed before
+    uint32_t cap_pairs;
+    Counters *counters;
+};
+// 4-byte words of part_counts for a pair capacity
+inline size_t list_count_words(uint32_t cap_pairs)
+{
+    return (size_t)kListViews * ((cap_pairs + kListPart - 1) / kListPart + 1) + kListViews;
+}
+// grid: blocks of kBlock threads for the count and scatter launches (persistent over partitions)
+void launch_lists(const ListArgs &a, int grid, cudaStream_t s);
 
 // Stage 6: ranges of the sorted pairs (ranges zeroed before)
 void launch_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const Counters *counters, uint32_t cap_pairs,

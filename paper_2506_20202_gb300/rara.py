@@ -57,7 +57,8 @@ class rara_frame_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_rendered", C.c_int64), ("n_cutoff", C.c_int64),
                 ("n_pairs", C.c_int64), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
                 ("n_evaluated", C.c_int64), ("n_walked", C.c_int64), ("n_cut_evaluated", C.c_int64),
-                ("n_tested", C.c_int64), ("n_pair_candidates", C.c_int64), ("n_depth_keys", C.c_int64)]
+                ("n_tested", C.c_int64), ("n_pair_candidates", C.c_int64), ("n_depth_keys", C.c_int64),
+                ("n_shared_pairs", C.c_int64)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/rara.h

@@ -49,6 +49,18 @@ def _batch_case(seed=0):
     return sc, views
 
 
+def _pairs(ctx, view):
+    """The view's exported tile lists: 64-bit keys, Gaussian indices, per-tile ranges."""
+    info = rara.rara_frame_info_get(ctx, view)
+    p, nt = int(info["n_pairs"]), info["tiles_x"] * info["tiles_y"]
+    keys = torch.zeros(max(p, 1), dtype=torch.int64, device="cuda")
+    vals = torch.zeros(max(p, 1), dtype=torch.int32, device="cuda")
+    ranges = torch.zeros((nt, 2), dtype=torch.int64, device="cuda")
+    rara.rara_frame_pairs(ctx, view, keys, vals, ranges)
+    torch.cuda.synchronize()
+    return keys[:p].cpu().numpy(), vals[:p].cpu().numpy(), ranges.cpu().numpy()
+
+
 def _render_batch(r, sc_t, views, graph=False):
     vs = []
     for (si, cam, pl, bg) in views:
@@ -168,9 +180,10 @@ def test_plane_sweep_from_one_camera_equals_single_renders():
 
 def test_one_camera_batch_sorts_once_and_equals_single_renders():
     """A batch of one scene whose views all share one camera sorts the Gaussians by depth once
-    and expands that order into every view: every view equals its single render bit for bit,
-    exactly and through graph replays with new planes, and a replay whose cameras differ
-    recaptures (the depth order then differs per view)."""
+    and lists and tile-sorts them once, every view's lists then being the union's without the
+    Gaussians it does not render: every view equals its single render bit for bit (image, T,
+    contributor counts and tile lists), exactly and through graph replays with new planes,
+    and a replay whose cameras differ recaptures (the depth order then differs per view)."""
     sc = scenes.general_scene(20_000, seed=9, sh_degree=2)
     cam = scenes.look_at_camera((0.3, 0.5, -2.9), (0.0, 0.0, 0.0), 176, 120, 60.0)
     nrm = np.float32(scenes.random_unit_normal(11))
@@ -185,12 +198,15 @@ def test_one_camera_batch_sorts_once_and_equals_single_renders():
         got = _render_batch(r, gs, views, graph=graph)
         single = rara.Renderer()
         try:
-            for (si, c, pl, bg), (img, T, nc) in zip(views, got):
+            for k, ((si, c, pl, bg), (img, T, nc)) in enumerate(zip(views, got)):
                 i0, T0, n0 = _outputs(c)
                 single.render(gs[0], c, pl, bg, out=(i0, T0, n0))
                 torch.cuda.synchronize()
                 assert np.array_equal(img, i0.cpu().numpy()) and np.array_equal(T, T0.cpu().numpy())
                 assert np.array_equal(nc, n0.cpu().numpy())
+                if not graph:   # the same tile lists as the single render's
+                    for a, b in zip(_pairs(r.ctx, k), _pairs(single.ctx, 0)):
+                        assert np.array_equal(a, b)
         finally:
             single.close()
 
@@ -207,3 +223,60 @@ def test_one_camera_batch_sorts_once_and_equals_single_renders():
         check(r, views_for(np.linspace(-0.5, 0.9, 6), [cam, other] * 3), graph=True)   # recapture
     finally:
         r.close()
+
+
+@pytest.mark.parametrize("tiling", [(16, 16, 256, 33, 33), (8, 8, 128, 9, 11), (32, 16, 32, 10, 12)])
+def test_one_camera_shared_lists_with_tilings_and_splits(tiling):
+    """The shared tile lists under other tile shapes, blend depths and split thresholds (tiles
+    split into 2 or 4 lanes per pixel by the per-view list lengths): still every view equals
+    its single render with the same setting, including views whose plane hides everything."""
+    from paper_2506_20202_gb300 import autotune
+    sc = scenes.general_scene(30_000, seed=4, sh_degree=3)
+    cam = scenes.look_at_camera((1.9, 0.6, -2.2), (0.0, 0.0, 0.0), 224, 160, 60.0)
+    nrm = np.float32(scenes.random_unit_normal(5))
+    gs = [rara.GaussianTensors.from_scene(sc)]
+    offsets = list(np.linspace(-0.8, 0.8, 7)) + [-50.0]      # the last view hides every Gaussian
+    views = [(0, cam, scenes.Plane(nrm, float(d), 3.0, scenes.MODE_RARA), (0.2, 0.1, 0.0)) for d in offsets]
+    r, single = rara.Renderer(), rara.Renderer()
+    try:
+        autotune.apply(r.ctx, tiling)
+        autotune.apply(single.ctx, tiling)
+        got = _render_batch(r, gs, views)
+        for k, ((si, c, pl, bg), (img, T, nc)) in enumerate(zip(views, got)):
+            i0, T0, n0 = _outputs(c)
+            single.render(gs[0], c, pl, bg, out=(i0, T0, n0))
+            torch.cuda.synchronize()
+            assert np.array_equal(img, i0.cpu().numpy()) and np.array_equal(T, T0.cpu().numpy())
+            assert np.array_equal(nc, n0.cpu().numpy())
+            for a, b in zip(_pairs(r.ctx, k), _pairs(single.ctx, 0)):
+                assert np.array_equal(a, b)
+        assert rara.rara_frame_info_get(r.ctx, len(views) - 1)["n_pairs"] == 0
+        assert np.all(got[-1][0] == np.float32([0.2, 0.1, 0.0])[:, None, None])
+    finally:
+        r.close()
+        single.close()
+
+
+def test_one_camera_batch_beyond_shared_list_views():
+    """A one-camera batch of more views than the shared listing's 32 keeps the per-view
+    listing over the expanded depth order; every view still equals its single render."""
+    sc = scenes.general_scene(6000, seed=6, sh_degree=1)
+    cam = scenes.look_at_camera((0.4, -0.3, -2.8), (0.0, 0.0, 0.0), 64, 48, 60.0)
+    nrm = np.float32(scenes.random_unit_normal(8))
+    gs = [rara.GaussianTensors.from_scene(sc)]
+    views = [(0, cam, scenes.Plane(nrm, float(d), 3.0, scenes.MODE_RARA), (0.0, 0.0, 0.0))
+             for d in np.linspace(-0.9, 0.9, 35)]
+    r, single = rara.Renderer(), rara.Renderer()
+    try:
+        got = _render_batch(r, gs, views)
+        for k, ((si, c, pl, bg), (img, T, nc)) in enumerate(zip(views, got)):
+            i0, T0, n0 = _outputs(c)
+            single.render(gs[0], c, pl, bg, out=(i0, T0, n0))
+            torch.cuda.synchronize()
+            assert np.array_equal(img, i0.cpu().numpy()) and np.array_equal(T, T0.cpu().numpy())
+            if k % 7 == 0:
+                for a, b in zip(_pairs(r.ctx, k), _pairs(single.ctx, 0)):
+                    assert np.array_equal(a, b)
+    finally:
+        r.close()
+        single.close()
