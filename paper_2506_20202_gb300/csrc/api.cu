@@ -617,12 +617,13 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
         la.views = (const ViewDev *)c->views_d.p;
         la.num_views = c->num_views;
         la.tile_bits = c->tile_bits;
+        la.slot_stride = (uint32_t)c->h_scenes[0].n;
         la.part_counts = (uint32_t *)c->list_counts.p;
         la.max_parts = (cap + kListPart - 1) / kListPart + 1;
         la.ranges = (int2 *)c->ranges.p;
         la.cap_pairs = cap;
         la.counters = dc;
-        launch_lists(la, c->sm_count * 4, s);
+        launch_lists(la, c->sm_count * 8, s);   // a warp per partition of the 40M-pair benchmark list
         if ((rc = launched(c, "shared listing", 3))) return rc;
     } else {
         launch_ranges((const uint32_t *)c->pkeys.p, (const uint32_t *)c->pkeys_b.p, dc, cap, c->num_tiles,

@@ -372,7 +372,8 @@ __global__ void k_ranges(const uint32_t *keys_a, const uint32_t *keys_b, const C
 
 // Shared listing, launch 1: view v's count of partition p (the union pairs [p kListPart,
 // (p + 1) kListPart) whose Gaussian view v renders), one warp per partition. Lane v adds up
-// the ballots of bit v of the 32 pairs' view masks.
+// the ballots of bit v of the pairs' view masks, four rounds of 32 pairs at a time (their
+// values, then their masks, loaded together).
 __global__ void __launch_bounds__(kBlock) k_list_count(ListArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -390,12 +391,20 @@ __global__ void __launch_bounds__(kBlock) k_list_count(ListArgs a)
     for (uint32_t part = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); part < parts; part += warps) {
         const uint32_t first = part * kListPart, last = min(first + kListPart, n);
         uint32_t c = 0;
-        for (uint32_t j0 = first; j0 < last; j0 += 32) {
-            const uint32_t j = j0 + (uint32_t)lane;
-            const uint32_t m = j < last ? __ldg(&a.vmask[__ldg(&vals[j])]) : 0u;
+        for (uint32_t j0 = first; j0 < last; j0 += 128) {
+            uint32_t m[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t j = j0 + 32u * k + (uint32_t)lane;
+                m[k] = j < last ? __ldg(&vals[j]) : 0xffffffffu;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) m[k] = m[k] != 0xffffffffu ? __ldg(&a.vmask[m[k]]) : 0u;
             for (int v = 0; v < nv; ++v) {
-                const uint32_t b = __ballot_sync(0xffffffffu, (m >> v) & 1u);
-                if (lane == v) c += (uint32_t)__popc(b);
+                uint32_t s = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) s += (uint32_t)__popc(__ballot_sync(0xffffffffu, (m[k] >> v) & 1u));
+                if (lane == v) c += s;
             }
         }
         if (lane < nv) a.part_counts[(size_t)lane * a.max_parts + part] = c;
@@ -460,7 +469,7 @@ __global__ void __launch_bounds__(kBlock) k_list_scatter(ListArgs a)
     }
     const unsigned long long all = __shfl_sync(0xffffffffu, base, 31);
     base -= tot;
-    const uint32_t sbase = lane < nv ? a.views[lane].slot_base : 0u;
+    const uint32_t stride = a.slot_stride;  // view v's slot of Gaussian g is v * stride + g
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.counters->n_pairs = all;
         if (all > cap) atomicOr(&a.counters->status, kStatusOverflow);
@@ -468,34 +477,55 @@ __global__ void __launch_bounds__(kBlock) k_list_scatter(ListArgs a)
     }
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t warps = gridDim.x * (kBlock / 32);
+    constexpr uint32_t kNone = 0xffffffffu;
     for (uint32_t part = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); part < parts; part += warps) {
         const uint32_t first = part * kListPart, last = min(first + kListPart, n);
-        unsigned long long run = lane < nv ? base + a.part_counts[(size_t)lane * a.max_parts + part] : 0ull;
+        // lane v: view v's next position, clamped at the capacity (positions past it are not
+        // written; the overflow is flagged above)
+        unsigned long long r64 = lane < nv ? base + a.part_counts[(size_t)lane * a.max_parts + part] : 0ull;
+        uint32_t run = (uint32_t)(r64 < cap ? r64 : cap);
+        const uint32_t key_before = first > 0 ? __ldg(&keys[first - 1]) : kNone;
+        const uint32_t key_after = last < n ? __ldg(&keys[last]) : kNone;
+        // loads run ahead: this round's value, key and mask, the next round's value and key
+        uint32_t j = first + (uint32_t)lane;
+        uint32_t g = j < last ? __ldg(&vals[j]) : 0u, t = j < last ? __ldg(&keys[j]) : kNone;
+        uint32_t g1 = j + 32 < last ? __ldg(&vals[j + 32]) : 0u, t1 = j + 32 < last ? __ldg(&keys[j + 32]) : kNone;
+        uint32_t m = j < last ? __ldg(&a.vmask[g]) : 0u;
+        uint32_t t_prev = key_before;  // the previous round's keys (every lane: the key before)
         for (uint32_t j0 = first; j0 < last; j0 += 32) {
-            const uint32_t j = j0 + (uint32_t)lane;
+            j = j0 + (uint32_t)lane;
             const bool ok = j < last;
-            const uint32_t g = ok ? __ldg(&vals[j]) : 0u;
-            const uint32_t m = ok ? __ldg(&a.vmask[g]) : 0u;
-            const uint32_t t = ok ? __ldg(&keys[j]) : 0xffffffffu;
+            const uint32_t m1 = j + 32 < last ? __ldg(&a.vmask[g1]) : 0u;
+            const uint32_t g2 = j + 64 < last ? __ldg(&vals[j + 64]) : 0u;
+            const uint32_t t2 = j + 64 < last ? __ldg(&keys[j + 64]) : kNone;
             uint32_t tp = __shfl_up_sync(0xffffffffu, t, 1);
             uint32_t tn = __shfl_down_sync(0xffffffffu, t, 1);
-            if (lane == 0) tp = j > 0 && ok ? __ldg(&keys[j - 1]) : 0xffffffffu;
-            if (lane == 31 || j + 1 >= last) tn = ok && j + 1 < n ? __ldg(&keys[j + 1]) : 0xffffffffu;
+            const uint32_t round_before = __shfl_sync(0xffffffffu, t_prev, 31);
+            const uint32_t round_after = __shfl_sync(0xffffffffu, t1, 0);
+            if (lane == 0) tp = round_before;
+            if (j + 1 == last) tn = key_after;
+            else if (lane == 31) tn = round_after;
             const bool start = ok && tp != t, end = ok && tn != t;
-            for (int v = 0; v < nv; ++v) {
+            uint32_t gv = g;  // the pair's slot in view v
+            for (int v = 0; v < nv; ++v, gv += stride) {
                 const bool bit = ((m >> v) & 1u) != 0u;
                 const uint32_t b = __ballot_sync(0xffffffffu, bit);
-                const unsigned long long pos = __shfl_sync(0xffffffffu, run, v) + (unsigned)__popc(b & lt);
-                const uint32_t sb = __shfl_sync(0xffffffffu, sbase, v);   // every lane takes part
-                if (bit && pos < cap) out[pos] = sb + g;
+                const uint32_t pos = __shfl_sync(0xffffffffu, run, v) + (uint32_t)__popc(b & lt);
+                if (bit && pos < cap) out[pos] = gv;
                 if (start || end) {
                     int2 *rg = &a.ranges[((uint32_t)v << a.tile_bits) | t];
                     if (start) rg->x = (int)(pos < cap ? pos : cap);
-                    const unsigned long long e = pos + (bit ? 1u : 0u);
+                    const uint32_t e = pos + (bit ? 1u : 0u);
                     if (end) rg->y = (int)(e < cap ? e : cap);
                 }
-                if (lane == v) run += (unsigned)__popc(b);
+                if (lane == v) {
+                    const uint32_t nr = run + (uint32_t)__popc(b);
+                    run = nr < cap ? nr : cap;
+                }
             }
+            t_prev = t;
+            g = g1; t = t1; m = m1;
+            g1 = g2; t1 = t2;
         }
     }
 }

@@ -298,6 +298,7 @@ struct ListArgs {
     const ViewDev *views;
     int num_views;
     int tile_bits;
+    uint32_t slot_stride;               // the scene's size: view v's slot of Gaussian g is v * slot_stride + g
     uint32_t *part_counts;              // [kListViews][max_parts] counts, then exclusive prefixes,
                                         // followed by the kListViews view totals
     uint32_t max_parts;                 // >= cap_pairs / kListPart rounded up

@@ -155,17 +155,26 @@ __device__ __forceinline__ void render_item(const RenderArgs &a, const ViewDev &
                 done = done || stop;
             };
             if (mw == 0u) {
-                // no entry of the chunk needs the decay weight (most chunks): no per-entry test
+                // no entry of the chunk needs the decay weight (most chunks): no per-entry
+                // test, two entries per loop trip
                 while (m) {
                     const int bit = __ffs(m) - 1;
                     m &= m - 1;
                     step(bit, false);
+                    if (!m) break;
+                    const int bit2 = __ffs(m) - 1;
+                    m &= m - 1;
+                    step(bit2, false);
                 }
             } else {
                 while (m) {
                     const int bit = __ffs(m) - 1;
                     m &= m - 1;
                     step(bit, ((mw >> bit) & 1u) != 0u);
+                    if (!m) break;
+                    const int bit2 = __ffs(m) - 1;
+                    m &= m - 1;
+                    step(bit2, ((mw >> bit2) & 1u) != 0u);
                 }
             }
         } else {
