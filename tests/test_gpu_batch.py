@@ -204,9 +204,12 @@ def test_one_camera_batch_sorts_once_and_equals_single_renders():
                 torch.cuda.synchronize()
                 assert np.array_equal(img, i0.cpu().numpy()) and np.array_equal(T, T0.cpu().numpy())
                 assert np.array_equal(nc, n0.cpu().numpy())
-                if not graph:   # the same tile lists as the single render's
+                if not graph:   # the same tile lists and per-Gaussian exports as the single render's
                     for a, b in zip(_pairs(r.ctx, k), _pairs(single.ctx, 0)):
                         assert np.array_equal(a, b)
+                    ga, gb = r.frame_gaussians(sc.n, k), single.frame_gaussians(sc.n, 0)
+                    for key in ga:
+                        assert torch.equal(ga[key], gb[key]), key
         finally:
             single.close()
 
@@ -280,3 +283,44 @@ def test_one_camera_batch_beyond_shared_list_views():
     finally:
         r.close()
         single.close()
+
+
+def test_one_camera_batch_backward_equals_single_view_backwards():
+    """The backward of a one-camera batch (shared lists and records) against the sum of the
+    views' single-frame backwards: the parameter gradients agree up to the order of the
+    floating-point atomics, and every view's plane gradient too."""
+    sc = scenes.general_scene(12_000, seed=17, sh_degree=2)
+    cam = scenes.look_at_camera((0.9, -0.4, -2.6), (0.0, 0.0, 0.0), 144, 112, 60.0)
+    nrm = np.float32(scenes.random_unit_normal(19))
+    planes = [scenes.Plane(nrm, float(d), 3.0, m) for d, m in
+              zip(np.linspace(-0.5, 0.5, 5), [scenes.MODE_RARA, scenes.MODE_RARA_ALL, scenes.MODE_HARD,
+                                               scenes.MODE_RARA, scenes.MODE_NONE])]
+    gs = rara.GaussianTensors.from_scene(sc)
+    rng = np.random.default_rng(5)
+    dimgs = [torch.from_numpy(np.float32(rng.standard_normal((3, cam.height, cam.width)))).cuda() for _ in planes]
+
+    def grads_of(views_planes, dims):
+        ctx = rara.rara_ctx_create(0)
+        try:
+            vs = [rara.View(0, cam, p, torch.empty((3, cam.height, cam.width), device="cuda"),
+                            torch.empty((cam.height, cam.width), device="cuda"),
+                            torch.empty((cam.height, cam.width), dtype=torch.int32, device="cuda"))
+                  for p in views_planes]
+            rara.rara_render_batch(ctx, [gs], vs)
+            g = gs.empty_like()
+            pg = torch.empty((len(vs), 4), device="cuda")
+            rara.rara_render_backward(ctx, dims, [g], pg)
+            torch.cuda.synchronize()
+            return [t.cpu().numpy().astype(np.float64) for t in
+                    (g.means, g.log_scales, g.quats, g.opacity_logits, g.sh)], pg.cpu().numpy().astype(np.float64)
+        finally:
+            rara.rara_ctx_destroy(ctx)
+
+    batch, batch_pg = grads_of(planes, dimgs)
+    total = None
+    for k, p in enumerate(planes):
+        one, one_pg = grads_of([p], [dimgs[k]])
+        total = one if total is None else [a + b for a, b in zip(total, one)]
+        assert np.allclose(batch_pg[k], one_pg[0], rtol=1e-4, atol=1e-6)
+    for a, b in zip(batch, total):
+        assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b) + 1e-7
