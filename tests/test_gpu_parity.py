@@ -272,3 +272,43 @@ def test_shells_batch_full_size_two_views_sampled_rows():
             assert gpu["info"]["n_cutoff"] > 1000
     finally:
         rara.rara_ctx_destroy(ctx)
+
+
+def test_general_sweep_batch_in_the_benchmark_launch_configuration():
+    """The benchmark's own launch configuration at full size: the 16-offset plane sweep of the
+    1M-Gaussian SH3 scene at 1920x1080 as one batch (one camera: one depth order and one shared
+    tile list), 16x32 tiles, 256-entry blend batches, one lane per pixel, rendered through the
+    CUDA graph (capture, then a replay); three views checked against the oracle binned with the
+    same tile: every label, tile count and list, and a band of 32 image rows."""
+    from paper_2506_20202_gb300 import autotune, rara
+    scene, cam, planes = scenes.general_workload()
+    gs = rara.GaussianTensors.from_scene(scene)
+    ctx = rara.rara_ctx_create(0)
+    try:
+        autotune.apply(ctx, (16, 32, 256, 33, 33))
+        views = [rara.View(0, cam, p, torch.empty((3, cam.height, cam.width), device="cuda"),
+                           torch.empty((cam.height, cam.width), device="cuda"),
+                           torch.empty((cam.height, cam.width), dtype=torch.int32, device="cuda")) for p in planes]
+        rara.rara_render_batch_graph(ctx, [gs], views)   # exact render, then the capture
+        rara.rara_render_batch_graph(ctx, [gs], views)   # a replay
+        rara.rara_ctx_sync(ctx)
+        assert rara.rara_frame_info_get(ctx, 0)["n_shared_pairs"] > 0     # the shared listing ran
+        for k in (2, 8, 12):       # 0.4%, 18% and 70% of the Gaussians cutoff
+            pl = planes[k]
+            gpu = _batch_view(ctx, k, scene.n)
+            gpu["image"] = views[k].image.cpu().numpy().astype(np.float64)
+            gpu["T"] = views[k].final_T.cpu().numpy().astype(np.float64)
+            report = {}
+            pre = oracle.preprocess(scene, cam, pl, tile=(16, 32))
+            kvr = oracle.build_keys(pre)
+            parity.check_gaussians(pre, gpu["g"], report)
+            parity.check_pairs(pre, kvr, gpu, report)
+            rows = (520, 552)
+            ref = oracle.render(scene, pre, cam, pl, (0.0, 0.0, 0.0), kvr, rows=rows)
+            # the oracle flags up to 2.7% of these bands (events near its thresholds)
+            parity.check_image(pre, ref, gpu, report, rows=rows, max_flag_frac=0.05)
+            print(k, report)
+            assert report["pixels"] == 32 * cam.width
+            assert gpu["info"]["n_cutoff"] > 1000
+    finally:
+        rara.rara_ctx_destroy(ctx)
