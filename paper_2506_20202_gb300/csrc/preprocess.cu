@@ -545,16 +545,37 @@ __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
         uint32_t key[kCompactItems];
         bool flag[kCompactItems];
         unsigned cnt = 0;
+        // the thread's consecutive items: 16-byte loads when all are in range (the arrays are
+        // 256-byte aligned and first is a multiple of kCompactItems), else one by one
+        uint32_t tk[kCompactItems], dk[kCompactItems];
+        const bool whole = first + kCompactItems <= a.num_slots;
+        const uint32_t *src0 = a.gkey ? a.gkey : a.tiles;
+#pragma unroll
+        for (int q = 0; q < kCompactItems / 4; ++q) {
+            uint4 t = make_uint4(0u, 0u, 0u, 0u), d = make_uint4(0u, 0u, 0u, 0u);
+            if (whole) {
+                t = __ldg(reinterpret_cast<const uint4 *>(src0 + first) + q);
+                if (!a.gkey) d = __ldg(reinterpret_cast<const uint4 *>(a.depth + first) + q);
+            }
+            tk[4 * q] = t.x; tk[4 * q + 1] = t.y; tk[4 * q + 2] = t.z; tk[4 * q + 3] = t.w;
+            dk[4 * q] = d.x; dk[4 * q + 1] = d.y; dk[4 * q + 2] = d.z; dk[4 * q + 3] = d.w;
+        }
+        if (!whole) {
+#pragma unroll
+            for (int r = 0; r < kCompactItems; ++r) {
+                const uint32_t slot = first + r;
+                tk[r] = slot < a.num_slots ? src0[slot] : (a.gkey ? kNoKey : 0u);
+                dk[r] = !a.gkey && slot < a.num_slots ? __float_as_uint(a.depth[slot]) : 0u;
+            }
+        }
 #pragma unroll
         for (int r = 0; r < kCompactItems; ++r) {
-            const uint32_t slot = first + r;  // a Gaussian index with gkey
-            if (a.gkey) {
-                const uint32_t k = slot < a.num_slots ? a.gkey[slot] : kNoKey;
-                flag[r] = k != kNoKey;
-                key[r] = flag[r] ? k : 0u;
-            } else {
-                flag[r] = slot < a.num_slots && a.tiles[slot] != 0u;
-                key[r] = flag[r] ? __float_as_uint(a.depth[slot]) : 0u;
+            if (a.gkey) {   // tk: the Gaussian's depth key, or kNoKey
+                flag[r] = tk[r] != kNoKey;
+                key[r] = flag[r] ? tk[r] : 0u;
+            } else {        // tk: the slot's tile count; dk: its depth bits
+                flag[r] = tk[r] != 0u;
+                key[r] = flag[r] ? dk[r] : 0u;
             }
             if (flag[r]) {
                 ++cnt;
