@@ -145,7 +145,7 @@ int rara_ctx_create(size_t budget_bytes, int32_t tile_w, int32_t tile_h, rara_ct
  * batches: 128, 256 or 512 list entries staged in shared memory by the whole block per render
  * batch, or 32 for each warp staging and walking its own 32-entry chunks (no block barrier
  * inside a work item); the
- * autotuner's knobs (the paper renders 16 x 16 tiles; the batch depth is this build's). The
+ * autotuner's knobs (the paper renders 16 x 16 tiles and names no batch depth). The
  * current frame's state is dropped when the tile changes, and a captured graph is
  * recaptured on the next rara_render_batch_graph. RARA_ERR_INVALID_ARG for unsupported
  * values. */

@@ -2,7 +2,7 @@
 clipping reproduces the RaRa-clipped images.
 
 The paper leaves re-optimising Gaussians after clipping to future work (Discussion,
-Limitations) and gives no method, so the objective here is this build's own. Given a scene,
+Limitations) and gives no method, so the objective is defined here. Given a scene,
 a clip plane and a set of cameras, the target is the RaRa render of the whole scene
 (Algorithm 1) from each camera. The baked scene drops the invisible Gaussians (Section 3.2:
 they never contribute) and keeps the visible ones unchanged (their decay weight is 1, so they
