@@ -291,6 +291,25 @@ typedef struct rara_gaussian_grads {
 int rara_render_backward(rara_ctx *ctx, const float *const *dL_dimages, const rara_gaussian_grads *grads,
                          float *plane_grads, void *stream);
 
+/* The L2 objective of a differentiation step on the last render's images, with its gradient,
+ * in one launch (the input rara_render_backward takes). The paper renders only; re-fitting
+ * Gaussians after clipping, which its Discussion leaves to future work, needs an objective,
+ * and the differentiation workload and the baking loop use this one. For every view v of the
+ * last render (the caller's view order) with d = image_v - target_v over its [3][H][W] image:
+ *   loss[v] = scale[v] * sum(d^2)   and   dL_dimages[v] = 2 scale[v] d
+ * (scale[v] = 1 / (3 H W) makes loss[v] the view's mean squared error).
+ *   targets     [num_views] device pointers, view v's target [3][H][W], read
+ *   dL_dimages  [num_views] device pointers, view v's gradient [3][H][W], written; it may be
+ *               the target itself, not the rendered image
+ *   scale       host float[num_views]
+ *   loss        device double[num_views], written
+ * Returns RARA_ERR_INVALID_ARG if there is no rendered frame or batch on the context, a
+ * pointer is NULL, a gradient output is the rendered image or a scale is not finite.
+ * Asynchronous on `stream`; the loss sums use double atomics, so their last bits are not
+ * reproducible. */
+int rara_loss_l2(rara_ctx *ctx, const float *const *targets, float *const *dL_dimages, const float *scale,
+                 double *loss, void *stream);
+
 /* GPU milliseconds of the last rara_render_backward: [0] the per-tile render backward,
  * [1] the per-Gaussian preprocess backward. Waits for them to finish. */
 int rara_ctx_backward_ms(rara_ctx *ctx, float out[2]);

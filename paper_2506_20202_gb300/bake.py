@@ -152,15 +152,12 @@ class GpuBake:
                                      torch.empty((c.height, c.width), dtype=torch.int32, device="cuda"), self.bg)
                            for c in self.cameras]
             self._dimg = [torch.empty_like(v.image) for v in self._views]
+            self._loss = torch.empty(len(self._views), dtype=torch.float64, device="cuda")
             self._grads = gs.empty_like()
         rara.rara_render_batch(self.ctx, [gs], self._views)
-        loss = torch.zeros((), device="cuda")
-        for v, t, d in zip(self._views, self.targets, self._dimg):
-            torch.sub(v.image, t, out=d)
-            loss += (d * d).sum()
-            d.mul_(2.0)
+        rara.rara_loss_l2(self.ctx, self.targets, self._dimg, [1.0] * len(self._views), self._loss)
         rara.rara_render_backward(self.ctx, self._dimg, [self._grads], None)
-        return float(loss), {k: getattr(self._grads, k) for k in PARAMS}
+        return float(self._loss.sum()), {k: getattr(self._grads, k) for k in PARAMS}
 
     def errors(self, cameras=None):
         """Mean squared error against the RaRa render of the original scene, on the fitting

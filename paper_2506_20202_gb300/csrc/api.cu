@@ -17,6 +17,7 @@ namespace {
 struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
+    unsigned gen = 0;  // bumped whenever the allocation is replaced or released
 };
 
 constexpr int kMaxViews = 4096;
@@ -93,9 +94,17 @@ struct rara_ctx {
 
     // backward: gradient records, tables of the dL/dimage and gradient pointers
     DevBuf grec, bviews_d, bscenes_d;
+    // grec is known to be all zero (allocation generation grec_zero_gen): the preprocess
+    // backward zeroes every record it reads, and the render backward adds only to those
+    bool grec_zero = false;
+    unsigned grec_zero_gen = 0;
     BwdView *h_bviews = nullptr;        // pinned [max_views]
     BwdScene *h_bscenes = nullptr;      // pinned [max_scenes]
     cudaEvent_t bwd_uploaded = nullptr;
+    // the L2 objective (rara_loss_l2): its view table
+    DevBuf lviews_d;
+    LossView *h_lviews = nullptr;       // pinned [max_views]
+    cudaEvent_t loss_uploaded = nullptr;
     cudaEvent_t bev[3] = {nullptr, nullptr, nullptr};
     int bpsm_render_bwd = 0;
 
@@ -163,6 +172,7 @@ int ensure(rara_ctx *c, DevBuf &b, size_t bytes, const char *name)
         b.p = nullptr;
         b.cap = 0;
     }
+    ++b.gen;
     cudaError_t e = cudaMalloc(&b.p, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -180,6 +190,7 @@ void release(rara_ctx *c, DevBuf &b)
     c->held -= b.cap;
     b.p = nullptr;
     b.cap = 0;
+    ++b.gen;
 }
 
 bool finite(float v) { return isfinite(v) != 0; }
@@ -696,6 +707,8 @@ void free_host(rara_ctx *c)
     if (c->h_bviews) cudaFreeHost(c->h_bviews);
     if (c->h_bscenes) cudaFreeHost(c->h_bscenes);
     if (c->bwd_uploaded) cudaEventDestroy(c->bwd_uploaded);
+    if (c->h_lviews) cudaFreeHost(c->h_lviews);
+    if (c->loss_uploaded) cudaEventDestroy(c->loss_uploaded);
     for (cudaEvent_t &e : c->bev)
         if (e) cudaEventDestroy(e);
     if (c->h_counters) cudaFreeHost(c->h_counters);
@@ -744,6 +757,8 @@ int rara_ctx_create(size_t budget_bytes, int32_t tile_w, int32_t tile_h, rara_ct
     ok = ok && cudaHostAlloc((void **)&c->h_bscenes, sizeof(BwdScene) * kMaxScenes, cudaHostAllocDefault) ==
                    cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&c->bwd_uploaded, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaHostAlloc((void **)&c->h_lviews, sizeof(LossView) * kMaxViews, cudaHostAllocDefault) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&c->loss_uploaded, cudaEventDisableTiming) == cudaSuccess;
     for (cudaEvent_t &e : c->bev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -765,7 +780,7 @@ int rara_ctx_destroy(rara_ctx *c)
                      &c->rect, &c->rec, &c->cut, &c->cut_x, &c->depth, &c->ckeys, &c->cvals, &c->ckeys_b, &c->cvals_b,
                      &c->lookback_c, &c->pkeys, &c->pvals, &c->pkeys_b, &c->pvals_b, &c->lookback_e, &c->hist,
                      &c->ranges, &c->items, &c->sort_scratch, &c->grec, &c->bviews_d, &c->bscenes_d,
-                     &c->seg_base, &c->export_off, &c->gkey, &c->vmask, &c->list_counts};
+                     &c->seg_base, &c->export_off, &c->gkey, &c->vmask, &c->list_counts, &c->lviews_d};
     for (DevBuf *b : all) release(c, *b);
     free_host(c);
     delete c;
@@ -1145,8 +1160,13 @@ int rara_render_backward(rara_ctx *c, const float *const *dL_dimages, const rara
         (rc = check_cuda(c, cudaEventRecord(c->bwd_uploaded, s), "backward table event")))
         return rc;
     Counters *dc = (Counters *)c->counters.p;
-    if ((rc = check_cuda(c, cudaMemsetAsync(c->grec.p, 0, nn * sizeof(GradRec), s), "memset gradient records")) ||
-        (rc = check_cuda(c, cudaMemsetAsync(&dc->bwd_queue, 0, sizeof(unsigned int), s), "memset queue")))
+    // The records are cleared in full only when the buffer is new or the last backward did not
+    // complete both launches; otherwise the last preprocess backward left them zero.
+    if (!(c->grec_zero && c->grec_zero_gen == c->grec.gen) &&
+        (rc = check_cuda(c, cudaMemsetAsync(c->grec.p, 0, c->grec.cap, s), "memset gradient records")))
+        return rc;
+    c->grec_zero = false;
+    if ((rc = check_cuda(c, cudaMemsetAsync(&dc->bwd_queue, 0, sizeof(unsigned int), s), "memset queue")))
         return rc;
     if (plane_grads &&
         (rc = check_cuda(c, cudaMemsetAsync(plane_grads, 0, sizeof(float) * 4 * (size_t)c->num_views, s),
@@ -1178,10 +1198,12 @@ int rara_render_backward(rara_ctx *c, const float *const *dL_dimages, const rara
     pa.bscenes = (const BwdScene *)c->bscenes_d.p;
     pa.labels = (const uint8_t *)c->labels.p;
     pa.tiles = (const uint32_t *)c->tiles.p;
-    pa.grec = (const GradRec *)c->grec.p;
+    pa.grec = (GradRec *)c->grec.p;
     if (launch_preprocess_bwd(pa, (int)c->num_units, max_degree, s))
         return fail(c, RARA_ERR_CUDA, "preprocess backward: shared-memory size not accepted");
     if ((rc = launched(c, "preprocess backward launch", c->num_units > 0))) return rc;
+    c->grec_zero = true;
+    c->grec_zero_gen = c->grec.gen;
     // Gaussians of scenes without views get zero gradients
     for (int si = 0; si < c->num_scenes; ++si) {
         const SceneDev &sd = c->h_scenes[si];
@@ -1198,6 +1220,50 @@ int rara_render_backward(rara_ctx *c, const float *const *dL_dimages, const rara
     cudaEventRecord(c->bev[2], s);
     c->last_stream = s;
     return RARA_OK;
+}
+
+int rara_loss_l2(rara_ctx *c, const float *const *targets, float *const *dL_dimages, const float *scale,
+                 double *loss, void *stream)
+{
+    if (!c) return RARA_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (!c->owns_host) return fail(c, RARA_ERR_INVALID_ARG, "the static context has no loss");
+    if (!c->rendered || c->stage < 2)
+        return fail(c, RARA_ERR_INVALID_ARG, "rara_loss_l2 needs a rendered frame or batch on this context");
+    if (!targets || !dL_dimages || !scale || !loss) return fail(c, RARA_ERR_INVALID_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    // the pinned table is refilled only after its last upload has been read
+    if ((rc = check_cuda(c, cudaEventSynchronize(c->loss_uploaded), "loss table wait"))) return rc;
+    uint64_t chunks = 0;
+    for (int v = 0; v < c->num_views; ++v) {
+        if (!targets[v] || !dL_dimages[v]) return fail(c, RARA_ERR_INVALID_ARG, "view %d has a null target or gradient", v);
+        if (!finite(scale[v])) return fail(c, RARA_ERR_INVALID_ARG, "view %d has a non-finite scale", v);
+        const ViewDev &vd = c->h_views[c->h_view_map[v]];
+        if (dL_dimages[v] == vd.image)
+            return fail(c, RARA_ERR_INVALID_ARG, "view %d: the gradient output is the rendered image", v);
+        const uint64_t n = 3ull * (uint64_t)vd.cam.W * (uint64_t)vd.cam.H;
+        if (n > 0xffffffffull) return fail(c, RARA_ERR_INVALID_ARG, "view %d has more than 2^32 image elements", v);
+        LossView &l = c->h_lviews[v];
+        l.image = vd.image;
+        l.target = targets[v];
+        l.dimage = dL_dimages[v];
+        l.loss = loss + v;
+        l.scale = scale[v];
+        l.n = (uint32_t)n;
+        l.chunk_begin = (uint32_t)chunks;
+        l.pad = 0;
+        chunks += (n + kLossChunk - 1) / kLossChunk;
+    }
+    if (chunks > 0x7fffffffull) return fail(c, RARA_ERR_INVALID_ARG, "the batch's images need too many blocks");
+    if ((rc = ensure(c, c->lviews_d, sizeof(LossView) * (size_t)(c->num_views > 0 ? c->num_views : 1), "loss view table")) ||
+        (rc = check_cuda(c, cudaMemcpyAsync(c->lviews_d.p, c->h_lviews, sizeof(LossView) * (size_t)c->num_views,
+                                            cudaMemcpyHostToDevice, s), "loss view table upload")) ||
+        (rc = check_cuda(c, cudaEventRecord(c->loss_uploaded, s), "loss table event")) ||
+        (rc = check_cuda(c, cudaMemsetAsync(loss, 0, sizeof(double) * (size_t)c->num_views, s), "memset loss")))
+        return rc;
+    launch_loss_l2((const LossView *)c->lviews_d.p, c->num_views, (uint32_t)chunks, s);
+    return launched(c, "loss launch", chunks > 0 && c->num_views > 0);
 }
 
 int rara_ctx_backward_ms(rara_ctx *c, float out[2])

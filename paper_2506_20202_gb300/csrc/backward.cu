@@ -42,28 +42,23 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 // Gradient of the decay weight where the plane splits the chord (0 < w < 1); returns false
-// (no gradient) where w is constant. It repeats rara_weight's arithmetic; with
-// w = 1/2 + s_mid / (2 H), H = sqrt(h2) |m.V| / |V|, it goes back through
+// (no gradient) where w is constant. It starts from the terms rara_weight_terms computed for
+// the weight itself (sp); with w = 1/2 + s_mid / (2 H), H = sqrt(h2) |m.V| / |V|, it goes back through
 // s_mid = d_ep + m.p - f (m.V), f = (G.p + p.p) / V.V, h2 = 1 - |u|^2 / V.V,
 // V.V = G.G + 2 G.p + p.p, m.V = m.G + m.p and the per-pixel polynomials G.p, p.p, m.p,
-// u = dx A + dy B. c0..c3 is the record's staged form (stage_cut), r2, r3 its own c2, c3
+// u = dx A + dy B. c0..c2 is the record's staged form (stage_cut), r2, r3 its own c2, c3
 // (which hold A and B). Outputs: dL/d(record products) in CutRec order (c0.x .. c3.w) in
 // gc[16], and dL/d(dx, dy) added to gdx, gdy.
-__device__ __forceinline__ bool rara_weight_grad(const float4 c0, const float4 c1, const float4 c2, const float4 c3,
-                                                 const float4 r2, const float4 r3, float dx, float dy, float gw,
-                                                 float gc[16], float &gdx, float &gdy)
+__device__ __forceinline__ bool rara_weight_grad(const SplitTerms &sp, const float4 c0, const float4 c1,
+                                                 const float4 c2, const float4 r2, const float4 r3, float dx, float dy,
+                                                 float gw, float gc[16], float &gdx, float &gdy)
 {
-    const RayTerms t = ray_terms(c0, c1, c2, c3, dx, dy);
-    if (!ray_hits_front(t)) return false;
-    const float mp = fmaf(c2.x, dx, c2.y * dy);
-    const float mV = c1.w + mp;
-    {   // w is constant (0 or 1) unless rara_weight's unclamped share lies strictly inside (0, 1)
-        const float num = fmaf(c0.w + mp, t.VV, -__fmul_rn(t.Gp + t.pp, mV));
-        const float den2 = __fmul_rn(t.VV - t.uu, __fmul_rn(mV, mV));
-        const float v = fmaf(__fmul_rn(num, rsqrtf(den2)), 0.5f, 0.5f);
-        if (!(v > 0.0f && v < 1.0f)) return false;
-    }
-    const float h2 = 1.0f - t.cc;
+    // w is constant (0 or 1) unless the ray hits and the unclamped share lies strictly inside (0, 1)
+    if (!(sp.hit && sp.v > 0.0f && sp.v < 1.0f)) return false;
+    const RayTerms &t = sp.t;
+    const float mp = sp.mp, mV = sp.mV;
+    const float cc = __fmul_rn(t.uu, t.rVV);
+    const float h2 = 1.0f - cc;
     const float f = __fmul_rn(t.Gp + t.pp, t.rVV);
     const float smid = c0.w + fmaf(-f, mV, mp);
     // H > 0 and mV != 0 here (the share is finite and strictly inside (0, 1)), h2 > 0 (cc < 1)
@@ -80,7 +75,7 @@ __device__ __forceinline__ bool rara_weight_grad(const float4 c0, const float4 c
     g_VV -= g_f * f * iVV;
     const float g_cc = -g_h2;
     const float g_uu = g_cc * iVV;
-    g_VV -= g_cc * t.cc * iVV;
+    g_VV -= g_cc * cc * iVV;
     const float g_Gp = 2.0f * g_VV + g_pV;
     const float g_pp = g_VV + g_pV;
     gc[0] = g_VV;                       // G.G
@@ -229,8 +224,10 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
                         const float a0 = splat_alpha0(q, s1.y);
                         if (a0 >= kAlphaMin) {
                             float w = 1.0f;
-                            if (mode != kWeightNone)
-                                w = decay_weight(mode, st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
+                            SplitTerms sp;  // a split weight's terms, reused by its gradient
+                            if (cut) w = rara_weight_terms(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy, sp);
+                            else if (mode != kWeightNone)
+                                w = rara_weight_hidden(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
                             const float au = __fmul_rn(a0, w);
                             const float alpha = fminf(kAlphaMax, au);
                             if (alpha >= kAlphaMin) {
@@ -258,8 +255,8 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
                                 float gdx = 2.0f * gq * fmaf(ca, dx, cb * dy);
                                 float gdy = 2.0f * gq * fmaf(cb, dx, cc * dy);
                                 if (cut)
-                                    rara_weight_grad(st.c0[j], st.c1[j], st.c2[j], st.c3[j], s_ab[0][j], s_ab[1][j], dx, dy, ga * a0, gc, gdx,
-                                                     gdy);
+                                    rara_weight_grad(sp, st.c0[j], st.c1[j], st.c2[j], s_ab[0][j], s_ab[1][j], dx, dy, ga * a0, gc,
+                                                     gdx, gdy);
                                 gmx = -gdx;
                                 gmy = -gdy;
                             }
@@ -578,6 +575,12 @@ __global__ void __launch_bounds__(kBlock, 2) k_preprocess_bwd(PreprocessBwdArgs 
                 // ---- camera-space mean t = W mu + t0
 #pragma unroll
                 for (int j = 0; j < 3; ++j) gmu[j] += cam.R[j] * gt[0] + cam.R[3 + j] * gt[1] + cam.R[6 + j] * gt[2];
+                // leave the record zeroed for the next backward: the render backward adds to
+                // v[0..8] of every listed slot and v[9..24] of split-weight (cutoff) slots only
+                float4 *gw = reinterpret_cast<float4 *>(a.grec[slot].v);
+                const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                gw[0] = z4; gw[1] = z4; gw[2] = z4;
+                if (cutoff) { gw[3] = z4; gw[4] = z4; gw[5] = z4; gw[6] = z4; }
             }
             const BwdView &bv = a.bviews[v];
             if (bv.plane_grad && __any_sync(kFull, has_plane)) {
@@ -615,6 +618,64 @@ __global__ void __launch_bounds__(kBlock, 2) k_preprocess_bwd(PreprocessBwdArgs 
     for (int k = 0; k < 3 * K; ++k) bs.sh[(size_t)k * n + i] = s_gsh[k * kBlock + threadIdx.x];
 }
 
+// The L2 objective of the differentiation step on the rendered images: d = image - target,
+// loss += scale sum(d^2), dimage = 2 scale d. A block takes kLossChunk consecutive elements
+// of one view (16 per thread: four float4 loads of each input, issued together, when the
+// chunk is whole and the pointers are 16-byte aligned) and adds its partial sum to the view's
+// loss once. The target is read with plain loads: it may be the gradient output itself.
+__global__ void __launch_bounds__(kBlock) k_loss_l2(const LossView *views, int num_views)
+{
+    const uint32_t b = blockIdx.x;
+    int lo = 0, hi = num_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].chunk_begin <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const LossView lv = views[lo];
+    const size_t e0 = (size_t)(b - lv.chunk_begin) * kLossChunk;
+    const float s2 = 2.0f * lv.scale;
+    float acc = 0.0f;
+    const bool vec = e0 + kLossChunk <= lv.n &&
+                     ((reinterpret_cast<uintptr_t>(lv.image) | reinterpret_cast<uintptr_t>(lv.target) |
+                       reinterpret_cast<uintptr_t>(lv.dimage)) & 15u) == 0;
+    if (vec) {
+        const float4 *im = reinterpret_cast<const float4 *>(lv.image + e0);
+        const float4 *tg = reinterpret_cast<const float4 *>(lv.target + e0);
+        float4 *dm = reinterpret_cast<float4 *>(lv.dimage + e0);
+        float4 x[4], t[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            x[r] = __ldg(&im[threadIdx.x + r * kBlock]);
+            t[r] = tg[threadIdx.x + r * kBlock];
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float4 d = make_float4(x[r].x - t[r].x, x[r].y - t[r].y, x[r].z - t[r].z, x[r].w - t[r].w);
+            acc = fmaf(d.x, d.x, fmaf(d.y, d.y, fmaf(d.z, d.z, fmaf(d.w, d.w, acc))));
+            dm[threadIdx.x + r * kBlock] = make_float4(s2 * d.x, s2 * d.y, s2 * d.z, s2 * d.w);
+        }
+    } else {
+        for (int r = 0; r < kLossChunk / kBlock; ++r) {
+            const size_t e = e0 + threadIdx.x + (size_t)r * kBlock;
+            if (e < lv.n) {
+                const float d = lv.image[e] - lv.target[e];
+                acc = fmaf(d, d, acc);
+                lv.dimage[e] = s2 * d;
+            }
+        }
+    }
+    __shared__ float s_part[kBlock / 32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < kBlock / 32 ? s_part[threadIdx.x] : 0.0f;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) atomicAdd(lv.loss, (double)v * (double)lv.scale);
+    }
+}
+
 }  // namespace
 
 int render_bwd_blocks_per_sm()
@@ -642,6 +703,11 @@ int launch_preprocess_bwd(const PreprocessBwdArgs &a_in, int grid, int max_sh_de
         return -1;
     k_preprocess_bwd<<<grid, kBlock, smem, s>>>(a);
     return 0;
+}
+
+void launch_loss_l2(const LossView *views, int num_views, uint32_t grid, cudaStream_t s)
+{
+    if (grid > 0 && num_views > 0) k_loss_l2<<<grid, kBlock, 0, s>>>(views, num_views);
 }
 
 }  // namespace rara

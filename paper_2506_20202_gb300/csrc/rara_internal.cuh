@@ -379,7 +379,7 @@ struct RenderBwdArgs {
     const ViewDev *views;
     const BwdView *bviews;
     int num_views;
-    GradRec *grec;        // [slots], zeroed before
+    GradRec *grec;        // [slots], all zero on entry
     Counters *counters;
 };
 void launch_render_bwd(const RenderBwdArgs &a, int grid, cudaStream_t s);
@@ -393,11 +393,26 @@ struct PreprocessBwdArgs {
     const BwdScene *bscenes;
     const uint8_t *labels;
     const uint32_t *tiles;
-    const GradRec *grec;
+    GradRec *grec;         // read, then zeroed, for every rendered slot
     int sh_stride;         // set by the launcher
 };
 // grid = preprocess units; max_sh_degree sizes the per-block SH gradient accumulators.
 int launch_preprocess_bwd(const PreprocessBwdArgs &a, int grid, int max_sh_degree, cudaStream_t s);
+
+// The L2 objective on a render's images (rara_loss_l2): per view its image, target, gradient
+// output and loss accumulator, and the first of its blocks (kLossChunk elements per block).
+struct LossView {
+    const float *image;
+    const float *target;
+    float *dimage;
+    double *loss;
+    float scale;
+    uint32_t n;            // elements, 3 H W
+    uint32_t chunk_begin;  // first block of this view
+    uint32_t pad;
+};
+constexpr int kLossChunk = 16 * kBlock;
+void launch_loss_l2(const LossView *views, int num_views, uint32_t grid, cudaStream_t s);
 
 // Debug exports of one view
 void launch_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_src, const uint32_t *tiles_src,

@@ -75,25 +75,39 @@ __device__ __forceinline__ bool ray_hits_front(const RayTerms &t)
 // (together: clamp(1/2 + s_mid / (2 |h|), 0, 1)).
 // Products that feed a sum are written with __fmul_rn so the forward and the backward,
 // which re-evaluates this function, round identically.
-__device__ __forceinline__ float rara_weight(const float4 c0, const float4 c1, const float4 c2, const float4 c3,
-                                             float dx, float dy)
+// rara_weight's intermediate values, which its gradient reuses.
+struct SplitTerms {
+    RayTerms t;
+    float mp, mV, v;  // m.p, m.V and the unclamped share 1/2 + s_mid / (2 H)
+    bool hit;
+};
+
+__device__ __forceinline__ float rara_weight_terms(const float4 c0, const float4 c1, const float4 c2, const float4 c3,
+                                                   float dx, float dy, SplitTerms &s)
 {
     // Every lane evaluates the whole expression and the cases are selected at the end, so a
     // warp whose pixels fall into different cases does not diverge; the values are the ones
     // the case-by-case form gives (the unselected ones may be NaN and are never used).
-    const RayTerms t = ray_terms(c0, c1, c2, c3, dx, dy);
-    const bool hit = ray_hits_front(t);
-    const float mp = fmaf(c2.x, dx, c2.y * dy);
-    const float mV = c1.w + mp;
+    s.t = ray_terms(c0, c1, c2, c3, dx, dy);
+    s.hit = ray_hits_front(s.t);
+    s.mp = fmaf(c2.x, dx, c2.y * dy);
+    s.mV = c1.w + s.mp;
     // With H = |h| the chord's ends are s_mid -/+ H and the visible share is
     // (s_mid + H) / (2 H) = 1/2 + s_mid / (2 H), which reaches 1 (or 0) exactly when both ends
     // are on the visible (or the invisible) side: clamped to [0, 1] it is w in every case.
     // Multiplied through by V.V: s_mid / H = num / sqrt(den2) with
     //   num = (d_ep + m.p) V.V - (G.p + p.p) m.V,  den2 = (V.V - |u|^2) (m.V)^2.
-    const float num = fmaf(c0.w + mp, t.VV, -__fmul_rn(t.Gp + t.pp, mV));
-    const float den2 = __fmul_rn(t.VV - t.uu, __fmul_rn(mV, mV));
-    const float w = __saturatef(fmaf(__fmul_rn(num, rsqrtf(den2)), 0.5f, 0.5f));
-    return hit ? w : 1.0f;  // a ray that misses, grazes or starts inside keeps rasterization
+    const float num = fmaf(c0.w + s.mp, s.t.VV, -__fmul_rn(s.t.Gp + s.t.pp, s.mV));
+    const float den2 = __fmul_rn(s.t.VV - s.t.uu, __fmul_rn(s.mV, s.mV));
+    s.v = fmaf(__fmul_rn(num, rsqrtf(den2)), 0.5f, 0.5f);
+    return s.hit ? __saturatef(s.v) : 1.0f;  // a ray that misses, grazes or starts inside keeps rasterization
+}
+
+__device__ __forceinline__ float rara_weight(const float4 c0, const float4 c1, const float4 c2, const float4 c3,
+                                             float dx, float dy)
+{
+    SplitTerms s;
+    return rara_weight_terms(c0, c1, c2, c3, dx, dy, s);
 }
 
 // Decay weight of a Gaussian that several planes of a convex clip volume split

@@ -94,7 +94,8 @@ class GpuViews:
                                          torch.empty((H, W), device="cuda"),
                                          torch.empty((H, W), dtype=torch.int32, device="cuda"), self.bg))
             self.views[key] = (vv, [torch.empty_like(x.image) for x in vv],
-                               torch.empty((len(vv), 4), device="cuda"))
+                               torch.empty((len(vv), 4), device="cuda"),
+                               torch.empty(len(vv), dtype=torch.float64, device="cuda"))
         return self.views[key]
 
     def __call__(self, idx, events=None):
@@ -104,7 +105,7 @@ class GpuViews:
         is made to wait for it (the all-reduce and the optimiser run there)."""
         import torch
         rara = self.rara
-        views, dimgs, pg = self._views(idx)
+        views, dimgs, pg, lv = self._views(idx)
         # the render reads the parameters the caller's stream last updated (the optimiser step)
         self.stream.wait_stream(torch.cuda.current_stream())
         if not views:
@@ -112,12 +113,11 @@ class GpuViews:
         rara.rara_render_batch_graph(self.ctx, [self.scene], views, self.stream)
         if events:
             events[0].record(self.stream)
+        # per-view mean squared error and its gradient, one launch for the batch
+        rara.rara_loss_l2(self.ctx, [self.targets[k] for k in idx], dimgs, [1.0 / d.numel() for d in dimgs], lv,
+                          self.stream)
         with torch.cuda.stream(self.stream):
-            loss = torch.zeros((), device="cuda")
-            for v, k, d in zip(views, idx, dimgs):
-                torch.sub(v.image, self.targets[k], out=d)
-                loss += (d * d).mean()
-                d.mul_(2.0 / d.numel())
+            loss = lv.sum().float()
         if events:
             events[1].record(self.stream)
         rara.rara_render_backward(self.ctx, dimgs, [self.grads], pg, self.stream)

@@ -87,6 +87,7 @@ SIGNATURES = {
     "rara_render_batch_graph": (C.c_int, [_P, C.POINTER(rara_gaussians), C.c_int32, C.POINTER(rara_view), C.c_int32,
                                           _P]),
     "rara_render_backward": (C.c_int, [_P, C.POINTER(C.c_void_p), C.POINTER(rara_gaussian_grads), _P, _P]),
+    "rara_loss_l2": (C.c_int, [_P, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_float), _P, _P]),
     "rara_ctx_backward_ms": (C.c_int, [_P, C.POINTER(C.c_float)]),
     "rara_frame_info_get": (C.c_int, [_P, C.c_int32, C.POINTER(rara_frame_info)]),
     "rara_frame_gaussians": (C.c_int, [_P, C.c_int32] + [_P] * 9),
@@ -357,6 +358,21 @@ def rara_render_backward(ctx, dL_dimages, grads, plane_grads=None, stream=None):
     if plane_grads is not None:
         assert plane_grads.is_cuda and plane_grads.is_contiguous() and plane_grads.shape[-1] == 4
     _check(ctx, load().rara_render_backward(ctx, ptrs, gs, _ptr(plane_grads), _stream(stream)))
+
+
+def rara_loss_l2(ctx, targets, dL_dimages, scale, loss, stream=None):
+    """L2 objective of the last render on ctx: per view v, loss[v] = scale[v] * sum((image -
+    target)^2) and dL_dimages[v] = 2 scale[v] (image - target). targets, dL_dimages: one
+    [3, H, W] float32 CUDA tensor per view (the forward's view order; an output may be its
+    target); scale: floats; loss: [num_views] float64 CUDA tensor (written)."""
+    for t in list(targets) + list(dL_dimages):
+        assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"
+    assert len(targets) == len(dL_dimages) == len(scale)
+    assert loss.is_cuda and loss.is_contiguous() and str(loss.dtype) == "torch.float64" and loss.numel() >= len(scale)
+    tp = (C.c_void_p * len(targets))(*[t.data_ptr() for t in targets])
+    dp_ = (C.c_void_p * len(dL_dimages))(*[t.data_ptr() for t in dL_dimages])
+    sc = (C.c_float * len(scale))(*[float(x) for x in scale])
+    _check(ctx, load().rara_loss_l2(ctx, tp, dp_, sc, _ptr(loss), _stream(stream)))
 
 
 def rara_ctx_backward_ms(ctx):

@@ -149,6 +149,66 @@ def test_backward_after_graph_capture_and_replay():
     r.close()
 
 
+def test_repeated_backwards_on_one_context_start_from_zero_records():
+    """The per-slot gradient records are zeroed by the backward that read them, not by a
+    clear of the whole buffer: backwards of different batches (view counts, sizes, a
+    one-camera sweep) in turn on one context, each twice, equal those of fresh contexts."""
+    sc = scenes.gradient_scene(300, seed=41, sh_degree=1)
+    sweep_cam = _views(44, scenes.MODE_RARA, sizes=((72, 56),))[0][0]
+    batches = [_views(41, scenes.MODE_RARA, sizes=((64, 64), (80, 48), (48, 72))),
+               _views(42, scenes.MODE_RARA_ALL, sizes=((96, 80),)),
+               [(sweep_cam, scenes.Plane(np.float32(scenes.random_unit_normal(45)), float(o), 3.0, scenes.MODE_RARA),
+                 (0.1, 0.2, 0.3)) for o in (-0.1, 0.0, 0.1)],
+               _views(43, scenes.MODE_RARA, sizes=((64, 64), (80, 48), (48, 72), (56, 56)))]
+    r = rara.Renderer()
+    for k, views in enumerate(batches):
+        weights = _weights(sc, views, 50 + k)
+        ref = gpu_gradients(sc, views, weights)
+        for rep in range(2):
+            got = gpu_gradients(sc, views, weights, renderer=r)
+            for name in list(fd.PARAMS) + ["planes"]:
+                assert np.linalg.norm(ref[name]) > 0, (k, name)
+                assert fd.rel_l2(got[name], ref[name]) <= 1e-5, (k, rep, name, fd.rel_l2(got[name], ref[name]))
+    r.close()
+
+
+def test_l2_loss_entry_point_against_a_plain_reference():
+    """rara_loss_l2 on a batch of views of mixed sizes (whole and ragged blocks, an element
+    count that is not a multiple of 4): the per-view loss and gradient equal the plain
+    float64 expressions; an output may be its target; invalid calls are refused."""
+    sc = scenes.gradient_scene(400, seed=61, sh_degree=1)
+    views = _views(61, scenes.MODE_RARA, sizes=((64, 64), (37, 29), (96, 80)))
+    g = rara.GaussianTensors.from_scene(sc)
+    r = rara.Renderer()
+    try:
+        with pytest.raises(rara.RaraError):   # nothing rendered on the context yet
+            rara.rara_loss_l2(r.ctx, [], [], [], torch.empty(1, dtype=torch.float64, device="cuda"))
+        vs = [rara.View(0, cam, pl, torch.empty((3, cam.height, cam.width), device="cuda"), None, None, bg)
+              for cam, pl, bg in views]
+        rara.rara_render_batch(r.ctx, [g], vs)
+        gen = torch.Generator(device="cuda").manual_seed(5)
+        targets = [torch.rand(v.image.shape, generator=gen, device="cuda") for v in vs]
+        scale = [1.0 / v.image.numel() for v in vs[:2]] + [0.25]
+        for alias in (False, True):
+            tg = [t.clone() for t in targets]
+            out = tg if alias else [torch.empty_like(t) for t in tg]
+            loss = torch.full((len(vs),), float("nan"), dtype=torch.float64, device="cuda")
+            rara.rara_loss_l2(r.ctx, tg, out, scale, loss)
+            torch.cuda.synchronize()
+            for k, v in enumerate(vs):
+                d = v.image.double() - targets[k].double()
+                ref_loss = float(scale[k] * (d * d).sum())
+                assert abs(float(loss[k]) - ref_loss) <= 1e-5 * abs(ref_loss), (alias, k)
+                ref_grad = (v.image - targets[k]) * float(np.float32(2.0) * np.float32(scale[k]))
+                assert torch.allclose(out[k], ref_grad, rtol=1e-6, atol=1e-12), (alias, k)
+        with pytest.raises(rara.RaraError):   # the gradient output is the rendered image
+            rara.rara_loss_l2(r.ctx, targets, [v.image for v in vs], scale, loss)
+        with pytest.raises(rara.RaraError):   # a non-finite scale
+            rara.rara_loss_l2(r.ctx, targets, [torch.empty_like(t) for t in targets], [1.0, float("inf"), 1.0], loss)
+    finally:
+        r.close()
+
+
 def test_autograd_function_matches_the_c_entry_point():
     from paper_2506_20202_gb300 import autograd
     sc = scenes.gradient_scene(64, seed=41, sh_degree=1)
