@@ -381,6 +381,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_preprocess_bwd(PreprocessBwdArgs 
     float gopacity = 0.f;
 
     const int view_end = sc.view_begin + sc.view_count;
+    // Tile counts are loaded two views ahead, and the next view's gradient record is
+    // prefetched into L2 when that view renders the Gaussian: a view's record loads then
+    // neither wait behind its tile count nor, mostly, on DRAM.
+    auto tiles_of = [&](int v) -> uint32_t {
+        return (valid && v < view_end) ? __ldg(&a.tiles[__ldg(&a.views[v].slot_base) + (uint32_t)i]) : 0u;
+    };
+    uint32_t t1 = tiles_of(sc.view_begin), t2 = tiles_of(sc.view_begin + 1);
     for (int vbase = sc.view_begin; vbase < view_end; vbase += kViewChunkBwd) {
         const int nv = min(kViewChunkBwd, view_end - vbase);
         __syncthreads();  // the previous chunk's tables are no longer read
@@ -399,7 +406,15 @@ __global__ void __launch_bounds__(kBlock, 2) k_preprocess_bwd(PreprocessBwdArgs 
             float gpn[4] = {0.f, 0.f, 0.f, 0.f};
             bool has_plane = false;
             const uint32_t slot = vw.slot_base + (uint32_t)i;
-            if (valid && a.tiles[slot] != 0u) {
+            const uint32_t tiles_here = t1;
+            t1 = t2;
+            t2 = tiles_of(v + 2);
+            if (t1 != 0u) {
+                const char *nr = reinterpret_cast<const char *>(a.grec + (__ldg(&a.views[v + 1].slot_base) + (uint32_t)i));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(nr));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(nr + 96));
+            }
+            if (valid && tiles_here != 0u) {
                 const float *grc = a.grec[slot].v;
                 const float4 g0 = reinterpret_cast<const float4 *>(grc)[0];
                 const float4 g1 = reinterpret_cast<const float4 *>(grc)[1];

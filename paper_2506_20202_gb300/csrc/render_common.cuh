@@ -73,9 +73,9 @@ __device__ __forceinline__ bool ray_hits_front(const RayTerms &t)
 // where c is the chord's midpoint, m.c = m.p - (p.V / V.V)(m.V). w = 1 if both ends are on
 // the visible side, 0 if both are not, else the visible share max(s1, s2) / |s2 - s1|
 // (together: clamp(1/2 + s_mid / (2 |h|), 0, 1)).
-// Products that feed a sum are written with __fmul_rn so the forward and the backward,
-// which re-evaluates this function, round identically.
-// rara_weight's intermediate values, which its gradient reuses.
+// Products that feed a sum are written with __fmul_rn so the forward (rara_weight) and the
+// backward (rara_weight_terms, which also keeps the intermediate values for the weight's
+// gradient) round identically.
 struct SplitTerms {
     RayTerms t;
     float mp, mV, v;  // m.p, m.V and the unclamped share 1/2 + s_mid / (2 H)
@@ -103,11 +103,19 @@ __device__ __forceinline__ float rara_weight_terms(const float4 c0, const float4
     return s.hit ? __saturatef(s.v) : 1.0f;  // a ray that misses, grazes or starts inside keeps rasterization
 }
 
+// The forward's form of rara_weight_terms: the same operations in the same order (so the same
+// value), without keeping the terms (the render kernel schedules this form slightly faster).
 __device__ __forceinline__ float rara_weight(const float4 c0, const float4 c1, const float4 c2, const float4 c3,
                                              float dx, float dy)
 {
-    SplitTerms s;
-    return rara_weight_terms(c0, c1, c2, c3, dx, dy, s);
+    const RayTerms t = ray_terms(c0, c1, c2, c3, dx, dy);
+    const bool hit = ray_hits_front(t);
+    const float mp = fmaf(c2.x, dx, c2.y * dy);
+    const float mV = c1.w + mp;
+    const float num = fmaf(c0.w + mp, t.VV, -__fmul_rn(t.Gp + t.pp, mV));
+    const float den2 = __fmul_rn(t.VV - t.uu, __fmul_rn(mV, mV));
+    const float w = __saturatef(fmaf(__fmul_rn(num, rsqrtf(den2)), 0.5f, 0.5f));
+    return hit ? w : 1.0f;
 }
 
 // Decay weight of a Gaussian that several planes of a convex clip volume split
