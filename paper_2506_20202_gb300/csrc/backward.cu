@@ -211,60 +211,48 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
                 const float ca = s0.z, cb = 0.5f * s0.w, cc = s1.x;  // conic (a, b, c)
                 const float mode = s1.w;
                 const bool cut = mode == kWeightSplit;  // the weight varies with the inputs
-                bool contrib = false;
-                float gmx = 0.f, gmy = 0.f, gCa = 0.f, gCb = 0.f, gCc = 0.f, gop = 0.f;
-                float gr = 0.f, gg = 0.f, gb = 0.f;
+                // Every lane evaluates the entry (the branches below are uniform over the warp);
+                // lanes that do not contribute select zero gradients and keep their state.
+                const float dx = pxf - s0.x, dy = pyf - s0.y;
+                const float q = splat_q(s0.z, s0.w, s1.x, dx, dy);
+                const float a0 = splat_alpha0(q, s1.y);
+                float w = 1.0f;
+                SplitTerms sp;  // a split weight's terms, reused by its gradient
+                if (cut) w = rara_weight_terms(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy, sp);
+                else if (mode != kWeightNone) w = rara_weight_hidden(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
+                const float au = __fmul_rn(a0, w);
+                const float alpha = fminf(kAlphaMax, au);
+                // (last = 0 outside the image)
+                const bool contrib = pos < last && q <= s1.z && a0 >= kAlphaMin && alpha >= kAlphaMin;
+                const unsigned who = __ballot_sync(kFull, contrib);
+                if (!who) continue;
+                const float oma = 1.0f - alpha;   // in [0.01, 1]
+                const float roma = __fdividef(1.0f, oma);
+                const float Tj = T * roma;
+                const float wgt = contrib ? alpha * Tj : 0.0f;
+                const float gr = dC0 * wgt, gg = dC1 * wgt, gb = dC2 * wgt;
+                float ga = Tj * (dC0 * (s2.x - B0) + dC1 * (s2.y - B1) + dC2 * (s2.z - B2)) - Tfin * bgdot * roma;
+                if (contrib) {
+                    B0 = fmaf(alpha, s2.x, oma * B0);
+                    B1 = fmaf(alpha, s2.y, oma * B1);
+                    B2 = fmaf(alpha, s2.z, oma * B2);
+                    T = Tj;
+                }
+                if (!contrib || au > kAlphaMax) ga = 0.0f;  // no contribution, or clamped at 0.99
+                const float ga0 = ga * w;
+                const float gop = contrib ? ga0 * __fdividef(a0, s2.w) : 0.0f;  // d alpha0 / d opacity = exp(-q/2)
+                const float gq = -0.5f * ga0 * a0;
+                const float gCa = gq * dx * dx;
+                const float gCb = 2.0f * gq * dx * dy;
+                const float gCc = gq * dy * dy;
+                float gdx = 2.0f * gq * fmaf(ca, dx, cb * dy);
+                float gdy = 2.0f * gq * fmaf(cb, dx, cc * dy);
                 float gc[16];  // cutoff record products (split weights only)
 #pragma unroll
                 for (int k = 0; k < 16; ++k) gc[k] = 0.f;
-                if (pos < last) {  // (last = 0 outside the image)
-                    const float dx = pxf - s0.x, dy = pyf - s0.y;
-                    const float q = splat_q(s0.z, s0.w, s1.x, dx, dy);
-                    if (q <= s1.z) {
-                        const float a0 = splat_alpha0(q, s1.y);
-                        if (a0 >= kAlphaMin) {
-                            float w = 1.0f;
-                            SplitTerms sp;  // a split weight's terms, reused by its gradient
-                            if (cut) w = rara_weight_terms(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy, sp);
-                            else if (mode != kWeightNone)
-                                w = rara_weight_hidden(st.c0[j], st.c1[j], st.c2[j], st.c3[j], dx, dy);
-                            const float au = __fmul_rn(a0, w);
-                            const float alpha = fminf(kAlphaMax, au);
-                            if (alpha >= kAlphaMin) {
-                                contrib = true;
-                                const float oma = 1.0f - alpha;   // in [0.01, 1)
-                                const float roma = __fdividef(1.0f, oma);
-                                const float Tj = T * roma;
-                                const float wgt = alpha * Tj;
-                                gr = dC0 * wgt;
-                                gg = dC1 * wgt;
-                                gb = dC2 * wgt;
-                                float ga = Tj * (dC0 * (s2.x - B0) + dC1 * (s2.y - B1) + dC2 * (s2.z - B2)) -
-                                           Tfin * bgdot * roma;
-                                B0 = fmaf(alpha, s2.x, oma * B0);
-                                B1 = fmaf(alpha, s2.y, oma * B1);
-                                B2 = fmaf(alpha, s2.z, oma * B2);
-                                T = Tj;
-                                if (au > kAlphaMax) ga = 0.0f;  // clamped at 0.99
-                                const float ga0 = ga * w;
-                                gop = ga0 * __fdividef(a0, s2.w);        // d alpha0 / d opacity = exp(-q/2)
-                                const float gq = -0.5f * ga0 * a0;
-                                gCa = gq * dx * dx;
-                                gCb = 2.0f * gq * dx * dy;
-                                gCc = gq * dy * dy;
-                                float gdx = 2.0f * gq * fmaf(ca, dx, cb * dy);
-                                float gdy = 2.0f * gq * fmaf(cb, dx, cc * dy);
-                                if (cut)
-                                    rara_weight_grad(sp, st.c0[j], st.c1[j], st.c2[j], s_ab[0][j], s_ab[1][j], dx, dy, ga * a0, gc,
-                                                     gdx, gdy);
-                                gmx = -gdx;
-                                gmy = -gdy;
-                            }
-                        }
-                    }
-                }
-                const unsigned who = __ballot_sync(kFull, contrib);
-                if (!who) continue;
+                if (cut && contrib)
+                    rara_weight_grad(sp, st.c0[j], st.c1[j], st.c2[j], s_ab[0][j], s_ab[1][j], dx, dy, ga * a0, gc, gdx, gdy);
+                const float gmx = -gdx, gmy = -gdy;
                 float *dst = a.grec[s_slot[j]].v;
                 if (__popc(who) <= kDirectAdds) {  // few pixels: each adds its own values
                     if (contrib) {
