@@ -41,20 +41,21 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Gradient of the decay weight where the plane splits the chord (0 < w < 1); returns false
-// (no gradient) where w is constant. It starts from the terms rara_weight_terms computed for
-// the weight itself (sp); with w = 1/2 + s_mid / (2 H), H = sqrt(h2) |m.V| / |V|, it goes back through
+// Gradient of the decay weight where the plane splits the chord (0 < w < 1; ok is false where
+// w is constant or the pixel does not contribute). It starts from the terms that
+// rara_weight_terms computed for the weight itself (sp); with w = 1/2 + s_mid / (2 H),
+// H = sqrt(h2) |m.V| / |V|, it goes back through
 // s_mid = d_ep + m.p - f (m.V), f = (G.p + p.p) / V.V, h2 = 1 - |u|^2 / V.V,
 // V.V = G.G + 2 G.p + p.p, m.V = m.G + m.p and the per-pixel polynomials G.p, p.p, m.p,
 // u = dx A + dy B. c0..c2 is the record's staged form (stage_cut), r2, r3 its own c2, c3
 // (which hold A and B). Outputs: dL/d(record products) in CutRec order (c0.x .. c3.w) in
 // gc[16], and dL/d(dx, dy) added to gdx, gdy.
-__device__ __forceinline__ bool rara_weight_grad(const SplitTerms &sp, const float4 c0, const float4 c1,
+__device__ __forceinline__ void rara_weight_grad(const SplitTerms &sp, const float4 c0, const float4 c1,
                                                  const float4 c2, const float4 r2, const float4 r3, float dx, float dy,
-                                                 float gw, float gc[16], float &gdx, float &gdy)
+                                                 float gw, bool ok, float gc[16], float &gdx, float &gdy)
 {
-    // w is constant (0 or 1) unless the ray hits and the unclamped share lies strictly inside (0, 1)
-    if (!(sp.hit && sp.v > 0.0f && sp.v < 1.0f)) return false;
+    // Every lane evaluates the expressions; where ok is false (no contribution, or w constant)
+    // the results, which may then be infinite or NaN, are replaced by zeros.
     const RayTerms &t = sp.t;
     const float mp = sp.mp, mV = sp.mV;
     const float cc = __fmul_rn(t.uu, t.rVV);
@@ -93,11 +94,14 @@ __device__ __forceinline__ bool rara_weight_grad(const SplitTerms &sp, const flo
     const float gu0 = 2.0f * g_uu * u0, gu1 = 2.0f * g_uu * u1, gu2 = 2.0f * g_uu * u2;
     gc[10] = gu0 * dx; gc[11] = gu1 * dx; gc[12] = gu2 * dx;   // A
     gc[13] = gu0 * dy; gc[14] = gu1 * dy; gc[15] = gu2 * dy;   // B
-    gdx += g_Gp * c0.y + g_pp * fmaf(2.0f * dx, c1.x, dy * c1.y) + g_mp * c2.x +
-           (gu0 * r2.z + gu1 * r2.w + gu2 * r3.x);
-    gdy += g_Gp * c0.z + g_pp * fmaf(dx, c1.y, 2.0f * dy * c1.z) + g_mp * c2.y +
-           (gu0 * r3.y + gu1 * r3.z + gu2 * r3.w);
-    return true;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) gc[k] = ok ? gc[k] : 0.0f;
+    const float ddx = g_Gp * c0.y + g_pp * fmaf(2.0f * dx, c1.x, dy * c1.y) + g_mp * c2.x +
+                      (gu0 * r2.z + gu1 * r2.w + gu2 * r3.x);
+    const float ddy = g_Gp * c0.z + g_pp * fmaf(dx, c1.y, 2.0f * dy * c1.z) + g_mp * c2.y +
+                      (gu0 * r3.y + gu1 * r3.z + gu2 * r3.w);
+    gdx += ok ? ddx : 0.0f;
+    gdy += ok ? ddy : 0.0f;
 }
 
 // Contributing pixels of an entry up to which each adds its own gradient values (2 or 7 vector
@@ -250,8 +254,14 @@ __device__ __forceinline__ void tile_bwd(const RenderBwdArgs &a, const ViewDev &
                 float gc[16];  // cutoff record products (split weights only)
 #pragma unroll
                 for (int k = 0; k < 16; ++k) gc[k] = 0.f;
-                if (cut && contrib)
-                    rara_weight_grad(sp, st.c0[j], st.c1[j], st.c2[j], s_ab[0][j], s_ab[1][j], dx, dy, ga * a0, gc, gdx, gdy);
+                if (cut) {
+                    // w is constant (0 or 1) unless the ray hits and the unclamped share lies
+                    // strictly inside (0, 1)
+                    const bool wok = contrib && sp.hit && sp.v > 0.0f && sp.v < 1.0f;
+                    if (__any_sync(kFull, wok))
+                        rara_weight_grad(sp, st.c0[j], st.c1[j], st.c2[j], s_ab[0][j], s_ab[1][j], dx, dy, ga * a0, wok,
+                                         gc, gdx, gdy);
+                }
                 const float gmx = -gdx, gmy = -gdy;
                 float *dst = a.grec[s_slot[j]].v;
                 if (__popc(who) <= kDirectAdds) {  // few pixels: each adds its own values
