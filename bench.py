@@ -180,7 +180,8 @@ def issue_slots_for_current_kernel():
     if not m or not _profile_matches_sources(text):
         return None
     return {"issue_active_frac": float(m.group(1)) / 100.0, "source": os.path.relpath(TRAFFIC_FILE, ROOT),
-            "note": "the kernel issues on this share of its SMs' active cycles (ncu, 4-view capture)"}
+            "note": "the kernel issues on this share of its SMs' active cycles (ncu, 4-view capture at 16x32 "
+                    "tiles, 256-entry batches)"}
 
 
 def _profile_matches_sources(text):
@@ -192,14 +193,16 @@ def _profile_matches_sources(text):
     return True
 
 
-def traffic_for_current_kernel():
+def traffic_for_current_kernel(tuning):
     """DRAM bytes of the benchmark's render launch from the committed ncu summary, if it was
-    taken on the current render sources (matched by hash); otherwise None."""
+    taken on the current render sources (matched by hash) with the same tiling and split
+    thresholds (tuning: tile_w, tile_h, depth, split2, split4); otherwise None."""
     try:
         text = open(TRAFFIC_FILE).read()
     except OSError:
         return None
-    b = re.search(r"dram_bytes_per_bench_launch:\s*([0-9.eE+]+)", text)
+    tag = ",".join(str(int(x)) for x in tuning)
+    b = re.search(r"dram_bytes_per_bench_launch \(tuning " + re.escape(tag) + r"\):\s*([0-9.eE+]+)", text)
     if not b:
         return None
     for path in RENDER_SRCS:
@@ -527,7 +530,7 @@ def run_ours(args):
     peak = sms * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     issue = issue_slots_for_current_kernel()
     roofline = {"bound": "alu", "kernel": "k_render (one launch for the 16-view batch)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for_current_kernel(),
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for_current_kernel(best),
                 "launch_ms": t_render, "launch_ms_exact_render": stage[2],
                 "flop_per_launch": flop,
                 "units": "15 FLOP per evaluated (pixel, Gaussian) pair + 30 per cutoff pair (the method's arithmetic)",
