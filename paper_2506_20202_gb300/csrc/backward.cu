@@ -23,14 +23,14 @@
 // atomics. Warps skip entries whose q <= 9 support misses their 8x4 rectangle, as in the
 // forward.
 //
-// Preprocess backward (per Gaussian, looping over its scene's views like the forward):
+// Preprocess backward (per Gaussian, over the views of its scene that render it):
 // the slot's gradient record is carried back through the projection (Eq. 9-10: conic ->
 // Sigma2 -> J W R S -> camera-space mean), the SH colour, the sigmoid opacity and the
 // ray-tracing record (G = M^-1 (mu - e), P, m = M^T n, d_ep = n.mu + d) to mu, sigma, R,
 // the opacity logit, the SH coefficients and the plane; the rotation's gradient goes
 // through the quaternion's normalisation once, after the views. Each Gaussian's gradients
-// have one writer (no atomics); each view's plane gradient is a sum over Gaussians
-// (warp sums + atomics).
+// have one writer (no atomics); each view's plane gradient is a sum over Gaussians (block
+// sums in shared memory, then one atomic per view, component and block).
 #include "rara_internal.cuh"
 #include "render_common.cuh"
 #include "sh.cuh"
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_render_bwd(RenderBwdArgs a)
 
 // Per-Gaussian backward over the scene's views. Dynamic shared memory: the block's SH
 // coefficient gradients, [3 (degree+1)^2][kBlock].
-constexpr int kViewChunkBwd = 16;  // views staged in shared memory at a time
+constexpr int kViewChunkBwd = 32;  // views staged in shared memory at a time
 
 __global__ void __launch_bounds__(kBlock, 2) k_preprocess_bwd(PreprocessBwdArgs a)
 {
@@ -379,40 +379,45 @@ __global__ void __launch_bounds__(kBlock, 2) k_preprocess_bwd(PreprocessBwdArgs 
     float gopacity = 0.f;
 
     const int view_end = sc.view_begin + sc.view_count;
-    // Tile counts are loaded two views ahead, and the next view's gradient record is
-    // prefetched into L2 when that view renders the Gaussian: a view's record loads then
-    // neither wait behind its tile count nor, mostly, on DRAM.
-    auto tiles_of = [&](int v) -> uint32_t {
-        return (valid && v < view_end) ? __ldg(&a.tiles[__ldg(&a.views[v].slot_base) + (uint32_t)i]) : 0u;
-    };
-    uint32_t t1 = tiles_of(sc.view_begin), t2 = tiles_of(sc.view_begin + 1);
+    // Per chunk of views, each thread first finds the views that render its Gaussian (one
+    // tile-count load per view, issued together). The views are then taken in rounds: in each
+    // round every lane takes its own next such view, so a lane does not sit through the views
+    // that render only its neighbours' Gaussians. Each view's plane gradient is summed in shared
+    // memory over the block and added once per chunk. The next round's gradient record is
+    // prefetched into L2.
+    __shared__ float s_gpl[kViewChunkBwd][4];
     for (int vbase = sc.view_begin; vbase < view_end; vbase += kViewChunkBwd) {
         const int nv = min(kViewChunkBwd, view_end - vbase);
-        __syncthreads();  // the previous chunk's tables are no longer read
+        __syncthreads();  // the previous chunk's tables and plane sums are no longer read
         {
             constexpr int kWords = (int)(sizeof(ViewDev) / sizeof(uint32_t));
             const uint32_t *src = reinterpret_cast<const uint32_t *>(a.views + vbase);
             uint32_t *dst = reinterpret_cast<uint32_t *>(s_views);
             for (int t = threadIdx.x; t < nv * kWords; t += kBlock) dst[t] = __ldg(&src[t]);
+            if (threadIdx.x < 4 * kViewChunkBwd) (&s_gpl[0][0])[threadIdx.x] = 0.0f;
         }
         __syncthreads();
-        for (int vv = 0; vv < nv; ++vv) {
-            const int v = vbase + vv;
+        uint32_t vm = 0;  // the chunk's views that render this Gaussian
+        if (valid) {
+            for (int vv = 0; vv < nv; ++vv)
+                if (__ldg(&a.tiles[s_views[vv].slot_base + (uint32_t)i]) != 0u) vm |= 1u << vv;
+        }
+        while (__any_sync(kFull, vm != 0u)) {
+            const bool has = vm != 0u;
+            const int vv = has ? __ffs(vm) - 1 : 0;
+            vm &= vm - 1u;
+            if (vm) {
+                const char *nr = reinterpret_cast<const char *>(a.grec + (s_views[__ffs(vm) - 1].slot_base + (uint32_t)i));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(nr));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(nr + 96));
+            }
             const ViewDev &vw = s_views[vv];
             const CamDev &cam = vw.cam;
             const PlaneDev &pl = vw.plane;
             float gpn[4] = {0.f, 0.f, 0.f, 0.f};
             bool has_plane = false;
             const uint32_t slot = vw.slot_base + (uint32_t)i;
-            const uint32_t tiles_here = t1;
-            t1 = t2;
-            t2 = tiles_of(v + 2);
-            if (t1 != 0u) {
-                const char *nr = reinterpret_cast<const char *>(a.grec + (__ldg(&a.views[v + 1].slot_base) + (uint32_t)i));
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(nr));
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(nr + 96));
-            }
-            if (valid && tiles_here != 0u) {
+            if (has) {
                 const float *grc = a.grec[slot].v;
                 const float4 g0 = reinterpret_cast<const float4 *>(grc)[0];
                 const float4 g1 = reinterpret_cast<const float4 *>(grc)[1];
@@ -595,16 +600,18 @@ __global__ void __launch_bounds__(kBlock, 2) k_preprocess_bwd(PreprocessBwdArgs 
                 gw[0] = z4; gw[1] = z4; gw[2] = z4;
                 if (cutoff) { gw[3] = z4; gw[4] = z4; gw[5] = z4; gw[6] = z4; }
             }
-            const BwdView &bv = a.bviews[v];
-            if (bv.plane_grad && __any_sync(kFull, has_plane)) {
+            if (has_plane) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) gpn[j] = warp_sum(gpn[j]);
-                if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (gpn[j] != 0.0f) atomicAdd(&bv.plane_grad[j], gpn[j]);
-                }
+                for (int j = 0; j < 4; ++j)
+                    if (gpn[j] != 0.0f) atomicAdd(&s_gpl[vv][j], gpn[j]);
             }
+        }
+        __syncthreads();
+        if (threadIdx.x < 4 * nv) {
+            const int vv = threadIdx.x >> 2, j = threadIdx.x & 3;
+            float *pg = a.bviews[vbase + vv].plane_grad;
+            const float g = s_gpl[vv][j];
+            if (pg && g != 0.0f) atomicAdd(&pg[j], g);
         }
     }
     if (!valid) return;
