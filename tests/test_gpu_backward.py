@@ -132,6 +132,26 @@ def test_batch_gradient_is_the_sum_of_single_view_gradients():
         assert np.allclose(whole["planes"][v], p["planes"][0], rtol=1e-5, atol=1e-7)
 
 
+def test_batch_gradient_over_more_views_than_a_chunk():
+    """35 views, more than the preprocess backward's chunk of 32 views (each lane takes the
+    chunk's views that render its Gaussian in rounds): the batch's parameter and plane
+    gradients equal the sums of the single-view backwards."""
+    sc = scenes.gradient_scene(300, seed=71, sh_degree=2)
+    sc.means = np.ascontiguousarray(sc.means * np.float32(1.4))
+    views = _views(71, scenes.MODE_RARA, sizes=tuple((32 + 4 * (k % 3), 28 + 4 * (k % 4)) for k in range(35)))
+    weights = _weights(sc, views, 72)
+    whole = gpu_gradients(sc, views, weights)
+    r = rara.Renderer()
+    parts = [gpu_gradients(sc, [v], [w], renderer=r) for v, w in zip(views, weights)]
+    r.close()
+    for k in fd.PARAMS:
+        s_ = sum(p[k] for p in parts)
+        assert np.linalg.norm(s_) > 0, k
+        assert fd.rel_l2(whole[k], s_) <= 1e-5, (k, fd.rel_l2(whole[k], s_))
+    for v, p in enumerate(parts):
+        assert np.allclose(whole["planes"][v], p["planes"][0], rtol=1e-4, atol=1e-6), v
+
+
 def test_backward_after_graph_capture_and_replay():
     """The first graph call captures (and replays once); a backward after it, and after a
     later replay with new cameras, equals the backward of the exact batch render."""
