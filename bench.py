@@ -327,18 +327,18 @@ def stage_hbm(kms, vinfo, scene, W, H, hbm_gbs, depth_keys=None, shared_pairs=0)
     GB/s over the stage's GPU time (rara_ctx_kernel_ms) and the fraction of the measured HBM
     copy bandwidth. Bytes per unit (the design notes list them):
       preprocess   the scene once (44 B of geometry + 12 (L+1)^2 B of SH per Gaussian), 5 B per
-                   (view, Gaussian) slot (label, tiles), 60 B per rendered slot (rectangle,
-                   splat record, depth), 64 B per cutoff slot (ray-tracing record)
+                   (view, Gaussian) slot (label, tiles), 84 B per rendered slot (emission
+                   record, splat record, depth), 64 B per cutoff slot (ray-tracing record)
       compaction   8 B per slot read (tiles, depth), 8 B per rendered slot written
       depth sort   16 B per key per digit pass launched (4 depth + 1 view pass over the
                    rendered slots; for a one-camera batch 4 depth passes over the Gaussians some
                    view renders, plus the expansion into the views' slots: 4 B of sorted value
                    and 4 B of tile count read per (view, key), 4 B written per rendered slot)
-      emission     44 B per rendered slot read (slot, rectangle, centre and conic), 8 B per pair
+      emission     36 B per rendered slot read (slot, its 32-byte emission record), 8 B per pair
       tile sort    16 B per pair per digit pass
       ranges       4 B per pair read, 8 B per tile written
     A one-camera batch of at most 32 views lists once (shared_pairs > 0): the depth sort has no
-    expansion; the emission reads 48 B per Gaussian some view renders (its view mask too) and
+    expansion; the emission reads 40 B per Gaussian some view renders (its view mask too) and
     writes 8 B per shared pair; the tile sort sorts the shared pairs; the listing reads 20 B per
     shared pair (value and mask twice, key once) and writes 4 B per view pair and 8 B per tile."""
     views = len(vinfo)
@@ -352,11 +352,11 @@ def stage_hbm(kms, vinfo, scene, W, H, hbm_gbs, depth_keys=None, shared_pairs=0)
     tile_passes = (tile_bits + 7) // 8
     view_passes = 0 if views == 1 else (1 if views <= 256 else 2)
     bytes_ = {
-        "preprocess": n * (44 + 4 * scene.sh.shape[0]) + 5 * slots + 60 * rendered + 64 * cutoff,
+        "preprocess": n * (44 + 4 * scene.sh.shape[0]) + 5 * slots + 84 * rendered + 64 * cutoff,
         "compaction": (8 * slots + 8 * rendered) if depth_keys is None else (4 * n + 8 * depth_keys),
         "depth_sort": 16 * rendered * (4 + view_passes) if depth_keys is None else
                       16 * depth_keys * 4 + (0 if shared_pairs else 8 * views * depth_keys + 4 * rendered),
-        "emission": 48 * depth_keys + 8 * shared_pairs if shared_pairs else 44 * rendered + 8 * pairs,
+        "emission": 40 * depth_keys + 8 * shared_pairs if shared_pairs else 36 * rendered + 8 * pairs,
         "tile_sort": 16 * (shared_pairs or pairs) * tile_passes,
         "ranges": (20 * shared_pairs + 4 * pairs + 8 * tiles) if shared_pairs else 4 * pairs + 8 * tiles,
     }

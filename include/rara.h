@@ -380,7 +380,7 @@ int rara_frame_pairs(rara_ctx *ctx, int32_t view, uint64_t *keys, uint32_t *valu
  * frame loop or a host callback, where an allocation would block or is not allowed, or a
  * process whose device memory belongs to another allocator. The call allocates nothing
  * (no cudaMalloc, cudaFree, pinned or heap memory): every scratch buffer is carved from one
- * file-scope static __device__ array of about 20.4 MB (19.5 MiB), which each GPU that loads
+ * file-scope static __device__ array of about 22.0 MB (21.0 MiB), which each GPU that loads
  * the library holds until the process exits. The caller passes inputs and outputs as for
  * rara_render_frame, with the same layouts and results.
  *

@@ -68,7 +68,7 @@ struct rara_ctx {
 
     // device
     DevBuf views_d, scenes_d, view_counters_d, counters;
-    DevBuf labels, tiles, rect, rec, cut, depth;
+    DevBuf labels, tiles, erec, rec, cut, depth;
     DevBuf cut_x;                       // further planes of clip-volume cutoff slots
     DevBuf gkey;                        // one-camera batches: per-Gaussian depth keys
     DevBuf vmask, list_counts;          // shared listing: per-Gaussian view masks, partition counts
@@ -427,7 +427,7 @@ int batch_setup(rara_ctx *c, const rara_gaussians *scenes, int ns, const rara_vi
         (rc = ensure(c, c->scenes_d, sizeof(SceneDev) * (size_t)ns, "scene table")) ||
         (rc = ensure(c, c->view_counters_d, sizeof(ViewCounters) * (size_t)nv, "view counters")) ||
         (rc = ensure(c, c->labels, nn, "labels")) || (rc = ensure(c, c->tiles, nn * 4, "tiles")) ||
-        (rc = ensure(c, c->rect, nn * 8, "rect")) || (rc = ensure(c, c->rec, nn * sizeof(SplatRec), "records")) ||
+        (rc = ensure(c, c->erec, nn * sizeof(EmitRec), "emission records")) || (rc = ensure(c, c->rec, nn * sizeof(SplatRec), "records")) ||
         (rc = ensure(c, c->cut, nn * sizeof(CutRec), "cutoff records")) ||
         (rc = ensure(c, c->depth, nn * 4, "depth")) || (rc = ensure(c, c->ckeys, nn * 4, "depth keys")) ||
         (rc = ensure(c, c->cvals, nn * 4, "depth values")) || (rc = ensure(c, c->ckeys_b, nn * 4, "depth keys B")) ||
@@ -466,7 +466,7 @@ int batch_preprocess(rara_ctx *c, cudaStream_t s)
     a.num_units = (int)c->num_units;
     a.labels = (uint8_t *)c->labels.p;
     a.tiles = (uint32_t *)c->tiles.p;
-    a.rect = (uint2 *)c->rect.p;
+    a.erec = (EmitRec *)c->erec.p;
     a.rec = (SplatRec *)c->rec.p;
     a.cut = (CutRec *)c->cut.p;
     a.cut_x = c->multi ? (CutExtra *)c->cut_x.p : nullptr;
@@ -587,8 +587,7 @@ int batch_bin(rara_ctx *c, uint32_t cap, cudaStream_t s)
     e.keys_b = (const uint32_t *)c->ckeys_b.p;
     e.vals_b = (const uint32_t *)c->cvals_b.p;
     e.tiles = (const uint32_t *)c->tiles.p;
-    e.rect = (const uint2 *)c->rect.p;
-    e.rec = (const SplatRec *)c->rec.p;
+    e.erec = (const EmitRec *)c->erec.p;
     e.views = (const ViewDev *)c->views_d.p;
     e.num_views = c->num_views;
     e.cap_pairs = cap;
@@ -777,7 +776,7 @@ int rara_ctx_destroy(rara_ctx *c)
     if (!c) return RARA_OK;
     cudaDeviceSynchronize();
     DevBuf *all[] = {&c->views_d, &c->scenes_d, &c->view_counters_d, &c->counters, &c->labels, &c->tiles,
-                     &c->rect, &c->rec, &c->cut, &c->cut_x, &c->depth, &c->ckeys, &c->cvals, &c->ckeys_b, &c->cvals_b,
+                     &c->erec, &c->rec, &c->cut, &c->cut_x, &c->depth, &c->ckeys, &c->cvals, &c->ckeys_b, &c->cvals_b,
                      &c->lookback_c, &c->pkeys, &c->pvals, &c->pkeys_b, &c->pvals_b, &c->lookback_e, &c->hist,
                      &c->ranges, &c->items, &c->sort_scratch, &c->grec, &c->bviews_d, &c->bscenes_d,
                      &c->seg_base, &c->export_off, &c->gkey, &c->vmask, &c->list_counts, &c->lviews_d};
@@ -824,7 +823,7 @@ int rara_ctx_reserve(rara_ctx *c, int64_t slots, int64_t pairs, int32_t views, i
         (rc = ensure(c, c->scenes_d, sizeof(SceneDev) * (size_t)c->max_scenes, "scene table")) ||
         (rc = ensure(c, c->view_counters_d, sizeof(ViewCounters) * (size_t)views, "view counters")) ||
         (rc = ensure(c, c->labels, nn, "labels")) || (rc = ensure(c, c->tiles, nn * 4, "tiles")) ||
-        (rc = ensure(c, c->rect, nn * 8, "rect")) || (rc = ensure(c, c->rec, nn * sizeof(SplatRec), "records")) ||
+        (rc = ensure(c, c->erec, nn * sizeof(EmitRec), "emission records")) || (rc = ensure(c, c->rec, nn * sizeof(SplatRec), "records")) ||
         (rc = ensure(c, c->cut, nn * sizeof(CutRec), "cutoff records")) ||
         (rc = ensure(c, c->depth, nn * 4, "depth")) || (rc = ensure(c, c->ckeys, nn * 4, "depth keys")) ||
         (rc = ensure(c, c->cvals, nn * 4, "depth values")) || (rc = ensure(c, c->ckeys_b, nn * 4, "depth keys B")) ||
@@ -1340,7 +1339,7 @@ int rara_frame_gaussians(rara_ctx *c, int32_t view, uint8_t *labels, float *dept
     if (view < 0 || view >= c->num_views) return fail(c, RARA_ERR_INVALID_ARG, "view %d of %d", view, c->num_views);
     const int k = c->h_view_map[view];
     launch_export_gaussians(c->h_view_n[k], c->h_views[k].slot_base, (const uint8_t *)c->labels.p,
-                            (const uint32_t *)c->tiles.p, (const uint2 *)c->rect.p, (const SplatRec *)c->rec.p,
+                            (const uint32_t *)c->tiles.p, (const EmitRec *)c->erec.p, (const SplatRec *)c->rec.p,
                             (const float *)c->depth.p, labels, depth, mean2d, conic, rgb, opacity, rect, tiles,
                             (cudaStream_t)stream);
     return launched(c, "export gaussians", c->h_view_n[k] > 0);
@@ -1412,7 +1411,7 @@ constexpr size_t kSzScenes = align256(sizeof(SceneDev));
 constexpr size_t kSzViewCounters = align256(sizeof(ViewCounters));
 constexpr size_t kSzLabels = align256(kStaticMaxGaussians);
 constexpr size_t kSzU32G = align256((size_t)kStaticMaxGaussians * 4);
-constexpr size_t kSzRect = align256((size_t)kStaticMaxGaussians * 8);
+constexpr size_t kSzErec = align256((size_t)kStaticMaxGaussians * sizeof(EmitRec));
 constexpr size_t kSzRec = align256((size_t)kStaticMaxGaussians * sizeof(SplatRec));
 constexpr size_t kSzCut = align256((size_t)kStaticMaxGaussians * sizeof(CutRec));
 constexpr size_t kSzLookC = align256((size_t)(kStaticMaxGaussians / 1024 + 2) * 8);
@@ -1426,11 +1425,11 @@ constexpr size_t kSzOrder = align256((size_t)kStaticMaxTiles * 16);
 // 1024 keys; static_setup checks it against the sort's own requirement
 constexpr size_t kSzSort = align256(4 * (4 * (size_t)((kStaticMaxPairs + 1023) / 1024) * 256));
 constexpr size_t kStaticBytes = kSzCounters + kSzViews + kSzScenes + kSzViewCounters + kSzLabels + 2 * kSzU32G +
-                                kSzRect + kSzRec + kSzCut + 4 * kSzU32G + kSzLookC + kSzLookE + 4 * kSzU32P +
+                                kSzErec + kSzRec + kSzCut + 4 * kSzU32G + kSzLookC + kSzLookE + 4 * kSzU32P +
                                 kSzHist + kSzSeg + kSzRanges + kSzOrder + kSzSort;
 
-// 20,396,544 bytes with the current record sizes; the header states "about 20.4 MB"
-static_assert(kStaticBytes <= 20500000, "the static scratch outgrew the size the header states");
+// 21,969,408 bytes with the current record sizes; the header states "about 22.0 MB"
+static_assert(kStaticBytes <= 22000000, "the static scratch outgrew the size the header states");
 
 static __device__ __align__(256) unsigned char g_rara_static_scratch[kStaticBytes];
 
@@ -1463,7 +1462,7 @@ int static_setup(int dev)
     take(c->view_counters_d, kSzViewCounters);
     take(c->labels, kSzLabels);
     take(c->tiles, kSzU32G);
-    take(c->rect, kSzRect);
+    take(c->erec, kSzErec);
     take(c->rec, kSzRec);
     take(c->cut, kSzCut);
     take(c->depth, kSzU32G);

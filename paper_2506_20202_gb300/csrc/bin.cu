@@ -62,7 +62,7 @@ struct SpanGeo {
     bool ok;
 };
 
-// r0, r1: the first two float4 of the slot's splat record (centre, conic, opacity).
+// From the slot's emission record (rectangle, centre, conic, q_cut).
 // sqrt(x) for x >= 0 from the special function unit's reciprocal square root (0 at 0);
 // the listing needs the spans only to within the float32 tolerance of its threshold.
 __device__ __forceinline__ float fast_sqrt(float x)
@@ -70,12 +70,13 @@ __device__ __forceinline__ float fast_sqrt(float x)
     return x > 0.0f ? __fmul_rn(x, rsqrtf(x)) : 0.0f;
 }
 
-__device__ __forceinline__ SpanGeo span_geo(const float4 r0, const float4 r1, uint2 rc, const ViewDev &vw)
+__device__ __forceinline__ SpanGeo span_geo(const EmitRec &e, const ViewDev &vw)
 {
     SpanGeo g;
-    const float a = r0.z, b = r0.w, c = r1.x;
-    const float qc = splat_qcut(__log2f(r1.y));
-    g.mx = r0.x; g.my = r0.y; g.b = b;
+    const float a = e.ca, b = e.cb, c = e.cc;
+    const float qc = e.qcut;
+    const uint2 rc = e.rect;
+    g.mx = e.mx; g.my = e.my; g.b = b;
     g.D = fmaf(a, c, -__fmul_rn(b, b));
     g.aq = __fmul_rn(a, qc);
     g.ia = __fdividef(1.0f, a);
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
                 sview[r] = vm ? __ffs(vm) - 1 : 0;
                 lslot[r] = a.views[sview[r]].slot_base + slot[r];
             }
-            rc[r] = i < n ? __ldg(&a.rect[lslot[r]]) : make_uint2(0u, 0u);
+            rc[r] = i < n ? __ldg(&a.erec[lslot[r]].rect) : make_uint2(0u, 0u);
             const int y0 = rc[r].x >> 16, y1 = rc[r].y >> 16;
             const int x0 = rc[r].x & 0xffff, x1 = rc[r].y & 0xffff;
             rows[r] = (i < n && x0 <= x1 && y0 <= y1) ? (uint32_t)(y1 - y0 + 1) : 0u;
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
             if (rows[r]) {
                 v = shared ? (uint32_t)sview[r] : (uint32_t)view_of_slot(a.views, a.num_views, slot[r]);
                 const ViewDev &vw = a.views[v];
-                const SpanGeo g = span_geo(a.rec[lslot[r]].r0, a.rec[lslot[r]].r1, rc[r], vw);
+                const SpanGeo g = span_geo(a.erec[lslot[r]], vw);
                 t0 = (shared ? 0u : vw.tile_base) + (uint32_t)(g.y0 * vw.tiles_x + g.x0);
                 txs = (uint32_t)vw.tiles_x;
                 const bool pooled = rbase + rows[r] <= kRowPool;
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(EmitArgs a)
                 dx = (int)s_rcol[rl] + (int)(r - s_rcum[rl]);
             } else {
                 const uint32_t sl = shared ? a.views[s_view[j]].slot_base + s_slot[j] : s_slot[j];
-                const SpanGeo g = span_geo(a.rec[sl].r0, a.rec[sl].r1, a.rect[sl], a.views[s_view[j]]);
+                const SpanGeo g = span_geo(a.erec[sl], a.views[s_view[j]]);
                 uint32_t rr = r;
                 for (int k2 = 0; k2 < (int)s_nrows[j]; ++k2) {  // the spans of the count phase
                     int lo2, c2;
@@ -616,7 +617,7 @@ __global__ void __launch_bounds__(kBlock) k_order_scatter(const int2 *__restrict
 }
 
 __global__ void k_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_src, const uint32_t *tiles_src,
-                                   const uint2 *rect_src, const SplatRec *rec, const float *depth_src,
+                                   const EmitRec *erec_src, const SplatRec *rec, const float *depth_src,
                                    uint8_t *labels, float *depth, float *mean2d, float *conic, float *rgb,
                                    float *opacity, int32_t *rect, uint32_t *tiles)
 {
@@ -634,7 +635,7 @@ __global__ void k_export_gaussians(int n, uint32_t slot_base, const uint8_t *lab
     if (rgb) { rgb[i] = r.r1.z; rgb[n + i] = r.r1.w; rgb[2 * n + i] = r.r2.x; }
     if (opacity) opacity[i] = r.r1.y;
     if (rect) {
-        const uint2 rc = rect_src[s];
+        const uint2 rc = erec_src[s].rect;
         rect[i] = rc.x & 0xffff; rect[n + i] = rc.x >> 16;
         rect[2 * n + i] = rc.y & 0xffff; rect[3 * n + i] = rc.y >> 16;
     }
@@ -705,12 +706,12 @@ void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int s
 }
 
 void launch_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_src, const uint32_t *tiles_src,
-                             const uint2 *rect_src, const SplatRec *rec, const float *depth_src, uint8_t *labels,
+                             const EmitRec *erec_src, const SplatRec *rec, const float *depth_src, uint8_t *labels,
                              float *depth, float *mean2d, float *conic, float *rgb, float *opacity, int32_t *rect,
                              uint32_t *tiles, cudaStream_t s)
 {
     if (n > 0)
-        k_export_gaussians<<<(n + 255) / 256, 256, 0, s>>>(n, slot_base, labels_src, tiles_src, rect_src, rec,
+        k_export_gaussians<<<(n + 255) / 256, 256, 0, s>>>(n, slot_base, labels_src, tiles_src, erec_src, rec,
                                                            depth_src, labels, depth, mean2d, conic, rgb, opacity,
                                                            rect, tiles);
 }

@@ -9,6 +9,7 @@
 // scan across blocks so the order is deterministic.
 #include "chained_scan.cuh"
 #include "rara_internal.cuh"
+#include "render_common.cuh"
 #include "sh.cuh"
 
 namespace rara {
@@ -383,7 +384,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_preprocess(PreprocessArgs a)
                         ntiles = pj.ntiles;
                         rendered = true;
                         cutoff = label == RARA_CUTOFF;
-                        a.rect[slot] = pj.rect;
+                        EmitRec er;
+                        er.rect = pj.rect;
+                        er.mx = pj.r0.x; er.my = pj.r0.y; er.ca = pj.r0.z; er.cb = pj.r0.w; er.cc = pj.r1x;
+                        er.qcut = splat_qcut(__log2f(op));
+                        a.erec[slot] = er;
                         SplatRec rec;
                         rec.r0 = pj.r0;
                         rec.r1 = make_float4(pj.r1x, op, pj.rgb0, pj.rgb1);

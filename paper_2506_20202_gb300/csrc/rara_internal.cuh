@@ -62,6 +62,17 @@ struct __align__(16) SplatRec {
     float4 r0, r1, r2;
 };
 
+// Per-slot emission record, written by the preprocess for rendered slots and gathered in
+// depth order by the emission (so in no particular slot order): what the exact row spans of
+// the slot's q <= q_cut ellipse need, in one 32-byte sector.
+//   rect = (tx0 | ty0 << 16, tx1 | ty1 << 16), the tile rectangle in the view
+//   (mx, my) the projected centre, (ca, cb, cc) the conic a, b, c
+//   qcut = splat_qcut(log2 opacity), the support the render culls with
+struct __align__(32) EmitRec {
+    uint2 rect;
+    float mx, my, ca, cb, cc, qcut;
+};
+
 // Decay-weight mode of a rendered slot (SplatRec r2.y). Only cutoff Gaussians whose
 // ellipsoid the plane actually meets need the per-pixel weight; a cutoff Gaussian wholly on
 // the visible side has w = 1 for every ray, one wholly on the invisible side has w = 0 for
@@ -177,7 +188,7 @@ struct PreprocessArgs {
     // dense per-slot outputs
     uint8_t *labels;
     uint32_t *tiles;       // tiles touched (0 = not rendered)
-    uint2 *rect;           // (tx0 | ty0 << 16, tx1 | ty1 << 16), tile coordinates in the view
+    EmitRec *erec;         // emission record (tile rectangle, centre, conic, q_cut)
     SplatRec *rec;
     CutRec *cut;
     CutExtra *cut_x;  // per slot, only for batches with clip volumes (else null)
@@ -256,8 +267,7 @@ void launch_expand(const ExpandArgs &a, int grid, cudaStream_t s);
 struct EmitArgs {
     const uint32_t *keys_a, *vals_a, *keys_b, *vals_b;  // the depth sort's two buffers
     const uint32_t *tiles;
-    const uint2 *rect;
-    const SplatRec *rec;     // the splats (the per-tile listing test)
+    const EmitRec *erec;     // the slots' rectangles and ellipses (the exact row spans)
     const ViewDev *views;
     int num_views;
     uint32_t cap_pairs;
@@ -416,7 +426,7 @@ void launch_loss_l2(const LossView *views, int num_views, uint32_t grid, cudaStr
 
 // Debug exports of one view
 void launch_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_src, const uint32_t *tiles_src,
-                             const uint2 *rect_src, const SplatRec *rec, const float *depth_src, uint8_t *labels,
+                             const EmitRec *erec_src, const SplatRec *rec, const float *depth_src, uint8_t *labels,
                              float *depth, float *mean2d, float *conic, float *rgb, float *opacity, int32_t *rect,
                              uint32_t *tiles, cudaStream_t s);
 // Pairs of one view in (local tile, depth) order: tile t's list goes to out_offset[t]

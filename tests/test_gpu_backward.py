@@ -148,8 +148,9 @@ def test_batch_gradient_over_more_views_than_a_chunk():
         s_ = sum(p[k] for p in parts)
         assert np.linalg.norm(s_) > 0, k
         assert fd.rel_l2(whole[k], s_) <= 1e-5, (k, fd.rel_l2(whole[k], s_))
-    for v, p in enumerate(parts):
-        assert np.allclose(whole["planes"][v], p["planes"][0], rtol=1e-4, atol=1e-6), v
+    for v, p in enumerate(parts):   # float sums in another order: relative to the vector's norm
+        d = np.linalg.norm(whole["planes"][v] - p["planes"][0])
+        assert d <= 1e-5 * np.linalg.norm(p["planes"][0]) + 1e-7, (v, d)
 
 
 def test_backward_after_graph_capture_and_replay():
