@@ -1339,7 +1339,9 @@ int rara_frame_gaussians(rara_ctx *c, int32_t view, uint8_t *labels, float *dept
     if (view < 0 || view >= c->num_views) return fail(c, RARA_ERR_INVALID_ARG, "view %d of %d", view, c->num_views);
     const int k = c->h_view_map[view];
     launch_export_gaussians(c->h_view_n[k], c->h_views[k].slot_base, (const uint8_t *)c->labels.p,
-                            (const uint32_t *)c->tiles.p, (const EmitRec *)c->erec.p, (const SplatRec *)c->rec.p,
+                            (const uint32_t *)c->tiles.p, (const EmitRec *)c->erec.p,
+                            c->shared_list ? (const uint32_t *)c->vmask.p : nullptr, (const ViewDev *)c->views_d.p,
+                            (const SplatRec *)c->rec.p,
                             (const float *)c->depth.p, labels, depth, mean2d, conic, rgb, opacity, rect, tiles,
                             (cudaStream_t)stream);
     return launched(c, "export gaussians", c->h_view_n[k] > 0);

@@ -617,7 +617,8 @@ __global__ void __launch_bounds__(kBlock) k_order_scatter(const int2 *__restrict
 }
 
 __global__ void k_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_src, const uint32_t *tiles_src,
-                                   const EmitRec *erec_src, const SplatRec *rec, const float *depth_src,
+                                   const EmitRec *erec_src, const uint32_t *vmask, const ViewDev *views,
+                                   const SplatRec *rec, const float *depth_src,
                                    uint8_t *labels, float *depth, float *mean2d, float *conic, float *rgb,
                                    float *opacity, int32_t *rect, uint32_t *tiles)
 {
@@ -635,7 +636,11 @@ __global__ void k_export_gaussians(int n, uint32_t slot_base, const uint8_t *lab
     if (rgb) { rgb[i] = r.r1.z; rgb[n + i] = r.r1.w; rgb[2 * n + i] = r.r2.x; }
     if (opacity) opacity[i] = r.r1.y;
     if (rect) {
-        const uint2 rc = erec_src[s].rect;
+        // a shared listing keeps the emission record in the first view that renders the
+        // Gaussian (the lowest bit of its view mask, set since this view renders it)
+        const uint32_t vm = vmask ? vmask[i] : 0u;
+        const uint32_t es = vm ? views[__ffs(vm) - 1].slot_base + (uint32_t)i : s;
+        const uint2 rc = erec_src[es].rect;
         rect[i] = rc.x & 0xffff; rect[n + i] = rc.x >> 16;
         rect[2 * n + i] = rc.y & 0xffff; rect[3 * n + i] = rc.y >> 16;
     }
@@ -706,12 +711,13 @@ void launch_tile_order(const int2 *ranges, int num_tiles, int split2_bits, int s
 }
 
 void launch_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_src, const uint32_t *tiles_src,
-                             const EmitRec *erec_src, const SplatRec *rec, const float *depth_src, uint8_t *labels,
+                             const EmitRec *erec_src, const uint32_t *vmask, const ViewDev *views,
+                             const SplatRec *rec, const float *depth_src, uint8_t *labels,
                              float *depth, float *mean2d, float *conic, float *rgb, float *opacity, int32_t *rect,
                              uint32_t *tiles, cudaStream_t s)
 {
     if (n > 0)
-        k_export_gaussians<<<(n + 255) / 256, 256, 0, s>>>(n, slot_base, labels_src, tiles_src, erec_src, rec,
+        k_export_gaussians<<<(n + 255) / 256, 256, 0, s>>>(n, slot_base, labels_src, tiles_src, erec_src, vmask, views, rec,
                                                            depth_src, labels, depth, mean2d, conic, rgb, opacity,
                                                            rect, tiles);
 }

@@ -384,11 +384,16 @@ __global__ void __launch_bounds__(kBlock, 3) k_preprocess(PreprocessArgs a)
                         ntiles = pj.ntiles;
                         rendered = true;
                         cutoff = label == RARA_CUTOFF;
-                        EmitRec er;
-                        er.rect = pj.rect;
-                        er.mx = pj.r0.x; er.my = pj.r0.y; er.ca = pj.r0.z; er.cb = pj.r0.w; er.cc = pj.r1x;
-                        er.qcut = splat_qcut(__log2f(op));
-                        a.erec[slot] = er;
+                        // A shared listing (one-camera batch) reads the emission record of the
+                        // first view that renders the Gaussian only (its lowest view-mask bit),
+                        // and so does the export of any view: the later views write none.
+                        if (!a.vmask || vmask == 0u) {
+                            EmitRec er;
+                            er.rect = pj.rect;
+                            er.mx = pj.r0.x; er.my = pj.r0.y; er.ca = pj.r0.z; er.cb = pj.r0.w; er.cc = pj.r1x;
+                            er.qcut = splat_qcut(__log2f(op));
+                            a.erec[slot] = er;
+                        }
                         SplatRec rec;
                         rec.r0 = pj.r0;
                         rec.r1 = make_float4(pj.r1x, op, pj.rgb0, pj.rgb1);

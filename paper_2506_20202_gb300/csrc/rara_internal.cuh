@@ -64,7 +64,8 @@ struct __align__(16) SplatRec {
 
 // Per-slot emission record, written by the preprocess for rendered slots and gathered in
 // depth order by the emission (so in no particular slot order): what the exact row spans of
-// the slot's q <= q_cut ellipse need, in one 32-byte sector.
+// the slot's q <= q_cut ellipse need, in one 32-byte sector. In a shared listing (one-camera
+// batch) only the first view that renders a Gaussian writes its record.
 //   rect = (tx0 | ty0 << 16, tx1 | ty1 << 16), the tile rectangle in the view
 //   (mx, my) the projected centre, (ca, cb, cc) the conic a, b, c
 //   qcut = splat_qcut(log2 opacity), the support the render culls with
@@ -426,7 +427,8 @@ void launch_loss_l2(const LossView *views, int num_views, uint32_t grid, cudaStr
 
 // Debug exports of one view
 void launch_export_gaussians(int n, uint32_t slot_base, const uint8_t *labels_src, const uint32_t *tiles_src,
-                             const EmitRec *erec_src, const SplatRec *rec, const float *depth_src, uint8_t *labels,
+                             const EmitRec *erec_src, const uint32_t *vmask, const ViewDev *views,
+                             const SplatRec *rec, const float *depth_src, uint8_t *labels,
                              float *depth, float *mean2d, float *conic, float *rgb, float *opacity, int32_t *rect,
                              uint32_t *tiles, cudaStream_t s);
 // Pairs of one view in (local tile, depth) order: tile t's list goes to out_offset[t]
