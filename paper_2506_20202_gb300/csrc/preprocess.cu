@@ -531,10 +531,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_preprocess(PreprocessArgs a)
     if (a.vmask && valid) a.vmask[i] = vmask;
 }
 
-// Compaction of rendered slots in slot order: partitions of 1024 slots (4 per thread,
+// Compaction of rendered slots in slot order: partitions of 4096 slots (16 per thread,
 // consecutive), block prefix by warp scans, global prefix by the chained scan; the 8-bit
 // digit histograms of the depth keys are accumulated on the way.
-constexpr int kCompactItems = 4;
+constexpr int kCompactItems = 16;
 
 __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
 {
