@@ -531,11 +531,16 @@ __global__ void __launch_bounds__(kBlock, 3) k_preprocess(PreprocessArgs a)
     if (a.vmask && valid) a.vmask[i] = vmask;
 }
 
-// Compaction of rendered slots in slot order: partitions of 4096 slots (16 per thread,
-// consecutive), block prefix by warp scans, global prefix by the chained scan; the 8-bit
-// digit histograms of the depth keys are accumulated on the way.
-constexpr int kCompactItems = 16;
+// Compaction of rendered slots in slot order: partitions of 256 x ITEMS slots (ITEMS
+// consecutive ones per thread), block prefix by warp scans, global prefix by the chained scan;
+// the 8-bit digit histograms of the depth keys are accumulated on the way. Large batches take
+// 16 slots per thread (fewer partitions, so fewer block barriers and look-backs), small ones
+// 4 (more partitions to spread over the SMs).
+constexpr int kCompactItemsLarge = 16, kCompactItemsSmall = 4;
+constexpr uint32_t kCompactLargeSlots = 1u << 23;
+constexpr int kExpandItems = 4;
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
 {
     __shared__ uint32_t s_hist[4][256];
@@ -544,24 +549,24 @@ __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
     __shared__ unsigned long long s_prefix;
     for (int t = threadIdx.x; t < 4 * 256; t += kBlock) (&s_hist[0][0])[t] = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t parts = (a.num_slots + kBlock * kCompactItems - 1) / (kBlock * kCompactItems);
+    const uint32_t parts = (a.num_slots + kBlock * ITEMS - 1) / (kBlock * ITEMS);
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_part = atomicAdd(&a.counters->ticket[kTicketCompact], 1u);
         __syncthreads();
         const uint32_t part = s_part;
         if (part >= parts) break;
-        const uint32_t first = part * (kBlock * kCompactItems) + threadIdx.x * kCompactItems;
-        uint32_t key[kCompactItems];
-        bool flag[kCompactItems];
+        const uint32_t first = part * (kBlock * ITEMS) + threadIdx.x * ITEMS;
+        uint32_t key[ITEMS];
+        bool flag[ITEMS];
         unsigned cnt = 0;
         // the thread's consecutive items: 16-byte loads when all are in range (the arrays are
-        // 256-byte aligned and first is a multiple of kCompactItems), else one by one
-        uint32_t tk[kCompactItems], dk[kCompactItems];
-        const bool whole = first + kCompactItems <= a.num_slots;
+        // 256-byte aligned and first is a multiple of ITEMS), else one by one
+        uint32_t tk[ITEMS], dk[ITEMS];
+        const bool whole = first + ITEMS <= a.num_slots;
         const uint32_t *src0 = a.gkey ? a.gkey : a.tiles;
 #pragma unroll
-        for (int q = 0; q < kCompactItems / 4; ++q) {
+        for (int q = 0; q < ITEMS / 4; ++q) {
             uint4 t = make_uint4(0u, 0u, 0u, 0u), d = make_uint4(0u, 0u, 0u, 0u);
             if (whole) {
                 t = __ldg(reinterpret_cast<const uint4 *>(src0 + first) + q);
@@ -572,14 +577,14 @@ __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
         }
         if (!whole) {
 #pragma unroll
-            for (int r = 0; r < kCompactItems; ++r) {
+            for (int r = 0; r < ITEMS; ++r) {
                 const uint32_t slot = first + r;
                 tk[r] = slot < a.num_slots ? src0[slot] : (a.gkey ? kNoKey : 0u);
                 dk[r] = !a.gkey && slot < a.num_slots ? __float_as_uint(a.depth[slot]) : 0u;
             }
         }
 #pragma unroll
-        for (int r = 0; r < kCompactItems; ++r) {
+        for (int r = 0; r < ITEMS; ++r) {
             if (a.gkey) {   // tk: the Gaussian's depth key, or kNoKey
                 flag[r] = tk[r] != kNoKey;
                 key[r] = flag[r] ? tk[r] : 0u;
@@ -621,7 +626,7 @@ __global__ void __launch_bounds__(kBlock) k_compact(CompactArgs a)
         __syncthreads();
         unsigned long long pos = s_prefix + s_warp[warp] + incl - cnt;
 #pragma unroll
-        for (int r = 0; r < kCompactItems; ++r)
+        for (int r = 0; r < ITEMS; ++r)
             if (flag[r]) {
                 a.keys[pos] = key[r];
                 a.vals[pos] = first + r;
@@ -661,21 +666,21 @@ __global__ void __launch_bounds__(kBlock) k_expand(ExpandArgs a)
     uint32_t *out = in_b ? a.out_a : a.out_b;
     const uint64_t nu = a.counters->n_union;
     const uint64_t total_elems = nu * (uint64_t)a.num_views;
-    const uint64_t parts = (total_elems + kBlock * kCompactItems - 1) / (kBlock * kCompactItems);
+    const uint64_t parts = (total_elems + kBlock * kExpandItems - 1) / (kBlock * kExpandItems);
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_part = atomicAdd(&a.counters->ticket[kTicketExpand], 1u);
         __syncthreads();
         const uint32_t part = s_part;
         if (part >= parts) break;
-        const uint64_t first = (uint64_t)part * (kBlock * kCompactItems) + threadIdx.x * kCompactItems;
-        uint32_t slot[kCompactItems];
-        bool flag[kCompactItems];
+        const uint64_t first = (uint64_t)part * (kBlock * kExpandItems) + threadIdx.x * kExpandItems;
+        uint32_t slot[kExpandItems];
+        bool flag[kExpandItems];
         unsigned cnt = 0;
         // element e = v * nu + j: view v, the j-th Gaussian in depth order
         uint64_t v = nu ? first / nu : 0, j = first - v * nu;
 #pragma unroll
-        for (int r = 0; r < kCompactItems; ++r) {
+        for (int r = 0; r < kExpandItems; ++r) {
             flag[r] = false;
             slot[r] = 0u;
             if (first + r < total_elems) {
@@ -711,7 +716,7 @@ __global__ void __launch_bounds__(kBlock) k_expand(ExpandArgs a)
         unsigned long long pos = s_prefix + s_warp[warp] + incl - cnt;
         const unsigned long long cap = a.counters->n_rendered;   // the expansion lists exactly these
 #pragma unroll
-        for (int r = 0; r < kCompactItems; ++r)
+        for (int r = 0; r < kExpandItems; ++r)
             if (flag[r]) {
                 if (pos < cap) out[pos] = slot[r];
                 ++pos;
@@ -745,7 +750,8 @@ void launch_preprocess(const PreprocessArgs &a, int grid, int max_sh_degree, int
 int compact_blocks_per_sm()
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact, kBlock, 0) != cudaSuccess || b < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact<kCompactItemsLarge>, kBlock, 0) != cudaSuccess ||
+        b < 1) {
         cudaGetLastError();
         b = 1;
     }
@@ -754,7 +760,9 @@ int compact_blocks_per_sm()
 
 void launch_compact(const CompactArgs &a, int grid, cudaStream_t s)
 {
-    if (grid > 0) k_compact<<<grid, kBlock, 0, s>>>(a);
+    if (grid <= 0) return;
+    if (a.num_slots >= kCompactLargeSlots) k_compact<kCompactItemsLarge><<<grid, kBlock, 0, s>>>(a);
+    else k_compact<kCompactItemsSmall><<<grid, kBlock, 0, s>>>(a);
 }
 
 }  // namespace rara
