@@ -328,7 +328,9 @@ def stage_hbm(kms, vinfo, scene, W, H, hbm_gbs, depth_keys=None, shared_pairs=0)
     copy bandwidth. Bytes per unit (the design notes list them):
       preprocess   the scene once (44 B of geometry + 12 (L+1)^2 B of SH per Gaussian), 5 B per
                    (view, Gaussian) slot (label, tiles), 84 B per rendered slot (emission
-                   record, splat record, depth), 64 B per cutoff slot (ray-tracing record)
+                   record, splat record, depth; with a shared listing the 32-byte emission
+                   record only once per Gaussian some view renders), 64 B per cutoff slot
+                   (ray-tracing record)
       compaction   8 B per slot read (tiles, depth), 8 B per rendered slot written
       depth sort   16 B per key per digit pass launched (4 depth + 1 view pass over the
                    rendered slots; for a one-camera batch 4 depth passes over the Gaussians some
@@ -352,7 +354,8 @@ def stage_hbm(kms, vinfo, scene, W, H, hbm_gbs, depth_keys=None, shared_pairs=0)
     tile_passes = (tile_bits + 7) // 8
     view_passes = 0 if views == 1 else (1 if views <= 256 else 2)
     bytes_ = {
-        "preprocess": n * (44 + 4 * scene.sh.shape[0]) + 5 * slots + 84 * rendered + 64 * cutoff,
+        "preprocess": n * (44 + 4 * scene.sh.shape[0]) + 5 * slots + 64 * cutoff +
+                      (52 * rendered + 32 * depth_keys if shared_pairs else 84 * rendered),
         "compaction": (8 * slots + 8 * rendered) if depth_keys is None else (4 * n + 8 * depth_keys),
         "depth_sort": 16 * rendered * (4 + view_passes) if depth_keys is None else
                       16 * depth_keys * 4 + (0 if shared_pairs else 8 * views * depth_keys + 4 * rendered),
