@@ -331,6 +331,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_preprocess(PreprocessArgs a)
             if (threadIdx.x < 3 * kViewChunk) (&s_cnt[0][0])[threadIdx.x] = 0ull;
         }
         __syncthreads();
+        uint32_t cmask = 0;  // the chunk's views that label this Gaussian cutoff
         for (int vv = 0; vv < nv; ++vv) {
             const ViewDev &vw = s_views[vv];
             const PlaneDev &pl = vw.plane;
@@ -400,7 +401,43 @@ __global__ void __launch_bounds__(kBlock, 3) k_preprocess(PreprocessArgs a)
                         float wmode = 0.0f;
                         a.depth[slot] = pj.depth;
                         ukey = __float_as_uint(pj.depth);
-                    if (cutoff) {
+                    if (cutoff) cmask |= 1u << vv;  // its ray-tracing record comes after the views
+
+                        rec.r2 = make_float4(pj.rgb2, wmode, pj.nbc, pj.nba);
+                        a.rec[slot] = rec;
+                    }
+                }
+                a.tiles[slot] = ntiles;
+                const int vbit = vbase - sc.view_begin + vv;
+                if (rendered && vbit < kListViews) vmask |= 1u << vbit;
+            }
+            // per-view counts: warp sums, then one shared-memory add per warp
+            const unsigned nr = __reduce_add_sync(0xffffffffu, rendered ? 1u : 0u);
+            const unsigned nc = __reduce_add_sync(0xffffffffu, cutoff ? 1u : 0u);
+            unsigned long long np = ntiles;
+            for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(0xffffffffu, np, o);
+            if (lane == 0) {
+                if (nr) atomicAdd(&s_cnt[0][vv], (unsigned long long)nr);
+                if (np) atomicAdd(&s_cnt[1][vv], np);
+                if (nc) atomicAdd(&s_cnt[2][vv], (unsigned long long)nc);
+            }
+        }
+        // Ray-tracing records of the cutoff slots, in rounds: every lane takes its own next
+        // cutoff view of the chunk, so the record's arithmetic runs for the lanes that need it
+        // instead of for every lane of a warp in which one lane is cutoff. The splat record
+        // written above gets the weight mode.
+        while (__any_sync(0xffffffffu, cmask != 0u)) {
+            const bool has = cmask != 0u;
+            const int vv = has ? __ffs(cmask) - 1 : 0;
+            cmask &= cmask - 1u;
+            if (has) {
+                const ViewDev &vw = s_views[vv];
+                const PlaneDev &pl = vw.plane;
+                const CamDev &cam = vw.cam;
+                const uint32_t slot = vw.slot_base + (uint32_t)i;
+                const float dep = fmaf(pl.n[0], mx, fmaf(pl.n[1], my, fmaf(pl.n[2], mz, pl.d)));
+                float wmode = kWeightNone;
+                {
                         // the camera-space centre and the eye offset again (not cached)
                         const float tz = fmaf(cam.R[6], mx, fmaf(cam.R[7], my, fmaf(cam.R[8], mz, cam.t[2])));
                         const float ex = mx - cam.eye[0], ey = my - cam.eye[1], ez = mz - cam.eye[2];
@@ -495,23 +532,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_preprocess(PreprocessArgs a)
                             }
                         }
                     }
-                        rec.r2 = make_float4(pj.rgb2, wmode, pj.nbc, pj.nba);
-                        a.rec[slot] = rec;
-                    }
-                }
-                a.tiles[slot] = ntiles;
-                const int vbit = vbase - sc.view_begin + vv;
-                if (rendered && vbit < kListViews) vmask |= 1u << vbit;
-            }
-            // per-view counts: warp sums, then one shared-memory add per warp
-            const unsigned nr = __reduce_add_sync(0xffffffffu, rendered ? 1u : 0u);
-            const unsigned nc = __reduce_add_sync(0xffffffffu, cutoff ? 1u : 0u);
-            unsigned long long np = ntiles;
-            for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(0xffffffffu, np, o);
-            if (lane == 0) {
-                if (nr) atomicAdd(&s_cnt[0][vv], (unsigned long long)nr);
-                if (np) atomicAdd(&s_cnt[1][vv], np);
-                if (nc) atomicAdd(&s_cnt[2][vv], (unsigned long long)nc);
+                a.rec[slot].r2.y = wmode;
             }
         }
         __syncthreads();
