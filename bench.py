@@ -722,7 +722,20 @@ def run_training(args, rank=0, world=1):
         best, tune_ms = autotune.parse(args.tuning), {}
         autotune.apply(ctx, best)
     else:
-        best, tune_ms = autotune.autotune(ctx, [gs], views, stream, reps=2)
+        # the tiling serves the backward too: tune on the forward + loss + backward of the views
+        def step_ms(reps):
+            local(mine)                                   # capture the forward's graph
+            torch.cuda.synchronize()
+            times = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(torch.cuda.current_stream())
+                local(mine)
+                e1.record(torch.cuda.current_stream())
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            return statistics.median(times)
+        best, tune_ms = autotune.autotune(ctx, [gs], views, stream, reps=2, timer=step_ms)
     grads = local.grads
     # Adam on the Gaussians' own storage (nn.Parameter shares it), gradients from the backward
     params = [torch.nn.Parameter(t) for t in (gs.means, gs.log_scales, gs.quats, gs.opacity_logits, gs.sh)]

@@ -74,12 +74,14 @@ def time_batch(ctx, scenes, views, stream, reps: int = 5) -> float:
 
 
 def autotune(ctx, scenes, views, stream=None, reps: int = 5, tiles=None, depths=None, candidates=None,
-             cache_path: str | None = None):
+             cache_path: str | None = None, timer=None):
     """Pick the fastest (tile_w, tile_h, depth, split2_bits, split4_bits) for this batch and
     set it on ctx.
 
     Returns (best, {setting: ms}). With cache_path, a stored choice for the same device and
-    batch shape is reused without timing, and a new choice is stored."""
+    batch shape is reused without timing, and a new choice is stored. timer(reps), if given,
+    times the candidate instead of the batch's graph replay (milliseconds): for example a
+    whole differentiation step, whose backward runs on the forward's tiles too."""
     import torch
     stream = stream or torch.cuda.current_stream()
     key = _shape_key(scenes, views)
@@ -96,7 +98,7 @@ def autotune(ctx, scenes, views, stream=None, reps: int = 5, tiles=None, depths=
     def trial(setting):
         if setting not in results:
             apply(ctx, setting)
-            results[setting] = time_batch(ctx, scenes, views, stream, reps)
+            results[setting] = timer(reps) if timer else time_batch(ctx, scenes, views, stream, reps)
         return results[setting]
 
     best = DEFAULT
